@@ -1,0 +1,266 @@
+/*
+ * gace.h -- C ABI of libgace, the GPU probe engine of GACE on GB300 (sm_103a).
+ *
+ * GACE (I.-S. Chang, "Risk-Aware GPU-Assisted Cardinality Estimation for
+ * Cost-Based Query Optimizers", arXiv 2512.19750) pairs a Risky Gate with a
+ * Measurement Engine that measures, on the GPU, the selectivity and the
+ * distribution of an optimizer's candidate conditions (Section III-B) using
+ * full scans, sampling and block-level summaries.  This library is that
+ * measurement path over device-resident columnar tables:
+ *
+ *   gace_probe_batch  counts of conjunctive EQ / RANGE / IN predicates over the
+ *                     full table, a seeded row sample or a seeded block sample,
+ *                     with per-term marginals and the PCS signal (Eq. 3);
+ *   gace_ndv          HyperLogLog registers and NDV estimate of a column (the
+ *                     NDV_est of the drift signal, Eq. 1);
+ *   gace_join_card    exact join cardinality of two filtered tables (and a
+ *                     three-table chain) as the dot product of filtered
+ *                     key-frequency histograms (join workload, Section IV-F).
+ *
+ * Conventions for every call:
+ *   - The return value is a gace_status; nothing aborts or exits.  On an error
+ *     the outputs are left untouched and gace_last_error() describes it.
+ *   - Caller-provided output arrays are HOST memory.
+ *   - A context serialises its calls on its own CUDA stream; calls on one
+ *     context from several threads are safe (they take a lock).
+ *   - Counts are exact unsigned 64-bit integers.  Doubles derived from them
+ *     (selectivity, PCS) come from one IEEE expression each, stated below.
+ */
+#ifndef GACE_H
+#define GACE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GACE_ABI_VERSION 1
+
+typedef enum {
+    GACE_OK = 0,
+    GACE_EINVAL = 1,    /* an argument is invalid (message in gace_last_error) */
+    GACE_ENOMEM = 2,    /* device or pinned memory exhausted, or HBM budget exceeded */
+    GACE_EBUSY = 3,     /* a queue is full */
+    GACE_EPENDING = 4,  /* the result is not ready yet */
+    GACE_ETIMEDOUT = 5, /* a device-side wait gave up after the context's wait limit */
+    GACE_ENOTFOUND = 6, /* unknown table id or ticket */
+    GACE_EOVERFLOW = 7, /* a join cardinality could exceed 2^63 - 1 */
+    GACE_ECUDA = 8      /* a CUDA runtime call failed (no GPU, launch error, ...) */
+} gace_status;
+
+typedef enum { GACE_I32 = 0, GACE_I64 = 1, GACE_F32 = 2 } gace_dtype;
+typedef enum { GACE_EQ = 0, GACE_RANGE = 1, GACE_IN = 2 } gace_op;
+typedef enum { GACE_FULL = 0, GACE_ROWS = 1, GACE_BLOCKS = 2 } gace_sample_kind;
+typedef enum { GACE_COPY = 0, GACE_BORROW = 1 } gace_load_flags;
+
+typedef struct gace_ctx gace_ctx;
+
+/* A constant: integer columns read .i, float32 columns read .f. */
+typedef union {
+    int64_t i;
+    double f;
+} gace_scalar;
+
+typedef struct {
+    int32_t device;            /* CUDA device ordinal */
+    uint32_t wait_timeout_ms;  /* limit of every device-side wait; 0 selects 2000 ms */
+    uint64_t hbm_budget_bytes; /* device bytes the context may hold (tables it copies,
+                                  workspaces); 0 = no limit */
+    void* stream;              /* cudaStream_t for all work; NULL = a private
+                                  non-blocking stream */
+} gace_config;
+
+/* One column of a table: nrows elements of dtype, densely packed. */
+typedef struct {
+    int32_t dtype;      /* gace_dtype */
+    int32_t on_device;  /* 1: data is a device pointer; 0: host pointer */
+    const void* data;
+} gace_column;
+
+/*
+ * A candidate condition on one column (Section III-B):
+ *   GACE_EQ     x == a
+ *   GACE_RANGE  a <= x < b                        (half-open; a >= b matches nothing)
+ *   GACE_IN     x equals one of in_values[in_off .. in_off + in_len)
+ * Integer columns compare exact integers (a constant outside the column's
+ * range simply matches nothing).  Float32 columns compare the value, widened
+ * to double, with double constants under IEEE rules: NaN matches nothing and
+ * -0 equals +0.  in_len is 1..4096.
+ */
+typedef struct {
+    uint32_t col;
+    uint32_t op;        /* gace_op */
+    gace_scalar a;
+    gace_scalar b;
+    uint32_t in_off;
+    uint32_t in_len;
+} gace_term;
+
+/* A predicate is the conjunction of terms[term_off .. term_off + term_cnt);
+ * term_cnt == 0 matches every row. */
+typedef struct {
+    uint32_t term_off;
+    uint32_t term_cnt;
+} gace_pred;
+
+/*
+ * The rows a probe counts over (dynamic sampling, Sections II-A and III-B):
+ *   GACE_FULL    every row.
+ *   GACE_ROWS    row i (0-based, table-global) is kept iff H(i, seed) < T(rate).
+ *   GACE_BLOCKS  block b = floor(i / block_rows) is kept iff H(b, seed) < T(rate);
+ *                all rows of a kept block count (the last block may be short).
+ * H(x, s) = splitmix64(x XOR splitmix64(s)) with the splitmix64 output function
+ * of Steele, Lea & Flood (OOPSLA 2014).  T(rate) = floor(rate * 2^64); rate <= 0
+ * keeps nothing and rate >= 1 keeps everything.  Samples are nested in rate.
+ */
+typedef struct {
+    uint32_t kind;        /* gace_sample_kind */
+    uint32_t block_rows;  /* GACE_BLOCKS: rows per block, >= 1 */
+    double rate;
+    uint64_t seed;
+} gace_sample;
+
+/*
+ * Result of one predicate on one row set:
+ *   match        rows of the set on which every term holds
+ *   sample_rows  rows in the set
+ *   sel          match / sample_rows as doubles (0 when sample_rows == 0)
+ *   pcs          for a predicate of exactly two terms A and B:
+ *                (double)c_AB * (double)n / ((double)c_A * (double)c_B),
+ *                with n = sample_rows and c_A, c_B the terms' marginal counts on
+ *                the same set (PCS = P(A,B)/(P(A)P(B)), Section III-C, Eq. 3);
+ *                NaN for other predicates or when c_A or c_B is zero.
+ */
+typedef struct {
+    uint64_t match;
+    uint64_t sample_rows;
+    double sel;
+    double pcs;
+} gace_pred_result;
+
+/* Creates a context on cfg->device (cfg may be NULL: device 0, defaults).
+ * Fails with GACE_ECUDA when no usable GPU is present. */
+gace_status gace_create(gace_ctx** out, const gace_config* cfg);
+
+/* Frees every table the context copied and every workspace.  NULL is a no-op. */
+gace_status gace_destroy(gace_ctx* ctx);
+
+/*
+ * Registers a table of nrows rows and ncols (1..64) columns.
+ * flags == GACE_COPY: the context copies each column (host or device source)
+ *   into device memory it owns, 256-byte aligned; counted against the budget.
+ * flags == GACE_BORROW: the context keeps the device pointers; the caller keeps
+ *   them alive and unchanged until gace_unload.  Every column must be on_device.
+ * The probe reads each column with 16-byte bulk copies when its base address is
+ * 16-byte aligned, and with plain loads otherwise (same results, slower).
+ */
+gace_status gace_load_columns(gace_ctx* ctx, uint64_t nrows, uint32_t ncols,
+                              const gace_column* cols, uint32_t flags,
+                              uint32_t* table_id_out);
+
+/* Forgets a table (frees its copies when it was loaded with GACE_COPY). */
+gace_status gace_unload(gace_ctx* ctx, uint32_t table_id);
+
+/*
+ * Measurement Engine probe (Section III-B; Key-Only + Bitmask evaluation,
+ * Section IV-I): one fused pass over the referenced columns evaluates every
+ * predicate on every requested row set.
+ *   samples[nsamples]   1..8 row sets
+ *   terms[nterms]       the terms the predicates index; identical terms are
+ *                       evaluated once
+ *   in_values[nin]      IN lists
+ *   preds[npreds]       conjunctions
+ *   results             out, nsamples * npreds entries, results[s * npreds + p]
+ *   term_marginals      out or NULL, nsamples * nterms entries: rows of set s
+ *                       on which term t holds
+ */
+gace_status gace_probe_batch(gace_ctx* ctx, uint32_t table_id,
+                             const gace_sample* samples, uint32_t nsamples,
+                             const gace_term* terms, uint32_t nterms,
+                             const gace_scalar* in_values, uint32_t nin,
+                             const gace_pred* preds, uint32_t npreds,
+                             gace_pred_result* results, uint64_t* term_marginals);
+
+/*
+ * HyperLogLog NDV of one column (the NDV_est of the drift signal D, Eq. 1;
+ * sketch of Flajolet, Fusy, Gandouet & Meunier, AofA 2007) with m = 2^p
+ * registers, p in 4..18.  Each value's canonical 64-bit key (int32
+ * sign-extended, int64 as is, float32 bit pattern zero-extended after mapping
+ * -0 to +0 and every NaN to 0x7FC00000) is hashed h = H(key, hash_seed);
+ * register j = top p bits of h; rho = 1-based position of the leftmost 1 in
+ * the remaining 64 - p bits (64 - p + 1 if they are all zero); M[j] = max rho.
+ *   registers_out  out or NULL, 2^p bytes
+ *   estimate_out   out or NULL: alpha_m m^2 / sum_j 2^-M[j] (alpha_m = 0.673,
+ *                  0.697, 0.709 for m = 16, 32, 64, else 0.7213/(1 + 1.079/m)),
+ *                  replaced by m ln(m / V) when it is <= 2.5 m and V, the number
+ *                  of zero registers, is positive.
+ */
+gace_status gace_ndv(gace_ctx* ctx, uint32_t table_id, uint32_t col, uint32_t p,
+                     uint64_t hash_seed, uint8_t* registers_out, double* estimate_out);
+
+/* One side of a join: a table, its key column (int32 or int64) and a
+ * conjunctive filter (nterms may be 0). */
+typedef struct {
+    uint32_t table_id;
+    uint32_t key_col;
+    const gace_term* terms;
+    uint32_t nterms;
+    uint32_t nin;
+    const gace_scalar* in_values;
+} gace_join_side;
+
+typedef enum { GACE_JOIN_AUTO = 0, GACE_JOIN_HIST_DOT = 1, GACE_JOIN_GATHER = 2 } gace_join_method;
+
+/*
+ * Join cardinality (the join-correlation failures of Sections I and IV-F):
+ *   hops == 1:  J = |sigma(fact) JOIN_{fact.key = dim.key} sigma(dim)|
+ *             = sum_k h_F[k] * h_D[k] over k in [0, key_domain), where h_X[k]
+ *               counts the filtered rows of X whose key equals k.
+ *   hops == 2:  chain fact -> dim -> dim2 through dim's column dim_fk2_col:
+ *               J = sum_k h_F[k] * w[k], w[k] = sum over filtered dim rows d
+ *               with d.key = k of h_D2[d.fk2], h_D2 over [0, key_domain2).
+ * Every filtered dim (and dim2) row must have its key inside its domain, else
+ * GACE_EINVAL; fact (and dim.fk2) keys outside the domain match nothing.
+ * GACE_EOVERFLOW when fact_rows * max_k h_D[k] >= 2^63 (hops == 1), or when
+ * dim_rows * max h_D2 >= 2^63 or fact_rows * max_k w[k] >= 2^63 (hops == 2).
+ * A histogrammed side must have fewer than 2^32 rows.
+ * method: GACE_JOIN_HIST_DOT builds both histograms and takes their dot
+ * product; GACE_JOIN_GATHER builds h_D (or w) only and sums h_D[fact.key] over
+ * the filtered fact rows, the same integer; GACE_JOIN_AUTO picks.
+ */
+typedef struct {
+    gace_join_side fact;
+    gace_join_side dim;
+    uint64_t key_domain;
+    gace_join_side dim2;
+    uint64_t key_domain2;
+    uint32_t dim_fk2_col;
+    uint32_t hops;      /* 1 or 2 */
+    uint32_t method;    /* gace_join_method */
+    uint32_t reserved;
+} gace_join;
+
+typedef struct {
+    int64_t card;       /* join cardinality */
+    uint64_t fact_rows; /* fact rows passing the fact filter */
+    uint64_t dim_rows;  /* dim rows passing the dim filter */
+    uint64_t dim2_rows; /* dim2 rows passing the dim2 filter (hops == 2) */
+} gace_join_result;
+
+gace_status gace_join_card(gace_ctx* ctx, const gace_join* spec, gace_join_result* out);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* gace_last_error(void);
+
+/* Name of a status code. */
+const char* gace_status_string(gace_status s);
+
+/* GACE_ABI_VERSION of the loaded library; needs no GPU. */
+uint32_t gace_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GACE_H */

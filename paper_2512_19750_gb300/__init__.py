@@ -1,0 +1,216 @@
+"""Python binding of libgace, the GB300 probe engine of GACE (arXiv 2512.19750).
+
+Same names as the C ABI (include/gace.h); this layer only marshals Python
+descriptions (workloads.Term / workloads.Sample, torch tensors, numpy arrays)
+into the C structures.  Every step of the probe runs in the library's CUDA
+kernels: nothing here computes a result, and there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _capi
+from ._capi import (GACE_BLOCKS, GACE_BORROW, GACE_COPY, GACE_EQ, GACE_F32, GACE_FULL, GACE_I32,
+                    GACE_I64, GACE_IN, GACE_JOIN_AUTO, GACE_JOIN_GATHER, GACE_JOIN_HIST_DOT,
+                    GACE_OK, GACE_RANGE, GACE_ROWS, GaceError, check, lib)
+
+RESULT_DTYPE = np.dtype([("match", "<u8"), ("sample_rows", "<u8"), ("sel", "<f8"), ("pcs", "<f8")])
+_NP_OF = {GACE_I32: np.int32, GACE_I64: np.int64, GACE_F32: np.float32}
+
+
+def _dtype_code(x) -> int:
+    name = str(getattr(x, "dtype", x))
+    if "int32" in name:
+        return GACE_I32
+    if "int64" in name:
+        return GACE_I64
+    if "float32" in name:
+        return GACE_F32
+    raise ValueError(f"unsupported column dtype {name}")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+# ----------------------------------------------------------------- marshalling
+
+class TermBatch:
+    """C arrays of a predicate batch: gace_term, gace_pred and in_values."""
+
+    def __init__(self, preds, dtypes):
+        flat = [t for p in preds for t in p]
+        self.nterms = len(flat)
+        self.npreds = len(preds)
+        self.terms = (_capi.gace_term * max(1, self.nterms))()
+        self.preds = (_capi.gace_pred * max(1, self.npreds))()
+        ins = []
+        for k, t in enumerate(flat):
+            s = self.terms[k]
+            s.col, s.op = int(t.col), int(t.op)
+            isf = 0 <= t.col < len(dtypes) and dtypes[t.col] == GACE_F32
+            if t.op == GACE_IN:
+                s.in_off, s.in_len = len(ins), len(t.values)
+                ins.extend((isf, v) for v in t.values)
+            elif isf:
+                s.a.f, s.b.f = float(t.a), float(t.b)
+            else:
+                s.a.i, s.b.i = int(t.a), int(t.b)
+        self.nin = len(ins)
+        self.in_values = (_capi.gace_scalar * max(1, self.nin))()
+        for k, (isf, v) in enumerate(ins):
+            if isf:
+                self.in_values[k].f = float(v)
+            else:
+                self.in_values[k].i = int(v)
+        off = 0
+        for k, p in enumerate(preds):
+            self.preds[k].term_off, self.preds[k].term_cnt = off, len(p)
+            off += len(p)
+
+
+def _samples(samples):
+    arr = (_capi.gace_sample * max(1, len(samples)))()
+    for k, s in enumerate(samples):
+        arr[k].kind = int(s.kind)
+        arr[k].block_rows = int(s.block_rows)
+        arr[k].rate = float(s.rate)
+        arr[k].seed = int(s.seed) & ((1 << 64) - 1)
+    return arr
+
+
+# ----------------------------------------------------------------- ABI wrappers
+
+def gace_abi_version() -> int:
+    return int(lib().gace_abi_version())
+
+
+def gace_create(device: int = 0, stream=None, hbm_budget_bytes: int = 0,
+                wait_timeout_ms: int = 0) -> int:
+    cfg = _capi.gace_config(device, wait_timeout_ms, hbm_budget_bytes, _stream_handle(stream))
+    out = C.c_void_p()
+    check(lib().gace_create(C.byref(out), C.byref(cfg)), "gace_create")
+    return out.value
+
+
+def gace_destroy(ctx) -> None:
+    check(lib().gace_destroy(ctx), "gace_destroy")
+
+
+def gace_load_columns(ctx, columns, borrow: bool = False) -> int:
+    """Registers a table; columns are torch tensors (CUDA or CPU) or numpy
+    arrays, all of one length.  borrow=True keeps the device pointers."""
+    n = len(columns)
+    arr = (_capi.gace_column * n)()
+    keep = []
+    nrows = None
+    for k, c in enumerate(columns):
+        if hasattr(c, "data_ptr"):
+            if not c.is_contiguous():
+                raise ValueError("column tensors must be contiguous")
+            arr[k].dtype = _dtype_code(c.dtype)
+            arr[k].on_device = 1 if c.is_cuda else 0
+            arr[k].data = c.data_ptr() if c.numel() else None
+            rows = int(c.shape[0])
+        else:
+            a = np.ascontiguousarray(c)
+            keep.append(a)
+            arr[k].dtype = _dtype_code(a.dtype)
+            arr[k].on_device = 0
+            arr[k].data = a.ctypes.data if a.size else None
+            rows = int(a.shape[0])
+        if nrows is None:
+            nrows = rows
+        elif rows != nrows:
+            raise ValueError("columns differ in length")
+    tid = C.c_uint32()
+    check(lib().gace_load_columns(ctx, nrows or 0, n, arr, GACE_BORROW if borrow else GACE_COPY,
+                                  C.byref(tid)), "gace_load_columns")
+    return int(tid.value)
+
+
+def gace_unload(ctx, table_id: int) -> None:
+    check(lib().gace_unload(ctx, table_id), "gace_unload")
+
+
+def gace_probe_batch(ctx, table_id: int, preds, samples, dtypes, marginals: bool = False,
+                     batch: TermBatch | None = None):
+    """Counts of conjunctive predicates on each row set.
+
+    Returns (results, term_marginals): results is a structured array of shape
+    (len(samples), len(preds)) with fields match, sample_rows, sel, pcs;
+    term_marginals is (len(samples), nterms) uint64 or None."""
+    b = batch or TermBatch(preds, dtypes)
+    smp = _samples(samples)
+    res = np.zeros((len(samples), b.npreds), dtype=RESULT_DTYPE)
+    marg = np.zeros((len(samples), b.nterms), dtype=np.uint64) if marginals else None
+    rc = lib().gace_probe_batch(
+        ctx, table_id, smp, len(samples), b.terms, b.nterms, b.in_values, b.nin, b.preds, b.npreds,
+        res.ctypes.data_as(C.POINTER(_capi.gace_pred_result)),
+        marg.ctypes.data_as(C.POINTER(C.c_uint64)) if marginals and b.nterms else None)
+    check(rc, "gace_probe_batch")
+    return res, marg
+
+
+def gace_ndv(ctx, table_id: int, col: int, p: int, hash_seed: int):
+    """(registers uint8[2^p], estimate) of HyperLogLog on one column."""
+    regs = np.zeros(1 << p, dtype=np.uint8)
+    est = C.c_double()
+    check(lib().gace_ndv(ctx, table_id, col, p, int(hash_seed) & ((1 << 64) - 1),
+                         regs.ctypes.data_as(C.POINTER(C.c_uint8)), C.byref(est)), "gace_ndv")
+    return regs, float(est.value)
+
+
+class JoinSideSpec:
+    """(table_id, key column, filter terms, column dtypes) of one join side."""
+
+    def __init__(self, table_id: int, key_col: int, terms=(), dtypes=()):
+        self.table_id, self.key_col = table_id, key_col
+        self.batch = TermBatch([list(terms)], list(dtypes))
+
+    def fill(self, s: _capi.gace_join_side):
+        s.table_id, s.key_col = self.table_id, self.key_col
+        s.terms = C.cast(self.batch.terms, C.POINTER(_capi.gace_term))
+        s.nterms = self.batch.nterms
+        s.in_values = C.cast(self.batch.in_values, C.POINTER(_capi.gace_scalar))
+        s.nin = self.batch.nin
+
+
+def gace_join_card(ctx, fact: JoinSideSpec, dim: JoinSideSpec, key_domain: int,
+                   dim2: JoinSideSpec | None = None, key_domain2: int = 0, dim_fk2_col: int = 0,
+                   method: int = GACE_JOIN_AUTO):
+    """dict(card, fact_rows, dim_rows, dim2_rows) of the (chain) join."""
+    spec = _capi.gace_join()
+    fact.fill(spec.fact)
+    dim.fill(spec.dim)
+    spec.key_domain = key_domain
+    if dim2 is not None:
+        dim2.fill(spec.dim2)
+        spec.key_domain2 = key_domain2
+        spec.dim_fk2_col = dim_fk2_col
+        spec.hops = 2
+    else:
+        spec.hops = 1
+    spec.method = method
+    out = _capi.gace_join_result()
+    check(lib().gace_join_card(ctx, C.byref(spec), C.byref(out)), "gace_join_card")
+    return {"card": int(out.card), "fact_rows": int(out.fact_rows), "dim_rows": int(out.dim_rows),
+            "dim2_rows": int(out.dim2_rows)}
+
+
+def gace_last_error() -> str:
+    return lib().gace_last_error().decode()
+
+
+def gace_status_string(s: int) -> str:
+    return lib().gace_status_string(s).decode()
+
+
+__all__ = [n for n in dir() if n.startswith(("gace_", "GACE_"))] + [
+    "GaceError", "JoinSideSpec", "RESULT_DTYPE", "TermBatch", "check", "lib"]

@@ -1,0 +1,1163 @@
+// gace_capi.cpp -- host runtime behind the C ABI of include/gace.h.
+//
+// A context owns one CUDA stream, the tables registered on it, a device
+// workspace and a pinned host staging buffer, all accounted against an HBM
+// budget.  Every entry point validates its arguments, compiles its request
+// into the kernels' compact forms (normalised terms, deduplicated, grouped by
+// column), launches on the context stream, reads back the integer results and
+// derives the doubles on the host.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <limits>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/gace.h"
+#include "gace_internal.h"
+
+using namespace gace;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+gace_status fail(gace_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+gace_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(GACE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call)                                           \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+// splitmix64 output function (Steele, Lea & Flood, OOPSLA 2014), host side.
+uint64_t splitmix64_host(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+uint32_t dtype_width(int dt) { return dt == GACE_I64 ? 8u : 4u; }
+
+uint64_t round_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+struct ColumnRec {
+    int dtype = 0;
+    void* dptr = nullptr;
+    bool owned = false;
+    uint64_t bytes = 0;
+};
+
+struct TableRec {
+    uint64_t nrows = 0;
+    std::vector<ColumnRec> cols;
+    uint64_t owned_bytes = 0;
+};
+
+}  // namespace
+
+struct gace_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int sms = 0;
+    int smem_optin = 0;
+    uint64_t budget = 0;       // 0 = unlimited
+    uint64_t used = 0;         // owned tables + workspace + pinned
+    uint64_t timeout_ns = 2000ull * 1000000ull;
+    std::mutex mu;
+    std::unordered_map<uint32_t, TableRec> tables;
+    uint32_t next_id = 1;
+    unsigned char* ws = nullptr;  // device workspace
+    uint64_t ws_cap = 0;
+    unsigned char* pin = nullptr;  // pinned host staging
+    uint64_t pin_cap = 0;
+    unsigned int* d_status = nullptr;
+
+    bool fits(uint64_t extra) const { return budget == 0 || used + extra <= budget; }
+
+    gace_status ensure_ws(uint64_t bytes) {
+        bytes = round_up(bytes ? bytes : 256, 1 << 20);
+        if (bytes <= ws_cap) return GACE_OK;
+        if (!fits(bytes - ws_cap))
+            return fail(GACE_ENOMEM, "workspace of %llu bytes exceeds the HBM budget",
+                        (unsigned long long)bytes);
+        CK(cudaStreamSynchronize(stream));
+        if (ws) {
+            cudaFree(ws);
+            used -= ws_cap;
+            ws = nullptr;
+            ws_cap = 0;
+        }
+        cudaError_t e = cudaMalloc(&ws, bytes);
+        if (e != cudaSuccess) {
+            ws = nullptr;
+            return fail(GACE_ENOMEM, "cudaMalloc(%llu) for the workspace: %s",
+                        (unsigned long long)bytes, cudaGetErrorString(e));
+        }
+        ws_cap = bytes;
+        used += bytes;
+        return GACE_OK;
+    }
+
+    gace_status ensure_pin(uint64_t bytes) {
+        bytes = round_up(bytes ? bytes : 256, 1 << 16);
+        if (bytes <= pin_cap) return GACE_OK;
+        CK(cudaStreamSynchronize(stream));
+        if (pin) {
+            cudaFreeHost(pin);
+            pin = nullptr;
+            pin_cap = 0;
+        }
+        cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&pin), bytes, cudaHostAllocDefault);
+        if (e != cudaSuccess) {
+            pin = nullptr;
+            return fail(GACE_ENOMEM, "cudaHostAlloc(%llu): %s", (unsigned long long)bytes,
+                        cudaGetErrorString(e));
+        }
+        pin_cap = bytes;
+        return GACE_OK;
+    }
+};
+
+namespace {
+
+// ---------------------------------------------------------------- terms
+
+struct NTerm {
+    uint32_t col = 0;
+    uint32_t kind = kFalse;
+    uint64_t a = 0, b = 0;
+    std::vector<uint32_t> in;  // pool words
+    bool operator<(const NTerm& o) const {
+        return std::tie(col, kind, a, b, in) < std::tie(o.col, o.kind, o.a, o.b, o.in);
+    }
+};
+
+uint32_t fbits(float f) {
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    return u;
+}
+
+// Smallest float >= x, and largest float < x (x a finite or infinite double).
+float float_at_or_above(double x) {
+    float f = static_cast<float>(x);
+    if (static_cast<double>(f) < x) f = std::nextafter(f, std::numeric_limits<float>::infinity());
+    return f;
+}
+float float_below(double x) {
+    float f = static_cast<float>(x);
+    if (static_cast<double>(f) >= x) f = std::nextafter(f, -std::numeric_limits<float>::infinity());
+    return f;
+}
+
+// Normalises a term on a column of dtype into an inclusive interval or a
+// deduplicated IN list in the column's own domain (or kFalse).
+gace_status normalize_term(const gace_term& t, int dtype, const gace_scalar* in_values,
+                           uint32_t nin, NTerm& out) {
+    out = NTerm();
+    out.col = t.col;
+    if (t.op > GACE_IN) return fail(GACE_EINVAL, "term op %u is not EQ/RANGE/IN", t.op);
+    if (t.op == GACE_IN) {
+        if (t.in_len == 0 || t.in_len > 4096)
+            return fail(GACE_EINVAL, "IN list length %u outside 1..4096", t.in_len);
+        if ((uint64_t)t.in_off + t.in_len > nin || in_values == nullptr)
+            return fail(GACE_EINVAL, "IN list [%u, %u) outside in_values[%u]", t.in_off,
+                        t.in_off + t.in_len, nin);
+    }
+    if (dtype == GACE_I32 || dtype == GACE_I64) {
+        const int64_t lo_lim = dtype == GACE_I32 ? INT32_MIN : INT64_MIN;
+        const int64_t hi_lim = dtype == GACE_I32 ? INT32_MAX : INT64_MAX;
+        const uint32_t rk = dtype == GACE_I32 ? kRangeI32 : kRangeI64;
+        auto set_range = [&](int64_t lo, int64_t hi) {  // inclusive, lo <= hi
+            out.kind = rk;
+            out.a = static_cast<uint64_t>(lo);
+            out.b = static_cast<uint64_t>(hi) - static_cast<uint64_t>(lo);
+            if (dtype == GACE_I32) {
+                out.a &= 0xFFFFFFFFull;
+                out.b &= 0xFFFFFFFFull;
+            }
+        };
+        if (t.op == GACE_EQ) {
+            const int64_t v = t.a.i;
+            if (v < lo_lim || v > hi_lim) return GACE_OK;  // kFalse
+            set_range(v, v);
+        } else if (t.op == GACE_RANGE) {
+            const int64_t lo = t.a.i, hi = t.b.i;
+            if (lo >= hi) return GACE_OK;
+            const int64_t l = std::max(lo, lo_lim);
+            const int64_t h = std::min(hi - 1, hi_lim);
+            if (l > h) return GACE_OK;
+            set_range(l, h);
+        } else {
+            std::vector<int64_t> v;
+            for (uint32_t k = 0; k < t.in_len; ++k) {
+                const int64_t x = in_values[t.in_off + k].i;
+                if (x >= lo_lim && x <= hi_lim) v.push_back(x);
+            }
+            std::sort(v.begin(), v.end());
+            v.erase(std::unique(v.begin(), v.end()), v.end());
+            if (v.empty()) return GACE_OK;
+            if (v.size() == 1) {
+                set_range(v[0], v[0]);
+            } else {
+                out.kind = dtype == GACE_I32 ? kInI32 : kInI64;
+                for (int64_t x : v) {
+                    out.in.push_back(static_cast<uint32_t>(static_cast<uint64_t>(x)));
+                    if (dtype == GACE_I64)
+                        out.in.push_back(static_cast<uint32_t>(static_cast<uint64_t>(x) >> 32));
+                }
+            }
+        }
+        return GACE_OK;
+    }
+    // float32 column, double constants compared exactly
+    if (t.op == GACE_EQ) {
+        const double v = t.a.f;
+        if (std::isnan(v)) return GACE_OK;
+        const float f = static_cast<float>(v);
+        if (static_cast<double>(f) != v) return GACE_OK;
+        out.kind = kRangeF32;
+        out.a = out.b = fbits(f);
+    } else if (t.op == GACE_RANGE) {
+        const double lo = t.a.f, hi = t.b.f;
+        if (std::isnan(lo) || std::isnan(hi) || !(lo < hi)) return GACE_OK;
+        const float fl = float_at_or_above(lo), fh = float_below(hi);
+        if (!(fl <= fh)) return GACE_OK;
+        out.kind = kRangeF32;
+        out.a = fbits(fl);
+        out.b = fbits(fh);
+    } else {
+        std::vector<uint32_t> v;
+        for (uint32_t k = 0; k < t.in_len; ++k) {
+            const double x = in_values[t.in_off + k].f;
+            if (std::isnan(x)) continue;
+            float f = static_cast<float>(x);
+            if (static_cast<double>(f) != x) continue;
+            if (f == 0.0f) f = 0.0f;  // -0 and +0 compare equal: keep one
+            v.push_back(fbits(f));
+        }
+        std::sort(v.begin(), v.end());
+        v.erase(std::unique(v.begin(), v.end()), v.end());
+        if (v.empty()) return GACE_OK;
+        out.kind = kRangeF32;
+        if (v.size() == 1) {
+            out.a = out.b = v[0];
+        } else {
+            out.kind = kInF32;
+            out.in = v;
+        }
+    }
+    return GACE_OK;
+}
+
+bool is_in_kind(uint32_t k) { return k == kInI32 || k == kInI64 || k == kInF32; }
+
+uint32_t in_count(const NTerm& t) {
+    return t.kind == kInI64 ? static_cast<uint32_t>(t.in.size() / 2) : static_cast<uint32_t>(t.in.size());
+}
+
+DevTerm make_devterm(const NTerm& t, uint32_t pool_off) {
+    DevTerm d{};
+    if (is_in_kind(t.kind)) {
+        d.a_lo = pool_off;
+        d.b_lo = in_count(t);
+    } else {
+        d.a_lo = static_cast<uint32_t>(t.a);
+        d.a_hi = static_cast<uint32_t>(t.a >> 32);
+        d.b_lo = static_cast<uint32_t>(t.b);
+        d.b_hi = static_cast<uint32_t>(t.b >> 32);
+    }
+    return d;
+}
+
+// ---------------------------------------------------------------- sets
+
+struct SetPlan {
+    SetDesc d;
+    uint32_t orig;
+};
+
+gace_status make_set(const gace_sample& s, SetDesc& d) {
+    d = SetDesc{};
+    if (s.kind > GACE_BLOCKS) return fail(GACE_EINVAL, "sample kind %u invalid", s.kind);
+    d.kind = s.kind;
+    d.mode = 1;
+    if (s.kind == GACE_FULL) return GACE_OK;
+    if (std::isnan(s.rate)) return fail(GACE_EINVAL, "sample rate is NaN");
+    if (s.kind == GACE_BLOCKS && s.block_rows == 0)
+        return fail(GACE_EINVAL, "block_rows must be >= 1");
+    if (!(s.rate > 0.0)) {
+        d.mode = 0;
+    } else if (s.rate >= 1.0) {
+        d.mode = 1;
+    } else {
+        d.mode = 2;
+        d.thresh = static_cast<uint64_t>(std::ldexp(s.rate, 64));
+    }
+    d.seedhash = splitmix64_host(s.seed);
+    d.block_rows = s.kind == GACE_BLOCKS ? s.block_rows : 1;
+    d.block_shift = -1;
+    if (s.kind == GACE_BLOCKS && (s.block_rows & (s.block_rows - 1)) == 0) {
+        int sh = 0;
+        while ((1ull << sh) < s.block_rows) ++sh;
+        d.block_shift = sh;
+    }
+    return GACE_OK;
+}
+
+// ---------------------------------------------------------------- probe plan
+
+constexpr uint32_t kPassTerms = 512;
+constexpr uint32_t kPassPreds = 1024;
+constexpr uint32_t kPassPool = 8192;
+
+struct Pass {
+    std::vector<uint32_t> preds;   // device predicate indices (input numbering)
+    std::vector<uint32_t> uterms;  // unique terms placed in this pass
+    // built:
+    std::vector<DevTerm> dterms;
+    std::vector<uint32_t> pool, poff, pterm;
+    std::vector<uint32_t> u_local;  // unique term -> local index (parallel to uterms order)
+    std::vector<std::pair<uint32_t, uint32_t>> slots;  // (col, first local term)
+    ProbeArgs args{};
+    uint64_t in_off = 0, out_off = 0;  // workspace offsets
+    uint64_t in_bytes = 0, out_bytes = 0;
+};
+
+struct Ws {
+    uint64_t off = 0;
+    uint64_t take(uint64_t bytes, uint64_t align = 256) {
+        off = round_up(off, align);
+        const uint64_t r = off;
+        off += bytes;
+        return r;
+    }
+};
+
+gace_status check_ctx(gace_ctx* ctx) {
+    if (!ctx) return fail(GACE_EINVAL, "context is NULL");
+    return GACE_OK;
+}
+
+TableRec* find_table(gace_ctx* ctx, uint32_t id) {
+    auto it = ctx->tables.find(id);
+    return it == ctx->tables.end() ? nullptr : &it->second;
+}
+
+gace_status read_status(gace_ctx* ctx, unsigned int st) {
+    if (st & kStatusTimeout)
+        return fail(GACE_ETIMEDOUT, "a device-side wait gave up after %llu ms",
+                    (unsigned long long)(ctx->timeout_ns / 1000000ull));
+    if (st & kStatusCasLimit) return fail(GACE_ETIMEDOUT, "a bounded device CAS loop gave up");
+    return GACE_OK;
+}
+
+// Builds the device form of a pass and the probe arguments (without pointers).
+gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::vector<NTerm>& uterms,
+                       const std::vector<std::vector<uint32_t>>& pred_u,
+                       const std::vector<SetPlan>& sets, bool want_marg) {
+    // order: by column, ranges before IN lists
+    std::vector<uint32_t> order = ps.uterms;
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+        const NTerm &a = uterms[x], &b = uterms[y];
+        const int ia = is_in_kind(a.kind), ib = is_in_kind(b.kind);
+        return std::tie(a.col, ia) < std::tie(b.col, ib);
+    });
+    std::map<uint32_t, uint32_t> local;
+    ps.uterms = order;
+    ps.slots.clear();
+    ps.dterms.clear();
+    ps.pool.clear();
+    ProbeArgs& A = ps.args;
+    A = ProbeArgs{};
+    uint32_t nslots = 0;
+    for (uint32_t i = 0; i < order.size(); ++i) {
+        const NTerm& t = uterms[order[i]];
+        local[order[i]] = i;
+        uint32_t poff = 0;
+        if (is_in_kind(t.kind)) {
+            poff = static_cast<uint32_t>(ps.pool.size());
+            ps.pool.insert(ps.pool.end(), t.in.begin(), t.in.end());
+        }
+        ps.dterms.push_back(make_devterm(t, poff));
+        if (nslots == 0 || ps.slots.back().first != t.col) {
+            if (nslots == kMaxSlots) return fail(GACE_EINVAL, "a pass references more than %d columns", kMaxSlots);
+            ps.slots.push_back({t.col, i});
+            SlotDesc& sd = A.slots[nslots++];
+            const ColumnRec& c = tab.cols[t.col];
+            sd.ptr = c.dptr;
+            sd.dtype = static_cast<uint32_t>(c.dtype);
+            sd.width = dtype_width(c.dtype);
+            sd.rbeg = i;
+            sd.rend = i;
+            sd.iend = i;
+        }
+        SlotDesc& sd = A.slots[nslots - 1];
+        if (is_in_kind(t.kind)) {
+            sd.iend = i + 1;
+        } else {
+            sd.rend = i + 1;
+            sd.iend = i + 1;
+        }
+    }
+    ps.poff.assign(1, 0);
+    ps.pterm.clear();
+    for (uint32_t p : ps.preds) {
+        for (uint32_t u : pred_u[p]) ps.pterm.push_back(local[u]);
+        ps.poff.push_back(static_cast<uint32_t>(ps.pterm.size()));
+    }
+    A.nrows = tab.nrows;
+    A.nslots = nslots;
+    A.nsets = static_cast<uint32_t>(sets.size());
+    for (uint32_t q = 0; q < sets.size(); ++q) A.sets[q] = sets[q].d;
+    A.nterms = static_cast<uint32_t>(ps.dterms.size());
+    A.npreds = static_cast<uint32_t>(ps.preds.size());
+    A.npool = static_cast<uint32_t>(ps.pool.size());
+    A.npredterms = static_cast<uint32_t>(ps.pterm.size());
+    A.want_marg = want_marg ? 1u : 0u;
+    A.timeout_ns = ctx->timeout_ns;
+
+    // tile geometry: ~32 KB stage buffers, rows a multiple of one CTA sweep
+    uint32_t rowbytes = 0;
+    for (uint32_t s = 0; s < nslots; ++s) rowbytes += A.slots[s].width;
+    const uint32_t sweep = kSliceRows * kProbeWarps;  // 1024 rows
+    uint32_t tile_rows = sweep;
+    if (rowbytes > 0)
+        while (tile_rows * 2 * rowbytes <= 32768 && tile_rows < 8 * sweep) tile_rows *= 2;
+    else
+        tile_rows = 8 * sweep;
+    A.tile_rows = tile_rows;
+    bool aligned = true;
+    for (uint32_t s = 0; s < nslots; ++s)
+        if (reinterpret_cast<uintptr_t>(A.slots[s].ptr) & 15u) aligned = false;
+    bool staged = aligned && nslots > 0;
+    uint32_t nst = 4;
+    for (;;) {
+        A.nstages = staged ? nst : 1;
+        A.stage_bytes = staged ? tile_rows * rowbytes : 0;
+        uint32_t off = 0;
+        for (uint32_t s = 0; s < nslots; ++s) {
+            A.slots[s].soff = off;
+            off += tile_rows * A.slots[s].width;
+        }
+        probe_layout(A);
+        if (A.smem_bytes <= static_cast<uint32_t>(ctx->smem_optin)) break;
+        if (staged && nst > 2) {
+            --nst;
+        } else if (staged && A.tile_rows > sweep) {
+            tile_rows /= 2;
+            A.tile_rows = tile_rows;
+        } else if (staged) {
+            staged = false;
+        } else {
+            return fail(GACE_EINVAL, "probe pass needs %u bytes of shared memory (limit %d)",
+                        A.smem_bytes, ctx->smem_optin);
+        }
+    }
+    A.ntiles = (tab.nrows + A.tile_rows - 1) / A.tile_rows;
+    A.nstaged = staged ? tab.nrows / A.tile_rows : 0;
+    return GACE_OK;
+}
+
+}  // namespace
+
+// ======================================================================== ABI
+
+extern "C" {
+
+uint32_t gace_abi_version(void) { return GACE_ABI_VERSION; }
+
+const char* gace_last_error(void) { return g_last_error.c_str(); }
+
+const char* gace_status_string(gace_status s) {
+    switch (s) {
+        case GACE_OK: return "GACE_OK";
+        case GACE_EINVAL: return "GACE_EINVAL";
+        case GACE_ENOMEM: return "GACE_ENOMEM";
+        case GACE_EBUSY: return "GACE_EBUSY";
+        case GACE_EPENDING: return "GACE_EPENDING";
+        case GACE_ETIMEDOUT: return "GACE_ETIMEDOUT";
+        case GACE_ENOTFOUND: return "GACE_ENOTFOUND";
+        case GACE_EOVERFLOW: return "GACE_EOVERFLOW";
+        case GACE_ECUDA: return "GACE_ECUDA";
+    }
+    return "GACE_UNKNOWN";
+}
+
+gace_status gace_create(gace_ctx** out, const gace_config* cfg) {
+    if (!out) return fail(GACE_EINVAL, "out is NULL");
+    gace_config c{};
+    if (cfg) c = *cfg;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0)
+        return fail(GACE_ECUDA, "no CUDA device: %s", e != cudaSuccess ? cudaGetErrorString(e) : "count is 0");
+    if (c.device < 0 || c.device >= n) return fail(GACE_EINVAL, "device %d outside 0..%d", c.device, n - 1);
+    DeviceGuard g(c.device);
+    gace_ctx* ctx = new gace_ctx();
+    ctx->device = c.device;
+    ctx->budget = c.hbm_budget_bytes;
+    if (c.wait_timeout_ms) ctx->timeout_ns = static_cast<uint64_t>(c.wait_timeout_ms) * 1000000ull;
+    auto bail = [&](gace_status s) {
+        gace_destroy(ctx);
+        return s;
+    };
+    if ((e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, c.device)) != cudaSuccess)
+        return bail(cuda_fail(e, "cudaDeviceGetAttribute(SM count)"));
+    if ((e = cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c.device)) !=
+        cudaSuccess)
+        return bail(cuda_fail(e, "cudaDeviceGetAttribute(smem opt-in)"));
+    if (c.stream) {
+        ctx->stream = static_cast<cudaStream_t>(c.stream);
+    } else {
+        if ((e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return bail(cuda_fail(e, "cudaStreamCreateWithFlags"));
+        ctx->own_stream = true;
+    }
+    if ((e = probe_configure()) != cudaSuccess) return bail(cuda_fail(e, "probe kernel attributes"));
+    if ((e = cudaMalloc(&ctx->d_status, 256)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(status)"));
+    *out = ctx;
+    return GACE_OK;
+}
+
+gace_status gace_destroy(gace_ctx* ctx) {
+    if (!ctx) return GACE_OK;
+    {
+        DeviceGuard g(ctx->device);
+        if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+        for (auto& kv : ctx->tables)
+            for (auto& c : kv.second.cols)
+                if (c.owned && c.dptr) cudaFree(c.dptr);
+        if (ctx->ws) cudaFree(ctx->ws);
+        if (ctx->pin) cudaFreeHost(ctx->pin);
+        if (ctx->d_status) cudaFree(ctx->d_status);
+        if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    }
+    delete ctx;
+    return GACE_OK;
+}
+
+gace_status gace_load_columns(gace_ctx* ctx, uint64_t nrows, uint32_t ncols, const gace_column* cols,
+                              uint32_t flags, uint32_t* table_id_out) {
+    if (gace_status s = check_ctx(ctx)) return s;
+    if (!cols || !table_id_out) return fail(GACE_EINVAL, "cols or table_id_out is NULL");
+    if (ncols == 0 || ncols > 64) return fail(GACE_EINVAL, "ncols %u outside 1..64", ncols);
+    if (flags > GACE_BORROW) return fail(GACE_EINVAL, "flags %u is neither COPY nor BORROW", flags);
+    if (nrows > (1ull << 40)) return fail(GACE_EINVAL, "nrows %llu above 2^40", (unsigned long long)nrows);
+    for (uint32_t c = 0; c < ncols; ++c) {
+        if (cols[c].dtype < GACE_I32 || cols[c].dtype > GACE_F32)
+            return fail(GACE_EINVAL, "column %u has dtype %d", c, cols[c].dtype);
+        if (nrows > 0 && !cols[c].data) return fail(GACE_EINVAL, "column %u data is NULL", c);
+        if (flags == GACE_BORROW && !cols[c].on_device)
+            return fail(GACE_EINVAL, "GACE_BORROW needs device columns (column %u is on the host)", c);
+    }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    TableRec tab;
+    tab.nrows = nrows;
+    uint64_t need = 0;
+    if (flags == GACE_COPY)
+        for (uint32_t c = 0; c < ncols; ++c) need += round_up(nrows * dtype_width(cols[c].dtype) + 16, 256);
+    if (!ctx->fits(need))
+        return fail(GACE_ENOMEM, "table of %llu bytes exceeds the HBM budget (%llu of %llu used)",
+                    (unsigned long long)need, (unsigned long long)ctx->used,
+                    (unsigned long long)ctx->budget);
+    for (uint32_t c = 0; c < ncols; ++c) {
+        ColumnRec r;
+        r.dtype = cols[c].dtype;
+        const uint64_t bytes = nrows * dtype_width(r.dtype);
+        r.bytes = bytes;
+        if (flags == GACE_BORROW) {
+            r.dptr = const_cast<void*>(cols[c].data);
+        } else {
+            const uint64_t alloc = round_up(bytes + 16, 256);
+            cudaError_t e = cudaMalloc(&r.dptr, alloc);
+            if (e != cudaSuccess) {
+                for (auto& x : tab.cols) cudaFree(x.dptr);
+                return fail(GACE_ENOMEM, "cudaMalloc(%llu) for column %u: %s", (unsigned long long)alloc, c,
+                            cudaGetErrorString(e));
+            }
+            r.owned = true;
+            tab.owned_bytes += alloc;
+            if (bytes) {
+                e = cudaMemcpyAsync(r.dptr, cols[c].data, bytes,
+                                    cols[c].on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                    ctx->stream);
+                if (e != cudaSuccess) {
+                    cudaFree(r.dptr);
+                    for (auto& x : tab.cols) cudaFree(x.dptr);
+                    return cuda_fail(e, "cudaMemcpyAsync(column)");
+                }
+            }
+        }
+        tab.cols.push_back(r);
+    }
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        for (auto& x : tab.cols)
+            if (x.owned) cudaFree(x.dptr);
+        return cuda_fail(e, "cudaStreamSynchronize(load)");
+    }
+    ctx->used += tab.owned_bytes;
+    const uint32_t id = ctx->next_id++;
+    ctx->tables.emplace(id, std::move(tab));
+    *table_id_out = id;
+    return GACE_OK;
+}
+
+gace_status gace_unload(gace_ctx* ctx, uint32_t table_id) {
+    if (gace_status s = check_ctx(ctx)) return s;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    auto it = ctx->tables.find(table_id);
+    if (it == ctx->tables.end()) return fail(GACE_ENOTFOUND, "table %u is not loaded", table_id);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& c : it->second.cols)
+        if (c.owned && c.dptr) cudaFree(c.dptr);
+    ctx->used -= it->second.owned_bytes;
+    ctx->tables.erase(it);
+    return GACE_OK;
+}
+
+gace_status gace_probe_batch(gace_ctx* ctx, uint32_t table_id, const gace_sample* samples, uint32_t nsamples,
+                             const gace_term* terms, uint32_t nterms, const gace_scalar* in_values, uint32_t nin,
+                             const gace_pred* preds, uint32_t npreds, gace_pred_result* results,
+                             uint64_t* term_marginals) {
+    if (gace_status s = check_ctx(ctx)) return s;
+    if (!samples || nsamples == 0 || nsamples > kMaxSets)
+        return fail(GACE_EINVAL, "nsamples %u outside 1..%d", nsamples, kMaxSets);
+    if (npreds && (!preds || !results)) return fail(GACE_EINVAL, "preds or results is NULL");
+    if (nterms && !terms) return fail(GACE_EINVAL, "terms is NULL");
+    if (nterms > (1u << 24) || npreds > (1u << 24)) return fail(GACE_EINVAL, "batch too large");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    TableRec* tab = find_table(ctx, table_id);
+    if (!tab) return fail(GACE_ENOTFOUND, "table %u is not loaded", table_id);
+    DeviceGuard g(ctx->device);
+
+    // row sets, ordered so that sets sharing a hash input are adjacent
+    std::vector<SetPlan> sets(nsamples);
+    for (uint32_t s = 0; s < nsamples; ++s) {
+        if (gace_status st = make_set(samples[s], sets[s].d)) return st;
+        sets[s].orig = s;
+    }
+    std::stable_sort(sets.begin(), sets.end(), [](const SetPlan& a, const SetPlan& b) {
+        return std::tie(a.d.kind, a.d.seedhash, a.d.block_rows) < std::tie(b.d.kind, b.d.seedhash, b.d.block_rows);
+    });
+    for (uint32_t q = 1; q < nsamples; ++q) {
+        const SetDesc &p = sets[q - 1].d, &c = sets[q].d;
+        sets[q].d.share_prev = (c.mode == 2 && p.mode == 2 && p.kind == c.kind && p.seedhash == c.seedhash &&
+                                p.block_rows == c.block_rows)
+                                   ? 1u
+                                   : 0u;
+        // a set between two hashing sets that does not hash breaks the chain
+    }
+    for (uint32_t q = 1; q < nsamples; ++q)
+        if (sets[q].d.share_prev && sets[q - 1].d.mode != 2) sets[q].d.share_prev = 0;
+    std::vector<uint32_t> set_pos(nsamples);
+    for (uint32_t q = 0; q < nsamples; ++q) set_pos[sets[q].orig] = q;
+
+    // normalise and deduplicate terms
+    std::vector<NTerm> uterms;
+    std::map<NTerm, uint32_t> dedup;
+    std::vector<uint32_t> t2u(nterms);
+    for (uint32_t t = 0; t < nterms; ++t) {
+        if (terms[t].col >= tab->cols.size())
+            return fail(GACE_EINVAL, "term %u references column %u of a %zu-column table", t, terms[t].col,
+                        tab->cols.size());
+        NTerm n;
+        if (gace_status st = normalize_term(terms[t], tab->cols[terms[t].col].dtype, in_values, nin, n)) return st;
+        if (n.kind == kFalse) {
+            t2u[t] = UINT32_MAX;
+            continue;
+        }
+        auto it = dedup.find(n);
+        if (it == dedup.end()) {
+            it = dedup.emplace(n, static_cast<uint32_t>(uterms.size())).first;
+            uterms.push_back(n);
+        }
+        t2u[t] = it->second;
+    }
+    // predicates: 0 device, 1 never true, 2 always true (no terms)
+    std::vector<uint8_t> pstate(npreds, 0);
+    std::vector<std::vector<uint32_t>> pred_u(npreds);
+    bool any_pair = false;
+    for (uint32_t p = 0; p < npreds; ++p) {
+        const gace_pred& pr = preds[p];
+        if ((uint64_t)pr.term_off + pr.term_cnt > nterms)
+            return fail(GACE_EINVAL, "predicate %u terms [%u, %u) outside terms[%u]", p, pr.term_off,
+                        pr.term_off + pr.term_cnt, nterms);
+        if (pr.term_cnt == 2) any_pair = true;
+        if (pr.term_cnt == 0) {
+            pstate[p] = 2;
+            continue;
+        }
+        for (uint32_t k = 0; k < pr.term_cnt; ++k) {
+            const uint32_t u = t2u[pr.term_off + k];
+            if (u == UINT32_MAX) {
+                pstate[p] = 1;
+                break;
+            }
+            pred_u[p].push_back(u);
+        }
+        std::sort(pred_u[p].begin(), pred_u[p].end());
+        pred_u[p].erase(std::unique(pred_u[p].begin(), pred_u[p].end()), pred_u[p].end());
+        if (pstate[p] == 1) pred_u[p].clear();
+    }
+    const bool want_marg = term_marginals != nullptr || any_pair;
+
+    // pack predicates into passes that fit the kernel's shared-memory tables
+    std::vector<Pass> passes;
+    std::vector<int32_t> u_pass(uterms.size(), -1);
+    {
+        Pass cur;
+        std::map<uint32_t, bool> in_cur;
+        uint32_t pool_words = 0;
+        std::map<uint32_t, bool> cols_cur;
+        auto flush = [&]() {
+            if (!cur.preds.empty() || !cur.uterms.empty()) passes.push_back(cur);
+            cur = Pass();
+            in_cur.clear();
+            cols_cur.clear();
+            pool_words = 0;
+        };
+        for (uint32_t p = 0; p < npreds; ++p) {
+            if (pstate[p] != 0) continue;
+            uint32_t add_t = 0, add_pool = 0, add_c = 0;
+            for (uint32_t u : pred_u[p])
+                if (!in_cur.count(u)) {
+                    ++add_t;
+                    add_pool += static_cast<uint32_t>(uterms[u].in.size());
+                    if (!cols_cur.count(uterms[u].col)) ++add_c;
+                }
+            if (pred_u[p].size() > kPassTerms) return fail(GACE_EINVAL, "predicate %u has too many terms", p);
+            if (!cur.preds.empty() &&
+                (cur.uterms.size() + add_t > kPassTerms || cur.preds.size() + 1 > kPassPreds ||
+                 pool_words + add_pool > kPassPool || cols_cur.size() + add_c > static_cast<size_t>(kMaxSlots)))
+                flush();
+            for (uint32_t u : pred_u[p])
+                if (!in_cur.count(u)) {
+                    in_cur[u] = true;
+                    cols_cur[uterms[u].col] = true;
+                    cur.uterms.push_back(u);
+                    pool_words += static_cast<uint32_t>(uterms[u].in.size());
+                    u_pass[u] = static_cast<int32_t>(passes.size());
+                }
+            cur.preds.push_back(p);
+            if (pool_words > kPassPool) return fail(GACE_EINVAL, "predicate %u IN lists too long", p);
+        }
+        // terms whose marginals are wanted but that no device predicate placed
+        if (want_marg) {
+            for (uint32_t u = 0; u < uterms.size(); ++u) {
+                if (u_pass[u] >= 0) continue;
+                const uint32_t add_c = cols_cur.count(uterms[u].col) ? 0 : 1;
+                if (cur.uterms.size() + 1 > kPassTerms || pool_words + uterms[u].in.size() > kPassPool ||
+                    cols_cur.size() + add_c > static_cast<size_t>(kMaxSlots))
+                    flush();
+                cur.uterms.push_back(u);
+                in_cur[u] = true;
+                cols_cur[uterms[u].col] = true;
+                pool_words += static_cast<uint32_t>(uterms[u].in.size());
+                u_pass[u] = static_cast<int32_t>(passes.size());
+            }
+        }
+        flush();
+    }
+    bool need_ns = false;
+    for (auto& s : sets)
+        if (s.d.kind != 0 && s.d.mode == 2) need_ns = true;
+    if (passes.empty() && need_ns) passes.push_back(Pass());  // counts sample rows only
+
+    // build passes and the workspace layout
+    Ws ws;
+    const uint64_t status_off = ws.take(256);
+    for (auto& ps : passes) {
+        if (gace_status st = build_pass(ctx, *tab, ps, uterms, pred_u, sets, want_marg)) return st;
+        ProbeArgs& A = ps.args;
+        ps.in_bytes = round_up(A.nterms * 16ull, 16) + round_up(A.npool * 4ull, 16) +
+                      round_up((A.npreds + 1) * 4ull, 16) + round_up(A.npredterms * 4ull, 16);
+        ps.out_bytes = (static_cast<uint64_t>(A.nsets) * A.npreds + static_cast<uint64_t>(A.nsets) * A.nterms +
+                        A.nsets) * 8ull;
+        ps.in_off = ws.take(ps.in_bytes);
+        ps.out_off = ws.take(ps.out_bytes);
+    }
+    const uint64_t out_lo = passes.empty() ? 0 : passes.front().out_off;
+    uint64_t pin_need = ws.off + 256;
+    if (gace_status st = ctx->ensure_ws(ws.off)) return st;
+    if (gace_status st = ctx->ensure_pin(pin_need)) return st;
+
+    // stage inputs into pinned memory, one H2D copy, zero outputs
+    unsigned char* pin = ctx->pin;
+    unsigned char* dws = ctx->ws;
+    for (auto& ps : passes) {
+        ProbeArgs& A = ps.args;
+        uint64_t o = ps.in_off;
+        auto put = [&](const void* src, uint64_t bytes) {
+            const uint64_t at = o;
+            if (bytes) memcpy(pin + o, src, bytes);
+            o += round_up(bytes, 16);
+            return at;
+        };
+        const uint64_t o_terms = put(ps.dterms.data(), ps.dterms.size() * 16ull);
+        const uint64_t o_pool = put(ps.pool.data(), ps.pool.size() * 4ull);
+        const uint64_t o_poff = put(ps.poff.data(), ps.poff.size() * 4ull);
+        const uint64_t o_pterm = put(ps.pterm.data(), ps.pterm.size() * 4ull);
+        A.terms = reinterpret_cast<const DevTerm*>(dws + o_terms);
+        A.pool = reinterpret_cast<const uint32_t*>(dws + o_pool);
+        A.pred_off = reinterpret_cast<const uint32_t*>(dws + o_poff);
+        A.pred_terms = reinterpret_cast<const uint32_t*>(dws + o_pterm);
+        unsigned long long* out = reinterpret_cast<unsigned long long*>(dws + ps.out_off);
+        A.counts = out;
+        A.marg = out + static_cast<uint64_t>(A.nsets) * A.npreds;
+        A.nsamp = A.marg + static_cast<uint64_t>(A.nsets) * A.nterms;
+        A.status = reinterpret_cast<unsigned int*>(dws + status_off);
+    }
+    if (!passes.empty()) {
+        const uint64_t first_in = passes.front().in_off;
+        CK(cudaMemcpyAsync(dws + first_in, pin + first_in, ws.off - first_in, cudaMemcpyHostToDevice,
+                           ctx->stream));
+        for (auto& ps : passes) CK(cudaMemsetAsync(dws + ps.out_off, 0, ps.out_bytes, ctx->stream));
+    }
+    CK(cudaMemsetAsync(dws + status_off, 0, 256, ctx->stream));
+    for (auto& ps : passes) {
+        const int occ = probe_occupancy(ps.args);
+        if (occ < 1) return fail(GACE_ECUDA, "probe kernel cannot be resident with %u bytes of shared memory",
+                                 ps.args.smem_bytes);
+        uint64_t grid = static_cast<uint64_t>(ctx->sms) * occ;
+        if (grid > ps.args.ntiles) grid = ps.args.ntiles;
+        if (grid < 1) grid = 1;
+        // each CTA keeps 32-bit row counters
+        while ((ps.args.ntiles + grid - 1) / grid * ps.args.tile_rows >= (1ull << 31)) grid *= 2;
+        if (grid > 0x7FFFFFFFull) return fail(GACE_EINVAL, "table too large for one probe grid");
+        CK(probe_launch(ps.args, static_cast<int>(grid), ctx->stream));
+    }
+    const uint64_t rb_lo = status_off, rb_hi = passes.empty() ? status_off + 256 : ws.off;
+    (void)out_lo;
+    CK(cudaMemcpyAsync(pin + rb_lo, dws + rb_lo, rb_hi - rb_lo, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (gace_status st = read_status(ctx, *reinterpret_cast<unsigned int*>(pin + status_off))) return st;
+
+    // assemble results
+    std::vector<uint64_t> ns(nsamples, 0);
+    for (uint32_t s = 0; s < nsamples; ++s) {
+        const SetDesc& d = sets[set_pos[s]].d;
+        if (d.mode == 0) ns[s] = 0;
+        else if (d.kind == 0 || d.mode == 1) ns[s] = tab->nrows;
+        else {
+            const Pass& ps = passes.front();
+            const unsigned long long* out = reinterpret_cast<const unsigned long long*>(pin + ps.out_off);
+            ns[s] = out[static_cast<uint64_t>(ps.args.nsets) * ps.args.npreds +
+                        static_cast<uint64_t>(ps.args.nsets) * ps.args.nterms + set_pos[s]];
+        }
+    }
+    // per unique term: (pass, local index)
+    std::vector<std::pair<int32_t, uint32_t>> uloc(uterms.size(), {-1, 0});
+    for (uint32_t k = 0; k < passes.size(); ++k)
+        for (uint32_t i = 0; i < passes[k].uterms.size(); ++i) uloc[passes[k].uterms[i]] = {static_cast<int32_t>(k), i};
+    auto marg_of = [&](uint32_t t, uint32_t s) -> uint64_t {
+        const uint32_t u = t2u[t];
+        if (u == UINT32_MAX) return 0;
+        const auto& L = uloc[u];
+        if (L.first < 0) return 0;
+        const Pass& ps = passes[L.first];
+        const unsigned long long* out = reinterpret_cast<const unsigned long long*>(pin + ps.out_off);
+        return out[static_cast<uint64_t>(ps.args.nsets) * ps.args.npreds +
+                   static_cast<uint64_t>(set_pos[s]) * ps.args.nterms + L.second];
+    };
+    std::vector<std::pair<int32_t, uint32_t>> ploc(npreds, {-1, 0});
+    for (uint32_t k = 0; k < passes.size(); ++k)
+        for (uint32_t i = 0; i < passes[k].preds.size(); ++i) ploc[passes[k].preds[i]] = {static_cast<int32_t>(k), i};
+    for (uint32_t s = 0; s < nsamples; ++s) {
+        for (uint32_t p = 0; p < npreds; ++p) {
+            uint64_t m = 0;
+            if (pstate[p] == 2) {
+                m = ns[s];
+            } else if (pstate[p] == 0) {
+                const Pass& ps = passes[ploc[p].first];
+                const unsigned long long* out = reinterpret_cast<const unsigned long long*>(pin + ps.out_off);
+                m = out[static_cast<uint64_t>(set_pos[s]) * ps.args.npreds + ploc[p].second];
+            }
+            gace_pred_result& r = results[static_cast<uint64_t>(s) * npreds + p];
+            r.match = m;
+            r.sample_rows = ns[s];
+            r.sel = ns[s] ? static_cast<double>(m) / static_cast<double>(ns[s]) : 0.0;
+            r.pcs = std::numeric_limits<double>::quiet_NaN();
+            if (preds[p].term_cnt == 2) {
+                const uint64_t ca = marg_of(preds[p].term_off, s), cb = marg_of(preds[p].term_off + 1, s);
+                if (ca != 0 && cb != 0)
+                    r.pcs = (static_cast<double>(m) * static_cast<double>(ns[s])) /
+                            (static_cast<double>(ca) * static_cast<double>(cb));
+            }
+        }
+        if (term_marginals)
+            for (uint32_t t = 0; t < nterms; ++t) term_marginals[static_cast<uint64_t>(s) * nterms + t] = marg_of(t, s);
+    }
+    return GACE_OK;
+}
+
+// ---------------------------------------------------------------- HLL
+
+static double hll_estimate_host(const uint8_t* regs, uint32_t p) {
+    const uint64_t m = 1ull << p;
+    uint64_t hist[66] = {0};
+    for (uint64_t j = 0; j < m; ++j) hist[regs[j] < 65 ? regs[j] : 65]++;
+    const double dm = static_cast<double>(m);
+    double alpha;
+    if (m == 16) alpha = 0.673;
+    else if (m == 32) alpha = 0.697;
+    else if (m == 64) alpha = 0.709;
+    else alpha = 0.7213 / (1.0 + 1.079 / dm);
+    double z = 0.0;
+    for (int k = 0; k <= 65; ++k) z += static_cast<double>(hist[k]) * std::ldexp(1.0, -k);
+    double e = alpha * dm * dm / z;
+    if (e <= 2.5 * dm && hist[0] > 0) e = dm * std::log(dm / static_cast<double>(hist[0]));
+    return e;
+}
+
+gace_status gace_ndv(gace_ctx* ctx, uint32_t table_id, uint32_t col, uint32_t p, uint64_t hash_seed,
+                     uint8_t* registers_out, double* estimate_out) {
+    if (gace_status s = check_ctx(ctx)) return s;
+    if (p < 4 || p > 18) return fail(GACE_EINVAL, "p = %u outside 4..18", p);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    TableRec* tab = find_table(ctx, table_id);
+    if (!tab) return fail(GACE_ENOTFOUND, "table %u is not loaded", table_id);
+    if (col >= tab->cols.size()) return fail(GACE_EINVAL, "column %u of a %zu-column table", col, tab->cols.size());
+    DeviceGuard g(ctx->device);
+    const uint64_t m = 1ull << p;
+    Ws ws;
+    const uint64_t status_off = ws.take(256);
+    const uint64_t regs_off = ws.take(m * 4);
+    if (gace_status st = ctx->ensure_ws(ws.off)) return st;
+    if (gace_status st = ctx->ensure_pin(ws.off)) return st;
+    CK(cudaMemsetAsync(ctx->ws, 0, ws.off, ctx->stream));
+    HllArgs a{};
+    a.col = tab->cols[col].dptr;
+    a.nrows = tab->nrows;
+    a.dtype = static_cast<uint32_t>(tab->cols[col].dtype);
+    a.p = p;
+    a.seedhash = splitmix64_host(hash_seed);
+    a.aligned = (reinterpret_cast<uintptr_t>(a.col) & 15u) == 0;
+    a.regs = reinterpret_cast<uint32_t*>(ctx->ws + regs_off);
+    a.status = reinterpret_cast<unsigned int*>(ctx->ws + status_off);
+    if (tab->nrows > 0) CK(hll_launch(a, ctx->sms, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->pin, ctx->ws, ws.off, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (gace_status st = read_status(ctx, *reinterpret_cast<unsigned int*>(ctx->pin + status_off))) return st;
+    const uint32_t* r32 = reinterpret_cast<const uint32_t*>(ctx->pin + regs_off);
+    std::vector<uint8_t> regs(m);
+    for (uint64_t j = 0; j < m; ++j) regs[j] = static_cast<uint8_t>(r32[j]);
+    if (registers_out) memcpy(registers_out, regs.data(), m);
+    if (estimate_out) *estimate_out = hll_estimate_host(regs.data(), p);
+    return GACE_OK;
+}
+
+// ---------------------------------------------------------------- joins
+
+static gace_status build_side(gace_ctx* ctx, const gace_join_side& js, const char* name, int extra_col,
+                              SideArgs& a, std::vector<uint32_t>& pool, TableRec** tab_out, uint32_t* extra_slot) {
+    TableRec* tab = find_table(ctx, js.table_id);
+    if (!tab) return fail(GACE_ENOTFOUND, "%s table %u is not loaded", name, js.table_id);
+    if (js.key_col >= tab->cols.size()) return fail(GACE_EINVAL, "%s key column %u out of range", name, js.key_col);
+    if (tab->cols[js.key_col].dtype == GACE_F32) return fail(GACE_EINVAL, "%s key column is float32", name);
+    if (js.nterms && !js.terms) return fail(GACE_EINVAL, "%s terms is NULL", name);
+    if (js.nterms > static_cast<uint32_t>(kMaxFilterTerms))
+        return fail(GACE_EINVAL, "%s filter has %u terms (max %d)", name, js.nterms, kMaxFilterTerms);
+    a = SideArgs{};
+    a.nrows = tab->nrows;
+    std::vector<uint32_t> slot_col;
+    auto slot_of = [&](uint32_t col) -> int {
+        for (uint32_t s = 0; s < slot_col.size(); ++s)
+            if (slot_col[s] == col) return static_cast<int>(s);
+        if (slot_col.size() == static_cast<size_t>(kMaxFilterSlots)) return -1;
+        slot_col.push_back(col);
+        return static_cast<int>(slot_col.size() - 1);
+    };
+    a.key_slot = static_cast<uint32_t>(slot_of(js.key_col));
+    if (extra_col >= 0) {
+        if (static_cast<uint32_t>(extra_col) >= tab->cols.size() || tab->cols[extra_col].dtype == GACE_F32)
+            return fail(GACE_EINVAL, "%s fk2 column %d invalid", name, extra_col);
+        *extra_slot = static_cast<uint32_t>(slot_of(static_cast<uint32_t>(extra_col)));
+    }
+    uint32_t nt = 0;
+    bool never = false;
+    for (uint32_t t = 0; t < js.nterms; ++t) {
+        if (js.terms[t].col >= tab->cols.size())
+            return fail(GACE_EINVAL, "%s term %u references column %u", name, t, js.terms[t].col);
+        NTerm n;
+        if (gace_status st = normalize_term(js.terms[t], tab->cols[js.terms[t].col].dtype, js.in_values, js.nin, n))
+            return st;
+        if (n.kind == kFalse) {
+            never = true;
+            continue;
+        }
+        const int s = slot_of(n.col);
+        if (s < 0) return fail(GACE_EINVAL, "%s filter references more than %d columns", name, kMaxFilterSlots);
+        FilterTerm& ft = a.terms[nt++];
+        ft.slot = static_cast<uint32_t>(s);
+        ft.kind = n.kind;
+        uint32_t poff = static_cast<uint32_t>(pool.size());
+        if (is_in_kind(n.kind)) pool.insert(pool.end(), n.in.begin(), n.in.end());
+        ft.c = make_devterm(n, poff);
+    }
+    if (never) {  // an always-false term: a range no value satisfies on the key column
+        nt = 0;
+        FilterTerm& ft = a.terms[nt++];
+        ft.slot = a.key_slot;
+        ft.kind = kInI32;
+        ft.c = DevTerm{0, 0, 0, 0};  // empty IN list
+    }
+    a.nterms = nt;
+    a.nslots = static_cast<uint32_t>(slot_col.size());
+    for (uint32_t s = 0; s < slot_col.size(); ++s) {
+        a.slot_ptr[s] = tab->cols[slot_col[s]].dptr;
+        a.slot_dtype[s] = static_cast<uint32_t>(tab->cols[slot_col[s]].dtype);
+        a.slot_aligned[s] = (reinterpret_cast<uintptr_t>(a.slot_ptr[s]) & 15u) == 0;
+    }
+    *tab_out = tab;
+    return GACE_OK;
+}
+
+gace_status gace_join_card(gace_ctx* ctx, const gace_join* spec, gace_join_result* out) {
+    if (gace_status s = check_ctx(ctx)) return s;
+    if (!spec || !out) return fail(GACE_EINVAL, "spec or out is NULL");
+    if (spec->hops != 1 && spec->hops != 2) return fail(GACE_EINVAL, "hops = %u (1 or 2)", spec->hops);
+    if (spec->method > GACE_JOIN_GATHER) return fail(GACE_EINVAL, "method %u invalid", spec->method);
+    if (spec->key_domain == 0 || spec->key_domain > (1ull << 32))
+        return fail(GACE_EINVAL, "key_domain %llu outside 1..2^32", (unsigned long long)spec->key_domain);
+    if (spec->hops == 2 && (spec->key_domain2 == 0 || spec->key_domain2 > (1ull << 32)))
+        return fail(GACE_EINVAL, "key_domain2 %llu outside 1..2^32", (unsigned long long)spec->key_domain2);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    std::vector<uint32_t> pool;
+    SideArgs F, D, D2;
+    TableRec *tf = nullptr, *td = nullptr, *td2 = nullptr;
+    uint32_t fk2_slot = 0;
+    if (gace_status st = build_side(ctx, spec->fact, "fact", -1, F, pool, &tf, nullptr)) return st;
+    if (gace_status st = build_side(ctx, spec->dim, "dim", spec->hops == 2 ? static_cast<int>(spec->dim_fk2_col) : -1, D,
+                                    pool, &td, &fk2_slot))
+        return st;
+    if (spec->hops == 2)
+        if (gace_status st = build_side(ctx, spec->dim2, "dim2", -1, D2, pool, &td2, nullptr)) return st;
+    const bool hist_dot = spec->method == GACE_JOIN_HIST_DOT;
+    if (td->nrows >= (1ull << 32) || (td2 && td2->nrows >= (1ull << 32)))
+        return fail(GACE_EINVAL, "a histogrammed dimension has 2^32 or more rows");
+    if (hist_dot && tf->nrows >= (1ull << 32))
+        return fail(GACE_EINVAL, "GACE_JOIN_HIST_DOT needs a fact table below 2^32 rows");
+    const uint64_t K = spec->key_domain, K2 = spec->hops == 2 ? spec->key_domain2 : 0;
+
+    // workspace: status | scalars | pool | h_D (or h_D2 + w) | h_F
+    Ws ws;
+    const uint64_t status_off = ws.take(256);
+    const uint64_t sc_off = ws.take(8 * 8);  // fact_pass dim_pass dim2_pass sum max_h max_w
+    const uint64_t pool_off = ws.take(pool.size() * 4 + 16);
+    const uint64_t hd_off = ws.take((spec->hops == 2 ? K2 : K) * 4);
+    const uint64_t w_off = spec->hops == 2 ? ws.take(K * 8) : 0;
+    const uint64_t hf_off = hist_dot ? ws.take(K * 4) : 0;
+    if (gace_status st = ctx->ensure_ws(ws.off)) return st;
+    if (gace_status st = ctx->ensure_pin(pool_off + pool.size() * 4 + 16)) return st;
+    unsigned char* w = ctx->ws;
+    unsigned long long* sc = reinterpret_cast<unsigned long long*>(w + sc_off);
+    unsigned int* status = reinterpret_cast<unsigned int*>(w + status_off);
+    const uint32_t* dpool = reinterpret_cast<const uint32_t*>(w + pool_off);
+    if (!pool.empty()) {
+        memcpy(ctx->pin + pool_off, pool.data(), pool.size() * 4);
+        CK(cudaMemcpyAsync(w + pool_off, ctx->pin + pool_off, pool.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    CK(cudaMemsetAsync(w, 0, pool_off, ctx->stream));
+    CK(cudaMemsetAsync(w + hd_off, 0, ws.off - hd_off, ctx->stream));
+    for (SideArgs* s : {&F, &D, &D2}) {
+        s->pool = dpool;
+        s->status = status;
+    }
+    F.domain = K;
+    F.pass_count = sc + 0;
+    D.domain = K;
+    D.pass_count = sc + 1;
+    const int sms = ctx->sms;
+    uint32_t* hD = reinterpret_cast<uint32_t*>(w + hd_off);
+    if (spec->hops == 1) {
+        CK(hist_launch(D, hD, 1, 0, sms, ctx->stream));
+        CK(max_launch(hD, 0, K, sc + 4, sms, ctx->stream));
+        if (hist_dot) {
+            uint32_t* hF = reinterpret_cast<uint32_t*>(w + hf_off);
+            CK(hist_launch(F, hF, 0, 1, sms, ctx->stream));
+            CK(dot_launch(hF, hD, 0, K, sc + 3, sms, ctx->stream));
+        } else {
+            CK(gather_launch(F, hD, 0, sc + 3, sms, ctx->stream));
+        }
+    } else {
+        D2.domain = K2;
+        D2.pass_count = sc + 2;
+        unsigned long long* wk = reinterpret_cast<unsigned long long*>(w + w_off);
+        CK(hist_launch(D2, hD, 1, 0, sms, ctx->stream));
+        CK(max_launch(hD, 0, K2, sc + 4, sms, ctx->stream));
+        CK(chain_weight_launch(D, fk2_slot, K2, hD, wk, sms, ctx->stream));
+        CK(max_launch(wk, 1, K, sc + 5, sms, ctx->stream));
+        if (hist_dot) {
+            uint32_t* hF = reinterpret_cast<uint32_t*>(w + hf_off);
+            CK(hist_launch(F, hF, 0, 1, sms, ctx->stream));
+            CK(dot_launch(hF, wk, 1, K, sc + 3, sms, ctx->stream));
+        } else {
+            CK(gather_launch(F, wk, 1, sc + 3, sms, ctx->stream));
+        }
+    }
+    CK(cudaMemcpyAsync(ctx->pin, w, sc_off + 64, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const unsigned int st = *reinterpret_cast<unsigned int*>(ctx->pin + status_off);
+    if (st & kStatusKeyDomain) return fail(GACE_EINVAL, "a filtered dimension row has a key outside its domain");
+    if (gace_status s = read_status(ctx, st)) return s;
+    const unsigned long long* h = reinterpret_cast<const unsigned long long*>(ctx->pin + sc_off);
+    const unsigned __int128 lim = static_cast<unsigned __int128>(1) << 63;
+    if (spec->hops == 1) {
+        if (static_cast<unsigned __int128>(h[0]) * h[4] >= lim)
+            return fail(GACE_EOVERFLOW, "fact_rows * max h_D >= 2^63");
+    } else {
+        if (static_cast<unsigned __int128>(h[1]) * h[4] >= lim)
+            return fail(GACE_EOVERFLOW, "dim_rows * max h_D2 >= 2^63");
+        if (static_cast<unsigned __int128>(h[0]) * h[5] >= lim)
+            return fail(GACE_EOVERFLOW, "fact_rows * max w >= 2^63");
+    }
+    out->card = static_cast<int64_t>(h[3]);
+    out->fact_rows = h[0];
+    out->dim_rows = h[1];
+    out->dim2_rows = spec->hops == 2 ? h[2] : 0;
+    return GACE_OK;
+}
+
+}  // extern "C"

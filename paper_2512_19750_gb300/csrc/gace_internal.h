@@ -1,0 +1,150 @@
+// gace_internal.h -- structures shared by the host runtime and the sm_103a
+// kernels of libgace.  Not part of the public ABI (include/gace.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gace {
+
+// ---------------------------------------------------------------- limits
+constexpr int kProbeWarps = 8;                  // warps per probe CTA
+constexpr int kRowsPerLane = 4;                 // consecutive rows per lane
+constexpr int kSliceRows = 32 * kRowsPerLane;   // rows per warp step (128)
+constexpr int kMaxSlots = 32;                   // distinct columns in one pass
+constexpr int kMaxSets = 8;                     // row sets in one probe
+constexpr int kMaxStages = 4;                   // bulk-copy pipeline depth
+
+// device status word bits (first error wins for the code, bits accumulate)
+constexpr unsigned kStatusTimeout = 1u;         // an mbarrier wait gave up
+constexpr unsigned kStatusKeyDomain = 2u;       // a dimension key outside its domain
+constexpr unsigned kStatusCasLimit = 4u;        // a bounded CAS loop gave up
+
+// ---------------------------------------------------------------- terms
+// Normalised term kinds.  Every RANGE/EQ becomes an inclusive interval in the
+// column's own domain; IN lists are deduplicated values of the column type.
+enum TermKind : uint32_t {
+    kRangeI32 = 0,  // (uint32)(x - a) <= b       a = lo, b = hi - lo
+    kRangeI64 = 1,  // (uint64)(x - a) <= b
+    kRangeF32 = 2,  // x >= a && x <= b            a, b float bit patterns
+    kInI32 = 3,     // x in pool32[a .. a + b)
+    kInI64 = 4,     // x in pool64 words [a .. a + 2b)
+    kInF32 = 5,     // x == any float in pool32[a .. a + b)
+    kFalse = 6      // matches nothing (host short-circuits it)
+};
+
+// 16-byte device term: 32-bit kinds read (a_lo, b_lo); 64-bit kinds read all.
+struct DevTerm {
+    uint32_t a_lo, b_lo, a_hi, b_hi;
+};
+
+// ---------------------------------------------------------------- probe
+struct SlotDesc {
+    const void* ptr;     // column base (device)
+    uint32_t dtype;      // 0 i32, 1 i64, 2 f32
+    uint32_t width;      // bytes per element
+    uint32_t rbeg;       // range terms of this slot: [rbeg, rend)
+    uint32_t rend;
+    uint32_t iend;       // IN terms: [rend, iend)
+    uint32_t soff;       // byte offset of the slot's tile inside a stage buffer
+};
+
+struct SetDesc {
+    uint32_t kind;       // 0 full, 1 rows, 2 blocks
+    uint32_t mode;       // 0 keep none, 1 keep all, 2 threshold
+    uint64_t thresh;     // keep iff hash < thresh
+    uint64_t seedhash;   // splitmix64(seed)
+    uint64_t block_rows;
+    int32_t block_shift; // log2(block_rows) when a power of two, else -1
+    uint32_t share_prev; // 1: same hash input as the previous set (reuse it)
+};
+
+struct ProbeArgs {
+    uint64_t nrows;
+    uint64_t ntiles;        // ceil(nrows / tile_rows)
+    uint64_t nstaged;       // tiles loaded by bulk copy (full tiles when staged)
+    uint32_t tile_rows;     // multiple of kSliceRows * kProbeWarps
+    uint32_t stage_bytes;   // bytes of one stage buffer (all slots)
+    uint32_t nstages;
+    uint32_t nslots, nsets, nterms, npreds, npool, npredterms;
+    uint32_t want_marg;
+    uint32_t smem_bytes;
+    // smem byte offsets
+    uint32_t off_stage, off_terms, off_pool, off_poff, off_pterm, off_tm, off_keep,
+        off_cnt, off_marg, off_ns;
+    uint64_t timeout_ns;
+    SlotDesc slots[kMaxSlots];
+    SetDesc sets[kMaxSets];
+    const DevTerm* terms;
+    const uint32_t* pool;
+    const uint32_t* pred_off;    // npreds + 1
+    const uint32_t* pred_terms;
+    unsigned long long* counts;  // [nsets][npreds]
+    unsigned long long* marg;    // [nsets][nterms]
+    unsigned long long* nsamp;   // [nsets]
+    unsigned int* status;
+};
+
+// Fills the smem layout fields of `a` (given counts) and returns total bytes.
+uint32_t probe_layout(ProbeArgs& a);
+cudaError_t probe_configure();  // one-time kernel attributes
+cudaError_t probe_launch(const ProbeArgs& a, int grid, cudaStream_t s);
+int probe_occupancy(const ProbeArgs& a);  // CTAs per SM for this smem size
+
+// ---------------------------------------------------------------- HyperLogLog
+struct HllArgs {
+    const void* col;
+    uint64_t nrows;
+    uint32_t dtype;
+    uint32_t p;
+    uint64_t seedhash;
+    uint32_t aligned;     // column base 16-byte aligned
+    uint32_t* regs;       // 2^p uint32 (global, zeroed)
+    unsigned int* status;
+};
+cudaError_t hll_launch(const HllArgs& a, int sms, cudaStream_t s);
+
+// ---------------------------------------------------------------- joins
+constexpr int kMaxFilterTerms = 64;
+constexpr int kMaxFilterSlots = 8;
+
+struct FilterTerm {
+    uint32_t slot;
+    uint32_t kind;
+    DevTerm c;
+};
+
+struct SideArgs {
+    uint64_t nrows;
+    uint32_t nslots;
+    uint32_t nterms;
+    uint32_t npool;
+    uint32_t key_slot;
+    const void* slot_ptr[kMaxFilterSlots];
+    uint32_t slot_dtype[kMaxFilterSlots];
+    uint32_t slot_aligned[kMaxFilterSlots];
+    FilterTerm terms[kMaxFilterTerms];
+    const uint32_t* pool;    // device
+    uint64_t domain;         // keys must lie in [0, domain)
+    unsigned long long* pass_count;
+    unsigned int* status;
+};
+
+// h[key] += 1 for filtered rows; strict: out-of-domain key sets kStatusKeyDomain
+cudaError_t hist_launch(const SideArgs& a, uint32_t* hist, int strict, int aggregate,
+                        int sms, cudaStream_t s);
+// w[key] += h2[fk2] for filtered rows of dim1 (key checked strictly)
+cudaError_t chain_weight_launch(const SideArgs& a, uint32_t fk2_slot, uint64_t domain2,
+                                const uint32_t* h2, unsigned long long* w, int sms,
+                                cudaStream_t s);
+// sum over filtered rows of weight[key] (uint32 or uint64 weights)
+cudaError_t gather_launch(const SideArgs& a, const void* weight, int weight64,
+                          unsigned long long* sum, int sms, cudaStream_t s);
+// sum_k a[k] * b[k]
+cudaError_t dot_launch(const uint32_t* a, const void* b, int b64, uint64_t n,
+                       unsigned long long* sum, int sms, cudaStream_t s);
+// max_k a[k]
+cudaError_t max_launch(const void* a, int a64, uint64_t n, unsigned long long* mx, int sms,
+                       cudaStream_t s);
+
+}  // namespace gace

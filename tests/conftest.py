@@ -19,3 +19,31 @@ def orc():
     oracle.build()
     oracle.lib()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def g():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2512_19750_gb300 as lib
+
+    return lib
+
+
+@pytest.fixture(scope="session")
+def gctx(g):
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    ctx = g.gace_create(0)
+    yield ctx
+    g.gace_destroy(ctx)
+
+
+@pytest.fixture(scope="session")
+def cuda():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return torch.device("cuda:0")
