@@ -344,9 +344,9 @@ gace_status make_set(const gace_sample& s, SetDesc& d) {
 
 // ---------------------------------------------------------------- probe plan
 
-constexpr uint32_t kPassTerms = 512;
-constexpr uint32_t kPassPreds = 1024;
-constexpr uint32_t kPassPool = 8192;
+constexpr uint32_t kPassTerms = 256;
+constexpr uint32_t kPassPreds = 256;
+constexpr uint32_t kPassPool = 4096;
 
 struct Pass {
     std::vector<uint32_t> preds;   // device predicate indices (input numbering)
@@ -454,21 +454,24 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
     A.want_marg = want_marg ? 1u : 0u;
     A.timeout_ns = ctx->timeout_ns;
 
-    // tile geometry: ~32 KB stage buffers, rows a multiple of one CTA sweep
+    // Narrow passes (the gate's single probes) stream staged tiles of about
+    // 16 KB through a 3-deep bulk-copy pipeline so that many CTAs fit on an SM;
+    // wide passes are ALU-bound and load directly.
     uint32_t rowbytes = 0;
     for (uint32_t s = 0; s < nslots; ++s) rowbytes += A.slots[s].width;
+    A.narrow = (A.npreds <= static_cast<uint32_t>(kNarrowMax) && A.nterms <= static_cast<uint32_t>(kNarrowMax)) ? 1u : 0u;
     const uint32_t sweep = kSliceRows * kProbeWarps;  // 1024 rows
     uint32_t tile_rows = sweep;
     if (rowbytes > 0)
-        while (tile_rows * 2 * rowbytes <= 32768 && tile_rows < 8 * sweep) tile_rows *= 2;
+        while (tile_rows * 2 * rowbytes <= 16384 && tile_rows < 8 * sweep) tile_rows *= 2;  // ~16 KB stages
     else
         tile_rows = 8 * sweep;
     A.tile_rows = tile_rows;
     bool aligned = true;
     for (uint32_t s = 0; s < nslots; ++s)
         if (reinterpret_cast<uintptr_t>(A.slots[s].ptr) & 15u) aligned = false;
-    bool staged = aligned && nslots > 0;
-    uint32_t nst = 4;
+    bool staged = A.narrow && aligned && nslots > 0;
+    uint32_t nst = 3;
     for (;;) {
         A.nstages = staged ? nst : 1;
         A.stage_bytes = staged ? tile_rows * rowbytes : 0;
@@ -481,9 +484,6 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
         if (A.smem_bytes <= static_cast<uint32_t>(ctx->smem_optin)) break;
         if (staged && nst > 2) {
             --nst;
-        } else if (staged && A.tile_rows > sweep) {
-            tile_rows /= 2;
-            A.tile_rows = tile_rows;
         } else if (staged) {
             staged = false;
         } else {
@@ -859,11 +859,14 @@ gace_status gace_probe_batch(gace_ctx* ctx, uint32_t table_id, const gace_sample
         const int occ = probe_occupancy(ps.args);
         if (occ < 1) return fail(GACE_ECUDA, "probe kernel cannot be resident with %u bytes of shared memory",
                                  ps.args.smem_bytes);
+        // work units: tiles (narrow) or 8-slice warp sweeps (wide)
+        const uint64_t unit_rows = ps.args.narrow ? ps.args.tile_rows : static_cast<uint64_t>(kSliceRows) * kProbeWarps;
+        const uint64_t units = (tab->nrows + unit_rows - 1) / unit_rows;
         uint64_t grid = static_cast<uint64_t>(ctx->sms) * occ;
-        if (grid > ps.args.ntiles) grid = ps.args.ntiles;
+        if (grid > units) grid = units;
         if (grid < 1) grid = 1;
         // each CTA keeps 32-bit row counters
-        while ((ps.args.ntiles + grid - 1) / grid * ps.args.tile_rows >= (1ull << 31)) grid *= 2;
+        while ((units + grid - 1) / grid * unit_rows >= (1ull << 31)) grid *= 2;
         if (grid > 0x7FFFFFFFull) return fail(GACE_EINVAL, "table too large for one probe grid");
         CK(probe_launch(ps.args, static_cast<int>(grid), ctx->stream));
     }

@@ -28,7 +28,7 @@ namespace {
 
 using namespace dev;
 
-constexpr int kHllThreads = 512;
+constexpr int kHllThreads = 1024;
 constexpr int kJoinThreads = 256;
 constexpr uint32_t kCasLimit = 1u << 20;
 
@@ -69,13 +69,14 @@ __device__ __forceinline__ void smem_byte_max(uint32_t* words, uint32_t j, uint3
 }
 
 template <bool SMEM>
-__global__ void __launch_bounds__(kHllThreads) k_hll(const __grid_constant__ HllArgs A) {
+__global__ void __launch_bounds__(kHllThreads, 2) k_hll(const __grid_constant__ HllArgs A) {
     extern __shared__ uint32_t sregs[];
     const uint32_t m = 1u << A.p;
     if (SMEM) {
         for (uint32_t i = threadIdx.x; i < m / 4; i += kHllThreads) sregs[i] = 0;
         __syncthreads();
     }
+    const unsigned char* sbytes = reinterpret_cast<const unsigned char*>(sregs);
     const uint32_t width = A.dtype == 1 ? 8 : 4;
     const uint64_t ngroups = (A.nrows + 3) / 4;
     const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kHllThreads;
@@ -84,24 +85,31 @@ __global__ void __launch_bounds__(kHllThreads) k_hll(const __grid_constant__ Hll
         const uint64_t row0 = g * 4;
         Quad v;
         load_quad_global(A.col, width, row0, A.nrows, v);
+        // ranks of the four values first (independent), then the register checks
+        uint32_t j[4], rho[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            if (row0 + r >= A.nrows) break;
-            uint32_t j, rho;
-            hll_rank(canonical_key(A.dtype, v.lo[r], v.hi[r]), A.seedhash, A.p, j, rho);
-            if (SMEM) {
-                smem_byte_max(sregs, j, rho, A.status);
-            } else {
-                if (rho > *reinterpret_cast<volatile uint32_t*>(&A.regs[j])) atomicMax(&A.regs[j], rho);
-            }
+            hll_rank(canonical_key(A.dtype, v.lo[r], v.hi[r]), A.seedhash, A.p, j[r], rho[r]);
+            if (row0 + r >= A.nrows) rho[r] = 0;  // past the end: never raises a register
+        }
+        if (SMEM) {
+            uint32_t cur[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) cur[r] = *reinterpret_cast<const volatile unsigned char*>(&sbytes[j[r]]);
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                if (rho[r] > cur[r]) smem_byte_max(sregs, j[r], rho[r], A.status);
+        } else {
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                if (rho[r] > *reinterpret_cast<volatile uint32_t*>(&A.regs[j[r]])) atomicMax(&A.regs[j[r]], rho[r]);
         }
     }
     if (SMEM) {
         __syncthreads();
-        const unsigned char* bytes = reinterpret_cast<const unsigned char*>(sregs);
-        for (uint32_t j = threadIdx.x; j < m; j += kHllThreads) {
-            const uint32_t r = bytes[j];
-            if (r && r > __ldcg(&A.regs[j])) atomicMax(&A.regs[j], r);
+        for (uint32_t jj = threadIdx.x; jj < m; jj += kHllThreads) {
+            const uint32_t r = sbytes[jj];
+            if (r && r > __ldcg(&A.regs[jj])) atomicMax(&A.regs[jj], r);
         }
     }
 }
@@ -149,12 +157,12 @@ __global__ void __launch_bounds__(kJoinThreads)
          gb < ngroups; gb += stride) {
         const uint64_t g = gb + lane;
         const uint64_t row0 = g * 4;
-        bool pass[4];
-        side_pass(A, row0, pass);
         int64_t key[4];
         side_keys(A, A.key_slot, row0, key);
         int64_t fk2[4] = {0, 0, 0, 0};
         if (MODE == 3) side_keys(A, fk2_slot, row0, fk2);
+        bool pass[4];
+        side_pass(A, row0, pass);
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const bool in_dom = key[r] >= 0 && static_cast<uint64_t>(key[r]) < A.domain;
@@ -247,11 +255,9 @@ cudaError_t hll_launch(const HllArgs& a, int sms, cudaStream_t s) {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_hll<true>, kHllThreads, smem);
         if (e != cudaSuccess) return e;
         if (occ < 1) occ = 1;
-        // fewer, fuller CTAs: each CTA merges 2^p registers at the end
-        if (occ > 2) occ = 2;
         k_hll<true><<<grid_for(groups, kHllThreads, sms, occ), kHllThreads, smem, s>>>(a);
     } else {
-        k_hll<false><<<grid_for(groups, kHllThreads, sms, 4), kHllThreads, 0, s>>>(a);
+        k_hll<false><<<grid_for(groups, kHllThreads, sms, 2), kHllThreads, 0, s>>>(a);
     }
     return cudaGetLastError();
 }

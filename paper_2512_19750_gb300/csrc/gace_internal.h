@@ -14,6 +14,7 @@ constexpr int kSliceRows = 32 * kRowsPerLane;   // rows per warp step (128)
 constexpr int kMaxSlots = 32;                   // distinct columns in one pass
 constexpr int kMaxSets = 8;                     // row sets in one probe
 constexpr int kMaxStages = 4;                   // bulk-copy pipeline depth
+constexpr int kNarrowMax = 32;                  // narrow kernel: predicates and terms per pass
 
 // device status word bits (first error wins for the code, bits accumulate)
 constexpr unsigned kStatusTimeout = 1u;         // an mbarrier wait gave up
@@ -63,11 +64,12 @@ struct ProbeArgs {
     uint64_t nrows;
     uint64_t ntiles;        // ceil(nrows / tile_rows)
     uint64_t nstaged;       // tiles loaded by bulk copy (full tiles when staged)
-    uint32_t tile_rows;     // multiple of kSliceRows * kProbeWarps
+    uint32_t tile_rows;     // multiple of kSliceRows * kProbeWarps (narrow kernel)
     uint32_t stage_bytes;   // bytes of one stage buffer (all slots)
     uint32_t nstages;
     uint32_t nslots, nsets, nterms, npreds, npool, npredterms;
     uint32_t want_marg;
+    uint32_t narrow;        // 1: lane-owned counters, staged tiles; 0: wide batch kernel
     uint32_t smem_bytes;
     // smem byte offsets
     uint32_t off_stage, off_terms, off_pool, off_poff, off_pterm, off_tm, off_keep,
@@ -89,7 +91,7 @@ struct ProbeArgs {
 uint32_t probe_layout(ProbeArgs& a);
 cudaError_t probe_configure();  // one-time kernel attributes
 cudaError_t probe_launch(const ProbeArgs& a, int grid, cudaStream_t s);
-int probe_occupancy(const ProbeArgs& a);  // CTAs per SM for this smem size
+int probe_occupancy(const ProbeArgs& a);  // CTAs per SM for this kernel and smem size
 
 // ---------------------------------------------------------------- HyperLogLog
 struct HllArgs {

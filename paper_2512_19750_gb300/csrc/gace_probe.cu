@@ -3,23 +3,27 @@
 // The Measurement Engine probe (Section III-B of the paper) counts the rows of
 // a full table, a seeded row sample or a seeded block sample on which each
 // candidate conjunction holds; Section IV-I evaluates the candidates with a
-// per-row bitmask ("Key-Only + Bitmask").  Here one pass evaluates a whole
-// batch on up to eight row sets at once:
+// per-row bitmask ("Key-Only + Bitmask").  One pass evaluates a whole batch on
+// up to eight row sets at once.  A warp takes 128-row slices, four
+// consecutive rows per lane; each term becomes four 32-row bit masks through
+// __ballot_sync, and a predicate's mask is the AND of its terms' masks,
+// counted with __popc against each row set's membership mask.  Row-set
+// membership is a counter-based hash of the global row (or block) id, so
+// samples do not depend on tiling.
 //
-//   * each CTA owns a strided set of row tiles; one thread streams the tiles of
-//     the referenced columns only into shared memory with bulk async copies
-//     (cp.async.bulk + mbarrier transaction counts), `nstages` tiles ahead;
-//   * a warp takes 128-row slices, four consecutive rows per lane; each term is
-//     evaluated per row and turned into 32-row bit masks with __ballot_sync
-//     (the bitmask of the paper), four masks per term per slice;
-//   * lanes then take predicates (and terms, for marginals): a predicate's mask
-//     is the AND of its terms' masks, counted with __popc against each row
-//     set's membership mask, and added to 32-bit shared counters;
-//   * counters go to the global 64-bit totals once per CTA at the end.
-//
-// Row-set membership is a counter-based hash of the global row (or block) id,
-// so samples do not depend on tiling.  Nothing spins without a limit: every
-// mbarrier wait gives up after the context's timeout and reports it.
+// Two kernels share that core:
+//   k_probe_narrow  a batch of at most 32 predicates and 32 distinct terms (the
+//                   single probes the gate issues): one thread streams tiles of
+//                   the referenced columns into shared memory with bulk async
+//                   copies (cp.async.bulk + mbarrier transaction counts) a few
+//                   tiles ahead; lane p keeps predicate p's counts in registers.
+//                   Small stages keep many CTAs per SM so the scan is HBM-bound.
+//   k_probe_wide    larger batches, split on the host into passes of at most
+//                   256 predicates / 256 terms: direct vectorised loads (the
+//                   pass is ALU-bound), unrolled term evaluation, lanes take
+//                   predicates and add to 32-bit shared counters.
+// Counters reach the global 64-bit totals once per CTA.  No wait spins without
+// a limit: every mbarrier wait gives up after the context's timeout.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -33,20 +37,65 @@ using namespace dev;
 
 constexpr int kThreads = kProbeWarps * 32;
 
-__device__ __forceinline__ void issue_tile(const ProbeArgs& A, unsigned char* stage_base,
-                                           uint64_t* bar, uint64_t tile) {
-    const uint32_t b = smem_u32(bar);
-    mbar_arrive_expect_tx(b, A.stage_bytes);
-    const uint64_t row0 = tile * A.tile_rows;
-    for (uint32_t s = 0; s < A.nslots; ++s) {
-        const SlotDesc& sd = A.slots[s];
-        const unsigned char* src =
-            static_cast<const unsigned char*>(sd.ptr) + row0 * sd.width;
-        bulk_g2s(smem_u32(stage_base + sd.soff), src, A.tile_rows * sd.width, b);
-    }
+struct Smem {
+    uint64_t* bars;
+    unsigned char* stages;
+    DevTerm* st;
+    uint32_t* pool;
+    uint32_t* poff;
+    uint32_t* pterm;
+    uint4* tm;    // this warp's term masks
+    uint4* keep;  // this warp's row-set masks
+    uint32_t* cnt;
+    uint32_t* marg;
+    uint32_t* ns;
+};
+
+__device__ __forceinline__ Smem carve(const ProbeArgs& A, unsigned char* smem, int warp) {
+    Smem s;
+    s.bars = reinterpret_cast<uint64_t*>(smem);
+    s.stages = smem + A.off_stage;
+    s.st = reinterpret_cast<DevTerm*>(smem + A.off_terms);
+    s.pool = reinterpret_cast<uint32_t*>(smem + A.off_pool);
+    s.poff = reinterpret_cast<uint32_t*>(smem + A.off_poff);
+    s.pterm = reinterpret_cast<uint32_t*>(smem + A.off_pterm);
+    s.tm = reinterpret_cast<uint4*>(smem + A.off_tm) + warp * A.nterms;
+    s.keep = reinterpret_cast<uint4*>(smem + A.off_keep) + warp * A.nsets;
+    s.cnt = reinterpret_cast<uint32_t*>(smem + A.off_cnt);
+    s.marg = reinterpret_cast<uint32_t*>(smem + A.off_marg);
+    s.ns = reinterpret_cast<uint32_t*>(smem + A.off_ns);
+    return s;
 }
 
-// Membership masks of the slice's 128 rows in every row set.
+// Copies the pass tables into shared memory and zeroes the CTA counters.
+__device__ __forceinline__ void load_tables(const ProbeArgs& A, const Smem& s, int tid) {
+    for (uint32_t i = tid; i < A.nterms; i += kThreads) s.st[i] = A.terms[i];
+    for (uint32_t i = tid; i < A.npool; i += kThreads) s.pool[i] = A.pool[i];
+    for (uint32_t i = tid; i <= A.npreds; i += kThreads) s.poff[i] = A.pred_off[i];
+    for (uint32_t i = tid; i < A.npredterms; i += kThreads) s.pterm[i] = A.pred_terms[i];
+    for (uint32_t i = tid; i < A.nsets * A.npreds; i += kThreads) s.cnt[i] = 0;
+    if (A.want_marg)
+        for (uint32_t i = tid; i < A.nsets * A.nterms; i += kThreads) s.marg[i] = 0;
+    for (uint32_t i = tid; i < A.nsets; i += kThreads) s.ns[i] = 0;
+}
+
+// CTA counters -> global 64-bit totals (zeros skipped).
+__device__ __forceinline__ void flush(const ProbeArgs& A, const Smem& s, int tid) {
+    for (uint32_t i = tid; i < A.nsets * A.npreds; i += kThreads) {
+        const uint32_t v = s.cnt[i];
+        if (v) atomicAdd(&A.counts[i], static_cast<unsigned long long>(v));
+    }
+    if (A.want_marg) {
+        for (uint32_t i = tid; i < A.nsets * A.nterms; i += kThreads) {
+            const uint32_t v = s.marg[i];
+            if (v) atomicAdd(&A.marg[i], static_cast<unsigned long long>(v));
+        }
+    }
+    for (uint32_t i = tid; i < A.nsets; i += kThreads)
+        if (s.ns[i]) atomicAdd(&A.nsamp[i], static_cast<unsigned long long>(s.ns[i]));
+}
+
+// Membership masks of a slice's 128 rows in every row set (stored per warp).
 __device__ __forceinline__ void set_masks(const ProbeArgs& A, uint64_t row0, uint4* keep,
                                           int lane) {
     bool valid[4];
@@ -64,12 +113,21 @@ __device__ __forceinline__ void set_masks(const ProbeArgs& A, uint64_t row0, uin
             for (int r = 0; r < 4; ++r) k[r] = false;
         } else {
             if (!sd.share_prev) {
+                if (sd.kind == 1) {
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    uint64_t x = row0 + r;
-                    if (sd.kind == 2)
-                        x = sd.block_shift >= 0 ? (x >> sd.block_shift) : (x / sd.block_rows);
-                    h[r] = splitmix64(x ^ sd.seedhash);
+                    for (int r = 0; r < 4; ++r) h[r] = splitmix64((row0 + r) ^ sd.seedhash);
+                } else if (sd.block_shift >= 2) {
+                    // the lane's four rows (row0 is a multiple of 4) share one block
+                    const uint64_t hb = splitmix64((row0 >> sd.block_shift) ^ sd.seedhash);
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) h[r] = hb;
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const uint64_t x = row0 + r;
+                        const uint64_t b = sd.block_shift >= 0 ? (x >> sd.block_shift) : (x / sd.block_rows);
+                        h[r] = splitmix64(b ^ sd.seedhash);
+                    }
                 }
             }
 #pragma unroll
@@ -84,35 +142,55 @@ __device__ __forceinline__ void set_masks(const ProbeArgs& A, uint64_t row0, uin
     }
 }
 
+#define GACE_BALLOT4(pred_expr, out)                 \
+    do {                                             \
+        out.x = __ballot_sync(kFullMask, pred_expr(0)); \
+        out.y = __ballot_sync(kFullMask, pred_expr(1)); \
+        out.z = __ballot_sync(kFullMask, pred_expr(2)); \
+        out.w = __ballot_sync(kFullMask, pred_expr(3)); \
+    } while (0)
+
 // Evaluates the terms of one column slot on the lane's four rows and stores
-// the warp's four 32-row masks per term.
+// the warp's four 32-row masks per term (range terms two at a time for ILP).
 __device__ __forceinline__ void eval_slot(const SlotDesc& sd, const Quad& v, const DevTerm* st,
                                           const uint32_t* pool, uint4* tm, int lane) {
     if (sd.dtype == 0) {
-        for (uint32_t t = sd.rbeg; t < sd.rend; ++t) {
-            const uint2 c = *reinterpret_cast<const uint2*>(&st[t]);
-            uint4 m;
-            m.x = __ballot_sync(kFullMask, (v.lo[0] - c.x) <= c.y);
-            m.y = __ballot_sync(kFullMask, (v.lo[1] - c.x) <= c.y);
-            m.z = __ballot_sync(kFullMask, (v.lo[2] - c.x) <= c.y);
-            m.w = __ballot_sync(kFullMask, (v.lo[3] - c.x) <= c.y);
-            if (lane == 0) tm[t] = m;
+        uint32_t t = sd.rbeg;
+        for (; t + 1 < sd.rend; t += 2) {
+            const uint2 c0 = *reinterpret_cast<const uint2*>(&st[t]);
+            const uint2 c1 = *reinterpret_cast<const uint2*>(&st[t + 1]);
+            uint4 m0, m1;
+#define P0(r) ((v.lo[r] - c0.x) <= c0.y)
+#define P1(r) ((v.lo[r] - c1.x) <= c1.y)
+            GACE_BALLOT4(P0, m0);
+            GACE_BALLOT4(P1, m1);
+#undef P0
+#undef P1
+            if (lane == 0) {
+                tm[t] = m0;
+                tm[t + 1] = m1;
+            }
         }
-        for (uint32_t t = sd.rend; t < sd.iend; ++t) {
+        if (t < sd.rend) {
+            const uint2 c0 = *reinterpret_cast<const uint2*>(&st[t]);
+            uint4 m0;
+#define P0(r) ((v.lo[r] - c0.x) <= c0.y)
+            GACE_BALLOT4(P0, m0);
+#undef P0
+            if (lane == 0) tm[t] = m0;
+        }
+        for (t = sd.rend; t < sd.iend; ++t) {
             const uint2 c = *reinterpret_cast<const uint2*>(&st[t]);
-            bool h0 = false, h1 = false, h2 = false, h3 = false;
+            bool h[4] = {false, false, false, false};
             for (uint32_t k = 0; k < c.y; ++k) {
                 const uint32_t x = pool[c.x + k];
-                h0 |= v.lo[0] == x;
-                h1 |= v.lo[1] == x;
-                h2 |= v.lo[2] == x;
-                h3 |= v.lo[3] == x;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) h[r] |= v.lo[r] == x;
             }
             uint4 m;
-            m.x = __ballot_sync(kFullMask, h0);
-            m.y = __ballot_sync(kFullMask, h1);
-            m.z = __ballot_sync(kFullMask, h2);
-            m.w = __ballot_sync(kFullMask, h3);
+#define PH(r) (h[r])
+            GACE_BALLOT4(PH, m);
+#undef PH
             if (lane == 0) tm[t] = m;
         }
     } else if (sd.dtype == 1) {
@@ -123,89 +201,95 @@ __device__ __forceinline__ void eval_slot(const SlotDesc& sd, const Quad& v, con
             const DevTerm c = st[t];
             const uint64_t lo = join64(c.a_lo, c.a_hi), span = join64(c.b_lo, c.b_hi);
             uint4 m;
-            m.x = __ballot_sync(kFullMask, (x[0] - lo) <= span);
-            m.y = __ballot_sync(kFullMask, (x[1] - lo) <= span);
-            m.z = __ballot_sync(kFullMask, (x[2] - lo) <= span);
-            m.w = __ballot_sync(kFullMask, (x[3] - lo) <= span);
+#define P0(r) ((x[r] - lo) <= span)
+            GACE_BALLOT4(P0, m);
+#undef P0
             if (lane == 0) tm[t] = m;
         }
         for (uint32_t t = sd.rend; t < sd.iend; ++t) {
             const uint2 c = *reinterpret_cast<const uint2*>(&st[t]);
-            bool h0 = false, h1 = false, h2 = false, h3 = false;
+            bool h[4] = {false, false, false, false};
             for (uint32_t k = 0; k < c.y; ++k) {
                 const uint64_t y = join64(pool[c.x + 2 * k], pool[c.x + 2 * k + 1]);
-                h0 |= x[0] == y;
-                h1 |= x[1] == y;
-                h2 |= x[2] == y;
-                h3 |= x[3] == y;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) h[r] |= x[r] == y;
             }
             uint4 m;
-            m.x = __ballot_sync(kFullMask, h0);
-            m.y = __ballot_sync(kFullMask, h1);
-            m.z = __ballot_sync(kFullMask, h2);
-            m.w = __ballot_sync(kFullMask, h3);
+#define PH(r) (h[r])
+            GACE_BALLOT4(PH, m);
+#undef PH
             if (lane == 0) tm[t] = m;
         }
     } else {
         float x[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) x[r] = __uint_as_float(v.lo[r]);
-        for (uint32_t t = sd.rbeg; t < sd.rend; ++t) {
-            const uint2 c = *reinterpret_cast<const uint2*>(&st[t]);
-            const float lo = __uint_as_float(c.x), hi = __uint_as_float(c.y);
-            uint4 m;
-            m.x = __ballot_sync(kFullMask, x[0] >= lo && x[0] <= hi);
-            m.y = __ballot_sync(kFullMask, x[1] >= lo && x[1] <= hi);
-            m.z = __ballot_sync(kFullMask, x[2] >= lo && x[2] <= hi);
-            m.w = __ballot_sync(kFullMask, x[3] >= lo && x[3] <= hi);
-            if (lane == 0) tm[t] = m;
+        uint32_t t = sd.rbeg;
+        for (; t + 1 < sd.rend; t += 2) {
+            const uint2 c0 = *reinterpret_cast<const uint2*>(&st[t]);
+            const uint2 c1 = *reinterpret_cast<const uint2*>(&st[t + 1]);
+            const float l0 = __uint_as_float(c0.x), h0 = __uint_as_float(c0.y);
+            const float l1 = __uint_as_float(c1.x), h1 = __uint_as_float(c1.y);
+            uint4 m0, m1;
+#define P0(r) (x[r] >= l0 && x[r] <= h0)
+#define P1(r) (x[r] >= l1 && x[r] <= h1)
+            GACE_BALLOT4(P0, m0);
+            GACE_BALLOT4(P1, m1);
+#undef P0
+#undef P1
+            if (lane == 0) {
+                tm[t] = m0;
+                tm[t + 1] = m1;
+            }
         }
-        for (uint32_t t = sd.rend; t < sd.iend; ++t) {
+        if (t < sd.rend) {
+            const uint2 c0 = *reinterpret_cast<const uint2*>(&st[t]);
+            const float l0 = __uint_as_float(c0.x), h0 = __uint_as_float(c0.y);
+            uint4 m0;
+#define P0(r) (x[r] >= l0 && x[r] <= h0)
+            GACE_BALLOT4(P0, m0);
+#undef P0
+            if (lane == 0) tm[t] = m0;
+        }
+        for (t = sd.rend; t < sd.iend; ++t) {
             const uint2 c = *reinterpret_cast<const uint2*>(&st[t]);
-            bool h0 = false, h1 = false, h2 = false, h3 = false;
+            bool h[4] = {false, false, false, false};
             for (uint32_t k = 0; k < c.y; ++k) {
                 const float y = __uint_as_float(pool[c.x + k]);
-                h0 |= x[0] == y;
-                h1 |= x[1] == y;
-                h2 |= x[2] == y;
-                h3 |= x[3] == y;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) h[r] |= x[r] == y;
             }
             uint4 m;
-            m.x = __ballot_sync(kFullMask, h0);
-            m.y = __ballot_sync(kFullMask, h1);
-            m.z = __ballot_sync(kFullMask, h2);
-            m.w = __ballot_sync(kFullMask, h3);
+#define PH(r) (h[r])
+            GACE_BALLOT4(PH, m);
+#undef PH
             if (lane == 0) tm[t] = m;
         }
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_probe(const __grid_constant__ ProbeArgs A) {
+// ---------------------------------------------------------------- narrow
+
+__device__ __forceinline__ void issue_tile(const ProbeArgs& A, unsigned char* stage_base,
+                                           uint64_t* bar, uint64_t tile) {
+    const uint32_t b = smem_u32(bar);
+    mbar_arrive_expect_tx(b, A.stage_bytes);
+    const uint64_t row0 = tile * A.tile_rows;
+    for (uint32_t s = 0; s < A.nslots; ++s) {
+        const SlotDesc& sd = A.slots[s];
+        const unsigned char* src = static_cast<const unsigned char*>(sd.ptr) + row0 * sd.width;
+        bulk_g2s(smem_u32(stage_base + sd.soff), src, A.tile_rows * sd.width, b);
+    }
+}
+
+template <int MAXS>
+__global__ void __launch_bounds__(kThreads, 4) k_probe_narrow(const __grid_constant__ ProbeArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-    unsigned char* stages = smem + A.off_stage;
-    DevTerm* st = reinterpret_cast<DevTerm*>(smem + A.off_terms);
-    uint32_t* spool = reinterpret_cast<uint32_t*>(smem + A.off_pool);
-    uint32_t* spoff = reinterpret_cast<uint32_t*>(smem + A.off_poff);
-    uint32_t* spterm = reinterpret_cast<uint32_t*>(smem + A.off_pterm);
-    uint4* tm = reinterpret_cast<uint4*>(smem + A.off_tm) + warp * A.nterms;
-    uint4* keep = reinterpret_cast<uint4*>(smem + A.off_keep) + warp * A.nsets;
-    uint32_t* scnt = reinterpret_cast<uint32_t*>(smem + A.off_cnt);
-    uint32_t* smarg = reinterpret_cast<uint32_t*>(smem + A.off_marg);
-    uint32_t* sns = reinterpret_cast<uint32_t*>(smem + A.off_ns);
-
-    for (uint32_t i = tid; i < A.nterms; i += kThreads) st[i] = A.terms[i];
-    for (uint32_t i = tid; i < A.npool; i += kThreads) spool[i] = A.pool[i];
-    for (uint32_t i = tid; i <= A.npreds; i += kThreads) spoff[i] = A.pred_off[i];
-    for (uint32_t i = tid; i < A.npredterms; i += kThreads) spterm[i] = A.pred_terms[i];
-    for (uint32_t i = tid; i < A.nsets * A.npreds; i += kThreads) scnt[i] = 0;
-    if (A.want_marg)
-        for (uint32_t i = tid; i < A.nsets * A.nterms; i += kThreads) smarg[i] = 0;
-    for (uint32_t i = tid; i < A.nsets; i += kThreads) sns[i] = 0;
+    const Smem S = carve(A, smem, warp);
+    load_tables(A, S, tid);
     if (tid == 0) {
-        for (uint32_t s = 0; s < A.nstages; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        for (uint32_t s = 0; s < A.nstages; ++s) mbar_init(smem_u32(&S.bars[s]), 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -214,9 +298,18 @@ __global__ void __launch_bounds__(kThreads) k_probe(const __grid_constant__ Prob
     if (tid == 0) {
         for (uint32_t s = 0; s < A.nstages; ++s) {
             const uint64_t tile = blockIdx.x + s * stride;
-            if (tile < A.nstaged) issue_tile(A, stages + s * A.stage_bytes, &bars[s], tile);
+            if (tile < A.nstaged) issue_tile(A, S.stages + s * A.stage_bytes, &S.bars[s], tile);
         }
     }
+
+    // lane-owned counters: predicate `lane`, term `lane`, row set `lane`
+    uint32_t cnt[MAXS], mc[MAXS];
+#pragma unroll
+    for (int q = 0; q < MAXS; ++q) cnt[q] = mc[q] = 0;
+    uint32_t nsr = 0;
+    const bool has_pred = lane < static_cast<int>(A.npreds);
+    const bool has_term = A.want_marg && lane < static_cast<int>(A.nterms);
+    const uint32_t pb = has_pred ? S.poff[lane] : 0, pe = has_pred ? S.poff[lane + 1] : 0;
 
     const uint32_t nslices = A.tile_rows / kSliceRows;
     uint64_t it = 0;
@@ -228,16 +321,16 @@ __global__ void __launch_bounds__(kThreads) k_probe(const __grid_constant__ Prob
         const uint32_t stage = static_cast<uint32_t>(it % A.nstages);
         bool fail = false;
         if (staged)
-            fail = !mbar_wait_bounded(smem_u32(&bars[stage]),
+            fail = !mbar_wait_bounded(smem_u32(&S.bars[stage]),
                                       static_cast<uint32_t>((it / A.nstages) & 1), A.timeout_ns);
         if (!fail) {
-            const unsigned char* sbuf = stages + stage * A.stage_bytes;
+            const unsigned char* sbuf = S.stages + stage * A.stage_bytes;
             const uint64_t tile_row0 = tile * A.tile_rows;
             for (uint32_t j = warp; j < nslices; j += kProbeWarps) {
                 const uint64_t slice0 = tile_row0 + static_cast<uint64_t>(j) * kSliceRows;
                 if (slice0 >= A.nrows) break;
                 const uint64_t row0 = slice0 + 4u * lane;
-                set_masks(A, row0, keep, lane);
+                set_masks(A, row0, S.keep, lane);
                 for (uint32_t s = 0; s < A.nslots; ++s) {
                     const SlotDesc& sd = A.slots[s];
                     Quad v;
@@ -246,30 +339,25 @@ __global__ void __launch_bounds__(kThreads) k_probe(const __grid_constant__ Prob
                                        sd.width, v);
                     else
                         load_quad_global(sd.ptr, sd.width, row0, A.nrows, v);
-                    eval_slot(sd, v, st, spool, tm, lane);
+                    eval_slot(sd, v, S.st, S.pool, S.tm, lane);
                 }
                 __syncwarp();
-                for (uint32_t p = lane; p < A.npreds; p += 32) {
-                    const uint32_t b = spoff[p], e = spoff[p + 1];
-                    uint4 acc = tm[spterm[b]];
-                    for (uint32_t k = b + 1; k < e; ++k) acc = and4(acc, tm[spterm[k]]);
-                    for (uint32_t q = 0; q < A.nsets; ++q) {
-                        const uint32_t c = popc4(acc, keep[q]);
-                        if (c) atomicAdd(&scnt[q * A.npreds + p], c);
-                    }
+                if (has_pred) {
+                    uint4 acc = S.tm[S.pterm[pb]];
+                    for (uint32_t k = pb + 1; k < pe; ++k) acc = and4(acc, S.tm[S.pterm[k]]);
+#pragma unroll
+                    for (int q = 0; q < MAXS; ++q)
+                        if (q < static_cast<int>(A.nsets)) cnt[q] += popc4(acc, S.keep[q]);
                 }
-                if (A.want_marg) {
-                    for (uint32_t t = lane; t < A.nterms; t += 32) {
-                        const uint4 m = tm[t];
-                        for (uint32_t q = 0; q < A.nsets; ++q) {
-                            const uint32_t c = popc4(m, keep[q]);
-                            if (c) atomicAdd(&smarg[q * A.nterms + t], c);
-                        }
-                    }
+                if (has_term) {
+                    const uint4 m = S.tm[lane];
+#pragma unroll
+                    for (int q = 0; q < MAXS; ++q)
+                        if (q < static_cast<int>(A.nsets)) mc[q] += popc4(m, S.keep[q]);
                 }
-                if (lane < A.nsets) {
-                    const uint4 k = keep[lane];
-                    atomicAdd(&sns[lane], __popc(k.x) + __popc(k.y) + __popc(k.z) + __popc(k.w));
+                if (lane < static_cast<int>(A.nsets)) {
+                    const uint4 k = S.keep[lane];
+                    nsr += __popc(k.x) + __popc(k.y) + __popc(k.z) + __popc(k.w);
                 }
                 __syncwarp();
             }
@@ -280,7 +368,7 @@ __global__ void __launch_bounds__(kThreads) k_probe(const __grid_constant__ Prob
         }
         if (tid == 0) {
             const uint64_t next = tile + A.nstages * stride;
-            if (next < A.nstaged) issue_tile(A, stages + stage * A.stage_bytes, &bars[stage], next);
+            if (next < A.nstaged) issue_tile(A, S.stages + stage * A.stage_bytes, &S.bars[stage], next);
         }
     }
 
@@ -292,26 +380,74 @@ __global__ void __launch_bounds__(kThreads) k_probe(const __grid_constant__ Prob
                 const uint64_t it2 = it + k;
                 const uint64_t tile2 = blockIdx.x + it2 * stride;
                 if (tile2 < A.nstaged)
-                    mbar_wait_bounded(smem_u32(&bars[it2 % A.nstages]),
+                    mbar_wait_bounded(smem_u32(&S.bars[it2 % A.nstages]),
                                       static_cast<uint32_t>((it2 / A.nstages) & 1), A.timeout_ns);
             }
         }
         return;
     }
-
-    __syncthreads();
-    for (uint32_t i = tid; i < A.nsets * A.npreds; i += kThreads) {
-        const uint32_t v = scnt[i];
-        if (v) atomicAdd(&A.counts[i], static_cast<unsigned long long>(v));
-    }
-    if (A.want_marg) {
-        for (uint32_t i = tid; i < A.nsets * A.nterms; i += kThreads) {
-            const uint32_t v = smarg[i];
-            if (v) atomicAdd(&A.marg[i], static_cast<unsigned long long>(v));
+    // warps -> CTA counters -> global
+#pragma unroll
+    for (int q = 0; q < MAXS; ++q) {
+        if (q < static_cast<int>(A.nsets)) {
+            if (has_pred && cnt[q]) atomicAdd(&S.cnt[q * A.npreds + lane], cnt[q]);
+            if (has_term && mc[q]) atomicAdd(&S.marg[q * A.nterms + lane], mc[q]);
         }
     }
-    for (uint32_t i = tid; i < A.nsets; i += kThreads)
-        if (sns[i]) atomicAdd(&A.nsamp[i], static_cast<unsigned long long>(sns[i]));
+    if (lane < static_cast<int>(A.nsets) && nsr) atomicAdd(&S.ns[lane], nsr);
+    __syncthreads();
+    flush(A, S, tid);
+}
+
+// ---------------------------------------------------------------- wide
+
+__global__ void __launch_bounds__(kThreads) k_probe_wide(const __grid_constant__ ProbeArgs A) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const Smem S = carve(A, smem, warp);
+    load_tables(A, S, tid);
+    __syncthreads();
+
+    const uint64_t nslices = (A.nrows + kSliceRows - 1) / kSliceRows;
+    const uint64_t wstride = static_cast<uint64_t>(gridDim.x) * kProbeWarps;
+    uint32_t nsr = 0;
+    for (uint64_t sl = static_cast<uint64_t>(blockIdx.x) * kProbeWarps + warp; sl < nslices; sl += wstride) {
+        const uint64_t row0 = sl * kSliceRows + 4u * lane;
+        set_masks(A, row0, S.keep, lane);
+        for (uint32_t s = 0; s < A.nslots; ++s) {
+            const SlotDesc& sd = A.slots[s];
+            Quad v;
+            load_quad_global(sd.ptr, sd.width, row0, A.nrows, v);
+            eval_slot(sd, v, S.st, S.pool, S.tm, lane);
+        }
+        __syncwarp();
+        for (uint32_t p = lane; p < A.npreds; p += 32) {
+            const uint32_t b = S.poff[p], e = S.poff[p + 1];
+            uint4 acc = S.tm[S.pterm[b]];
+            for (uint32_t k = b + 1; k < e; ++k) acc = and4(acc, S.tm[S.pterm[k]]);
+            for (uint32_t q = 0; q < A.nsets; ++q) {
+                const uint32_t c = popc4(acc, S.keep[q]);
+                if (c) atomicAdd(&S.cnt[q * A.npreds + p], c);
+            }
+        }
+        if (A.want_marg) {
+            for (uint32_t t = lane; t < A.nterms; t += 32) {
+                const uint4 m = S.tm[t];
+                for (uint32_t q = 0; q < A.nsets; ++q) {
+                    const uint32_t c = popc4(m, S.keep[q]);
+                    if (c) atomicAdd(&S.marg[q * A.nterms + t], c);
+                }
+            }
+        }
+        if (lane < static_cast<int>(A.nsets)) {
+            const uint4 k = S.keep[lane];
+            nsr += __popc(k.x) + __popc(k.y) + __popc(k.z) + __popc(k.w);
+        }
+        __syncwarp();
+    }
+    if (lane < static_cast<int>(A.nsets) && nsr) atomicAdd(&S.ns[lane], nsr);
+    __syncthreads();
+    flush(A, S, tid);
 }
 
 uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
@@ -351,19 +487,33 @@ cudaError_t probe_configure() {
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_probe, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if ((e = cudaFuncSetAttribute(k_probe_narrow<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_probe_narrow<kMaxSets>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  optin)))
+        return e;
+    return cudaFuncSetAttribute(k_probe_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
 }
 
 int probe_occupancy(const ProbeArgs& a) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe, kThreads, a.smem_bytes) !=
-        cudaSuccess)
-        return 0;
-    return n;
+    cudaError_t e;
+    if (!a.narrow)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_wide, kThreads, a.smem_bytes);
+    else if (a.nsets == 1)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_narrow<1>, kThreads, a.smem_bytes);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_narrow<kMaxSets>, kThreads, a.smem_bytes);
+    return e == cudaSuccess ? n : 0;
 }
 
 cudaError_t probe_launch(const ProbeArgs& a, int grid, cudaStream_t s) {
-    k_probe<<<grid, kThreads, a.smem_bytes, s>>>(a);
+    if (!a.narrow)
+        k_probe_wide<<<grid, kThreads, a.smem_bytes, s>>>(a);
+    else if (a.nsets == 1)
+        k_probe_narrow<1><<<grid, kThreads, a.smem_bytes, s>>>(a);
+    else
+        k_probe_narrow<kMaxSets><<<grid, kThreads, a.smem_bytes, s>>>(a);
     return cudaGetLastError();
 }
 
