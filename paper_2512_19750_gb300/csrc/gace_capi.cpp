@@ -460,7 +460,7 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
     uint32_t rowbytes = 0;
     for (uint32_t s = 0; s < nslots; ++s) rowbytes += A.slots[s].width;
     A.narrow = (A.npreds <= static_cast<uint32_t>(kNarrowMax) && A.nterms <= static_cast<uint32_t>(kNarrowMax)) ? 1u : 0u;
-    const uint32_t sweep = kSliceRows * kProbeWarps;  // 1024 rows
+    const uint32_t sweep = (A.narrow ? 2u : 1u) * kSliceRows * kProbeWarps;  // rows of one CTA sweep
     uint32_t tile_rows = sweep;
     if (rowbytes > 0)
         while (tile_rows * 2 * rowbytes <= 16384 && tile_rows < 8 * sweep) tile_rows *= 2;  // ~16 KB stages
@@ -671,27 +671,50 @@ gace_status gace_probe_batch(gace_ctx* ctx, uint32_t table_id, const gace_sample
     if (!tab) return fail(GACE_ENOTFOUND, "table %u is not loaded", table_id);
     DeviceGuard g(ctx->device);
 
-    // row sets, ordered so that sets sharing a hash input are adjacent
-    std::vector<SetPlan> sets(nsamples);
-    for (uint32_t s = 0; s < nsamples; ++s) {
-        if (gace_status st = make_set(samples[s], sets[s].d)) return st;
-        sets[s].orig = s;
-    }
-    std::stable_sort(sets.begin(), sets.end(), [](const SetPlan& a, const SetPlan& b) {
-        return std::tie(a.d.kind, a.d.seedhash, a.d.block_rows) < std::tie(b.d.kind, b.d.seedhash, b.d.block_rows);
+    // Device row sets: one set for every sample that keeps all rows (full
+    // scans, rate >= 1), then one per distinct hashed sample, ordered so that
+    // sets sharing a hash input are adjacent.  Samples of rate <= 0 need no
+    // device work.
+    std::vector<SetDesc> sdesc(nsamples);
+    for (uint32_t s = 0; s < nsamples; ++s)
+        if (gace_status st = make_set(samples[s], sdesc[s])) return st;
+    std::vector<SetPlan> sets;
+    std::vector<int32_t> set_dev(nsamples, -1);
+    for (uint32_t s = 0; s < nsamples; ++s)
+        if (sdesc[s].mode == 1) {
+            if (sets.empty()) {
+                SetPlan v;
+                v.d = SetDesc{};
+                v.d.kind = 0;
+                v.d.mode = 1;
+                v.d.block_shift = -1;
+                v.orig = s;
+                sets.push_back(v);
+            }
+            set_dev[s] = 0;
+        }
+    std::vector<SetPlan> hashed;
+    for (uint32_t s = 0; s < nsamples; ++s)
+        if (sdesc[s].mode == 2) hashed.push_back({sdesc[s], s});
+    std::stable_sort(hashed.begin(), hashed.end(), [](const SetPlan& a, const SetPlan& b) {
+        return std::tie(a.d.kind, a.d.seedhash, a.d.block_rows, a.d.thresh) <
+               std::tie(b.d.kind, b.d.seedhash, b.d.block_rows, b.d.thresh);
     });
-    for (uint32_t q = 1; q < nsamples; ++q) {
-        const SetDesc &p = sets[q - 1].d, &c = sets[q].d;
-        sets[q].d.share_prev = (c.mode == 2 && p.mode == 2 && p.kind == c.kind && p.seedhash == c.seedhash &&
-                                p.block_rows == c.block_rows)
-                                   ? 1u
-                                   : 0u;
-        // a set between two hashing sets that does not hash breaks the chain
+    for (const SetPlan& h : hashed) {
+        const SetDesc* last = sets.empty() ? nullptr : &sets.back().d;
+        if (last && last->mode == 2 && last->kind == h.d.kind && last->seedhash == h.d.seedhash &&
+            last->block_rows == h.d.block_rows && last->thresh == h.d.thresh) {
+            set_dev[h.orig] = static_cast<int32_t>(sets.size() - 1);  // identical sample
+            continue;
+        }
+        SetPlan c = h;
+        c.d.share_prev = (last && last->mode == 2 && last->kind == c.d.kind && last->seedhash == c.d.seedhash &&
+                          last->block_rows == c.d.block_rows)
+                             ? 1u
+                             : 0u;
+        set_dev[h.orig] = static_cast<int32_t>(sets.size());
+        sets.push_back(c);
     }
-    for (uint32_t q = 1; q < nsamples; ++q)
-        if (sets[q].d.share_prev && sets[q - 1].d.mode != 2) sets[q].d.share_prev = 0;
-    std::vector<uint32_t> set_pos(nsamples);
-    for (uint32_t q = 0; q < nsamples; ++q) set_pos[sets[q].orig] = q;
 
     // normalise and deduplicate terms
     std::vector<NTerm> uterms;
@@ -801,7 +824,8 @@ gace_status gace_probe_batch(gace_ctx* ctx, uint32_t table_id, const gace_sample
     }
     bool need_ns = false;
     for (auto& s : sets)
-        if (s.d.kind != 0 && s.d.mode == 2) need_ns = true;
+        if (s.d.mode == 2) need_ns = true;
+    if (sets.empty()) passes.clear();  // every sample is empty: nothing to count
     if (passes.empty() && need_ns) passes.push_back(Pass());  // counts sample rows only
 
     // build passes and the workspace layout
@@ -879,14 +903,15 @@ gace_status gace_probe_batch(gace_ctx* ctx, uint32_t table_id, const gace_sample
     // assemble results
     std::vector<uint64_t> ns(nsamples, 0);
     for (uint32_t s = 0; s < nsamples; ++s) {
-        const SetDesc& d = sets[set_pos[s]].d;
-        if (d.mode == 0) ns[s] = 0;
-        else if (d.kind == 0 || d.mode == 1) ns[s] = tab->nrows;
-        else {
+        if (set_dev[s] < 0) continue;
+        const SetDesc& d = sets[set_dev[s]].d;
+        if (d.mode == 1) {
+            ns[s] = tab->nrows;
+        } else {
             const Pass& ps = passes.front();
             const unsigned long long* out = reinterpret_cast<const unsigned long long*>(pin + ps.out_off);
             ns[s] = out[static_cast<uint64_t>(ps.args.nsets) * ps.args.npreds +
-                        static_cast<uint64_t>(ps.args.nsets) * ps.args.nterms + set_pos[s]];
+                        static_cast<uint64_t>(ps.args.nsets) * ps.args.nterms + set_dev[s]];
         }
     }
     // per unique term: (pass, local index)
@@ -897,11 +922,11 @@ gace_status gace_probe_batch(gace_ctx* ctx, uint32_t table_id, const gace_sample
         const uint32_t u = t2u[t];
         if (u == UINT32_MAX) return 0;
         const auto& L = uloc[u];
-        if (L.first < 0) return 0;
+        if (L.first < 0 || set_dev[s] < 0) return 0;
         const Pass& ps = passes[L.first];
         const unsigned long long* out = reinterpret_cast<const unsigned long long*>(pin + ps.out_off);
         return out[static_cast<uint64_t>(ps.args.nsets) * ps.args.npreds +
-                   static_cast<uint64_t>(set_pos[s]) * ps.args.nterms + L.second];
+                   static_cast<uint64_t>(set_dev[s]) * ps.args.nterms + L.second];
     };
     std::vector<std::pair<int32_t, uint32_t>> ploc(npreds, {-1, 0});
     for (uint32_t k = 0; k < passes.size(); ++k)
@@ -911,10 +936,10 @@ gace_status gace_probe_batch(gace_ctx* ctx, uint32_t table_id, const gace_sample
             uint64_t m = 0;
             if (pstate[p] == 2) {
                 m = ns[s];
-            } else if (pstate[p] == 0) {
+            } else if (pstate[p] == 0 && set_dev[s] >= 0) {
                 const Pass& ps = passes[ploc[p].first];
                 const unsigned long long* out = reinterpret_cast<const unsigned long long*>(pin + ps.out_off);
-                m = out[static_cast<uint64_t>(set_pos[s]) * ps.args.npreds + ploc[p].second];
+                m = out[static_cast<uint64_t>(set_dev[s]) * ps.args.npreds + ploc[p].second];
             }
             gace_pred_result& r = results[static_cast<uint64_t>(s) * npreds + p];
             r.match = m;

@@ -68,7 +68,7 @@ __device__ __forceinline__ void smem_byte_max(uint32_t* words, uint32_t j, uint3
     }
 }
 
-template <bool SMEM>
+template <bool SMEM, int DT>
 __global__ void __launch_bounds__(kHllThreads, 2) k_hll(const __grid_constant__ HllArgs A) {
     extern __shared__ uint32_t sregs[];
     const uint32_t m = 1u << A.p;
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kHllThreads, 2) k_hll(const __grid_constant__ 
         __syncthreads();
     }
     const unsigned char* sbytes = reinterpret_cast<const unsigned char*>(sregs);
-    const uint32_t width = A.dtype == 1 ? 8 : 4;
+    constexpr uint32_t width = DT == 1 ? 8 : 4;
     const uint64_t ngroups = (A.nrows + 3) / 4;
     const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kHllThreads;
     for (uint64_t g = static_cast<uint64_t>(blockIdx.x) * kHllThreads + threadIdx.x; g < ngroups;
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kHllThreads, 2) k_hll(const __grid_constant__ 
         uint32_t j[4], rho[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            hll_rank(canonical_key(A.dtype, v.lo[r], v.hi[r]), A.seedhash, A.p, j[r], rho[r]);
+            hll_rank(canonical_key(DT, v.lo[r], v.hi[r]), A.seedhash, A.p, j[r], rho[r]);
             if (row0 + r >= A.nrows) rho[r] = 0;  // past the end: never raises a register
         }
         if (SMEM) {
@@ -244,22 +244,29 @@ int grid_for(uint64_t units, int per_cta, int sms, int ctas_per_sm) {
 
 }  // namespace
 
-cudaError_t hll_launch(const HllArgs& a, int sms, cudaStream_t s) {
+template <bool SMEM, int DT>
+static cudaError_t hll_launch_t(const HllArgs& a, int sms, cudaStream_t s) {
     const uint64_t groups = (a.nrows + 3) / 4;
-    if (a.p <= 17) {
-        const uint32_t smem = (1u << a.p);
-        cudaError_t e = cudaFuncSetAttribute(k_hll<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(smem));
-        if (e != cudaSuccess) return e;
-        int occ = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_hll<true>, kHllThreads, smem);
-        if (e != cudaSuccess) return e;
-        if (occ < 1) occ = 1;
-        k_hll<true><<<grid_for(groups, kHllThreads, sms, occ), kHllThreads, smem, s>>>(a);
-    } else {
-        k_hll<false><<<grid_for(groups, kHllThreads, sms, 2), kHllThreads, 0, s>>>(a);
-    }
+    const uint32_t smem = SMEM ? (1u << a.p) : 0u;
+    cudaError_t e = cudaFuncSetAttribute(k_hll<SMEM, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_hll<SMEM, DT>, kHllThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    k_hll<SMEM, DT><<<grid_for(groups, kHllThreads, sms, occ), kHllThreads, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t hll_launch(const HllArgs& a, int sms, cudaStream_t s) {
+    // registers in shared memory up to p = 17 (128 KB), else straight to global
+    const bool sm = a.p <= 17;
+    switch (a.dtype) {
+        case 0: return sm ? hll_launch_t<true, 0>(a, sms, s) : hll_launch_t<false, 0>(a, sms, s);
+        case 1: return sm ? hll_launch_t<true, 1>(a, sms, s) : hll_launch_t<false, 1>(a, sms, s);
+        default: return sm ? hll_launch_t<true, 2>(a, sms, s) : hll_launch_t<false, 2>(a, sms, s);
+    }
 }
 
 cudaError_t hist_launch(const SideArgs& a, uint32_t* hist, int strict, int aggregate, int sms,

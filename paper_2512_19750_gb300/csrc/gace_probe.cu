@@ -59,8 +59,9 @@ __device__ __forceinline__ Smem carve(const ProbeArgs& A, unsigned char* smem, i
     s.pool = reinterpret_cast<uint32_t*>(smem + A.off_pool);
     s.poff = reinterpret_cast<uint32_t*>(smem + A.off_poff);
     s.pterm = reinterpret_cast<uint32_t*>(smem + A.off_pterm);
-    s.tm = reinterpret_cast<uint4*>(smem + A.off_tm) + warp * A.nterms;
-    s.keep = reinterpret_cast<uint4*>(smem + A.off_keep) + warp * A.nsets;
+    const uint32_t nq = A.narrow ? 2 : 1;
+    s.tm = reinterpret_cast<uint4*>(smem + A.off_tm) + warp * A.nterms * nq;
+    s.keep = reinterpret_cast<uint4*>(smem + A.off_keep) + warp * A.nsets * nq;
     s.cnt = reinterpret_cast<uint32_t*>(smem + A.off_cnt);
     s.marg = reinterpret_cast<uint32_t*>(smem + A.off_marg);
     s.ns = reinterpret_cast<uint32_t*>(smem + A.off_ns);
@@ -95,175 +96,207 @@ __device__ __forceinline__ void flush(const ProbeArgs& A, const Smem& s, int tid
         if (s.ns[i]) atomicAdd(&A.nsamp[i], static_cast<unsigned long long>(s.ns[i]));
 }
 
-// Membership masks of a slice's 128 rows in every row set (stored per warp).
-__device__ __forceinline__ void set_masks(const ProbeArgs& A, uint64_t row0, uint4* keep,
-                                          int lane) {
-    bool valid[4];
+// Values of NQ quads per lane: quad h covers rows slice0 + 128 h + 4 lane + r.
+template <int NQ>
+struct Vals {
+    uint32_t lo[4 * NQ];
+    uint32_t hi[4 * NQ];
+};
+
+template <int NQ>
+__device__ __forceinline__ void load_vals_smem(const unsigned char* slot_tile, uint32_t slice_local,
+                                               uint32_t width, int lane, Vals<NQ>& v) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) valid[r] = row0 + r < A.nrows;
-    uint64_t h[4] = {0, 0, 0, 0};
+    for (int h = 0; h < NQ; ++h) {
+        Quad q;
+        load_quad_smem(slot_tile + (slice_local + 128u * h + 4u * lane) * width, width, q);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            v.lo[4 * h + r] = q.lo[r];
+            v.hi[4 * h + r] = q.hi[r];
+        }
+    }
+}
+
+template <int NQ>
+__device__ __forceinline__ void load_vals_global(const void* ptr, uint32_t width, uint64_t slice0,
+                                                 uint64_t nrows, int lane, Vals<NQ>& v) {
+#pragma unroll
+    for (int h = 0; h < NQ; ++h) {
+        Quad q;
+        load_quad_global(ptr, width, slice0 + 128u * h + 4u * lane, nrows, q);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            v.lo[4 * h + r] = q.lo[r];
+            v.hi[4 * h + r] = q.hi[r];
+        }
+    }
+}
+
+// Ballots of a per-row predicate over the lane's 4 NQ rows: NQ masks of 4 x 32 rows.
+#define GACE_BALLOTS(NQ_, pred_expr, out)                               \
+    _Pragma("unroll") for (int h_ = 0; h_ < NQ_; ++h_) {               \
+        out[h_].x = __ballot_sync(kFullMask, pred_expr(4 * h_ + 0));    \
+        out[h_].y = __ballot_sync(kFullMask, pred_expr(4 * h_ + 1));    \
+        out[h_].z = __ballot_sync(kFullMask, pred_expr(4 * h_ + 2));    \
+        out[h_].w = __ballot_sync(kFullMask, pred_expr(4 * h_ + 3));    \
+    }
+
+// Membership masks of a slice's rows in every row set: keep[q * NQ + h].
+template <int NQ>
+__device__ __forceinline__ void set_masks(const ProbeArgs& A, uint64_t slice0, uint4* keep,
+                                          int lane) {
+    constexpr int R = 4 * NQ;
+    bool valid[R];
+    uint64_t row[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        row[i] = slice0 + 128u * (i / 4) + 4u * lane + (i % 4);
+        valid[i] = row[i] < A.nrows;
+    }
+    uint64_t hsh[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) hsh[i] = 0;
     for (uint32_t q = 0; q < A.nsets; ++q) {
         const SetDesc& sd = A.sets[q];
-        bool k[4];
+        bool k[R];
         if (sd.kind == 0 || sd.mode == 1) {
 #pragma unroll
-            for (int r = 0; r < 4; ++r) k[r] = valid[r];
+            for (int i = 0; i < R; ++i) k[i] = valid[i];
         } else if (sd.mode == 0) {
 #pragma unroll
-            for (int r = 0; r < 4; ++r) k[r] = false;
+            for (int i = 0; i < R; ++i) k[i] = false;
         } else {
             if (!sd.share_prev) {
                 if (sd.kind == 1) {
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) h[r] = splitmix64((row0 + r) ^ sd.seedhash);
+                    for (int i = 0; i < R; ++i) hsh[i] = splitmix64(row[i] ^ sd.seedhash);
                 } else if (sd.block_shift >= 2) {
-                    // the lane's four rows (row0 is a multiple of 4) share one block
-                    const uint64_t hb = splitmix64((row0 >> sd.block_shift) ^ sd.seedhash);
+                    // the four rows of a quad (a multiple of 4 apart from 0) share one block
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) h[r] = hb;
+                    for (int h = 0; h < NQ; ++h) {
+                        const uint64_t hb = splitmix64((row[4 * h] >> sd.block_shift) ^ sd.seedhash);
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) hsh[4 * h + r] = hb;
+                    }
                 } else {
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        const uint64_t x = row0 + r;
-                        const uint64_t b = sd.block_shift >= 0 ? (x >> sd.block_shift) : (x / sd.block_rows);
-                        h[r] = splitmix64(b ^ sd.seedhash);
+                    for (int i = 0; i < R; ++i) {
+                        const uint64_t b = sd.block_shift >= 0 ? (row[i] >> sd.block_shift) : (row[i] / sd.block_rows);
+                        hsh[i] = splitmix64(b ^ sd.seedhash);
                     }
                 }
             }
 #pragma unroll
-            for (int r = 0; r < 4; ++r) k[r] = valid[r] && (h[r] < sd.thresh);
+            for (int i = 0; i < R; ++i) k[i] = valid[i] && (hsh[i] < sd.thresh);
         }
-        uint4 m;
-        m.x = __ballot_sync(kFullMask, k[0]);
-        m.y = __ballot_sync(kFullMask, k[1]);
-        m.z = __ballot_sync(kFullMask, k[2]);
-        m.w = __ballot_sync(kFullMask, k[3]);
-        if (lane == 0) keep[q] = m;
+        uint4 m[NQ];
+#define PK(i) (k[i])
+        GACE_BALLOTS(NQ, PK, m);
+#undef PK
+        if (lane == 0) {
+#pragma unroll
+            for (int h = 0; h < NQ; ++h) keep[q * NQ + h] = m[h];
+        }
     }
 }
 
-#define GACE_BALLOT4(pred_expr, out)                 \
-    do {                                             \
-        out.x = __ballot_sync(kFullMask, pred_expr(0)); \
-        out.y = __ballot_sync(kFullMask, pred_expr(1)); \
-        out.z = __ballot_sync(kFullMask, pred_expr(2)); \
-        out.w = __ballot_sync(kFullMask, pred_expr(3)); \
-    } while (0)
+template <int NQ>
+__device__ __forceinline__ void store_masks(uint4* tm, uint32_t t, const uint4 (&m)[NQ], int lane) {
+    if (lane == 0) {
+#pragma unroll
+        for (int h = 0; h < NQ; ++h) tm[t * NQ + h] = m[h];
+    }
+}
 
-// Evaluates the terms of one column slot on the lane's four rows and stores
-// the warp's four 32-row masks per term (range terms two at a time for ILP).
-__device__ __forceinline__ void eval_slot(const SlotDesc& sd, const Quad& v, const DevTerm* st,
+// Evaluates the terms of one column slot on the lane's 4 NQ rows and stores the
+// warp's NQ x 4 masks of 32 rows per term at tm[t * NQ + h].
+template <int NQ>
+__device__ __forceinline__ void eval_slot(const SlotDesc& sd, const Vals<NQ>& v, const DevTerm* st,
                                           const uint32_t* pool, uint4* tm, int lane) {
+    constexpr int R = 4 * NQ;
     if (sd.dtype == 0) {
-        uint32_t t = sd.rbeg;
-        for (; t + 1 < sd.rend; t += 2) {
-            const uint2 c0 = *reinterpret_cast<const uint2*>(&st[t]);
-            const uint2 c1 = *reinterpret_cast<const uint2*>(&st[t + 1]);
-            uint4 m0, m1;
-#define P0(r) ((v.lo[r] - c0.x) <= c0.y)
-#define P1(r) ((v.lo[r] - c1.x) <= c1.y)
-            GACE_BALLOT4(P0, m0);
-            GACE_BALLOT4(P1, m1);
-#undef P0
-#undef P1
-            if (lane == 0) {
-                tm[t] = m0;
-                tm[t + 1] = m1;
-            }
-        }
-        if (t < sd.rend) {
-            const uint2 c0 = *reinterpret_cast<const uint2*>(&st[t]);
-            uint4 m0;
-#define P0(r) ((v.lo[r] - c0.x) <= c0.y)
-            GACE_BALLOT4(P0, m0);
-#undef P0
-            if (lane == 0) tm[t] = m0;
-        }
-        for (t = sd.rend; t < sd.iend; ++t) {
-            const uint2 c = *reinterpret_cast<const uint2*>(&st[t]);
-            bool h[4] = {false, false, false, false};
-            for (uint32_t k = 0; k < c.y; ++k) {
-                const uint32_t x = pool[c.x + k];
-#pragma unroll
-                for (int r = 0; r < 4; ++r) h[r] |= v.lo[r] == x;
-            }
-            uint4 m;
-#define PH(r) (h[r])
-            GACE_BALLOT4(PH, m);
-#undef PH
-            if (lane == 0) tm[t] = m;
-        }
-    } else if (sd.dtype == 1) {
-        uint64_t x[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) x[r] = join64(v.lo[r], v.hi[r]);
         for (uint32_t t = sd.rbeg; t < sd.rend; ++t) {
-            const DevTerm c = st[t];
-            const uint64_t lo = join64(c.a_lo, c.a_hi), span = join64(c.b_lo, c.b_hi);
-            uint4 m;
-#define P0(r) ((x[r] - lo) <= span)
-            GACE_BALLOT4(P0, m);
-#undef P0
-            if (lane == 0) tm[t] = m;
+            const uint2 c = *reinterpret_cast<const uint2*>(&st[t]);
+            uint4 m[NQ];
+#define PR(i) ((v.lo[i] - c.x) <= c.y)
+            GACE_BALLOTS(NQ, PR, m);
+#undef PR
+            store_masks<NQ>(tm, t, m, lane);
         }
         for (uint32_t t = sd.rend; t < sd.iend; ++t) {
             const uint2 c = *reinterpret_cast<const uint2*>(&st[t]);
-            bool h[4] = {false, false, false, false};
+            bool hit[R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) hit[i] = false;
+            for (uint32_t k = 0; k < c.y; ++k) {
+                const uint32_t x = pool[c.x + k];
+#pragma unroll
+                for (int i = 0; i < R; ++i) hit[i] |= v.lo[i] == x;
+            }
+            uint4 m[NQ];
+#define PH(i) (hit[i])
+            GACE_BALLOTS(NQ, PH, m);
+#undef PH
+            store_masks<NQ>(tm, t, m, lane);
+        }
+    } else if (sd.dtype == 1) {
+        uint64_t x[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) x[i] = join64(v.lo[i], v.hi[i]);
+        for (uint32_t t = sd.rbeg; t < sd.rend; ++t) {
+            const DevTerm c = st[t];
+            const uint64_t lo = join64(c.a_lo, c.a_hi), span = join64(c.b_lo, c.b_hi);
+            uint4 m[NQ];
+#define PR(i) ((x[i] - lo) <= span)
+            GACE_BALLOTS(NQ, PR, m);
+#undef PR
+            store_masks<NQ>(tm, t, m, lane);
+        }
+        for (uint32_t t = sd.rend; t < sd.iend; ++t) {
+            const uint2 c = *reinterpret_cast<const uint2*>(&st[t]);
+            bool hit[R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) hit[i] = false;
             for (uint32_t k = 0; k < c.y; ++k) {
                 const uint64_t y = join64(pool[c.x + 2 * k], pool[c.x + 2 * k + 1]);
 #pragma unroll
-                for (int r = 0; r < 4; ++r) h[r] |= x[r] == y;
+                for (int i = 0; i < R; ++i) hit[i] |= x[i] == y;
             }
-            uint4 m;
-#define PH(r) (h[r])
-            GACE_BALLOT4(PH, m);
+            uint4 m[NQ];
+#define PH(i) (hit[i])
+            GACE_BALLOTS(NQ, PH, m);
 #undef PH
-            if (lane == 0) tm[t] = m;
+            store_masks<NQ>(tm, t, m, lane);
         }
     } else {
-        float x[4];
+        float x[R];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) x[r] = __uint_as_float(v.lo[r]);
-        uint32_t t = sd.rbeg;
-        for (; t + 1 < sd.rend; t += 2) {
-            const uint2 c0 = *reinterpret_cast<const uint2*>(&st[t]);
-            const uint2 c1 = *reinterpret_cast<const uint2*>(&st[t + 1]);
-            const float l0 = __uint_as_float(c0.x), h0 = __uint_as_float(c0.y);
-            const float l1 = __uint_as_float(c1.x), h1 = __uint_as_float(c1.y);
-            uint4 m0, m1;
-#define P0(r) (x[r] >= l0 && x[r] <= h0)
-#define P1(r) (x[r] >= l1 && x[r] <= h1)
-            GACE_BALLOT4(P0, m0);
-            GACE_BALLOT4(P1, m1);
-#undef P0
-#undef P1
-            if (lane == 0) {
-                tm[t] = m0;
-                tm[t + 1] = m1;
-            }
-        }
-        if (t < sd.rend) {
-            const uint2 c0 = *reinterpret_cast<const uint2*>(&st[t]);
-            const float l0 = __uint_as_float(c0.x), h0 = __uint_as_float(c0.y);
-            uint4 m0;
-#define P0(r) (x[r] >= l0 && x[r] <= h0)
-            GACE_BALLOT4(P0, m0);
-#undef P0
-            if (lane == 0) tm[t] = m0;
-        }
-        for (t = sd.rend; t < sd.iend; ++t) {
+        for (int i = 0; i < R; ++i) x[i] = __uint_as_float(v.lo[i]);
+        for (uint32_t t = sd.rbeg; t < sd.rend; ++t) {
             const uint2 c = *reinterpret_cast<const uint2*>(&st[t]);
-            bool h[4] = {false, false, false, false};
+            const float lo = __uint_as_float(c.x), hi = __uint_as_float(c.y);
+            uint4 m[NQ];
+#define PR(i) (x[i] >= lo && x[i] <= hi)
+            GACE_BALLOTS(NQ, PR, m);
+#undef PR
+            store_masks<NQ>(tm, t, m, lane);
+        }
+        for (uint32_t t = sd.rend; t < sd.iend; ++t) {
+            const uint2 c = *reinterpret_cast<const uint2*>(&st[t]);
+            bool hit[R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) hit[i] = false;
             for (uint32_t k = 0; k < c.y; ++k) {
                 const float y = __uint_as_float(pool[c.x + k]);
 #pragma unroll
-                for (int r = 0; r < 4; ++r) h[r] |= x[r] == y;
+                for (int i = 0; i < R; ++i) hit[i] |= x[i] == y;
             }
-            uint4 m;
-#define PH(r) (h[r])
-            GACE_BALLOT4(PH, m);
+            uint4 m[NQ];
+#define PH(i) (hit[i])
+            GACE_BALLOTS(NQ, PH, m);
 #undef PH
-            if (lane == 0) tm[t] = m;
+            store_masks<NQ>(tm, t, m, lane);
         }
     }
 }
@@ -282,8 +315,13 @@ __device__ __forceinline__ void issue_tile(const ProbeArgs& A, unsigned char* st
     }
 }
 
-template <int MAXS>
+// HASH: some row set is a hashed sample (else the only device set is "all rows",
+// whose mask is the validity mask, all ones on full tiles).  MAXS: sets held
+// in registers per lane.
+template <bool HASH, int MAXS>
 __global__ void __launch_bounds__(kThreads, 4) k_probe_narrow(const __grid_constant__ ProbeArgs A) {
+    constexpr int NQ = 2;
+    constexpr uint32_t kSlice = 128 * NQ;
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const Smem S = carve(A, smem, warp);
@@ -310,8 +348,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_probe_narrow(const __grid_const
     const bool has_pred = lane < static_cast<int>(A.npreds);
     const bool has_term = A.want_marg && lane < static_cast<int>(A.nterms);
     const uint32_t pb = has_pred ? S.poff[lane] : 0, pe = has_pred ? S.poff[lane + 1] : 0;
+    const uint32_t nsets = HASH ? A.nsets : 1;
 
-    const uint32_t nslices = A.tile_rows / kSliceRows;
+    const uint32_t nslices = A.tile_rows / kSlice;
     uint64_t it = 0;
     bool aborted = false;
     for (;; ++it) {
@@ -326,38 +365,73 @@ __global__ void __launch_bounds__(kThreads, 4) k_probe_narrow(const __grid_const
         if (!fail) {
             const unsigned char* sbuf = S.stages + stage * A.stage_bytes;
             const uint64_t tile_row0 = tile * A.tile_rows;
+            const bool tile_full = tile_row0 + A.tile_rows <= A.nrows;
             for (uint32_t j = warp; j < nslices; j += kProbeWarps) {
-                const uint64_t slice0 = tile_row0 + static_cast<uint64_t>(j) * kSliceRows;
+                const uint64_t slice0 = tile_row0 + static_cast<uint64_t>(j) * kSlice;
                 if (slice0 >= A.nrows) break;
-                const uint64_t row0 = slice0 + 4u * lane;
-                set_masks(A, row0, S.keep, lane);
+                uint4 vm[NQ];
+                if (HASH) {
+                    set_masks<NQ>(A, slice0, S.keep, lane);
+                } else if (!tile_full) {
+#define PV(i) (slice0 + 128u * ((i) / 4) + 4u * lane + ((i) % 4) < A.nrows)
+                    GACE_BALLOTS(NQ, PV, vm);
+#undef PV
+                }
                 for (uint32_t s = 0; s < A.nslots; ++s) {
                     const SlotDesc& sd = A.slots[s];
-                    Quad v;
+                    Vals<NQ> v;
                     if (staged)
-                        load_quad_smem(sbuf + sd.soff + (j * kSliceRows + 4u * lane) * sd.width,
-                                       sd.width, v);
+                        load_vals_smem<NQ>(sbuf + sd.soff, j * kSlice, sd.width, lane, v);
                     else
-                        load_quad_global(sd.ptr, sd.width, row0, A.nrows, v);
-                    eval_slot(sd, v, S.st, S.pool, S.tm, lane);
+                        load_vals_global<NQ>(sd.ptr, sd.width, slice0, A.nrows, lane, v);
+                    eval_slot<NQ>(sd, v, S.st, S.pool, S.tm, lane);
                 }
                 __syncwarp();
                 if (has_pred) {
-                    uint4 acc = S.tm[S.pterm[pb]];
-                    for (uint32_t k = pb + 1; k < pe; ++k) acc = and4(acc, S.tm[S.pterm[k]]);
+                    uint4 acc[NQ];
 #pragma unroll
-                    for (int q = 0; q < MAXS; ++q)
-                        if (q < static_cast<int>(A.nsets)) cnt[q] += popc4(acc, S.keep[q]);
+                    for (int h = 0; h < NQ; ++h) acc[h] = S.tm[S.pterm[pb] * NQ + h];
+                    for (uint32_t k = pb + 1; k < pe; ++k) {
+                        const uint32_t t = S.pterm[k];
+#pragma unroll
+                        for (int h = 0; h < NQ; ++h) acc[h] = and4(acc[h], S.tm[t * NQ + h]);
+                    }
+                    if (HASH) {
+#pragma unroll
+                        for (int q = 0; q < MAXS; ++q)
+                            if (q < static_cast<int>(nsets))
+#pragma unroll
+                                for (int h = 0; h < NQ; ++h) cnt[q] += popc4(acc[h], S.keep[q * NQ + h]);
+                    } else if (tile_full) {
+#pragma unroll
+                        for (int h = 0; h < NQ; ++h)
+                            cnt[0] += __popc(acc[h].x) + __popc(acc[h].y) + __popc(acc[h].z) + __popc(acc[h].w);
+                    } else {
+#pragma unroll
+                        for (int h = 0; h < NQ; ++h) cnt[0] += popc4(acc[h], vm[h]);
+                    }
                 }
                 if (has_term) {
-                    const uint4 m = S.tm[lane];
 #pragma unroll
-                    for (int q = 0; q < MAXS; ++q)
-                        if (q < static_cast<int>(A.nsets)) mc[q] += popc4(m, S.keep[q]);
+                    for (int h = 0; h < NQ; ++h) {
+                        const uint4 m = S.tm[lane * NQ + h];
+                        if (HASH) {
+#pragma unroll
+                            for (int q = 0; q < MAXS; ++q)
+                                if (q < static_cast<int>(nsets)) mc[q] += popc4(m, S.keep[q * NQ + h]);
+                        } else if (tile_full) {
+                            mc[0] += __popc(m.x) + __popc(m.y) + __popc(m.z) + __popc(m.w);
+                        } else {
+                            mc[0] += popc4(m, vm[h]);
+                        }
+                    }
                 }
-                if (lane < static_cast<int>(A.nsets)) {
-                    const uint4 k = S.keep[lane];
-                    nsr += __popc(k.x) + __popc(k.y) + __popc(k.z) + __popc(k.w);
+                if (HASH && lane < static_cast<int>(nsets)) {
+#pragma unroll
+                    for (int h = 0; h < NQ; ++h) {
+                        const uint4 k = S.keep[lane * NQ + h];
+                        nsr += __popc(k.x) + __popc(k.y) + __popc(k.z) + __popc(k.w);
+                    }
                 }
                 __syncwarp();
             }
@@ -389,12 +463,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_probe_narrow(const __grid_const
     // warps -> CTA counters -> global
 #pragma unroll
     for (int q = 0; q < MAXS; ++q) {
-        if (q < static_cast<int>(A.nsets)) {
+        if (q < static_cast<int>(nsets)) {
             if (has_pred && cnt[q]) atomicAdd(&S.cnt[q * A.npreds + lane], cnt[q]);
             if (has_term && mc[q]) atomicAdd(&S.marg[q * A.nterms + lane], mc[q]);
         }
     }
-    if (lane < static_cast<int>(A.nsets) && nsr) atomicAdd(&S.ns[lane], nsr);
+    if (HASH && lane < static_cast<int>(nsets) && nsr) atomicAdd(&S.ns[lane], nsr);
     __syncthreads();
     flush(A, S, tid);
 }
@@ -412,13 +486,13 @@ __global__ void __launch_bounds__(kThreads) k_probe_wide(const __grid_constant__
     const uint64_t wstride = static_cast<uint64_t>(gridDim.x) * kProbeWarps;
     uint32_t nsr = 0;
     for (uint64_t sl = static_cast<uint64_t>(blockIdx.x) * kProbeWarps + warp; sl < nslices; sl += wstride) {
-        const uint64_t row0 = sl * kSliceRows + 4u * lane;
-        set_masks(A, row0, S.keep, lane);
+        const uint64_t slice0 = sl * kSliceRows;
+        set_masks<1>(A, slice0, S.keep, lane);
         for (uint32_t s = 0; s < A.nslots; ++s) {
             const SlotDesc& sd = A.slots[s];
-            Quad v;
-            load_quad_global(sd.ptr, sd.width, row0, A.nrows, v);
-            eval_slot(sd, v, S.st, S.pool, S.tm, lane);
+            Vals<1> v;
+            load_vals_global<1>(sd.ptr, sd.width, slice0, A.nrows, lane, v);
+            eval_slot<1>(sd, v, S.st, S.pool, S.tm, lane);
         }
         __syncwarp();
         for (uint32_t p = lane; p < A.npreds; p += 32) {
@@ -467,10 +541,11 @@ uint32_t probe_layout(ProbeArgs& a) {
     off += (a.npreds + 1) * 4;
     a.off_pterm = off;
     off = align_up(off + a.npredterms * 4, 16);
+    const uint32_t nq = a.narrow ? 2 : 1;  // quads per lane
     a.off_tm = off;
-    off += kProbeWarps * a.nterms * 16;
+    off += kProbeWarps * a.nterms * 16 * nq;
     a.off_keep = off;
-    off += kProbeWarps * a.nsets * 16;
+    off += kProbeWarps * a.nsets * 16 * nq;
     a.off_cnt = off;
     off += a.nsets * a.npreds * 4;
     a.off_marg = off;
@@ -481,39 +556,52 @@ uint32_t probe_layout(ProbeArgs& a) {
     return off;
 }
 
+template <typename K>
+static cudaError_t set_smem(K kernel, int optin) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+}
+
+// 0: wide, 1: narrow all rows, 2: narrow hashed single set, 3: narrow hashed sets
+static int variant(const ProbeArgs& a) {
+    if (!a.narrow) return 0;
+    bool hash = false;
+    for (uint32_t q = 0; q < a.nsets; ++q)
+        if (a.sets[q].mode == 2) hash = true;
+    if (!hash) return 1;
+    return a.nsets == 1 ? 2 : 3;
+}
+
 cudaError_t probe_configure() {
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_probe_narrow<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin)))
-        return e;
-    if ((e = cudaFuncSetAttribute(k_probe_narrow<kMaxSets>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  optin)))
-        return e;
-    return cudaFuncSetAttribute(k_probe_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if ((e = set_smem(k_probe_narrow<false, 1>, optin))) return e;
+    if ((e = set_smem(k_probe_narrow<true, 1>, optin))) return e;
+    if ((e = set_smem(k_probe_narrow<true, kMaxSets>, optin))) return e;
+    return set_smem(k_probe_wide, optin);
 }
 
 int probe_occupancy(const ProbeArgs& a) {
     int n = 0;
-    cudaError_t e;
-    if (!a.narrow)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_wide, kThreads, a.smem_bytes);
-    else if (a.nsets == 1)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_narrow<1>, kThreads, a.smem_bytes);
-    else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_narrow<kMaxSets>, kThreads, a.smem_bytes);
+    cudaError_t e = cudaSuccess;
+    switch (variant(a)) {
+        case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_wide, kThreads, a.smem_bytes); break;
+        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_narrow<false, 1>, kThreads, a.smem_bytes); break;
+        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_narrow<true, 1>, kThreads, a.smem_bytes); break;
+        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_narrow<true, kMaxSets>, kThreads, a.smem_bytes); break;
+    }
     return e == cudaSuccess ? n : 0;
 }
 
 cudaError_t probe_launch(const ProbeArgs& a, int grid, cudaStream_t s) {
-    if (!a.narrow)
-        k_probe_wide<<<grid, kThreads, a.smem_bytes, s>>>(a);
-    else if (a.nsets == 1)
-        k_probe_narrow<1><<<grid, kThreads, a.smem_bytes, s>>>(a);
-    else
-        k_probe_narrow<kMaxSets><<<grid, kThreads, a.smem_bytes, s>>>(a);
+    switch (variant(a)) {
+        case 0: k_probe_wide<<<grid, kThreads, a.smem_bytes, s>>>(a); break;
+        case 1: k_probe_narrow<false, 1><<<grid, kThreads, a.smem_bytes, s>>>(a); break;
+        case 2: k_probe_narrow<true, 1><<<grid, kThreads, a.smem_bytes, s>>>(a); break;
+        default: k_probe_narrow<true, kMaxSets><<<grid, kThreads, a.smem_bytes, s>>>(a); break;
+    }
     return cudaGetLastError();
 }
 
