@@ -1,0 +1,437 @@
+#!/usr/bin/env python
+"""Benchmark of the GACE probe path on GB300.
+
+One step is the skew + correlation measurement: a 100M-row x 8-column table
+(4 int32, 2 int64, 2 float32; Zipf s = 1.2 and a rho = 0.9 copula on two column
+pairs, N(0,1) floats), 1024 conjunctive predicates of 1-4 terms counted on the
+full table, 0.1 % / 1 % / 10 % row samples and a 1 % sample of 4096-row blocks
+(seed 42) with per-term marginals and PCS, plus HyperLogLog (p = 14) of every
+column.  value = rows measured per second, device-timed with CUDA events on the
+stream the library launches on, inputs resident in HBM.
+
+Also reported in the same line: the dominant kernel's roofline (live CUDA-event
+times from the library's own tracing), the same metric end to end through the
+C ABI from pinned host memory, single-probe scans against the HBM roofline, the
+500M-row join probe, and the CPU oracle timed on a bounded sample.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "probe rows/s & HBM % of peak; batched vs plain probes/s; p50/p99 probe ms"
+WORKLOAD = ("skew_corr: 100M rows x 8 cols (4 i32, 2 i64, 2 f32), 1024 preds of 1-4 terms "
+            "x {full, rows 0.1/1/10 %, blocks 4096 @ 1 %} with marginals + PCS, HLL p=14 x 8 cols")
+SM_COUNT_FALLBACK = 152
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gace", "reference"], default="gace")
+    ap.add_argument("--rows", type=int, default=100_000_000)
+    ap.add_argument("--cpu-rows", type=int, default=250_000,
+                    help="rows of the bounded sample the CPU oracle measures")
+    ap.add_argument("--no-extras", action="store_true", help="skip single-probe, join and e2e legs")
+    return ap.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return {"hbm_gbs": float(p["hbm_gbs"]), "sm_max_mhz": float(p.get("sm_max_mhz", 2070.0)),
+                "source": "measured"}
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.idx)], stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx = max(mx, float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- distributed
+
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+
+    def init(self, backend):
+        if self.world > 1:
+            import torch.distributed as dist
+
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float, device) -> float:
+        if not self.pg:
+            return x
+        import torch
+
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def done(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ----------------------------------------------------------------- workload
+
+SAMPLES_SPEC = [("full", 0, 1.0, 0), ("rows", 1, 0.001, 0), ("rows", 1, 0.01, 0), ("rows", 1, 0.1, 0),
+                ("blocks", 2, 0.01, 4096)]
+
+
+def make_workload(n_rows, device, seed_offset=0):
+    from workloads import Sample, make_predicates, make_skew_corr
+
+    table = make_skew_corr(n=n_rows, seed=1002 + seed_offset, device=device)
+    preds = make_predicates(table, 1024, 1, 4, seed=2002 + seed_offset)
+    samples = [Sample(kind, rate, 42, block or 4096) for _, kind, rate, block in SAMPLES_SPEC]
+    return table, preds, samples
+
+
+def cpu_oracle_rate(table, preds, samples, rows: int):
+    """Rows/s of the single-threaded oracle over the first `rows` rows of the
+    same workload (every sample and every HLL sketch)."""
+    import oracle
+
+    oracle.build()
+    host = [c[:rows].cpu().numpy() for c in table.columns]
+    t0 = time.perf_counter()
+    for s in samples:
+        oracle.probe(host, table.dtypes, preds, s, marginals=True)
+    for c in range(len(host)):
+        oracle.hll_registers(host[c], table.dtypes[c], 14, 42)
+    dt = time.perf_counter() - t0
+    return rows / dt, dt
+
+
+# ----------------------------------------------------------------- reference arm
+
+def run_reference(args, d: Dist):
+    if d.rank != 0:
+        return
+    import torch
+
+    from workloads import make_predicates, make_skew_corr, Sample
+
+    n = min(args.cpu_rows, args.rows)
+    table = make_skew_corr(n=n, seed=1002, device="cpu")
+    preds = make_predicates(table, 1024, 1, 4, seed=2002)
+    samples = [Sample(kind, rate, 42, block or 4096) for _, kind, rate, block in SAMPLES_SPEC]
+    times = []
+    for i in range(args.warmup + args.steps):
+        _, dt = cpu_oracle_rate(table, preds, samples, n)
+        if i >= args.warmup:
+            times.append(dt)
+    ms = 1000.0 * sum(times) / len(times)
+    value = n / (ms / 1000.0)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "rows_per_step": n,
+                   "note": "the reference is the single-threaded CPU oracle on a bounded sample"},
+        "cpu_baseline": {"value": value, "unit": "rows/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {n} rows of the workload, every sample and sketch"},
+        "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    del torch
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- GACE arm
+
+def roofline_of(stats, peaks, sms):
+    """Roofline object of the kernel family with the most device time."""
+    fam, st = max(stats.items(), key=lambda kv: kv[1]["total_ms"])
+    sec = st["total_ms"] / 1000.0
+    if fam == "probe_wide":
+        # compare operations against the INT32 lane peak: SMs x 128 lanes x max clock
+        peak = sms * 128 * peaks["sm_max_mhz"] * 1e6 / 1e12
+        achieved = st["ops"] / sec / 1e12
+        return fam, {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "work": "compare ops (EQ 1, RANGE 2, IN-k k per row)",
+                     "peak_source": f"{sms} SMs x 128 INT32 lanes x {peaks['sm_max_mhz']:.0f} MHz",
+                     "launches": st["launches"], "avg_launch_ms": st["total_ms"] / st["launches"]}
+    achieved = st["bytes"] / sec / 1e9
+    return fam, {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                 "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                 "launches": st["launches"], "avg_launch_ms": st["total_ms"] / st["launches"]}
+
+
+def run_gace(args, d: Dist):
+    import numpy as np
+    import torch
+
+    import paper_2512_19750_gb300 as g
+
+    d.init("nccl")
+    dev = torch.device("cuda", d.local)
+    torch.cuda.set_device(dev)
+    peaks = load_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count or SM_COUNT_FALLBACK
+    stream = torch.cuda.current_stream(dev)
+    table, preds, samples = make_workload(args.rows, dev, seed_offset=d.rank)
+    n = table.nrows
+    table_bytes = int(sum(c.numel() * c.element_size() for c in table.columns))
+    ctx = g.gace_create(d.local, stream=stream)
+    tid = g.gace_load_columns(ctx, table.columns, borrow=True)
+    batch = g.TermBatch(preds, table.dtypes)
+
+    def step(table_id):
+        res, marg = g.gace_probe_batch(ctx, table_id, preds, samples, table.dtypes, marginals=True,
+                                       batch=batch)
+        regs = [g.gace_ndv(ctx, table_id, c, 14, 42) for c in range(len(table.columns))]
+        return res, marg, regs
+
+    for _ in range(args.warmup):
+        step(tid)
+    g.gace_stats_reset(ctx, time_kernels=True)
+    clk = ClockSampler(d.local)
+    d.barrier()
+    torch.cuda.synchronize(dev)
+    clk.start()
+    t_a = torch.cuda.Event(enable_timing=True)
+    t_b = torch.cuda.Event(enable_timing=True)
+    t_a.record(stream)
+    for _ in range(args.steps):
+        step(tid)
+    t_b.record(stream)
+    torch.cuda.synchronize(dev)
+    d.barrier()
+    clocks = clk.stop()
+    ms_total = d.max(t_a.elapsed_time(t_b), dev)
+    stats = g.gace_stats_read(ctx)
+    ms_per_step = ms_total / args.steps
+    value = d.world * n * args.steps / (ms_total / 1000.0)
+    gpu_launches = sum(s["launches"] for s in stats.values())
+    fam, roof = roofline_of(stats, peaks, sms)
+    roof["kernel"] = fam
+    roof["peak_source"] = roof.get("peak_source", f"MEASURED_PEAKS.json hbm_gbs ({peaks['source']})")
+    kernels = {k: {"launches": v["launches"], "total_ms": round(v["total_ms"], 3),
+                   "share": round(v["total_ms"] / max(1e-9, sum(x["total_ms"] for x in stats.values())), 4)}
+               for k, v in stats.items()}
+
+    cpu = None
+    if d.rank == 0 and d.world == 1:
+        m = min(args.cpu_rows, n)
+        rate, dt = cpu_oracle_rate(table, preds, samples, m)
+        cpu = {"value": rate, "unit": "rows/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {m} rows of the same table and batch (all 5 row sets, marginals, "
+                         f"8 HLL sketches), single-threaded, {dt:.1f} s"}
+
+    extras = {}
+    if not args.no_extras:
+        extras["single_probe"] = single_probes(g, ctx, tid, table, peaks, stream)
+        extras["e2e"] = e2e_leg(g, ctx, table, preds, samples, batch, args, stream)
+    g.gace_unload(ctx, tid)
+    if not args.no_extras:
+        del table
+        torch.cuda.empty_cache()
+        extras["join"] = join_leg(g, ctx, dev, peaks, stream)
+    g.gace_destroy(ctx)
+
+    d.barrier()
+    if d.rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": d.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rows": n, "predicates": len(preds),
+                       "terms": sum(len(p) for p in preds), "row_sets": len(samples),
+                       "table_bytes": table_bytes,
+                       "l2": "inputs (4 GB) larger than the 129 MB L2; no flush needed",
+                       "parallelism": f"replicas x{d.world}"},
+            "roofline": roof,
+            "kernels": kernels,
+            "cpu_baseline": cpu,
+            "e2e": extras.get("e2e"),
+            "gpu_launches": gpu_launches,
+            "clocks": clocks,
+            "single_probe": extras.get("single_probe"),
+            "join": extras.get("join"),
+        }
+        print(json.dumps(line), flush=True)
+    d.done()
+
+
+def _timed_calls(g, ctx, fn, reps):
+    g.gace_stats_reset(ctx, time_kernels=True)
+    for _ in range(reps):
+        fn()
+    return g.gace_stats_read(ctx)
+
+
+def single_probes(g, ctx, tid, table, peaks, stream):
+    """One-predicate full scans (the gate's single probes): HBM roofline."""
+    from workloads import FULL, F32, RANGE, Sample, Term
+
+    out = {}
+    n = table.nrows
+    cases = {"1 x int32 RANGE": [0], "1 x int64 RANGE": [4], "2 x int32 RANGE (PCS)": [0, 1],
+             "4 x int32 RANGE": [0, 1, 2, 3]}
+    for name, cols in cases.items():
+        pred = [[Term(c, RANGE, 0, 1000) if table.dtypes[c] != F32 else Term(c, RANGE, -1.0, 1.0)
+                 for c in cols]]
+        b = g.TermBatch(pred, table.dtypes)
+        g.gace_probe_batch(ctx, tid, pred, [Sample(FULL)], table.dtypes, batch=b)
+        st = _timed_calls(g, ctx, lambda: g.gace_probe_batch(ctx, tid, pred, [Sample(FULL)], table.dtypes,
+                                                             batch=b), 10)
+        k = st["probe_narrow"]
+        ms = k["total_ms"] / k["launches"]
+        gbs = k["bytes"] / k["launches"] / (ms / 1000.0) / 1e9
+        out[name] = {"kernel_ms": round(ms, 4), "rows_per_s": n / (ms / 1000.0), "gbs": gbs,
+                     "frac_of_measured_hbm": gbs / peaks["hbm_gbs"]}
+    return out
+
+
+def e2e_leg(g, ctx, table, preds, samples, batch, args, stream):
+    """The same step through the C ABI from pinned host memory: H2D of the
+    table, the probe batch and the 8 sketches, results read back."""
+    import torch
+
+    host = [c.cpu().pin_memory() for c in table.columns]
+    h2d = sum(h.numel() * h.element_size() for h in host)
+
+    def once():
+        t = g.gace_load_columns(ctx, host)
+        res, marg = g.gace_probe_batch(ctx, t, preds, samples, table.dtypes, marginals=True, batch=batch)
+        regs = [g.gace_ndv(ctx, t, c, 14, 42) for c in range(len(table.columns))]
+        g.gace_unload(ctx, t)
+        return res, marg, regs
+
+    res, marg, regs = once()
+    d2h = res.nbytes + marg.nbytes + sum(r[0].nbytes for r in regs)
+    reps = max(2, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        once()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / reps
+    return {"value": table.nrows / dt, "unit": "rows/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1000.0, "steps": reps}
+
+
+def join_leg(g, ctx, dev, peaks, stream):
+    """Join probe: 500M-row fact (Zipf FK over 10M keys) x 10M-row dimension,
+    filters at 1 % and 10 %, gather method; plus the 3-table chain."""
+    import torch
+
+    from workloads import RANGE, Term, make_join
+
+    f, dm, d2 = make_join(seed=1003, device=dev)
+    fid = g.gace_load_columns(ctx, f.columns, borrow=True)
+    did = g.gace_load_columns(ctx, dm.columns, borrow=True)
+    d2id = g.gace_load_columns(ctx, d2.columns, borrow=True)
+    out = {}
+    for w in (10, 100):
+        F = g.JoinSideSpec(fid, 0, [Term(1, RANGE, 0, w)], f.dtypes)
+        D = g.JoinSideSpec(did, 0, [Term(1, RANGE, 0, w)], dm.dtypes)
+        g.gace_join_card(ctx, F, D, 10_000_000)
+        st = _timed_calls(g, ctx, lambda: g.gace_join_card(ctx, F, D, 10_000_000), 5)
+        tot = sum(v["total_ms"] for v in st.values()) / 5
+        gk = st["join_gather"]
+        gms = gk["total_ms"] / gk["launches"]
+        gbs = gk["bytes"] / gk["launches"] / (gms / 1000.0) / 1e9
+        out[f"2-table sel {w / 10:.0f}%"] = {
+            "kernels_ms": round(tot, 4), "fact_rows_per_s": f.nrows / (tot / 1000.0),
+            "gather_gbs": gbs, "gather_frac_of_measured_hbm": gbs / peaks["hbm_gbs"]}
+    F = g.JoinSideSpec(fid, 0, [Term(1, RANGE, 0, 100)], f.dtypes)
+    D = g.JoinSideSpec(did, 0, [Term(1, RANGE, 0, 500)], dm.dtypes)
+    D2 = g.JoinSideSpec(d2id, 0, [Term(1, RANGE, 0, 500)], d2.dtypes)
+    st = _timed_calls(g, ctx, lambda: g.gace_join_card(ctx, F, D, 10_000_000, D2, 1_000_000, 3), 3)
+    out["3-table chain"] = {"kernels_ms": round(sum(v["total_ms"] for v in st.values()) / 3, 4)}
+    for t in (fid, did, d2id):
+        g.gace_unload(ctx, t)
+    del f, dm, d2
+    torch.cuda.empty_cache()
+    return out
+
+
+def main():
+    args = parse_args()
+    d = Dist()
+    if args.impl == "reference":
+        run_reference(args, d)
+        return
+    run_gace(args, d)
+
+
+if __name__ == "__main__":
+    main()

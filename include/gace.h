@@ -251,6 +251,32 @@ typedef struct {
 
 gace_status gace_join_card(gace_ctx* ctx, const gace_join* spec, gace_join_result* out);
 
+/*
+ * Kernel statistics of a context (tracing; the paper decomposes probe time
+ * into transfer, kernel and reduction phases, Section IV-B).  Every launch is
+ * counted with the algorithmic work it was given: rows scanned, bytes of the
+ * referenced columns (the key-only bytes a scan must read), and compare
+ * operations (per row: 1 for an equality, 2 for a range, k for an IN list of
+ * k values, 1 per hashed key or histogram update).  When time_kernels is set,
+ * each launch is also bracketed by CUDA events on the context stream and its
+ * device time accumulated.
+ */
+typedef struct {
+    char name[24];      /* kernel family, NUL-terminated */
+    uint64_t launches;
+    uint64_t rows;
+    uint64_t bytes;
+    uint64_t ops;
+    double total_ms;    /* 0 unless timing was enabled */
+} gace_kernel_stat;
+
+/* Clears the statistics; time_kernels = 1 turns event timing on. */
+gace_status gace_stats_reset(gace_ctx* ctx, uint32_t time_kernels);
+
+/* Copies up to cap entries (one per kernel family seen) into out; *n_out is
+ * the number of families.  Waits for the context stream first. */
+gace_status gace_stats_read(gace_ctx* ctx, gace_kernel_stat* out, uint32_t cap, uint32_t* n_out);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* gace_last_error(void);
 

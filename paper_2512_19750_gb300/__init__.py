@@ -204,6 +204,21 @@ def gace_join_card(ctx, fact: JoinSideSpec, dim: JoinSideSpec, key_domain: int,
             "dim2_rows": int(out.dim2_rows)}
 
 
+def gace_stats_reset(ctx, time_kernels: bool = False) -> None:
+    check(lib().gace_stats_reset(ctx, 1 if time_kernels else 0), "gace_stats_reset")
+
+
+def gace_stats_read(ctx) -> dict:
+    """{kernel family: dict(launches, rows, bytes, ops, total_ms)} since the last reset."""
+    n = C.c_uint32()
+    check(lib().gace_stats_read(ctx, None, 0, C.byref(n)), "gace_stats_read")
+    arr = (_capi.gace_kernel_stat * max(1, n.value))()
+    check(lib().gace_stats_read(ctx, arr, n.value, C.byref(n)), "gace_stats_read")
+    return {arr[i].name.decode(): {"launches": int(arr[i].launches), "rows": int(arr[i].rows),
+                                   "bytes": int(arr[i].bytes), "ops": int(arr[i].ops),
+                                   "total_ms": float(arr[i].total_ms)} for i in range(n.value)}
+
+
 def gace_last_error() -> str:
     return lib().gace_last_error().decode()
 

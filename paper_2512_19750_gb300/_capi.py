@@ -70,6 +70,11 @@ class gace_join_result(C.Structure):
                 ("dim2_rows", C.c_uint64)]
 
 
+class gace_kernel_stat(C.Structure):
+    _fields_ = [("name", C.c_char * 24), ("launches", C.c_uint64), ("rows", C.c_uint64),
+                ("bytes", C.c_uint64), ("ops", C.c_uint64), ("total_ms", C.c_double)]
+
+
 ctx_p = C.c_void_p
 
 # name -> (restype, argtypes); every function declared in include/gace.h
@@ -86,6 +91,9 @@ PROTOTYPES = {
     "gace_ndv": (C.c_int, [ctx_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint64,
                            C.POINTER(C.c_uint8), C.POINTER(C.c_double)]),
     "gace_join_card": (C.c_int, [ctx_p, C.POINTER(gace_join), C.POINTER(gace_join_result)]),
+    "gace_stats_reset": (C.c_int, [ctx_p, C.c_uint32]),
+    "gace_stats_read": (C.c_int, [ctx_p, C.POINTER(gace_kernel_stat), C.c_uint32,
+                                  C.POINTER(C.c_uint32)]),
     "gace_last_error": (C.c_char_p, []),
     "gace_status_string": (C.c_char_p, [C.c_int]),
     "gace_abi_version": (C.c_uint32, []),

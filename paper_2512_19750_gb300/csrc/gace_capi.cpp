@@ -109,6 +109,60 @@ struct gace_ctx {
     uint64_t pin_cap = 0;
     unsigned int* d_status = nullptr;
 
+    // kernel statistics (tracing)
+    struct KStat {
+        uint64_t launches = 0, rows = 0, bytes = 0, ops = 0;
+        double ms = 0.0;
+    };
+    struct Timed {
+        std::string name;
+        cudaEvent_t a, b;
+    };
+    std::map<std::string, KStat> stats;
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<Timed> pending;
+
+    cudaEvent_t take_event() {
+        if (!ev_free.empty()) {
+            cudaEvent_t e = ev_free.back();
+            ev_free.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        return e;
+    }
+
+    // Counts one launch with its algorithmic work and, when timing, brackets
+    // it with events on the context stream.
+    template <typename F>
+    cudaError_t traced(const char* name, uint64_t rows, uint64_t bytes, uint64_t ops, F&& launch) {
+        KStat& k = stats[name];
+        k.launches++;
+        k.rows += rows;
+        k.bytes += bytes;
+        k.ops += ops;
+        if (!timing) return launch();
+        cudaEvent_t a = take_event(), b = take_event();
+        if (a) cudaEventRecord(a, stream);
+        cudaError_t e = launch();
+        if (b) cudaEventRecord(b, stream);
+        if (a && b) pending.push_back({name, a, b});
+        return e;
+    }
+
+    // After a stream synchronisation: fold event pairs into the statistics.
+    void collect() {
+        for (auto& t : pending) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) stats[t.name].ms += ms;
+            ev_free.push_back(t.a);
+            ev_free.push_back(t.b);
+        }
+        pending.clear();
+    }
+
     bool fits(uint64_t extra) const { return budget == 0 || used + extra <= budget; }
 
     gace_status ensure_ws(uint64_t bytes) {
@@ -293,6 +347,14 @@ uint32_t in_count(const NTerm& t) {
     return t.kind == kInI64 ? static_cast<uint32_t>(t.in.size() / 2) : static_cast<uint32_t>(t.in.size());
 }
 
+// Minimum compares a row needs for a term: one for a single value, two for a
+// range, k for an IN list of k values.
+uint64_t term_cost(const NTerm& t) {
+    if (is_in_kind(t.kind)) return in_count(t);
+    const bool single = t.kind == kRangeF32 ? t.a == t.b : t.b == 0;
+    return single ? 1 : 2;
+}
+
 DevTerm make_devterm(const NTerm& t, uint32_t pool_off) {
     DevTerm d{};
     if (is_in_kind(t.kind)) {
@@ -358,6 +420,8 @@ struct Pass {
     std::vector<std::pair<uint32_t, uint32_t>> slots;  // (col, first local term)
     ProbeArgs args{};
     uint64_t in_off = 0, out_off = 0;  // workspace offsets
+    uint64_t ops_per_row = 0;          // compares per row (statistics)
+    uint32_t rowbytes = 0;             // bytes per row of the referenced columns
     uint64_t in_bytes = 0, out_bytes = 0;
 };
 
@@ -417,6 +481,7 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
             ps.pool.insert(ps.pool.end(), t.in.begin(), t.in.end());
         }
         ps.dterms.push_back(make_devterm(t, poff));
+        ps.ops_per_row += term_cost(t);
         if (nslots == 0 || ps.slots.back().first != t.col) {
             if (nslots == kMaxSlots) return fail(GACE_EINVAL, "a pass references more than %d columns", kMaxSlots);
             ps.slots.push_back({t.col, i});
@@ -459,6 +524,7 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
     // wide passes are ALU-bound and load directly.
     uint32_t rowbytes = 0;
     for (uint32_t s = 0; s < nslots; ++s) rowbytes += A.slots[s].width;
+    ps.rowbytes = rowbytes;
     A.narrow = (A.npreds <= static_cast<uint32_t>(kNarrowMax) && A.nterms <= static_cast<uint32_t>(kNarrowMax)) ? 1u : 0u;
     const uint32_t sweep = (A.narrow ? 2u : 1u) * kSliceRows * kProbeWarps;  // rows of one CTA sweep
     uint32_t tile_rows = sweep;
@@ -568,6 +634,8 @@ gace_status gace_destroy(gace_ctx* ctx) {
         if (ctx->ws) cudaFree(ctx->ws);
         if (ctx->pin) cudaFreeHost(ctx->pin);
         if (ctx->d_status) cudaFree(ctx->d_status);
+        ctx->collect();
+        for (cudaEvent_t e : ctx->ev_free) cudaEventDestroy(e);
         if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     }
     delete ctx;
@@ -892,12 +960,15 @@ gace_status gace_probe_batch(gace_ctx* ctx, uint32_t table_id, const gace_sample
         // each CTA keeps 32-bit row counters
         while ((units + grid - 1) / grid * unit_rows >= (1ull << 31)) grid *= 2;
         if (grid > 0x7FFFFFFFull) return fail(GACE_EINVAL, "table too large for one probe grid");
-        CK(probe_launch(ps.args, static_cast<int>(grid), ctx->stream));
+        const uint64_t n = tab->nrows;
+        CK(ctx->traced(ps.args.narrow ? "probe_narrow" : "probe_wide", n, n * ps.rowbytes, n * ps.ops_per_row,
+                       [&] { return probe_launch(ps.args, static_cast<int>(grid), ctx->stream); }));
     }
     const uint64_t rb_lo = status_off, rb_hi = passes.empty() ? status_off + 256 : ws.off;
     (void)out_lo;
     CK(cudaMemcpyAsync(pin + rb_lo, dws + rb_lo, rb_hi - rb_lo, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    ctx->collect();
     if (gace_status st = read_status(ctx, *reinterpret_cast<unsigned int*>(pin + status_off))) return st;
 
     // assemble results
@@ -1003,9 +1074,14 @@ gace_status gace_ndv(gace_ctx* ctx, uint32_t table_id, uint32_t col, uint32_t p,
     a.aligned = (reinterpret_cast<uintptr_t>(a.col) & 15u) == 0;
     a.regs = reinterpret_cast<uint32_t*>(ctx->ws + regs_off);
     a.status = reinterpret_cast<unsigned int*>(ctx->ws + status_off);
-    if (tab->nrows > 0) CK(hll_launch(a, ctx->sms, ctx->stream));
+    if (tab->nrows > 0) {
+        const uint64_t n = tab->nrows;
+        CK(ctx->traced("hll", n, n * dtype_width(tab->cols[col].dtype), n,
+                       [&] { return hll_launch(a, ctx->sms, ctx->stream); }));
+    }
     CK(cudaMemcpyAsync(ctx->pin, ctx->ws, ws.off, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    ctx->collect();
     if (gace_status st = read_status(ctx, *reinterpret_cast<unsigned int*>(ctx->pin + status_off))) return st;
     const uint32_t* r32 = reinterpret_cast<const uint32_t*>(ctx->pin + regs_off);
     std::vector<uint8_t> regs(m);
@@ -1017,8 +1093,13 @@ gace_status gace_ndv(gace_ctx* ctx, uint32_t table_id, uint32_t col, uint32_t p,
 
 // ---------------------------------------------------------------- joins
 
+struct SideWork {
+    uint64_t rows = 0, rowbytes = 0, ops_per_row = 1;
+};
+
 static gace_status build_side(gace_ctx* ctx, const gace_join_side& js, const char* name, int extra_col,
-                              SideArgs& a, std::vector<uint32_t>& pool, TableRec** tab_out, uint32_t* extra_slot) {
+                              SideArgs& a, std::vector<uint32_t>& pool, TableRec** tab_out, uint32_t* extra_slot,
+                              SideWork& work) {
     TableRec* tab = find_table(ctx, js.table_id);
     if (!tab) return fail(GACE_ENOTFOUND, "%s table %u is not loaded", name, js.table_id);
     if (js.key_col >= tab->cols.size()) return fail(GACE_EINVAL, "%s key column %u out of range", name, js.key_col);
@@ -1059,6 +1140,7 @@ static gace_status build_side(gace_ctx* ctx, const gace_join_side& js, const cha
         FilterTerm& ft = a.terms[nt++];
         ft.slot = static_cast<uint32_t>(s);
         ft.kind = n.kind;
+        work.ops_per_row += term_cost(n);
         uint32_t poff = static_cast<uint32_t>(pool.size());
         if (is_in_kind(n.kind)) pool.insert(pool.end(), n.in.begin(), n.in.end());
         ft.c = make_devterm(n, poff);
@@ -1072,6 +1154,8 @@ static gace_status build_side(gace_ctx* ctx, const gace_join_side& js, const cha
     }
     a.nterms = nt;
     a.nslots = static_cast<uint32_t>(slot_col.size());
+    work.rows = tab->nrows;
+    for (uint32_t c : slot_col) work.rowbytes += dtype_width(tab->cols[c].dtype);
     for (uint32_t s = 0; s < slot_col.size(); ++s) {
         a.slot_ptr[s] = tab->cols[slot_col[s]].dptr;
         a.slot_dtype[s] = static_cast<uint32_t>(tab->cols[slot_col[s]].dtype);
@@ -1096,12 +1180,19 @@ gace_status gace_join_card(gace_ctx* ctx, const gace_join* spec, gace_join_resul
     SideArgs F, D, D2;
     TableRec *tf = nullptr, *td = nullptr, *td2 = nullptr;
     uint32_t fk2_slot = 0;
-    if (gace_status st = build_side(ctx, spec->fact, "fact", -1, F, pool, &tf, nullptr)) return st;
+    SideWork wf, wd, wd2;
+    if (gace_status st = build_side(ctx, spec->fact, "fact", -1, F, pool, &tf, nullptr, wf)) return st;
     if (gace_status st = build_side(ctx, spec->dim, "dim", spec->hops == 2 ? static_cast<int>(spec->dim_fk2_col) : -1, D,
-                                    pool, &td, &fk2_slot))
+                                    pool, &td, &fk2_slot, wd))
         return st;
     if (spec->hops == 2)
-        if (gace_status st = build_side(ctx, spec->dim2, "dim2", -1, D2, pool, &td2, nullptr)) return st;
+        if (gace_status st = build_side(ctx, spec->dim2, "dim2", -1, D2, pool, &td2, nullptr, wd2)) return st;
+    auto side = [&](const char* nm, const SideWork& w, auto&& f) {
+        return ctx->traced(nm, w.rows, w.rows * w.rowbytes, w.rows * w.ops_per_row, f);
+    };
+    auto vec = [&](const char* nm, uint64_t n, uint64_t bytes_per, auto&& f) {
+        return ctx->traced(nm, n, n * bytes_per, n, f);
+    };
     const bool hist_dot = spec->method == GACE_JOIN_HIST_DOT;
     if (td->nrows >= (1ull << 32) || (td2 && td2->nrows >= (1ull << 32)))
         return fail(GACE_EINVAL, "a histogrammed dimension has 2^32 or more rows");
@@ -1140,33 +1231,34 @@ gace_status gace_join_card(gace_ctx* ctx, const gace_join* spec, gace_join_resul
     const int sms = ctx->sms;
     uint32_t* hD = reinterpret_cast<uint32_t*>(w + hd_off);
     if (spec->hops == 1) {
-        CK(hist_launch(D, hD, 1, 0, sms, ctx->stream));
-        CK(max_launch(hD, 0, K, sc + 4, sms, ctx->stream));
+        CK(side("join_hist", wd, [&] { return hist_launch(D, hD, 1, 0, sms, ctx->stream); }));
+        CK(vec("join_max", K, 4, [&] { return max_launch(hD, 0, K, sc + 4, sms, ctx->stream); }));
         if (hist_dot) {
             uint32_t* hF = reinterpret_cast<uint32_t*>(w + hf_off);
-            CK(hist_launch(F, hF, 0, 1, sms, ctx->stream));
-            CK(dot_launch(hF, hD, 0, K, sc + 3, sms, ctx->stream));
+            CK(side("join_hist", wf, [&] { return hist_launch(F, hF, 0, 1, sms, ctx->stream); }));
+            CK(vec("join_dot", K, 8, [&] { return dot_launch(hF, hD, 0, K, sc + 3, sms, ctx->stream); }));
         } else {
-            CK(gather_launch(F, hD, 0, sc + 3, sms, ctx->stream));
+            CK(side("join_gather", wf, [&] { return gather_launch(F, hD, 0, sc + 3, sms, ctx->stream); }));
         }
     } else {
         D2.domain = K2;
         D2.pass_count = sc + 2;
         unsigned long long* wk = reinterpret_cast<unsigned long long*>(w + w_off);
-        CK(hist_launch(D2, hD, 1, 0, sms, ctx->stream));
-        CK(max_launch(hD, 0, K2, sc + 4, sms, ctx->stream));
-        CK(chain_weight_launch(D, fk2_slot, K2, hD, wk, sms, ctx->stream));
-        CK(max_launch(wk, 1, K, sc + 5, sms, ctx->stream));
+        CK(side("join_hist", wd2, [&] { return hist_launch(D2, hD, 1, 0, sms, ctx->stream); }));
+        CK(vec("join_max", K2, 4, [&] { return max_launch(hD, 0, K2, sc + 4, sms, ctx->stream); }));
+        CK(side("join_chain", wd, [&] { return chain_weight_launch(D, fk2_slot, K2, hD, wk, sms, ctx->stream); }));
+        CK(vec("join_max", K, 8, [&] { return max_launch(wk, 1, K, sc + 5, sms, ctx->stream); }));
         if (hist_dot) {
             uint32_t* hF = reinterpret_cast<uint32_t*>(w + hf_off);
-            CK(hist_launch(F, hF, 0, 1, sms, ctx->stream));
-            CK(dot_launch(hF, wk, 1, K, sc + 3, sms, ctx->stream));
+            CK(side("join_hist", wf, [&] { return hist_launch(F, hF, 0, 1, sms, ctx->stream); }));
+            CK(vec("join_dot", K, 12, [&] { return dot_launch(hF, wk, 1, K, sc + 3, sms, ctx->stream); }));
         } else {
-            CK(gather_launch(F, wk, 1, sc + 3, sms, ctx->stream));
+            CK(side("join_gather", wf, [&] { return gather_launch(F, wk, 1, sc + 3, sms, ctx->stream); }));
         }
     }
     CK(cudaMemcpyAsync(ctx->pin, w, sc_off + 64, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    ctx->collect();
     const unsigned int st = *reinterpret_cast<unsigned int*>(ctx->pin + status_off);
     if (st & kStatusKeyDomain) return fail(GACE_EINVAL, "a filtered dimension row has a key outside its domain");
     if (gace_status s = read_status(ctx, st)) return s;
@@ -1185,6 +1277,42 @@ gace_status gace_join_card(gace_ctx* ctx, const gace_join* spec, gace_join_resul
     out->fact_rows = h[0];
     out->dim_rows = h[1];
     out->dim2_rows = spec->hops == 2 ? h[2] : 0;
+    return GACE_OK;
+}
+
+gace_status gace_stats_reset(gace_ctx* ctx, uint32_t time_kernels) {
+    if (gace_status s = check_ctx(ctx)) return s;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->collect();
+    ctx->stats.clear();
+    ctx->timing = time_kernels != 0;
+    return GACE_OK;
+}
+
+gace_status gace_stats_read(gace_ctx* ctx, gace_kernel_stat* out, uint32_t cap, uint32_t* n_out) {
+    if (gace_status s = check_ctx(ctx)) return s;
+    if (!n_out || (cap && !out)) return fail(GACE_EINVAL, "out or n_out is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->collect();
+    uint32_t i = 0;
+    for (const auto& kv : ctx->stats) {
+        if (i < cap) {
+            gace_kernel_stat& o = out[i];
+            memset(&o, 0, sizeof(o));
+            strncpy(o.name, kv.first.c_str(), sizeof(o.name) - 1);
+            o.launches = kv.second.launches;
+            o.rows = kv.second.rows;
+            o.bytes = kv.second.bytes;
+            o.ops = kv.second.ops;
+            o.total_ms = kv.second.ms;
+        }
+        ++i;
+    }
+    *n_out = i;
     return GACE_OK;
 }
 
