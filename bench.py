@@ -45,6 +45,8 @@ def parse_args():
     ap.add_argument("--rows", type=int, default=100_000_000)
     ap.add_argument("--cpu-rows", type=int, default=250_000,
                     help="rows of the bounded sample the CPU oracle measures")
+    ap.add_argument("--ref-rows", type=int, default=50_000,
+                    help="rows per step of the reference arm (the oracle)")
     ap.add_argument("--no-extras", action="store_true", help="skip single-probe, join and e2e legs")
     return ap.parse_args()
 
@@ -188,7 +190,7 @@ def run_reference(args, d: Dist):
 
     from workloads import make_predicates, make_skew_corr, Sample
 
-    n = min(args.cpu_rows, args.rows)
+    n = min(args.ref_rows, args.rows)
     table = make_skew_corr(n=n, seed=1002, device="cpu")
     preds = make_predicates(table, 1024, 1, 4, seed=2002)
     samples = [Sample(kind, rate, 42, block or 4096) for _, kind, rate, block in SAMPLES_SPEC]
