@@ -48,6 +48,10 @@ def parse_args():
     ap.add_argument("--ref-rows", type=int, default=50_000,
                     help="rows per step of the reference arm (the oracle)")
     ap.add_argument("--no-extras", action="store_true", help="skip single-probe, join and e2e legs")
+    ap.add_argument("--case", default=None,
+                    choices=["narrow_i32", "narrow_4xi32", "narrow_rows1pct", "wide_batch", "hll_i32",
+                             "join_gather"],
+                    help="profiling driver: run one kernel family three times on a small (--rows) case")
     return ap.parse_args()
 
 
@@ -426,8 +430,50 @@ def join_leg(g, ctx, dev, peaks, stream):
     return out
 
 
+def run_case(args):
+    """Small single-kernel cases for profiler captures (inputs above the L2
+    size, a few GB on the device at most)."""
+    import torch
+
+    import paper_2512_19750_gb300 as g
+    from workloads import FULL, RANGE, ROWS, Sample, Term, make_join, make_predicates
+
+    dev = torch.device("cuda:0")
+    ctx = g.gace_create(0, stream=torch.cuda.current_stream())
+    if args.case == "join_gather":
+        f, dm, _ = make_join(n_fact=args.rows, n_dim=10_000_000, n_dim2=1000, seed=1003, device=dev)
+        fid = g.gace_load_columns(ctx, f.columns, borrow=True)
+        did = g.gace_load_columns(ctx, dm.columns, borrow=True)
+        F = g.JoinSideSpec(fid, 0, [Term(1, RANGE, 0, 100)], f.dtypes)
+        D = g.JoinSideSpec(did, 0, [Term(1, RANGE, 0, 100)], dm.dtypes)
+        for _ in range(3):
+            out = g.gace_join_card(ctx, F, D, 10_000_000)
+        print(json.dumps({"case": args.case, "rows": args.rows, "card": out["card"]}))
+        g.gace_destroy(ctx)
+        return
+    table, preds, samples = make_workload(args.rows, dev)
+    tid = g.gace_load_columns(ctx, table.columns, borrow=True)
+    if args.case.startswith("narrow"):
+        cols = [0, 1, 2, 3] if args.case == "narrow_4xi32" else [0]
+        pred = [[Term(c, RANGE, 0, 1000) for c in cols]]
+        smp = [Sample(ROWS, 0.01, 42)] if args.case == "narrow_rows1pct" else [Sample(FULL)]
+        for _ in range(3):
+            g.gace_probe_batch(ctx, tid, pred, smp, table.dtypes)
+    elif args.case == "wide_batch":
+        for _ in range(1):
+            g.gace_probe_batch(ctx, tid, preds, samples, table.dtypes, marginals=True)
+    elif args.case == "hll_i32":
+        for _ in range(3):
+            g.gace_ndv(ctx, tid, 0, 14, 42)
+    print(json.dumps({"case": args.case, "rows": args.rows}))
+    g.gace_destroy(ctx)
+
+
 def main():
     args = parse_args()
+    if args.case:
+        run_case(args)
+        return
     d = Dist()
     if args.impl == "reference":
         run_reference(args, d)

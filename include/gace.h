@@ -165,7 +165,7 @@ gace_status gace_unload(gace_ctx* ctx, uint32_t table_id);
 
 /*
  * Measurement Engine probe (Section III-B; Key-Only + Bitmask evaluation,
- * Section IV-I): one fused pass over the referenced columns evaluates every
+ * Section IV-H): one fused pass over the referenced columns evaluates every
  * predicate on every requested row set.
  *   samples[nsamples]   1..8 row sets
  *   terms[nterms]       the terms the predicates index; identical terms are

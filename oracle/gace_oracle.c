@@ -11,7 +11,7 @@
  *   - Section III-B: the Measurement Engine measures the selectivity of
  *     candidate conditions by full scans, sampling or block-level summaries.
  *   - Section III-C, Eq. 3: PCS = P(A,B) / (P(A) P(B)).
- *   - Section IV-I (Experiment D): candidate conditions evaluated row by row
+ *   - Section IV-H (Experiment D): candidate conditions evaluated row by row
  *     ("Key-Only + Bitmask").
  *   - Section IV-F (join workload): join cardinality is the measured quantity.
  * The paper names no sampler, no sketch and no join formula; the readings used

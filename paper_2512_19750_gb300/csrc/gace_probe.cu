@@ -2,7 +2,7 @@
 //
 // The Measurement Engine probe (Section III-B of the paper) counts the rows of
 // a full table, a seeded row sample or a seeded block sample on which each
-// candidate conjunction holds; Section IV-I evaluates the candidates with a
+// candidate conjunction holds; Section IV-H evaluates the candidates with a
 // per-row bitmask ("Key-Only + Bitmask").  One pass evaluates a whole batch on
 // up to eight row sets at once.  A warp takes 128-row slices, four
 // consecutive rows per lane; each term becomes four 32-row bit masks through
