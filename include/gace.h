@@ -252,6 +252,37 @@ typedef struct {
 gace_status gace_join_card(gace_ctx* ctx, const gace_join* spec, gace_join_result* out);
 
 /*
+ * HyperLogLog of one device column WITHOUT ANY ALLOCATION, for callers that
+ * cannot allocate device memory: an optimizer's planning hook that must not
+ * trigger cudaMalloc's device-wide synchronisation and unbounded latency while
+ * a query is planned, or a process whose device memory belongs to another
+ * allocator (a database buffer manager, a framework's caching allocator under
+ * a hard cap).  The paper has no counterpart for this entry point; it computes
+ * exactly what gace_ndv computes, without a context.
+ *
+ * Scratch: one fixed array of 328,448 bytes inside the library (32-bit and byte
+ * registers for up to 2^GACE_NOALLOC_MAX_P of them, a value histogram, a status
+ * word); every GPU that loads the library holds it until the process exits.
+ * Every call uses all of it and clears what must start at zero, so calls that
+ * overlap on the GPU (other streams or host threads) race and must be
+ * serialised by the caller.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress, on the current device); make that first
+ * call before any stream capture.  No cudaMalloc, cudaFree or allocating
+ * library routine is called.
+ *   column         device pointer to nrows elements of dtype (the current device)
+ *   p              4..GACE_NOALLOC_MAX_P; larger p is rejected with GACE_EINVAL
+ *   stream         cudaStream_t to run on (NULL: the default stream); the call
+ *                  waits for it before returning
+ *   registers_out  HOST, 2^p bytes, or NULL (may be written even if a device
+ *                  wait then reports GACE_ETIMEDOUT)
+ *   estimate_out   HOST or NULL, as in gace_ndv
+ */
+#define GACE_NOALLOC_MAX_P 16
+gace_status gace_ndv_noalloc(const void* column, int32_t dtype, uint64_t nrows, uint32_t p,
+                             uint64_t hash_seed, void* stream, uint8_t* registers_out,
+                             double* estimate_out);
+
+/*
  * Kernel statistics of a context (tracing; the paper decomposes probe time
  * into transfer, kernel and reduction phases, Section IV-B).  Every launch is
  * counted with the algorithmic work it was given: rows scanned, bytes of the

@@ -167,6 +167,20 @@ def gace_ndv(ctx, table_id: int, col: int, p: int, hash_seed: int):
     return regs, float(est.value)
 
 
+def gace_ndv_noalloc(column, p: int, hash_seed: int, stream=None):
+    """(registers uint8[2^p], estimate) of one CUDA tensor column through the
+    no-allocation entry point (no context; fixed scratch inside the library)."""
+    if not (hasattr(column, "is_cuda") and column.is_cuda and column.is_contiguous()):
+        raise ValueError("column must be a contiguous CUDA tensor")
+    regs = np.zeros(1 << p, dtype=np.uint8)
+    est = C.c_double()
+    check(lib().gace_ndv_noalloc(column.data_ptr() if column.numel() else None, _dtype_code(column.dtype),
+                                 column.numel(), p, int(hash_seed) & ((1 << 64) - 1),
+                                 _stream_handle(stream), regs.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                 C.byref(est)), "gace_ndv_noalloc")
+    return regs, float(est.value)
+
+
 class JoinSideSpec:
     """(table_id, key column, filter terms, column dtypes) of one join side."""
 

@@ -91,6 +91,8 @@ PROTOTYPES = {
     "gace_ndv": (C.c_int, [ctx_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint64,
                            C.POINTER(C.c_uint8), C.POINTER(C.c_double)]),
     "gace_join_card": (C.c_int, [ctx_p, C.POINTER(gace_join), C.POINTER(gace_join_result)]),
+    "gace_ndv_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_uint64, C.c_uint32, C.c_uint64,
+                                   C.c_void_p, C.POINTER(C.c_uint8), C.POINTER(C.c_double)]),
     "gace_stats_reset": (C.c_int, [ctx_p, C.c_uint32]),
     "gace_stats_read": (C.c_int, [ctx_p, C.POINTER(gace_kernel_stat), C.c_uint32,
                                   C.POINTER(C.c_uint32)]),

@@ -14,7 +14,7 @@ LIB = os.path.join(HERE, "libgace.so")
 OBJDIR = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["gace_probe.cu", "gace_hll_join.cu"]
+CUDA_SOURCES = ["gace_probe.cu", "gace_hll_join.cu", "gace_noalloc.cu"]
 HOST_SOURCES = ["gace_capi.cpp"]
 
 

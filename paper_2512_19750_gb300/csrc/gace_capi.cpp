@@ -31,6 +31,12 @@ namespace {
 
 thread_local std::string g_last_error;
 
+}  // namespace
+
+void gace::set_last_error_message(const char* msg) { g_last_error = msg; }
+
+namespace {
+
 gace_status fail(gace_status s, const char* fmt, ...) {
     char buf[512];
     va_list ap;

@@ -106,6 +106,9 @@ struct HllArgs {
 };
 cudaError_t hll_launch(const HllArgs& a, int sms, cudaStream_t s);
 
+// Sets the thread-local message returned by gace_last_error().
+void set_last_error_message(const char* msg);
+
 // ---------------------------------------------------------------- joins
 constexpr int kMaxFilterTerms = 64;
 constexpr int kMaxFilterSlots = 8;
