@@ -353,6 +353,13 @@ uint32_t in_count(const NTerm& t) {
     return t.kind == kInI64 ? static_cast<uint32_t>(t.in.size() / 2) : static_cast<uint32_t>(t.in.size());
 }
 
+// Upper bound of the pool words a term adds to a pass: its IN values (narrow
+// passes) or its entries in a column table of up to 4x as many entries as
+// values, 2 words per 32-bit key and 4 per 64-bit key (wide passes).
+uint32_t pool_estimate(const NTerm& t) {
+    return 16u * static_cast<uint32_t>(std::max<size_t>(1, t.in.size()));
+}
+
 // Minimum compares a row needs for a term: one for a single value, two for a
 // range, k for an IN list of k values.
 uint64_t term_cost(const NTerm& t) {
@@ -414,7 +421,7 @@ gace_status make_set(const gace_sample& s, SetDesc& d) {
 
 constexpr uint32_t kPassTerms = 256;
 constexpr uint32_t kPassPreds = 256;
-constexpr uint32_t kPassPool = 4096;
+constexpr uint32_t kPassPool = 16384;  // pool words: IN lists (narrow) or EQ/IN tables (wide)
 
 struct Pass {
     std::vector<uint32_t> preds;   // device predicate indices (input numbering)
@@ -463,11 +470,19 @@ gace_status read_status(gace_ctx* ctx, unsigned int st) {
 gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::vector<NTerm>& uterms,
                        const std::vector<std::vector<uint32_t>>& pred_u,
                        const std::vector<SetPlan>& sets, bool want_marg) {
-    // order: by column, ranges before IN lists
+    // Narrow passes (at most 32 predicates and terms) evaluate IN lists by
+    // compare; wide passes look up every EQ and IN term of a column in that
+    // column's hash tables.  Order: by column, ranges (or, wide, multi-value
+    // ranges) first, then IN lists (or, wide, single values and IN lists).
+    const bool narrow = ps.preds.size() <= static_cast<size_t>(kNarrowMax) &&
+                        ps.uterms.size() <= static_cast<size_t>(kNarrowMax);
+    auto valueset = [&](const NTerm& t) {
+        return is_in_kind(t.kind) || (!narrow && term_cost(t) == 1);
+    };
     std::vector<uint32_t> order = ps.uterms;
     std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
         const NTerm &a = uterms[x], &b = uterms[y];
-        const int ia = is_in_kind(a.kind), ib = is_in_kind(b.kind);
+        const int ia = valueset(a), ib = valueset(b);
         return std::tie(a.col, ia) < std::tie(b.col, ib);
     });
     std::map<uint32_t, uint32_t> local;
@@ -482,7 +497,7 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
         const NTerm& t = uterms[order[i]];
         local[order[i]] = i;
         uint32_t poff = 0;
-        if (is_in_kind(t.kind)) {
+        if (narrow && is_in_kind(t.kind)) {
             poff = static_cast<uint32_t>(ps.pool.size());
             ps.pool.insert(ps.pool.end(), t.in.begin(), t.in.end());
         }
@@ -501,11 +516,72 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
             sd.iend = i;
         }
         SlotDesc& sd = A.slots[nslots - 1];
-        if (is_in_kind(t.kind)) {
+        if (valueset(t)) {
             sd.iend = i + 1;
         } else {
             sd.rend = i + 1;
             sd.iend = i + 1;
+        }
+    }
+    if (!narrow) {
+        // one open-addressing table per group of 32 EQ/IN terms of a column:
+        // key -> mask of the group's terms that contain it
+        for (uint32_t s = 0; s < nslots; ++s) {
+            SlotDesc& sd = A.slots[s];
+            const uint32_t nvs = sd.iend - sd.rend;
+            if (nvs == 0) continue;
+            const bool is64 = sd.dtype == GACE_I64;
+            const uint32_t ew = is64 ? 4u : 2u;
+            sd.ngroups = (nvs + 31) / 32;
+            // values of each term as (lo, hi) keys, floats with -0 -> +0
+            std::vector<std::vector<std::pair<uint32_t, uint32_t>>> vals(nvs);
+            size_t most = 0;
+            for (uint32_t k = 0; k < nvs; ++k) {
+                const NTerm& t = uterms[order[sd.rend + k]];
+                if (is_in_kind(t.kind)) {
+                    for (size_t w = 0; w < t.in.size(); w += is64 ? 2 : 1)
+                        vals[k].push_back({t.in[w], is64 ? t.in[w + 1] : 0u});
+                } else {
+                    vals[k].push_back({static_cast<uint32_t>(t.a), is64 ? static_cast<uint32_t>(t.a >> 32) : 0u});
+                }
+                if (sd.dtype == GACE_F32)
+                    for (auto& kv : vals[k])
+                        if ((kv.first << 1) == 0) kv.first = 0;
+            }
+            for (uint32_t g = 0; g < sd.ngroups; ++g) {
+                size_t n = 0;
+                for (uint32_t k = 32 * g; k < std::min(nvs, 32 * g + 32); ++k) n += vals[k].size();
+                most = std::max(most, n);
+            }
+            uint32_t tlog = 6;
+            while ((1ull << tlog) < 2 * most) ++tlog;
+            sd.tlog = tlog;
+            const uint32_t cap = 1u << tlog;
+            sd.toff = static_cast<uint32_t>(ps.pool.size());
+            ps.pool.resize(ps.pool.size() + static_cast<size_t>(sd.ngroups) * cap * ew, 0u);
+            for (uint32_t g = 0; g < sd.ngroups; ++g) {
+                uint32_t* tab = ps.pool.data() + sd.toff + static_cast<size_t>(g) * cap * ew;
+                for (uint32_t k = 32 * g; k < std::min(nvs, 32 * g + 32); ++k) {
+                    const uint32_t bit = 1u << (k - 32 * g);
+                    for (const auto& kv : vals[k]) {
+                        uint32_t at = vs_hash(kv.first, kv.second, is64, tlog);
+                        for (;; at = (at + 1) & (cap - 1)) {
+                            uint32_t* e = tab + static_cast<size_t>(at) * ew;
+                            uint32_t& mask = is64 ? e[2] : e[1];
+                            if (mask == 0) {
+                                e[0] = kv.first;
+                                if (is64) e[1] = kv.second;
+                                mask = bit;
+                                break;
+                            }
+                            if (e[0] == kv.first && (!is64 || e[1] == kv.second)) {
+                                mask |= bit;
+                                break;
+                            }
+                        }
+                    }
+                }
+            }
         }
     }
     ps.poff.assign(1, 0);
@@ -531,7 +607,7 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
     uint32_t rowbytes = 0;
     for (uint32_t s = 0; s < nslots; ++s) rowbytes += A.slots[s].width;
     ps.rowbytes = rowbytes;
-    A.narrow = (A.npreds <= static_cast<uint32_t>(kNarrowMax) && A.nterms <= static_cast<uint32_t>(kNarrowMax)) ? 1u : 0u;
+    A.narrow = narrow ? 1u : 0u;
     const uint32_t sweep = (A.narrow ? 2u : 1u) * kSliceRows * kProbeWarps;  // rows of one CTA sweep
     uint32_t tile_rows = sweep;
     if (rowbytes > 0)
@@ -860,10 +936,15 @@ gace_status gace_probe_batch(gace_ctx* ctx, uint32_t table_id, const gace_sample
             for (uint32_t u : pred_u[p])
                 if (!in_cur.count(u)) {
                     ++add_t;
-                    add_pool += static_cast<uint32_t>(uterms[u].in.size());
-                    if (!cols_cur.count(uterms[u].col)) ++add_c;
+                    add_pool += pool_estimate(uterms[u]);
+                    if (!cols_cur.count(uterms[u].col)) {
+                        ++add_c;
+                        add_pool += 256;  // smallest table of a new column
+                    }
                 }
             if (pred_u[p].size() > kPassTerms) return fail(GACE_EINVAL, "predicate %u has too many terms", p);
+            // a predicate too large for a shared pass gets one of its own (a
+            // single predicate evaluates IN lists by compare, with no tables)
             if (!cur.preds.empty() &&
                 (cur.uterms.size() + add_t > kPassTerms || cur.preds.size() + 1 > kPassPreds ||
                  pool_words + add_pool > kPassPool || cols_cur.size() + add_c > static_cast<size_t>(kMaxSlots)))
@@ -873,24 +954,25 @@ gace_status gace_probe_batch(gace_ctx* ctx, uint32_t table_id, const gace_sample
                     in_cur[u] = true;
                     cols_cur[uterms[u].col] = true;
                     cur.uterms.push_back(u);
-                    pool_words += static_cast<uint32_t>(uterms[u].in.size());
                     u_pass[u] = static_cast<int32_t>(passes.size());
                 }
+            pool_words += add_pool;
             cur.preds.push_back(p);
-            if (pool_words > kPassPool) return fail(GACE_EINVAL, "predicate %u IN lists too long", p);
         }
         // terms whose marginals are wanted but that no device predicate placed
         if (want_marg) {
             for (uint32_t u = 0; u < uterms.size(); ++u) {
                 if (u_pass[u] >= 0) continue;
                 const uint32_t add_c = cols_cur.count(uterms[u].col) ? 0 : 1;
-                if (cur.uterms.size() + 1 > kPassTerms || pool_words + uterms[u].in.size() > kPassPool ||
-                    cols_cur.size() + add_c > static_cast<size_t>(kMaxSlots))
+                const uint32_t add_pool = pool_estimate(uterms[u]) + 256 * add_c;
+                if (!cur.uterms.empty() &&
+                    (cur.uterms.size() + 1 > kPassTerms || pool_words + add_pool > kPassPool ||
+                     cols_cur.size() + add_c > static_cast<size_t>(kMaxSlots)))
                     flush();
                 cur.uterms.push_back(u);
                 in_cur[u] = true;
                 cols_cur[uterms[u].col] = true;
-                pool_words += static_cast<uint32_t>(uterms[u].in.size());
+                pool_words += add_pool;
                 u_pass[u] = static_cast<int32_t>(passes.size());
             }
         }

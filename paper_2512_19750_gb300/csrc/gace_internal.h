@@ -46,9 +46,23 @@ struct SlotDesc {
     uint32_t width;      // bytes per element
     uint32_t rbeg;       // range terms of this slot: [rbeg, rend)
     uint32_t rend;
-    uint32_t iend;       // IN terms: [rend, iend)
+    uint32_t iend;       // narrow passes: IN terms [rend, iend); wide passes: EQ and
+                         // IN terms [rend, iend), looked up in the slot's hash tables
     uint32_t soff;       // byte offset of the slot's tile inside a stage buffer
+    uint32_t toff;       // wide passes: pool word offset of the slot's hash tables
+    uint32_t tlog;       // log2 of each table's capacity (entries)
+    uint32_t ngroups;    // tables (groups of up to 32 EQ/IN terms)
 };
+
+// Hash of a key into a wide pass's EQ/IN table of 2^tlog entries (host and
+// device build and probe the same tables).
+#if defined(__CUDACC__)
+__host__ __device__
+#endif
+inline uint32_t vs_hash(uint32_t lo, uint32_t hi, bool is64, uint32_t tlog) {
+    const uint32_t x = is64 ? (lo ^ (hi * 0x85EBCA6Bu)) : lo;
+    return (x * 0x9E3779B1u) >> (32 - tlog);
+}
 
 struct SetDesc {
     uint32_t kind;       // 0 full, 1 rows, 2 blocks

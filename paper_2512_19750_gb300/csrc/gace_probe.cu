@@ -315,23 +315,20 @@ __device__ __forceinline__ void issue_tile(const ProbeArgs& A, unsigned char* st
     }
 }
 
-// HASH: some row set is a hashed sample (else the only device set is "all rows",
-// whose mask is the validity mask, all ones on full tiles).  MAXS: sets held
-// in registers per lane.
-template <bool HASH, int MAXS>
-__global__ void __launch_bounds__(kThreads, 4) k_probe_narrow(const __grid_constant__ ProbeArgs A) {
-    constexpr int NQ = 2;
-    constexpr uint32_t kSlice = 128 * NQ;
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const Smem S = carve(A, smem, warp);
-    load_tables(A, S, tid);
+// The staged tile pipeline shared by the narrow kernels: one thread keeps
+// `nstages` bulk copies of the referenced columns in flight; each warp runs
+// `body(staged, sbuf, j, slice0, tile_full)` on its slices of every tile.  The
+// last (partial) tile, and every tile when a column is not 16-byte aligned, is
+// read with plain loads by the body.  Returns false when a wait gave up (the
+// status bit is set and the CTA's copies in flight have been waited for).
+template <uint32_t kSlice, class Body>
+__device__ __forceinline__ bool run_tiles(const ProbeArgs& A, const Smem& S, int tid, int warp,
+                                          Body&& body) {
     if (tid == 0) {
         for (uint32_t s = 0; s < A.nstages; ++s) mbar_init(smem_u32(&S.bars[s]), 1);
         fence_mbar_init();
     }
     __syncthreads();
-
     const uint64_t stride = gridDim.x;
     if (tid == 0) {
         for (uint32_t s = 0; s < A.nstages; ++s) {
@@ -339,23 +336,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_probe_narrow(const __grid_const
             if (tile < A.nstaged) issue_tile(A, S.stages + s * A.stage_bytes, &S.bars[s], tile);
         }
     }
-
-    // lane-owned counters: predicate `lane`, term `lane`, row set `lane`
-    uint32_t cnt[MAXS], mc[MAXS];
-#pragma unroll
-    for (int q = 0; q < MAXS; ++q) cnt[q] = mc[q] = 0;
-    uint32_t nsr = 0;
-    const bool has_pred = lane < static_cast<int>(A.npreds);
-    const bool has_term = A.want_marg && lane < static_cast<int>(A.nterms);
-    const uint32_t pb = has_pred ? S.poff[lane] : 0, pe = has_pred ? S.poff[lane + 1] : 0;
-    const uint32_t nsets = HASH ? A.nsets : 1;
-
     const uint32_t nslices = A.tile_rows / kSlice;
     uint64_t it = 0;
-    bool aborted = false;
     for (;; ++it) {
         const uint64_t tile = blockIdx.x + it * stride;
-        if (tile >= A.ntiles) break;
+        if (tile >= A.ntiles) return true;
         const bool staged = tile < A.nstaged;
         const uint32_t stage = static_cast<uint32_t>(it % A.nstages);
         bool fail = false;
@@ -369,97 +354,120 @@ __global__ void __launch_bounds__(kThreads, 4) k_probe_narrow(const __grid_const
             for (uint32_t j = warp; j < nslices; j += kProbeWarps) {
                 const uint64_t slice0 = tile_row0 + static_cast<uint64_t>(j) * kSlice;
                 if (slice0 >= A.nrows) break;
-                uint4 vm[NQ];
-                if (HASH) {
-                    set_masks<NQ>(A, slice0, S.keep, lane);
-                } else if (!tile_full) {
-#define PV(i) (slice0 + 128u * ((i) / 4) + 4u * lane + ((i) % 4) < A.nrows)
-                    GACE_BALLOTS(NQ, PV, vm);
-#undef PV
-                }
-                for (uint32_t s = 0; s < A.nslots; ++s) {
-                    const SlotDesc& sd = A.slots[s];
-                    Vals<NQ> v;
-                    if (staged)
-                        load_vals_smem<NQ>(sbuf + sd.soff, j * kSlice, sd.width, lane, v);
-                    else
-                        load_vals_global<NQ>(sd.ptr, sd.width, slice0, A.nrows, lane, v);
-                    eval_slot<NQ>(sd, v, S.st, S.pool, S.tm, lane);
-                }
-                __syncwarp();
-                if (has_pred) {
-                    uint4 acc[NQ];
-#pragma unroll
-                    for (int h = 0; h < NQ; ++h) acc[h] = S.tm[S.pterm[pb] * NQ + h];
-                    for (uint32_t k = pb + 1; k < pe; ++k) {
-                        const uint32_t t = S.pterm[k];
-#pragma unroll
-                        for (int h = 0; h < NQ; ++h) acc[h] = and4(acc[h], S.tm[t * NQ + h]);
-                    }
-                    if (HASH) {
-#pragma unroll
-                        for (int q = 0; q < MAXS; ++q)
-                            if (q < static_cast<int>(nsets))
-#pragma unroll
-                                for (int h = 0; h < NQ; ++h) cnt[q] += popc4(acc[h], S.keep[q * NQ + h]);
-                    } else if (tile_full) {
-#pragma unroll
-                        for (int h = 0; h < NQ; ++h)
-                            cnt[0] += __popc(acc[h].x) + __popc(acc[h].y) + __popc(acc[h].z) + __popc(acc[h].w);
-                    } else {
-#pragma unroll
-                        for (int h = 0; h < NQ; ++h) cnt[0] += popc4(acc[h], vm[h]);
-                    }
-                }
-                if (has_term) {
-#pragma unroll
-                    for (int h = 0; h < NQ; ++h) {
-                        const uint4 m = S.tm[lane * NQ + h];
-                        if (HASH) {
-#pragma unroll
-                            for (int q = 0; q < MAXS; ++q)
-                                if (q < static_cast<int>(nsets)) mc[q] += popc4(m, S.keep[q * NQ + h]);
-                        } else if (tile_full) {
-                            mc[0] += __popc(m.x) + __popc(m.y) + __popc(m.z) + __popc(m.w);
-                        } else {
-                            mc[0] += popc4(m, vm[h]);
-                        }
-                    }
-                }
-                if (HASH && lane < static_cast<int>(nsets)) {
-#pragma unroll
-                    for (int h = 0; h < NQ; ++h) {
-                        const uint4 k = S.keep[lane * NQ + h];
-                        nsr += __popc(k.x) + __popc(k.y) + __popc(k.z) + __popc(k.w);
-                    }
-                }
-                __syncwarp();
+                body(staged, sbuf, j, slice0, tile_full);
             }
         }
-        if (__syncthreads_or(fail)) {
-            aborted = true;
-            break;
-        }
+        if (__syncthreads_or(fail)) break;
         if (tid == 0) {
             const uint64_t next = tile + A.nstages * stride;
             if (next < A.nstaged) issue_tile(A, S.stages + stage * A.stage_bytes, &S.bars[stage], next);
         }
     }
+    if (tid == 0) {
+        atomicOr(A.status, kStatusTimeout);
+        // let this CTA's copies in flight land before its shared memory goes away
+        for (uint32_t k = 0; k < A.nstages; ++k) {
+            const uint64_t it2 = it + k;
+            const uint64_t tile2 = blockIdx.x + it2 * stride;
+            if (tile2 < A.nstaged)
+                mbar_wait_bounded(smem_u32(&S.bars[it2 % A.nstages]),
+                                  static_cast<uint32_t>((it2 / A.nstages) & 1), A.timeout_ns);
+        }
+    }
+    return false;
+}
 
-    if (aborted) {
-        if (tid == 0) {
-            atomicOr(A.status, kStatusTimeout);
-            // let this CTA's copies in flight land before its shared memory goes away
-            for (uint32_t k = 0; k < A.nstages; ++k) {
-                const uint64_t it2 = it + k;
-                const uint64_t tile2 = blockIdx.x + it2 * stride;
-                if (tile2 < A.nstaged)
-                    mbar_wait_bounded(smem_u32(&S.bars[it2 % A.nstages]),
-                                      static_cast<uint32_t>((it2 / A.nstages) & 1), A.timeout_ns);
+// HASH: some row set is a hashed sample (else the only device set is "all rows",
+// whose mask is the validity mask, all ones on full tiles).  MAXS: sets held
+// in registers per lane.
+template <bool HASH, int MAXS>
+__global__ void __launch_bounds__(kThreads, 4) k_probe_narrow(const __grid_constant__ ProbeArgs A) {
+    constexpr int NQ = 2;
+    constexpr uint32_t kSlice = 128 * NQ;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const Smem S = carve(A, smem, warp);
+    load_tables(A, S, tid);
+
+    // lane-owned counters: predicate `lane`, term `lane`, row set `lane`
+    uint32_t cnt[MAXS], mc[MAXS];
+#pragma unroll
+    for (int q = 0; q < MAXS; ++q) cnt[q] = mc[q] = 0;
+    uint32_t nsr = 0;
+    const bool has_pred = lane < static_cast<int>(A.npreds);
+    const bool has_term = A.want_marg && lane < static_cast<int>(A.nterms);
+    const uint32_t pb = has_pred ? S.poff[lane] : 0, pe = has_pred ? S.poff[lane + 1] : 0;
+    const uint32_t nsets = HASH ? A.nsets : 1;
+
+    const bool ok = run_tiles<kSlice>(A, S, tid, warp, [&](bool staged, const unsigned char* sbuf, uint32_t j,
+                                                           uint64_t slice0, bool tile_full) {
+        uint4 vm[NQ];
+        if (HASH) {
+            set_masks<NQ>(A, slice0, S.keep, lane);
+        } else if (!tile_full) {
+#define PV(i) (slice0 + 128u * ((i) / 4) + 4u * lane + ((i) % 4) < A.nrows)
+            GACE_BALLOTS(NQ, PV, vm);
+#undef PV
+        }
+        for (uint32_t s = 0; s < A.nslots; ++s) {
+            const SlotDesc& sd = A.slots[s];
+            Vals<NQ> v;
+            if (staged)
+                load_vals_smem<NQ>(sbuf + sd.soff, j * kSlice, sd.width, lane, v);
+            else
+                load_vals_global<NQ>(sd.ptr, sd.width, slice0, A.nrows, lane, v);
+            eval_slot<NQ>(sd, v, S.st, S.pool, S.tm, lane);
+        }
+        __syncwarp();
+        if (has_pred) {
+            uint4 acc[NQ];
+#pragma unroll
+            for (int h = 0; h < NQ; ++h) acc[h] = S.tm[S.pterm[pb] * NQ + h];
+            for (uint32_t k = pb + 1; k < pe; ++k) {
+                const uint32_t t = S.pterm[k];
+#pragma unroll
+                for (int h = 0; h < NQ; ++h) acc[h] = and4(acc[h], S.tm[t * NQ + h]);
+            }
+            if (HASH) {
+#pragma unroll
+                for (int q = 0; q < MAXS; ++q)
+                    if (q < static_cast<int>(nsets))
+#pragma unroll
+                        for (int h = 0; h < NQ; ++h) cnt[q] += popc4(acc[h], S.keep[q * NQ + h]);
+            } else if (tile_full) {
+#pragma unroll
+                for (int h = 0; h < NQ; ++h)
+                    cnt[0] += __popc(acc[h].x) + __popc(acc[h].y) + __popc(acc[h].z) + __popc(acc[h].w);
+            } else {
+#pragma unroll
+                for (int h = 0; h < NQ; ++h) cnt[0] += popc4(acc[h], vm[h]);
             }
         }
-        return;
-    }
+        if (has_term) {
+#pragma unroll
+            for (int h = 0; h < NQ; ++h) {
+                const uint4 m = S.tm[lane * NQ + h];
+                if (HASH) {
+#pragma unroll
+                    for (int q = 0; q < MAXS; ++q)
+                        if (q < static_cast<int>(nsets)) mc[q] += popc4(m, S.keep[q * NQ + h]);
+                } else if (tile_full) {
+                    mc[0] += __popc(m.x) + __popc(m.y) + __popc(m.z) + __popc(m.w);
+                } else {
+                    mc[0] += popc4(m, vm[h]);
+                }
+            }
+        }
+        if (HASH && lane < static_cast<int>(nsets)) {
+#pragma unroll
+            for (int h = 0; h < NQ; ++h) {
+                const uint4 k = S.keep[lane * NQ + h];
+                nsr += __popc(k.x) + __popc(k.y) + __popc(k.z) + __popc(k.w);
+            }
+        }
+        __syncwarp();
+    });
+    if (!ok) return;
     // warps -> CTA counters -> global
 #pragma unroll
     for (int q = 0; q < MAXS; ++q) {
@@ -473,7 +481,226 @@ __global__ void __launch_bounds__(kThreads, 4) k_probe_narrow(const __grid_const
     flush(A, S, tid);
 }
 
+// Marginal of term t on the warp's rows: lane t accumulates the popcount of
+// the rows (in `base`) on which the term holds.
+template <int R>
+__device__ __forceinline__ void single_marg(uint32_t t, const bool (&cond)[R], const bool (&base)[R],
+                                            int lane, uint32_t& tc) {
+    uint32_t c = 0;
+#pragma unroll
+    for (int i = 0; i < R; ++i) c += __popc(__ballot_sync(kFullMask, cond[i] && base[i]));
+    if (lane == static_cast<int>(t)) tc += c;
+}
+
+// Single-predicate evaluation of one column slot: ok[i] &= term(row i) for
+// every term of the slot (terms of one predicate are ANDed in registers).
+template <int NQ>
+__device__ __forceinline__ void single_slot(const SlotDesc& sd, const Vals<NQ>& v, const DevTerm* st,
+                                            const uint32_t* pool, bool (&ok)[4 * NQ],
+                                            const bool (&base)[4 * NQ], bool marg, int lane,
+                                            uint32_t& tc) {
+    constexpr int R = 4 * NQ;
+    bool cond[R];
+    for (uint32_t t = sd.rbeg; t < sd.iend; ++t) {
+        const bool is_in = t >= sd.rend;
+        if (sd.dtype == 0) {
+            const uint2 c = *reinterpret_cast<const uint2*>(&st[t]);
+            if (!is_in) {
+#pragma unroll
+                for (int i = 0; i < R; ++i) cond[i] = (v.lo[i] - c.x) <= c.y;
+            } else {
+#pragma unroll
+                for (int i = 0; i < R; ++i) cond[i] = false;
+                for (uint32_t k = 0; k < c.y; ++k) {
+                    const uint32_t x = pool[c.x + k];
+#pragma unroll
+                    for (int i = 0; i < R; ++i) cond[i] = cond[i] || v.lo[i] == x;
+                }
+            }
+        } else if (sd.dtype == 1) {
+            if (!is_in) {
+                const DevTerm c = st[t];
+                const uint64_t lo = join64(c.a_lo, c.a_hi), span = join64(c.b_lo, c.b_hi);
+#pragma unroll
+                for (int i = 0; i < R; ++i) cond[i] = (join64(v.lo[i], v.hi[i]) - lo) <= span;
+            } else {
+                const uint2 c = *reinterpret_cast<const uint2*>(&st[t]);
+#pragma unroll
+                for (int i = 0; i < R; ++i) cond[i] = false;
+                for (uint32_t k = 0; k < c.y; ++k) {
+                    const uint32_t xl = pool[c.x + 2 * k], xh = pool[c.x + 2 * k + 1];
+#pragma unroll
+                    for (int i = 0; i < R; ++i) cond[i] = cond[i] || (v.lo[i] == xl && v.hi[i] == xh);
+                }
+            }
+        } else {
+            const uint2 c = *reinterpret_cast<const uint2*>(&st[t]);
+            if (!is_in) {
+                const float lo = __uint_as_float(c.x), hi = __uint_as_float(c.y);
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    const float x = __uint_as_float(v.lo[i]);
+                    cond[i] = x >= lo && x <= hi;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < R; ++i) cond[i] = false;
+                for (uint32_t k = 0; k < c.y; ++k) {
+                    const float y = __uint_as_float(pool[c.x + k]);
+#pragma unroll
+                    for (int i = 0; i < R; ++i) cond[i] = cond[i] || __uint_as_float(v.lo[i]) == y;
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < R; ++i) ok[i] = ok[i] && cond[i];
+        if (marg) single_marg<R>(t, cond, base, lane, tc);
+    }
+}
+
+// One predicate on one row set (the gate's single probe): every lane ANDs the
+// terms of its eight rows in predicate registers and counts the rows that pass;
+// no per-term masks go through shared memory.  HASH: the set is a hashed sample.
+template <bool HASH>
+__global__ void __launch_bounds__(kThreads, 4) k_probe_single(const __grid_constant__ ProbeArgs A) {
+    constexpr int NQ = 2, R = 4 * NQ;
+    constexpr uint32_t kSlice = 128 * NQ;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const Smem S = carve(A, smem, warp);
+    load_tables(A, S, tid);
+    uint32_t cnt = 0, nsr = 0, tc = 0;
+    const bool marg = A.want_marg != 0;
+
+    const bool ok_run = run_tiles<kSlice>(A, S, tid, warp, [&](bool staged, const unsigned char* sbuf, uint32_t j,
+                                                               uint64_t slice0, bool tile_full) {
+        bool base[R];
+        if (HASH) {
+            const SetDesc& sd = A.sets[0];
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                const uint64_t row = slice0 + 128u * (i / 4) + 4u * lane + (i % 4);
+                uint64_t x = row;
+                if (sd.kind == 2) x = sd.block_shift >= 0 ? (row >> sd.block_shift) : (row / sd.block_rows);
+                base[i] = row < A.nrows && splitmix64(x ^ sd.seedhash) < sd.thresh;
+            }
+        } else if (!tile_full) {
+#pragma unroll
+            for (int i = 0; i < R; ++i) base[i] = slice0 + 128u * (i / 4) + 4u * lane + (i % 4) < A.nrows;
+        } else {
+#pragma unroll
+            for (int i = 0; i < R; ++i) base[i] = true;
+        }
+        bool ok[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) ok[i] = base[i];
+        for (uint32_t s = 0; s < A.nslots; ++s) {
+            const SlotDesc& sd = A.slots[s];
+            Vals<NQ> v;
+            if (staged)
+                load_vals_smem<NQ>(sbuf + sd.soff, j * kSlice, sd.width, lane, v);
+            else
+                load_vals_global<NQ>(sd.ptr, sd.width, slice0, A.nrows, lane, v);
+            single_slot<NQ>(sd, v, S.st, S.pool, ok, base, marg, lane, tc);
+        }
+#pragma unroll
+        for (int i = 0; i < R; ++i) cnt += ok[i] ? 1u : 0u;
+        if (HASH) {
+#pragma unroll
+            for (int i = 0; i < R; ++i) nsr += base[i] ? 1u : 0u;
+        }
+    });
+    if (!ok_run) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        cnt += __shfl_down_sync(kFullMask, cnt, o);
+        nsr += __shfl_down_sync(kFullMask, nsr, o);
+    }
+    if (lane == 0 && cnt) atomicAdd(&S.cnt[0], cnt);
+    if (HASH && lane == 0 && nsr) atomicAdd(&S.ns[0], nsr);
+    if (marg && lane < static_cast<int>(A.nterms) && tc) atomicAdd(&S.marg[lane], tc);
+    __syncthreads();
+    flush(A, S, tid);
+}
+
 // ---------------------------------------------------------------- wide
+
+// 32 x 32 bit transpose across a warp: lane i holds row i (bit j = M[i][j]);
+// afterwards lane j holds column j (bit i = M[i][j]).  Five butterfly stages
+// swap the off-diagonal blocks of halving size.
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const uint32_t m = s == 16 ? 0x0000FFFFu
+                         : s == 8  ? 0x00FF00FFu
+                         : s == 4  ? 0x0F0F0F0Fu
+                         : s == 2  ? 0x33333333u
+                                   : 0x55555555u;
+        const uint32_t y = __shfl_xor_sync(kFullMask, x, s);
+        x = (lane & s) ? ((x & ~m) | ((y & ~m) >> s)) : ((x & m) | ((y & m) << s));
+    }
+    return x;
+}
+
+// Mask of the group's EQ/IN terms that hold for key (lo, hi): open addressing,
+// linear probing; an entry with an empty mask ends the search.
+__device__ __forceinline__ uint32_t vs_lookup(const uint32_t* tab, uint32_t cap, bool is64, uint32_t h,
+                                              uint32_t lo, uint32_t hi) {
+    for (uint32_t p = 0; p < cap; ++p) {
+        const uint32_t at = (h + p) & (cap - 1);
+        if (is64) {
+            const uint4 e = reinterpret_cast<const uint4*>(tab)[at];
+            if (e.z == 0) return 0;
+            if (e.x == lo && e.y == hi) return e.z;
+        } else {
+            const uint2 e = reinterpret_cast<const uint2*>(tab)[at];
+            if (e.y == 0) return 0;
+            if (e.x == lo) return e.y;
+        }
+    }
+    return 0;
+}
+
+// EQ and IN terms of one column slot in a wide pass: one table lookup per row
+// gives the 32-bit mask of the group's terms that hold; a warp transpose of
+// each row-group's masks hands lane t the 32-row mask of term t.
+template <int NQ>
+__device__ __forceinline__ void eval_valueset(const SlotDesc& sd, const Vals<NQ>& v, const uint32_t* pool,
+                                              uint4* tm, int lane) {
+    constexpr int R = 4 * NQ;
+    const bool is64 = sd.dtype == 1;
+    const uint32_t cap = 1u << sd.tlog;
+    const uint32_t ew = is64 ? 4u : 2u;
+    uint32_t klo[R], khi[R], hb[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        klo[i] = v.lo[i];
+        khi[i] = is64 ? v.hi[i] : 0u;
+        if (sd.dtype == 2 && (klo[i] << 1) == 0) klo[i] = 0;  // -0 equals +0
+        hb[i] = vs_hash(klo[i], khi[i], is64, sd.tlog);
+    }
+    const uint32_t nvs = sd.iend - sd.rend;
+    for (uint32_t g = 0; g < sd.ngroups; ++g) {
+        const uint32_t* tab = pool + sd.toff + g * cap * ew;
+        uint32_t w[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) w[i] = vs_lookup(tab, cap, is64, hb[i], klo[i], khi[i]);
+        uint4 out[NQ];
+#pragma unroll
+        for (int h = 0; h < NQ; ++h) {
+            out[h].x = transpose32(w[4 * h + 0], lane);
+            out[h].y = transpose32(w[4 * h + 1], lane);
+            out[h].z = transpose32(w[4 * h + 2], lane);
+            out[h].w = transpose32(w[4 * h + 3], lane);
+        }
+        const uint32_t k = 32u * g + lane;
+        if (k < nvs) {
+#pragma unroll
+            for (int h = 0; h < NQ; ++h) tm[(sd.rend + k) * NQ + h] = out[h];
+        }
+    }
+}
+
 
 __global__ void __launch_bounds__(kThreads) k_probe_wide(const __grid_constant__ ProbeArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -492,7 +719,10 @@ __global__ void __launch_bounds__(kThreads) k_probe_wide(const __grid_constant__
             const SlotDesc& sd = A.slots[s];
             Vals<1> v;
             load_vals_global<1>(sd.ptr, sd.width, slice0, A.nrows, lane, v);
-            eval_slot<1>(sd, v, S.st, S.pool, S.tm, lane);
+            SlotDesc ranges = sd;  // ranges by compare; EQ and IN terms by table
+            ranges.iend = sd.rend;
+            eval_slot<1>(ranges, v, S.st, S.pool, S.tm, lane);
+            if (sd.iend > sd.rend) eval_valueset<1>(sd, v, S.pool, S.tm, lane);
         }
         __syncwarp();
         for (uint32_t p = lane; p < A.npreds; p += 32) {
@@ -561,12 +791,15 @@ static cudaError_t set_smem(K kernel, int optin) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
 }
 
-// 0: wide, 1: narrow all rows, 2: narrow hashed single set, 3: narrow hashed sets
+// 0: wide, 1: narrow all rows, 2: narrow hashed single set, 3: narrow hashed
+// sets, 4: single predicate on all rows, 5: single predicate on one hashed set
 static int variant(const ProbeArgs& a) {
     if (!a.narrow) return 0;
     bool hash = false;
     for (uint32_t q = 0; q < a.nsets; ++q)
         if (a.sets[q].mode == 2) hash = true;
+    // the single kernel ANDs every term of the pass: only when the one predicate uses them all
+    if (a.npreds == 1 && a.nsets == 1 && a.npredterms == a.nterms) return hash ? 5 : 4;
     if (!hash) return 1;
     return a.nsets == 1 ? 2 : 3;
 }
@@ -580,6 +813,8 @@ cudaError_t probe_configure() {
     if ((e = set_smem(k_probe_narrow<false, 1>, optin))) return e;
     if ((e = set_smem(k_probe_narrow<true, 1>, optin))) return e;
     if ((e = set_smem(k_probe_narrow<true, kMaxSets>, optin))) return e;
+    if ((e = set_smem(k_probe_single<false>, optin))) return e;
+    if ((e = set_smem(k_probe_single<true>, optin))) return e;
     return set_smem(k_probe_wide, optin);
 }
 
@@ -590,7 +825,9 @@ int probe_occupancy(const ProbeArgs& a) {
         case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_wide, kThreads, a.smem_bytes); break;
         case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_narrow<false, 1>, kThreads, a.smem_bytes); break;
         case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_narrow<true, 1>, kThreads, a.smem_bytes); break;
-        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_narrow<true, kMaxSets>, kThreads, a.smem_bytes); break;
+        case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_narrow<true, kMaxSets>, kThreads, a.smem_bytes); break;
+        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_single<false>, kThreads, a.smem_bytes); break;
+        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_single<true>, kThreads, a.smem_bytes); break;
     }
     return e == cudaSuccess ? n : 0;
 }
@@ -600,7 +837,9 @@ cudaError_t probe_launch(const ProbeArgs& a, int grid, cudaStream_t s) {
         case 0: k_probe_wide<<<grid, kThreads, a.smem_bytes, s>>>(a); break;
         case 1: k_probe_narrow<false, 1><<<grid, kThreads, a.smem_bytes, s>>>(a); break;
         case 2: k_probe_narrow<true, 1><<<grid, kThreads, a.smem_bytes, s>>>(a); break;
-        default: k_probe_narrow<true, kMaxSets><<<grid, kThreads, a.smem_bytes, s>>>(a); break;
+        case 3: k_probe_narrow<true, kMaxSets><<<grid, kThreads, a.smem_bytes, s>>>(a); break;
+        case 4: k_probe_single<false><<<grid, kThreads, a.smem_bytes, s>>>(a); break;
+        default: k_probe_single<true><<<grid, kThreads, a.smem_bytes, s>>>(a); break;
     }
     return cudaGetLastError();
 }

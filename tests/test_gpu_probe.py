@@ -234,3 +234,60 @@ def test_hbm_budget_refuses_table(g, cuda):
         g.gace_load_columns(ctx, [torch.zeros(1 << 20, dtype=torch.int32, device=cuda)], borrow=True)
     finally:
         g.gace_destroy(ctx)
+
+
+def test_single_predicate_kernel_shapes(g, gctx, orc, cuda):
+    """One predicate on one row set (the single-predicate kernel): every
+    dtype, IN lists, hashed samples, marginals for PCS, ragged tails, and a
+    batch whose marginal-only terms must not join the predicate."""
+    for n in (1, 255, 257, 4097, 300_001):
+        t = make_skew_corr(n=n, seed=60 + n % 97, device=cuda, domain=1000)
+        tid = g.gace_load_columns(gctx, t.columns)
+        host = host_columns(t)
+        try:
+            cases = [
+                [Term(0, RANGE, 0, 30)], [Term(4, IN, values=(0, 1, 5, 9))], [Term(6, RANGE, -0.5, 0.5)],
+                [Term(0, RANGE, 0, 30), Term(1, EQ, 0)], [Term(2, IN, values=(0, 3)), Term(5, RANGE, 0, 7),
+                                                          Term(7, RANGE, 0.0, 2.0)],
+            ]
+            for pred in cases:
+                for smp in (Sample(FULL), Sample(ROWS, 0.05, 42), Sample(BLOCKS, 0.2, 9, 512),
+                            Sample(BLOCKS, 0.3, 9, 3)):
+                    check_probe(g, orc, gctx, tid, host, t.dtypes, [pred], [smp])
+            # an always-false predicate leaves marginal-only terms in the pass
+            check_probe(g, orc, gctx, tid, host, t.dtypes,
+                        [[Term(0, RANGE, 0, 30)], [Term(1, EQ, 0), Term(3, EQ, 2**40)]], [Sample(FULL)])
+        finally:
+            g.gace_unload(gctx, tid)
+
+
+def test_wide_pass_value_tables(g, gctx, orc, cuda):
+    """Wide passes look EQ and IN terms up in per-column hash tables: many
+    groups of 32 terms on one column, int64 keys, float -0/+0/NaN, values
+    shared by several terms, and values absent from the column."""
+    rng = np.random.default_rng(3)
+    n = 100_003
+    i32 = rng.integers(-50, 50, n).astype(np.int32)
+    i64 = (rng.integers(-40, 40, n).astype(np.int64) * (2**33 + 1))
+    f32 = rng.choice(np.array([0.0, -0.0, 1.5, -2.25, np.nan, np.inf, 3.0], dtype=np.float32), n)
+    cols = [i32, i64, f32]
+    preds = []
+    for v in range(-60, 60):
+        preds.append([Term(0, EQ, v)])
+    for k in range(40):
+        vals = tuple(int(x) for x in rng.integers(-55, 55, 1 + k % 9))
+        preds.append([Term(0, IN, values=vals)])
+    for v in range(-45, 45, 2):
+        preds.append([Term(1, EQ, v * (2**33 + 1))])
+        preds.append([Term(1, IN, values=(v * (2**33 + 1), (v + 1) * (2**33 + 1), 7))])
+    for x in (0.0, -0.0, 1.5, -2.25, float("nan"), float("inf"), 2.0):
+        preds.append([Term(2, EQ, x)])
+    preds.append([Term(2, IN, values=(-0.0, 3.0, float("nan")))])
+    preds.append([Term(0, EQ, 3), Term(1, IN, values=(0, 2**33 + 1)), Term(2, EQ, 0.0)])
+    preds.append([Term(0, RANGE, -10, 10), Term(0, IN, values=(1, 2, 3, 99))])
+    tid = g.gace_load_columns(gctx, cols)
+    try:
+        check_probe(g, orc, gctx, tid, cols, [I32, I64, F32], preds,
+                    [Sample(FULL), Sample(ROWS, 0.4, 5), Sample(BLOCKS, 0.5, 5, 128)])
+    finally:
+        g.gace_unload(gctx, tid)
