@@ -388,6 +388,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_probe_narrow(const __grid_const
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const Smem S = carve(A, smem, warp);
     load_tables(A, S, tid);
+    __syncthreads();  // the tables are read below, before the pipeline's own barrier
 
     // lane-owned counters: predicate `lane`, term `lane`, row set `lane`
     uint32_t cnt[MAXS], mc[MAXS];
@@ -569,6 +570,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_probe_single(const __grid_const
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const Smem S = carve(A, smem, warp);
     load_tables(A, S, tid);
+    __syncthreads();
     uint32_t cnt = 0, nsr = 0, tc = 0;
     const bool marg = A.want_marg != 0;
 
