@@ -482,80 +482,85 @@ __global__ void __launch_bounds__(kThreads, 4) k_probe_narrow(const __grid_const
     flush(A, S, tid);
 }
 
-// Marginal of term t on the warp's rows: lane t accumulates the popcount of
-// the rows (in `base`) on which the term holds.
-template <int R>
-__device__ __forceinline__ void single_marg(uint32_t t, const bool (&cond)[R], const bool (&base)[R],
-                                            int lane, uint32_t& tc) {
-    uint32_t c = 0;
-#pragma unroll
-    for (int i = 0; i < R; ++i) c += __popc(__ballot_sync(kFullMask, cond[i] && base[i]));
-    if (lane == static_cast<int>(t)) tc += c;
-}
+// Bit i of the result: per-row predicate `pred_expr(i)` for the lane's 4 NQ rows.
+#define GACE_ROWBITS(R_, pred_expr, out)               \
+    do {                                               \
+        out = 0u;                                      \
+        _Pragma("unroll") for (int i_ = 0; i_ < R_; ++i_) \
+            if (pred_expr(i_)) out |= 1u << i_;        \
+    } while (0)
 
-// Single-predicate evaluation of one column slot: ok[i] &= term(row i) for
-// every term of the slot (terms of one predicate are ANDed in registers).
+// Single-predicate evaluation of one column slot: for every term of the slot,
+// the lane's row results as a bit mask; ok &= mask; with marginals, the warp
+// total of (mask & base) goes to lane t.
 template <int NQ>
 __device__ __forceinline__ void single_slot(const SlotDesc& sd, const Vals<NQ>& v, const DevTerm* st,
-                                            const uint32_t* pool, bool (&ok)[4 * NQ],
-                                            const bool (&base)[4 * NQ], bool marg, int lane,
-                                            uint32_t& tc) {
+                                            const uint32_t* pool, uint32_t& ok, uint32_t base, bool marg,
+                                            int lane, uint32_t& tc) {
     constexpr int R = 4 * NQ;
-    bool cond[R];
-    for (uint32_t t = sd.rbeg; t < sd.iend; ++t) {
-        const bool is_in = t >= sd.rend;
+    const uint32_t rb = sd.rbeg, re = sd.rend, ie = sd.iend;
+    for (uint32_t t = rb; t < ie; ++t) {
+        uint32_t cb;
         if (sd.dtype == 0) {
             const uint2 c = *reinterpret_cast<const uint2*>(&st[t]);
-            if (!is_in) {
-#pragma unroll
-                for (int i = 0; i < R; ++i) cond[i] = (v.lo[i] - c.x) <= c.y;
+            if (t < re) {
+#define PR(i) ((v.lo[i] - c.x) <= c.y)
+                GACE_ROWBITS(R, PR, cb);
+#undef PR
             } else {
-#pragma unroll
-                for (int i = 0; i < R; ++i) cond[i] = false;
+                cb = 0u;
                 for (uint32_t k = 0; k < c.y; ++k) {
                     const uint32_t x = pool[c.x + k];
-#pragma unroll
-                    for (int i = 0; i < R; ++i) cond[i] = cond[i] || v.lo[i] == x;
+                    uint32_t e;
+#define PE(i) (v.lo[i] == x)
+                    GACE_ROWBITS(R, PE, e);
+#undef PE
+                    cb |= e;
                 }
             }
         } else if (sd.dtype == 1) {
-            if (!is_in) {
+            if (t < re) {
                 const DevTerm c = st[t];
                 const uint64_t lo = join64(c.a_lo, c.a_hi), span = join64(c.b_lo, c.b_hi);
-#pragma unroll
-                for (int i = 0; i < R; ++i) cond[i] = (join64(v.lo[i], v.hi[i]) - lo) <= span;
+#define PR(i) ((join64(v.lo[i], v.hi[i]) - lo) <= span)
+                GACE_ROWBITS(R, PR, cb);
+#undef PR
             } else {
                 const uint2 c = *reinterpret_cast<const uint2*>(&st[t]);
-#pragma unroll
-                for (int i = 0; i < R; ++i) cond[i] = false;
+                cb = 0u;
                 for (uint32_t k = 0; k < c.y; ++k) {
                     const uint32_t xl = pool[c.x + 2 * k], xh = pool[c.x + 2 * k + 1];
-#pragma unroll
-                    for (int i = 0; i < R; ++i) cond[i] = cond[i] || (v.lo[i] == xl && v.hi[i] == xh);
+                    uint32_t e;
+#define PE(i) (v.lo[i] == xl && v.hi[i] == xh)
+                    GACE_ROWBITS(R, PE, e);
+#undef PE
+                    cb |= e;
                 }
             }
         } else {
             const uint2 c = *reinterpret_cast<const uint2*>(&st[t]);
-            if (!is_in) {
+            if (t < re) {
                 const float lo = __uint_as_float(c.x), hi = __uint_as_float(c.y);
-#pragma unroll
-                for (int i = 0; i < R; ++i) {
-                    const float x = __uint_as_float(v.lo[i]);
-                    cond[i] = x >= lo && x <= hi;
-                }
+#define PR(i) (__uint_as_float(v.lo[i]) >= lo && __uint_as_float(v.lo[i]) <= hi)
+                GACE_ROWBITS(R, PR, cb);
+#undef PR
             } else {
-#pragma unroll
-                for (int i = 0; i < R; ++i) cond[i] = false;
+                cb = 0u;
                 for (uint32_t k = 0; k < c.y; ++k) {
                     const float y = __uint_as_float(pool[c.x + k]);
-#pragma unroll
-                    for (int i = 0; i < R; ++i) cond[i] = cond[i] || __uint_as_float(v.lo[i]) == y;
+                    uint32_t e;
+#define PE(i) (__uint_as_float(v.lo[i]) == y)
+                    GACE_ROWBITS(R, PE, e);
+#undef PE
+                    cb |= e;
                 }
             }
         }
-#pragma unroll
-        for (int i = 0; i < R; ++i) ok[i] = ok[i] && cond[i];
-        if (marg) single_marg<R>(t, cond, base, lane, tc);
+        ok &= cb;
+        if (marg) {
+            const uint32_t c = __reduce_add_sync(kFullMask, __popc(cb & base));
+            if (lane == static_cast<int>(t)) tc += c;
+        }
     }
 }
 
@@ -566,6 +571,7 @@ template <bool HASH>
 __global__ void __launch_bounds__(kThreads, 4) k_probe_single(const __grid_constant__ ProbeArgs A) {
     constexpr int NQ = 2, R = 4 * NQ;
     constexpr uint32_t kSlice = 128 * NQ;
+    constexpr uint32_t kAll = (1u << R) - 1u;
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const Smem S = carve(A, smem, warp);
@@ -576,26 +582,24 @@ __global__ void __launch_bounds__(kThreads, 4) k_probe_single(const __grid_const
 
     const bool ok_run = run_tiles<kSlice>(A, S, tid, warp, [&](bool staged, const unsigned char* sbuf, uint32_t j,
                                                                uint64_t slice0, bool tile_full) {
-        bool base[R];
+        // bit i: row slice0 + 128 (i / 4) + 4 lane + i % 4 is in the row set
+        uint32_t base = kAll;
         if (HASH) {
             const SetDesc& sd = A.sets[0];
+            base = 0u;
 #pragma unroll
             for (int i = 0; i < R; ++i) {
                 const uint64_t row = slice0 + 128u * (i / 4) + 4u * lane + (i % 4);
                 uint64_t x = row;
                 if (sd.kind == 2) x = sd.block_shift >= 0 ? (row >> sd.block_shift) : (row / sd.block_rows);
-                base[i] = row < A.nrows && splitmix64(x ^ sd.seedhash) < sd.thresh;
+                if (row < A.nrows && splitmix64(x ^ sd.seedhash) < sd.thresh) base |= 1u << i;
             }
         } else if (!tile_full) {
-#pragma unroll
-            for (int i = 0; i < R; ++i) base[i] = slice0 + 128u * (i / 4) + 4u * lane + (i % 4) < A.nrows;
-        } else {
-#pragma unroll
-            for (int i = 0; i < R; ++i) base[i] = true;
+#define PV(i) (slice0 + 128u * ((i) / 4) + 4u * lane + ((i) % 4) < A.nrows)
+            GACE_ROWBITS(R, PV, base);
+#undef PV
         }
-        bool ok[R];
-#pragma unroll
-        for (int i = 0; i < R; ++i) ok[i] = base[i];
+        uint32_t ok = base;
         for (uint32_t s = 0; s < A.nslots; ++s) {
             const SlotDesc& sd = A.slots[s];
             Vals<NQ> v;
@@ -605,19 +609,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_probe_single(const __grid_const
                 load_vals_global<NQ>(sd.ptr, sd.width, slice0, A.nrows, lane, v);
             single_slot<NQ>(sd, v, S.st, S.pool, ok, base, marg, lane, tc);
         }
-#pragma unroll
-        for (int i = 0; i < R; ++i) cnt += ok[i] ? 1u : 0u;
-        if (HASH) {
-#pragma unroll
-            for (int i = 0; i < R; ++i) nsr += base[i] ? 1u : 0u;
-        }
+        cnt += __popc(ok);
+        if (HASH) nsr += __popc(base);
     });
     if (!ok_run) return;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        cnt += __shfl_down_sync(kFullMask, cnt, o);
-        nsr += __shfl_down_sync(kFullMask, nsr, o);
-    }
+    cnt = __reduce_add_sync(kFullMask, cnt);
+    nsr = __reduce_add_sync(kFullMask, nsr);
     if (lane == 0 && cnt) atomicAdd(&S.cnt[0], cnt);
     if (HASH && lane == 0 && nsr) atomicAdd(&S.ns[0], nsr);
     if (marg && lane < static_cast<int>(A.nterms) && tc) atomicAdd(&S.marg[lane], tc);
