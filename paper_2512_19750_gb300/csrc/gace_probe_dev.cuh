@@ -1,0 +1,411 @@
+// gace_probe_dev.cuh -- device code of the predicate-batch probe shared by the
+// probe kernels and the batched work-queue kernel (one definition, included by
+// each translation unit that launches it).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gace_device.cuh"
+#include "gace_internal.h"
+
+namespace gace {
+namespace probe_dev {
+
+using namespace dev;
+
+constexpr int kThreads = kProbeWarps * 32;
+
+struct Smem {
+    uint64_t* bars;
+    unsigned char* stages;
+    DevTerm* st;
+    uint32_t* pool;
+    uint32_t* poff;
+    uint32_t* pterm;
+    uint4* tm;    // this warp's term masks
+    uint4* keep;  // this warp's row-set masks
+    uint32_t* cnt;
+    uint32_t* marg;
+    uint32_t* ns;
+};
+
+__device__ __forceinline__ Smem carve(const ProbeArgs& A, unsigned char* smem, int warp) {
+    Smem s;
+    s.bars = reinterpret_cast<uint64_t*>(smem);
+    s.stages = smem + A.off_stage;
+    s.st = reinterpret_cast<DevTerm*>(smem + A.off_terms);
+    s.pool = reinterpret_cast<uint32_t*>(smem + A.off_pool);
+    s.poff = reinterpret_cast<uint32_t*>(smem + A.off_poff);
+    s.pterm = reinterpret_cast<uint32_t*>(smem + A.off_pterm);
+    const uint32_t nq = A.narrow ? 2 : 1;
+    s.tm = reinterpret_cast<uint4*>(smem + A.off_tm) + warp * A.nterms * nq;
+    s.keep = reinterpret_cast<uint4*>(smem + A.off_keep) + warp * A.nsets * nq;
+    s.cnt = reinterpret_cast<uint32_t*>(smem + A.off_cnt);
+    s.marg = reinterpret_cast<uint32_t*>(smem + A.off_marg);
+    s.ns = reinterpret_cast<uint32_t*>(smem + A.off_ns);
+    return s;
+}
+
+// Copies the pass tables into shared memory and zeroes the CTA counters.
+__device__ __forceinline__ void load_tables(const ProbeArgs& A, const Smem& s, int tid) {
+    for (uint32_t i = tid; i < A.nterms; i += kThreads) s.st[i] = A.terms[i];
+    for (uint32_t i = tid; i < A.npool; i += kThreads) s.pool[i] = A.pool[i];
+    for (uint32_t i = tid; i <= A.npreds; i += kThreads) s.poff[i] = A.pred_off[i];
+    for (uint32_t i = tid; i < A.npredterms; i += kThreads) s.pterm[i] = A.pred_terms[i];
+    for (uint32_t i = tid; i < A.nsets * A.npreds; i += kThreads) s.cnt[i] = 0;
+    if (A.want_marg)
+        for (uint32_t i = tid; i < A.nsets * A.nterms; i += kThreads) s.marg[i] = 0;
+    for (uint32_t i = tid; i < A.nsets; i += kThreads) s.ns[i] = 0;
+}
+
+// CTA counters -> global 64-bit totals (zeros skipped).
+__device__ __forceinline__ void flush(const ProbeArgs& A, const Smem& s, int tid) {
+    for (uint32_t i = tid; i < A.nsets * A.npreds; i += kThreads) {
+        const uint32_t v = s.cnt[i];
+        if (v) atomicAdd(&A.counts[i], static_cast<unsigned long long>(v));
+    }
+    if (A.want_marg) {
+        for (uint32_t i = tid; i < A.nsets * A.nterms; i += kThreads) {
+            const uint32_t v = s.marg[i];
+            if (v) atomicAdd(&A.marg[i], static_cast<unsigned long long>(v));
+        }
+    }
+    for (uint32_t i = tid; i < A.nsets; i += kThreads)
+        if (s.ns[i]) atomicAdd(&A.nsamp[i], static_cast<unsigned long long>(s.ns[i]));
+}
+
+// Values of NQ quads per lane: quad h covers rows slice0 + 128 h + 4 lane + r.
+template <int NQ>
+struct Vals {
+    uint32_t lo[4 * NQ];
+    uint32_t hi[4 * NQ];
+};
+
+template <int NQ>
+__device__ __forceinline__ void load_vals_smem(const unsigned char* slot_tile, uint32_t slice_local,
+                                               uint32_t width, int lane, Vals<NQ>& v) {
+#pragma unroll
+    for (int h = 0; h < NQ; ++h) {
+        Quad q;
+        load_quad_smem(slot_tile + (slice_local + 128u * h + 4u * lane) * width, width, q);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            v.lo[4 * h + r] = q.lo[r];
+            v.hi[4 * h + r] = q.hi[r];
+        }
+    }
+}
+
+template <int NQ>
+__device__ __forceinline__ void load_vals_global(const void* ptr, uint32_t width, uint64_t slice0,
+                                                 uint64_t nrows, int lane, Vals<NQ>& v) {
+#pragma unroll
+    for (int h = 0; h < NQ; ++h) {
+        Quad q;
+        load_quad_global(ptr, width, slice0 + 128u * h + 4u * lane, nrows, q);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            v.lo[4 * h + r] = q.lo[r];
+            v.hi[4 * h + r] = q.hi[r];
+        }
+    }
+}
+
+// Ballots of a per-row predicate over the lane's 4 NQ rows: NQ masks of 4 x 32 rows.
+#define GACE_BALLOTS(NQ_, pred_expr, out)                               \
+    _Pragma("unroll") for (int h_ = 0; h_ < NQ_; ++h_) {               \
+        out[h_].x = __ballot_sync(kFullMask, pred_expr(4 * h_ + 0));    \
+        out[h_].y = __ballot_sync(kFullMask, pred_expr(4 * h_ + 1));    \
+        out[h_].z = __ballot_sync(kFullMask, pred_expr(4 * h_ + 2));    \
+        out[h_].w = __ballot_sync(kFullMask, pred_expr(4 * h_ + 3));    \
+    }
+
+// Membership masks of a slice's rows in every row set: keep[q * NQ + h].
+template <int NQ>
+__device__ __forceinline__ void set_masks(const ProbeArgs& A, uint64_t slice0, uint4* keep,
+                                          int lane) {
+    constexpr int R = 4 * NQ;
+    bool valid[R];
+    uint64_t row[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        row[i] = slice0 + 128u * (i / 4) + 4u * lane + (i % 4);
+        valid[i] = row[i] < A.nrows;
+    }
+    uint64_t hsh[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) hsh[i] = 0;
+    for (uint32_t q = 0; q < A.nsets; ++q) {
+        const SetDesc& sd = A.sets[q];
+        bool k[R];
+        if (sd.kind == 0 || sd.mode == 1) {
+#pragma unroll
+            for (int i = 0; i < R; ++i) k[i] = valid[i];
+        } else if (sd.mode == 0) {
+#pragma unroll
+            for (int i = 0; i < R; ++i) k[i] = false;
+        } else {
+            if (!sd.share_prev) {
+                if (sd.kind == 1) {
+#pragma unroll
+                    for (int i = 0; i < R; ++i) hsh[i] = splitmix64(row[i] ^ sd.seedhash);
+                } else if (sd.block_shift >= 2) {
+                    // the four rows of a quad (a multiple of 4 apart from 0) share one block
+#pragma unroll
+                    for (int h = 0; h < NQ; ++h) {
+                        const uint64_t hb = splitmix64((row[4 * h] >> sd.block_shift) ^ sd.seedhash);
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) hsh[4 * h + r] = hb;
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < R; ++i) {
+                        const uint64_t b = sd.block_shift >= 0 ? (row[i] >> sd.block_shift) : (row[i] / sd.block_rows);
+                        hsh[i] = splitmix64(b ^ sd.seedhash);
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < R; ++i) k[i] = valid[i] && (hsh[i] < sd.thresh);
+        }
+        uint4 m[NQ];
+#define PK(i) (k[i])
+        GACE_BALLOTS(NQ, PK, m);
+#undef PK
+        if (lane == 0) {
+#pragma unroll
+            for (int h = 0; h < NQ; ++h) keep[q * NQ + h] = m[h];
+        }
+    }
+}
+
+template <int NQ>
+__device__ __forceinline__ void store_masks(uint4* tm, uint32_t t, const uint4 (&m)[NQ], int lane) {
+    if (lane == 0) {
+#pragma unroll
+        for (int h = 0; h < NQ; ++h) tm[t * NQ + h] = m[h];
+    }
+}
+
+// Evaluates the terms of one column slot on the lane's 4 NQ rows and stores the
+// warp's NQ x 4 masks of 32 rows per term at tm[t * NQ + h].
+template <int NQ>
+__device__ __forceinline__ void eval_slot(const SlotDesc& sd, const Vals<NQ>& v, const DevTerm* st,
+                                          const uint32_t* pool, uint4* tm, int lane) {
+    constexpr int R = 4 * NQ;
+    if (sd.dtype == 0) {
+        for (uint32_t t = sd.rbeg; t < sd.rend; ++t) {
+            const uint2 c = *reinterpret_cast<const uint2*>(&st[t]);
+            uint4 m[NQ];
+#define PR(i) ((v.lo[i] - c.x) <= c.y)
+            GACE_BALLOTS(NQ, PR, m);
+#undef PR
+            store_masks<NQ>(tm, t, m, lane);
+        }
+        for (uint32_t t = sd.rend; t < sd.iend; ++t) {
+            const uint2 c = *reinterpret_cast<const uint2*>(&st[t]);
+            bool hit[R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) hit[i] = false;
+            for (uint32_t k = 0; k < c.y; ++k) {
+                const uint32_t x = pool[c.x + k];
+#pragma unroll
+                for (int i = 0; i < R; ++i) hit[i] |= v.lo[i] == x;
+            }
+            uint4 m[NQ];
+#define PH(i) (hit[i])
+            GACE_BALLOTS(NQ, PH, m);
+#undef PH
+            store_masks<NQ>(tm, t, m, lane);
+        }
+    } else if (sd.dtype == 1) {
+        uint64_t x[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) x[i] = join64(v.lo[i], v.hi[i]);
+        for (uint32_t t = sd.rbeg; t < sd.rend; ++t) {
+            const DevTerm c = st[t];
+            const uint64_t lo = join64(c.a_lo, c.a_hi), span = join64(c.b_lo, c.b_hi);
+            uint4 m[NQ];
+#define PR(i) ((x[i] - lo) <= span)
+            GACE_BALLOTS(NQ, PR, m);
+#undef PR
+            store_masks<NQ>(tm, t, m, lane);
+        }
+        for (uint32_t t = sd.rend; t < sd.iend; ++t) {
+            const uint2 c = *reinterpret_cast<const uint2*>(&st[t]);
+            bool hit[R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) hit[i] = false;
+            for (uint32_t k = 0; k < c.y; ++k) {
+                const uint64_t y = join64(pool[c.x + 2 * k], pool[c.x + 2 * k + 1]);
+#pragma unroll
+                for (int i = 0; i < R; ++i) hit[i] |= x[i] == y;
+            }
+            uint4 m[NQ];
+#define PH(i) (hit[i])
+            GACE_BALLOTS(NQ, PH, m);
+#undef PH
+            store_masks<NQ>(tm, t, m, lane);
+        }
+    } else {
+        float x[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) x[i] = __uint_as_float(v.lo[i]);
+        for (uint32_t t = sd.rbeg; t < sd.rend; ++t) {
+            const uint2 c = *reinterpret_cast<const uint2*>(&st[t]);
+            const float lo = __uint_as_float(c.x), hi = __uint_as_float(c.y);
+            uint4 m[NQ];
+#define PR(i) (x[i] >= lo && x[i] <= hi)
+            GACE_BALLOTS(NQ, PR, m);
+#undef PR
+            store_masks<NQ>(tm, t, m, lane);
+        }
+        for (uint32_t t = sd.rend; t < sd.iend; ++t) {
+            const uint2 c = *reinterpret_cast<const uint2*>(&st[t]);
+            bool hit[R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) hit[i] = false;
+            for (uint32_t k = 0; k < c.y; ++k) {
+                const float y = __uint_as_float(pool[c.x + k]);
+#pragma unroll
+                for (int i = 0; i < R; ++i) hit[i] |= x[i] == y;
+            }
+            uint4 m[NQ];
+#define PH(i) (hit[i])
+            GACE_BALLOTS(NQ, PH, m);
+#undef PH
+            store_masks<NQ>(tm, t, m, lane);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- wide
+
+// 32 x 32 bit transpose across a warp: lane i holds row i (bit j = M[i][j]);
+// afterwards lane j holds column j (bit i = M[i][j]).  Five butterfly stages
+// swap the off-diagonal blocks of halving size.
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const uint32_t m = s == 16 ? 0x0000FFFFu
+                         : s == 8  ? 0x00FF00FFu
+                         : s == 4  ? 0x0F0F0F0Fu
+                         : s == 2  ? 0x33333333u
+                                   : 0x55555555u;
+        const uint32_t y = __shfl_xor_sync(kFullMask, x, s);
+        x = (lane & s) ? ((x & ~m) | ((y & ~m) >> s)) : ((x & m) | ((y & m) << s));
+    }
+    return x;
+}
+
+// Mask of the group's EQ/IN terms that hold for key (lo, hi): open addressing,
+// linear probing; an entry with an empty mask ends the search.
+__device__ __forceinline__ uint32_t vs_lookup(const uint32_t* tab, uint32_t cap, bool is64, uint32_t h,
+                                              uint32_t lo, uint32_t hi) {
+    for (uint32_t p = 0; p < cap; ++p) {
+        const uint32_t at = (h + p) & (cap - 1);
+        if (is64) {
+            const uint4 e = reinterpret_cast<const uint4*>(tab)[at];
+            if (e.z == 0) return 0;
+            if (e.x == lo && e.y == hi) return e.z;
+        } else {
+            const uint2 e = reinterpret_cast<const uint2*>(tab)[at];
+            if (e.y == 0) return 0;
+            if (e.x == lo) return e.y;
+        }
+    }
+    return 0;
+}
+
+// EQ and IN terms of one column slot in a wide pass: one table lookup per row
+// gives the 32-bit mask of the group's terms that hold; a warp transpose of
+// each row-group's masks hands lane t the 32-row mask of term t.
+template <int NQ>
+__device__ __forceinline__ void eval_valueset(const SlotDesc& sd, const Vals<NQ>& v, const uint32_t* pool,
+                                              uint4* tm, int lane) {
+    constexpr int R = 4 * NQ;
+    const bool is64 = sd.dtype == 1;
+    const uint32_t cap = 1u << sd.tlog;
+    const uint32_t ew = is64 ? 4u : 2u;
+    uint32_t klo[R], khi[R], hb[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        klo[i] = v.lo[i];
+        khi[i] = is64 ? v.hi[i] : 0u;
+        if (sd.dtype == 2 && (klo[i] << 1) == 0) klo[i] = 0;  // -0 equals +0
+        hb[i] = vs_hash(klo[i], khi[i], is64, sd.tlog);
+    }
+    const uint32_t nvs = sd.iend - sd.rend;
+    for (uint32_t g = 0; g < sd.ngroups; ++g) {
+        const uint32_t* tab = pool + sd.toff + g * cap * ew;
+        uint32_t w[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) w[i] = vs_lookup(tab, cap, is64, hb[i], klo[i], khi[i]);
+        uint4 out[NQ];
+#pragma unroll
+        for (int h = 0; h < NQ; ++h) {
+            out[h].x = transpose32(w[4 * h + 0], lane);
+            out[h].y = transpose32(w[4 * h + 1], lane);
+            out[h].z = transpose32(w[4 * h + 2], lane);
+            out[h].w = transpose32(w[4 * h + 3], lane);
+        }
+        const uint32_t k = 32u * g + lane;
+        if (k < nvs) {
+#pragma unroll
+            for (int h = 0; h < NQ; ++h) tm[(sd.rend + k) * NQ + h] = out[h];
+        }
+    }
+}
+
+
+// The wide pass over warp slices sl = first, first + stride, ... < end of
+// 128 rows each: row-set masks, range terms by compare, EQ and IN terms by
+// table, then lanes take predicates (and terms, for marginals) and add
+// popcounts into the CTA's 32-bit counters.  Returns the warp's count of
+// rows in each row set `lane` (lanes < nsets).
+__device__ __forceinline__ uint32_t wide_slices(const ProbeArgs& A, const Smem& S, int lane, uint64_t first,
+                                                uint64_t end, uint64_t stride) {
+    uint32_t nsr = 0;
+    for (uint64_t sl = first; sl < end; sl += stride) {
+        const uint64_t slice0 = sl * kSliceRows;
+        set_masks<1>(A, slice0, S.keep, lane);
+        for (uint32_t s = 0; s < A.nslots; ++s) {
+            const SlotDesc& sd = A.slots[s];
+            Vals<1> v;
+            load_vals_global<1>(sd.ptr, sd.width, slice0, A.nrows, lane, v);
+            SlotDesc ranges = sd;  // ranges by compare; EQ and IN terms by table
+            ranges.iend = sd.rend;
+            eval_slot<1>(ranges, v, S.st, S.pool, S.tm, lane);
+            if (sd.iend > sd.rend) eval_valueset<1>(sd, v, S.pool, S.tm, lane);
+        }
+        __syncwarp();
+        for (uint32_t p = lane; p < A.npreds; p += 32) {
+            const uint32_t b = S.poff[p], e = S.poff[p + 1];
+            uint4 acc = S.tm[S.pterm[b]];
+            for (uint32_t k = b + 1; k < e; ++k) acc = and4(acc, S.tm[S.pterm[k]]);
+            for (uint32_t q = 0; q < A.nsets; ++q) {
+                const uint32_t c = popc4(acc, S.keep[q]);
+                if (c) atomicAdd(&S.cnt[q * A.npreds + p], c);
+            }
+        }
+        if (A.want_marg) {
+            for (uint32_t t = lane; t < A.nterms; t += 32) {
+                const uint4 m = S.tm[t];
+                for (uint32_t q = 0; q < A.nsets; ++q) {
+                    const uint32_t c = popc4(m, S.keep[q]);
+                    if (c) atomicAdd(&S.marg[q * A.nterms + t], c);
+                }
+            }
+        }
+        if (lane < static_cast<int>(A.nsets)) {
+            const uint4 k = S.keep[lane];
+            nsr += __popc(k.x) + __popc(k.y) + __popc(k.z) + __popc(k.w);
+        }
+        __syncwarp();
+    }
+    return nsr;
+}
+
+}  // namespace probe_dev
+}  // namespace gace
