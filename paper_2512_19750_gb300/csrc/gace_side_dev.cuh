@@ -1,0 +1,217 @@
+// gace_side_dev.cuh -- device code of HyperLogLog and of the join sides,
+// written over ranges of rows so that the dedicated kernels and the batched
+// work-queue kernel run the same code.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gace_device.cuh"
+#include "gace_internal.h"
+
+namespace gace {
+namespace side_dev {
+
+using namespace dev;
+
+constexpr uint32_t kCasLimit = 1u << 20;
+
+// Canonical 64-bit key of an element: int32 sign-extended, int64 as is,
+// float32 bits zero-extended with -0 -> +0 and every NaN -> 0x7FC00000.
+__device__ __forceinline__ uint64_t canonical_key(uint32_t dtype, uint32_t lo, uint32_t hi) {
+    if (dtype == 0) return static_cast<uint64_t>(static_cast<int64_t>(static_cast<int32_t>(lo)));
+    if (dtype == 1) return join64(lo, hi);
+    if ((lo & 0x7FFFFFFFu) == 0) return 0;
+    if ((lo & 0x7F800000u) == 0x7F800000u && (lo & 0x007FFFFFu) != 0) return 0x7FC00000ull;
+    return lo;
+}
+
+__device__ __forceinline__ void hll_rank(uint64_t key, uint64_t seedhash, uint32_t p,
+                                         uint32_t& j, uint32_t& rho) {
+    const uint64_t h = splitmix64(key ^ seedhash);
+    j = static_cast<uint32_t>(h >> (64 - p));
+    const uint64_t w = h << p;
+    rho = w ? static_cast<uint32_t>(__clzll(static_cast<long long>(w))) + 1u : 65u - p;
+}
+
+// byte-wise max in shared memory via CAS on the containing word (bounded)
+__device__ __forceinline__ void smem_byte_max(uint32_t* words, uint32_t j, uint32_t rho,
+                                              unsigned int* status) {
+    uint32_t* w = &words[j >> 2];
+    const uint32_t sh = (j & 3u) * 8u;
+    uint32_t old = *reinterpret_cast<volatile uint32_t*>(w);
+    for (uint32_t n = 0; ((old >> sh) & 0xFFu) < rho; ++n) {
+        if (n >= kCasLimit) {
+            atomicOr(status, kStatusCasLimit);
+            return;
+        }
+        const uint32_t nw = (old & ~(0xFFu << sh)) | (rho << sh);
+        const uint32_t prev = atomicCAS(w, old, nw);
+        if (prev == old) return;
+        old = prev;
+    }
+}
+
+// HLL over groups of four rows g = first, first + stride, ... < end: rank of
+// each value, then a max-update of its register (CTA copy in shared memory
+// when SMEM, else the global 32-bit registers).
+template <bool SMEM, int DT>
+__device__ __forceinline__ void hll_groups(const HllArgs& A, uint32_t* sregs, uint64_t first, uint64_t end,
+                                           uint64_t stride) {
+    const unsigned char* sbytes = reinterpret_cast<const unsigned char*>(sregs);
+    constexpr uint32_t width = DT == 1 ? 8 : 4;
+    for (uint64_t g = first; g < end; g += stride) {
+        const uint64_t row0 = g * 4;
+        Quad v;
+        load_quad_global(A.col, width, row0, A.nrows, v);
+        // ranks of the four values first (independent), then the register checks
+        uint32_t j[4], rho[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            hll_rank(canonical_key(DT, v.lo[r], v.hi[r]), A.seedhash, A.p, j[r], rho[r]);
+            if (row0 + r >= A.nrows) rho[r] = 0;  // past the end: never raises a register
+        }
+        if (SMEM) {
+            uint32_t cur[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) cur[r] = *reinterpret_cast<const volatile unsigned char*>(&sbytes[j[r]]);
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                if (rho[r] > cur[r]) smem_byte_max(sregs, j[r], rho[r], A.status);
+        } else {
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                if (rho[r] > *reinterpret_cast<volatile uint32_t*>(&A.regs[j[r]])) atomicMax(&A.regs[j[r]], rho[r]);
+        }
+    }
+}
+
+// A CTA's shared-memory registers into the global ones, only where larger.
+__device__ __forceinline__ void hll_merge(const HllArgs& A, const uint32_t* sregs, uint32_t m, uint32_t tid,
+                                          uint32_t nthreads) {
+    const unsigned char* sbytes = reinterpret_cast<const unsigned char*>(sregs);
+    for (uint32_t jj = tid; jj < m; jj += nthreads) {
+        const uint32_t r = sbytes[jj];
+        if (r && r > __ldcg(&A.regs[jj])) atomicMax(&A.regs[jj], r);
+    }
+}
+
+// ---------------------------------------------------------------- join sides
+
+__device__ __forceinline__ void side_pass(const SideArgs& A, uint64_t row0, bool pass[4]) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) pass[r] = row0 + r < A.nrows;
+    for (uint32_t t = 0; t < A.nterms; ++t) {
+        const FilterTerm& ft = A.terms[t];
+        Quad v;
+        load_quad_global(A.slot_ptr[ft.slot], A.slot_dtype[ft.slot] == 1 ? 8 : 4, row0, A.nrows, v);
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            pass[r] = pass[r] && term_holds(ft.kind, ft.c, v.lo[r], v.hi[r], A.pool);
+    }
+}
+
+__device__ __forceinline__ void side_keys(const SideArgs& A, uint32_t slot, uint64_t row0,
+                                          int64_t key[4]) {
+    Quad v;
+    const uint32_t dt = A.slot_dtype[slot];
+    load_quad_global(A.slot_ptr[slot], dt == 1 ? 8 : 4, row0, A.nrows, v);
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+        key[r] = dt == 1 ? static_cast<int64_t>(join64(v.lo[r], v.hi[r]))
+                         : static_cast<int64_t>(static_cast<int32_t>(v.lo[r]));
+}
+
+
+// One side of a join over warp-uniform groups of four rows: gb = first (the
+// warp's first group), first + stride, ... < end, lane l taking group gb + l.
+// MODE 0: h[key] += 1 (AGG: equal keys of a warp combined with match_any);
+// 1: acc += weight32[key]; 2: acc += weight64[key]; 3: w64[key] += h2[fk2].
+// npass counts the rows that pass the filter; a passing row with a key outside
+// [0, domain) sets kStatusKeyDomain when strict.
+template <int MODE, bool AGG>
+__device__ __forceinline__ void side_groups(const SideArgs& A, uint32_t* hist, int strict, const void* weight,
+                                            uint32_t fk2_slot, uint64_t domain2, unsigned long long* w64,
+                                            uint64_t first, uint64_t end, uint64_t stride,
+                                            unsigned long long& npass, unsigned long long& acc) {
+    const int lane = threadIdx.x & 31;
+    for (uint64_t gb = first; gb < end; gb += stride) {
+        const uint64_t g = gb + lane;
+        const uint64_t row0 = g * 4;
+        const bool mine = g < end;  // groups past the range read as rows past the table
+        int64_t key[4];
+        side_keys(A, A.key_slot, row0, key);
+        int64_t fk2[4] = {0, 0, 0, 0};
+        if (MODE == 3) side_keys(A, fk2_slot, row0, fk2);
+        bool pass[4];
+        side_pass(A, row0, pass);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            pass[r] = pass[r] && mine;
+            const bool in_dom = key[r] >= 0 && static_cast<uint64_t>(key[r]) < A.domain;
+            npass += pass[r] ? 1 : 0;
+            if (pass[r] && !in_dom && strict) atomicOr(A.status, kStatusKeyDomain);
+            const bool use = pass[r] && in_dom;
+            if (MODE == 0) {
+                if (AGG) {
+                    const unsigned long long k = use ? static_cast<unsigned long long>(key[r]) : ~0ull;
+                    const unsigned grp = __match_any_sync(kFullMask, k);
+                    if (use && (__ffs(grp) - 1) == lane) atomicAdd(&hist[k], __popc(grp));
+                } else if (use) {
+                    atomicAdd(&hist[key[r]], 1u);
+                }
+            } else if (MODE == 1) {
+                if (use) acc += static_cast<const uint32_t*>(weight)[key[r]];
+            } else if (MODE == 2) {
+                if (use) acc += static_cast<const unsigned long long*>(weight)[key[r]];
+            } else {
+                if (use && fk2[r] >= 0 && static_cast<uint64_t>(fk2[r]) < domain2) {
+                    const uint32_t h = static_cast<const uint32_t*>(weight)[fk2[r]];
+                    if (h) atomicAdd(&w64[key[r]], static_cast<unsigned long long>(h));
+                }
+            }
+        }
+    }
+}
+
+// Largest element of a[first], a[first + stride], ... < end (per thread).
+template <bool B64>
+__device__ __forceinline__ unsigned long long max_range(const void* a, uint64_t first, uint64_t end,
+                                                        uint64_t stride) {
+    unsigned long long best = 0;
+    for (uint64_t i = first; i < end; i += stride) {
+        const unsigned long long x = B64 ? static_cast<const unsigned long long*>(a)[i]
+                                         : static_cast<const uint32_t*>(a)[i];
+        best = x > best ? x : best;
+    }
+    return best;
+}
+
+// sum of a[i] * b[i] over i = first, first + stride, ... < end (per thread).
+template <bool B64>
+__device__ __forceinline__ unsigned long long dot_range(const uint32_t* a, const void* b, uint64_t first,
+                                                        uint64_t end, uint64_t stride) {
+    unsigned long long acc = 0;
+    for (uint64_t i = first; i < end; i += stride) {
+        const unsigned long long x = a[i];
+        if (x) {
+            if (B64)
+                acc += x * static_cast<const unsigned long long*>(b)[i];
+            else
+                acc += x * static_cast<unsigned long long>(static_cast<const uint32_t*>(b)[i]);
+        }
+    }
+    return acc;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_down_sync(kFullMask, v, o);
+        v = y > v ? y : v;
+    }
+    return v;
+}
+
+}  // namespace side_dev
+}  // namespace gace
