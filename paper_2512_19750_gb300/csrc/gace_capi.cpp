@@ -22,10 +22,7 @@
 #include <unordered_map>
 #include <vector>
 
-#include "../../include/gace.h"
-#include "gace_internal.h"
-
-using namespace gace;
+#include "gace_host.h"
 
 namespace {
 
@@ -35,7 +32,8 @@ thread_local std::string g_last_error;
 
 void gace::set_last_error_message(const char* msg) { g_last_error = msg; }
 
-namespace {
+namespace gace {
+namespace host {
 
 gace_status fail(gace_status s, const char* fmt, ...) {
     char buf[512];
@@ -51,183 +49,16 @@ gace_status cuda_fail(cudaError_t e, const char* what) {
     return fail(GACE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define CK(call)                                           \
-    do {                                                   \
-        cudaError_t e_ = (call);                           \
-        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
-    } while (0)
 
-// splitmix64 output function (Steele, Lea & Flood, OOPSLA 2014), host side.
-uint64_t splitmix64_host(uint64_t x) {
-    x += 0x9E3779B97F4A7C15ull;
-    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
-    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
-    return x ^ (x >> 31);
-}
 
-uint32_t dtype_width(int dt) { return dt == GACE_I64 ? 8u : 4u; }
 
-uint64_t round_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 
-// Restores the caller's current device on scope exit.
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
 
-struct ColumnRec {
-    int dtype = 0;
-    void* dptr = nullptr;
-    bool owned = false;
-    uint64_t bytes = 0;
-};
 
-struct TableRec {
-    uint64_t nrows = 0;
-    std::vector<ColumnRec> cols;
-    uint64_t owned_bytes = 0;
-};
 
-}  // namespace
-
-struct gace_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    int sms = 0;
-    int smem_optin = 0;
-    uint64_t budget = 0;       // 0 = unlimited
-    uint64_t used = 0;         // owned tables + workspace + pinned
-    uint64_t timeout_ns = 2000ull * 1000000ull;
-    std::mutex mu;
-    std::unordered_map<uint32_t, TableRec> tables;
-    uint32_t next_id = 1;
-    unsigned char* ws = nullptr;  // device workspace
-    uint64_t ws_cap = 0;
-    unsigned char* pin = nullptr;  // pinned host staging
-    uint64_t pin_cap = 0;
-    unsigned int* d_status = nullptr;
-
-    // kernel statistics (tracing)
-    struct KStat {
-        uint64_t launches = 0, rows = 0, bytes = 0, ops = 0;
-        double ms = 0.0;
-    };
-    struct Timed {
-        std::string name;
-        cudaEvent_t a, b;
-    };
-    std::map<std::string, KStat> stats;
-    bool timing = false;
-    std::vector<cudaEvent_t> ev_free;
-    std::vector<Timed> pending;
-
-    cudaEvent_t take_event() {
-        if (!ev_free.empty()) {
-            cudaEvent_t e = ev_free.back();
-            ev_free.pop_back();
-            return e;
-        }
-        cudaEvent_t e = nullptr;
-        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-        return e;
-    }
-
-    // Counts one launch with its algorithmic work and, when timing, brackets
-    // it with events on the context stream.
-    template <typename F>
-    cudaError_t traced(const char* name, uint64_t rows, uint64_t bytes, uint64_t ops, F&& launch) {
-        KStat& k = stats[name];
-        k.launches++;
-        k.rows += rows;
-        k.bytes += bytes;
-        k.ops += ops;
-        if (!timing) return launch();
-        cudaEvent_t a = take_event(), b = take_event();
-        if (a) cudaEventRecord(a, stream);
-        cudaError_t e = launch();
-        if (b) cudaEventRecord(b, stream);
-        if (a && b) pending.push_back({name, a, b});
-        return e;
-    }
-
-    // After a stream synchronisation: fold event pairs into the statistics.
-    void collect() {
-        for (auto& t : pending) {
-            float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) stats[t.name].ms += ms;
-            ev_free.push_back(t.a);
-            ev_free.push_back(t.b);
-        }
-        pending.clear();
-    }
-
-    bool fits(uint64_t extra) const { return budget == 0 || used + extra <= budget; }
-
-    gace_status ensure_ws(uint64_t bytes) {
-        bytes = round_up(bytes ? bytes : 256, 1 << 20);
-        if (bytes <= ws_cap) return GACE_OK;
-        if (!fits(bytes - ws_cap))
-            return fail(GACE_ENOMEM, "workspace of %llu bytes exceeds the HBM budget",
-                        (unsigned long long)bytes);
-        CK(cudaStreamSynchronize(stream));
-        if (ws) {
-            cudaFree(ws);
-            used -= ws_cap;
-            ws = nullptr;
-            ws_cap = 0;
-        }
-        cudaError_t e = cudaMalloc(&ws, bytes);
-        if (e != cudaSuccess) {
-            ws = nullptr;
-            return fail(GACE_ENOMEM, "cudaMalloc(%llu) for the workspace: %s",
-                        (unsigned long long)bytes, cudaGetErrorString(e));
-        }
-        ws_cap = bytes;
-        used += bytes;
-        return GACE_OK;
-    }
-
-    gace_status ensure_pin(uint64_t bytes) {
-        bytes = round_up(bytes ? bytes : 256, 1 << 16);
-        if (bytes <= pin_cap) return GACE_OK;
-        CK(cudaStreamSynchronize(stream));
-        if (pin) {
-            cudaFreeHost(pin);
-            pin = nullptr;
-            pin_cap = 0;
-        }
-        cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&pin), bytes, cudaHostAllocDefault);
-        if (e != cudaSuccess) {
-            pin = nullptr;
-            return fail(GACE_ENOMEM, "cudaHostAlloc(%llu): %s", (unsigned long long)bytes,
-                        cudaGetErrorString(e));
-        }
-        pin_cap = bytes;
-        return GACE_OK;
-    }
-};
-
-namespace {
 
 // ---------------------------------------------------------------- terms
 
-struct NTerm {
-    uint32_t col = 0;
-    uint32_t kind = kFalse;
-    uint64_t a = 0, b = 0;
-    std::vector<uint32_t> in;  // pool words
-    bool operator<(const NTerm& o) const {
-        return std::tie(col, kind, a, b, in) < std::tie(o.col, o.kind, o.a, o.b, o.in);
-    }
-};
 
 uint32_t fbits(float f) {
     uint32_t u;
@@ -384,10 +215,6 @@ DevTerm make_devterm(const NTerm& t, uint32_t pool_off) {
 
 // ---------------------------------------------------------------- sets
 
-struct SetPlan {
-    SetDesc d;
-    uint32_t orig;
-};
 
 gace_status make_set(const gace_sample& s, SetDesc& d) {
     d = SetDesc{};
@@ -419,34 +246,6 @@ gace_status make_set(const gace_sample& s, SetDesc& d) {
 
 // ---------------------------------------------------------------- probe plan
 
-constexpr uint32_t kPassTerms = 256;
-constexpr uint32_t kPassPreds = 256;
-constexpr uint32_t kPassPool = 16384;  // pool words: IN lists (narrow) or EQ/IN tables (wide)
-
-struct Pass {
-    std::vector<uint32_t> preds;   // device predicate indices (input numbering)
-    std::vector<uint32_t> uterms;  // unique terms placed in this pass
-    // built:
-    std::vector<DevTerm> dterms;
-    std::vector<uint32_t> pool, poff, pterm;
-    std::vector<uint32_t> u_local;  // unique term -> local index (parallel to uterms order)
-    std::vector<std::pair<uint32_t, uint32_t>> slots;  // (col, first local term)
-    ProbeArgs args{};
-    uint64_t in_off = 0, out_off = 0;  // workspace offsets
-    uint64_t ops_per_row = 0;          // compares per row (statistics)
-    uint32_t rowbytes = 0;             // bytes per row of the referenced columns
-    uint64_t in_bytes = 0, out_bytes = 0;
-};
-
-struct Ws {
-    uint64_t off = 0;
-    uint64_t take(uint64_t bytes, uint64_t align = 256) {
-        off = round_up(off, align);
-        const uint64_t r = off;
-        off += bytes;
-        return r;
-    }
-};
 
 gace_status check_ctx(gace_ctx* ctx) {
     if (!ctx) return fail(GACE_EINVAL, "context is NULL");
@@ -469,12 +268,12 @@ gace_status read_status(gace_ctx* ctx, unsigned int st) {
 // Builds the device form of a pass and the probe arguments (without pointers).
 gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::vector<NTerm>& uterms,
                        const std::vector<std::vector<uint32_t>>& pred_u,
-                       const std::vector<SetPlan>& sets, bool want_marg) {
+                       const std::vector<SetPlan>& sets, bool want_marg, bool force_wide) {
     // Narrow passes (at most 32 predicates and terms) evaluate IN lists by
     // compare; wide passes look up every EQ and IN term of a column in that
     // column's hash tables.  Order: by column, ranges (or, wide, multi-value
     // ranges) first, then IN lists (or, wide, single values and IN lists).
-    const bool narrow = ps.preds.size() <= static_cast<size_t>(kNarrowMax) &&
+    const bool narrow = !force_wide && ps.preds.size() <= static_cast<size_t>(kNarrowMax) &&
                         ps.uterms.size() <= static_cast<size_t>(kNarrowMax);
     auto valueset = [&](const NTerm& t) {
         return is_in_kind(t.kind) || (!narrow && term_cost(t) == 1);
@@ -644,7 +443,376 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
     return GACE_OK;
 }
 
-}  // namespace
+
+double hll_estimate_host(const uint8_t* regs, uint32_t p) {
+    const uint64_t m = 1ull << p;
+    uint64_t hist[66] = {0};
+    for (uint64_t j = 0; j < m; ++j) hist[regs[j] < 65 ? regs[j] : 65]++;
+    const double dm = static_cast<double>(m);
+    double alpha;
+    if (m == 16) alpha = 0.673;
+    else if (m == 32) alpha = 0.697;
+    else if (m == 64) alpha = 0.709;
+    else alpha = 0.7213 / (1.0 + 1.079 / dm);
+    double z = 0.0;
+    for (int k = 0; k <= 65; ++k) z += static_cast<double>(hist[k]) * std::ldexp(1.0, -k);
+    double e = alpha * dm * dm / z;
+    if (e <= 2.5 * dm && hist[0] > 0) e = dm * std::log(dm / static_cast<double>(hist[0]));
+    return e;
+}
+
+gace_status build_side(gace_ctx* ctx, const gace_join_side& js, const char* name, int extra_col,
+                              SideArgs& a, std::vector<uint32_t>& pool, TableRec** tab_out, uint32_t* extra_slot,
+                              SideWork& work) {
+    TableRec* tab = find_table(ctx, js.table_id);
+    if (!tab) return fail(GACE_ENOTFOUND, "%s table %u is not loaded", name, js.table_id);
+    if (js.key_col >= tab->cols.size()) return fail(GACE_EINVAL, "%s key column %u out of range", name, js.key_col);
+    if (tab->cols[js.key_col].dtype == GACE_F32) return fail(GACE_EINVAL, "%s key column is float32", name);
+    if (js.nterms && !js.terms) return fail(GACE_EINVAL, "%s terms is NULL", name);
+    if (js.nterms > static_cast<uint32_t>(kMaxFilterTerms))
+        return fail(GACE_EINVAL, "%s filter has %u terms (max %d)", name, js.nterms, kMaxFilterTerms);
+    a = SideArgs{};
+    a.nrows = tab->nrows;
+    std::vector<uint32_t> slot_col;
+    auto slot_of = [&](uint32_t col) -> int {
+        for (uint32_t s = 0; s < slot_col.size(); ++s)
+            if (slot_col[s] == col) return static_cast<int>(s);
+        if (slot_col.size() == static_cast<size_t>(kMaxFilterSlots)) return -1;
+        slot_col.push_back(col);
+        return static_cast<int>(slot_col.size() - 1);
+    };
+    a.key_slot = static_cast<uint32_t>(slot_of(js.key_col));
+    if (extra_col >= 0) {
+        if (static_cast<uint32_t>(extra_col) >= tab->cols.size() || tab->cols[extra_col].dtype == GACE_F32)
+            return fail(GACE_EINVAL, "%s fk2 column %d invalid", name, extra_col);
+        *extra_slot = static_cast<uint32_t>(slot_of(static_cast<uint32_t>(extra_col)));
+    }
+    uint32_t nt = 0;
+    bool never = false;
+    for (uint32_t t = 0; t < js.nterms; ++t) {
+        if (js.terms[t].col >= tab->cols.size())
+            return fail(GACE_EINVAL, "%s term %u references column %u", name, t, js.terms[t].col);
+        NTerm n;
+        if (gace_status st = normalize_term(js.terms[t], tab->cols[js.terms[t].col].dtype, js.in_values, js.nin, n))
+            return st;
+        if (n.kind == kFalse) {
+            never = true;
+            continue;
+        }
+        const int s = slot_of(n.col);
+        if (s < 0) return fail(GACE_EINVAL, "%s filter references more than %d columns", name, kMaxFilterSlots);
+        FilterTerm& ft = a.terms[nt++];
+        ft.slot = static_cast<uint32_t>(s);
+        ft.kind = n.kind;
+        work.ops_per_row += term_cost(n);
+        uint32_t poff = static_cast<uint32_t>(pool.size());
+        if (is_in_kind(n.kind)) pool.insert(pool.end(), n.in.begin(), n.in.end());
+        ft.c = make_devterm(n, poff);
+    }
+    if (never) {  // an always-false term: a range no value satisfies on the key column
+        nt = 0;
+        FilterTerm& ft = a.terms[nt++];
+        ft.slot = a.key_slot;
+        ft.kind = kInI32;
+        ft.c = DevTerm{0, 0, 0, 0};  // empty IN list
+    }
+    a.nterms = nt;
+    a.nslots = static_cast<uint32_t>(slot_col.size());
+    work.rows = tab->nrows;
+    for (uint32_t c : slot_col) work.rowbytes += dtype_width(tab->cols[c].dtype);
+    for (uint32_t s = 0; s < slot_col.size(); ++s) {
+        a.slot_ptr[s] = tab->cols[slot_col[s]].dptr;
+        a.slot_dtype[s] = static_cast<uint32_t>(tab->cols[slot_col[s]].dtype);
+        a.slot_aligned[s] = (reinterpret_cast<uintptr_t>(a.slot_ptr[s]) & 15u) == 0;
+    }
+    *tab_out = tab;
+    return GACE_OK;
+}
+
+// ---------------------------------------------------------------- probe
+
+gace_status check_probe_request(const ProbeRequest& r) {
+    if (!r.samples || r.nsamples == 0 || r.nsamples > kMaxSets)
+        return fail(GACE_EINVAL, "nsamples %u outside 1..%d", r.nsamples, kMaxSets);
+    if (r.npreds && (!r.preds || !r.results)) return fail(GACE_EINVAL, "preds or results is NULL");
+    if (r.nterms && !r.terms) return fail(GACE_EINVAL, "terms is NULL");
+    if (r.nterms > (1u << 24) || r.npreds > (1u << 24)) return fail(GACE_EINVAL, "batch too large");
+    return GACE_OK;
+}
+
+gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r, bool force_wide,
+                       ProbePlan& plan) {
+    plan = ProbePlan();
+    plan.tab = &tab;
+    const uint32_t nsamples = r.nsamples, nterms = r.nterms, npreds = r.npreds;
+    // Device row sets: one set for every sample that keeps all rows (full
+    // scans, rate >= 1), then one per distinct hashed sample, ordered so that
+    // sets sharing a hash input are adjacent.  Samples of rate <= 0 need no
+    // device work.
+    std::vector<SetDesc> sdesc(nsamples);
+    for (uint32_t s = 0; s < nsamples; ++s)
+        if (gace_status st = make_set(r.samples[s], sdesc[s])) return st;
+    std::vector<SetPlan>& sets = plan.sets;
+    std::vector<int32_t>& set_dev = plan.set_dev;
+    set_dev.assign(nsamples, -1);
+    for (uint32_t s = 0; s < nsamples; ++s)
+        if (sdesc[s].mode == 1) {
+            if (sets.empty()) {
+                SetPlan v;
+                v.d = SetDesc{};
+                v.d.kind = 0;
+                v.d.mode = 1;
+                v.d.block_shift = -1;
+                v.orig = s;
+                sets.push_back(v);
+            }
+            set_dev[s] = 0;
+        }
+    std::vector<SetPlan> hashed;
+    for (uint32_t s = 0; s < nsamples; ++s)
+        if (sdesc[s].mode == 2) hashed.push_back({sdesc[s], s});
+    std::stable_sort(hashed.begin(), hashed.end(), [](const SetPlan& a, const SetPlan& b) {
+        return std::tie(a.d.kind, a.d.seedhash, a.d.block_rows, a.d.thresh) <
+               std::tie(b.d.kind, b.d.seedhash, b.d.block_rows, b.d.thresh);
+    });
+    for (const SetPlan& h : hashed) {
+        const SetDesc* last = sets.empty() ? nullptr : &sets.back().d;
+        if (last && last->mode == 2 && last->kind == h.d.kind && last->seedhash == h.d.seedhash &&
+            last->block_rows == h.d.block_rows && last->thresh == h.d.thresh) {
+            set_dev[h.orig] = static_cast<int32_t>(sets.size() - 1);  // identical sample
+            continue;
+        }
+        SetPlan c = h;
+        c.d.share_prev = (last && last->mode == 2 && last->kind == c.d.kind && last->seedhash == c.d.seedhash &&
+                          last->block_rows == c.d.block_rows)
+                             ? 1u
+                             : 0u;
+        set_dev[h.orig] = static_cast<int32_t>(sets.size());
+        sets.push_back(c);
+    }
+
+    // normalise and deduplicate terms
+    std::vector<NTerm>& uterms = plan.uterms;
+    std::map<NTerm, uint32_t> dedup;
+    plan.t2u.assign(nterms, 0);
+    for (uint32_t t = 0; t < nterms; ++t) {
+        if (r.terms[t].col >= tab.cols.size())
+            return fail(GACE_EINVAL, "term %u references column %u of a %zu-column table", t, r.terms[t].col,
+                        tab.cols.size());
+        NTerm n;
+        if (gace_status st = normalize_term(r.terms[t], tab.cols[r.terms[t].col].dtype, r.in_values, r.nin, n))
+            return st;
+        if (n.kind == kFalse) {
+            plan.t2u[t] = UINT32_MAX;
+            continue;
+        }
+        auto it = dedup.find(n);
+        if (it == dedup.end()) {
+            it = dedup.emplace(n, static_cast<uint32_t>(uterms.size())).first;
+            uterms.push_back(n);
+        }
+        plan.t2u[t] = it->second;
+    }
+    // predicates: 0 device, 1 never true, 2 always true (no terms)
+    plan.pstate.assign(npreds, 0);
+    plan.pred_u.assign(npreds, {});
+    bool any_pair = false;
+    for (uint32_t p = 0; p < npreds; ++p) {
+        const gace_pred& pr = r.preds[p];
+        if ((uint64_t)pr.term_off + pr.term_cnt > nterms)
+            return fail(GACE_EINVAL, "predicate %u terms [%u, %u) outside terms[%u]", p, pr.term_off,
+                        pr.term_off + pr.term_cnt, nterms);
+        if (pr.term_cnt == 2) any_pair = true;
+        if (pr.term_cnt == 0) {
+            plan.pstate[p] = 2;
+            continue;
+        }
+        std::vector<uint32_t>& pu = plan.pred_u[p];
+        for (uint32_t k = 0; k < pr.term_cnt; ++k) {
+            const uint32_t u = plan.t2u[pr.term_off + k];
+            if (u == UINT32_MAX) {
+                plan.pstate[p] = 1;
+                break;
+            }
+            pu.push_back(u);
+        }
+        std::sort(pu.begin(), pu.end());
+        pu.erase(std::unique(pu.begin(), pu.end()), pu.end());
+        if (plan.pstate[p] == 1) pu.clear();
+    }
+    plan.want_marg = r.term_marginals != nullptr || any_pair;
+
+    // pack predicates into passes that fit the kernel's shared-memory tables
+    std::vector<Pass>& passes = plan.passes;
+    std::vector<int32_t> u_pass(uterms.size(), -1);
+    {
+        Pass cur;
+        std::map<uint32_t, bool> in_cur;
+        uint32_t pool_words = 0;
+        std::map<uint32_t, bool> cols_cur;
+        auto flush = [&]() {
+            if (!cur.preds.empty() || !cur.uterms.empty()) passes.push_back(cur);
+            cur = Pass();
+            in_cur.clear();
+            cols_cur.clear();
+            pool_words = 0;
+        };
+        for (uint32_t p = 0; p < npreds; ++p) {
+            if (plan.pstate[p] != 0) continue;
+            const std::vector<uint32_t>& pu = plan.pred_u[p];
+            uint32_t add_t = 0, add_pool = 0, add_c = 0;
+            for (uint32_t u : pu)
+                if (!in_cur.count(u)) {
+                    ++add_t;
+                    add_pool += pool_estimate(uterms[u]);
+                    if (!cols_cur.count(uterms[u].col)) {
+                        ++add_c;
+                        add_pool += 256;  // smallest table of a new column
+                    }
+                }
+            if (pu.size() > kPassTerms) return fail(GACE_EINVAL, "predicate %u has too many terms", p);
+            // a predicate too large for a shared pass gets one of its own (a
+            // single predicate evaluates IN lists by compare, with no tables)
+            if (!cur.preds.empty() &&
+                (cur.uterms.size() + add_t > kPassTerms || cur.preds.size() + 1 > kPassPreds ||
+                 pool_words + add_pool > kPassPool || cols_cur.size() + add_c > static_cast<size_t>(kMaxSlots)))
+                flush();
+            for (uint32_t u : pu)
+                if (!in_cur.count(u)) {
+                    in_cur[u] = true;
+                    cols_cur[uterms[u].col] = true;
+                    cur.uterms.push_back(u);
+                    u_pass[u] = static_cast<int32_t>(passes.size());
+                }
+            pool_words += add_pool;
+            cur.preds.push_back(p);
+        }
+        // terms whose marginals are wanted but that no device predicate placed
+        if (plan.want_marg) {
+            for (uint32_t u = 0; u < uterms.size(); ++u) {
+                if (u_pass[u] >= 0) continue;
+                const uint32_t add_c = cols_cur.count(uterms[u].col) ? 0 : 1;
+                const uint32_t add_pool = pool_estimate(uterms[u]) + 256 * add_c;
+                if (!cur.uterms.empty() &&
+                    (cur.uterms.size() + 1 > kPassTerms || pool_words + add_pool > kPassPool ||
+                     cols_cur.size() + add_c > static_cast<size_t>(kMaxSlots)))
+                    flush();
+                cur.uterms.push_back(u);
+                in_cur[u] = true;
+                cols_cur[uterms[u].col] = true;
+                pool_words += add_pool;
+                u_pass[u] = static_cast<int32_t>(passes.size());
+            }
+        }
+        flush();
+    }
+    bool need_ns = false;
+    for (auto& s : sets)
+        if (s.d.mode == 2) need_ns = true;
+    if (sets.empty()) passes.clear();  // every sample is empty: nothing to count
+    if (passes.empty() && need_ns) passes.push_back(Pass());  // counts sample rows only
+    for (auto& ps : passes) {
+        if (gace_status st = build_pass(ctx, tab, ps, uterms, plan.pred_u, sets, plan.want_marg, force_wide))
+            return st;
+        pass_sizes(ps);
+    }
+    return GACE_OK;
+}
+
+void pass_sizes(Pass& ps) {
+    const ProbeArgs& A = ps.args;
+    ps.in_bytes = round_up(A.nterms * 16ull, 16) + round_up(A.npool * 4ull, 16) + round_up((A.npreds + 1) * 4ull, 16) +
+                  round_up(A.npredterms * 4ull, 16);
+    ps.out_bytes =
+        (static_cast<uint64_t>(A.nsets) * A.npreds + static_cast<uint64_t>(A.nsets) * A.nterms + A.nsets) * 8ull;
+}
+
+void stage_pass(Pass& ps, unsigned char* pin, unsigned char* dws, unsigned int* status) {
+    ProbeArgs& A = ps.args;
+    uint64_t o = ps.in_off;
+    auto put = [&](const void* src, uint64_t bytes) {
+        const uint64_t at = o;
+        if (bytes) memcpy(pin + o, src, bytes);
+        o += round_up(bytes, 16);
+        return at;
+    };
+    const uint64_t o_terms = put(ps.dterms.data(), ps.dterms.size() * 16ull);
+    const uint64_t o_pool = put(ps.pool.data(), ps.pool.size() * 4ull);
+    const uint64_t o_poff = put(ps.poff.data(), ps.poff.size() * 4ull);
+    const uint64_t o_pterm = put(ps.pterm.data(), ps.pterm.size() * 4ull);
+    A.terms = reinterpret_cast<const DevTerm*>(dws + o_terms);
+    A.pool = reinterpret_cast<const uint32_t*>(dws + o_pool);
+    A.pred_off = reinterpret_cast<const uint32_t*>(dws + o_poff);
+    A.pred_terms = reinterpret_cast<const uint32_t*>(dws + o_pterm);
+    unsigned long long* out = reinterpret_cast<unsigned long long*>(dws + ps.out_off);
+    A.counts = out;
+    A.marg = out + static_cast<uint64_t>(A.nsets) * A.npreds;
+    A.nsamp = A.marg + static_cast<uint64_t>(A.nsets) * A.nterms;
+    A.status = status;
+}
+
+void assemble_probe(const ProbePlan& plan, const ProbeRequest& r,
+                    const std::vector<const unsigned long long*>& pass_out) {
+    const uint32_t nsamples = r.nsamples, nterms = r.nterms, npreds = r.npreds;
+    const std::vector<Pass>& passes = plan.passes;
+    std::vector<uint64_t> ns(nsamples, 0);
+    for (uint32_t s = 0; s < nsamples; ++s) {
+        if (plan.set_dev[s] < 0) continue;
+        const SetDesc& d = plan.sets[plan.set_dev[s]].d;
+        if (d.mode == 1) {
+            ns[s] = plan.tab->nrows;
+        } else {
+            const Pass& ps = passes.front();
+            ns[s] = pass_out[0][static_cast<uint64_t>(ps.args.nsets) * ps.args.npreds +
+                                static_cast<uint64_t>(ps.args.nsets) * ps.args.nterms + plan.set_dev[s]];
+        }
+    }
+    // per unique term: (pass, local index)
+    std::vector<std::pair<int32_t, uint32_t>> uloc(plan.uterms.size(), {-1, 0});
+    for (uint32_t k = 0; k < passes.size(); ++k)
+        for (uint32_t i = 0; i < passes[k].uterms.size(); ++i)
+            uloc[passes[k].uterms[i]] = {static_cast<int32_t>(k), i};
+    auto marg_of = [&](uint32_t t, uint32_t s) -> uint64_t {
+        const uint32_t u = plan.t2u[t];
+        if (u == UINT32_MAX) return 0;
+        const auto& L = uloc[u];
+        if (L.first < 0 || plan.set_dev[s] < 0) return 0;
+        const Pass& ps = passes[L.first];
+        return pass_out[L.first][static_cast<uint64_t>(ps.args.nsets) * ps.args.npreds +
+                                 static_cast<uint64_t>(plan.set_dev[s]) * ps.args.nterms + L.second];
+    };
+    std::vector<std::pair<int32_t, uint32_t>> ploc(npreds, {-1, 0});
+    for (uint32_t k = 0; k < passes.size(); ++k)
+        for (uint32_t i = 0; i < passes[k].preds.size(); ++i)
+            ploc[passes[k].preds[i]] = {static_cast<int32_t>(k), i};
+    for (uint32_t s = 0; s < nsamples; ++s) {
+        for (uint32_t p = 0; p < npreds; ++p) {
+            uint64_t m = 0;
+            if (plan.pstate[p] == 2) {
+                m = ns[s];
+            } else if (plan.pstate[p] == 0 && plan.set_dev[s] >= 0) {
+                const Pass& ps = passes[ploc[p].first];
+                m = pass_out[ploc[p].first][static_cast<uint64_t>(plan.set_dev[s]) * ps.args.npreds + ploc[p].second];
+            }
+            gace_pred_result& res = r.results[static_cast<uint64_t>(s) * npreds + p];
+            res.match = m;
+            res.sample_rows = ns[s];
+            res.sel = ns[s] ? static_cast<double>(m) / static_cast<double>(ns[s]) : 0.0;
+            res.pcs = std::numeric_limits<double>::quiet_NaN();
+            if (r.preds[p].term_cnt == 2) {
+                const uint64_t ca = marg_of(r.preds[p].term_off, s), cb = marg_of(r.preds[p].term_off + 1, s);
+                if (ca != 0 && cb != 0)
+                    res.pcs = (static_cast<double>(m) * static_cast<double>(ns[s])) /
+                              (static_cast<double>(ca) * static_cast<double>(cb));
+            }
+        }
+        if (r.term_marginals)
+            for (uint32_t t = 0; t < nterms; ++t) r.term_marginals[static_cast<uint64_t>(s) * nterms + t] = marg_of(t, s);
+    }
+}
+
+}  // namespace host
+}  // namespace gace
 
 // ======================================================================== ABI
 
@@ -811,223 +979,41 @@ gace_status gace_probe_batch(gace_ctx* ctx, uint32_t table_id, const gace_sample
                              const gace_pred* preds, uint32_t npreds, gace_pred_result* results,
                              uint64_t* term_marginals) {
     if (gace_status s = check_ctx(ctx)) return s;
-    if (!samples || nsamples == 0 || nsamples > kMaxSets)
-        return fail(GACE_EINVAL, "nsamples %u outside 1..%d", nsamples, kMaxSets);
-    if (npreds && (!preds || !results)) return fail(GACE_EINVAL, "preds or results is NULL");
-    if (nterms && !terms) return fail(GACE_EINVAL, "terms is NULL");
-    if (nterms > (1u << 24) || npreds > (1u << 24)) return fail(GACE_EINVAL, "batch too large");
+    ProbeRequest r;
+    r.samples = samples;
+    r.nsamples = nsamples;
+    r.terms = terms;
+    r.nterms = nterms;
+    r.in_values = in_values;
+    r.nin = nin;
+    r.preds = preds;
+    r.npreds = npreds;
+    r.results = results;
+    r.term_marginals = term_marginals;
+    if (gace_status s = check_probe_request(r)) return s;
     std::lock_guard<std::mutex> lk(ctx->mu);
     TableRec* tab = find_table(ctx, table_id);
     if (!tab) return fail(GACE_ENOTFOUND, "table %u is not loaded", table_id);
     DeviceGuard g(ctx->device);
+    ProbePlan plan;
+    if (gace_status st = plan_probe(ctx, *tab, r, false, plan)) return st;
+    std::vector<Pass>& passes = plan.passes;
 
-    // Device row sets: one set for every sample that keeps all rows (full
-    // scans, rate >= 1), then one per distinct hashed sample, ordered so that
-    // sets sharing a hash input are adjacent.  Samples of rate <= 0 need no
-    // device work.
-    std::vector<SetDesc> sdesc(nsamples);
-    for (uint32_t s = 0; s < nsamples; ++s)
-        if (gace_status st = make_set(samples[s], sdesc[s])) return st;
-    std::vector<SetPlan> sets;
-    std::vector<int32_t> set_dev(nsamples, -1);
-    for (uint32_t s = 0; s < nsamples; ++s)
-        if (sdesc[s].mode == 1) {
-            if (sets.empty()) {
-                SetPlan v;
-                v.d = SetDesc{};
-                v.d.kind = 0;
-                v.d.mode = 1;
-                v.d.block_shift = -1;
-                v.orig = s;
-                sets.push_back(v);
-            }
-            set_dev[s] = 0;
-        }
-    std::vector<SetPlan> hashed;
-    for (uint32_t s = 0; s < nsamples; ++s)
-        if (sdesc[s].mode == 2) hashed.push_back({sdesc[s], s});
-    std::stable_sort(hashed.begin(), hashed.end(), [](const SetPlan& a, const SetPlan& b) {
-        return std::tie(a.d.kind, a.d.seedhash, a.d.block_rows, a.d.thresh) <
-               std::tie(b.d.kind, b.d.seedhash, b.d.block_rows, b.d.thresh);
-    });
-    for (const SetPlan& h : hashed) {
-        const SetDesc* last = sets.empty() ? nullptr : &sets.back().d;
-        if (last && last->mode == 2 && last->kind == h.d.kind && last->seedhash == h.d.seedhash &&
-            last->block_rows == h.d.block_rows && last->thresh == h.d.thresh) {
-            set_dev[h.orig] = static_cast<int32_t>(sets.size() - 1);  // identical sample
-            continue;
-        }
-        SetPlan c = h;
-        c.d.share_prev = (last && last->mode == 2 && last->kind == c.d.kind && last->seedhash == c.d.seedhash &&
-                          last->block_rows == c.d.block_rows)
-                             ? 1u
-                             : 0u;
-        set_dev[h.orig] = static_cast<int32_t>(sets.size());
-        sets.push_back(c);
-    }
-
-    // normalise and deduplicate terms
-    std::vector<NTerm> uterms;
-    std::map<NTerm, uint32_t> dedup;
-    std::vector<uint32_t> t2u(nterms);
-    for (uint32_t t = 0; t < nterms; ++t) {
-        if (terms[t].col >= tab->cols.size())
-            return fail(GACE_EINVAL, "term %u references column %u of a %zu-column table", t, terms[t].col,
-                        tab->cols.size());
-        NTerm n;
-        if (gace_status st = normalize_term(terms[t], tab->cols[terms[t].col].dtype, in_values, nin, n)) return st;
-        if (n.kind == kFalse) {
-            t2u[t] = UINT32_MAX;
-            continue;
-        }
-        auto it = dedup.find(n);
-        if (it == dedup.end()) {
-            it = dedup.emplace(n, static_cast<uint32_t>(uterms.size())).first;
-            uterms.push_back(n);
-        }
-        t2u[t] = it->second;
-    }
-    // predicates: 0 device, 1 never true, 2 always true (no terms)
-    std::vector<uint8_t> pstate(npreds, 0);
-    std::vector<std::vector<uint32_t>> pred_u(npreds);
-    bool any_pair = false;
-    for (uint32_t p = 0; p < npreds; ++p) {
-        const gace_pred& pr = preds[p];
-        if ((uint64_t)pr.term_off + pr.term_cnt > nterms)
-            return fail(GACE_EINVAL, "predicate %u terms [%u, %u) outside terms[%u]", p, pr.term_off,
-                        pr.term_off + pr.term_cnt, nterms);
-        if (pr.term_cnt == 2) any_pair = true;
-        if (pr.term_cnt == 0) {
-            pstate[p] = 2;
-            continue;
-        }
-        for (uint32_t k = 0; k < pr.term_cnt; ++k) {
-            const uint32_t u = t2u[pr.term_off + k];
-            if (u == UINT32_MAX) {
-                pstate[p] = 1;
-                break;
-            }
-            pred_u[p].push_back(u);
-        }
-        std::sort(pred_u[p].begin(), pred_u[p].end());
-        pred_u[p].erase(std::unique(pred_u[p].begin(), pred_u[p].end()), pred_u[p].end());
-        if (pstate[p] == 1) pred_u[p].clear();
-    }
-    const bool want_marg = term_marginals != nullptr || any_pair;
-
-    // pack predicates into passes that fit the kernel's shared-memory tables
-    std::vector<Pass> passes;
-    std::vector<int32_t> u_pass(uterms.size(), -1);
-    {
-        Pass cur;
-        std::map<uint32_t, bool> in_cur;
-        uint32_t pool_words = 0;
-        std::map<uint32_t, bool> cols_cur;
-        auto flush = [&]() {
-            if (!cur.preds.empty() || !cur.uterms.empty()) passes.push_back(cur);
-            cur = Pass();
-            in_cur.clear();
-            cols_cur.clear();
-            pool_words = 0;
-        };
-        for (uint32_t p = 0; p < npreds; ++p) {
-            if (pstate[p] != 0) continue;
-            uint32_t add_t = 0, add_pool = 0, add_c = 0;
-            for (uint32_t u : pred_u[p])
-                if (!in_cur.count(u)) {
-                    ++add_t;
-                    add_pool += pool_estimate(uterms[u]);
-                    if (!cols_cur.count(uterms[u].col)) {
-                        ++add_c;
-                        add_pool += 256;  // smallest table of a new column
-                    }
-                }
-            if (pred_u[p].size() > kPassTerms) return fail(GACE_EINVAL, "predicate %u has too many terms", p);
-            // a predicate too large for a shared pass gets one of its own (a
-            // single predicate evaluates IN lists by compare, with no tables)
-            if (!cur.preds.empty() &&
-                (cur.uterms.size() + add_t > kPassTerms || cur.preds.size() + 1 > kPassPreds ||
-                 pool_words + add_pool > kPassPool || cols_cur.size() + add_c > static_cast<size_t>(kMaxSlots)))
-                flush();
-            for (uint32_t u : pred_u[p])
-                if (!in_cur.count(u)) {
-                    in_cur[u] = true;
-                    cols_cur[uterms[u].col] = true;
-                    cur.uterms.push_back(u);
-                    u_pass[u] = static_cast<int32_t>(passes.size());
-                }
-            pool_words += add_pool;
-            cur.preds.push_back(p);
-        }
-        // terms whose marginals are wanted but that no device predicate placed
-        if (want_marg) {
-            for (uint32_t u = 0; u < uterms.size(); ++u) {
-                if (u_pass[u] >= 0) continue;
-                const uint32_t add_c = cols_cur.count(uterms[u].col) ? 0 : 1;
-                const uint32_t add_pool = pool_estimate(uterms[u]) + 256 * add_c;
-                if (!cur.uterms.empty() &&
-                    (cur.uterms.size() + 1 > kPassTerms || pool_words + add_pool > kPassPool ||
-                     cols_cur.size() + add_c > static_cast<size_t>(kMaxSlots)))
-                    flush();
-                cur.uterms.push_back(u);
-                in_cur[u] = true;
-                cols_cur[uterms[u].col] = true;
-                pool_words += add_pool;
-                u_pass[u] = static_cast<int32_t>(passes.size());
-            }
-        }
-        flush();
-    }
-    bool need_ns = false;
-    for (auto& s : sets)
-        if (s.d.mode == 2) need_ns = true;
-    if (sets.empty()) passes.clear();  // every sample is empty: nothing to count
-    if (passes.empty() && need_ns) passes.push_back(Pass());  // counts sample rows only
-
-    // build passes and the workspace layout
+    // workspace: status | per pass: inputs, outputs
     Ws ws;
     const uint64_t status_off = ws.take(256);
     for (auto& ps : passes) {
-        if (gace_status st = build_pass(ctx, *tab, ps, uterms, pred_u, sets, want_marg)) return st;
-        ProbeArgs& A = ps.args;
-        ps.in_bytes = round_up(A.nterms * 16ull, 16) + round_up(A.npool * 4ull, 16) +
-                      round_up((A.npreds + 1) * 4ull, 16) + round_up(A.npredterms * 4ull, 16);
-        ps.out_bytes = (static_cast<uint64_t>(A.nsets) * A.npreds + static_cast<uint64_t>(A.nsets) * A.nterms +
-                        A.nsets) * 8ull;
         ps.in_off = ws.take(ps.in_bytes);
         ps.out_off = ws.take(ps.out_bytes);
     }
-    const uint64_t out_lo = passes.empty() ? 0 : passes.front().out_off;
-    uint64_t pin_need = ws.off + 256;
     if (gace_status st = ctx->ensure_ws(ws.off)) return st;
-    if (gace_status st = ctx->ensure_pin(pin_need)) return st;
+    if (gace_status st = ctx->ensure_pin(ws.off + 256)) return st;
 
     // stage inputs into pinned memory, one H2D copy, zero outputs
     unsigned char* pin = ctx->pin;
     unsigned char* dws = ctx->ws;
-    for (auto& ps : passes) {
-        ProbeArgs& A = ps.args;
-        uint64_t o = ps.in_off;
-        auto put = [&](const void* src, uint64_t bytes) {
-            const uint64_t at = o;
-            if (bytes) memcpy(pin + o, src, bytes);
-            o += round_up(bytes, 16);
-            return at;
-        };
-        const uint64_t o_terms = put(ps.dterms.data(), ps.dterms.size() * 16ull);
-        const uint64_t o_pool = put(ps.pool.data(), ps.pool.size() * 4ull);
-        const uint64_t o_poff = put(ps.poff.data(), ps.poff.size() * 4ull);
-        const uint64_t o_pterm = put(ps.pterm.data(), ps.pterm.size() * 4ull);
-        A.terms = reinterpret_cast<const DevTerm*>(dws + o_terms);
-        A.pool = reinterpret_cast<const uint32_t*>(dws + o_pool);
-        A.pred_off = reinterpret_cast<const uint32_t*>(dws + o_poff);
-        A.pred_terms = reinterpret_cast<const uint32_t*>(dws + o_pterm);
-        unsigned long long* out = reinterpret_cast<unsigned long long*>(dws + ps.out_off);
-        A.counts = out;
-        A.marg = out + static_cast<uint64_t>(A.nsets) * A.npreds;
-        A.nsamp = A.marg + static_cast<uint64_t>(A.nsets) * A.nterms;
-        A.status = reinterpret_cast<unsigned int*>(dws + status_off);
-    }
+    unsigned int* dstatus = reinterpret_cast<unsigned int*>(dws + status_off);
+    for (auto& ps : passes) stage_pass(ps, pin, dws, dstatus);
     if (!passes.empty()) {
         const uint64_t first_in = passes.front().in_off;
         CK(cudaMemcpyAsync(dws + first_in, pin + first_in, ws.off - first_in, cudaMemcpyHostToDevice,
@@ -1052,90 +1038,19 @@ gace_status gace_probe_batch(gace_ctx* ctx, uint32_t table_id, const gace_sample
         CK(ctx->traced(ps.args.narrow ? "probe_narrow" : "probe_wide", n, n * ps.rowbytes, n * ps.ops_per_row,
                        [&] { return probe_launch(ps.args, static_cast<int>(grid), ctx->stream); }));
     }
-    const uint64_t rb_lo = status_off, rb_hi = passes.empty() ? status_off + 256 : ws.off;
-    (void)out_lo;
-    CK(cudaMemcpyAsync(pin + rb_lo, dws + rb_lo, rb_hi - rb_lo, cudaMemcpyDeviceToHost, ctx->stream));
+    const uint64_t rb_hi = passes.empty() ? status_off + 256 : ws.off;
+    CK(cudaMemcpyAsync(pin + status_off, dws + status_off, rb_hi - status_off, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->collect();
     if (gace_status st = read_status(ctx, *reinterpret_cast<unsigned int*>(pin + status_off))) return st;
-
-    // assemble results
-    std::vector<uint64_t> ns(nsamples, 0);
-    for (uint32_t s = 0; s < nsamples; ++s) {
-        if (set_dev[s] < 0) continue;
-        const SetDesc& d = sets[set_dev[s]].d;
-        if (d.mode == 1) {
-            ns[s] = tab->nrows;
-        } else {
-            const Pass& ps = passes.front();
-            const unsigned long long* out = reinterpret_cast<const unsigned long long*>(pin + ps.out_off);
-            ns[s] = out[static_cast<uint64_t>(ps.args.nsets) * ps.args.npreds +
-                        static_cast<uint64_t>(ps.args.nsets) * ps.args.nterms + set_dev[s]];
-        }
-    }
-    // per unique term: (pass, local index)
-    std::vector<std::pair<int32_t, uint32_t>> uloc(uterms.size(), {-1, 0});
-    for (uint32_t k = 0; k < passes.size(); ++k)
-        for (uint32_t i = 0; i < passes[k].uterms.size(); ++i) uloc[passes[k].uterms[i]] = {static_cast<int32_t>(k), i};
-    auto marg_of = [&](uint32_t t, uint32_t s) -> uint64_t {
-        const uint32_t u = t2u[t];
-        if (u == UINT32_MAX) return 0;
-        const auto& L = uloc[u];
-        if (L.first < 0 || set_dev[s] < 0) return 0;
-        const Pass& ps = passes[L.first];
-        const unsigned long long* out = reinterpret_cast<const unsigned long long*>(pin + ps.out_off);
-        return out[static_cast<uint64_t>(ps.args.nsets) * ps.args.npreds +
-                   static_cast<uint64_t>(set_dev[s]) * ps.args.nterms + L.second];
-    };
-    std::vector<std::pair<int32_t, uint32_t>> ploc(npreds, {-1, 0});
-    for (uint32_t k = 0; k < passes.size(); ++k)
-        for (uint32_t i = 0; i < passes[k].preds.size(); ++i) ploc[passes[k].preds[i]] = {static_cast<int32_t>(k), i};
-    for (uint32_t s = 0; s < nsamples; ++s) {
-        for (uint32_t p = 0; p < npreds; ++p) {
-            uint64_t m = 0;
-            if (pstate[p] == 2) {
-                m = ns[s];
-            } else if (pstate[p] == 0 && set_dev[s] >= 0) {
-                const Pass& ps = passes[ploc[p].first];
-                const unsigned long long* out = reinterpret_cast<const unsigned long long*>(pin + ps.out_off);
-                m = out[static_cast<uint64_t>(set_dev[s]) * ps.args.npreds + ploc[p].second];
-            }
-            gace_pred_result& r = results[static_cast<uint64_t>(s) * npreds + p];
-            r.match = m;
-            r.sample_rows = ns[s];
-            r.sel = ns[s] ? static_cast<double>(m) / static_cast<double>(ns[s]) : 0.0;
-            r.pcs = std::numeric_limits<double>::quiet_NaN();
-            if (preds[p].term_cnt == 2) {
-                const uint64_t ca = marg_of(preds[p].term_off, s), cb = marg_of(preds[p].term_off + 1, s);
-                if (ca != 0 && cb != 0)
-                    r.pcs = (static_cast<double>(m) * static_cast<double>(ns[s])) /
-                            (static_cast<double>(ca) * static_cast<double>(cb));
-            }
-        }
-        if (term_marginals)
-            for (uint32_t t = 0; t < nterms; ++t) term_marginals[static_cast<uint64_t>(s) * nterms + t] = marg_of(t, s);
-    }
+    std::vector<const unsigned long long*> outs;
+    for (auto& ps : passes) outs.push_back(reinterpret_cast<const unsigned long long*>(pin + ps.out_off));
+    assemble_probe(plan, r, outs);
     return GACE_OK;
 }
 
 // ---------------------------------------------------------------- HLL
 
-static double hll_estimate_host(const uint8_t* regs, uint32_t p) {
-    const uint64_t m = 1ull << p;
-    uint64_t hist[66] = {0};
-    for (uint64_t j = 0; j < m; ++j) hist[regs[j] < 65 ? regs[j] : 65]++;
-    const double dm = static_cast<double>(m);
-    double alpha;
-    if (m == 16) alpha = 0.673;
-    else if (m == 32) alpha = 0.697;
-    else if (m == 64) alpha = 0.709;
-    else alpha = 0.7213 / (1.0 + 1.079 / dm);
-    double z = 0.0;
-    for (int k = 0; k <= 65; ++k) z += static_cast<double>(hist[k]) * std::ldexp(1.0, -k);
-    double e = alpha * dm * dm / z;
-    if (e <= 2.5 * dm && hist[0] > 0) e = dm * std::log(dm / static_cast<double>(hist[0]));
-    return e;
-}
 
 gace_status gace_ndv(gace_ctx* ctx, uint32_t table_id, uint32_t col, uint32_t p, uint64_t hash_seed,
                      uint8_t* registers_out, double* estimate_out) {
@@ -1181,77 +1096,7 @@ gace_status gace_ndv(gace_ctx* ctx, uint32_t table_id, uint32_t col, uint32_t p,
 
 // ---------------------------------------------------------------- joins
 
-struct SideWork {
-    uint64_t rows = 0, rowbytes = 0, ops_per_row = 1;
-};
 
-static gace_status build_side(gace_ctx* ctx, const gace_join_side& js, const char* name, int extra_col,
-                              SideArgs& a, std::vector<uint32_t>& pool, TableRec** tab_out, uint32_t* extra_slot,
-                              SideWork& work) {
-    TableRec* tab = find_table(ctx, js.table_id);
-    if (!tab) return fail(GACE_ENOTFOUND, "%s table %u is not loaded", name, js.table_id);
-    if (js.key_col >= tab->cols.size()) return fail(GACE_EINVAL, "%s key column %u out of range", name, js.key_col);
-    if (tab->cols[js.key_col].dtype == GACE_F32) return fail(GACE_EINVAL, "%s key column is float32", name);
-    if (js.nterms && !js.terms) return fail(GACE_EINVAL, "%s terms is NULL", name);
-    if (js.nterms > static_cast<uint32_t>(kMaxFilterTerms))
-        return fail(GACE_EINVAL, "%s filter has %u terms (max %d)", name, js.nterms, kMaxFilterTerms);
-    a = SideArgs{};
-    a.nrows = tab->nrows;
-    std::vector<uint32_t> slot_col;
-    auto slot_of = [&](uint32_t col) -> int {
-        for (uint32_t s = 0; s < slot_col.size(); ++s)
-            if (slot_col[s] == col) return static_cast<int>(s);
-        if (slot_col.size() == static_cast<size_t>(kMaxFilterSlots)) return -1;
-        slot_col.push_back(col);
-        return static_cast<int>(slot_col.size() - 1);
-    };
-    a.key_slot = static_cast<uint32_t>(slot_of(js.key_col));
-    if (extra_col >= 0) {
-        if (static_cast<uint32_t>(extra_col) >= tab->cols.size() || tab->cols[extra_col].dtype == GACE_F32)
-            return fail(GACE_EINVAL, "%s fk2 column %d invalid", name, extra_col);
-        *extra_slot = static_cast<uint32_t>(slot_of(static_cast<uint32_t>(extra_col)));
-    }
-    uint32_t nt = 0;
-    bool never = false;
-    for (uint32_t t = 0; t < js.nterms; ++t) {
-        if (js.terms[t].col >= tab->cols.size())
-            return fail(GACE_EINVAL, "%s term %u references column %u", name, t, js.terms[t].col);
-        NTerm n;
-        if (gace_status st = normalize_term(js.terms[t], tab->cols[js.terms[t].col].dtype, js.in_values, js.nin, n))
-            return st;
-        if (n.kind == kFalse) {
-            never = true;
-            continue;
-        }
-        const int s = slot_of(n.col);
-        if (s < 0) return fail(GACE_EINVAL, "%s filter references more than %d columns", name, kMaxFilterSlots);
-        FilterTerm& ft = a.terms[nt++];
-        ft.slot = static_cast<uint32_t>(s);
-        ft.kind = n.kind;
-        work.ops_per_row += term_cost(n);
-        uint32_t poff = static_cast<uint32_t>(pool.size());
-        if (is_in_kind(n.kind)) pool.insert(pool.end(), n.in.begin(), n.in.end());
-        ft.c = make_devterm(n, poff);
-    }
-    if (never) {  // an always-false term: a range no value satisfies on the key column
-        nt = 0;
-        FilterTerm& ft = a.terms[nt++];
-        ft.slot = a.key_slot;
-        ft.kind = kInI32;
-        ft.c = DevTerm{0, 0, 0, 0};  // empty IN list
-    }
-    a.nterms = nt;
-    a.nslots = static_cast<uint32_t>(slot_col.size());
-    work.rows = tab->nrows;
-    for (uint32_t c : slot_col) work.rowbytes += dtype_width(tab->cols[c].dtype);
-    for (uint32_t s = 0; s < slot_col.size(); ++s) {
-        a.slot_ptr[s] = tab->cols[slot_col[s]].dptr;
-        a.slot_dtype[s] = static_cast<uint32_t>(tab->cols[slot_col[s]].dtype);
-        a.slot_aligned[s] = (reinterpret_cast<uintptr_t>(a.slot_ptr[s]) & 15u) == 0;
-    }
-    *tab_out = tab;
-    return GACE_OK;
-}
 
 gace_status gace_join_card(gace_ctx* ctx, const gace_join* spec, gace_join_result* out) {
     if (gace_status s = check_ctx(ctx)) return s;

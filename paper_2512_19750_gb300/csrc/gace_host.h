@@ -1,0 +1,317 @@
+// gace_host.h -- host-runtime types and helpers shared by the translation
+// units of libgace (context, tables, term normalisation, probe planning).
+// Internal: not part of the public ABI (include/gace.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/gace.h"
+#include "gace_internal.h"
+
+struct gace_ctx;
+
+namespace gace {
+namespace host {
+
+// Sets the thread-local error message and returns s.
+gace_status fail(gace_status s, const char* fmt, ...);
+gace_status cuda_fail(cudaError_t e, const char* what);
+
+#define CK(call)                                           \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return ::gace::host::cuda_fail(e_, #call); \
+    } while (0)
+
+// splitmix64 output function (Steele, Lea & Flood, OOPSLA 2014), host side.
+inline uint64_t splitmix64_host(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+inline uint32_t dtype_width(int dt) { return dt == GACE_I64 ? 8u : 4u; }
+
+inline uint64_t round_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+struct ColumnRec {
+    int dtype = 0;
+    void* dptr = nullptr;
+    bool owned = false;
+    uint64_t bytes = 0;
+};
+
+struct TableRec {
+    uint64_t nrows = 0;
+    std::vector<ColumnRec> cols;
+    uint64_t owned_bytes = 0;
+};
+
+}  // namespace host
+}  // namespace gace
+
+using namespace gace;
+using namespace gace::host;
+
+struct gace_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int sms = 0;
+    int smem_optin = 0;
+    uint64_t budget = 0;       // 0 = unlimited
+    uint64_t used = 0;         // owned tables + workspace + pinned
+    uint64_t timeout_ns = 2000ull * 1000000ull;
+    std::mutex mu;
+    std::unordered_map<uint32_t, TableRec> tables;
+    uint32_t next_id = 1;
+    unsigned char* ws = nullptr;  // device workspace
+    uint64_t ws_cap = 0;
+    unsigned char* pin = nullptr;  // pinned host staging
+    uint64_t pin_cap = 0;
+    unsigned int* d_status = nullptr;
+
+    // kernel statistics (tracing)
+    struct KStat {
+        uint64_t launches = 0, rows = 0, bytes = 0, ops = 0;
+        double ms = 0.0;
+    };
+    struct Timed {
+        std::string name;
+        cudaEvent_t a, b;
+    };
+    std::map<std::string, KStat> stats;
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<Timed> pending;
+
+    cudaEvent_t take_event() {
+        if (!ev_free.empty()) {
+            cudaEvent_t e = ev_free.back();
+            ev_free.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        return e;
+    }
+
+    // Counts one launch with its algorithmic work and, when timing, brackets
+    // it with events on the context stream.
+    template <typename F>
+    cudaError_t traced(const char* name, uint64_t rows, uint64_t bytes, uint64_t ops, F&& launch) {
+        KStat& k = stats[name];
+        k.launches++;
+        k.rows += rows;
+        k.bytes += bytes;
+        k.ops += ops;
+        if (!timing) return launch();
+        cudaEvent_t a = take_event(), b = take_event();
+        if (a) cudaEventRecord(a, stream);
+        cudaError_t e = launch();
+        if (b) cudaEventRecord(b, stream);
+        if (a && b) pending.push_back({name, a, b});
+        return e;
+    }
+
+    // After a stream synchronisation: fold event pairs into the statistics.
+    void collect() {
+        for (auto& t : pending) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) stats[t.name].ms += ms;
+            ev_free.push_back(t.a);
+            ev_free.push_back(t.b);
+        }
+        pending.clear();
+    }
+
+    bool fits(uint64_t extra) const { return budget == 0 || used + extra <= budget; }
+
+    gace_status ensure_ws(uint64_t bytes) {
+        bytes = round_up(bytes ? bytes : 256, 1 << 20);
+        if (bytes <= ws_cap) return GACE_OK;
+        if (!fits(bytes - ws_cap))
+            return fail(GACE_ENOMEM, "workspace of %llu bytes exceeds the HBM budget",
+                        (unsigned long long)bytes);
+        CK(cudaStreamSynchronize(stream));
+        if (ws) {
+            cudaFree(ws);
+            used -= ws_cap;
+            ws = nullptr;
+            ws_cap = 0;
+        }
+        cudaError_t e = cudaMalloc(&ws, bytes);
+        if (e != cudaSuccess) {
+            ws = nullptr;
+            return fail(GACE_ENOMEM, "cudaMalloc(%llu) for the workspace: %s",
+                        (unsigned long long)bytes, cudaGetErrorString(e));
+        }
+        ws_cap = bytes;
+        used += bytes;
+        return GACE_OK;
+    }
+
+    gace_status ensure_pin(uint64_t bytes) {
+        bytes = round_up(bytes ? bytes : 256, 1 << 16);
+        if (bytes <= pin_cap) return GACE_OK;
+        CK(cudaStreamSynchronize(stream));
+        if (pin) {
+            cudaFreeHost(pin);
+            pin = nullptr;
+            pin_cap = 0;
+        }
+        cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&pin), bytes, cudaHostAllocDefault);
+        if (e != cudaSuccess) {
+            pin = nullptr;
+            return fail(GACE_ENOMEM, "cudaHostAlloc(%llu): %s", (unsigned long long)bytes,
+                        cudaGetErrorString(e));
+        }
+        pin_cap = bytes;
+        return GACE_OK;
+    }
+};
+
+
+namespace gace {
+namespace host {
+
+// ---------------------------------------------------------------- terms
+
+struct NTerm {
+    uint32_t col = 0;
+    uint32_t kind = kFalse;
+    uint64_t a = 0, b = 0;
+    std::vector<uint32_t> in;  // pool words
+    bool operator<(const NTerm& o) const {
+        return std::tie(col, kind, a, b, in) < std::tie(o.col, o.kind, o.a, o.b, o.in);
+    }
+};
+
+gace_status normalize_term(const gace_term& t, int dtype, const gace_scalar* in_values, uint32_t nin, NTerm& out);
+bool is_in_kind(uint32_t k);
+uint32_t in_count(const NTerm& t);
+uint32_t pool_estimate(const NTerm& t);
+uint64_t term_cost(const NTerm& t);
+DevTerm make_devterm(const NTerm& t, uint32_t pool_off);
+
+// ---------------------------------------------------------------- sets
+
+struct SetPlan {
+    SetDesc d;
+    uint32_t orig;
+};
+
+gace_status make_set(const gace_sample& s, SetDesc& d);
+
+// ---------------------------------------------------------------- probe plan
+
+constexpr uint32_t kPassTerms = 256;
+constexpr uint32_t kPassPreds = 256;
+constexpr uint32_t kPassPool = 16384;  // pool words: IN lists (narrow) or EQ/IN tables (wide)
+
+struct Pass {
+    std::vector<uint32_t> preds;   // device predicate indices (input numbering)
+    std::vector<uint32_t> uterms;  // unique terms placed in this pass
+    // built:
+    std::vector<DevTerm> dterms;
+    std::vector<uint32_t> pool, poff, pterm;
+    std::vector<uint32_t> u_local;  // unique term -> local index (parallel to uterms order)
+    std::vector<std::pair<uint32_t, uint32_t>> slots;  // (col, first local term)
+    ProbeArgs args{};
+    uint64_t in_off = 0, out_off = 0;  // workspace offsets
+    uint64_t ops_per_row = 0;          // compares per row (statistics)
+    uint32_t rowbytes = 0;             // bytes per row of the referenced columns
+    uint64_t in_bytes = 0, out_bytes = 0;
+};
+
+struct Ws {
+    uint64_t off = 0;
+    uint64_t take(uint64_t bytes, uint64_t align = 256) {
+        off = round_up(off, align);
+        const uint64_t r = off;
+        off += bytes;
+        return r;
+    }
+};
+
+gace_status check_ctx(gace_ctx* ctx);
+TableRec* find_table(gace_ctx* ctx, uint32_t id);
+gace_status read_status(gace_ctx* ctx, unsigned int st);
+
+// The arguments of one probe (gace_probe_batch, or a probe request of a batch).
+struct ProbeRequest {
+    const gace_sample* samples = nullptr;
+    uint32_t nsamples = 0;
+    const gace_term* terms = nullptr;
+    uint32_t nterms = 0;
+    const gace_scalar* in_values = nullptr;
+    uint32_t nin = 0;
+    const gace_pred* preds = nullptr;
+    uint32_t npreds = 0;
+    gace_pred_result* results = nullptr;
+    uint64_t* term_marginals = nullptr;
+};
+
+// A probe compiled into device passes: row sets, deduplicated terms, the
+// predicates' states and the passes that evaluate them.
+struct ProbePlan {
+    const TableRec* tab = nullptr;
+    std::vector<SetPlan> sets;     // device row sets
+    std::vector<int32_t> set_dev;  // sample -> device set, -1 if empty
+    std::vector<NTerm> uterms;
+    std::vector<uint32_t> t2u;     // input term -> unique term (UINT32_MAX: never true)
+    std::vector<uint8_t> pstate;   // 0 device, 1 never true, 2 always true
+    std::vector<std::vector<uint32_t>> pred_u;
+    bool want_marg = false;
+    std::vector<Pass> passes;
+};
+
+// Argument checks that need no table.
+gace_status check_probe_request(const ProbeRequest& r);
+// Compiles a probe; force_wide builds every pass in the wide-kernel layout.
+gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r, bool force_wide,
+                       ProbePlan& plan);
+// Bytes of a pass's inputs (terms, pool, predicate CSR) and outputs (counters).
+void pass_sizes(Pass& ps);
+// Copies a pass's inputs into pinned staging at ps.in_off and points its
+// arguments at their device copies (workspace base dws) and at its outputs.
+void stage_pass(Pass& ps, unsigned char* pin, unsigned char* dws, unsigned int* status);
+// Results from the passes' counters (host copies, one pointer per pass).
+void assemble_probe(const ProbePlan& plan, const ProbeRequest& r,
+                    const std::vector<const unsigned long long*>& pass_out);
+
+// ---------------------------------------------------------------- HLL, joins
+
+double hll_estimate_host(const uint8_t* regs, uint32_t p);
+
+struct SideWork {
+    uint64_t rows = 0, rowbytes = 0, ops_per_row = 1;
+};
+gace_status build_side(gace_ctx* ctx, const gace_join_side& js, const char* name, int extra_col, SideArgs& a,
+                       std::vector<uint32_t>& pool, TableRec** tab_out, uint32_t* extra_slot, SideWork& work);
+
+}  // namespace host
+}  // namespace gace
