@@ -282,6 +282,65 @@ gace_status gace_ndv_noalloc(const void* column, int32_t dtype, uint64_t nrows, 
                              uint64_t hash_seed, void* stream, uint8_t* registers_out,
                              double* estimate_out);
 
+/* ------------------------------------------------------------ batched form */
+
+typedef enum { GACE_REQ_PROBE = 0, GACE_REQ_NDV = 1, GACE_REQ_JOIN = 2 } gace_req_kind;
+
+/*
+ * One request of a batch (gace_run_batch): the arguments and outputs of the
+ * matching synchronous call (gace_probe_batch, gace_ndv or gace_join_card),
+ * fields of the other kinds ignored.  Output pointers are HOST memory.  The
+ * paper's Risky Gate issues many such probes per query workload (Section
+ * III-A); the batch runs them together.
+ */
+typedef struct {
+    uint32_t kind;                /* gace_req_kind */
+    uint32_t table_id;            /* PROBE, NDV */
+    const gace_sample* samples;   /* PROBE */
+    uint32_t nsamples;
+    uint32_t nterms;
+    const gace_term* terms;
+    const gace_scalar* in_values;
+    uint32_t nin;
+    uint32_t npreds;
+    const gace_pred* preds;
+    gace_pred_result* results;    /* out, nsamples * npreds */
+    uint64_t* term_marginals;     /* out or NULL */
+    uint32_t col;                 /* NDV */
+    uint32_t p;
+    uint64_t hash_seed;
+    uint8_t* registers_out;       /* out or NULL */
+    double* estimate_out;         /* out or NULL */
+    const gace_join* join;        /* JOIN */
+    gace_join_result* join_out;   /* out */
+} gace_request;
+
+/*
+ * Runs n requests as one batch: every request is compiled into jobs, each job
+ * split into row chunks, and one persistent kernel per dependency phase (join
+ * histograms before the sums that read them) drains the chunks from a device
+ * work queue.  The upload of the compiled batch, the clearing of its
+ * counters, the phase launches and the read-back form one CUDA graph that is
+ * replayed while batches keep the same shape.  Chunk size and grid come from
+ * the context's tuning table (gace_tune_batch), else defaults.  Results are
+ * identical to the synchronous calls'.  statuses (out, n entries, may be NULL)
+ * receives each request's status; the return value is GACE_OK when every
+ * request succeeded, else the first failing request's status.
+ */
+gace_status gace_run_batch(gace_ctx* ctx, const gace_request* reqs, uint32_t n, gace_status* statuses);
+
+/*
+ * Autotuner: runs the batch with each candidate chunk size (128K..8M rows)
+ * and grid (1, 2 or the maximum of CTAs per SM), times every candidate with
+ * CUDA events, and records the fastest for batches of this shape (jobs and
+ * rows, each bucketed by powers of two) in the context's tuning table.
+ */
+gace_status gace_tune_batch(gace_ctx* ctx, const gace_request* reqs, uint32_t n);
+
+/* The tuning table as JSON lines (save) / merged from such a file (load). */
+gace_status gace_tune_save(gace_ctx* ctx, const char* path);
+gace_status gace_tune_load(gace_ctx* ctx, const char* path);
+
 /*
  * Kernel statistics of a context (tracing; the paper decomposes probe time
  * into transfer, kernel and reduction phases, Section IV-B).  Every launch is

@@ -14,7 +14,8 @@ import numpy as np
 from . import _capi
 from ._capi import (GACE_BLOCKS, GACE_BORROW, GACE_COPY, GACE_EQ, GACE_F32, GACE_FULL, GACE_I32,
                     GACE_I64, GACE_IN, GACE_JOIN_AUTO, GACE_JOIN_GATHER, GACE_JOIN_HIST_DOT,
-                    GACE_OK, GACE_RANGE, GACE_ROWS, GaceError, check, lib)
+                    GACE_OK, GACE_RANGE, GACE_REQ_JOIN, GACE_REQ_NDV, GACE_REQ_PROBE, GACE_ROWS,
+                    GaceError, check, lib)
 
 RESULT_DTYPE = np.dtype([("match", "<u8"), ("sample_rows", "<u8"), ("sel", "<f8"), ("pcs", "<f8")])
 _NP_OF = {GACE_I32: np.int32, GACE_I64: np.int64, GACE_F32: np.float32}
@@ -218,6 +219,112 @@ def gace_join_card(ctx, fact: JoinSideSpec, dim: JoinSideSpec, key_domain: int,
             "dim2_rows": int(out.dim2_rows)}
 
 
+# ----------------------------------------------------------------- batched form
+
+class ProbeRequest:
+    """A probe request of a batch; after the batch, .results / .marginals
+    hold what gace_probe_batch would return."""
+
+    def __init__(self, table_id: int, preds, samples, dtypes, marginals: bool = False,
+                 batch: TermBatch | None = None):
+        self.table_id = table_id
+        self.b = batch or TermBatch(preds, dtypes)
+        self.smp = _samples(samples)
+        self.nsamples = len(samples)
+        self.results = np.zeros((len(samples), self.b.npreds), dtype=RESULT_DTYPE)
+        self.marginals = np.zeros((len(samples), self.b.nterms), dtype=np.uint64) if marginals else None
+
+    def fill(self, r):
+        r.kind, r.table_id = _capi.GACE_REQ_PROBE, self.table_id
+        r.samples, r.nsamples = C.cast(self.smp, C.POINTER(_capi.gace_sample)), self.nsamples
+        r.terms, r.nterms = C.cast(self.b.terms, C.POINTER(_capi.gace_term)), self.b.nterms
+        r.in_values, r.nin = C.cast(self.b.in_values, C.POINTER(_capi.gace_scalar)), self.b.nin
+        r.preds, r.npreds = C.cast(self.b.preds, C.POINTER(_capi.gace_pred)), self.b.npreds
+        r.results = self.results.ctypes.data_as(C.POINTER(_capi.gace_pred_result))
+        r.term_marginals = (self.marginals.ctypes.data_as(C.POINTER(C.c_uint64))
+                            if self.marginals is not None and self.b.nterms else None)
+
+
+class NdvRequest:
+    """An HLL request of a batch; after the batch, .registers / .estimate."""
+
+    def __init__(self, table_id: int, col: int, p: int, hash_seed: int):
+        self.table_id, self.col, self.p, self.seed = table_id, col, p, int(hash_seed) & ((1 << 64) - 1)
+        self.registers = np.zeros(1 << p, dtype=np.uint8)
+        self._est = C.c_double()
+
+    @property
+    def estimate(self) -> float:
+        return float(self._est.value)
+
+    def fill(self, r):
+        r.kind, r.table_id, r.col, r.p, r.hash_seed = _capi.GACE_REQ_NDV, self.table_id, self.col, self.p, self.seed
+        r.registers_out = self.registers.ctypes.data_as(C.POINTER(C.c_uint8))
+        r.estimate_out = C.pointer(self._est)
+
+
+class JoinRequest:
+    """A join request of a batch; after the batch, .result (as gace_join_card)."""
+
+    def __init__(self, fact: "JoinSideSpec", dim: "JoinSideSpec", key_domain: int, dim2=None,
+                 key_domain2: int = 0, dim_fk2_col: int = 0, method: int = GACE_JOIN_AUTO):
+        self.sides = (fact, dim, dim2)
+        self.spec = _capi.gace_join()
+        fact.fill(self.spec.fact)
+        dim.fill(self.spec.dim)
+        self.spec.key_domain = key_domain
+        if dim2 is not None:
+            dim2.fill(self.spec.dim2)
+            self.spec.key_domain2, self.spec.dim_fk2_col, self.spec.hops = key_domain2, dim_fk2_col, 2
+        else:
+            self.spec.hops = 1
+        self.spec.method = method
+        self.out = _capi.gace_join_result()
+
+    @property
+    def result(self) -> dict:
+        o = self.out
+        return {"card": int(o.card), "fact_rows": int(o.fact_rows), "dim_rows": int(o.dim_rows),
+                "dim2_rows": int(o.dim2_rows)}
+
+    def fill(self, r):
+        r.kind = _capi.GACE_REQ_JOIN
+        r.join = C.pointer(self.spec)
+        r.join_out = C.pointer(self.out)
+
+
+def _request_array(requests):
+    arr = (_capi.gace_request * max(1, len(requests)))()
+    for k, q in enumerate(requests):
+        q.fill(arr[k])
+    return arr
+
+
+def gace_run_batch(ctx, requests, raise_on_error: bool = True):
+    """Runs ProbeRequest / NdvRequest / JoinRequest objects as one batch;
+    returns the per-request statuses (and raises on the first failure unless
+    raise_on_error is False)."""
+    arr = _request_array(requests)
+    st = (C.c_int * max(1, len(requests)))()
+    rc = lib().gace_run_batch(ctx, arr, len(requests), st)
+    if raise_on_error:
+        check(rc, "gace_run_batch")
+    return [int(st[i]) for i in range(len(requests))]
+
+
+def gace_tune_batch(ctx, requests) -> None:
+    arr = _request_array(requests)
+    check(lib().gace_tune_batch(ctx, arr, len(requests)), "gace_tune_batch")
+
+
+def gace_tune_save(ctx, path: str) -> None:
+    check(lib().gace_tune_save(ctx, path.encode()), "gace_tune_save")
+
+
+def gace_tune_load(ctx, path: str) -> None:
+    check(lib().gace_tune_load(ctx, path.encode()), "gace_tune_load")
+
+
 def gace_stats_reset(ctx, time_kernels: bool = False) -> None:
     check(lib().gace_stats_reset(ctx, 1 if time_kernels else 0), "gace_stats_reset")
 
@@ -242,4 +349,5 @@ def gace_status_string(s: int) -> str:
 
 
 __all__ = [n for n in dir() if n.startswith(("gace_", "GACE_"))] + [
-    "GaceError", "JoinSideSpec", "RESULT_DTYPE", "TermBatch", "check", "lib"]
+    "GaceError", "JoinRequest", "JoinSideSpec", "NdvRequest", "ProbeRequest", "RESULT_DTYPE", "TermBatch",
+    "check", "lib"]

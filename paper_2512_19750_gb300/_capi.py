@@ -18,6 +18,7 @@ GACE_EQ, GACE_RANGE, GACE_IN = 0, 1, 2
 GACE_FULL, GACE_ROWS, GACE_BLOCKS = 0, 1, 2
 GACE_COPY, GACE_BORROW = 0, 1
 GACE_JOIN_AUTO, GACE_JOIN_HIST_DOT, GACE_JOIN_GATHER = 0, 1, 2
+GACE_REQ_PROBE, GACE_REQ_NDV, GACE_REQ_JOIN = 0, 1, 2
 
 
 class gace_scalar(C.Union):
@@ -70,6 +71,18 @@ class gace_join_result(C.Structure):
                 ("dim2_rows", C.c_uint64)]
 
 
+class gace_request(C.Structure):
+    _fields_ = [("kind", C.c_uint32), ("table_id", C.c_uint32),
+                ("samples", C.POINTER(gace_sample)), ("nsamples", C.c_uint32),
+                ("nterms", C.c_uint32), ("terms", C.POINTER(gace_term)),
+                ("in_values", C.POINTER(gace_scalar)), ("nin", C.c_uint32), ("npreds", C.c_uint32),
+                ("preds", C.POINTER(gace_pred)), ("results", C.POINTER(gace_pred_result)),
+                ("term_marginals", C.POINTER(C.c_uint64)), ("col", C.c_uint32), ("p", C.c_uint32),
+                ("hash_seed", C.c_uint64), ("registers_out", C.POINTER(C.c_uint8)),
+                ("estimate_out", C.POINTER(C.c_double)), ("join", C.POINTER(gace_join)),
+                ("join_out", C.POINTER(gace_join_result))]
+
+
 class gace_kernel_stat(C.Structure):
     _fields_ = [("name", C.c_char * 24), ("launches", C.c_uint64), ("rows", C.c_uint64),
                 ("bytes", C.c_uint64), ("ops", C.c_uint64), ("total_ms", C.c_double)]
@@ -93,6 +106,10 @@ PROTOTYPES = {
     "gace_join_card": (C.c_int, [ctx_p, C.POINTER(gace_join), C.POINTER(gace_join_result)]),
     "gace_ndv_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_uint64, C.c_uint32, C.c_uint64,
                                    C.c_void_p, C.POINTER(C.c_uint8), C.POINTER(C.c_double)]),
+    "gace_run_batch": (C.c_int, [ctx_p, C.POINTER(gace_request), C.c_uint32, C.POINTER(C.c_int)]),
+    "gace_tune_batch": (C.c_int, [ctx_p, C.POINTER(gace_request), C.c_uint32]),
+    "gace_tune_save": (C.c_int, [ctx_p, C.c_char_p]),
+    "gace_tune_load": (C.c_int, [ctx_p, C.c_char_p]),
     "gace_stats_reset": (C.c_int, [ctx_p, C.c_uint32]),
     "gace_stats_read": (C.c_int, [ctx_p, C.POINTER(gace_kernel_stat), C.c_uint32,
                                   C.POINTER(C.c_uint32)]),

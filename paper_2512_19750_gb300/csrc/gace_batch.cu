@@ -1,0 +1,154 @@
+// gace_batch.cu -- the batched form: one persistent kernel drains a device
+// work queue of (job, row-range) items.
+//
+// A batch mixes predicate probes, HyperLogLog sketches and join phases over
+// many tables.  Every CTA repeatedly takes the next item index with one
+// atomicAdd on the phase's queue head and runs that item with all its warps:
+//   probe      the wide-pass code over the item's 128-row slices, counters in
+//              shared memory, added to the job's 64-bit totals at item end;
+//   HLL        a CTA copy of the registers in shared memory for the item's
+//              rows, merged into the job's global registers where larger;
+//   join side  filtered histogram, gather or chain-weight update over the
+//              item's rows, pass counts and sums reduced per CTA;
+//   max / dot  over a range of histogram entries.
+// Items of one job are independent, so CTAs never wait on each other; jobs
+// that read what other jobs write (a join's sum reads its histogram) are put
+// in a later phase, i.e. a later launch.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gace_device.cuh"
+#include "gace_internal.h"
+#include "gace_probe_dev.cuh"
+#include "gace_side_dev.cuh"
+
+namespace gace {
+namespace {
+
+using namespace dev;
+using namespace probe_dev;
+using namespace side_dev;
+
+__device__ __forceinline__ void probe_item(const BatchJob& J, const BatchItem& it, unsigned char* smem, int tid,
+                                           int lane, int warp) {
+    const ProbeArgs& A = *J.probe;
+    const Smem S = carve(A, smem, warp);
+    load_tables(A, S, tid);
+    __syncthreads();
+    const uint64_t first = it.begin / kSliceRows + warp;
+    const uint64_t end = (it.end + kSliceRows - 1) / kSliceRows;
+    const uint32_t nsr = wide_slices(A, S, lane, first, end, kProbeWarps);
+    if (lane < static_cast<int>(A.nsets) && nsr) atomicAdd(&S.ns[lane], nsr);
+    __syncthreads();
+    flush(A, S, tid);
+}
+
+template <int DT>
+__device__ __forceinline__ void hll_item_t(const HllArgs& H, const BatchItem& it, uint32_t* sregs, int tid) {
+    const uint64_t first = it.begin / 4 + tid, end = (it.end + 3) / 4;
+    if (H.p <= 16) {  // the host sizes shared memory for 2^16 one-byte registers
+        const uint32_t m = 1u << H.p;
+        for (uint32_t i = tid; i < m / 4; i += kThreads) sregs[i] = 0;
+        __syncthreads();
+        hll_groups<true, DT>(H, sregs, first, end, kThreads);
+        __syncthreads();
+        hll_merge(H, sregs, m, tid, kThreads);
+    } else {
+        hll_groups<false, DT>(H, sregs, first, end, kThreads);
+    }
+}
+
+__device__ __forceinline__ void side_item(const BatchJob& J, const BatchItem& it, unsigned long long* scratch,
+                                          int tid, int lane) {
+    const SideArgs& SA = *J.side;
+    unsigned long long npass = 0, acc = 0;
+    const uint64_t first = it.begin / 4 + static_cast<uint64_t>(tid - lane);
+    const uint64_t end = (it.end + 3) / 4;
+    switch (J.kind) {
+        case kJobHist:
+            side_groups<0, false>(SA, J.hist, J.strict, nullptr, 0, 0, nullptr, first, end, kThreads, npass, acc);
+            break;
+        case kJobHistAgg:
+            side_groups<0, true>(SA, J.hist, J.strict, nullptr, 0, 0, nullptr, first, end, kThreads, npass, acc);
+            break;
+        case kJobGather32:
+            side_groups<1, false>(SA, nullptr, 0, J.weight, 0, 0, nullptr, first, end, kThreads, npass, acc);
+            break;
+        case kJobGather64:
+            side_groups<2, false>(SA, nullptr, 0, J.weight, 0, 0, nullptr, first, end, kThreads, npass, acc);
+            break;
+        default:  // kJobChain
+            side_groups<3, false>(SA, nullptr, 1, J.weight, J.fk2_slot, J.domain2, J.w64, first, end, kThreads,
+                                  npass, acc);
+            break;
+    }
+    const unsigned long long tp = block_sum_u64<kProbeWarps>(npass, scratch);
+    if (tid == 0 && tp) atomicAdd(SA.pass_count, tp);
+    if (J.kind == kJobGather32 || J.kind == kJobGather64) {
+        const unsigned long long ta = block_sum_u64<kProbeWarps>(acc, scratch);
+        if (tid == 0 && ta) atomicAdd(J.out, ta);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_batch(const BatchItem* __restrict__ items, uint32_t nitems,
+                                                    const BatchJob* __restrict__ jobs, unsigned int* head) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint32_t s_item;
+    __shared__ unsigned long long scratch[kProbeWarps];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(head, 1u);
+        __syncthreads();
+        const uint32_t k = s_item;
+        __syncthreads();  // every thread has read s_item before it is overwritten
+        if (k >= nitems) return;
+        const BatchItem it = items[k];
+        const BatchJob& J = jobs[it.job];
+        const uint32_t kind = J.kind;
+        if (kind == kJobProbe) {
+            probe_item(J, it, smem, tid, lane, warp);
+        } else if (kind == kJobHll) {
+            uint32_t* sregs = reinterpret_cast<uint32_t*>(smem);
+            if (J.hll.dtype == 0)
+                hll_item_t<0>(J.hll, it, sregs, tid);
+            else if (J.hll.dtype == 1)
+                hll_item_t<1>(J.hll, it, sregs, tid);
+            else
+                hll_item_t<2>(J.hll, it, sregs, tid);
+        } else if (kind <= kJobChain) {
+            side_item(J, it, scratch, tid, lane);
+        } else if (kind == kJobMax32 || kind == kJobMax64) {
+            const unsigned long long best = warp_max_u64(
+                kind == kJobMax64 ? max_range<true>(J.weight, it.begin + tid, it.end, kThreads)
+                                  : max_range<false>(J.weight, it.begin + tid, it.end, kThreads));
+            if (lane == 0 && best) atomicMax(J.out, best);
+        } else {
+            const unsigned long long acc =
+                kind == kJobDot64 ? dot_range<true>(J.hist, J.weight, it.begin + tid, it.end, kThreads)
+                                  : dot_range<false>(J.hist, J.weight, it.begin + tid, it.end, kThreads);
+            const unsigned long long t = block_sum_u64<kProbeWarps>(acc, scratch);
+            if (tid == 0 && t) atomicAdd(J.out, t);
+        }
+        __syncthreads();  // shared memory is reused by the next item
+    }
+}
+
+}  // namespace
+
+cudaError_t batch_configure(int smem_optin) {
+    return cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+}
+
+int batch_occupancy(uint32_t smem_bytes) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch, kThreads, smem_bytes) != cudaSuccess) return 0;
+    return n;
+}
+
+cudaError_t batch_launch(const BatchItem* items, uint32_t nitems, const BatchJob* jobs, unsigned int* head,
+                         int grid, uint32_t smem_bytes, cudaStream_t s) {
+    k_batch<<<grid, kThreads, smem_bytes, s>>>(items, nitems, jobs, head);
+    return cudaGetLastError();
+}
+
+}  // namespace gace

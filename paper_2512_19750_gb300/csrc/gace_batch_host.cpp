@@ -1,0 +1,703 @@
+// gace_batch_host.cpp -- host side of the batched form (gace_run_batch) and
+// its autotuner.
+//
+// A batch of requests is compiled into jobs: a probe into its passes (in the
+// wide layout, so one kernel evaluates any of them), an NDV request into one
+// HLL job, a join into histogram jobs and, in later phases, the jobs that read
+// those histograms (the largest entry for the overflow check, then the gather
+// or dot product; a chain adds the weight update between).  Each job is cut
+// into items of `chunk` rows.  Everything the kernels read lives in one
+// workspace arena:
+//
+//   [jobs][items][probe arguments, pass inputs, join sides, IN pools]   uploaded
+//   [status, queue heads, counters, registers, join scalars]  cleared, read back
+//   [join histograms and weights]                                     cleared
+//
+// The upload, the clearing, one persistent launch per phase and the read-back
+// are captured as one CUDA graph and replayed while later batches have the
+// same shape (same sizes and addresses); only the pinned staging contents
+// change.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <fstream>
+#include <limits>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "gace_host.h"
+
+namespace gace {
+namespace host {
+namespace {
+
+constexpr uint64_t kDefaultChunk = 1ull << 20;
+constexpr int kPhases = 3;
+constexpr uint32_t kHllSmem = 1u << 16;  // one-byte registers for p <= 16
+
+struct JobRec {
+    BatchJob job{};
+    uint32_t phase = 0;
+    uint64_t units = 0;  // rows, or histogram entries
+    const char* family = "";
+    uint64_t rows = 0, bytes = 0, ops = 0;  // statistics
+};
+
+// A compiled request: its plan and where its data sits in the arena
+// (offsets relative to the input, small-output and big-output regions).
+struct ReqPlan {
+    gace_status status = GACE_OK;
+    std::string error;
+    uint32_t kind = 0;
+    const gace_request* q = nullptr;
+    // probe
+    ProbeRequest pr;
+    ProbePlan plan;
+    std::vector<uint64_t> args_off;  // input region: ProbeArgs copy per pass
+    // ndv
+    uint64_t regs_off = 0;  // small region
+    HllArgs hll{};
+    TableRec* tab = nullptr;
+    // join
+    gace_join spec{};
+    SideArgs side[3]{};
+    SideWork work[3]{};
+    TableRec* tabs[3]{};
+    uint32_t fk2_slot = 0;
+    bool hist_dot = false;
+    uint64_t K = 0, K2 = 0;
+    std::vector<uint32_t> pool;
+    uint64_t pool_off = 0, side_off[3] = {0, 0, 0};  // input region
+    uint64_t sc_off = 0;                              // small region: scalars and status
+    uint64_t hd_off = 0, w_off = 0, hf_off = 0;       // big region
+};
+
+int log2_bucket(uint64_t x) {
+    int b = 0;
+    while (x > 1) {
+        x >>= 1;
+        ++b;
+    }
+    return b;
+}
+
+// Compiles one request (argument checks, plans, join sides).
+gace_status compile_request(gace_ctx* ctx, const gace_request& q, ReqPlan& rp) {
+    rp.q = &q;
+    rp.kind = q.kind;
+    if (q.kind == GACE_REQ_PROBE) {
+        ProbeRequest& r = rp.pr;
+        r.samples = q.samples;
+        r.nsamples = q.nsamples;
+        r.terms = q.terms;
+        r.nterms = q.nterms;
+        r.in_values = q.in_values;
+        r.nin = q.nin;
+        r.preds = q.preds;
+        r.npreds = q.npreds;
+        r.results = q.results;
+        r.term_marginals = q.term_marginals;
+        if (gace_status s = check_probe_request(r)) return s;
+        TableRec* tab = find_table(ctx, q.table_id);
+        if (!tab) return fail(GACE_ENOTFOUND, "table %u is not loaded", q.table_id);
+        return plan_probe(ctx, *tab, r, true, rp.plan);
+    }
+    if (q.kind == GACE_REQ_NDV) {
+        if (q.p < 4 || q.p > 18) return fail(GACE_EINVAL, "p = %u outside 4..18", q.p);
+        TableRec* tab = find_table(ctx, q.table_id);
+        if (!tab) return fail(GACE_ENOTFOUND, "table %u is not loaded", q.table_id);
+        if (q.col >= tab->cols.size())
+            return fail(GACE_EINVAL, "column %u of a %zu-column table", q.col, tab->cols.size());
+        rp.tab = tab;
+        HllArgs& a = rp.hll;
+        a.col = tab->cols[q.col].dptr;
+        a.nrows = tab->nrows;
+        a.dtype = static_cast<uint32_t>(tab->cols[q.col].dtype);
+        a.p = q.p;
+        a.seedhash = splitmix64_host(q.hash_seed);
+        a.aligned = (reinterpret_cast<uintptr_t>(a.col) & 15u) == 0;
+        return GACE_OK;
+    }
+    if (q.kind != GACE_REQ_JOIN) return fail(GACE_EINVAL, "request kind %u invalid", q.kind);
+    if (!q.join || !q.join_out) return fail(GACE_EINVAL, "join or join_out is NULL");
+    const gace_join& spec = *q.join;
+    rp.spec = spec;
+    if (spec.hops != 1 && spec.hops != 2) return fail(GACE_EINVAL, "hops = %u (1 or 2)", spec.hops);
+    if (spec.method > GACE_JOIN_GATHER) return fail(GACE_EINVAL, "method %u invalid", spec.method);
+    if (spec.key_domain == 0 || spec.key_domain > (1ull << 32))
+        return fail(GACE_EINVAL, "key_domain %llu outside 1..2^32", (unsigned long long)spec.key_domain);
+    if (spec.hops == 2 && (spec.key_domain2 == 0 || spec.key_domain2 > (1ull << 32)))
+        return fail(GACE_EINVAL, "key_domain2 %llu outside 1..2^32", (unsigned long long)spec.key_domain2);
+    if (gace_status st = build_side(ctx, spec.fact, "fact", -1, rp.side[0], rp.pool, &rp.tabs[0], nullptr, rp.work[0]))
+        return st;
+    if (gace_status st = build_side(ctx, spec.dim, "dim", spec.hops == 2 ? static_cast<int>(spec.dim_fk2_col) : -1,
+                                    rp.side[1], rp.pool, &rp.tabs[1], &rp.fk2_slot, rp.work[1]))
+        return st;
+    if (spec.hops == 2)
+        if (gace_status st = build_side(ctx, spec.dim2, "dim2", -1, rp.side[2], rp.pool, &rp.tabs[2], nullptr,
+                                        rp.work[2]))
+            return st;
+    rp.hist_dot = spec.method == GACE_JOIN_HIST_DOT;
+    if (rp.tabs[1]->nrows >= (1ull << 32) || (rp.tabs[2] && rp.tabs[2]->nrows >= (1ull << 32)))
+        return fail(GACE_EINVAL, "a histogrammed dimension has 2^32 or more rows");
+    if (rp.hist_dot && rp.tabs[0]->nrows >= (1ull << 32))
+        return fail(GACE_EINVAL, "GACE_JOIN_HIST_DOT needs a fact table below 2^32 rows");
+    rp.K = spec.key_domain;
+    rp.K2 = spec.hops == 2 ? spec.key_domain2 : 0;
+    return GACE_OK;
+}
+
+
+// Offsets of a request's data inside the input, small-output and big-output
+// regions (relative to each region).
+void place_request(ReqPlan& rp, Ws& win, Ws& wsmall, Ws& wbig) {
+    if (rp.status != GACE_OK) return;
+    if (rp.kind == GACE_REQ_PROBE) {
+        rp.args_off.clear();
+        for (Pass& ps : rp.plan.passes) {
+            rp.args_off.push_back(win.take(sizeof(ProbeArgs)));
+            ps.in_off = win.take(ps.in_bytes);
+            ps.out_off = wsmall.take(ps.out_bytes);
+        }
+    } else if (rp.kind == GACE_REQ_NDV) {
+        rp.regs_off = wsmall.take((1ull << rp.hll.p) * 4);
+    } else {
+        const int nsides = rp.spec.hops == 2 ? 3 : 2;
+        for (int i = 0; i < nsides; ++i) rp.side_off[i] = win.take(sizeof(SideArgs));
+        rp.pool_off = win.take(rp.pool.size() * 4 + 16);
+        rp.sc_off = wsmall.take(64 + 16);  // fact_pass dim_pass dim2_pass sum max_h max_w | status
+        rp.hd_off = wbig.take((rp.spec.hops == 2 ? rp.K2 : rp.K) * 4);
+        if (rp.spec.hops == 2) rp.w_off = wbig.take(rp.K * 8);
+        if (rp.hist_dot) rp.hf_off = wbig.take(rp.K * 4);
+    }
+}
+
+void shift_request(ReqPlan& rp, uint64_t in_base, uint64_t small_base, uint64_t big_base) {
+    if (rp.status != GACE_OK) return;
+    if (rp.kind == GACE_REQ_PROBE) {
+        for (uint64_t& o : rp.args_off) o += in_base;
+        for (Pass& ps : rp.plan.passes) {
+            ps.in_off += in_base;
+            ps.out_off += small_base;
+        }
+    } else if (rp.kind == GACE_REQ_NDV) {
+        rp.regs_off += small_base;
+    } else {
+        for (uint64_t& o : rp.side_off) o += in_base;
+        rp.pool_off += in_base;
+        rp.sc_off += small_base;
+        rp.hd_off += big_base;
+        rp.w_off += big_base;
+        rp.hf_off += big_base;
+    }
+}
+
+// The jobs of a request, with device pointers into the arena at dws (dws may
+// be null when only the count, units and phases are wanted).
+void emit_jobs(ReqPlan& rp, unsigned char* dws, unsigned int* batch_status, std::vector<JobRec>& jobs) {
+    if (rp.status != GACE_OK) return;
+    if (rp.kind == GACE_REQ_PROBE) {
+        for (size_t k = 0; k < rp.plan.passes.size(); ++k) {
+            const Pass& ps = rp.plan.passes[k];
+            JobRec jr;
+            jr.job.kind = kJobProbe;
+            jr.job.probe = reinterpret_cast<const ProbeArgs*>(dws + rp.args_off[k]);
+            jr.units = rp.plan.tab->nrows;
+            jr.family = "batch_probe";
+            jr.rows = jr.units;
+            jr.bytes = jr.units * ps.rowbytes;
+            jr.ops = jr.units * ps.ops_per_row;
+            jobs.push_back(jr);
+        }
+        return;
+    }
+    if (rp.kind == GACE_REQ_NDV) {
+        JobRec jr;
+        jr.job.kind = kJobHll;
+        jr.job.hll = rp.hll;
+        jr.job.hll.regs = reinterpret_cast<uint32_t*>(dws + rp.regs_off);
+        jr.job.hll.status = batch_status;
+        jr.units = rp.hll.nrows;
+        jr.family = "batch_hll";
+        jr.rows = jr.units;
+        jr.bytes = jr.units * dtype_width(static_cast<int>(rp.hll.dtype));
+        jr.ops = jr.units;
+        jobs.push_back(jr);
+        return;
+    }
+    // join: sides point at the pool, the per-request status word and the pass counters
+    unsigned long long* sc = reinterpret_cast<unsigned long long*>(dws + rp.sc_off);
+    unsigned int* jstatus = reinterpret_cast<unsigned int*>(dws + rp.sc_off + 64);
+    const bool two = rp.spec.hops == 2;
+    const int nsides = two ? 3 : 2;
+    for (int i = 0; i < nsides; ++i) {
+        rp.side[i].pool = reinterpret_cast<const uint32_t*>(dws + rp.pool_off);
+        rp.side[i].status = jstatus;
+        rp.side[i].pass_count = sc + i;
+    }
+    rp.side[0].domain = rp.K;
+    rp.side[1].domain = rp.K;
+    if (two) rp.side[2].domain = rp.K2;
+    auto side_dev = [&](int i) { return reinterpret_cast<const SideArgs*>(dws + rp.side_off[i]); };
+    uint32_t* hd = reinterpret_cast<uint32_t*>(dws + rp.hd_off);
+    unsigned long long* w = reinterpret_cast<unsigned long long*>(dws + rp.w_off);
+    uint32_t* hf = reinterpret_cast<uint32_t*>(dws + rp.hf_off);
+    auto side_job = [&](uint32_t kind, int i, uint32_t phase, uint32_t strict) {
+        JobRec jr;
+        jr.job.kind = kind;
+        jr.job.side = side_dev(i);
+        jr.job.strict = strict;
+        jr.phase = phase;
+        jr.units = rp.work[i].rows;
+        jr.family = "batch_join";
+        jr.rows = rp.work[i].rows;
+        jr.bytes = rp.work[i].rows * rp.work[i].rowbytes;
+        jr.ops = rp.work[i].rows * rp.work[i].ops_per_row;
+        return jr;
+    };
+    auto vec_job = [&](uint32_t kind, uint64_t n, uint32_t phase, uint64_t bytes_per) {
+        JobRec jr;
+        jr.job.kind = kind;
+        jr.phase = phase;
+        jr.units = n;
+        jr.family = "batch_join";
+        jr.rows = n;
+        jr.bytes = n * bytes_per;
+        jr.ops = n;
+        return jr;
+    };
+    // phase 0: the dimension histogram the others read (and the fact histogram)
+    JobRec h = side_job(kJobHist, two ? 2 : 1, 0, 1);
+    h.job.hist = hd;
+    jobs.push_back(h);
+    if (rp.hist_dot) {
+        JobRec hfj = side_job(kJobHistAgg, 0, 0, 0);
+        hfj.job.hist = hf;
+        jobs.push_back(hfj);
+    }
+    // its largest entry for the overflow check
+    JobRec mx = vec_job(kJobMax32, two ? rp.K2 : rp.K, 1, 4);
+    mx.job.weight = hd;
+    mx.job.out = sc + 4;
+    jobs.push_back(mx);
+    uint32_t last = 1;
+    const void* weight = hd;
+    if (two) {  // chain weights w[k1] += h_D2[fk2] over the filtered first dimension
+        JobRec ch = side_job(kJobChain, 1, 1, 1);
+        ch.job.weight = hd;
+        ch.job.fk2_slot = rp.fk2_slot;
+        ch.job.domain2 = rp.K2;
+        ch.job.w64 = w;
+        jobs.push_back(ch);
+        JobRec mw = vec_job(kJobMax64, rp.K, 2, 8);
+        mw.job.weight = w;
+        mw.job.out = sc + 5;
+        jobs.push_back(mw);
+        last = 2;
+        weight = w;
+    }
+    if (rp.hist_dot) {
+        JobRec d = vec_job(two ? kJobDot64 : kJobDot32, rp.K, last, two ? 12 : 8);
+        d.job.hist = hf;
+        d.job.weight = weight;
+        d.job.out = sc + 3;
+        jobs.push_back(d);
+    } else {
+        JobRec gj = side_job(two ? kJobGather64 : kJobGather32, 0, last, 0);
+        gj.job.weight = weight;
+        gj.job.out = sc + 3;
+        jobs.push_back(gj);
+    }
+}
+
+// Items of `chunk` units per job, ordered by phase; per-phase ranges.
+void make_items(const std::vector<JobRec>& jobs, uint64_t chunk, std::vector<BatchItem>& items,
+                uint32_t (&pbeg)[kPhases], uint32_t (&pcnt)[kPhases]) {
+    items.clear();
+    for (int ph = 0; ph < kPhases; ++ph) {
+        pbeg[ph] = static_cast<uint32_t>(items.size());
+        for (uint32_t j = 0; j < jobs.size(); ++j) {
+            if (jobs[j].phase != static_cast<uint32_t>(ph)) continue;
+            for (uint64_t b = 0; b < jobs[j].units; b += chunk) {
+                BatchItem it{};
+                it.job = j;
+                it.begin = b;
+                it.end = std::min(jobs[j].units, b + chunk);
+                items.push_back(it);
+            }
+        }
+        pcnt[ph] = static_cast<uint32_t>(items.size()) - pbeg[ph];
+    }
+}
+
+
+struct BatchRun {
+    std::vector<JobRec> jobs;
+    std::vector<BatchItem> items;
+    uint32_t pbeg[kPhases] = {0, 0, 0}, pcnt[kPhases] = {0, 0, 0};
+    uint64_t jobs_off = 0, items_off = 0, in_end = 0, small_base = 0, small_end = 0, end = 0;
+    uint32_t smem = 0;
+    int grid = 1;
+    uint64_t rows = 0, bytes = 0, ops = 0;
+};
+
+// Lays out the arena for `chunk`-unit items and a grid of ctas_per_sm CTAs per
+// SM (0 = as many as fit), and writes every input into pinned staging.
+gace_status build_batch(gace_ctx* ctx, std::vector<ReqPlan>& rps, uint64_t chunk, int ctas_per_sm, BatchRun& br) {
+    br = BatchRun();
+    Ws win, wsmall, wbig;
+    wsmall.take(512);  // batch status word, queue heads
+    for (ReqPlan& rp : rps) place_request(rp, win, wsmall, wbig);
+    for (ReqPlan& rp : rps) emit_jobs(rp, nullptr, nullptr, br.jobs);
+    make_items(br.jobs, chunk, br.items, br.pbeg, br.pcnt);
+    Ws main;
+    br.jobs_off = main.take(std::max<size_t>(1, br.jobs.size()) * sizeof(BatchJob));
+    br.items_off = main.take(std::max<size_t>(1, br.items.size()) * sizeof(BatchItem));
+    const uint64_t in_base = main.take(win.off);
+    br.in_end = main.off;
+    br.small_base = main.take(wsmall.off);
+    br.small_end = main.off;
+    const uint64_t big_base = main.take(wbig.off);
+    br.end = main.off;
+    for (ReqPlan& rp : rps) shift_request(rp, in_base, br.small_base, big_base);
+    if (gace_status st = ctx->ensure_ws(br.end)) return st;
+    if (gace_status st = ctx->ensure_pin(br.small_end)) return st;
+    unsigned char* pin = ctx->pin;
+    unsigned char* dws = ctx->ws;
+    unsigned int* bstatus = reinterpret_cast<unsigned int*>(dws + br.small_base);
+    // inputs: pass tables and argument copies, join sides and pools
+    br.smem = 0;
+    bool any_hll = false;
+    for (ReqPlan& rp : rps) {
+        if (rp.status != GACE_OK) continue;
+        if (rp.kind == GACE_REQ_PROBE) {
+            for (size_t k = 0; k < rp.plan.passes.size(); ++k) {
+                Pass& ps = rp.plan.passes[k];
+                stage_pass(ps, pin, dws, bstatus);
+                memcpy(pin + rp.args_off[k], &ps.args, sizeof(ProbeArgs));
+                br.smem = std::max(br.smem, ps.args.smem_bytes);
+            }
+        } else if (rp.kind == GACE_REQ_NDV) {
+            any_hll = true;
+        }
+    }
+    if (any_hll) br.smem = std::max(br.smem, kHllSmem);
+    br.jobs.clear();
+    for (ReqPlan& rp : rps) emit_jobs(rp, dws, bstatus, br.jobs);
+    for (ReqPlan& rp : rps) {
+        if (rp.status != GACE_OK || rp.kind != GACE_REQ_JOIN) continue;
+        const int nsides = rp.spec.hops == 2 ? 3 : 2;
+        for (int i = 0; i < nsides; ++i) memcpy(pin + rp.side_off[i], &rp.side[i], sizeof(SideArgs));
+        if (!rp.pool.empty()) memcpy(pin + rp.pool_off, rp.pool.data(), rp.pool.size() * 4);
+    }
+    std::vector<BatchJob> jobs(br.jobs.size());
+    for (size_t j = 0; j < br.jobs.size(); ++j) {
+        jobs[j] = br.jobs[j].job;
+        br.rows += br.jobs[j].rows;
+        br.bytes += br.jobs[j].bytes;
+        br.ops += br.jobs[j].ops;
+    }
+    if (!jobs.empty()) memcpy(pin + br.jobs_off, jobs.data(), jobs.size() * sizeof(BatchJob));
+    if (!br.items.empty()) memcpy(pin + br.items_off, br.items.data(), br.items.size() * sizeof(BatchItem));
+    const int occ = batch_occupancy(br.smem);
+    if (occ < 1) return fail(GACE_ECUDA, "batch kernel cannot be resident with %u bytes of shared memory", br.smem);
+    const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ) : occ;
+    br.grid = std::max(1, ctx->sms * per_sm);
+    return GACE_OK;
+}
+
+// Upload, clear, one launch per phase, read-back: on stream s.
+cudaError_t enqueue_batch(gace_ctx* ctx, const BatchRun& br, cudaStream_t s) {
+    unsigned char* dws = ctx->ws;
+    unsigned char* pin = ctx->pin;
+    cudaError_t e = cudaMemcpyAsync(dws, pin, br.in_end, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(dws + br.small_base, 0, br.end - br.small_base, s)) != cudaSuccess) return e;
+    const BatchItem* items = reinterpret_cast<const BatchItem*>(dws + br.items_off);
+    const BatchJob* jobs = reinterpret_cast<const BatchJob*>(dws + br.jobs_off);
+    unsigned int* heads = reinterpret_cast<unsigned int*>(dws + br.small_base + 256);
+    for (int ph = 0; ph < kPhases; ++ph) {
+        if (!br.pcnt[ph]) continue;
+        if ((e = batch_launch(items + br.pbeg[ph], br.pcnt[ph], jobs, heads + ph, br.grid, br.smem, s)) !=
+            cudaSuccess)
+            return e;
+    }
+    return cudaMemcpyAsync(pin + br.small_base, dws + br.small_base, br.small_end - br.small_base,
+                           cudaMemcpyDeviceToHost, s);
+}
+
+// Runs a built batch: through the cached graph when the shape repeats (or a
+// new capture), or eagerly; waits for it.
+gace_status exec_batch(gace_ctx* ctx, const BatchRun& br, bool use_graph) {
+    std::vector<uint64_t> key = {reinterpret_cast<uint64_t>(ctx->ws), reinterpret_cast<uint64_t>(ctx->pin),
+                                 br.jobs_off, br.items_off, br.in_end, br.small_base, br.small_end, br.end,
+                                 br.smem, static_cast<uint64_t>(br.grid)};
+    for (int ph = 0; ph < kPhases; ++ph) {
+        key.push_back(br.pbeg[ph]);
+        key.push_back(br.pcnt[ph]);
+    }
+    auto launch = [&]() -> cudaError_t {
+        if (!use_graph) return enqueue_batch(ctx, br, ctx->stream);
+        if (!ctx->graph_exec || ctx->graph_key != key) {
+            if (ctx->graph_exec) {
+                cudaGraphExecDestroy(ctx->graph_exec);
+                ctx->graph_exec = nullptr;
+            }
+            if (!ctx->capture_stream) {
+                cudaError_t e = cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking);
+                if (e != cudaSuccess) return e;
+            }
+            cudaError_t e = cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return e;
+            cudaError_t ee = enqueue_batch(ctx, br, ctx->capture_stream);
+            cudaGraph_t graph = nullptr;
+            e = cudaStreamEndCapture(ctx->capture_stream, &graph);
+            if (ee != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                return ee;
+            }
+            if (e != cudaSuccess) return e;
+            e = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                ctx->graph_exec = nullptr;
+                return e;
+            }
+            ctx->graph_key = key;
+        }
+        return cudaGraphLaunch(ctx->graph_exec, ctx->stream);
+    };
+    CK(ctx->traced("batch", br.rows, br.bytes, br.ops, launch));
+    ctx->stats["batch_kernel"].launches += (br.pcnt[0] > 0) + (br.pcnt[1] > 0) + (br.pcnt[2] > 0);
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->collect();
+    return GACE_OK;
+}
+
+// Outputs of every request from the read-back counters.
+void finish_batch(gace_ctx* ctx, std::vector<ReqPlan>& rps, const BatchRun& br) {
+    const unsigned char* pin = ctx->pin;
+    const unsigned int bst = *reinterpret_cast<const unsigned int*>(pin + br.small_base);
+    const unsigned __int128 lim = static_cast<unsigned __int128>(1) << 63;
+    for (ReqPlan& rp : rps) {
+        if (rp.status != GACE_OK) continue;
+        if (rp.kind != GACE_REQ_JOIN && bst) {
+            rp.status = read_status(ctx, bst);
+            rp.error = gace_last_error();
+            continue;
+        }
+        if (rp.kind == GACE_REQ_PROBE) {
+            std::vector<const unsigned long long*> outs;
+            for (const Pass& ps : rp.plan.passes)
+                outs.push_back(reinterpret_cast<const unsigned long long*>(pin + ps.out_off));
+            assemble_probe(rp.plan, rp.pr, outs);
+        } else if (rp.kind == GACE_REQ_NDV) {
+            const uint64_t m = 1ull << rp.hll.p;
+            const uint32_t* r32 = reinterpret_cast<const uint32_t*>(pin + rp.regs_off);
+            std::vector<uint8_t> regs(m);
+            for (uint64_t j = 0; j < m; ++j) regs[j] = static_cast<uint8_t>(r32[j]);
+            if (rp.q->registers_out) memcpy(rp.q->registers_out, regs.data(), m);
+            if (rp.q->estimate_out) *rp.q->estimate_out = hll_estimate_host(regs.data(), rp.hll.p);
+        } else {
+            const unsigned long long* h = reinterpret_cast<const unsigned long long*>(pin + rp.sc_off);
+            const unsigned int st = *reinterpret_cast<const unsigned int*>(pin + rp.sc_off + 64);
+            gace_status err = GACE_OK;
+            if (st & kStatusKeyDomain)
+                err = fail(GACE_EINVAL, "a filtered dimension row has a key outside its domain");
+            else if (rp.spec.hops == 1 && static_cast<unsigned __int128>(h[0]) * h[4] >= lim)
+                err = fail(GACE_EOVERFLOW, "fact_rows * max h_D >= 2^63");
+            else if (rp.spec.hops == 2 && static_cast<unsigned __int128>(h[1]) * h[4] >= lim)
+                err = fail(GACE_EOVERFLOW, "dim_rows * max h_D2 >= 2^63");
+            else if (rp.spec.hops == 2 && static_cast<unsigned __int128>(h[0]) * h[5] >= lim)
+                err = fail(GACE_EOVERFLOW, "fact_rows * max w >= 2^63");
+            if (err != GACE_OK) {
+                rp.status = err;
+                rp.error = gace_last_error();
+                continue;
+            }
+            gace_join_result& out = *rp.q->join_out;
+            out.card = static_cast<int64_t>(h[3]);
+            out.fact_rows = h[0];
+            out.dim_rows = h[1];
+            out.dim2_rows = rp.spec.hops == 2 ? h[2] : 0;
+        }
+    }
+}
+
+gace_status compile_all(gace_ctx* ctx, const gace_request* reqs, uint32_t n, std::vector<ReqPlan>& rps) {
+    rps.assign(n, ReqPlan());
+    for (uint32_t i = 0; i < n; ++i) {
+        rps[i].status = compile_request(ctx, reqs[i], rps[i]);
+        if (rps[i].status != GACE_OK) rps[i].error = gace_last_error();
+    }
+    return GACE_OK;
+}
+
+std::pair<int, int> shape_key(const std::vector<ReqPlan>& rps) {
+    uint64_t njobs = 0, units = 0;
+    for (const ReqPlan& rp : rps) {
+        if (rp.status != GACE_OK) continue;
+        if (rp.kind == GACE_REQ_PROBE) {
+            njobs += rp.plan.passes.size();
+            units += rp.plan.passes.size() * rp.plan.tab->nrows;
+        } else if (rp.kind == GACE_REQ_NDV) {
+            njobs += 1;
+            units += rp.hll.nrows;
+        } else {
+            njobs += 4;
+            units += rp.work[0].rows + rp.work[1].rows + rp.work[2].rows;
+        }
+    }
+    return {log2_bucket(njobs), log2_bucket(units)};
+}
+
+gace_status report(const std::vector<ReqPlan>& rps, gace_status* statuses) {
+    gace_status first = GACE_OK;
+    std::string msg;
+    for (size_t i = 0; i < rps.size(); ++i) {
+        if (statuses) statuses[i] = rps[i].status;
+        if (first == GACE_OK && rps[i].status != GACE_OK) {
+            first = rps[i].status;
+            msg = "request " + std::to_string(i) + ": " + rps[i].error;
+        }
+    }
+    if (first != GACE_OK) set_last_error_message(msg.c_str());
+    return first;
+}
+
+}  // namespace
+}  // namespace host
+}  // namespace gace
+
+using namespace gace::host;
+
+namespace {
+
+gace_status batch_prologue(gace_ctx* ctx, const gace_request* reqs, uint32_t n) {
+    if (gace_status s = check_ctx(ctx)) return s;
+    if (n && !reqs) return fail(GACE_EINVAL, "reqs is NULL");
+    if (!ctx->batch_ready) {
+        cudaError_t e = batch_configure(ctx->smem_optin);
+        if (e != cudaSuccess) return cuda_fail(e, "batch kernel attributes");
+        ctx->batch_ready = true;
+    }
+    return GACE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gace_status gace_run_batch(gace_ctx* ctx, const gace_request* reqs, uint32_t n, gace_status* statuses) {
+    if (!ctx) return fail(GACE_EINVAL, "context is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    if (gace_status s = batch_prologue(ctx, reqs, n)) return s;
+    std::vector<ReqPlan> rps;
+    compile_all(ctx, reqs, n, rps);
+    uint64_t chunk = kDefaultChunk;
+    int per_sm = 0;
+    const auto it = ctx->tune.find(shape_key(rps));
+    if (it != ctx->tune.end()) {
+        chunk = it->second.chunk;
+        per_sm = it->second.ctas_per_sm;
+    }
+    BatchRun br;
+    if (gace_status st = build_batch(ctx, rps, chunk, per_sm, br)) return st;
+    if (gace_status st = exec_batch(ctx, br, true)) return st;
+    finish_batch(ctx, rps, br);
+    return report(rps, statuses);
+}
+
+gace_status gace_tune_batch(gace_ctx* ctx, const gace_request* reqs, uint32_t n) {
+    if (!ctx) return fail(GACE_EINVAL, "context is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    if (gace_status s = batch_prologue(ctx, reqs, n)) return s;
+    std::vector<ReqPlan> rps;
+    compile_all(ctx, reqs, n, rps);
+    const std::pair<int, int> key = shape_key(rps);
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    gace_ctx::TuneEntry best;
+    best.ms = std::numeric_limits<double>::infinity();
+    gace_status rc = GACE_OK;
+    for (uint64_t chunk = 1ull << 17; chunk <= (1ull << 23) && rc == GACE_OK; chunk <<= 2) {
+        for (int per_sm : {1, 2, 0}) {
+            BatchRun br;
+            if ((rc = build_batch(ctx, rps, chunk, per_sm, br)) != GACE_OK) break;
+            double ms = std::numeric_limits<double>::infinity();
+            for (int rep = 0; rep < 2 && rc == GACE_OK; ++rep) {
+                cudaEventRecord(a, ctx->stream);
+                cudaError_t e = enqueue_batch(ctx, br, ctx->stream);
+                cudaEventRecord(b, ctx->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(b);
+                float t = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+                if (e != cudaSuccess) rc = cuda_fail(e, "tuning run");
+                ms = std::min(ms, static_cast<double>(t));
+            }
+            if (rc == GACE_OK && ms < best.ms) {
+                best.ms = ms;
+                best.chunk = chunk;
+                best.ctas_per_sm = per_sm;
+            }
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (rc != GACE_OK) return rc;
+    ctx->tune[key] = best;
+    // leave the requests' outputs from a run with the chosen configuration
+    BatchRun br;
+    if (gace_status st = build_batch(ctx, rps, best.chunk, best.ctas_per_sm, br)) return st;
+    if (gace_status st = exec_batch(ctx, br, false)) return st;
+    finish_batch(ctx, rps, br);
+    return report(rps, nullptr);
+}
+
+gace_status gace_tune_save(gace_ctx* ctx, const char* path) {
+    if (gace_status s = check_ctx(ctx)) return s;
+    if (!path) return fail(GACE_EINVAL, "path is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    std::ofstream f(path);
+    if (!f) return fail(GACE_EINVAL, "cannot write %s", path);
+    for (const auto& kv : ctx->tune)
+        f << "{\"jobs_log2\": " << kv.first.first << ", \"units_log2\": " << kv.first.second
+          << ", \"chunk\": " << kv.second.chunk << ", \"ctas_per_sm\": " << kv.second.ctas_per_sm
+          << ", \"ms\": " << kv.second.ms << "}\n";
+    return f ? GACE_OK : fail(GACE_EINVAL, "cannot write %s", path);
+}
+
+gace_status gace_tune_load(gace_ctx* ctx, const char* path) {
+    if (gace_status s = check_ctx(ctx)) return s;
+    if (!path) return fail(GACE_EINVAL, "path is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    std::ifstream f(path);
+    if (!f) return fail(GACE_ENOTFOUND, "cannot read %s", path);
+    std::string line;
+    while (std::getline(f, line)) {
+        int jl = 0, ul = 0, per_sm = 0;
+        unsigned long long chunk = 0;
+        double ms = 0;
+        if (sscanf(line.c_str(), " {\"jobs_log2\": %d, \"units_log2\": %d, \"chunk\": %llu, \"ctas_per_sm\": %d, \"ms\": %lf",
+                   &jl, &ul, &chunk, &per_sm, &ms) != 5)
+            continue;
+        if (chunk < 128 || (chunk & (chunk - 1))) continue;  // chunks are powers of two >= 128
+        gace_ctx::TuneEntry e;
+        e.chunk = chunk;
+        e.ctas_per_sm = per_sm;
+        e.ms = ms;
+        ctx->tune[{jl, ul}] = e;
+    }
+    return GACE_OK;
+}
+
+}  // extern "C"

@@ -886,6 +886,8 @@ gace_status gace_destroy(gace_ctx* ctx) {
         if (ctx->d_status) cudaFree(ctx->d_status);
         ctx->collect();
         for (cudaEvent_t e : ctx->ev_free) cudaEventDestroy(e);
+        if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+        if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
         if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     }
     delete ctx;

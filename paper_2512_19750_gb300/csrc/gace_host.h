@@ -148,6 +148,18 @@ struct gace_ctx {
         pending.clear();
     }
 
+    // batched form: tuning table, capture stream and the last batch's graph
+    struct TuneEntry {
+        uint64_t chunk = 0;
+        int ctas_per_sm = 0;
+        double ms = 0.0;
+    };
+    std::map<std::pair<int, int>, TuneEntry> tune;  // (log2 jobs, log2 rows) -> best
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<uint64_t> graph_key;
+    bool batch_ready = false;
+
     bool fits(uint64_t extra) const { return budget == 0 || used + extra <= budget; }
 
     gace_status ensure_ws(uint64_t bytes) {

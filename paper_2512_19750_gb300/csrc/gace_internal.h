@@ -166,4 +166,49 @@ cudaError_t dot_launch(const uint32_t* a, const void* b, int b64, uint64_t n,
 cudaError_t max_launch(const void* a, int a64, uint64_t n, unsigned long long* mx, int sms,
                        cudaStream_t s);
 
+// ---------------------------------------------------------------- batch
+// A batch is a set of jobs (one probe pass, one HLL sketch, one join side or
+// histogram reduction each) cut into items of rows (or histogram elements)
+// that a persistent kernel takes from a device work queue.
+enum BatchJobKind : uint32_t {
+    kJobProbe = 0,
+    kJobHll = 1,
+    kJobHist = 2,      // h[key] += 1 over filtered rows
+    kJobHistAgg = 3,   // the same, equal keys of a warp combined first
+    kJobGather32 = 4,  // out += h[key] over filtered rows
+    kJobGather64 = 5,  // out += w[key]
+    kJobChain = 6,     // w[key] += h2[fk2]
+    kJobMax32 = 7,     // out = max h[i]
+    kJobMax64 = 8,
+    kJobDot32 = 9,     // out += a[i] * b32[i]
+    kJobDot64 = 10     // out += a[i] * b64[i]
+};
+
+struct BatchJob {
+    uint32_t kind;
+    uint32_t strict;            // join histograms: key outside the domain is an error
+    uint32_t fk2_slot;          // chain
+    uint32_t pad;
+    uint64_t domain2;           // chain
+    const ProbeArgs* probe;     // kJobProbe (device copy, wide layout)
+    const SideArgs* side;       // join sides (device copy)
+    HllArgs hll;                // kJobHll
+    uint32_t* hist;             // histogram built (Hist*), or a of a dot product
+    const void* weight;         // weights read (gather, chain), b of a dot, input of a max
+    unsigned long long* out;    // sum (gather, dot) or maximum
+    unsigned long long* w64;    // chain weights
+};
+
+struct BatchItem {
+    uint32_t job;
+    uint32_t pad;
+    uint64_t begin;             // rows (elements for max and dot); a multiple of 128
+    uint64_t end;
+};
+
+cudaError_t batch_configure(int smem_optin);
+int batch_occupancy(uint32_t smem_bytes);
+cudaError_t batch_launch(const BatchItem* items, uint32_t nitems, const BatchJob* jobs, unsigned int* head,
+                         int grid, uint32_t smem_bytes, cudaStream_t s);
+
 }  // namespace gace

@@ -1,0 +1,188 @@
+"""GPU tests of the batched form (gace_run_batch): every request of a mixed
+batch gives exactly what its synchronous call gives (which the other GPU tests
+pin to the oracle), a sample of them is checked against the oracle directly,
+a replayed graph with new contents stays exact, a bad request fails alone,
+and tuning changes nothing but speed."""
+import os
+
+import numpy as np
+import pytest
+
+from parity import check_probe, close, host_columns
+from workloads import (BLOCKS, FULL, I32, RANGE, ROWS, JoinSide, Sample, Table, Term, make_batched,
+                       make_join, make_predicates)
+
+pytestmark = pytest.mark.gpu
+
+
+def _to_requests(g, tids, tables, reqs):
+    out = []
+    for r in reqs:
+        if r["kind"] == "probe":
+            t = tables[r["table"]]
+            out.append(g.ProbeRequest(tids[r["table"]], r["preds"], r["samples"], t.dtypes, marginals=True))
+        elif r["kind"] == "ndv":
+            out.append(g.NdvRequest(tids[r["table"]], r["col"], r["p"], r["seed"]))
+        else:
+            f, d = tables[r["fact"]], tables[r["dim"]]
+            out.append(g.JoinRequest(g.JoinSideSpec(tids[r["fact"]], 0, r["fact_terms"], f.dtypes),
+                                     g.JoinSideSpec(tids[r["dim"]], 0, r["dim_terms"], d.dtypes),
+                                     r["key_domain"]))
+    return out
+
+
+def _check_against_sync(g, gctx, tids, tables, reqs, breqs):
+    for r, q in zip(reqs, breqs):
+        if r["kind"] == "probe":
+            t = tables[r["table"]]
+            res, marg = g.gace_probe_batch(gctx, tids[r["table"]], r["preds"], r["samples"], t.dtypes, marginals=True)
+            for f in ("match", "sample_rows", "sel"):
+                assert np.array_equal(q.results[f], res[f]), (r, f)
+            assert np.array_equal(q.results["pcs"], res["pcs"], equal_nan=True)
+            assert np.array_equal(q.marginals, marg)
+        elif r["kind"] == "ndv":
+            regs, est = g.gace_ndv(gctx, tids[r["table"]], r["col"], r["p"], r["seed"])
+            assert np.array_equal(q.registers, regs) and q.estimate == est
+        else:
+            f, d = tables[r["fact"]], tables[r["dim"]]
+            ref = g.gace_join_card(gctx, g.JoinSideSpec(tids[r["fact"]], 0, r["fact_terms"], f.dtypes),
+                                   g.JoinSideSpec(tids[r["dim"]], 0, r["dim_terms"], d.dtypes), r["key_domain"])
+            assert q.result == ref, (r, q.result, ref)
+
+
+@pytest.fixture(scope="module")
+def batched(g, gctx, cuda):
+    tables, reqs = make_batched(ntables=12, min_rows=1000, max_rows=400_000, nprobes=150, seed=11, device=cuda)
+    tids = [g.gace_load_columns(gctx, t.columns) for t in tables]
+    yield tables, reqs, tids
+    for t in tids:
+        g.gace_unload(gctx, t)
+
+
+def test_mixed_batch_equals_synchronous_calls(g, gctx, batched):
+    tables, reqs, tids = batched
+    breqs = _to_requests(g, tids, tables, reqs)
+    st = g.gace_run_batch(gctx, breqs)
+    assert st == [0] * len(reqs)
+    _check_against_sync(g, gctx, tids, tables, reqs, breqs)
+    # replay: same shape, so the captured graph runs again with the same result
+    breqs2 = _to_requests(g, tids, tables, reqs)
+    g.gace_run_batch(gctx, breqs2)
+    for a, b in zip(breqs, breqs2):
+        if isinstance(a, g.ProbeRequest):
+            assert np.array_equal(a.results["match"], b.results["match"])
+        elif isinstance(a, g.NdvRequest):
+            assert np.array_equal(a.registers, b.registers)
+        else:
+            assert a.result == b.result
+
+
+def test_batch_against_oracle(g, gctx, orc, batched):
+    tables, reqs, tids = batched
+    pick = [r for r in reqs if r["kind"] != "join"][:25] + [r for r in reqs if r["kind"] == "join"][:4]
+    breqs = _to_requests(g, tids, tables, pick)
+    g.gace_run_batch(gctx, breqs)
+    for r, q in zip(pick, breqs):
+        if r["kind"] == "probe":
+            t = tables[r["table"]]
+            ref = orc.probe(host_columns(t), t.dtypes, r["preds"], r["samples"][0])
+            assert np.array_equal(q.results["match"][0], ref.counts)
+            assert int(q.results["sample_rows"][0][0]) == ref.n_sample
+            assert np.array_equal(q.marginals[0], ref.marginals)
+        elif r["kind"] == "ndv":
+            t = tables[r["table"]]
+            regs = orc.hll_registers(t.columns[r["col"]].cpu(), t.dtypes[r["col"]], r["p"], r["seed"])
+            assert np.array_equal(q.registers, regs)
+            assert close(q.estimate, orc.hll_estimate(regs, r["p"]))
+        else:
+            f, d = tables[r["fact"]], tables[r["dim"]]
+            fh = Table("f", host_columns(f), f.dtypes)
+            dh = Table("d", host_columns(d), d.dtypes)
+            rc, card, fp, dp = orc.join_card(JoinSide(fh, 0, r["fact_terms"]), JoinSide(dh, 0, r["dim_terms"]),
+                                             r["key_domain"])
+            assert rc == 0 and q.result["card"] == card and q.result["fact_rows"] == fp
+
+
+def test_graph_replay_with_new_contents(g, gctx, batched):
+    """Two batches of the same shape but different constants: the second
+    replays the first's graph with new staging contents."""
+    tables, reqs, tids = batched
+    probes = [r for r in reqs if r["kind"] == "probe"][:40]
+    moved = []
+    for r in probes:
+        t = tables[r["table"]]
+        preds = make_predicates(t, 1, len(r["preds"][0]), len(r["preds"][0]), seed=hash(str(r)) % 10000)
+        moved.append(dict(r, preds=preds))
+    for batch in (probes, moved, probes):
+        breqs = _to_requests(g, tids, tables, batch)
+        g.gace_run_batch(gctx, breqs)
+        _check_against_sync(g, gctx, tids, tables, batch, breqs)
+
+
+def test_joins_every_method_and_chain(g, gctx, orc, cuda):
+    f, d, d2 = make_join(n_fact=700_001, n_dim=50_000, n_dim2=5000, seed=5, device=cuda)
+    fid, did, d2id = (g.gace_load_columns(gctx, t.columns) for t in (f, d, d2))
+    try:
+        ft, dt, d2t = [Term(1, RANGE, 0, 300)], [Term(2, RANGE, 100, 900)], [Term(1, RANGE, 0, 500)]
+        F = g.JoinSideSpec(fid, 0, ft, f.dtypes)
+        D = g.JoinSideSpec(did, 0, dt, d.dtypes)
+        D2 = g.JoinSideSpec(d2id, 0, d2t, d2.dtypes)
+        breqs = []
+        for method in (0, 1, 2):
+            breqs.append(g.JoinRequest(F, D, 50_000, method=method))
+            breqs.append(g.JoinRequest(F, D, 50_000, D2, 5000, 3, method=method))
+        assert g.gace_run_batch(gctx, breqs) == [0] * len(breqs)
+        for k, q in enumerate(breqs):
+            if k % 2 == 0:
+                ref = g.gace_join_card(gctx, F, D, 50_000)
+            else:
+                ref = g.gace_join_card(gctx, F, D, 50_000, D2, 5000, 3)
+            assert q.result == ref
+        fh, dh, d2h = (Table(t.name, host_columns(t), t.dtypes) for t in (f, d, d2))
+        rc, card, *_ = orc.chain_card(JoinSide(fh, 0, ft), JoinSide(dh, 0, dt), 3, JoinSide(d2h, 0, d2t), 50_000, 5000)
+        assert rc == 0 and breqs[1].result["card"] == card
+    finally:
+        for t in (fid, did, d2id):
+            g.gace_unload(gctx, t)
+
+
+def test_bad_request_fails_alone(g, gctx, batched):
+    tables, reqs, tids = batched
+    good = [r for r in reqs if r["kind"] == "probe"][:3]
+    breqs = _to_requests(g, tids, tables, good)
+    bad = g.ProbeRequest(tids[0], [[Term(99, RANGE, 0, 1)]], [Sample(FULL)], tables[0].dtypes)
+    missing = g.NdvRequest(12345, 0, 12, 1)
+    st = g.gace_run_batch(gctx, [breqs[0], bad, breqs[1], missing, breqs[2]], raise_on_error=False)
+    assert st[0] == st[2] == st[4] == 0 and st[1] == 1 and st[3] == 6
+    _check_against_sync(g, gctx, tids, tables, good, breqs)
+
+
+def test_tuning_changes_only_speed(g, gctx, batched, tmp_path):
+    tables, reqs, tids = batched
+    sub = reqs[:60]
+    g.gace_tune_batch(gctx, _to_requests(g, tids, tables, sub))
+    path = str(tmp_path / "tune.jsonl")
+    g.gace_tune_save(gctx, path)
+    assert os.path.getsize(path) > 0
+    ctx2 = g.gace_create(0)
+    try:
+        g.gace_tune_load(ctx2, path)
+        tids2 = [g.gace_load_columns(ctx2, t.columns, borrow=True) for t in tables]
+        breqs = _to_requests(g, tids2, tables, sub)
+        g.gace_run_batch(ctx2, breqs)
+        _check_against_sync(g, ctx2, tids2, tables, sub, breqs)
+    finally:
+        g.gace_destroy(ctx2)
+
+
+def test_empty_batch_and_empty_tables(g, gctx, cuda):
+    assert g.gace_run_batch(gctx, []) == []
+    import torch
+    tid = g.gace_load_columns(gctx, [torch.zeros(0, dtype=torch.int32, device=cuda)])
+    try:
+        q = [g.ProbeRequest(tid, [[Term(0, RANGE, 0, 5)]], [Sample(FULL), Sample(ROWS, 0.5, 1)], [I32]),
+             g.NdvRequest(tid, 0, 10, 3)]
+        assert g.gace_run_batch(gctx, q) == [0, 0]
+        assert not q[0].results["match"].any() and not q[1].registers.any() and q[1].estimate == 0.0
+    finally:
+        g.gace_unload(gctx, tid)

@@ -212,3 +212,61 @@ def make_predicates(table: Table, npreds: int, min_terms: int, max_terms: int,
                 pred.append(Term(c, IN, values=tuple(int(v) for v in vals)))
         preds.append(pred)
     return preds
+
+
+# ----------------------------------------------------------------- batched workload
+
+def make_batched(ntables: int = 256, min_rows: int = 10_000, max_rows: int = 50_000_000,
+                 nprobes: int = 4096, seed: int = 1004, device="cpu", key_domain: int = 1 << 15):
+    """Many tables and a mixed request list for the batched form.
+
+    Tables: rows log-uniform in [min_rows, max_rows]; 4-8 columns; column 0 an
+    int32 join key Zipf(s) over `key_domain` values, the others int32 Zipf(s)
+    over 2^20 values or float32 N(0,1), half and half; s uniform in [0.8, 1.5]
+    per table.  Requests: 70 % predicate probes of 1-4 terms (50 % full scan,
+    30 % a 1 % row sample, 20 % a 1 % sample of 4096-row blocks), 20 % HLL
+    sketches (p = 12 or 14), 10 % joins between random table pairs on their
+    key columns with a RANGE filter on each side.  Returns (tables, requests),
+    each request a dict of plain data."""
+    rng = np.random.default_rng(seed)
+    g = _gen(seed, device)
+    tables = []
+    for t in range(ntables):
+        n = int(math.exp(rng.uniform(math.log(min_rows), math.log(max_rows))))
+        ncols = int(rng.integers(4, 9))
+        s = float(rng.uniform(0.8, 1.5))
+        cols = [zipf_column(n, s, key_domain, g, device)]
+        dtypes, domains = [I32], [key_domain]
+        for _ in range(ncols - 1):
+            if rng.random() < 0.5:
+                cols.append(zipf_column(n, s, 1 << 20, g, device))
+                dtypes.append(I32)
+                domains.append(1 << 20)
+            else:
+                cols.append(normal_column(n, g, device))
+                dtypes.append(F32)
+                domains.append(8.0)
+        tables.append(Table(f"t{t}", cols, dtypes, domains))
+    from .spec import BLOCKS, FULL, ROWS, Sample
+    requests = []
+    for i in range(nprobes):
+        u = rng.random()
+        t = int(rng.integers(0, ntables))
+        if u < 0.7:
+            preds = make_predicates(tables[t], 1, 1, 4, seed=seed * 1000 + i)
+            v = rng.random()
+            smp = Sample(FULL) if v < 0.5 else (Sample(ROWS, 0.01, 42) if v < 0.8 else Sample(BLOCKS, 0.01, 42, 4096))
+            requests.append({"kind": "probe", "table": t, "preds": preds, "samples": [smp]})
+        elif u < 0.9:
+            requests.append({"kind": "ndv", "table": t, "col": int(rng.integers(0, len(tables[t].columns))),
+                             "p": 12 if rng.random() < 0.5 else 14, "seed": 42})
+        else:
+            d = int(rng.integers(0, ntables))
+            wf, wd = int(rng.integers(1, 1 << 20)), int(rng.integers(1, 1 << 20))
+            fcol = [c for c in range(1, len(tables[t].columns)) if tables[t].dtypes[c] == I32]
+            dcol = [c for c in range(1, len(tables[d].columns)) if tables[d].dtypes[c] == I32]
+            fterms = [Term(fcol[0], RANGE, 0, wf)] if fcol else []
+            dterms = [Term(dcol[0], RANGE, 0, wd)] if dcol else []
+            requests.append({"kind": "join", "fact": t, "dim": d, "fact_terms": fterms, "dim_terms": dterms,
+                             "key_domain": key_domain})
+    return tables, requests
