@@ -136,7 +136,12 @@ __global__ void __launch_bounds__(kThreads) k_batch(const BatchItem* __restrict_
 }  // namespace
 
 cudaError_t batch_configure(int smem_optin) {
-    return cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+    // the kernel's own static shared memory counts against the opt-in limit
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_batch);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem_optin - static_cast<int>(fa.sharedSizeBytes));
 }
 
 int batch_occupancy(uint32_t smem_bytes) {
