@@ -341,6 +341,74 @@ gace_status gace_tune_batch(gace_ctx* ctx, const gace_request* reqs, uint32_t n)
 gace_status gace_tune_save(gace_ctx* ctx, const char* path);
 gace_status gace_tune_load(gace_ctx* ctx, const char* path);
 
+/* ------------------------------------------------------------ served form */
+
+/*
+ * Serving: requests arrive one by one (the Risky Gate's invocations while
+ * queries are planned, Section III-A) and are answered with continuous
+ * batching.  gace_submit copies a request's inputs, checks and compiles it
+ * (as a batch would) and queues it.  A scheduler thread owns a device arena
+ * for the state of requests in flight; a queued request is admitted, in
+ * arrival order, once its state fits in the arena and fewer than
+ * max_inflight requests are in flight (admission by memory).  Each
+ * scheduling step is one persistent launch of the batch kernel over up to
+ * step_rows units of chunks taken round-robin from every request in flight,
+ * so a small probe that arrives while a long scan is on the GPU is answered
+ * after the next step, not after the scan.  Steps are issued back to back,
+ * two in flight, each with one upload, one scatter of the newly admitted
+ * requests' inputs, the batch launch, one gather of the finished requests'
+ * counters and one read-back.  A request completes when its last chunk has
+ * run; its results are identical to the synchronous call's.  Results of
+ * NDV requests are kept on the host as a sketch cache (LRU) that answers
+ * later requests for the same table, column, p and seed at submission.
+ * gace_unload forgets a table's sketches and fails with GACE_EBUSY while
+ * requests on that table are queued or in flight.
+ */
+typedef struct {
+    uint64_t arena_bytes;   /* device bytes for the state of requests in flight; 0 = 1 GiB */
+    uint32_t max_inflight;  /* requests admitted at once; 0 = 4096 */
+    int32_t sketch_cache;   /* NDV results kept for reuse (entries); 0 = 1024, < 0 = no cache */
+    uint64_t step_rows;     /* units (rows) per scheduling step; 0 = 2^27 */
+    uint64_t chunk_rows;    /* rows per chunk, rounded up to a multiple of 128; 0 = 2^18 */
+} gace_serve_config;
+
+/* Starts the scheduler (cfg may be NULL: defaults); its arena counts against
+ * the context's HBM budget.  GACE_EBUSY when it is already running: stop it
+ * first to change the configuration. */
+gace_status gace_serve_start(gace_ctx* ctx, const gace_serve_config* cfg);
+
+/* Stops the scheduler after every queued and in-flight request has finished,
+ * and frees its arena.  A no-op when it is not running. */
+gace_status gace_serve_stop(gace_ctx* ctx);
+
+/* Queues a request and returns its ticket.  Its inputs are copied; its output
+ * pointers must stay valid until gace_poll reports completion.  Argument
+ * errors (the checks of the synchronous call) are returned here and no ticket
+ * is made; GACE_ENOMEM when the request's state exceeds the whole arena.
+ * Starts the scheduler with defaults when it is not running. */
+gace_status gace_submit(gace_ctx* ctx, const gace_request* req, uint64_t* ticket_out);
+
+/* Waits up to timeout_us for a request: GACE_OK when it has completed (its
+ * outputs are written; the ticket is then forgotten), GACE_EPENDING if it has
+ * not yet, its error status if it failed (also forgotten), GACE_ENOTFOUND for
+ * an unknown ticket. */
+gace_status gace_poll(gace_ctx* ctx, uint64_t ticket, uint64_t timeout_us);
+
+/*
+ * Open-loop load driver: submits reqs[i] at arrival_ns[i] (nanoseconds from
+ * the start of the call, non-decreasing) from the calling thread and records
+ * in done_ns[i] the time, on the same clock, at which its outputs were
+ * written.  mode 0 goes through the served form (starting it with defaults
+ * if needed); mode 1 is the plain path for comparison: one synchronous call
+ * per request (gace_probe_batch, gace_ndv or gace_join_card), in arrival
+ * order, each starting when both its arrival time and the previous call have
+ * passed.  statuses (may be NULL) receives each request's status; the return
+ * value is GACE_OK when every request succeeded, else the first failing
+ * request's status.
+ */
+gace_status gace_serve_replay(gace_ctx* ctx, const gace_request* reqs, uint32_t n, const uint64_t* arrival_ns,
+                              uint32_t mode, uint64_t* done_ns, gace_status* statuses);
+
 /*
  * Kernel statistics of a context (tracing; the paper decomposes probe time
  * into transfer, kernel and reduction phases, Section IV-B).  Every launch is

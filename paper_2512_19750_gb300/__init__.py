@@ -12,7 +12,9 @@ import ctypes as C
 import numpy as np
 
 from . import _capi
-from ._capi import (GACE_BLOCKS, GACE_BORROW, GACE_COPY, GACE_EQ, GACE_F32, GACE_FULL, GACE_I32,
+from ._capi import (GACE_BLOCKS, GACE_BORROW, GACE_COPY, GACE_EBUSY, GACE_ECUDA, GACE_EINVAL, GACE_ENOMEM,
+                    GACE_ENOTFOUND, GACE_EOVERFLOW, GACE_EPENDING, GACE_EQ, GACE_ETIMEDOUT,
+                    GACE_F32, GACE_FULL, GACE_I32,
                     GACE_I64, GACE_IN, GACE_JOIN_AUTO, GACE_JOIN_GATHER, GACE_JOIN_HIST_DOT,
                     GACE_OK, GACE_RANGE, GACE_REQ_JOIN, GACE_REQ_NDV, GACE_REQ_PROBE, GACE_ROWS,
                     GaceError, check, lib)
@@ -101,7 +103,10 @@ def gace_create(device: int = 0, stream=None, hbm_budget_bytes: int = 0,
 
 
 def gace_destroy(ctx) -> None:
+    """Frees the context; a running scheduler first finishes its requests."""
     check(lib().gace_destroy(ctx), "gace_destroy")
+    for key in [k for k in _SUBMITTED if k[0] == _ctx_key(ctx)]:
+        del _SUBMITTED[key]
 
 
 def gace_load_columns(ctx, columns, borrow: bool = False) -> int:
@@ -323,6 +328,63 @@ def gace_tune_save(ctx, path: str) -> None:
 
 def gace_tune_load(ctx, path: str) -> None:
     check(lib().gace_tune_load(ctx, path.encode()), "gace_tune_load")
+
+
+# ----------------------------------------------------------------- served form
+
+_SUBMITTED: dict = {}  # (context, ticket) -> request object whose outputs are pending
+
+
+def gace_serve_start(ctx, arena_bytes: int = 0, max_inflight: int = 0, sketch_cache: int = 0,
+                     step_rows: int = 0, chunk_rows: int = 0) -> None:
+    cfg = _capi.gace_serve_config(arena_bytes, max_inflight, sketch_cache, step_rows, chunk_rows)
+    check(lib().gace_serve_start(ctx, C.byref(cfg)), "gace_serve_start")
+
+
+def gace_serve_stop(ctx) -> None:
+    check(lib().gace_serve_stop(ctx), "gace_serve_stop")
+    for key in [k for k in _SUBMITTED if k[0] == _ctx_key(ctx)]:
+        del _SUBMITTED[key]
+
+
+def _ctx_key(ctx) -> int:
+    return C.cast(ctx, C.c_void_p).value or 0
+
+
+def gace_submit(ctx, request) -> int:
+    """Queues a ProbeRequest / NdvRequest / JoinRequest; returns its ticket.
+    The request object receives the outputs once gace_poll reports completion."""
+    r = _capi.gace_request()
+    request.fill(r)
+    t = C.c_uint64()
+    check(lib().gace_submit(ctx, C.byref(r), C.byref(t)), "gace_submit")
+    _SUBMITTED[(_ctx_key(ctx), t.value)] = request
+    return t.value
+
+
+def gace_poll(ctx, ticket: int, timeout_us: int = 0) -> bool:
+    """True once the request has completed (its outputs are in the request
+    object), False while it is pending; raises GaceError if it failed."""
+    rc = lib().gace_poll(ctx, ticket, timeout_us)
+    if rc == GACE_EPENDING:
+        return False
+    _SUBMITTED.pop((_ctx_key(ctx), ticket), None)
+    check(rc, "gace_poll")
+    return True
+
+
+def gace_serve_replay(ctx, requests, arrival_ns, mode: int = 0):
+    """Open-loop replay: request i is submitted at arrival_ns[i] nanoseconds
+    after the start (mode 0 served, mode 1 one synchronous call per request).
+    Returns (done_ns, statuses) as numpy arrays."""
+    n = len(requests)
+    arr = _request_array(requests)
+    arrival = np.ascontiguousarray(arrival_ns, dtype=np.uint64)
+    done = np.zeros(max(1, n), dtype=np.uint64)
+    st = np.zeros(max(1, n), dtype=np.int32)
+    lib().gace_serve_replay(ctx, arr, n, arrival.ctypes.data_as(C.POINTER(C.c_uint64)), mode,
+                            done.ctypes.data_as(C.POINTER(C.c_uint64)), st.ctypes.data_as(C.POINTER(C.c_int)))
+    return done[:n], st[:n]
 
 
 def gace_stats_reset(ctx, time_kernels: bool = False) -> None:

@@ -83,6 +83,11 @@ class gace_request(C.Structure):
                 ("join_out", C.POINTER(gace_join_result))]
 
 
+class gace_serve_config(C.Structure):
+    _fields_ = [("arena_bytes", C.c_uint64), ("max_inflight", C.c_uint32), ("sketch_cache", C.c_int32),
+                ("step_rows", C.c_uint64), ("chunk_rows", C.c_uint64)]
+
+
 class gace_kernel_stat(C.Structure):
     _fields_ = [("name", C.c_char * 24), ("launches", C.c_uint64), ("rows", C.c_uint64),
                 ("bytes", C.c_uint64), ("ops", C.c_uint64), ("total_ms", C.c_double)]
@@ -110,6 +115,12 @@ PROTOTYPES = {
     "gace_tune_batch": (C.c_int, [ctx_p, C.POINTER(gace_request), C.c_uint32]),
     "gace_tune_save": (C.c_int, [ctx_p, C.c_char_p]),
     "gace_tune_load": (C.c_int, [ctx_p, C.c_char_p]),
+    "gace_serve_start": (C.c_int, [ctx_p, C.POINTER(gace_serve_config)]),
+    "gace_serve_stop": (C.c_int, [ctx_p]),
+    "gace_submit": (C.c_int, [ctx_p, C.POINTER(gace_request), C.POINTER(C.c_uint64)]),
+    "gace_poll": (C.c_int, [ctx_p, C.c_uint64, C.c_uint64]),
+    "gace_serve_replay": (C.c_int, [ctx_p, C.POINTER(gace_request), C.c_uint32, C.POINTER(C.c_uint64),
+                                    C.c_uint32, C.POINTER(C.c_uint64), C.POINTER(C.c_int)]),
     "gace_stats_reset": (C.c_int, [ctx_p, C.c_uint32]),
     "gace_stats_read": (C.c_int, [ctx_p, C.POINTER(gace_kernel_stat), C.c_uint32,
                                   C.POINTER(C.c_uint32)]),

@@ -133,7 +133,27 @@ __global__ void __launch_bounds__(kThreads) k_batch(const BatchItem* __restrict_
     }
 }
 
+// Scatter / gather of the served form: CTA b takes descriptors b, b + grid, ...
+__global__ void __launch_bounds__(256) k_copy(const CopyDesc* __restrict__ d, uint32_t n) {
+    for (uint32_t k = blockIdx.x; k < n; k += gridDim.x) {
+        const CopyDesc c = d[k];
+        uint4* dst = reinterpret_cast<uint4*>(c.dst);
+        const uint64_t nw = c.bytes / 16;
+        if (c.src) {
+            const uint4* src = reinterpret_cast<const uint4*>(c.src);
+            for (uint64_t i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
+        } else {
+            for (uint64_t i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t copy_launch(const CopyDesc* descs, uint32_t n, int grid, cudaStream_t s) {
+    k_copy<<<grid, 256, 0, s>>>(descs, n);
+    return cudaGetLastError();
+}
 
 cudaError_t batch_configure(int smem_optin) {
     // the kernel's own static shared memory counts against the opt-in limit

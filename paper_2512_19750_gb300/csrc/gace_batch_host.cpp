@@ -37,46 +37,8 @@ namespace gace {
 namespace host {
 namespace {
 
-constexpr uint64_t kDefaultChunk = 1ull << 20;
-constexpr int kPhases = 3;
-constexpr uint32_t kHllSmem = 1u << 16;  // one-byte registers for p <= 16
 
-struct JobRec {
-    BatchJob job{};
-    uint32_t phase = 0;
-    uint64_t units = 0;  // rows, or histogram entries
-    const char* family = "";
-    uint64_t rows = 0, bytes = 0, ops = 0;  // statistics
-};
 
-// A compiled request: its plan and where its data sits in the arena
-// (offsets relative to the input, small-output and big-output regions).
-struct ReqPlan {
-    gace_status status = GACE_OK;
-    std::string error;
-    uint32_t kind = 0;
-    const gace_request* q = nullptr;
-    // probe
-    ProbeRequest pr;
-    ProbePlan plan;
-    std::vector<uint64_t> args_off;  // input region: ProbeArgs copy per pass
-    // ndv
-    uint64_t regs_off = 0;  // small region
-    HllArgs hll{};
-    TableRec* tab = nullptr;
-    // join
-    gace_join spec{};
-    SideArgs side[3]{};
-    SideWork work[3]{};
-    TableRec* tabs[3]{};
-    uint32_t fk2_slot = 0;
-    bool hist_dot = false;
-    uint64_t K = 0, K2 = 0;
-    std::vector<uint32_t> pool;
-    uint64_t pool_off = 0, side_off[3] = {0, 0, 0};  // input region
-    uint64_t sc_off = 0;                              // small region: scalars and status
-    uint64_t hd_off = 0, w_off = 0, hf_off = 0;       // big region
-};
 
 int log2_bucket(uint64_t x) {
     int b = 0;
@@ -86,6 +48,8 @@ int log2_bucket(uint64_t x) {
     }
     return b;
 }
+
+}  // namespace
 
 // Compiles one request (argument checks, plans, join sides).
 gace_status compile_request(gace_ctx* ctx, const gace_request& q, ReqPlan& rp) {
@@ -337,6 +301,8 @@ void make_items(const std::vector<JobRec>& jobs, uint64_t chunk, std::vector<Bat
 }
 
 
+namespace {
+
 struct BatchRun {
     std::vector<JobRec> jobs;
     std::vector<BatchItem> items;
@@ -480,54 +446,62 @@ gace_status exec_batch(gace_ctx* ctx, const BatchRun& br, bool use_graph) {
     return GACE_OK;
 }
 
+}  // namespace
+
+// Outputs of one request from its read-back counters: host_base + offset
+// addresses what the request's small-output region held; status is the word
+// its probe and HLL jobs reported to.
+void finish_request(gace_ctx* ctx, ReqPlan& rp, const unsigned char* host_base, unsigned int status) {
+    const unsigned __int128 lim = static_cast<unsigned __int128>(1) << 63;
+    if (rp.status != GACE_OK) return;
+    if (rp.kind != GACE_REQ_JOIN && status) {
+        rp.status = read_status(ctx, status);
+        rp.error = gace_last_error();
+        return;
+    }
+    if (rp.kind == GACE_REQ_PROBE) {
+        std::vector<const unsigned long long*> outs;
+        for (const Pass& ps : rp.plan.passes)
+            outs.push_back(reinterpret_cast<const unsigned long long*>(host_base + ps.out_off));
+        assemble_probe(rp.plan, rp.pr, outs);
+    } else if (rp.kind == GACE_REQ_NDV) {
+        const uint64_t m = 1ull << rp.hll.p;
+        const uint32_t* r32 = reinterpret_cast<const uint32_t*>(host_base + rp.regs_off);
+        std::vector<uint8_t> regs(m);
+        for (uint64_t j = 0; j < m; ++j) regs[j] = static_cast<uint8_t>(r32[j]);
+        if (rp.q->registers_out) memcpy(rp.q->registers_out, regs.data(), m);
+        if (rp.q->estimate_out) *rp.q->estimate_out = hll_estimate_host(regs.data(), rp.hll.p);
+    } else {
+        const unsigned long long* h = reinterpret_cast<const unsigned long long*>(host_base + rp.sc_off);
+        const unsigned int st = *reinterpret_cast<const unsigned int*>(host_base + rp.sc_off + 64);
+        gace_status err = GACE_OK;
+        if (st & kStatusKeyDomain)
+            err = fail(GACE_EINVAL, "a filtered dimension row has a key outside its domain");
+        else if (rp.spec.hops == 1 && static_cast<unsigned __int128>(h[0]) * h[4] >= lim)
+            err = fail(GACE_EOVERFLOW, "fact_rows * max h_D >= 2^63");
+        else if (rp.spec.hops == 2 && static_cast<unsigned __int128>(h[1]) * h[4] >= lim)
+            err = fail(GACE_EOVERFLOW, "dim_rows * max h_D2 >= 2^63");
+        else if (rp.spec.hops == 2 && static_cast<unsigned __int128>(h[0]) * h[5] >= lim)
+            err = fail(GACE_EOVERFLOW, "fact_rows * max w >= 2^63");
+        if (err != GACE_OK) {
+            rp.status = err;
+            rp.error = gace_last_error();
+            return;
+        }
+        gace_join_result& out = *rp.q->join_out;
+        out.card = static_cast<int64_t>(h[3]);
+        out.fact_rows = h[0];
+        out.dim_rows = h[1];
+        out.dim2_rows = rp.spec.hops == 2 ? h[2] : 0;
+    }
+}
+
+namespace {
+
 // Outputs of every request from the read-back counters.
 void finish_batch(gace_ctx* ctx, std::vector<ReqPlan>& rps, const BatchRun& br) {
-    const unsigned char* pin = ctx->pin;
-    const unsigned int bst = *reinterpret_cast<const unsigned int*>(pin + br.small_base);
-    const unsigned __int128 lim = static_cast<unsigned __int128>(1) << 63;
-    for (ReqPlan& rp : rps) {
-        if (rp.status != GACE_OK) continue;
-        if (rp.kind != GACE_REQ_JOIN && bst) {
-            rp.status = read_status(ctx, bst);
-            rp.error = gace_last_error();
-            continue;
-        }
-        if (rp.kind == GACE_REQ_PROBE) {
-            std::vector<const unsigned long long*> outs;
-            for (const Pass& ps : rp.plan.passes)
-                outs.push_back(reinterpret_cast<const unsigned long long*>(pin + ps.out_off));
-            assemble_probe(rp.plan, rp.pr, outs);
-        } else if (rp.kind == GACE_REQ_NDV) {
-            const uint64_t m = 1ull << rp.hll.p;
-            const uint32_t* r32 = reinterpret_cast<const uint32_t*>(pin + rp.regs_off);
-            std::vector<uint8_t> regs(m);
-            for (uint64_t j = 0; j < m; ++j) regs[j] = static_cast<uint8_t>(r32[j]);
-            if (rp.q->registers_out) memcpy(rp.q->registers_out, regs.data(), m);
-            if (rp.q->estimate_out) *rp.q->estimate_out = hll_estimate_host(regs.data(), rp.hll.p);
-        } else {
-            const unsigned long long* h = reinterpret_cast<const unsigned long long*>(pin + rp.sc_off);
-            const unsigned int st = *reinterpret_cast<const unsigned int*>(pin + rp.sc_off + 64);
-            gace_status err = GACE_OK;
-            if (st & kStatusKeyDomain)
-                err = fail(GACE_EINVAL, "a filtered dimension row has a key outside its domain");
-            else if (rp.spec.hops == 1 && static_cast<unsigned __int128>(h[0]) * h[4] >= lim)
-                err = fail(GACE_EOVERFLOW, "fact_rows * max h_D >= 2^63");
-            else if (rp.spec.hops == 2 && static_cast<unsigned __int128>(h[1]) * h[4] >= lim)
-                err = fail(GACE_EOVERFLOW, "dim_rows * max h_D2 >= 2^63");
-            else if (rp.spec.hops == 2 && static_cast<unsigned __int128>(h[0]) * h[5] >= lim)
-                err = fail(GACE_EOVERFLOW, "fact_rows * max w >= 2^63");
-            if (err != GACE_OK) {
-                rp.status = err;
-                rp.error = gace_last_error();
-                continue;
-            }
-            gace_join_result& out = *rp.q->join_out;
-            out.card = static_cast<int64_t>(h[3]);
-            out.fact_rows = h[0];
-            out.dim_rows = h[1];
-            out.dim2_rows = rp.spec.hops == 2 ? h[2] : 0;
-        }
-    }
+    const unsigned int bst = *reinterpret_cast<const unsigned int*>(ctx->pin + br.small_base);
+    for (ReqPlan& rp : rps) finish_request(ctx, rp, ctx->pin, bst);
 }
 
 gace_status compile_all(gace_ctx* ctx, const gace_request* reqs, uint32_t n, std::vector<ReqPlan>& rps) {

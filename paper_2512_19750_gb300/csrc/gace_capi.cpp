@@ -875,6 +875,7 @@ gace_status gace_create(gace_ctx** out, const gace_config* cfg) {
 
 gace_status gace_destroy(gace_ctx* ctx) {
     if (!ctx) return GACE_OK;
+    serve_shutdown(ctx);
     {
         DeviceGuard g(ctx->device);
         if (ctx->stream) cudaStreamSynchronize(ctx->stream);
@@ -968,6 +969,7 @@ gace_status gace_unload(gace_ctx* ctx, uint32_t table_id) {
     DeviceGuard g(ctx->device);
     auto it = ctx->tables.find(table_id);
     if (it == ctx->tables.end()) return fail(GACE_ENOTFOUND, "table %u is not loaded", table_id);
+    if (gace_status s = serve_forget_table(ctx, table_id)) return s;
     cudaStreamSynchronize(ctx->stream);
     for (auto& c : it->second.cols)
         if (c.owned && c.dptr) cudaFree(c.dptr);

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <tuple>
@@ -21,6 +22,8 @@ struct gace_ctx;
 
 namespace gace {
 namespace host {
+
+struct ServeState;  // the served form's scheduler (gace_serve.cpp)
 
 // Sets the thread-local error message and returns s.
 gace_status fail(gace_status s, const char* fmt, ...);
@@ -159,6 +162,10 @@ struct gace_ctx {
     cudaGraphExec_t graph_exec = nullptr;
     std::vector<uint64_t> graph_key;
     bool batch_ready = false;
+
+    // served form: the scheduler, when running
+    std::mutex serve_mu;
+    std::shared_ptr<ServeState> serve;
 
     bool fits(uint64_t extra) const { return budget == 0 || used + extra <= budget; }
 
@@ -324,6 +331,70 @@ struct SideWork {
 };
 gace_status build_side(gace_ctx* ctx, const gace_join_side& js, const char* name, int extra_col, SideArgs& a,
                        std::vector<uint32_t>& pool, TableRec** tab_out, uint32_t* extra_slot, SideWork& work);
+
+
+// ---------------------------------------------------------------- batched and served forms
+
+constexpr uint64_t kDefaultChunk = 1ull << 20;
+constexpr int kPhases = 3;
+constexpr uint32_t kHllSmem = 1u << 16;  // one-byte registers for p <= 16
+
+struct JobRec {
+    BatchJob job{};
+    uint32_t phase = 0;
+    uint64_t units = 0;  // rows, or histogram entries
+    const char* family = "";
+    uint64_t rows = 0, bytes = 0, ops = 0;  // statistics
+};
+
+// A compiled request: its plan and where its data sits in the arena
+// (offsets relative to the input, small-output and big-output regions).
+struct ReqPlan {
+    gace_status status = GACE_OK;
+    std::string error;
+    uint32_t kind = 0;
+    const gace_request* q = nullptr;
+    // probe
+    ProbeRequest pr;
+    ProbePlan plan;
+    std::vector<uint64_t> args_off;  // input region: ProbeArgs copy per pass
+    // ndv
+    uint64_t regs_off = 0;  // small region
+    HllArgs hll{};
+    TableRec* tab = nullptr;
+    // join
+    gace_join spec{};
+    SideArgs side[3]{};
+    SideWork work[3]{};
+    TableRec* tabs[3]{};
+    uint32_t fk2_slot = 0;
+    bool hist_dot = false;
+    uint64_t K = 0, K2 = 0;
+    std::vector<uint32_t> pool;
+    uint64_t pool_off = 0, side_off[3] = {0, 0, 0};  // input region
+    uint64_t sc_off = 0;                              // small region: scalars and status
+    uint64_t hd_off = 0, w_off = 0, hf_off = 0;       // big region
+};
+
+// Argument checks and plans of one request.
+gace_status compile_request(gace_ctx* ctx, const gace_request& q, ReqPlan& rp);
+// Offsets of a request's data in the input, small-output and big-output regions.
+void place_request(ReqPlan& rp, Ws& win, Ws& wsmall, Ws& wbig);
+// Adds the regions' bases to those offsets.
+void shift_request(ReqPlan& rp, uint64_t in_base, uint64_t small_base, uint64_t big_base);
+// Jobs of a request, with device pointers into the workspace at dws.
+void emit_jobs(ReqPlan& rp, unsigned char* dws, unsigned int* status, std::vector<JobRec>& jobs);
+// Items of `chunk` units per job, ordered by phase.
+void make_items(const std::vector<JobRec>& jobs, uint64_t chunk, std::vector<BatchItem>& items,
+                uint32_t (&pbeg)[kPhases], uint32_t (&pcnt)[kPhases]);
+// A request's outputs from what its small-output region held.
+void finish_request(gace_ctx* ctx, ReqPlan& rp, const unsigned char* host_base, unsigned int status);
+
+// Served form: stops the scheduler of a context (after its requests have
+// finished); forgets a table's cached sketches, GACE_EBUSY while requests on
+// the table are in flight.  The caller holds ctx->mu for serve_forget_table.
+void serve_shutdown(gace_ctx* ctx);
+gace_status serve_forget_table(gace_ctx* ctx, uint32_t table_id);
 
 }  // namespace host
 }  // namespace gace

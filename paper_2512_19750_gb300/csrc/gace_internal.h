@@ -206,9 +206,19 @@ struct BatchItem {
     uint64_t end;
 };
 
+// One 16-byte-granular copy (src == nullptr: zero fill) of the served form's
+// scatter and gather launches; dst, src and bytes are multiples of 16.
+struct CopyDesc {
+    unsigned char* dst;
+    const unsigned char* src;
+    uint64_t bytes;
+    uint64_t pad;
+};
+
 cudaError_t batch_configure(int smem_optin);
 int batch_occupancy(uint32_t smem_bytes);
 cudaError_t batch_launch(const BatchItem* items, uint32_t nitems, const BatchJob* jobs, unsigned int* head,
                          int grid, uint32_t smem_bytes, cudaStream_t s);
+cudaError_t copy_launch(const CopyDesc* descs, uint32_t n, int grid, cudaStream_t s);
 
 }  // namespace gace

@@ -1,0 +1,994 @@
+// gace_serve.cpp -- the served form: continuous batching of requests that
+// arrive one at a time (gace_submit / gace_poll) and an open-loop load driver
+// (gace_serve_replay).
+//
+// A request is copied, checked and compiled at submission (the same plans,
+// jobs and phases as the batched form) and laid out as one block:
+//
+//   [inputs: probe arguments, pass tables, join sides, IN pools]  uploaded once
+//   [small outputs: status word, counters, HLL registers, join scalars]  cleared, gathered at the end
+//   [big state: join histograms and chain weights]                cleared
+//
+// The scheduler thread admits queued requests in arrival order while their
+// blocks fit in the arena (first fit) and fewer than max_inflight are in
+// flight.  Each step takes chunks round-robin from every admitted request's
+// current phase until step_rows units are taken; a request's next phase
+// starts in a later step than the one that issued its previous phase's last
+// chunk, which stream order then guarantees has finished.  One step is, on
+// the server's stream:
+//
+//   upload [queue head | new inputs | items | jobs | scatter | gather]
+//   k_copy   scatter: new inputs into their blocks, zero their outputs
+//   k_batch  the step's items over the persistent work queue
+//   k_copy   gather: the small outputs of requests whose last chunk ran
+//   read-back of the gathered outputs, then an event
+//
+// Two steps are in flight at once (double-buffered staging); a finished
+// step's requests are assembled on the host, their blocks freed, and their
+// tickets completed.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <list>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "gace_host.h"
+
+namespace gace {
+namespace host {
+
+namespace {
+
+constexpr uint64_t kDefaultArena = 1ull << 30;
+constexpr uint32_t kDefaultInflight = 4096;
+constexpr int32_t kDefaultSketches = 1024;
+constexpr uint64_t kDefaultStepRows = 1ull << 27;
+constexpr uint64_t kDefaultServeChunk = 1ull << 18;
+constexpr uint64_t kCopyPiece = 1ull << 16;    // bytes per scatter / gather descriptor
+constexpr size_t kMaxStepItems = 1u << 16;     // items per step
+
+uint64_t now_ns() {
+    return static_cast<uint64_t>(std::chrono::duration_cast<std::chrono::nanoseconds>(
+                                     std::chrono::steady_clock::now().time_since_epoch())
+                                     .count());
+}
+
+// A request with its own copies of every input array.
+struct OwnedRequest {
+    gace_request q{};
+    std::vector<gace_sample> samples;
+    std::vector<gace_term> terms;
+    std::vector<gace_scalar> in_values;
+    std::vector<gace_pred> preds;
+    gace_join join{};
+    std::vector<gace_term> side_terms[3];
+    std::vector<gace_scalar> side_in[3];
+
+    template <typename T>
+    static const T* own(std::vector<T>& v, const T* src, uint64_t n) {
+        if (!src) return nullptr;  // the request's checks report a NULL array with n > 0
+        v.assign(src, src + n);
+        return v.data();
+    }
+
+    void copy_from(const gace_request& r) {
+        q = r;
+        if (r.kind == GACE_REQ_PROBE) {
+            q.samples = own(samples, r.samples, r.nsamples);
+            q.terms = own(terms, r.terms, r.nterms);
+            q.in_values = own(in_values, r.in_values, r.nin);
+            q.preds = own(preds, r.preds, r.npreds);
+        } else if (r.kind == GACE_REQ_JOIN && r.join) {
+            join = *r.join;
+            gace_join_side* sides[3] = {&join.fact, &join.dim, &join.dim2};
+            for (int i = 0; i < 3; ++i) {
+                sides[i]->terms = own(side_terms[i], sides[i]->terms, sides[i]->nterms);
+                sides[i]->in_values = own(side_in[i], sides[i]->in_values, sides[i]->nin);
+            }
+            q.join = &join;
+        }
+    }
+};
+
+// Where a replayed request's completion goes.
+struct ReplaySink {
+    uint64_t t0 = 0;
+    uint64_t* done_ns = nullptr;
+    gace_status* statuses = nullptr;
+    uint32_t remaining = 0;  // guarded by ServeState::mu
+};
+
+struct SketchKey {
+    uint32_t table, col, p;
+    uint64_t seed;
+    bool operator<(const SketchKey& o) const {
+        return std::tie(table, col, p, seed) < std::tie(o.table, o.col, o.p, o.seed);
+    }
+};
+
+struct Sketch {
+    std::vector<uint8_t> regs;
+    double estimate = 0.0;
+    std::list<SketchKey>::iterator lru;
+};
+
+// One request from submission to completion.
+struct Live {
+    uint64_t ticket = 0;
+    OwnedRequest req;
+    ReqPlan rp;
+    uint32_t tables[3] = {0, 0, 0};
+    int ntables = 0;
+    // block layout (offsets from the block's start)
+    uint64_t in_bytes = 0, small_rel = 0, small_bytes = 0, block_bytes = 0;
+    uint64_t block = ~0ull;  // arena offset once admitted
+    // device form, after admission
+    std::vector<JobRec> jobs;
+    std::vector<uint32_t> job_smem;
+    uint32_t phase_list[kPhases] = {0, 0, 0};
+    int nphases = 0;
+    // issue state
+    int pi = -1;                     // index into phase_list
+    std::vector<uint32_t> pjobs;     // jobs of the current phase with units
+    size_t jk = 0;                   // next job of pjobs
+    uint64_t unit = 0;               // next unit of that job
+    int64_t last_step = -1;          // step that issued the current phase's last chunk
+    bool issued_all = false;
+    int64_t step_stamp = -1;         // step whose job table holds this request's jobs
+    uint32_t step_job_base = 0;
+    // completion
+    ReplaySink* sink = nullptr;
+    uint32_t sink_index = 0;
+    bool cacheable = false;
+    bool finished = false;
+};
+
+struct Done {
+    gace_status status = GACE_OK;
+    std::string error;
+};
+
+// First-fit allocator over the arena's offsets.
+struct Arena {
+    std::map<uint64_t, uint64_t> free_;  // offset -> bytes
+    void reset(uint64_t bytes) {
+        free_.clear();
+        if (bytes) free_[0] = bytes;
+    }
+    uint64_t alloc(uint64_t bytes) {
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < bytes) continue;
+            const uint64_t off = it->first, rest = it->second - bytes;
+            free_.erase(it);
+            if (rest) free_[off + bytes] = rest;
+            return off;
+        }
+        return ~0ull;
+    }
+    void release(uint64_t off, uint64_t bytes) {
+        auto next = free_.lower_bound(off);
+        if (next != free_.end() && off + bytes == next->first) {
+            bytes += next->second;
+            next = free_.erase(next);
+        }
+        if (next != free_.begin()) {
+            auto prev = std::prev(next);
+            if (prev->first + prev->second == off) {
+                prev->second += bytes;
+                return;
+            }
+        }
+        free_[off] = bytes;
+    }
+};
+
+// Staging of one step (two of them alternate).
+struct StepSet {
+    unsigned char* host = nullptr;  // pinned upload
+    unsigned char* dev = nullptr;   // its device copy
+    uint64_t cap = 0;
+    unsigned char* rb_host = nullptr;  // pinned read-back
+    unsigned char* rb_dev = nullptr;   // gathered small outputs
+    uint64_t rb_cap = 0;
+    cudaEvent_t done = nullptr, k0 = nullptr, k1 = nullptr;
+    bool busy = false, timed = false;
+    std::vector<std::pair<Live*, uint64_t>> finishing;  // request, read-back offset
+    uint64_t rows = 0, bytes = 0, ops = 0;
+    uint32_t copies = 0;
+};
+
+}  // namespace
+
+struct ServeState {
+    gace_ctx* ctx = nullptr;
+    gace_serve_config cfg{};
+    uint64_t chunk = 0;
+    unsigned char* arena = nullptr;
+    Arena alloc;
+    cudaStream_t stream = nullptr;
+    std::thread thr;
+
+    // guarded by mu
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    bool stop = false;
+    std::deque<std::unique_ptr<Live>> pending;
+    std::unordered_map<uint64_t, Done> done;
+    std::unordered_map<uint64_t, bool> open;  // submitted, not yet completed
+    std::unordered_map<uint32_t, int> table_refs;
+    uint64_t next_ticket = 1;
+    uint32_t nlive = 0;
+    std::map<SketchKey, Sketch> cache;
+    std::list<SketchKey> lru;
+    gace_status sticky = GACE_OK;  // a CUDA failure of the scheduler
+    std::string sticky_msg;
+
+    // scheduler thread only
+    std::vector<std::unique_ptr<Live>> live;
+    StepSet sets[2];
+    int64_t step = 0;
+    uint64_t rr = 0;
+    std::map<uint32_t, int> occ;  // dynamic shared memory -> CTAs per SM
+
+    void run();
+    bool admit(std::vector<std::unique_ptr<Live>>& admitted, bool& blocked);
+    gace_status build_step(StepSet& S, std::vector<std::unique_ptr<Live>>& admitted);
+    void complete(StepSet& S);
+    void finish(Live& lv, gace_status st, const std::string& err);
+    void fail_all(gace_status st, const std::string& msg);
+    int occupancy(uint32_t smem);  // CTAs of the batch kernel per SM
+};
+
+namespace {
+
+// Block layout of a compiled request; its plan's offsets become offsets from
+// the block's start.
+void layout_request(Live& lv) {
+    Ws win, wsmall, wbig;
+    wsmall.take(256);  // the status word of the request's probe and HLL jobs
+    place_request(lv.rp, win, wsmall, wbig);
+    lv.in_bytes = round_up(win.off, 16);
+    lv.small_rel = round_up(win.off, 256);
+    lv.small_bytes = round_up(wsmall.off, 16);
+    const uint64_t big_rel = lv.small_rel + round_up(wsmall.off, 256);
+    lv.block_bytes = std::max<uint64_t>(256, big_rel + round_up(wbig.off, 256));
+    shift_request(lv.rp, 0, lv.small_rel, big_rel);
+    const gace_request& q = lv.req.q;
+    if (q.kind == GACE_REQ_JOIN) {
+        lv.tables[lv.ntables++] = q.join->fact.table_id;
+        lv.tables[lv.ntables++] = q.join->dim.table_id;
+        if (q.join->hops == 2) lv.tables[lv.ntables++] = q.join->dim2.table_id;
+    } else {
+        lv.tables[lv.ntables++] = q.table_id;
+    }
+}
+
+// Inputs of an admitted request into host staging at pin (offsets as in its
+// block), device pointers into its block at dws; its jobs and phases.
+void stage_request(Live& lv, unsigned char* pin, unsigned char* dws) {
+    ReqPlan& rp = lv.rp;
+    unsigned int* status = reinterpret_cast<unsigned int*>(dws + lv.small_rel);
+    if (rp.kind == GACE_REQ_PROBE) {
+        for (size_t k = 0; k < rp.plan.passes.size(); ++k) {
+            Pass& ps = rp.plan.passes[k];
+            stage_pass(ps, pin, dws, status);
+            memcpy(pin + rp.args_off[k], &ps.args, sizeof(ProbeArgs));
+        }
+    }
+    lv.jobs.clear();
+    emit_jobs(rp, dws, status, lv.jobs);
+    if (rp.kind == GACE_REQ_JOIN) {
+        const int nsides = rp.spec.hops == 2 ? 3 : 2;
+        for (int i = 0; i < nsides; ++i) memcpy(pin + rp.side_off[i], &rp.side[i], sizeof(SideArgs));
+        if (!rp.pool.empty()) memcpy(pin + rp.pool_off, rp.pool.data(), rp.pool.size() * 4);
+    }
+    lv.job_smem.assign(lv.jobs.size(), 0);
+    for (size_t j = 0; j < lv.jobs.size(); ++j) {
+        if (rp.kind == GACE_REQ_PROBE) lv.job_smem[j] = rp.plan.passes[j].args.smem_bytes;
+        if (rp.kind == GACE_REQ_NDV && rp.hll.p <= 16) lv.job_smem[j] = 1u << rp.hll.p;
+    }
+    lv.nphases = 0;
+    for (uint32_t ph = 0; ph < static_cast<uint32_t>(kPhases); ++ph)
+        for (const JobRec& jr : lv.jobs)
+            if (jr.phase == ph && jr.units) {
+                lv.phase_list[lv.nphases++] = ph;
+                break;
+            }
+}
+
+void enter_phase(Live& lv) {
+    lv.pjobs.clear();
+    const uint32_t ph = lv.phase_list[lv.pi];
+    for (uint32_t j = 0; j < lv.jobs.size(); ++j)
+        if (lv.jobs[j].phase == ph && lv.jobs[j].units) lv.pjobs.push_back(j);
+    lv.jk = 0;
+    lv.unit = 0;
+}
+
+void add_copies(std::vector<CopyDesc>& v, unsigned char* dst, const unsigned char* src, uint64_t bytes) {
+    for (uint64_t o = 0; o < bytes; o += kCopyPiece) {
+        CopyDesc d{};
+        d.dst = dst + o;
+        d.src = src ? src + o : nullptr;
+        d.bytes = std::min(kCopyPiece, bytes - o);
+        v.push_back(d);
+    }
+}
+
+// Completion of a ticket (the caller holds srv.mu).
+void deliver(ServeState& srv, uint64_t ticket, ReplaySink* sink, uint32_t idx, gace_status st,
+             const std::string& err) {
+    if (sink) {
+        sink->done_ns[idx] = now_ns() - sink->t0;
+        sink->statuses[idx] = st;
+        --sink->remaining;
+    } else {
+        Done& d = srv.done[ticket];
+        d.status = st;
+        d.error = err;
+        srv.open.erase(ticket);
+    }
+    srv.cv_done.notify_all();
+}
+
+void cache_put(ServeState& srv, const SketchKey& key, std::vector<uint8_t>&& regs, double est) {
+    const size_t cap = static_cast<size_t>(srv.cfg.sketch_cache);
+    auto it = srv.cache.find(key);
+    if (it != srv.cache.end()) {
+        srv.lru.erase(it->second.lru);
+        srv.cache.erase(it);
+    }
+    srv.lru.push_front(key);
+    Sketch& s = srv.cache[key];
+    s.regs = std::move(regs);
+    s.estimate = est;
+    s.lru = srv.lru.begin();
+    while (srv.cache.size() > cap) {
+        srv.cache.erase(srv.lru.back());
+        srv.lru.pop_back();
+    }
+}
+
+SketchKey sketch_key(const gace_request& q) { return SketchKey{q.table_id, q.col, q.p, q.hash_seed}; }
+
+gace_status alloc_step(StepSet& S, uint64_t up, uint64_t rb) {
+    if (up > S.cap) {
+        if (S.host) cudaFreeHost(S.host);
+        if (S.dev) cudaFree(S.dev);
+        S.host = nullptr;
+        S.dev = nullptr;
+        S.cap = 0;
+        const uint64_t cap = round_up(std::max<uint64_t>(up + up / 2, 1ull << 20), 1ull << 16);
+        CK(cudaHostAlloc(reinterpret_cast<void**>(&S.host), cap, cudaHostAllocDefault));
+        CK(cudaMalloc(&S.dev, cap));
+        S.cap = cap;
+    }
+    if (rb > S.rb_cap) {
+        if (S.rb_host) cudaFreeHost(S.rb_host);
+        if (S.rb_dev) cudaFree(S.rb_dev);
+        S.rb_host = nullptr;
+        S.rb_dev = nullptr;
+        S.rb_cap = 0;
+        const uint64_t cap = round_up(std::max<uint64_t>(rb + rb / 2, 1ull << 20), 1ull << 16);
+        CK(cudaHostAlloc(reinterpret_cast<void**>(&S.rb_host), cap, cudaHostAllocDefault));
+        CK(cudaMalloc(&S.rb_dev, cap));
+        S.rb_cap = cap;
+    }
+    return GACE_OK;
+}
+
+}  // namespace
+
+int ServeState::occupancy(uint32_t smem) {
+    auto it = occ.find(smem);
+    return it == occ.end() ? (occ[smem] = batch_occupancy(smem)) : it->second;
+}
+
+// Admits queued requests in arrival order (the caller holds mu).
+bool ServeState::admit(std::vector<std::unique_ptr<Live>>& admitted, bool& blocked) {
+    while (!pending.empty()) {
+        if (nlive >= cfg.max_inflight) {
+            blocked = true;
+            break;
+        }
+        Live& lv = *pending.front();
+        const uint64_t off = alloc.alloc(lv.block_bytes);
+        if (off == ~0ull) {
+            blocked = true;
+            break;
+        }
+        lv.block = off;
+        ++nlive;
+        admitted.push_back(std::move(pending.front()));
+        pending.pop_front();
+    }
+    return !admitted.empty();
+}
+
+// A request is done: free its block, drop its table references, complete its ticket.
+void ServeState::finish(Live& lv, gace_status st, const std::string& err) {
+    if (lv.block != ~0ull) alloc.release(lv.block, lv.block_bytes);
+    lv.block = ~0ull;
+    lv.issued_all = true;
+    std::lock_guard<std::mutex> lk(mu);
+    for (int i = 0; i < lv.ntables; ++i)
+        if (--table_refs[lv.tables[i]] == 0) table_refs.erase(lv.tables[i]);
+    --nlive;
+    if (st == GACE_OK && lv.cacheable && lv.rp.kind == GACE_REQ_NDV) {
+        std::vector<uint8_t> regs(lv.req.q.registers_out, lv.req.q.registers_out + (1ull << lv.rp.hll.p));
+        cache_put(*this, sketch_key(lv.req.q), std::move(regs), *lv.req.q.estimate_out);
+    }
+    deliver(*this, lv.ticket, lv.sink, lv.sink_index, st, err);
+    lv.finished = true;
+}
+
+void ServeState::fail_all(gace_status st, const std::string& msg) {
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (sticky == GACE_OK) {
+            sticky = st;
+            sticky_msg = msg;
+        }
+    }
+    cudaStreamSynchronize(stream);
+    for (StepSet& S : sets) {
+        S.busy = false;
+        S.finishing.clear();
+    }
+    for (auto& p : live)
+        if (!p->finished) finish(*p, st, msg);
+    live.clear();
+}
+
+gace_status ServeState::build_step(StepSet& S, std::vector<std::unique_ptr<Live>>& admitted) {
+    S.finishing.clear();
+    S.rows = S.bytes = S.ops = 0;
+    S.copies = 0;
+    // newly admitted requests: stage their inputs
+    std::vector<unsigned char> inbuf;
+    std::vector<std::pair<Live*, uint64_t>> scat;  // request, offset in inbuf
+    uint64_t in_total = 0;
+    for (auto& p : admitted) in_total += round_up(p->in_bytes, 256);
+    inbuf.resize(in_total);
+    uint64_t pos = 0;
+    for (auto& p : admitted) {
+        stage_request(*p, inbuf.data() + pos, arena + p->block);
+        scat.emplace_back(p.get(), pos);
+        pos += round_up(p->in_bytes, 256);
+        live.push_back(std::move(p));
+    }
+    admitted.clear();
+    // phases and the round-robin ring
+    std::vector<Live*> ring;
+    uint64_t rb_total = 0;
+    auto finishing = [&](Live* lv) {
+        lv->issued_all = true;
+        S.finishing.emplace_back(lv, rb_total);
+        rb_total += round_up(lv->small_bytes, 256);
+    };
+    for (auto& p : live) {
+        Live& lv = *p;
+        if (lv.issued_all) continue;
+        if (lv.nphases == 0) {
+            finishing(&lv);
+            continue;
+        }
+        if (lv.pi < 0 || (lv.jk >= lv.pjobs.size() && lv.last_step < step)) {
+            ++lv.pi;
+            enter_phase(lv);
+        }
+        if (lv.jk < lv.pjobs.size()) ring.push_back(&lv);
+    }
+    std::vector<BatchItem> items;
+    std::vector<BatchJob> jobs;
+    uint32_t smem = 0;
+    if (!ring.empty()) {
+        const size_t n = ring.size();
+        const size_t start = static_cast<size_t>(rr++ % n);
+        uint64_t budget = cfg.step_rows;
+        bool progress = true;
+        while (budget > 0 && progress && items.size() < kMaxStepItems) {
+            progress = false;
+            for (size_t i = 0; i < n && budget > 0 && items.size() < kMaxStepItems; ++i) {
+                Live& lv = *ring[(start + i) % n];
+                if (lv.jk >= lv.pjobs.size()) continue;
+                if (lv.step_stamp != step) {
+                    lv.step_stamp = step;
+                    lv.step_job_base = static_cast<uint32_t>(jobs.size());
+                    for (size_t j = 0; j < lv.jobs.size(); ++j) {
+                        jobs.push_back(lv.jobs[j].job);
+                        smem = std::max(smem, lv.job_smem[j]);
+                    }
+                }
+                const uint32_t j = lv.pjobs[lv.jk];
+                const JobRec& jr = lv.jobs[j];
+                const uint64_t b = lv.unit, e = std::min(jr.units, b + chunk);
+                BatchItem it{};
+                it.job = lv.step_job_base + j;
+                it.begin = b;
+                it.end = e;
+                items.push_back(it);
+                S.rows += (e - b) * (jr.rows / jr.units);
+                S.bytes += (e - b) * (jr.bytes / jr.units);
+                S.ops += (e - b) * (jr.ops / jr.units);
+                budget -= std::min(budget, e - b);
+                progress = true;
+                lv.unit = e;
+                if (lv.unit >= jr.units) {
+                    ++lv.jk;
+                    lv.unit = 0;
+                }
+                if (lv.jk >= lv.pjobs.size()) {
+                    lv.last_step = step;
+                    if (lv.pi == lv.nphases - 1) finishing(&lv);
+                }
+            }
+        }
+    }
+    if (scat.empty() && items.empty() && S.finishing.empty()) return GACE_OK;
+    // upload layout: [queue head | inputs | items | jobs | scatter | gather]
+    Ws u;
+    u.take(256);
+    const uint64_t in_off = u.take(in_total);
+    const uint64_t items_off = u.take(items.size() * sizeof(BatchItem));
+    const uint64_t jobs_off = u.take(jobs.size() * sizeof(BatchJob));
+    size_t nscat = 0, ngath = 0;
+    for (auto& sp : scat)
+        nscat += (sp.first->in_bytes + kCopyPiece - 1) / kCopyPiece +
+                 (sp.first->block_bytes - sp.first->small_rel + kCopyPiece - 1) / kCopyPiece;
+    for (auto& f : S.finishing) ngath += (f.first->small_bytes + kCopyPiece - 1) / kCopyPiece;
+    const uint64_t scat_off = u.take(nscat * sizeof(CopyDesc));
+    const uint64_t gath_off = u.take(ngath * sizeof(CopyDesc));
+    if (gace_status st = alloc_step(S, u.off, rb_total)) return st;
+    std::vector<CopyDesc> sdesc, gdesc;
+    for (auto& sp : scat) {
+        Live& lv = *sp.first;
+        unsigned char* blk = arena + lv.block;
+        add_copies(sdesc, blk, S.dev + in_off + sp.second, lv.in_bytes);
+        add_copies(sdesc, blk + lv.small_rel, nullptr, lv.block_bytes - lv.small_rel);
+    }
+    for (auto& f : S.finishing)
+        add_copies(gdesc, S.rb_dev + f.second, arena + f.first->block + f.first->small_rel, f.first->small_bytes);
+    if (sdesc.size() != nscat || gdesc.size() != ngath)
+        return fail(GACE_ECUDA, "serving step: %zu / %zu copy descriptors, %zu / %zu expected", sdesc.size(),
+                    gdesc.size(), nscat, ngath);
+    memset(S.host, 0, 256);
+    if (in_total) memcpy(S.host + in_off, inbuf.data(), in_total);
+    if (!items.empty()) memcpy(S.host + items_off, items.data(), items.size() * sizeof(BatchItem));
+    if (!jobs.empty()) memcpy(S.host + jobs_off, jobs.data(), jobs.size() * sizeof(BatchJob));
+    if (nscat) memcpy(S.host + scat_off, sdesc.data(), nscat * sizeof(CopyDesc));
+    if (ngath) memcpy(S.host + gath_off, gdesc.data(), ngath * sizeof(CopyDesc));
+    const int copy_grid = std::max(1, ctx->sms * 4);
+    CK(cudaMemcpyAsync(S.dev, S.host, u.off, cudaMemcpyHostToDevice, stream));
+    if (nscat) {
+        CK(copy_launch(reinterpret_cast<const CopyDesc*>(S.dev + scat_off), static_cast<uint32_t>(nscat),
+                       std::min<int>(copy_grid, static_cast<int>(nscat)), stream));
+        ++S.copies;
+    }
+    S.timed = !items.empty();
+    if (!items.empty()) {
+        const int per_sm = occupancy(smem);
+        if (per_sm < 1)
+            return fail(GACE_ECUDA, "batch kernel cannot be resident with %u bytes of shared memory", smem);
+        const int grid = std::min<int>(per_sm * ctx->sms, static_cast<int>(items.size()));
+        CK(cudaEventRecord(S.k0, stream));
+        CK(batch_launch(reinterpret_cast<const BatchItem*>(S.dev + items_off), static_cast<uint32_t>(items.size()),
+                        reinterpret_cast<const BatchJob*>(S.dev + jobs_off), reinterpret_cast<unsigned int*>(S.dev),
+                        grid, smem, stream));
+        CK(cudaEventRecord(S.k1, stream));
+    }
+    if (ngath) {
+        CK(copy_launch(reinterpret_cast<const CopyDesc*>(S.dev + gath_off), static_cast<uint32_t>(ngath),
+                       std::min<int>(copy_grid, static_cast<int>(ngath)), stream));
+        ++S.copies;
+    }
+    if (rb_total) CK(cudaMemcpyAsync(S.rb_host, S.rb_dev, rb_total, cudaMemcpyDeviceToHost, stream));
+    CK(cudaEventRecord(S.done, stream));
+    S.busy = true;
+    ++step;
+    return GACE_OK;
+}
+
+// Waits for a step and completes the requests whose last chunk it ran.
+void ServeState::complete(StepSet& S) {
+    if (!S.busy) return;
+    cudaError_t e = cudaEventSynchronize(S.done);
+    if (e != cudaSuccess) {
+        fail_all(cuda_fail(e, "a serving step"), gace_last_error());
+        return;
+    }
+    S.busy = false;
+    float ms = 0.f;
+    if (S.timed) cudaEventElapsedTime(&ms, S.k0, S.k1);
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        gace_ctx::KStat& k = ctx->stats["serve_step"];
+        k.launches += S.timed ? 1 : 0;
+        k.rows += S.rows;
+        k.bytes += S.bytes;
+        k.ops += S.ops;
+        if (ctx->timing) k.ms += ms;
+        if (S.timed) ctx->stats["batch_kernel"].launches += 1;
+        if (S.copies) ctx->stats["serve_copy"].launches += S.copies;
+    }
+    for (auto& f : S.finishing) {
+        Live& lv = *f.first;
+        const unsigned char* rb = S.rb_host + f.second;
+        const unsigned int status = *reinterpret_cast<const unsigned int*>(rb);
+        // host_base + (an offset in the small region) addresses its read-back copy
+        const unsigned char* host_base =
+            reinterpret_cast<const unsigned char*>(reinterpret_cast<uintptr_t>(rb) - lv.small_rel);
+        lv.rp.status = GACE_OK;
+        std::vector<uint8_t> regs;
+        if (lv.rp.kind == GACE_REQ_NDV && lv.cacheable && !lv.req.q.registers_out) {
+            // the cache keeps the registers even when the caller does not want them
+            regs.resize(1ull << lv.rp.hll.p);
+            lv.req.q.registers_out = regs.data();
+        }
+        double est = 0.0;
+        if (lv.rp.kind == GACE_REQ_NDV && lv.cacheable && !lv.req.q.estimate_out) lv.req.q.estimate_out = &est;
+        finish_request(ctx, lv.rp, host_base, status);
+        finish(lv, lv.rp.status, lv.rp.error);
+    }
+    S.finishing.clear();
+    live.erase(std::remove_if(live.begin(), live.end(),
+                              [](const std::unique_ptr<Live>& p) { return p->finished; }),
+               live.end());
+}
+
+void ServeState::run() {
+    cudaSetDevice(ctx->device);
+    for (;;) {
+        std::vector<std::unique_ptr<Live>> admitted;
+        bool blocked = false, quit = false;
+        auto issuable = [&]() {
+            for (auto& p : live)
+                if (!p->issued_all) return true;
+            return false;
+        };
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            for (;;) {
+                if (!pending.empty() || issuable() || sets[0].busy || sets[1].busy) break;
+                if (stop) {
+                    quit = true;
+                    break;
+                }
+                cv_work.wait(lk);
+            }
+            if (!quit && sticky != GACE_OK) {
+                // after a CUDA failure every request fails with it
+                while (!pending.empty()) {
+                    Live& lv = *pending.front();
+                    for (int i = 0; i < lv.ntables; ++i)
+                        if (--table_refs[lv.tables[i]] == 0) table_refs.erase(lv.tables[i]);
+                    deliver(*this, lv.ticket, lv.sink, lv.sink_index, sticky, sticky_msg);
+                    pending.pop_front();
+                }
+            } else if (!quit) {
+                admit(admitted, blocked);
+            }
+        }
+        if (quit) break;
+        if (!admitted.empty() || issuable()) {
+            StepSet& S = sets[step & 1];
+            if (S.busy) complete(S);
+            if (gace_status st = build_step(S, admitted)) fail_all(st, gace_last_error());
+            continue;
+        }
+        StepSet* oldest = sets[step & 1].busy ? &sets[step & 1] : (sets[(step + 1) & 1].busy ? &sets[(step + 1) & 1] : nullptr);
+        if (!oldest) continue;
+        if (blocked || cudaEventQuery(oldest->done) != cudaErrorNotReady) {
+            complete(*oldest);
+        } else {
+            std::unique_lock<std::mutex> lk(mu);
+            cv_work.wait_for(lk, std::chrono::microseconds(20), [&]() { return !pending.empty() || stop; });
+        }
+    }
+}
+
+namespace {
+
+std::shared_ptr<ServeState> get_server(gace_ctx* ctx) {
+    std::lock_guard<std::mutex> lk(ctx->serve_mu);
+    return ctx->serve;
+}
+
+void free_server(ServeState& s) {
+    if (s.stream) cudaStreamSynchronize(s.stream);
+    for (StepSet& S : s.sets) {
+        if (S.host) cudaFreeHost(S.host);
+        if (S.dev) cudaFree(S.dev);
+        if (S.rb_host) cudaFreeHost(S.rb_host);
+        if (S.rb_dev) cudaFree(S.rb_dev);
+        for (cudaEvent_t e : {S.done, S.k0, S.k1})
+            if (e) cudaEventDestroy(e);
+        S = StepSet();
+    }
+    if (s.arena) cudaFree(s.arena);
+    s.arena = nullptr;
+    if (s.stream) cudaStreamDestroy(s.stream);
+    s.stream = nullptr;
+}
+
+// Starts the scheduler; the caller holds ctx->mu and ctx->serve is empty.
+gace_status start_locked(gace_ctx* ctx, const gace_serve_config* cfg, std::shared_ptr<ServeState>& out) {
+    auto s = std::make_shared<ServeState>();
+    s->ctx = ctx;
+    if (cfg) s->cfg = *cfg;
+    gace_serve_config& c = s->cfg;
+    if (!c.arena_bytes) c.arena_bytes = kDefaultArena;
+    if (!c.max_inflight) c.max_inflight = kDefaultInflight;
+    if (!c.sketch_cache) c.sketch_cache = kDefaultSketches;
+    if (c.sketch_cache < 0) c.sketch_cache = 0;
+    if (!c.step_rows) c.step_rows = kDefaultStepRows;
+    if (!c.chunk_rows) c.chunk_rows = kDefaultServeChunk;
+    if (c.chunk_rows > (1ull << 40)) return fail(GACE_EINVAL, "chunk_rows %llu above 2^40", (unsigned long long)c.chunk_rows);
+    s->chunk = round_up(c.chunk_rows, 128);
+    c.arena_bytes = round_up(c.arena_bytes, 1 << 20);
+    if (!ctx->fits(c.arena_bytes))
+        return fail(GACE_ENOMEM, "serving arena of %llu bytes exceeds the HBM budget",
+                    (unsigned long long)c.arena_bytes);
+    DeviceGuard g(ctx->device);
+    if (!ctx->batch_ready) {
+        cudaError_t e = batch_configure(ctx->smem_optin);
+        if (e != cudaSuccess) return cuda_fail(e, "batch kernel attributes");
+        ctx->batch_ready = true;
+    }
+    auto undo = [&](gace_status st) {
+        free_server(*s);
+        return st;
+    };
+    cudaError_t e = cudaMalloc(&s->arena, c.arena_bytes);
+    if (e != cudaSuccess) {
+        s->arena = nullptr;
+        return fail(GACE_ENOMEM, "cudaMalloc(%llu) for the serving arena: %s", (unsigned long long)c.arena_bytes,
+                    cudaGetErrorString(e));
+    }
+    if ((e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return undo(cuda_fail(e, "serving stream"));
+    for (StepSet& S : s->sets) {
+        if ((e = cudaEventCreateWithFlags(&S.done, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreate(&S.k0)) != cudaSuccess || (e = cudaEventCreate(&S.k1)) != cudaSuccess)
+            return undo(cuda_fail(e, "serving events"));
+    }
+    s->alloc.reset(c.arena_bytes);
+    ctx->used += c.arena_bytes;
+    ServeState* raw = s.get();
+    s->thr = std::thread([raw]() { raw->run(); });
+    {
+        std::lock_guard<std::mutex> lk(ctx->serve_mu);
+        ctx->serve = s;
+    }
+    out = s;
+    return GACE_OK;
+}
+
+// The running scheduler, started with defaults when there is none (the
+// caller holds ctx->mu).
+gace_status ensure_server(gace_ctx* ctx, std::shared_ptr<ServeState>& out) {
+    out = get_server(ctx);
+    if (out) return GACE_OK;
+    return start_locked(ctx, nullptr, out);
+}
+
+gace_status stop_server(gace_ctx* ctx) {
+    std::shared_ptr<ServeState> s = get_server(ctx);
+    if (!s) return GACE_OK;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) return GACE_OK;  // another caller is stopping it
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->thr.joinable()) s->thr.join();
+    {
+        DeviceGuard g(ctx->device);
+        free_server(*s);
+    }
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->used -= s->cfg.arena_bytes;
+    }
+    std::lock_guard<std::mutex> lk(ctx->serve_mu);
+    if (ctx->serve == s) ctx->serve.reset();
+    return GACE_OK;
+}
+
+// Copies, checks and queues one request; completion goes to the ticket table,
+// or to sink[idx] when sink is set.
+gace_status submit_request(gace_ctx* ctx, const gace_request& req, uint64_t* ticket_out, ReplaySink* sink,
+                           uint32_t idx) {
+    auto lv = std::make_unique<Live>();
+    lv->req.copy_from(req);
+    lv->sink = sink;
+    lv->sink_index = idx;
+    const gace_request& q = lv->req.q;
+    std::shared_ptr<ServeState> srv;
+    std::lock_guard<std::mutex> ck(ctx->mu);
+    if (gace_status s = ensure_server(ctx, srv)) return s;
+    if (q.kind == GACE_REQ_NDV && srv->cfg.sketch_cache > 0) {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        auto it = srv->cache.find(sketch_key(q));
+        if (it != srv->cache.end()) {
+            Sketch& sk = it->second;
+            if (q.registers_out) memcpy(q.registers_out, sk.regs.data(), sk.regs.size());
+            if (q.estimate_out) *q.estimate_out = sk.estimate;
+            srv->lru.splice(srv->lru.begin(), srv->lru, sk.lru);
+            const uint64_t t = srv->next_ticket++;
+            if (ticket_out) *ticket_out = t;
+            if (!sink) srv->open[t] = true;
+            deliver(*srv, t, sink, idx, GACE_OK, std::string());
+            return GACE_OK;
+        }
+        lv->cacheable = true;
+    }
+    if (gace_status s = compile_request(ctx, q, lv->rp)) return s;
+    layout_request(*lv);
+    if (lv->block_bytes > srv->cfg.arena_bytes)
+        return fail(GACE_ENOMEM, "the request needs %llu bytes of the %llu-byte serving arena",
+                    (unsigned long long)lv->block_bytes, (unsigned long long)srv->cfg.arena_bytes);
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        if (srv->stop) return fail(GACE_EBUSY, "the scheduler is stopping");
+        if (srv->sticky != GACE_OK) return fail(srv->sticky, "%s", srv->sticky_msg.c_str());
+        lv->ticket = srv->next_ticket++;
+        if (ticket_out) *ticket_out = lv->ticket;
+        if (!sink) srv->open[lv->ticket] = true;
+        for (int i = 0; i < lv->ntables; ++i) ++srv->table_refs[lv->tables[i]];
+        srv->pending.push_back(std::move(lv));
+    }
+    srv->cv_work.notify_one();
+    return GACE_OK;
+}
+
+gace_status run_plain(gace_ctx* ctx, const gace_request& q) {
+    switch (q.kind) {
+        case GACE_REQ_PROBE:
+            return gace_probe_batch(ctx, q.table_id, q.samples, q.nsamples, q.terms, q.nterms, q.in_values, q.nin,
+                                    q.preds, q.npreds, q.results, q.term_marginals);
+        case GACE_REQ_NDV:
+            return gace_ndv(ctx, q.table_id, q.col, q.p, q.hash_seed, q.registers_out, q.estimate_out);
+        case GACE_REQ_JOIN:
+            return gace_join_card(ctx, q.join, q.join_out);
+        default:
+            return fail(GACE_EINVAL, "request kind %u invalid", q.kind);
+    }
+}
+
+void wait_until(uint64_t t) {
+    for (;;) {
+        const uint64_t n = now_ns();
+        if (n >= t) return;
+        const uint64_t d = t - n;
+        if (d > 200000)
+            std::this_thread::sleep_for(std::chrono::nanoseconds(d - 100000));
+        else if (d > 20000)
+            std::this_thread::yield();
+    }
+}
+
+}  // namespace
+
+void serve_shutdown(gace_ctx* ctx) { stop_server(ctx); }
+
+gace_status serve_forget_table(gace_ctx* ctx, uint32_t table_id) {
+    std::shared_ptr<ServeState> s = get_server(ctx);
+    if (!s) return GACE_OK;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->table_refs.count(table_id))
+        return fail(GACE_EBUSY, "requests on table %u are queued or in flight", table_id);
+    for (auto it = s->cache.begin(); it != s->cache.end();) {
+        if (it->first.table == table_id) {
+            s->lru.erase(it->second.lru);
+            it = s->cache.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    return GACE_OK;
+}
+
+}  // namespace host
+}  // namespace gace
+
+extern "C" {
+
+gace_status gace_serve_start(gace_ctx* ctx, const gace_serve_config* cfg) {
+    if (gace_status s = check_ctx(ctx)) return s;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (get_server(ctx)) return fail(GACE_EBUSY, "the scheduler is already running");
+    std::shared_ptr<ServeState> s;
+    return start_locked(ctx, cfg, s);
+}
+
+gace_status gace_serve_stop(gace_ctx* ctx) {
+    if (gace_status s = check_ctx(ctx)) return s;
+    return stop_server(ctx);
+}
+
+gace_status gace_submit(gace_ctx* ctx, const gace_request* req, uint64_t* ticket_out) {
+    if (gace_status s = check_ctx(ctx)) return s;
+    if (!req || !ticket_out) return fail(GACE_EINVAL, "req or ticket_out is NULL");
+    return submit_request(ctx, *req, ticket_out, nullptr, 0);
+}
+
+gace_status gace_poll(gace_ctx* ctx, uint64_t ticket, uint64_t timeout_us) {
+    if (gace_status s = check_ctx(ctx)) return s;
+    std::shared_ptr<ServeState> s = get_server(ctx);
+    if (!s) return fail(GACE_ENOTFOUND, "ticket %llu unknown: the scheduler is not running", (unsigned long long)ticket);
+    Done d;
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        auto ready = [&]() { return s->done.count(ticket) != 0; };
+        if (!ready()) {
+            if (!s->open.count(ticket)) return fail(GACE_ENOTFOUND, "ticket %llu unknown", (unsigned long long)ticket);
+            if (timeout_us)
+                s->cv_done.wait_for(lk, std::chrono::microseconds(std::min<uint64_t>(timeout_us, 1ull << 40)), ready);
+            if (!ready()) return GACE_EPENDING;
+        }
+        auto it = s->done.find(ticket);
+        d = std::move(it->second);
+        s->done.erase(it);
+    }
+    if (d.status != GACE_OK) set_last_error_message(d.error.c_str());
+    return d.status;
+}
+
+gace_status gace_serve_replay(gace_ctx* ctx, const gace_request* reqs, uint32_t n, const uint64_t* arrival_ns,
+                              uint32_t mode, uint64_t* done_ns, gace_status* statuses) {
+    if (gace_status s = check_ctx(ctx)) return s;
+    if (n && (!reqs || !arrival_ns || !done_ns)) return fail(GACE_EINVAL, "reqs, arrival_ns or done_ns is NULL");
+    if (mode > 1) return fail(GACE_EINVAL, "mode %u (0 served, 1 plain)", mode);
+    for (uint32_t i = 1; i < n; ++i)
+        if (arrival_ns[i] < arrival_ns[i - 1]) return fail(GACE_EINVAL, "arrival_ns decreases at %u", i);
+    std::vector<gace_status> local(statuses ? 0 : n);
+    gace_status* st = statuses ? statuses : local.data();
+    if (mode == 1) {
+        const uint64_t t0 = now_ns();
+        for (uint32_t i = 0; i < n; ++i) {
+            wait_until(t0 + arrival_ns[i]);
+            st[i] = run_plain(ctx, reqs[i]);
+            done_ns[i] = now_ns() - t0;
+        }
+    } else {
+        std::shared_ptr<ServeState> srv;
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            if (gace_status s = ensure_server(ctx, srv)) return s;
+        }
+        ReplaySink sink;
+        sink.done_ns = done_ns;
+        sink.statuses = st;
+        sink.remaining = n;
+        sink.t0 = now_ns();
+        for (uint32_t i = 0; i < n; ++i) {
+            wait_until(sink.t0 + arrival_ns[i]);
+            const gace_status rc = submit_request(ctx, reqs[i], nullptr, &sink, i);
+            if (rc != GACE_OK) {  // rejected at submission: complete it here
+                std::lock_guard<std::mutex> lk(srv->mu);
+                deliver(*srv, 0, &sink, i, rc, std::string());
+            }
+        }
+        std::unique_lock<std::mutex> lk(srv->mu);
+        srv->cv_done.wait(lk, [&]() { return sink.remaining == 0; });
+    }
+    for (uint32_t i = 0; i < n; ++i)
+        if (st[i] != GACE_OK) return st[i];
+    return GACE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,163 @@
+"""GPU tests of the served form (gace_submit / gace_poll / gace_serve_replay):
+every request answered in the mix of a continuous batch gives exactly what its
+synchronous call gives, also when admission by memory makes requests wait,
+when chunks and steps are tiny (many phases spread over many steps), through
+the sketch cache, and through both replay modes; the ticket, unload and stop
+rules hold."""
+import numpy as np
+import pytest
+
+from batch_util import check_against_sync, to_requests
+from workloads import FULL, I32, RANGE, Sample, Term, make_batched, make_join
+
+pytestmark = pytest.mark.gpu
+
+POLL_US = 60_000_000
+
+
+@pytest.fixture(scope="module")
+def sctx(g, cuda):
+    ctx = g.gace_create(0)
+    yield ctx
+    g.gace_destroy(ctx)
+
+
+@pytest.fixture(scope="module")
+def served(g, sctx, cuda):
+    tables, reqs = make_batched(ntables=10, min_rows=1000, max_rows=300_000, nprobes=120, seed=21, device=cuda)
+    tids = [g.gace_load_columns(sctx, t.columns, borrow=True) for t in tables]
+    yield tables, reqs, tids
+    g.gace_serve_stop(sctx)
+    for t in tids:
+        g.gace_unload(sctx, t)
+
+
+def _submit_all(g, ctx, breqs):
+    tickets = [g.gace_submit(ctx, q) for q in breqs]
+    for t in tickets:
+        assert g.gace_poll(ctx, t, POLL_US)
+    return tickets
+
+
+@pytest.mark.parametrize("step_rows,chunk_rows", [(0, 0), (1 << 16, 1 << 12), (300, 128)])
+def test_served_equals_synchronous_calls(g, sctx, served, step_rows, chunk_rows):
+    tables, reqs, tids = served
+    g.gace_serve_start(sctx, step_rows=step_rows, chunk_rows=chunk_rows, sketch_cache=-1)
+    try:
+        breqs = to_requests(g, tids, tables, reqs)
+        _submit_all(g, sctx, breqs)
+        check_against_sync(g, sctx, tids, tables, reqs, breqs)
+    finally:
+        g.gace_serve_stop(sctx)
+
+
+def test_admission_by_memory(g, sctx, served):
+    """A 1 MiB arena and two slots: most requests wait for admission and all
+    still come back exact."""
+    tables, reqs, tids = served
+    g.gace_serve_start(sctx, arena_bytes=1 << 20, max_inflight=2, sketch_cache=-1)
+    try:
+        pick = reqs[:60]
+        breqs = to_requests(g, tids, tables, pick)
+        _submit_all(g, sctx, breqs)
+        check_against_sync(g, sctx, tids, tables, pick, breqs)
+        # a join whose histogram alone exceeds the arena is refused at submission
+        f = tables[0]
+        big = g.JoinRequest(g.JoinSideSpec(tids[0], 0, [], f.dtypes), g.JoinSideSpec(tids[1], 0, [], tables[1].dtypes),
+                            1 << 22)
+        with pytest.raises(g.GaceError) as e:
+            g.gace_submit(sctx, big)
+        assert e.value.status == g.GACE_ENOMEM
+    finally:
+        g.gace_serve_stop(sctx)
+
+
+def test_tickets_cache_and_unload(g, sctx, served, cuda):
+    tables, reqs, tids = served
+    g.gace_serve_start(sctx, step_rows=128, chunk_rows=128)
+    try:
+        with pytest.raises(g.GaceError) as e:
+            g.gace_poll(sctx, 987654321, 0)
+        assert e.value.status == g.GACE_ENOTFOUND
+        # sketch cache: the second identical NDV request completes at submission
+        q1 = g.NdvRequest(tids[2], 1, 12, 77)
+        t1 = g.gace_submit(sctx, q1)
+        assert g.gace_poll(sctx, t1, POLL_US)
+        q2 = g.NdvRequest(tids[2], 1, 12, 77)
+        t2 = g.gace_submit(sctx, q2)
+        assert g.gace_poll(sctx, t2, 0)
+        assert np.array_equal(q1.registers, q2.registers) and q1.estimate == q2.estimate
+        regs, est = g.gace_ndv(sctx, tids[2], 1, 12, 77)
+        assert np.array_equal(regs, q2.registers) and est == q2.estimate
+        # polled tickets are forgotten
+        with pytest.raises(g.GaceError):
+            g.gace_poll(sctx, t1, 0)
+        # a table with a request in flight cannot be unloaded; 128-row steps
+        # keep a 1M-row probe on the GPU for thousands of steps
+        import torch
+        col = torch.arange(1_000_000, dtype=torch.int32, device=cuda)
+        tid = g.gace_load_columns(sctx, [col], borrow=True)
+        q = g.ProbeRequest(tid, [[Term(0, RANGE, 10, 500_010)]], [Sample(FULL)], [I32])
+        t = g.gace_submit(sctx, q)
+        with pytest.raises(g.GaceError) as e:
+            g.gace_unload(sctx, tid)
+        assert e.value.status == g.GACE_EBUSY
+        assert g.gace_poll(sctx, t, POLL_US)
+        assert int(q.results["match"][0, 0]) == 500_000
+        g.gace_unload(sctx, tid)
+        # argument errors come back from submission, without a ticket
+        with pytest.raises(g.GaceError) as e:
+            g.gace_submit(sctx, g.NdvRequest(tids[0], 0, 30, 1))
+        assert e.value.status == g.GACE_EINVAL
+        with pytest.raises(g.GaceError) as e:
+            g.gace_submit(sctx, g.NdvRequest(99999, 0, 12, 1))
+        assert e.value.status == g.GACE_ENOTFOUND
+    finally:
+        g.gace_serve_stop(sctx)
+
+
+def test_replay_modes(g, sctx, served):
+    tables, reqs, tids = served
+    pick = reqs[:80]
+    rng = np.random.default_rng(5)
+    arrival = np.cumsum(rng.exponential(20_000.0, len(pick))).astype(np.uint64)  # 50k requests/s
+    for mode in (0, 1):
+        breqs = to_requests(g, tids, tables, pick)
+        done, st = g.gace_serve_replay(sctx, breqs, arrival, mode)
+        assert (st == 0).all()
+        assert (done >= arrival).all()
+        check_against_sync(g, sctx, tids, tables, pick, breqs)
+    g.gace_serve_stop(sctx)
+
+
+def test_join_chain_served(g, sctx, orc, cuda):
+    f, d, d2 = make_join(n_fact=300_001, n_dim=20_000, n_dim2=3000, seed=8, device=cuda)
+    fid, did, d2id = (g.gace_load_columns(sctx, t.columns, borrow=True) for t in (f, d, d2))
+    try:
+        g.gace_serve_start(sctx, step_rows=1 << 15, chunk_rows=1 << 13)
+        F = g.JoinSideSpec(fid, 0, [Term(1, RANGE, 0, 300)], f.dtypes)
+        D = g.JoinSideSpec(did, 0, [Term(2, RANGE, 100, 900)], d.dtypes)
+        D2 = g.JoinSideSpec(d2id, 0, [Term(1, RANGE, 0, 500)], d2.dtypes)
+        breqs = []
+        for method in (0, 1, 2):
+            breqs.append(g.JoinRequest(F, D, 20_000, method=method))
+            breqs.append(g.JoinRequest(F, D, 20_000, D2, 3000, 3, method=method))
+        _submit_all(g, sctx, breqs)
+        one = g.gace_join_card(sctx, F, D, 20_000)
+        two = g.gace_join_card(sctx, F, D, 20_000, D2, 3000, 3)
+        for k, q in enumerate(breqs):
+            assert q.result == (one if k % 2 == 0 else two)
+    finally:
+        g.gace_serve_stop(sctx)
+        for t in (fid, did, d2id):
+            g.gace_unload(sctx, t)
+
+
+def test_destroy_drains_a_running_server(g, served, cuda):
+    tables, reqs, _ = served
+    ctx = g.gace_create(0)
+    tids = [g.gace_load_columns(ctx, t.columns, borrow=True) for t in tables]
+    breqs = to_requests(g, tids, tables, reqs[:20])
+    tickets = [g.gace_submit(ctx, q) for q in breqs]
+    assert tickets == sorted(tickets)
+    g.gace_destroy(ctx)  # waits for the queued requests, then frees the arena
