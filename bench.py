@@ -12,7 +12,10 @@ stream the library launches on, inputs resident in HBM.
 Also reported in the same line: the dominant kernel's roofline (live CUDA-event
 times from the library's own tracing), the same metric end to end through the
 C ABI from pinned host memory, single-probe scans against the HBM roofline, the
-500M-row join probe, and the CPU oracle timed on a bounded sample.
+500M-row join probe, the CPU oracle timed on a bounded sample, the batched
+form (4096 mixed requests over 256 tables in one batch) against one
+synchronous call per request, and the served form under Poisson arrivals
+(p50 / p99 latency and throughput) against the plain path at the same rates.
 
     python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 """
@@ -20,6 +23,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -48,6 +52,11 @@ def parse_args():
     ap.add_argument("--ref-rows", type=int, default=50_000,
                     help="rows per step of the reference arm (the oracle)")
     ap.add_argument("--no-extras", action="store_true", help="skip single-probe, join and e2e legs")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched and served legs")
+    ap.add_argument("--serve-rates", default="1000,10000,50000,100000,200000",
+                    help="Poisson arrival rates (requests/s) of the served leg")
+    ap.add_argument("--serve-window", type=float, default=2.0, help="seconds of arrivals per rate")
+    ap.add_argument("--serve-cap", type=int, default=20000, help="requests per rate at most")
     ap.add_argument("--case", default=None,
                     choices=["narrow_i32", "narrow_4xi32", "narrow_rows1pct", "wide_batch", "hll_i32",
                              "join_gather"],
@@ -310,6 +319,9 @@ def run_gace(args, d: Dist):
         del table
         torch.cuda.empty_cache()
         extras["join"] = join_leg(g, ctx, dev, peaks, stream)
+    if not args.no_batch and d.world == 1:
+        extras["batched"] = batched_leg(g, ctx, dev, args)
+        extras["served"] = served_leg(g, ctx, dev, args)
     g.gace_destroy(ctx)
 
     d.barrier()
@@ -331,6 +343,8 @@ def run_gace(args, d: Dist):
             "clocks": clocks,
             "single_probe": extras.get("single_probe"),
             "join": extras.get("join"),
+            "batched": extras.get("batched"),
+            "served": extras.get("served"),
         }
         print(json.dumps(line), flush=True)
     d.done()
@@ -426,6 +440,153 @@ def join_leg(g, ctx, dev, peaks, stream):
     for t in (fid, did, d2id):
         g.gace_unload(ctx, t)
     del f, dm, d2
+    torch.cuda.empty_cache()
+    return out
+
+
+def to_gace_requests(g, tids, tables, reqs):
+    """Request objects of the library from the generated mixed workload."""
+    out = []
+    for r in reqs:
+        if r["kind"] == "probe":
+            t = tables[r["table"]]
+            out.append(g.ProbeRequest(tids[r["table"]], r["preds"], r["samples"], t.dtypes, marginals=True))
+        elif r["kind"] == "ndv":
+            out.append(g.NdvRequest(tids[r["table"]], r["col"], r["p"], r["seed"]))
+        else:
+            f, d = tables[r["fact"]], tables[r["dim"]]
+            out.append(g.JoinRequest(g.JoinSideSpec(tids[r["fact"]], 0, r["fact_terms"], f.dtypes),
+                                     g.JoinSideSpec(tids[r["dim"]], 0, r["dim_terms"], d.dtypes),
+                                     r["key_domain"]))
+    return out
+
+
+def request_bytes(tables, reqs):
+    """Algorithmic bytes of each request run alone: the referenced columns of
+    every table it scans, once."""
+    out = []
+    for r in reqs:
+        if r["kind"] == "probe":
+            t = tables[r["table"]]
+            cols = {term.col for p in r["preds"] for term in p}
+            out.append(t.nrows * sum(t.columns[c].element_size() for c in cols))
+        elif r["kind"] == "ndv":
+            t = tables[r["table"]]
+            out.append(t.nrows * t.columns[r["col"]].element_size())
+        else:
+            b = 0
+            for side, terms in ((r["fact"], r["fact_terms"]), (r["dim"], r["dim_terms"])):
+                t = tables[side]
+                cols = {0} | {term.col for term in terms}
+                b += t.nrows * sum(t.columns[c].element_size() for c in cols)
+            out.append(b)
+    return out
+
+
+def batched_leg(g, ctx, dev, args):
+    """4096 mixed requests over 256 tables: one batch (persistent kernel,
+    graph, autotuned chunk and grid) against one synchronous call per request
+    and against the served form with every request arriving at once."""
+    import numpy as np
+    import torch
+
+    from workloads import make_batched
+
+    tables, reqs = make_batched(ntables=256, min_rows=10_000, max_rows=50_000_000, nprobes=4096, seed=1004,
+                                device=dev)
+    tids = [g.gace_load_columns(ctx, t.columns, borrow=True) for t in tables]
+    nbytes = sum(request_bytes(tables, reqs))
+    n = len(reqs)
+    g.gace_tune_batch(ctx, to_gace_requests(g, tids, tables, reqs))
+    breqs = to_gace_requests(g, tids, tables, reqs)
+    for _ in range(2):
+        g.gace_run_batch(ctx, breqs)
+    g.gace_stats_reset(ctx, time_kernels=True)
+    walls = []
+    for _ in range(5):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        g.gace_run_batch(ctx, breqs)
+        walls.append(time.perf_counter() - t0)
+    st = g.gace_stats_read(ctx)
+    batch_ms = st["batch"]["total_ms"] / max(1, st["batch"]["launches"])
+    wall = float(np.median(walls))
+    zero = np.zeros(n, dtype=np.uint64)
+    plain_done, plain_st = g.gace_serve_replay(ctx, to_gace_requests(g, tids, tables, reqs), zero, mode=1)
+    plain_wall = float(plain_done.max()) / 1e9
+    g.gace_serve_start(ctx, sketch_cache=-1)
+    g.gace_serve_replay(ctx, to_gace_requests(g, tids, tables, reqs), zero, mode=0)  # warm-up
+    served_done, served_st = g.gace_serve_replay(ctx, to_gace_requests(g, tids, tables, reqs), zero, mode=0)
+    g.gace_serve_stop(ctx)
+    served_wall = float(served_done.max()) / 1e9
+    for t in tids:
+        g.gace_unload(ctx, t)
+    rows = sum(t.nrows for t in tables)
+    del tables
+    torch.cuda.empty_cache()
+    return {
+        "workload": "256 tables, rows log-uniform [1e4, 5e7]; 4096 requests (70% predicate probes, 20% HLL, "
+                    "10% joins)",
+        "requests": n, "table_rows": rows, "request_bytes": nbytes,
+        "batched_probes_per_s": n / wall, "batched_ms": wall * 1000.0, "batch_graph_ms": batch_ms,
+        "plain_probes_per_s": n / plain_wall, "plain_ms": plain_wall * 1000.0,
+        "served_at_once_probes_per_s": n / served_wall, "served_at_once_ms": served_wall * 1000.0,
+        "batched_vs_plain": plain_wall / wall,
+        "batched_gbs": nbytes / wall / 1e9,
+        "all_ok": bool((plain_st == 0).all() and (served_st == 0).all()),
+        "plain": "one synchronous call per request (probe / ndv / join_card) from a native loop",
+    }
+
+
+def served_leg(g, ctx, dev, args):
+    """Open-loop Poisson arrivals of the config-4 mix over 64 tables of 1M to
+    200M rows, served (continuous batching) and plain (one synchronous call
+    per request in arrival order) at each rate: p50 / p99 latency and
+    throughput."""
+    import numpy as np
+    import torch
+
+    from workloads import make_batched
+
+    rates = [int(r) for r in args.serve_rates.split(",") if r]
+    nmax = int(max(rates) * args.serve_window)
+    tables, reqs = make_batched(ntables=64, min_rows=1_000_000, max_rows=200_000_000,
+                                nprobes=min(nmax, args.serve_cap), seed=1005, device=dev)
+    tids = [g.gace_load_columns(ctx, t.columns, borrow=True) for t in tables]
+    rb = np.array(request_bytes(tables, reqs), dtype=np.float64)
+    rng = np.random.default_rng(7)
+    out = {"workload": "64 tables, rows log-uniform [1e6, 2e8], the config-4 request mix",
+           "table_rows": sum(t.nrows for t in tables), "mean_request_bytes": float(rb.mean()),
+           "window_s": args.serve_window, "cap_requests": args.serve_cap, "rates": {}}
+
+    def stats(arrival, done, st):
+        lat = (done.astype(np.float64) - arrival.astype(np.float64)) / 1e6
+        srt = np.sort(lat)
+        k = len(srt)
+        p50 = float(srt[max(0, math.ceil(0.50 * k) - 1)])
+        p99 = float(srt[max(0, math.ceil(0.99 * k) - 1)])
+        return {"p50_ms": p50, "p99_ms": p99, "throughput_per_s": k / (float(done.max()) / 1e9),
+                "ok": bool((st == 0).all())}
+
+    # warm-up of both paths
+    warm = to_gace_requests(g, tids, tables, reqs[:64])
+    g.gace_serve_replay(ctx, warm, np.zeros(len(warm), dtype=np.uint64), mode=1)
+    for rate in rates:
+        n = min(int(rate * args.serve_window), args.serve_cap, len(reqs))
+        gaps = rng.exponential(1e9 / rate, n)
+        arrival = np.cumsum(gaps).astype(np.uint64)
+        sub = reqs[:n]
+        entry = {"requests": n}
+        g.gace_serve_start(ctx)
+        done, st = g.gace_serve_replay(ctx, to_gace_requests(g, tids, tables, sub), arrival, mode=0)
+        g.gace_serve_stop(ctx)
+        entry["served"] = stats(arrival, done, st)
+        done, st = g.gace_serve_replay(ctx, to_gace_requests(g, tids, tables, sub), arrival, mode=1)
+        entry["plain"] = stats(arrival, done, st)
+        out["rates"][str(rate)] = entry
+    for t in tids:
+        g.gace_unload(ctx, t)
+    del tables
     torch.cuda.empty_cache()
     return out
 

@@ -368,8 +368,9 @@ typedef struct {
     uint64_t arena_bytes;   /* device bytes for the state of requests in flight; 0 = 1 GiB */
     uint32_t max_inflight;  /* requests admitted at once; 0 = 4096 */
     int32_t sketch_cache;   /* NDV results kept for reuse (entries); 0 = 1024, < 0 = no cache */
-    uint64_t step_rows;     /* units (rows) per scheduling step; 0 = 2^27 */
-    uint64_t chunk_rows;    /* rows per chunk, rounded up to a multiple of 128; 0 = 2^18 */
+    uint64_t step_rows;     /* units (rows) per scheduling step; 0 = 2^29 */
+    uint64_t chunk_rows;    /* rows per chunk (at most 2^30), rounded up to a multiple of 128, and
+                               for a narrow probe pass to a multiple of its tile; 0 = 2^18 */
 } gace_serve_config;
 
 /* Starts the scheduler (cfg may be NULL: defaults); its arena counts against
@@ -417,7 +418,14 @@ gace_status gace_serve_replay(gace_ctx* ctx, const gace_request* reqs, uint32_t 
  * operations (per row: 1 for an equality, 2 for a range, k for an IN list of
  * k values, 1 per hashed key or histogram update).  When time_kernels is set,
  * each launch is also bracketed by CUDA events on the context stream and its
- * device time accumulated.
+ * device time accumulated.  The served form adds "serve_step" (its batch
+ * launches, timed on the scheduler's stream), "serve_copy" (scatter and
+ * gather launches) and four entries that split the latency of completed
+ * requests, with launches = requests and total_ms = the summed wall time:
+ * serve_req_queue (submission to admission), serve_req_run (admission to the
+ * step with the request's last chunk), serve_req_gpu (that step's enqueue to
+ * the scheduler seeing it complete), serve_req_finish (outputs assembled and
+ * the ticket completed).
  */
 typedef struct {
     char name[24];      /* kernel family, NUL-terminated */

@@ -4,8 +4,10 @@
 // A batch mixes predicate probes, HyperLogLog sketches and join phases over
 // many tables.  Every CTA repeatedly takes the next item index with one
 // atomicAdd on the phase's queue head and runs that item with all its warps:
-//   probe      the wide-pass code over the item's 128-row slices, counters in
-//              shared memory, added to the job's 64-bit totals at item end;
+//   probe      wide passes: the wide-pass code over the item's 128-row
+//              slices, counters in shared memory, added to the job's 64-bit
+//              totals at item end (narrow passes are drained by
+//              k_batch_probe, the staged pipeline over whole tiles);
 //   HLL        a CTA copy of the registers in shared memory for the item's
 //              rows, merged into the job's global registers where larger;
 //   join side  filtered histogram, gather or chain-weight update over the
@@ -20,6 +22,7 @@
 #include "gace_device.cuh"
 #include "gace_internal.h"
 #include "gace_probe_dev.cuh"
+#include "gace_probe_narrow.cuh"
 #include "gace_side_dev.cuh"
 
 namespace gace {
@@ -29,6 +32,8 @@ using namespace dev;
 using namespace probe_dev;
 using namespace side_dev;
 
+// A wide probe item (narrow ones go to k_batch_probe): the wide-pass code
+// over the item's 128-row slices, then the CTA counters into the pass's totals.
 __device__ __forceinline__ void probe_item(const BatchJob& J, const BatchItem& it, unsigned char* smem, int tid,
                                            int lane, int warp) {
     const ProbeArgs& A = *J.probe;
@@ -66,9 +71,7 @@ __device__ __forceinline__ void side_item(const BatchJob& J, const BatchItem& it
     const uint64_t end = (it.end + 3) / 4;
     switch (J.kind) {
         case kJobHist:
-            side_groups<0, false>(SA, J.hist, J.strict, nullptr, 0, 0, nullptr, first, end, kThreads, npass, acc);
-            break;
-        case kJobHistAgg:
+        case kJobHistAgg:  // equal keys of a warp combined: skewed keys do not serialise on one address
             side_groups<0, true>(SA, J.hist, J.strict, nullptr, 0, 0, nullptr, first, end, kThreads, npass, acc);
             break;
         case kJobGather32:
@@ -133,6 +136,50 @@ __global__ void __launch_bounds__(kThreads) k_batch(const BatchItem* __restrict_
     }
 }
 
+// Narrow and single-predicate probe items only: the gate's small probes, which
+// are HBM-bound and want the register budget and occupancy of the plain
+// narrow kernels rather than the general kernel's.  The pass arguments are
+// copied into shared memory once per item.
+__global__ void __launch_bounds__(kThreads, 4) k_batch_probe(const BatchItem* __restrict__ items, uint32_t nitems,
+                                                             const BatchJob* __restrict__ jobs, unsigned int* head) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint32_t s_item;
+    __shared__ __align__(16) ProbeArgs sA;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(head, 1u);
+        __syncthreads();
+        const uint32_t k = s_item;
+        if (k >= nitems) return;
+        const BatchItem it = items[k];
+        {
+            const uint4* src = reinterpret_cast<const uint4*>(jobs[it.job].probe);
+            uint4* dst = reinterpret_cast<uint4*>(&sA);
+            for (uint32_t i = tid; i < sizeof(ProbeArgs) / 16; i += kThreads) dst[i] = src[i];
+        }
+        __syncthreads();  // sA and s_item are read below; both are rewritten only after the next barrier
+        const ProbeArgs& A = sA;
+        const Smem S = carve(A, smem, warp);
+        load_tables(A, S, tid);
+        __syncthreads();
+        const uint64_t first = it.begin / A.tile_rows;
+        uint64_t end = (it.end + A.tile_rows - 1) / A.tile_rows;
+        if (end > A.ntiles) end = A.ntiles;
+        bool ok;
+        switch (probe_variant(A)) {
+            case 1: ok = narrow_run<false, 1>(A, S, tid, lane, warp, first, end, 1); break;
+            case 2: ok = narrow_run<true, 1>(A, S, tid, lane, warp, first, end, 1); break;
+            case 3: ok = narrow_run<true, kMaxSets>(A, S, tid, lane, warp, first, end, 1); break;
+            case 4: ok = single_run<false>(A, S, tid, lane, warp, first, end, 1); break;
+            default: ok = single_run<true>(A, S, tid, lane, warp, first, end, 1); break;
+        }
+        if (!ok) return;  // uniform over the CTA; the status word says why
+        __syncthreads();
+        flush(A, S, tid);
+        __syncthreads();  // shared memory is reused by the next item
+    }
+}
+
 // Scatter / gather of the served form: CTA b takes descriptors b, b + grid, ...
 __global__ void __launch_bounds__(256) k_copy(const CopyDesc* __restrict__ d, uint32_t n) {
     for (uint32_t k = blockIdx.x; k < n; k += gridDim.x) {
@@ -155,24 +202,37 @@ cudaError_t copy_launch(const CopyDesc* descs, uint32_t n, int grid, cudaStream_
     return cudaGetLastError();
 }
 
-cudaError_t batch_configure(int smem_optin) {
+template <typename K>
+static cudaError_t configure_one(K kernel, int smem_optin) {
     // the kernel's own static shared memory counts against the opt-in limit
     cudaFuncAttributes fa{};
-    cudaError_t e = cudaFuncGetAttributes(&fa, k_batch);
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 smem_optin - static_cast<int>(fa.sharedSizeBytes));
 }
 
-int batch_occupancy(uint32_t smem_bytes) {
+cudaError_t batch_configure(int smem_optin) {
+    cudaError_t e = configure_one(k_batch, smem_optin);
+    if (e != cudaSuccess) return e;
+    return configure_one(k_batch_probe, smem_optin);
+}
+
+int batch_occupancy(uint32_t smem_bytes, int cls) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch, kThreads, smem_bytes) != cudaSuccess) return 0;
-    return n;
+    const cudaError_t e =
+        cls == kClassProbe
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_probe, kThreads, smem_bytes)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch, kThreads, smem_bytes);
+    return e == cudaSuccess ? n : 0;
 }
 
 cudaError_t batch_launch(const BatchItem* items, uint32_t nitems, const BatchJob* jobs, unsigned int* head,
-                         int grid, uint32_t smem_bytes, cudaStream_t s) {
-    k_batch<<<grid, kThreads, smem_bytes, s>>>(items, nitems, jobs, head);
+                         int grid, uint32_t smem_bytes, int cls, cudaStream_t s) {
+    if (cls == kClassProbe)
+        k_batch_probe<<<grid, kThreads, smem_bytes, s>>>(items, nitems, jobs, head);
+    else
+        k_batch<<<grid, kThreads, smem_bytes, s>>>(items, nitems, jobs, head);
     return cudaGetLastError();
 }
 

@@ -27,6 +27,8 @@
 #include <cstdio>
 #include <fstream>
 #include <limits>
+#include <map>
+#include <memory>
 #include <sstream>
 #include <string>
 #include <vector>
@@ -51,27 +53,131 @@ int log2_bucket(uint64_t x) {
 
 }  // namespace
 
+bool fusable_probe(const gace_request& r) {
+    if (r.kind != GACE_REQ_PROBE || !r.samples || r.nsamples == 0 || r.nsamples > kMaxSets) return false;
+    if (r.npreds > static_cast<uint32_t>(kNarrowMax) || r.nterms > static_cast<uint32_t>(kNarrowMax)) return false;
+    if (r.nin > FusedProbe::kMaxIn) return false;
+    if (r.npreds && (!r.preds || !r.results)) return false;
+    if (r.nterms && !r.terms) return false;
+    // every index must stay inside the member's own arrays once they are concatenated
+    for (uint32_t p = 0; p < r.npreds; ++p)
+        if (static_cast<uint64_t>(r.preds[p].term_off) + r.preds[p].term_cnt > r.nterms) return false;
+    for (uint32_t t = 0; t < r.nterms; ++t)
+        if (r.terms[t].op == GACE_IN &&
+            (!r.in_values || static_cast<uint64_t>(r.terms[t].in_off) + r.terms[t].in_len > r.nin))
+            return false;
+    return true;
+}
+
+namespace {
+
+bool same_sample(const gace_sample& a, const gace_sample& b) {
+    return a.kind == b.kind && a.block_rows == b.block_rows && a.seed == b.seed &&
+           memcmp(&a.rate, &b.rate, sizeof(double)) == 0;
+}
+
+}  // namespace
+
+bool FusedProbe::fits(const gace_request& r) const {
+    if (preds.size() + r.npreds > static_cast<size_t>(kNarrowMax)) return false;
+    if (terms.size() + r.nterms > static_cast<size_t>(kNarrowMax)) return false;
+    if (in_values.size() + r.nin > kMaxIn) return false;
+    size_t nsets = samples.size();
+    for (uint32_t s = 0; s < r.nsamples; ++s) {
+        bool found = false;
+        for (const gace_sample& x : samples) found = found || same_sample(x, r.samples[s]);
+        for (uint32_t u = 0; u < s && !found; ++u) found = same_sample(r.samples[u], r.samples[s]);
+        if (!found) ++nsets;
+    }
+    return nsets <= static_cast<size_t>(kMaxSets);
+}
+
+void FusedProbe::add(uint32_t index, const gace_request& r) {
+    Member m;
+    m.index = index;
+    m.q = &r;
+    m.term_off = static_cast<uint32_t>(terms.size());
+    m.pred_off = static_cast<uint32_t>(preds.size());
+    const uint32_t in_base = static_cast<uint32_t>(in_values.size());
+    for (uint32_t t = 0; t < r.nterms; ++t) {
+        gace_term x = r.terms[t];
+        if (x.op == GACE_IN) x.in_off += in_base;
+        terms.push_back(x);
+    }
+    if (r.nin) in_values.insert(in_values.end(), r.in_values, r.in_values + r.nin);
+    for (uint32_t p = 0; p < r.npreds; ++p) {
+        gace_pred x = r.preds[p];
+        x.term_off += m.term_off;
+        preds.push_back(x);
+    }
+    for (uint32_t s = 0; s < r.nsamples; ++s) {
+        uint32_t k = 0;
+        while (k < samples.size() && !same_sample(samples[k], r.samples[s])) ++k;
+        if (k == samples.size()) samples.push_back(r.samples[s]);
+        m.set_map[s] = k;
+    }
+    table_id = r.table_id;
+    members.push_back(m);
+}
+
+void FusedProbe::seal() {
+    bool want_marg = false;
+    for (const Member& m : members) want_marg = want_marg || m.q->term_marginals;
+    results.assign(samples.size() * preds.size(), gace_pred_result{});
+    marg.assign(want_marg ? samples.size() * terms.size() : 0, 0);
+    q = gace_request{};
+    q.kind = GACE_REQ_PROBE;
+    q.table_id = table_id;
+    q.samples = samples.data();
+    q.nsamples = static_cast<uint32_t>(samples.size());
+    q.terms = terms.data();
+    q.nterms = static_cast<uint32_t>(terms.size());
+    q.in_values = in_values.data();
+    q.nin = static_cast<uint32_t>(in_values.size());
+    q.preds = preds.data();
+    q.npreds = static_cast<uint32_t>(preds.size());
+    q.results = results.data();
+    q.term_marginals = want_marg ? marg.data() : nullptr;
+}
+
+void FusedProbe::scatter() const {
+    const size_t np = preds.size(), nt = terms.size();
+    for (const Member& m : members) {
+        const gace_request& r = *m.q;
+        for (uint32_t s = 0; s < r.nsamples; ++s) {
+            for (uint32_t p = 0; p < r.npreds; ++p) r.results[s * r.npreds + p] = results[m.set_map[s] * np + m.pred_off + p];
+            if (r.term_marginals)
+                for (uint32_t t = 0; t < r.nterms; ++t)
+                    r.term_marginals[s * r.nterms + t] = marg[m.set_map[s] * nt + m.term_off + t];
+        }
+    }
+}
+
+gace_status compile_probe(gace_ctx* ctx, const TableRec* tab, const gace_request& q, ReqPlan& rp) {
+    rp.q = &q;
+    rp.kind = GACE_REQ_PROBE;
+    ProbeRequest& r = rp.pr;
+    r.samples = q.samples;
+    r.nsamples = q.nsamples;
+    r.terms = q.terms;
+    r.nterms = q.nterms;
+    r.in_values = q.in_values;
+    r.nin = q.nin;
+    r.preds = q.preds;
+    r.npreds = q.npreds;
+    r.results = q.results;
+    r.term_marginals = q.term_marginals;
+    if (gace_status s = check_probe_request(r)) return s;
+    if (!tab) tab = find_table(ctx, q.table_id);
+    if (!tab) return fail(GACE_ENOTFOUND, "table %u is not loaded", q.table_id);
+    return plan_probe(ctx, *tab, r, false, rp.plan);
+}
+
 // Compiles one request (argument checks, plans, join sides).
 gace_status compile_request(gace_ctx* ctx, const gace_request& q, ReqPlan& rp) {
     rp.q = &q;
     rp.kind = q.kind;
-    if (q.kind == GACE_REQ_PROBE) {
-        ProbeRequest& r = rp.pr;
-        r.samples = q.samples;
-        r.nsamples = q.nsamples;
-        r.terms = q.terms;
-        r.nterms = q.nterms;
-        r.in_values = q.in_values;
-        r.nin = q.nin;
-        r.preds = q.preds;
-        r.npreds = q.npreds;
-        r.results = q.results;
-        r.term_marginals = q.term_marginals;
-        if (gace_status s = check_probe_request(r)) return s;
-        TableRec* tab = find_table(ctx, q.table_id);
-        if (!tab) return fail(GACE_ENOTFOUND, "table %u is not loaded", q.table_id);
-        return plan_probe(ctx, *tab, r, true, rp.plan);
-    }
+    if (q.kind == GACE_REQ_PROBE) return compile_probe(ctx, nullptr, q, rp);
     if (q.kind == GACE_REQ_NDV) {
         if (q.p < 4 || q.p > 18) return fail(GACE_EINVAL, "p = %u outside 4..18", q.p);
         TableRec* tab = find_table(ctx, q.table_id);
@@ -121,7 +227,7 @@ gace_status compile_request(gace_ctx* ctx, const gace_request& q, ReqPlan& rp) {
 // Offsets of a request's data inside the input, small-output and big-output
 // regions (relative to each region).
 void place_request(ReqPlan& rp, Ws& win, Ws& wsmall, Ws& wbig) {
-    if (rp.status != GACE_OK) return;
+    if (rp.status != GACE_OK || rp.fused >= 0) return;
     if (rp.kind == GACE_REQ_PROBE) {
         rp.args_off.clear();
         for (Pass& ps : rp.plan.passes) {
@@ -143,7 +249,7 @@ void place_request(ReqPlan& rp, Ws& win, Ws& wsmall, Ws& wbig) {
 }
 
 void shift_request(ReqPlan& rp, uint64_t in_base, uint64_t small_base, uint64_t big_base) {
-    if (rp.status != GACE_OK) return;
+    if (rp.status != GACE_OK || rp.fused >= 0) return;
     if (rp.kind == GACE_REQ_PROBE) {
         for (uint64_t& o : rp.args_off) o += in_base;
         for (Pass& ps : rp.plan.passes) {
@@ -165,7 +271,7 @@ void shift_request(ReqPlan& rp, uint64_t in_base, uint64_t small_base, uint64_t 
 // The jobs of a request, with device pointers into the arena at dws (dws may
 // be null when only the count, units and phases are wanted).
 void emit_jobs(ReqPlan& rp, unsigned char* dws, unsigned int* batch_status, std::vector<JobRec>& jobs) {
-    if (rp.status != GACE_OK) return;
+    if (rp.status != GACE_OK || rp.fused >= 0) return;
     if (rp.kind == GACE_REQ_PROBE) {
         for (size_t k = 0; k < rp.plan.passes.size(); ++k) {
             const Pass& ps = rp.plan.passes[k];
@@ -173,6 +279,10 @@ void emit_jobs(ReqPlan& rp, unsigned char* dws, unsigned int* batch_status, std:
             jr.job.kind = kJobProbe;
             jr.job.probe = reinterpret_cast<const ProbeArgs*>(dws + rp.args_off[k]);
             jr.units = rp.plan.tab->nrows;
+            if (ps.args.narrow) {
+                jr.granule = ps.args.tile_rows;
+                jr.cls = kClassProbe;
+            }
             jr.family = "batch_probe";
             jr.rows = jr.units;
             jr.bytes = jr.units * ps.rowbytes;
@@ -280,23 +390,27 @@ void emit_jobs(ReqPlan& rp, unsigned char* dws, unsigned int* batch_status, std:
     }
 }
 
-// Items of `chunk` units per job, ordered by phase; per-phase ranges.
+// Items of `chunk` units per job, ordered by phase, then class; the range of
+// each (phase, class).
 void make_items(const std::vector<JobRec>& jobs, uint64_t chunk, std::vector<BatchItem>& items,
-                uint32_t (&pbeg)[kPhases], uint32_t (&pcnt)[kPhases]) {
+                uint32_t (&pbeg)[kPhases][kClasses], uint32_t (&pcnt)[kPhases][kClasses]) {
     items.clear();
     for (int ph = 0; ph < kPhases; ++ph) {
-        pbeg[ph] = static_cast<uint32_t>(items.size());
-        for (uint32_t j = 0; j < jobs.size(); ++j) {
-            if (jobs[j].phase != static_cast<uint32_t>(ph)) continue;
-            for (uint64_t b = 0; b < jobs[j].units; b += chunk) {
-                BatchItem it{};
-                it.job = j;
-                it.begin = b;
-                it.end = std::min(jobs[j].units, b + chunk);
-                items.push_back(it);
+        for (int c = 0; c < kClasses; ++c) {
+            pbeg[ph][c] = static_cast<uint32_t>(items.size());
+            for (uint32_t j = 0; j < jobs.size(); ++j) {
+                if (jobs[j].phase != static_cast<uint32_t>(ph) || jobs[j].cls != c) continue;
+                const uint64_t step = round_up(chunk, jobs[j].granule);
+                for (uint64_t b = 0; b < jobs[j].units; b += step) {
+                    BatchItem it{};
+                    it.job = j;
+                    it.begin = b;
+                    it.end = std::min(jobs[j].units, b + step);
+                    items.push_back(it);
+                }
             }
+            pcnt[ph][c] = static_cast<uint32_t>(items.size()) - pbeg[ph][c];
         }
-        pcnt[ph] = static_cast<uint32_t>(items.size()) - pbeg[ph];
     }
 }
 
@@ -306,11 +420,12 @@ namespace {
 struct BatchRun {
     std::vector<JobRec> jobs;
     std::vector<BatchItem> items;
-    uint32_t pbeg[kPhases] = {0, 0, 0}, pcnt[kPhases] = {0, 0, 0};
+    uint32_t pbeg[kPhases][kClasses] = {}, pcnt[kPhases][kClasses] = {};
     uint64_t jobs_off = 0, items_off = 0, in_end = 0, small_base = 0, small_end = 0, end = 0;
-    uint32_t smem = 0;
-    int grid = 1;
+    uint32_t smem[kClasses] = {0, 0};
+    int grid[kClasses] = {1, 1};
     uint64_t rows = 0, bytes = 0, ops = 0;
+    int launches = 0;
 };
 
 // Lays out the arena for `chunk`-unit items and a grid of ctas_per_sm CTAs per
@@ -338,22 +453,20 @@ gace_status build_batch(gace_ctx* ctx, std::vector<ReqPlan>& rps, uint64_t chunk
     unsigned char* dws = ctx->ws;
     unsigned int* bstatus = reinterpret_cast<unsigned int*>(dws + br.small_base);
     // inputs: pass tables and argument copies, join sides and pools
-    br.smem = 0;
-    bool any_hll = false;
     for (ReqPlan& rp : rps) {
-        if (rp.status != GACE_OK) continue;
+        if (rp.status != GACE_OK || rp.fused >= 0) continue;
         if (rp.kind == GACE_REQ_PROBE) {
             for (size_t k = 0; k < rp.plan.passes.size(); ++k) {
                 Pass& ps = rp.plan.passes[k];
                 stage_pass(ps, pin, dws, bstatus);
                 memcpy(pin + rp.args_off[k], &ps.args, sizeof(ProbeArgs));
-                br.smem = std::max(br.smem, ps.args.smem_bytes);
+                uint32_t& sm = br.smem[ps.args.narrow ? kClassProbe : kClassGeneral];
+                sm = std::max(sm, ps.args.smem_bytes);
             }
         } else if (rp.kind == GACE_REQ_NDV) {
-            any_hll = true;
+            br.smem[kClassGeneral] = std::max(br.smem[kClassGeneral], rp.hll.p <= 16 ? (1u << rp.hll.p) : 0u);
         }
     }
-    if (any_hll) br.smem = std::max(br.smem, kHllSmem);
     br.jobs.clear();
     for (ReqPlan& rp : rps) emit_jobs(rp, dws, bstatus, br.jobs);
     for (ReqPlan& rp : rps) {
@@ -371,10 +484,19 @@ gace_status build_batch(gace_ctx* ctx, std::vector<ReqPlan>& rps, uint64_t chunk
     }
     if (!jobs.empty()) memcpy(pin + br.jobs_off, jobs.data(), jobs.size() * sizeof(BatchJob));
     if (!br.items.empty()) memcpy(pin + br.items_off, br.items.data(), br.items.size() * sizeof(BatchItem));
-    const int occ = batch_occupancy(br.smem);
-    if (occ < 1) return fail(GACE_ECUDA, "batch kernel cannot be resident with %u bytes of shared memory", br.smem);
-    const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ) : occ;
-    br.grid = std::max(1, ctx->sms * per_sm);
+    for (int c = 0; c < kClasses; ++c) {
+        uint32_t items = 0;
+        for (int ph = 0; ph < kPhases; ++ph) {
+            items = std::max(items, br.pcnt[ph][c]);
+            br.launches += br.pcnt[ph][c] > 0;
+        }
+        if (!items) continue;
+        const int occ = batch_occupancy(br.smem[c], c);
+        if (occ < 1)
+            return fail(GACE_ECUDA, "batch kernel cannot be resident with %u bytes of shared memory", br.smem[c]);
+        const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ) : occ;
+        br.grid[c] = std::max(1, ctx->sms * per_sm);
+    }
     return GACE_OK;
 }
 
@@ -388,12 +510,13 @@ cudaError_t enqueue_batch(gace_ctx* ctx, const BatchRun& br, cudaStream_t s) {
     const BatchItem* items = reinterpret_cast<const BatchItem*>(dws + br.items_off);
     const BatchJob* jobs = reinterpret_cast<const BatchJob*>(dws + br.jobs_off);
     unsigned int* heads = reinterpret_cast<unsigned int*>(dws + br.small_base + 256);
-    for (int ph = 0; ph < kPhases; ++ph) {
-        if (!br.pcnt[ph]) continue;
-        if ((e = batch_launch(items + br.pbeg[ph], br.pcnt[ph], jobs, heads + ph, br.grid, br.smem, s)) !=
-            cudaSuccess)
-            return e;
-    }
+    for (int ph = 0; ph < kPhases; ++ph)
+        for (int c = 0; c < kClasses; ++c) {
+            if (!br.pcnt[ph][c]) continue;
+            if ((e = batch_launch(items + br.pbeg[ph][c], br.pcnt[ph][c], jobs, heads + ph * kClasses + c,
+                                  br.grid[c], br.smem[c], c, s)) != cudaSuccess)
+                return e;
+        }
     return cudaMemcpyAsync(pin + br.small_base, dws + br.small_base, br.small_end - br.small_base,
                            cudaMemcpyDeviceToHost, s);
 }
@@ -402,11 +525,14 @@ cudaError_t enqueue_batch(gace_ctx* ctx, const BatchRun& br, cudaStream_t s) {
 // new capture), or eagerly; waits for it.
 gace_status exec_batch(gace_ctx* ctx, const BatchRun& br, bool use_graph) {
     std::vector<uint64_t> key = {reinterpret_cast<uint64_t>(ctx->ws), reinterpret_cast<uint64_t>(ctx->pin),
-                                 br.jobs_off, br.items_off, br.in_end, br.small_base, br.small_end, br.end,
-                                 br.smem, static_cast<uint64_t>(br.grid)};
-    for (int ph = 0; ph < kPhases; ++ph) {
-        key.push_back(br.pbeg[ph]);
-        key.push_back(br.pcnt[ph]);
+                                 br.jobs_off, br.items_off, br.in_end, br.small_base, br.small_end, br.end};
+    for (int c = 0; c < kClasses; ++c) {
+        key.push_back(br.smem[c]);
+        key.push_back(static_cast<uint64_t>(br.grid[c]));
+        for (int ph = 0; ph < kPhases; ++ph) {
+            key.push_back(br.pbeg[ph][c]);
+            key.push_back(br.pcnt[ph][c]);
+        }
     }
     auto launch = [&]() -> cudaError_t {
         if (!use_graph) return enqueue_batch(ctx, br, ctx->stream);
@@ -440,7 +566,7 @@ gace_status exec_batch(gace_ctx* ctx, const BatchRun& br, bool use_graph) {
         return cudaGraphLaunch(ctx->graph_exec, ctx->stream);
     };
     CK(ctx->traced("batch", br.rows, br.bytes, br.ops, launch));
-    ctx->stats["batch_kernel"].launches += (br.pcnt[0] > 0) + (br.pcnt[1] > 0) + (br.pcnt[2] > 0);
+    ctx->stats["batch_kernel"].launches += br.launches;
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->collect();
     return GACE_OK;
@@ -453,7 +579,7 @@ gace_status exec_batch(gace_ctx* ctx, const BatchRun& br, bool use_graph) {
 // its probe and HLL jobs reported to.
 void finish_request(gace_ctx* ctx, ReqPlan& rp, const unsigned char* host_base, unsigned int status) {
     const unsigned __int128 lim = static_cast<unsigned __int128>(1) << 63;
-    if (rp.status != GACE_OK) return;
+    if (rp.status != GACE_OK || rp.fused >= 0) return;
     if (rp.kind != GACE_REQ_JOIN && status) {
         rp.status = read_status(ctx, status);
         rp.error = gace_last_error();
@@ -504,19 +630,73 @@ void finish_batch(gace_ctx* ctx, std::vector<ReqPlan>& rps, const BatchRun& br) 
     for (ReqPlan& rp : rps) finish_request(ctx, rp, ctx->pin, bst);
 }
 
-gace_status compile_all(gace_ctx* ctx, const gace_request* reqs, uint32_t n, std::vector<ReqPlan>& rps) {
+// Plans of a batch: probes on one table are fused greedily in request order
+// (the fused plans follow the n requests' own entries in rps); a fused
+// request that does not compile is undone and its members compiled alone,
+// so each reports its own error.
+gace_status compile_all(gace_ctx* ctx, const gace_request* reqs, uint32_t n, std::vector<ReqPlan>& rps,
+                        std::vector<std::unique_ptr<FusedProbe>>& fused) {
     rps.assign(n, ReqPlan());
+    fused.clear();
+    std::map<uint32_t, size_t> open;  // table -> fused probe still taking members
+    std::vector<bool> alone(n, true);
     for (uint32_t i = 0; i < n; ++i) {
+        if (!fusable_probe(reqs[i])) continue;
+        auto it = open.find(reqs[i].table_id);
+        if (it == open.end() || !fused[it->second]->fits(reqs[i])) {
+            fused.push_back(std::make_unique<FusedProbe>());
+            it = open.insert_or_assign(reqs[i].table_id, fused.size() - 1).first;
+        }
+        fused[it->second]->add(i, reqs[i]);
+        alone[i] = false;
+    }
+    for (size_t f = 0; f < fused.size(); ++f) {
+        FusedProbe& fp = *fused[f];
+        if (fp.members.size() == 1) {  // nothing shared: the request runs as itself
+            alone[fp.members[0].index] = true;
+            continue;
+        }
+        fp.seal();
+        ReqPlan rp;
+        rp.status = compile_request(ctx, fp.q, rp);
+        if (rp.status != GACE_OK) {
+            for (const FusedProbe::Member& m : fp.members) alone[m.index] = true;
+            continue;
+        }
+        for (const FusedProbe::Member& m : fp.members) {
+            rps[m.index].kind = GACE_REQ_PROBE;
+            rps[m.index].q = &reqs[m.index];
+            rps[m.index].fused = static_cast<int>(rps.size());
+        }
+        rps.push_back(std::move(rp));
+    }
+    for (uint32_t i = 0; i < n; ++i) {
+        if (!alone[i]) continue;
         rps[i].status = compile_request(ctx, reqs[i], rps[i]);
         if (rps[i].status != GACE_OK) rps[i].error = gace_last_error();
     }
     return GACE_OK;
 }
 
+// Members of fused probes take the fused request's status and results.
+void finish_fused(std::vector<ReqPlan>& rps, const std::vector<std::unique_ptr<FusedProbe>>& fused, uint32_t n) {
+    for (uint32_t i = 0; i < n; ++i) {
+        ReqPlan& rp = rps[i];
+        if (rp.fused < 0) continue;
+        const ReqPlan& fp = rps[rp.fused];
+        rp.status = fp.status;
+        rp.error = fp.error;
+    }
+    for (const auto& f : fused)
+        if (f->members.size() > 1 && rps[f->members[0].index].fused >= 0 &&
+            rps[rps[f->members[0].index].fused].status == GACE_OK)
+            f->scatter();
+}
+
 std::pair<int, int> shape_key(const std::vector<ReqPlan>& rps) {
     uint64_t njobs = 0, units = 0;
     for (const ReqPlan& rp : rps) {
-        if (rp.status != GACE_OK) continue;
+        if (rp.status != GACE_OK || rp.fused >= 0) continue;
         if (rp.kind == GACE_REQ_PROBE) {
             njobs += rp.plan.passes.size();
             units += rp.plan.passes.size() * rp.plan.tab->nrows;
@@ -531,10 +711,10 @@ std::pair<int, int> shape_key(const std::vector<ReqPlan>& rps) {
     return {log2_bucket(njobs), log2_bucket(units)};
 }
 
-gace_status report(const std::vector<ReqPlan>& rps, gace_status* statuses) {
+gace_status report(const std::vector<ReqPlan>& rps, uint32_t n, gace_status* statuses) {
     gace_status first = GACE_OK;
     std::string msg;
-    for (size_t i = 0; i < rps.size(); ++i) {
+    for (size_t i = 0; i < n; ++i) {
         if (statuses) statuses[i] = rps[i].status;
         if (first == GACE_OK && rps[i].status != GACE_OK) {
             first = rps[i].status;
@@ -574,7 +754,8 @@ gace_status gace_run_batch(gace_ctx* ctx, const gace_request* reqs, uint32_t n, 
     DeviceGuard g(ctx->device);
     if (gace_status s = batch_prologue(ctx, reqs, n)) return s;
     std::vector<ReqPlan> rps;
-    compile_all(ctx, reqs, n, rps);
+    std::vector<std::unique_ptr<FusedProbe>> fused;
+    compile_all(ctx, reqs, n, rps, fused);
     uint64_t chunk = kDefaultChunk;
     int per_sm = 0;
     const auto it = ctx->tune.find(shape_key(rps));
@@ -586,7 +767,8 @@ gace_status gace_run_batch(gace_ctx* ctx, const gace_request* reqs, uint32_t n, 
     if (gace_status st = build_batch(ctx, rps, chunk, per_sm, br)) return st;
     if (gace_status st = exec_batch(ctx, br, true)) return st;
     finish_batch(ctx, rps, br);
-    return report(rps, statuses);
+    finish_fused(rps, fused, n);
+    return report(rps, n, statuses);
 }
 
 gace_status gace_tune_batch(gace_ctx* ctx, const gace_request* reqs, uint32_t n) {
@@ -595,7 +777,8 @@ gace_status gace_tune_batch(gace_ctx* ctx, const gace_request* reqs, uint32_t n)
     DeviceGuard g(ctx->device);
     if (gace_status s = batch_prologue(ctx, reqs, n)) return s;
     std::vector<ReqPlan> rps;
-    compile_all(ctx, reqs, n, rps);
+    std::vector<std::unique_ptr<FusedProbe>> fused;
+    compile_all(ctx, reqs, n, rps, fused);
     const std::pair<int, int> key = shape_key(rps);
     cudaEvent_t a = nullptr, b = nullptr;
     CK(cudaEventCreate(&a));
@@ -634,7 +817,8 @@ gace_status gace_tune_batch(gace_ctx* ctx, const gace_request* reqs, uint32_t n)
     if (gace_status st = build_batch(ctx, rps, best.chunk, best.ctas_per_sm, br)) return st;
     if (gace_status st = exec_batch(ctx, br, false)) return st;
     finish_batch(ctx, rps, br);
-    return report(rps, nullptr);
+    finish_fused(rps, fused, n);
+    return report(rps, n, nullptr);
 }
 
 gace_status gace_tune_save(gace_ctx* ctx, const char* path) {

@@ -1168,7 +1168,7 @@ gace_status gace_join_card(gace_ctx* ctx, const gace_join* spec, gace_join_resul
     const int sms = ctx->sms;
     uint32_t* hD = reinterpret_cast<uint32_t*>(w + hd_off);
     if (spec->hops == 1) {
-        CK(side("join_hist", wd, [&] { return hist_launch(D, hD, 1, 0, sms, ctx->stream); }));
+        CK(side("join_hist", wd, [&] { return hist_launch(D, hD, 1, 1, sms, ctx->stream); }));
         CK(vec("join_max", K, 4, [&] { return max_launch(hD, 0, K, sc + 4, sms, ctx->stream); }));
         if (hist_dot) {
             uint32_t* hF = reinterpret_cast<uint32_t*>(w + hf_off);
@@ -1181,7 +1181,7 @@ gace_status gace_join_card(gace_ctx* ctx, const gace_join* spec, gace_join_resul
         D2.domain = K2;
         D2.pass_count = sc + 2;
         unsigned long long* wk = reinterpret_cast<unsigned long long*>(w + w_off);
-        CK(side("join_hist", wd2, [&] { return hist_launch(D2, hD, 1, 0, sms, ctx->stream); }));
+        CK(side("join_hist", wd2, [&] { return hist_launch(D2, hD, 1, 1, sms, ctx->stream); }));
         CK(vec("join_max", K2, 4, [&] { return max_launch(hD, 0, K2, sc + 4, sms, ctx->stream); }));
         CK(side("join_chain", wd, [&] { return chain_weight_launch(D, fk2_slot, K2, hD, wk, sms, ctx->stream); }));
         CK(vec("join_max", K, 8, [&] { return max_launch(wk, 1, K, sc + 5, sms, ctx->stream); }));

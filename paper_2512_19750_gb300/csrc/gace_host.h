@@ -343,6 +343,8 @@ struct JobRec {
     BatchJob job{};
     uint32_t phase = 0;
     uint64_t units = 0;  // rows, or histogram entries
+    uint64_t granule = 128;  // items start on multiples of this (a narrow pass's tile)
+    int cls = kClassGeneral;  // the persistent kernel that drains its items
     const char* family = "";
     uint64_t rows = 0, bytes = 0, ops = 0;  // statistics
 };
@@ -374,19 +376,57 @@ struct ReqPlan {
     uint64_t pool_off = 0, side_off[3] = {0, 0, 0};  // input region
     uint64_t sc_off = 0;                              // small region: scalars and status
     uint64_t hd_off = 0, w_off = 0, hf_off = 0;       // big region
+    int fused = -1;  // >= 0: absorbed into that fused probe, which runs instead
 };
+
+// Shared scans: probe requests on one table fused into one request whose
+// passes evaluate every member's predicates on the union of their row sets
+// (limits of a narrow pass), so the table's columns are read once.  Counts
+// are exact integers, so each member's results equal its own call's.
+struct FusedProbe {
+    struct Member {
+        uint32_t index = 0;  // the member's position in its batch (or queue)
+        const gace_request* q = nullptr;
+        uint32_t pred_off = 0, term_off = 0;
+        uint32_t set_map[kMaxSets] = {0};
+    };
+    uint32_t table_id = 0;
+    std::vector<gace_sample> samples;
+    std::vector<gace_term> terms;
+    std::vector<gace_scalar> in_values;
+    std::vector<gace_pred> preds;
+    std::vector<gace_pred_result> results;
+    std::vector<uint64_t> marg;
+    std::vector<Member> members;
+    gace_request q{};
+
+    static constexpr uint32_t kMaxIn = 1024;  // IN values of all members
+    // Whether r (a probe on table_id with at most 32 predicates) can join.
+    bool fits(const gace_request& r) const;
+    void add(uint32_t index, const gace_request& r);
+    // Points q at the merged arrays and sizes the result buffers.
+    void seal();
+    // Each member's results and marginals from the fused ones.
+    void scatter() const;
+};
+
+// Whether a probe request is a candidate for fusion.
+bool fusable_probe(const gace_request& r);
 
 // Argument checks and plans of one request.
 gace_status compile_request(gace_ctx* ctx, const gace_request& q, ReqPlan& rp);
+// The same for a probe; with tab set, on that table without a look-up in the
+// context's table map.
+gace_status compile_probe(gace_ctx* ctx, const TableRec* tab, const gace_request& q, ReqPlan& rp);
 // Offsets of a request's data in the input, small-output and big-output regions.
 void place_request(ReqPlan& rp, Ws& win, Ws& wsmall, Ws& wbig);
 // Adds the regions' bases to those offsets.
 void shift_request(ReqPlan& rp, uint64_t in_base, uint64_t small_base, uint64_t big_base);
 // Jobs of a request, with device pointers into the workspace at dws.
 void emit_jobs(ReqPlan& rp, unsigned char* dws, unsigned int* status, std::vector<JobRec>& jobs);
-// Items of `chunk` units per job, ordered by phase.
+// Items of `chunk` units per job, ordered by phase, then class.
 void make_items(const std::vector<JobRec>& jobs, uint64_t chunk, std::vector<BatchItem>& items,
-                uint32_t (&pbeg)[kPhases], uint32_t (&pcnt)[kPhases]);
+                uint32_t (&pbeg)[kPhases][kClasses], uint32_t (&pcnt)[kPhases][kClasses]);
 // A request's outputs from what its small-output region held.
 void finish_request(gace_ctx* ctx, ReqPlan& rp, const unsigned char* host_base, unsigned int status);
 

@@ -74,7 +74,7 @@ struct SetDesc {
     uint32_t share_prev; // 1: same hash input as the previous set (reuse it)
 };
 
-struct ProbeArgs {
+struct alignas(16) ProbeArgs {
     uint64_t nrows;
     uint64_t ntiles;        // ceil(nrows / tile_rows)
     uint64_t nstaged;       // tiles loaded by bulk copy (full tiles when staged)
@@ -100,6 +100,28 @@ struct ProbeArgs {
     unsigned long long* nsamp;   // [nsets]
     unsigned int* status;
 };
+
+#ifdef __CUDACC__
+#define GACE_HD __host__ __device__
+#else
+#define GACE_HD
+#endif
+
+// Which evaluation a pass takes: 0 wide, 1 narrow on all rows, 2 narrow on
+// one hashed set, 3 narrow on several sets with a hashed one, 4 single
+// predicate on all rows, 5 single predicate on one hashed set.
+GACE_HD inline int probe_variant(const ProbeArgs& a) {
+    if (!a.narrow) return 0;
+    bool hash = false;
+    for (uint32_t q = 0; q < a.nsets; ++q)
+        if (a.sets[q].mode == 2) hash = true;
+    // the single evaluation ANDs every term of the pass: only when the one predicate uses them all
+    if (a.npreds == 1 && a.nsets == 1 && a.npredterms == a.nterms) return hash ? 5 : 4;
+    if (!hash) return 1;
+    return a.nsets == 1 ? 2 : 3;
+}
+
+static_assert(sizeof(ProbeArgs) % 16 == 0, "ProbeArgs is copied in 16-byte words");
 
 // Fills the smem layout fields of `a` (given counts) and returns total bytes.
 uint32_t probe_layout(ProbeArgs& a);
@@ -215,10 +237,16 @@ struct CopyDesc {
     uint64_t pad;
 };
 
+// Item classes, each drained by its own persistent kernel: narrow and
+// single-predicate probe items (k_batch_probe), everything else (k_batch).
+constexpr int kClassProbe = 0;
+constexpr int kClassGeneral = 1;
+constexpr int kClasses = 2;
+
 cudaError_t batch_configure(int smem_optin);
-int batch_occupancy(uint32_t smem_bytes);
+int batch_occupancy(uint32_t smem_bytes, int cls);
 cudaError_t batch_launch(const BatchItem* items, uint32_t nitems, const BatchJob* jobs, unsigned int* head,
-                         int grid, uint32_t smem_bytes, cudaStream_t s);
+                         int grid, uint32_t smem_bytes, int cls, cudaStream_t s);
 cudaError_t copy_launch(const CopyDesc* descs, uint32_t n, int grid, cudaStream_t s);
 
 }  // namespace gace

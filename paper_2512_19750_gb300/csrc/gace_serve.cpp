@@ -55,7 +55,7 @@ namespace {
 constexpr uint64_t kDefaultArena = 1ull << 30;
 constexpr uint32_t kDefaultInflight = 4096;
 constexpr int32_t kDefaultSketches = 1024;
-constexpr uint64_t kDefaultStepRows = 1ull << 27;
+constexpr uint64_t kDefaultStepRows = 1ull << 29;
 constexpr uint64_t kDefaultServeChunk = 1ull << 18;
 constexpr uint64_t kCopyPiece = 1ull << 16;    // bytes per scatter / gather descriptor
 constexpr size_t kMaxStepItems = 1u << 16;     // items per step
@@ -130,6 +130,8 @@ struct Live {
     uint64_t ticket = 0;
     OwnedRequest req;
     ReqPlan rp;
+    // tracing: submission, admission, the enqueue of the step with its last chunk
+    uint64_t t_submit = 0, t_admit = 0, t_last = 0;
     uint32_t tables[3] = {0, 0, 0};
     int ntables = 0;
     // block layout (offsets from the block's start)
@@ -154,6 +156,11 @@ struct Live {
     uint32_t sink_index = 0;
     bool cacheable = false;
     bool finished = false;
+    bool fusable = false;  // a probe that may share its table's scan with others
+    // a fused group: the members' predicates run as one request (fp); the
+    // members keep their tickets and table references
+    std::unique_ptr<FusedProbe> fp;
+    std::vector<std::unique_ptr<Live>> members;
 };
 
 struct Done {
@@ -167,18 +174,22 @@ struct Arena {
     void reset(uint64_t bytes) {
         free_.clear();
         if (bytes) free_[0] = bytes;
+        free_bytes = bytes;
     }
+    uint64_t free_bytes = 0;
     uint64_t alloc(uint64_t bytes) {
         for (auto it = free_.begin(); it != free_.end(); ++it) {
             if (it->second < bytes) continue;
             const uint64_t off = it->first, rest = it->second - bytes;
             free_.erase(it);
             if (rest) free_[off + bytes] = rest;
+            free_bytes -= bytes;
             return off;
         }
         return ~0ull;
     }
     void release(uint64_t off, uint64_t bytes) {
+        free_bytes += bytes;
         auto next = free_.lower_bound(off);
         if (next != free_.end() && off + bytes == next->first) {
             bytes += next->second;
@@ -207,7 +218,13 @@ struct StepSet {
     bool busy = false, timed = false;
     std::vector<std::pair<Live*, uint64_t>> finishing;  // request, read-back offset
     uint64_t rows = 0, bytes = 0, ops = 0;
-    uint32_t copies = 0;
+    uint32_t copies = 0, launches = 0;
+    uint64_t t_enqueued = 0;
+};
+
+// Where a served request's time goes (sums over completed requests, ns).
+struct Phases {
+    uint64_t n = 0, queue = 0, run = 0, gpu = 0, finish = 0;
 };
 
 }  // namespace
@@ -230,26 +247,29 @@ struct ServeState {
     std::unordered_map<uint64_t, bool> open;  // submitted, not yet completed
     std::unordered_map<uint32_t, int> table_refs;
     uint64_t next_ticket = 1;
-    uint32_t nlive = 0;
     std::map<SketchKey, Sketch> cache;
     std::list<SketchKey> lru;
     gace_status sticky = GACE_OK;  // a CUDA failure of the scheduler
     std::string sticky_msg;
 
     // scheduler thread only
+    uint32_t nlive = 0;  // admitted requests (members of fused groups counted one by one)
     std::vector<std::unique_ptr<Live>> live;
     StepSet sets[2];
     int64_t step = 0;
     uint64_t rr = 0;
-    std::map<uint32_t, int> occ;  // dynamic shared memory -> CTAs per SM
+    std::map<uint64_t, int> occ;  // (class, dynamic shared memory) -> CTAs per SM
+    Phases phases;                // published with the kernel statistics
 
     void run();
-    bool admit(std::vector<std::unique_ptr<Live>>& admitted, bool& blocked);
+    void take(std::vector<std::unique_ptr<Live>>& cands);
+    void admit(std::vector<std::unique_ptr<Live>>& cands, std::vector<std::unique_ptr<Live>>& admitted,
+               bool& blocked);
     gace_status build_step(StepSet& S, std::vector<std::unique_ptr<Live>>& admitted);
     void complete(StepSet& S);
     void finish(Live& lv, gace_status st, const std::string& err);
     void fail_all(gace_status st, const std::string& msg);
-    int occupancy(uint32_t smem);  // CTAs of the batch kernel per SM
+    int occupancy(uint32_t smem, int cls);  // CTAs of a batch kernel per SM
 };
 
 namespace {
@@ -266,6 +286,7 @@ void layout_request(Live& lv) {
     const uint64_t big_rel = lv.small_rel + round_up(wsmall.off, 256);
     lv.block_bytes = std::max<uint64_t>(256, big_rel + round_up(wbig.off, 256));
     shift_request(lv.rp, 0, lv.small_rel, big_rel);
+    if (lv.fp) return;  // a fused group: its members hold the table references
     const gace_request& q = lv.req.q;
     if (q.kind == GACE_REQ_JOIN) {
         lv.tables[lv.ntables++] = q.join->fact.table_id;
@@ -392,30 +413,101 @@ gace_status alloc_step(StepSet& S, uint64_t up, uint64_t rb) {
 
 }  // namespace
 
-int ServeState::occupancy(uint32_t smem) {
-    auto it = occ.find(smem);
-    return it == occ.end() ? (occ[smem] = batch_occupancy(smem)) : it->second;
+int ServeState::occupancy(uint32_t smem, int cls) {
+    const uint64_t key = (static_cast<uint64_t>(cls) << 32) | smem;
+    auto it = occ.find(key);
+    return it == occ.end() ? (occ[key] = batch_occupancy(smem, cls)) : it->second;
 }
 
-// Admits queued requests in arrival order (the caller holds mu).
-bool ServeState::admit(std::vector<std::unique_ptr<Live>>& admitted, bool& blocked) {
-    while (!pending.empty()) {
-        if (nlive >= cfg.max_inflight) {
-            blocked = true;
-            break;
-        }
-        Live& lv = *pending.front();
-        const uint64_t off = alloc.alloc(lv.block_bytes);
-        if (off == ~0ull) {
-            blocked = true;
-            break;
-        }
-        lv.block = off;
-        ++nlive;
-        admitted.push_back(std::move(pending.front()));
+constexpr size_t kAdmitWindow = 1024;  // queued requests considered per admission round
+
+// Moves queued requests, in arrival order, out of the queue while slots and
+// the arena's free bytes allow (the caller holds mu).
+void ServeState::take(std::vector<std::unique_ptr<Live>>& cands) {
+    uint64_t room = alloc.free_bytes;
+    while (!pending.empty() && cands.size() < kAdmitWindow && nlive + cands.size() < cfg.max_inflight) {
+        if (pending.front()->block_bytes > room) break;
+        room -= pending.front()->block_bytes;
+        cands.push_back(std::move(pending.front()));
         pending.pop_front();
     }
-    return !admitted.empty();
+}
+
+// Admission of the requests taken from the queue: probes on one table are
+// fused (shared scans) and compiled as one request; then blocks are
+// allocated in order, first fit.  What does not fit goes back to the head of
+// the queue.
+void ServeState::admit(std::vector<std::unique_ptr<Live>>& cands, std::vector<std::unique_ptr<Live>>& admitted,
+                       bool& blocked) {
+    std::vector<std::unique_ptr<Live>> units;
+    std::map<uint32_t, Live*> open;  // table -> group still taking members
+    for (auto& c : cands) {
+        if (!c->fusable) {
+            units.push_back(std::move(c));
+            continue;
+        }
+        const uint32_t t = c->req.q.table_id;
+        auto it = open.find(t);
+        if (it == open.end() || !it->second->fp->fits(c->req.q)) {
+            auto grp = std::make_unique<Live>();
+            grp->fp = std::make_unique<FusedProbe>();
+            open[t] = grp.get();
+            units.push_back(std::move(grp));
+            it = open.find(t);
+        }
+        Live& grp = *it->second;
+        grp.fp->add(static_cast<uint32_t>(grp.members.size()), c->req.q);
+        grp.members.push_back(std::move(c));
+    }
+    cands.clear();
+    std::vector<std::unique_ptr<Live>> ready;
+    for (auto& u : units) {
+        if (!u->fp) {
+            ready.push_back(std::move(u));
+            continue;
+        }
+        if (u->members.size() == 1) {  // nothing shared: the request runs with its own plan
+            ready.push_back(std::move(u->members[0]));
+            continue;
+        }
+        u->fp->seal();
+        if (compile_probe(ctx, u->members[0]->rp.plan.tab, u->fp->q, u->rp) != GACE_OK) {
+            for (auto& m : u->members) ready.push_back(std::move(m));  // each runs alone
+            continue;
+        }
+        layout_request(*u);
+        ready.push_back(std::move(u));
+    }
+    size_t i = 0;
+    while (i < ready.size()) {
+        Live& u = *ready[i];
+        const uint64_t off = alloc.alloc(u.block_bytes);
+        if (off == ~0ull) {
+            if (!u.fp) break;
+            // a group that does not fit runs as its members, each of which fits the arena alone
+            std::vector<std::unique_ptr<Live>> ms = std::move(u.members);
+            ready.erase(ready.begin() + static_cast<std::ptrdiff_t>(i));
+            ready.insert(ready.begin() + static_cast<std::ptrdiff_t>(i), std::make_move_iterator(ms.begin()),
+                         std::make_move_iterator(ms.end()));
+            continue;
+        }
+        u.block = off;
+        nlive += u.fp ? static_cast<uint32_t>(u.members.size()) : 1u;
+        admitted.push_back(std::move(ready[i]));
+        ++i;
+    }
+    if (i < ready.size()) {
+        blocked = true;
+        std::vector<std::unique_ptr<Live>> back;
+        for (; i < ready.size(); ++i) {
+            if (ready[i]->fp)
+                for (auto& m : ready[i]->members) back.push_back(std::move(m));
+            else
+                back.push_back(std::move(ready[i]));
+        }
+        std::lock_guard<std::mutex> lk(mu);
+        for (auto it = back.rbegin(); it != back.rend(); ++it) pending.push_front(std::move(*it));
+    }
 }
 
 // A request is done: free its block, drop its table references, complete its ticket.
@@ -423,6 +515,12 @@ void ServeState::finish(Live& lv, gace_status st, const std::string& err) {
     if (lv.block != ~0ull) alloc.release(lv.block, lv.block_bytes);
     lv.block = ~0ull;
     lv.issued_all = true;
+    if (lv.fp) {  // a fused group: every member completes with the group's status
+        if (st == GACE_OK) lv.fp->scatter();
+        for (auto& m : lv.members) finish(*m, st, err);
+        lv.finished = true;
+        return;
+    }
     std::lock_guard<std::mutex> lk(mu);
     for (int i = 0; i < lv.ntables; ++i)
         if (--table_refs[lv.tables[i]] == 0) table_refs.erase(lv.tables[i]);
@@ -464,7 +562,10 @@ gace_status ServeState::build_step(StepSet& S, std::vector<std::unique_ptr<Live>
     for (auto& p : admitted) in_total += round_up(p->in_bytes, 256);
     inbuf.resize(in_total);
     uint64_t pos = 0;
+    const uint64_t t_build = now_ns();
     for (auto& p : admitted) {
+        p->t_admit = t_build;
+        for (auto& m : p->members) m->t_admit = t_build;
         stage_request(*p, inbuf.data() + pos, arena + p->block);
         scat.emplace_back(p.get(), pos);
         pos += round_up(p->in_bytes, 256);
@@ -492,17 +593,18 @@ gace_status ServeState::build_step(StepSet& S, std::vector<std::unique_ptr<Live>
         }
         if (lv.jk < lv.pjobs.size()) ring.push_back(&lv);
     }
-    std::vector<BatchItem> items;
+    std::vector<BatchItem> citems[kClasses];
     std::vector<BatchJob> jobs;
-    uint32_t smem = 0;
+    uint32_t smem[kClasses] = {0, 0};
+    size_t nitems = 0;
     if (!ring.empty()) {
         const size_t n = ring.size();
         const size_t start = static_cast<size_t>(rr++ % n);
         uint64_t budget = cfg.step_rows;
         bool progress = true;
-        while (budget > 0 && progress && items.size() < kMaxStepItems) {
+        while (budget > 0 && progress && nitems < kMaxStepItems) {
             progress = false;
-            for (size_t i = 0; i < n && budget > 0 && items.size() < kMaxStepItems; ++i) {
+            for (size_t i = 0; i < n && budget > 0 && nitems < kMaxStepItems; ++i) {
                 Live& lv = *ring[(start + i) % n];
                 if (lv.jk >= lv.pjobs.size()) continue;
                 if (lv.step_stamp != step) {
@@ -510,17 +612,19 @@ gace_status ServeState::build_step(StepSet& S, std::vector<std::unique_ptr<Live>
                     lv.step_job_base = static_cast<uint32_t>(jobs.size());
                     for (size_t j = 0; j < lv.jobs.size(); ++j) {
                         jobs.push_back(lv.jobs[j].job);
-                        smem = std::max(smem, lv.job_smem[j]);
+                        uint32_t& sm = smem[lv.jobs[j].cls];
+                        sm = std::max(sm, lv.job_smem[j]);
                     }
                 }
                 const uint32_t j = lv.pjobs[lv.jk];
                 const JobRec& jr = lv.jobs[j];
-                const uint64_t b = lv.unit, e = std::min(jr.units, b + chunk);
+                const uint64_t b = lv.unit, e = std::min(jr.units, b + round_up(chunk, jr.granule));
                 BatchItem it{};
                 it.job = lv.step_job_base + j;
                 it.begin = b;
                 it.end = e;
-                items.push_back(it);
+                citems[jr.cls].push_back(it);
+                ++nitems;
                 S.rows += (e - b) * (jr.rows / jr.units);
                 S.bytes += (e - b) * (jr.bytes / jr.units);
                 S.ops += (e - b) * (jr.ops / jr.units);
@@ -538,11 +642,14 @@ gace_status ServeState::build_step(StepSet& S, std::vector<std::unique_ptr<Live>
             }
         }
     }
-    if (scat.empty() && items.empty() && S.finishing.empty()) return GACE_OK;
-    // upload layout: [queue head | inputs | items | jobs | scatter | gather]
+    if (scat.empty() && nitems == 0 && S.finishing.empty()) return GACE_OK;
+    // upload layout: [queue heads | inputs | items by class | jobs | scatter | gather]
     Ws u;
     u.take(256);
     const uint64_t in_off = u.take(in_total);
+    std::vector<BatchItem> items;
+    items.reserve(nitems);
+    for (int c = 0; c < kClasses; ++c) items.insert(items.end(), citems[c].begin(), citems[c].end());
     const uint64_t items_off = u.take(items.size() * sizeof(BatchItem));
     const uint64_t jobs_off = u.take(jobs.size() * sizeof(BatchJob));
     size_t nscat = 0, ngath = 0;
@@ -579,15 +686,23 @@ gace_status ServeState::build_step(StepSet& S, std::vector<std::unique_ptr<Live>
         ++S.copies;
     }
     S.timed = !items.empty();
+    S.launches = 0;
     if (!items.empty()) {
-        const int per_sm = occupancy(smem);
-        if (per_sm < 1)
-            return fail(GACE_ECUDA, "batch kernel cannot be resident with %u bytes of shared memory", smem);
-        const int grid = std::min<int>(per_sm * ctx->sms, static_cast<int>(items.size()));
         CK(cudaEventRecord(S.k0, stream));
-        CK(batch_launch(reinterpret_cast<const BatchItem*>(S.dev + items_off), static_cast<uint32_t>(items.size()),
-                        reinterpret_cast<const BatchJob*>(S.dev + jobs_off), reinterpret_cast<unsigned int*>(S.dev),
-                        grid, smem, stream));
+        size_t first = 0;
+        for (int c = 0; c < kClasses; ++c) {
+            const size_t cnt = citems[c].size();
+            if (!cnt) continue;
+            const int per_sm = occupancy(smem[c], c);
+            if (per_sm < 1)
+                return fail(GACE_ECUDA, "batch kernel cannot be resident with %u bytes of shared memory", smem[c]);
+            const int grid = static_cast<int>(std::min<size_t>(static_cast<size_t>(per_sm) * ctx->sms, cnt));
+            CK(batch_launch(reinterpret_cast<const BatchItem*>(S.dev + items_off) + first, static_cast<uint32_t>(cnt),
+                            reinterpret_cast<const BatchJob*>(S.dev + jobs_off),
+                            reinterpret_cast<unsigned int*>(S.dev) + c, grid, smem[c], c, stream));
+            first += cnt;
+            ++S.launches;
+        }
         CK(cudaEventRecord(S.k1, stream));
     }
     if (ngath) {
@@ -598,6 +713,11 @@ gace_status ServeState::build_step(StepSet& S, std::vector<std::unique_ptr<Live>
     if (rb_total) CK(cudaMemcpyAsync(S.rb_host, S.rb_dev, rb_total, cudaMemcpyDeviceToHost, stream));
     CK(cudaEventRecord(S.done, stream));
     S.busy = true;
+    S.t_enqueued = now_ns();
+    for (auto& f : S.finishing) {
+        f.first->t_last = S.t_enqueued;
+        for (auto& m : f.first->members) m->t_last = S.t_enqueued;
+    }
     ++step;
     return GACE_OK;
 }
@@ -611,19 +731,9 @@ void ServeState::complete(StepSet& S) {
         return;
     }
     S.busy = false;
+    const uint64_t t_detect = now_ns();
     float ms = 0.f;
     if (S.timed) cudaEventElapsedTime(&ms, S.k0, S.k1);
-    {
-        std::lock_guard<std::mutex> lk(ctx->mu);
-        gace_ctx::KStat& k = ctx->stats["serve_step"];
-        k.launches += S.timed ? 1 : 0;
-        k.rows += S.rows;
-        k.bytes += S.bytes;
-        k.ops += S.ops;
-        if (ctx->timing) k.ms += ms;
-        if (S.timed) ctx->stats["batch_kernel"].launches += 1;
-        if (S.copies) ctx->stats["serve_copy"].launches += S.copies;
-    }
     for (auto& f : S.finishing) {
         Live& lv = *f.first;
         const unsigned char* rb = S.rb_host + f.second;
@@ -642,8 +752,40 @@ void ServeState::complete(StepSet& S) {
         if (lv.rp.kind == GACE_REQ_NDV && lv.cacheable && !lv.req.q.estimate_out) lv.req.q.estimate_out = &est;
         finish_request(ctx, lv.rp, host_base, status);
         finish(lv, lv.rp.status, lv.rp.error);
+        const uint64_t t_done = now_ns();
+        auto account = [&](const Live& r) {
+            phases.n += 1;
+            phases.queue += r.t_admit - r.t_submit;
+            phases.run += r.t_last - r.t_admit;
+            phases.gpu += t_detect - r.t_last;
+            phases.finish += t_done - t_detect;
+        };
+        if (lv.fp)
+            for (auto& m : lv.members) account(*m);
+        else
+            account(lv);
     }
     S.finishing.clear();
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        gace_ctx::KStat& k = ctx->stats["serve_step"];
+        k.launches += S.timed ? 1 : 0;
+        k.rows += S.rows;
+        k.bytes += S.bytes;
+        k.ops += S.ops;
+        if (ctx->timing) k.ms += ms;
+        if (S.launches) ctx->stats["batch_kernel"].launches += S.launches;
+        if (S.copies) ctx->stats["serve_copy"].launches += S.copies;
+        // request phases: launches = requests, total_ms = summed time
+        const char* names[4] = {"serve_req_queue", "serve_req_run", "serve_req_gpu", "serve_req_finish"};
+        const uint64_t vals[4] = {phases.queue, phases.run, phases.gpu, phases.finish};
+        for (int i = 0; i < 4; ++i) {
+            gace_ctx::KStat& q = ctx->stats[names[i]];
+            q.launches += phases.n;
+            q.ms += vals[i] / 1e6;
+        }
+        phases = Phases();
+    }
     live.erase(std::remove_if(live.begin(), live.end(),
                               [](const std::unique_ptr<Live>& p) { return p->finished; }),
                live.end());
@@ -652,7 +794,7 @@ void ServeState::complete(StepSet& S) {
 void ServeState::run() {
     cudaSetDevice(ctx->device);
     for (;;) {
-        std::vector<std::unique_ptr<Live>> admitted;
+        std::vector<std::unique_ptr<Live>> cands, admitted;
         bool blocked = false, quit = false;
         auto issuable = [&]() {
             for (auto& p : live)
@@ -679,10 +821,12 @@ void ServeState::run() {
                     pending.pop_front();
                 }
             } else if (!quit) {
-                admit(admitted, blocked);
+                take(cands);
+                if (cands.empty() && !pending.empty()) blocked = true;
             }
         }
         if (quit) break;
+        if (!cands.empty()) admit(cands, admitted, blocked);
         if (!admitted.empty() || issuable()) {
             StepSet& S = sets[step & 1];
             if (S.busy) complete(S);
@@ -736,7 +880,9 @@ gace_status start_locked(gace_ctx* ctx, const gace_serve_config* cfg, std::share
     if (c.sketch_cache < 0) c.sketch_cache = 0;
     if (!c.step_rows) c.step_rows = kDefaultStepRows;
     if (!c.chunk_rows) c.chunk_rows = kDefaultServeChunk;
-    if (c.chunk_rows > (1ull << 40)) return fail(GACE_EINVAL, "chunk_rows %llu above 2^40", (unsigned long long)c.chunk_rows);
+    // the kernels count an item's rows in 32-bit shared counters
+    if (c.chunk_rows > (1ull << 30))
+        return fail(GACE_EINVAL, "chunk_rows %llu above 2^30", (unsigned long long)c.chunk_rows);
     s->chunk = round_up(c.chunk_rows, 128);
     c.arena_bytes = round_up(c.arena_bytes, 1 << 20);
     if (!ctx->fits(c.arena_bytes))
@@ -816,6 +962,7 @@ gace_status submit_request(gace_ctx* ctx, const gace_request& req, uint64_t* tic
     lv->req.copy_from(req);
     lv->sink = sink;
     lv->sink_index = idx;
+    lv->t_submit = now_ns();
     const gace_request& q = lv->req.q;
     std::shared_ptr<ServeState> srv;
     std::lock_guard<std::mutex> ck(ctx->mu);
@@ -838,6 +985,7 @@ gace_status submit_request(gace_ctx* ctx, const gace_request& req, uint64_t* tic
     }
     if (gace_status s = compile_request(ctx, q, lv->rp)) return s;
     layout_request(*lv);
+    lv->fusable = fusable_probe(q) && lv->rp.plan.passes.size() <= 1;
     if (lv->block_bytes > srv->cfg.arena_bytes)
         return fail(GACE_ENOMEM, "the request needs %llu bytes of the %llu-byte serving arena",
                     (unsigned long long)lv->block_bytes, (unsigned long long)srv->cfg.arena_bytes);

@@ -153,3 +153,31 @@ def test_empty_batch_and_empty_tables(g, gctx, cuda):
         assert not q[0].results["match"].any() and not q[1].registers.any() and q[1].estimate == 0.0
     finally:
         g.gace_unload(gctx, tid)
+
+
+def test_fused_probes_on_one_table(g, gctx, batched):
+    """Probes on one table run as fused requests (shared scans): more distinct
+    row sets than one request holds, marginals wanted by some members only,
+    and one member with a bad column, which fails alone."""
+    tables, reqs, tids = batched
+    t, tid = tables[3], tids[3]
+    pool = [Sample(FULL), Sample(ROWS, 0.01, 42), Sample(ROWS, 0.1, 7), Sample(BLOCKS, 0.05, 9, 4096),
+            Sample(ROWS, 0.5, 1), Sample(BLOCKS, 0.2, 3, 512), Sample(ROWS, 0.3, 11), Sample(ROWS, 0.7, 12),
+            Sample(BLOCKS, 0.5, 5, 100), Sample(ROWS, 1.0, 2)]
+    rng = np.random.default_rng(17)
+    specs = []
+    for i in range(40):
+        preds = make_predicates(t, int(rng.integers(1, 4)), 1, 3, seed=500 + i)
+        smp = [pool[k] for k in rng.choice(len(pool), int(rng.integers(1, 4)), replace=False)]
+        specs.append((preds, smp, bool(rng.random() < 0.5)))
+    breqs = [g.ProbeRequest(tid, p, s, t.dtypes, marginals=m) for p, s, m in specs]
+    bad = g.ProbeRequest(tid, [[Term(99, RANGE, 0, 1)]], [Sample(FULL)], t.dtypes)
+    st = g.gace_run_batch(gctx, breqs[:20] + [bad] + breqs[20:], raise_on_error=False)
+    assert st[20] == g.GACE_EINVAL and st[:20] + st[21:] == [0] * 40
+    for (preds, smp, m), q in zip(specs, breqs):
+        res, marg = g.gace_probe_batch(gctx, tid, preds, smp, t.dtypes, marginals=m)
+        for f in ("match", "sample_rows", "sel"):
+            assert np.array_equal(q.results[f], res[f])
+        assert np.array_equal(q.results["pcs"], res["pcs"], equal_nan=True)
+        if m:
+            assert np.array_equal(q.marginals, marg)

@@ -161,3 +161,46 @@ def test_destroy_drains_a_running_server(g, served, cuda):
     tickets = [g.gace_submit(ctx, q) for q in breqs]
     assert tickets == sorted(tickets)
     g.gace_destroy(ctx)  # waits for the queued requests, then frees the arena
+
+
+def test_fused_admission(g, sctx, served, cuda):
+    """Probes on one table that queue up while the GPU is busy are admitted
+    together and run as fused requests (shared scans); each member's results
+    equal its own synchronous call's."""
+    import torch
+
+    from workloads import BLOCKS, ROWS, make_predicates
+
+    tables, reqs, tids = served
+    t, tid = tables[4], tids[4]
+    col = torch.arange(2_000_000, dtype=torch.int32, device=cuda)
+    slow = g.gace_load_columns(sctx, [col], borrow=True)
+    pool = [Sample(FULL), Sample(ROWS, 0.01, 42), Sample(ROWS, 0.1, 7), Sample(BLOCKS, 0.05, 9, 4096),
+            Sample(ROWS, 0.5, 1), Sample(BLOCKS, 0.2, 3, 512), Sample(ROWS, 0.3, 11), Sample(ROWS, 0.7, 12),
+            Sample(BLOCKS, 0.5, 5, 100), Sample(ROWS, 1.0, 2)]
+    rng = np.random.default_rng(23)
+    specs = []
+    for i in range(40):
+        preds = make_predicates(t, int(rng.integers(1, 4)), 1, 3, seed=900 + i)
+        smp = [pool[k] for k in rng.choice(len(pool), int(rng.integers(1, 4)), replace=False)]
+        specs.append((preds, smp, bool(rng.random() < 0.5)))
+    g.gace_serve_start(sctx, step_rows=4096, chunk_rows=4096)
+    try:
+        hold = g.ProbeRequest(slow, [[Term(0, RANGE, 0, 1000)]], [Sample(FULL)], [I32])
+        th = g.gace_submit(sctx, hold)
+        breqs = [g.ProbeRequest(tid, p, s, t.dtypes, marginals=m) for p, s, m in specs]
+        tickets = [g.gace_submit(sctx, q) for q in breqs]
+        g.gace_stats_reset(sctx)
+        for tk in tickets + [th]:
+            assert g.gace_poll(sctx, tk, POLL_US)
+        assert int(hold.results["match"][0, 0]) == 1000
+        for (preds, smp, m), q in zip(specs, breqs):
+            res, marg = g.gace_probe_batch(sctx, tid, preds, smp, t.dtypes, marginals=m)
+            for f in ("match", "sample_rows", "sel"):
+                assert np.array_equal(q.results[f], res[f])
+            assert np.array_equal(q.results["pcs"], res["pcs"], equal_nan=True)
+            if m:
+                assert np.array_equal(q.marginals, marg)
+    finally:
+        g.gace_serve_stop(sctx)
+        g.gace_unload(sctx, slow)

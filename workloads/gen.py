@@ -269,4 +269,5 @@ def make_batched(ntables: int = 256, min_rows: int = 10_000, max_rows: int = 50_
             dterms = [Term(dcol[0], RANGE, 0, wd)] if dcol else []
             requests.append({"kind": "join", "fact": t, "dim": d, "fact_terms": fterms, "dim_terms": dterms,
                              "key_domain": key_domain})
+    _cdf_cache.clear()  # one table per (s, domain): do not keep them on the device
     return tables, requests
