@@ -436,6 +436,12 @@ gace_status build_batch(gace_ctx* ctx, std::vector<ReqPlan>& rps, uint64_t chunk
     wsmall.take(512);  // batch status word, queue heads
     for (ReqPlan& rp : rps) place_request(rp, win, wsmall, wbig);
     for (ReqPlan& rp : rps) emit_jobs(rp, nullptr, nullptr, br.jobs);
+    // a light batch is cut finer (down to one tile) so that it still spreads
+    // over every SM: about four items per resident CTA
+    uint64_t work = 0;
+    for (const JobRec& jr : br.jobs) work += jr.units;
+    const uint64_t want = static_cast<uint64_t>(ctx->sms) * 3 * 4;
+    chunk = std::max<uint64_t>(128, std::min(chunk, round_up(work / want, 128)));
     make_items(br.jobs, chunk, br.items, br.pbeg, br.pcnt);
     Ws main;
     br.jobs_off = main.take(std::max<size_t>(1, br.jobs.size()) * sizeof(BatchJob));

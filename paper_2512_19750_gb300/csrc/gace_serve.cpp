@@ -59,6 +59,9 @@ constexpr uint64_t kDefaultStepRows = 1ull << 29;
 constexpr uint64_t kDefaultServeChunk = 1ull << 18;
 constexpr uint64_t kCopyPiece = 1ull << 16;    // bytes per scatter / gather descriptor
 constexpr size_t kMaxStepItems = 1u << 16;     // items per step
+constexpr uint64_t kCtasPerSmGuess = 3;         // resident batch CTAs per SM, for sizing light steps
+constexpr uint64_t kItemsPerCta = 4;
+constexpr uint64_t kSpinNs = 500000;            // busy-wait on a step's completion before sleeping
 
 uint64_t now_ns() {
     return static_cast<uint64_t>(std::chrono::duration_cast<std::chrono::nanoseconds>(
@@ -243,6 +246,7 @@ struct ServeState {
     std::condition_variable cv_work, cv_done;
     bool stop = false;
     std::deque<std::unique_ptr<Live>> pending;
+    std::atomic<uint32_t> npending{0};  // pending.size(), readable without mu
     std::unordered_map<uint64_t, Done> done;
     std::unordered_map<uint64_t, bool> open;  // submitted, not yet completed
     std::unordered_map<uint32_t, int> table_refs;
@@ -431,6 +435,7 @@ void ServeState::take(std::vector<std::unique_ptr<Live>>& cands) {
         cands.push_back(std::move(pending.front()));
         pending.pop_front();
     }
+    npending.store(static_cast<uint32_t>(pending.size()), std::memory_order_relaxed);
 }
 
 // Admission of the requests taken from the queue: probes on one table are
@@ -507,6 +512,7 @@ void ServeState::admit(std::vector<std::unique_ptr<Live>>& cands, std::vector<st
         }
         std::lock_guard<std::mutex> lk(mu);
         for (auto it = back.rbegin(); it != back.rend(); ++it) pending.push_front(std::move(*it));
+        npending.store(static_cast<uint32_t>(pending.size()), std::memory_order_relaxed);
     }
 }
 
@@ -601,6 +607,16 @@ gace_status ServeState::build_step(StepSet& S, std::vector<std::unique_ptr<Live>
         const size_t n = ring.size();
         const size_t start = static_cast<size_t>(rr++ % n);
         uint64_t budget = cfg.step_rows;
+        // A light step (a few small requests) is cut finer, down to one tile,
+        // so that it still spreads over every SM: about kItemsPerCta items per
+        // resident CTA, never more than the configured chunk.
+        uint64_t work = 0;
+        for (Live* lv : ring)
+            for (size_t k = lv->jk; k < lv->pjobs.size() && work < budget; ++k)
+                work += lv->jobs[lv->pjobs[k]].units - (k == lv->jk ? lv->unit : 0);
+        work = std::min(work, budget);
+        const uint64_t want = static_cast<uint64_t>(ctx->sms) * kCtasPerSmGuess * kItemsPerCta;
+        const uint64_t step_chunk = std::max<uint64_t>(128, std::min(chunk, round_up(work / want, 128)));
         bool progress = true;
         while (budget > 0 && progress && nitems < kMaxStepItems) {
             progress = false;
@@ -618,7 +634,7 @@ gace_status ServeState::build_step(StepSet& S, std::vector<std::unique_ptr<Live>
                 }
                 const uint32_t j = lv.pjobs[lv.jk];
                 const JobRec& jr = lv.jobs[j];
-                const uint64_t b = lv.unit, e = std::min(jr.units, b + round_up(chunk, jr.granule));
+                const uint64_t b = lv.unit, e = std::min(jr.units, b + round_up(step_chunk, jr.granule));
                 BatchItem it{};
                 it.job = lv.step_job_base + j;
                 it.begin = b;
@@ -820,6 +836,7 @@ void ServeState::run() {
                     deliver(*this, lv.ticket, lv.sink, lv.sink_index, sticky, sticky_msg);
                     pending.pop_front();
                 }
+                npending.store(0, std::memory_order_relaxed);
             } else if (!quit) {
                 take(cands);
                 if (cands.empty() && !pending.empty()) blocked = true;
@@ -835,11 +852,23 @@ void ServeState::run() {
         }
         StepSet* oldest = sets[step & 1].busy ? &sets[step & 1] : (sets[(step + 1) & 1].busy ? &sets[(step + 1) & 1] : nullptr);
         if (!oldest) continue;
-        if (blocked || cudaEventQuery(oldest->done) != cudaErrorNotReady) {
+        if (blocked) {
             complete(*oldest);
-        } else {
+            continue;
+        }
+        // Nothing to issue: spin on the step for a while (a sleep costs tens of
+        // microseconds of wake-up), leaving as soon as a request arrives.
+        const uint64_t t0 = now_ns();
+        cudaError_t q = cudaEventQuery(oldest->done);
+        while (q == cudaErrorNotReady && npending.load(std::memory_order_relaxed) == 0 && now_ns() - t0 < kSpinNs) {
+            std::this_thread::yield();
+            q = cudaEventQuery(oldest->done);
+        }
+        if (q != cudaErrorNotReady) {
+            complete(*oldest);
+        } else if (npending.load(std::memory_order_relaxed) == 0) {
             std::unique_lock<std::mutex> lk(mu);
-            cv_work.wait_for(lk, std::chrono::microseconds(20), [&]() { return !pending.empty() || stop; });
+            cv_work.wait_for(lk, std::chrono::microseconds(50), [&]() { return !pending.empty() || stop; });
         }
     }
 }
@@ -998,6 +1027,7 @@ gace_status submit_request(gace_ctx* ctx, const gace_request& req, uint64_t* tic
         if (!sink) srv->open[lv->ticket] = true;
         for (int i = 0; i < lv->ntables; ++i) ++srv->table_refs[lv->tables[i]];
         srv->pending.push_back(std::move(lv));
+        srv->npending.store(static_cast<uint32_t>(srv->pending.size()), std::memory_order_relaxed);
     }
     srv->cv_work.notify_one();
     return GACE_OK;
