@@ -59,7 +59,7 @@ def parse_args():
     ap.add_argument("--serve-cap", type=int, default=20000, help="requests per rate at most")
     ap.add_argument("--case", default=None,
                     choices=["narrow_i32", "narrow_4xi32", "narrow_rows1pct", "wide_batch", "hll_i32",
-                             "join_gather"],
+                             "join_gather", "batch_mix", "batch_probes", "join_skew"],
                     help="profiling driver: run one kernel family three times on a small (--rows) case")
     return ap.parse_args()
 
@@ -610,6 +610,48 @@ def run_case(args):
         for _ in range(3):
             out = g.gace_join_card(ctx, F, D, 10_000_000)
         print(json.dumps({"case": args.case, "rows": args.rows, "card": out["card"]}))
+        g.gace_destroy(ctx)
+        return
+    if args.case == "batch_probes":
+        # the config-4 probe requests over 16 tables of 1e6..5e7 rows (about 3 GB)
+        from workloads import make_batched
+        tables, reqs = make_batched(ntables=16, min_rows=1_000_000, max_rows=50_000_000, nprobes=600, seed=1005,
+                                    device=dev)
+        reqs = [r for r in reqs if r["kind"] == "probe"]
+        tids = [g.gace_load_columns(ctx, t.columns, borrow=True) for t in tables]
+        for _ in range(2):
+            st = g.gace_run_batch(ctx, to_gace_requests(g, tids, tables, reqs))
+        for r in reqs[:20]:  # the same probes one by one, for the plain kernels
+            g.gace_probe_batch(ctx, tids[r["table"]], r["preds"], r["samples"], tables[r["table"]].dtypes)
+        print(json.dumps({"case": args.case, "requests": len(reqs), "ok": st == [0] * len(reqs)}))
+        g.gace_destroy(ctx)
+        return
+    if args.case == "join_skew":
+        # fact and dimension of 40M rows each, keys Zipf(1.2) over 2^15 values
+        from workloads import I32, Table, uniform_int_column, zipf_column
+        from workloads.gen import _gen
+        gen = _gen(1006, dev)
+        n = args.rows
+        f = Table("f", [zipf_column(n, 1.2, 1 << 15, gen, dev), uniform_int_column(n, 0, 1000, gen, dev)], [I32, I32])
+        d = Table("d", [zipf_column(n, 1.2, 1 << 15, gen, dev), uniform_int_column(n, 0, 1000, gen, dev)], [I32, I32])
+        fid = g.gace_load_columns(ctx, f.columns, borrow=True)
+        did = g.gace_load_columns(ctx, d.columns, borrow=True)
+        F = g.JoinSideSpec(fid, 0, [Term(1, RANGE, 0, 500)], f.dtypes)
+        D = g.JoinSideSpec(did, 0, [Term(1, RANGE, 0, 500)], d.dtypes)
+        for _ in range(3):
+            out = g.gace_join_card(ctx, F, D, 1 << 15)
+        print(json.dumps({"case": args.case, "rows": n, "card": out["card"]}))
+        g.gace_destroy(ctx)
+        return
+    if args.case == "batch_mix":
+        # the config-4 request mix over 32 tables of 1e5..2e7 rows (about 2 GB)
+        from workloads import make_batched
+        tables, reqs = make_batched(ntables=32, min_rows=100_000, max_rows=20_000_000, nprobes=512, seed=1004,
+                                    device=dev)
+        tids = [g.gace_load_columns(ctx, t.columns, borrow=True) for t in tables]
+        for _ in range(2):
+            st = g.gace_run_batch(ctx, to_gace_requests(g, tids, tables, reqs))
+        print(json.dumps({"case": args.case, "requests": len(reqs), "ok": st == [0] * len(reqs)}))
         g.gace_destroy(ctx)
         return
     table, preds, samples = make_workload(args.rows, dev)

@@ -55,11 +55,11 @@ __device__ __forceinline__ void hll_item_t(const HllArgs& H, const BatchItem& it
         const uint32_t m = 1u << H.p;
         for (uint32_t i = tid; i < m / 4; i += kThreads) sregs[i] = 0;
         __syncthreads();
-        hll_groups<true, DT>(H, sregs, first, end, kThreads);
+        hll_groups<true, DT, 2>(H, sregs, first, end, kThreads);
         __syncthreads();
         hll_merge(H, sregs, m, tid, kThreads);
     } else {
-        hll_groups<false, DT>(H, sregs, first, end, kThreads);
+        hll_groups<false, DT, 2>(H, sregs, first, end, kThreads);
     }
 }
 
@@ -93,7 +93,7 @@ __device__ __forceinline__ void side_item(const BatchJob& J, const BatchItem& it
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_batch(const BatchItem* __restrict__ items, uint32_t nitems,
+__global__ void __launch_bounds__(kThreads, 3) k_batch(const BatchItem* __restrict__ items, uint32_t nitems,
                                                     const BatchJob* __restrict__ jobs, unsigned int* head) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint32_t s_item;
@@ -180,6 +180,37 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch_probe(const BatchItem* __
     }
 }
 
+// Join histograms over small key domains: per item, a shared-memory
+// histogram of the item's rows (equal keys of a warp combined first), then
+// its nonzero bins into the job's global histogram.
+__global__ void __launch_bounds__(kHistThreads, 1) k_batch_hist(const BatchItem* __restrict__ items, uint32_t nitems,
+                                                                const BatchJob* __restrict__ jobs,
+                                                                unsigned int* head) {
+    extern __shared__ __align__(16) uint32_t shist[];
+    __shared__ uint32_t s_item;
+    __shared__ unsigned long long scratch[kHistThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(head, 1u);
+        __syncthreads();
+        const uint32_t k = s_item;
+        if (k >= nitems) return;
+        const BatchItem it = items[k];
+        const BatchJob& J = jobs[it.job];
+        const SideArgs& SA = *J.side;
+        const uint32_t K = static_cast<uint32_t>(SA.domain);
+        for (uint32_t i = tid; i < K; i += kHistThreads) shist[i] = 0;
+        __syncthreads();  // also: every thread has read s_item
+        unsigned long long npass = 0, acc = 0;
+        side_groups<0, true>(SA, shist, J.strict, nullptr, 0, 0, nullptr, it.begin / 4 + (tid - lane),
+                             (it.end + 3) / 4, kHistThreads, npass, acc);
+        __syncthreads();
+        hist_merge(shist, J.hist, K, tid, kHistThreads);
+        const unsigned long long tp = block_sum_u64<kHistThreads / 32>(npass, scratch);  // synchronises
+        if (tid == 0 && tp) atomicAdd(SA.pass_count, tp);
+    }
+}
+
 // Scatter / gather of the served form: CTA b takes descriptors b, b + grid, ...
 __global__ void __launch_bounds__(256) k_copy(const CopyDesc* __restrict__ d, uint32_t n) {
     for (uint32_t k = blockIdx.x; k < n; k += gridDim.x) {
@@ -214,16 +245,20 @@ static cudaError_t configure_one(K kernel, int smem_optin) {
 
 cudaError_t batch_configure(int smem_optin) {
     cudaError_t e = configure_one(k_batch, smem_optin);
-    if (e != cudaSuccess) return e;
-    return configure_one(k_batch_probe, smem_optin);
+    if (e == cudaSuccess) e = configure_one(k_batch_probe, smem_optin);
+    if (e == cudaSuccess) e = configure_one(k_batch_hist, smem_optin);
+    return e;
 }
 
 int batch_occupancy(uint32_t smem_bytes, int cls) {
     int n = 0;
-    const cudaError_t e =
-        cls == kClassProbe
-            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_probe, kThreads, smem_bytes)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch, kThreads, smem_bytes);
+    cudaError_t e;
+    if (cls == kClassProbe)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_probe, kThreads, smem_bytes);
+    else if (cls == kClassHist)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_hist, kHistThreads, smem_bytes);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch, kThreads, smem_bytes);
     return e == cudaSuccess ? n : 0;
 }
 
@@ -231,6 +266,8 @@ cudaError_t batch_launch(const BatchItem* items, uint32_t nitems, const BatchJob
                          int grid, uint32_t smem_bytes, int cls, cudaStream_t s) {
     if (cls == kClassProbe)
         k_batch_probe<<<grid, kThreads, smem_bytes, s>>>(items, nitems, jobs, head);
+    else if (cls == kClassHist)
+        k_batch_hist<<<grid, kHistThreads, smem_bytes, s>>>(items, nitems, jobs, head);
     else
         k_batch<<<grid, kThreads, smem_bytes, s>>>(items, nitems, jobs, head);
     return cudaGetLastError();

@@ -55,6 +55,10 @@ int log2_bucket(uint64_t x) {
 
 bool fusable_probe(const gace_request& r) {
     if (r.kind != GACE_REQ_PROBE || !r.samples || r.nsamples == 0 || r.nsamples > kMaxSets) return false;
+    // one predicate on one row set runs the register-only single-predicate
+    // evaluation, cheaper per row than the narrow evaluation a fused group
+    // needs: fusing it would trade its bytes for more instructions per row
+    if (r.npreds <= 1 && r.nsamples <= 1) return false;
     if (r.npreds > static_cast<uint32_t>(kNarrowMax) || r.nterms > static_cast<uint32_t>(kNarrowMax)) return false;
     if (r.nin > FusedProbe::kMaxIn) return false;
     if (r.npreds && (!r.preds || !r.results)) return false;
@@ -78,7 +82,36 @@ bool same_sample(const gace_sample& a, const gace_sample& b) {
 
 }  // namespace
 
-bool FusedProbe::fits(const gace_request& r) const {
+uint64_t probe_colmask(const gace_request& r) {
+    uint64_t m = 0;
+    for (uint32_t t = 0; t < r.nterms; ++t) {
+        if (r.terms[t].col >= 64) return ~0ull;
+        m |= 1ull << r.terms[t].col;
+    }
+    return m;
+}
+
+namespace {
+
+uint32_t mask_rowbytes(uint64_t m, const TableRec& t) {
+    uint32_t b = 0;
+    for (uint32_t c = 0; c < 64; ++c)
+        if (m >> c & 1) b += c < t.cols.size() ? dtype_width(t.cols[c].dtype) : 1000;
+    return b;
+}
+
+}  // namespace
+
+bool FusedProbe::fits(const gace_request& r, const TableRec& t) const {
+    if (!GACE_FUSE) return false;
+    const uint64_t m = probe_colmask(r);
+    if (m == ~0ull || mask_rowbytes(colmask | m, t) > kMaxRowBytes) return false;
+    if (!members.empty()) {
+        if ((m | colmask) != colmask) return false;  // a new column: no saving on it
+        if (r.nsamples != members[0].q->nsamples) return false;
+        for (uint32_t k = 0; k < r.nsamples; ++k)
+            if (!same_sample(r.samples[k], members[0].q->samples[k])) return false;
+    }
     if (preds.size() + r.npreds > static_cast<size_t>(kNarrowMax)) return false;
     if (terms.size() + r.nterms > static_cast<size_t>(kNarrowMax)) return false;
     if (in_values.size() + r.nin > kMaxIn) return false;
@@ -92,7 +125,9 @@ bool FusedProbe::fits(const gace_request& r) const {
     return nsets <= static_cast<size_t>(kMaxSets);
 }
 
-void FusedProbe::add(uint32_t index, const gace_request& r) {
+void FusedProbe::add(uint32_t index, const gace_request& r, const TableRec& t) {
+    tab = &t;
+    colmask |= probe_colmask(r);
     Member m;
     m.index = index;
     m.q = &r;
@@ -279,6 +314,7 @@ void emit_jobs(ReqPlan& rp, unsigned char* dws, unsigned int* batch_status, std:
             jr.job.kind = kJobProbe;
             jr.job.probe = reinterpret_cast<const ProbeArgs*>(dws + rp.args_off[k]);
             jr.units = rp.plan.tab->nrows;
+            jr.smem = ps.args.smem_bytes;
             if (ps.args.narrow) {
                 jr.granule = ps.args.tile_rows;
                 jr.cls = kClassProbe;
@@ -298,6 +334,7 @@ void emit_jobs(ReqPlan& rp, unsigned char* dws, unsigned int* batch_status, std:
         jr.job.hll.regs = reinterpret_cast<uint32_t*>(dws + rp.regs_off);
         jr.job.hll.status = batch_status;
         jr.units = rp.hll.nrows;
+        jr.smem = rp.hll.p <= 16 ? (1u << rp.hll.p) : 0u;
         jr.family = "batch_hll";
         jr.rows = jr.units;
         jr.bytes = jr.units * dtype_width(static_cast<int>(rp.hll.dtype));
@@ -346,13 +383,22 @@ void emit_jobs(ReqPlan& rp, unsigned char* dws, unsigned int* batch_status, std:
         jr.ops = n;
         return jr;
     };
+    // small key domains are histogrammed per CTA in shared memory
+    auto smem_hist = [&](JobRec& jr, uint64_t domain) {
+        if (domain > kSmemHistMax) return;
+        jr.cls = kClassHist;
+        jr.smem = static_cast<uint32_t>(domain) * 4u;
+        jr.granule = round_up(16 * domain, 128);  // at least 16 rows per bin and item
+    };
     // phase 0: the dimension histogram the others read (and the fact histogram)
     JobRec h = side_job(kJobHist, two ? 2 : 1, 0, 1);
     h.job.hist = hd;
+    smem_hist(h, two ? rp.K2 : rp.K);
     jobs.push_back(h);
     if (rp.hist_dot) {
         JobRec hfj = side_job(kJobHistAgg, 0, 0, 0);
         hfj.job.hist = hf;
+        smem_hist(hfj, rp.K);
         jobs.push_back(hfj);
     }
     // its largest entry for the overflow check
@@ -400,7 +446,10 @@ void make_items(const std::vector<JobRec>& jobs, uint64_t chunk, std::vector<Bat
             pbeg[ph][c] = static_cast<uint32_t>(items.size());
             for (uint32_t j = 0; j < jobs.size(); ++j) {
                 if (jobs[j].phase != static_cast<uint32_t>(ph) || jobs[j].cls != c) continue;
-                const uint64_t step = round_up(chunk, jobs[j].granule);
+                // a probe item spans a few tiles, so that its bulk copies overlap
+                const uint64_t piece = jobs[j].cls == kClassProbe ? std::max<uint64_t>(chunk, 4 * jobs[j].granule)
+                                                                  : chunk;
+                const uint64_t step = round_up(piece, jobs[j].granule);
                 for (uint64_t b = 0; b < jobs[j].units; b += step) {
                     BatchItem it{};
                     it.job = j;
@@ -422,8 +471,8 @@ struct BatchRun {
     std::vector<BatchItem> items;
     uint32_t pbeg[kPhases][kClasses] = {}, pcnt[kPhases][kClasses] = {};
     uint64_t jobs_off = 0, items_off = 0, in_end = 0, small_base = 0, small_end = 0, end = 0;
-    uint32_t smem[kClasses] = {0, 0};
-    int grid[kClasses] = {1, 1};
+    uint32_t smem[kClasses] = {0, 0, 0};
+    int grid[kClasses] = {1, 1, 1};
     uint64_t rows = 0, bytes = 0, ops = 0;
     int launches = 0;
 };
@@ -436,11 +485,11 @@ gace_status build_batch(gace_ctx* ctx, std::vector<ReqPlan>& rps, uint64_t chunk
     wsmall.take(512);  // batch status word, queue heads
     for (ReqPlan& rp : rps) place_request(rp, win, wsmall, wbig);
     for (ReqPlan& rp : rps) emit_jobs(rp, nullptr, nullptr, br.jobs);
-    // a light batch is cut finer (down to one tile) so that it still spreads
-    // over every SM: about four items per resident CTA
+    // a light batch is cut finer so that it still spreads over every SM:
+    // about two items per resident CTA
     uint64_t work = 0;
     for (const JobRec& jr : br.jobs) work += jr.units;
-    const uint64_t want = static_cast<uint64_t>(ctx->sms) * 3 * 4;
+    const uint64_t want = static_cast<uint64_t>(ctx->sms) * 3 * 2;
     chunk = std::max<uint64_t>(128, std::min(chunk, round_up(work / want, 128)));
     make_items(br.jobs, chunk, br.items, br.pbeg, br.pcnt);
     Ws main;
@@ -460,19 +509,14 @@ gace_status build_batch(gace_ctx* ctx, std::vector<ReqPlan>& rps, uint64_t chunk
     unsigned int* bstatus = reinterpret_cast<unsigned int*>(dws + br.small_base);
     // inputs: pass tables and argument copies, join sides and pools
     for (ReqPlan& rp : rps) {
-        if (rp.status != GACE_OK || rp.fused >= 0) continue;
-        if (rp.kind == GACE_REQ_PROBE) {
-            for (size_t k = 0; k < rp.plan.passes.size(); ++k) {
-                Pass& ps = rp.plan.passes[k];
-                stage_pass(ps, pin, dws, bstatus);
-                memcpy(pin + rp.args_off[k], &ps.args, sizeof(ProbeArgs));
-                uint32_t& sm = br.smem[ps.args.narrow ? kClassProbe : kClassGeneral];
-                sm = std::max(sm, ps.args.smem_bytes);
-            }
-        } else if (rp.kind == GACE_REQ_NDV) {
-            br.smem[kClassGeneral] = std::max(br.smem[kClassGeneral], rp.hll.p <= 16 ? (1u << rp.hll.p) : 0u);
+        if (rp.status != GACE_OK || rp.fused >= 0 || rp.kind != GACE_REQ_PROBE) continue;
+        for (size_t k = 0; k < rp.plan.passes.size(); ++k) {
+            Pass& ps = rp.plan.passes[k];
+            stage_pass(ps, pin, dws, bstatus);
+            memcpy(pin + rp.args_off[k], &ps.args, sizeof(ProbeArgs));
         }
     }
+    for (const JobRec& jr : br.jobs) br.smem[jr.cls] = std::max(br.smem[jr.cls], jr.smem);
     br.jobs.clear();
     for (ReqPlan& rp : rps) emit_jobs(rp, dws, bstatus, br.jobs);
     for (ReqPlan& rp : rps) {
@@ -644,16 +688,26 @@ gace_status compile_all(gace_ctx* ctx, const gace_request* reqs, uint32_t n, std
                         std::vector<std::unique_ptr<FusedProbe>>& fused) {
     rps.assign(n, ReqPlan());
     fused.clear();
-    std::map<uint32_t, size_t> open;  // table -> fused probe still taking members
     std::vector<bool> alone(n, true);
+    // candidates by table, the requests reading the most columns first (they seed the groups)
+    std::vector<std::pair<uint32_t, const TableRec*>> cand;
     for (uint32_t i = 0; i < n; ++i) {
         if (!fusable_probe(reqs[i])) continue;
-        auto it = open.find(reqs[i].table_id);
-        if (it == open.end() || !fused[it->second]->fits(reqs[i])) {
-            fused.push_back(std::make_unique<FusedProbe>());
-            it = open.insert_or_assign(reqs[i].table_id, fused.size() - 1).first;
-        }
-        fused[it->second]->add(i, reqs[i]);
+        const TableRec* tab = find_table(ctx, reqs[i].table_id);
+        if (tab) cand.emplace_back(i, tab);  // else compiled alone, which reports it
+    }
+    std::stable_sort(cand.begin(), cand.end(), [&](const auto& a, const auto& b) {
+        if (reqs[a.first].table_id != reqs[b.first].table_id) return reqs[a.first].table_id < reqs[b.first].table_id;
+        return __builtin_popcountll(probe_colmask(reqs[a.first])) > __builtin_popcountll(probe_colmask(reqs[b.first]));
+    });
+    size_t table_begin = 0;  // groups of the current table start here in `fused`
+    for (size_t c = 0; c < cand.size(); ++c) {
+        const uint32_t i = cand[c].first;
+        if (c > 0 && reqs[cand[c - 1].first].table_id != reqs[i].table_id) table_begin = fused.size();
+        size_t gi = table_begin;
+        while (gi < fused.size() && !fused[gi]->fits(reqs[i], *cand[c].second)) ++gi;
+        if (gi == fused.size()) fused.push_back(std::make_unique<FusedProbe>());
+        fused[gi]->add(i, reqs[i], *cand[c].second);
         alone[i] = false;
     }
     for (size_t f = 0; f < fused.size(); ++f) {

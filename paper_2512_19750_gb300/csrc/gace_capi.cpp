@@ -418,7 +418,17 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
     for (uint32_t s = 0; s < nslots; ++s)
         if (reinterpret_cast<uintptr_t>(A.slots[s].ptr) & 15u) aligned = false;
     bool staged = A.narrow && aligned && nslots > 0;
+    // At most kStageBudget bytes of stages per CTA, so that three or four CTAs
+    // fit on an SM whatever the referenced columns (a fused pass over many
+    // wide columns would otherwise hold a whole SM's shared memory); rows too
+    // wide for two stages are read with plain loads.
+#ifndef GACE_STAGE_BUDGET_KB
+#define GACE_STAGE_BUDGET_KB 64
+#endif
+    constexpr uint32_t kStageBudget = static_cast<uint32_t>(GACE_STAGE_BUDGET_KB) << 10;
     uint32_t nst = 3;
+    while (staged && nst > 2 && nst * tile_rows * rowbytes > kStageBudget) --nst;
+    if (staged && nst * tile_rows * rowbytes > kStageBudget) staged = false;
     for (;;) {
         A.nstages = staged ? nst : 1;
         A.stage_bytes = staged ? tile_rows * rowbytes : 0;

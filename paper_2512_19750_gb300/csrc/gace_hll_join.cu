@@ -49,8 +49,28 @@ __global__ void __launch_bounds__(kHllThreads, 2) k_hll(const __grid_constant__ 
     }
 }
 
+// h[key] += 1 over a small key domain: a shared-memory histogram per CTA
+// (equal keys of a warp combined first), then its nonzero bins into h.
+__global__ void __launch_bounds__(kHistThreads, 1)
+    k_hist_smem(const __grid_constant__ SideArgs A, uint32_t* hist, int strict) {
+    extern __shared__ __align__(16) uint32_t shist[];
+    __shared__ unsigned long long scratch[kHistThreads / 32];
+    const uint32_t K = static_cast<uint32_t>(A.domain);
+    const int lane = threadIdx.x & 31;
+    for (uint32_t i = threadIdx.x; i < K; i += kHistThreads) shist[i] = 0;
+    __syncthreads();
+    unsigned long long npass = 0, acc = 0;
+    side_groups<0, true>(A, shist, strict, nullptr, 0, 0, nullptr,
+                         static_cast<uint64_t>(blockIdx.x) * kHistThreads + (threadIdx.x - lane), (A.nrows + 3) / 4,
+                         static_cast<uint64_t>(gridDim.x) * kHistThreads, npass, acc);
+    __syncthreads();
+    hist_merge(shist, hist, K, threadIdx.x, kHistThreads);
+    const unsigned long long tp = block_sum_u64<kHistThreads / 32>(npass, scratch);
+    if (threadIdx.x == 0 && tp) atomicAdd(A.pass_count, tp);
+}
+
 template <int MODE, bool AGG>
-__global__ void __launch_bounds__(kJoinThreads)
+__global__ void __launch_bounds__(kJoinThreads, 4)
     k_side(const __grid_constant__ SideArgs A, uint32_t* hist, int strict, const void* weight,
            unsigned long long* out_sum, uint32_t fk2_slot, uint64_t domain2,
            unsigned long long* w64) {
@@ -123,6 +143,18 @@ cudaError_t hll_launch(const HllArgs& a, int sms, cudaStream_t s) {
 
 cudaError_t hist_launch(const SideArgs& a, uint32_t* hist, int strict, int aggregate, int sms,
                         cudaStream_t s) {
+    // small domains over enough rows (each CTA at least 16 rows per bin, so
+    // that its merge stays a small part of its work): shared-memory histograms
+    if (aggregate && a.domain <= kSmemHistMax && a.nrows >= 16 * a.domain * 8) {
+        const uint32_t smem = static_cast<uint32_t>(a.domain) * 4u;
+        cudaError_t e = cudaFuncSetAttribute(k_hist_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        const uint64_t want = a.nrows / (16 * a.domain);
+        const int grid = static_cast<int>(want < static_cast<uint64_t>(sms) ? want : sms);
+        k_hist_smem<<<grid, kHistThreads, smem, s>>>(a, hist, strict);
+        return cudaGetLastError();
+    }
     const int grid = grid_for((a.nrows + 3) / 4, kJoinThreads, sms, 8);
     if (aggregate)
         k_side<0, true><<<grid, kJoinThreads, 0, s>>>(a, hist, strict, nullptr, nullptr, 0, 0, nullptr);

@@ -345,6 +345,7 @@ struct JobRec {
     uint64_t units = 0;  // rows, or histogram entries
     uint64_t granule = 128;  // items start on multiples of this (a narrow pass's tile)
     int cls = kClassGeneral;  // the persistent kernel that drains its items
+    uint32_t smem = 0;        // dynamic shared memory its items need
     const char* family = "";
     uint64_t rows = 0, bytes = 0, ops = 0;  // statistics
 };
@@ -380,9 +381,9 @@ struct ReqPlan {
 };
 
 // Shared scans: probe requests on one table fused into one request whose
-// passes evaluate every member's predicates on the union of their row sets
-// (limits of a narrow pass), so the table's columns are read once.  Counts
-// are exact integers, so each member's results equal its own call's.
+// passes evaluate every member's predicates on their common row sets (limits
+// of a narrow pass), so the table's columns are read once.  Counts are exact
+// integers, so each member's results equal its own call's.
 struct FusedProbe {
     struct Member {
         uint32_t index = 0;  // the member's position in its batch (or queue)
@@ -391,6 +392,8 @@ struct FusedProbe {
         uint32_t set_map[kMaxSets] = {0};
     };
     uint32_t table_id = 0;
+    const TableRec* tab = nullptr;
+    uint64_t colmask = 0;  // columns referenced by the members' terms
     std::vector<gace_sample> samples;
     std::vector<gace_term> terms;
     std::vector<gace_scalar> in_values;
@@ -400,10 +403,19 @@ struct FusedProbe {
     std::vector<Member> members;
     gace_request q{};
 
-    static constexpr uint32_t kMaxIn = 1024;  // IN values of all members
-    // Whether r (a probe on table_id with at most 32 predicates) can join.
-    bool fits(const gace_request& r) const;
-    void add(uint32_t index, const gace_request& r);
+    static constexpr uint32_t kMaxIn = 1024;     // IN values of all members
+#ifndef GACE_FUSE
+#define GACE_FUSE 1
+#endif
+    static constexpr uint32_t kMaxRowBytes = 16;  // bytes per row of the referenced columns: the
+                                                  // pass's tiles still stage
+    // Whether r (a fusable probe on table t) can join: the same row sets as the
+    // group's and no column the group does not read already, so that joining
+    // removes r's whole scan and adds no hashing or counting per row beyond
+    // r's own predicates (the probe kernels are issue-bound, not HBM-bound,
+    // once a pass evaluates many predicates on many row sets).
+    bool fits(const gace_request& r, const TableRec& t) const;
+    void add(uint32_t index, const gace_request& r, const TableRec& t);
     // Points q at the merged arrays and sizes the result buffers.
     void seal();
     // Each member's results and marginals from the fused ones.
@@ -412,6 +424,9 @@ struct FusedProbe {
 
 // Whether a probe request is a candidate for fusion.
 bool fusable_probe(const gace_request& r);
+// The columns a probe's terms reference as a bit mask (~0 when one is >= 64);
+// fused groups are seeded with the requests that read the most columns.
+uint64_t probe_colmask(const gace_request& r);
 
 // Argument checks and plans of one request.
 gace_status compile_request(gace_ctx* ctx, const gace_request& q, ReqPlan& rp);

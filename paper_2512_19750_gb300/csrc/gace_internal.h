@@ -238,10 +238,19 @@ struct CopyDesc {
 };
 
 // Item classes, each drained by its own persistent kernel: narrow and
-// single-predicate probe items (k_batch_probe), everything else (k_batch).
+// single-predicate probe items (k_batch_probe), join histograms over small
+// key domains counted in shared memory (k_batch_hist), everything else
+// (k_batch).
 constexpr int kClassProbe = 0;
 constexpr int kClassGeneral = 1;
-constexpr int kClasses = 2;
+constexpr int kClassHist = 2;
+constexpr int kClasses = 3;
+
+// Key domains up to this many entries are histogrammed per CTA in shared
+// memory (hierarchical atomics: skewed keys do not serialise on one global
+// address), the CTA's nonzero bins then added to the global histogram.
+constexpr uint64_t kSmemHistMax = 1u << 15;
+constexpr int kHistThreads = 1024;
 
 cudaError_t batch_configure(int smem_optin);
 int batch_occupancy(uint32_t smem_bytes, int cls);

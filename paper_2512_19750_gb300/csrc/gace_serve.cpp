@@ -60,7 +60,10 @@ constexpr uint64_t kDefaultServeChunk = 1ull << 18;
 constexpr uint64_t kCopyPiece = 1ull << 16;    // bytes per scatter / gather descriptor
 constexpr size_t kMaxStepItems = 1u << 16;     // items per step
 constexpr uint64_t kCtasPerSmGuess = 3;         // resident batch CTAs per SM, for sizing light steps
-constexpr uint64_t kItemsPerCta = 4;
+constexpr uint64_t kItemsPerCta = 2;
+constexpr uint64_t kMinTilesPerItem = 4;        // a probe item spans a few tiles, so its copies overlap
+constexpr size_t kDirectCopies = 2;             // at most this many blocks moved by plain copies per step
+constexpr uint64_t kDirectBlockMax = 256u << 10;
 constexpr uint64_t kSpinNs = 500000;            // busy-wait on a step's completion before sleeping
 
 uint64_t now_ns() {
@@ -142,7 +145,6 @@ struct Live {
     uint64_t block = ~0ull;  // arena offset once admitted
     // device form, after admission
     std::vector<JobRec> jobs;
-    std::vector<uint32_t> job_smem;
     uint32_t phase_list[kPhases] = {0, 0, 0};
     int nphases = 0;
     // issue state
@@ -320,11 +322,6 @@ void stage_request(Live& lv, unsigned char* pin, unsigned char* dws) {
         for (int i = 0; i < nsides; ++i) memcpy(pin + rp.side_off[i], &rp.side[i], sizeof(SideArgs));
         if (!rp.pool.empty()) memcpy(pin + rp.pool_off, rp.pool.data(), rp.pool.size() * 4);
     }
-    lv.job_smem.assign(lv.jobs.size(), 0);
-    for (size_t j = 0; j < lv.jobs.size(); ++j) {
-        if (rp.kind == GACE_REQ_PROBE) lv.job_smem[j] = rp.plan.passes[j].args.smem_bytes;
-        if (rp.kind == GACE_REQ_NDV && rp.hll.p <= 16) lv.job_smem[j] = 1u << rp.hll.p;
-    }
     lv.nphases = 0;
     for (uint32_t ph = 0; ph < static_cast<uint32_t>(kPhases); ++ph)
         for (const JobRec& jr : lv.jobs)
@@ -445,24 +442,35 @@ void ServeState::take(std::vector<std::unique_ptr<Live>>& cands) {
 void ServeState::admit(std::vector<std::unique_ptr<Live>>& cands, std::vector<std::unique_ptr<Live>>& admitted,
                        bool& blocked) {
     std::vector<std::unique_ptr<Live>> units;
-    std::map<uint32_t, Live*> open;  // table -> group still taking members
+    std::map<uint32_t, std::vector<Live*>> open;  // table -> its groups
+    // fusable probes that read the most columns seed the groups
+    std::stable_sort(cands.begin(), cands.end(), [](const std::unique_ptr<Live>& a, const std::unique_ptr<Live>& b) {
+        const int ca = a->fusable ? __builtin_popcountll(probe_colmask(a->req.q)) : 99;
+        const int cb = b->fusable ? __builtin_popcountll(probe_colmask(b->req.q)) : 99;
+        return ca > cb;
+    });
     for (auto& c : cands) {
         if (!c->fusable) {
             units.push_back(std::move(c));
             continue;
         }
-        const uint32_t t = c->req.q.table_id;
-        auto it = open.find(t);
-        if (it == open.end() || !it->second->fp->fits(c->req.q)) {
-            auto grp = std::make_unique<Live>();
-            grp->fp = std::make_unique<FusedProbe>();
-            open[t] = grp.get();
-            units.push_back(std::move(grp));
-            it = open.find(t);
+        const TableRec& tab = *c->rp.plan.tab;
+        std::vector<Live*>& groups = open[c->req.q.table_id];
+        Live* grp = nullptr;
+        for (Live* g2 : groups)
+            if (g2->fp->fits(c->req.q, tab)) {
+                grp = g2;
+                break;
+            }
+        if (!grp) {
+            auto fresh = std::make_unique<Live>();
+            fresh->fp = std::make_unique<FusedProbe>();
+            grp = fresh.get();
+            groups.push_back(grp);
+            units.push_back(std::move(fresh));
         }
-        Live& grp = *it->second;
-        grp.fp->add(static_cast<uint32_t>(grp.members.size()), c->req.q);
-        grp.members.push_back(std::move(c));
+        grp->fp->add(static_cast<uint32_t>(grp->members.size()), c->req.q, tab);
+        grp->members.push_back(std::move(c));
     }
     cands.clear();
     std::vector<std::unique_ptr<Live>> ready;
@@ -476,7 +484,7 @@ void ServeState::admit(std::vector<std::unique_ptr<Live>>& cands, std::vector<st
             continue;
         }
         u->fp->seal();
-        if (compile_probe(ctx, u->members[0]->rp.plan.tab, u->fp->q, u->rp) != GACE_OK) {
+        if (compile_probe(ctx, u->fp->tab, u->fp->q, u->rp) != GACE_OK) {
             for (auto& m : u->members) ready.push_back(std::move(m));  // each runs alone
             continue;
         }
@@ -601,7 +609,7 @@ gace_status ServeState::build_step(StepSet& S, std::vector<std::unique_ptr<Live>
     }
     std::vector<BatchItem> citems[kClasses];
     std::vector<BatchJob> jobs;
-    uint32_t smem[kClasses] = {0, 0};
+    uint32_t smem[kClasses] = {0, 0, 0};
     size_t nitems = 0;
     if (!ring.empty()) {
         const size_t n = ring.size();
@@ -629,12 +637,14 @@ gace_status ServeState::build_step(StepSet& S, std::vector<std::unique_ptr<Live>
                     for (size_t j = 0; j < lv.jobs.size(); ++j) {
                         jobs.push_back(lv.jobs[j].job);
                         uint32_t& sm = smem[lv.jobs[j].cls];
-                        sm = std::max(sm, lv.job_smem[j]);
+                        sm = std::max(sm, lv.jobs[j].smem);
                     }
                 }
                 const uint32_t j = lv.pjobs[lv.jk];
                 const JobRec& jr = lv.jobs[j];
-                const uint64_t b = lv.unit, e = std::min(jr.units, b + round_up(step_chunk, jr.granule));
+                const uint64_t piece = jr.cls == kClassProbe ? std::max(step_chunk, kMinTilesPerItem * jr.granule)
+                                                             : step_chunk;
+                const uint64_t b = lv.unit, e = std::min(jr.units, b + round_up(piece, jr.granule));
                 BatchItem it{};
                 it.job = lv.step_job_base + j;
                 it.begin = b;
@@ -659,43 +669,74 @@ gace_status ServeState::build_step(StepSet& S, std::vector<std::unique_ptr<Live>
         }
     }
     if (scat.empty() && nitems == 0 && S.finishing.empty()) return GACE_OK;
+    // A light step (a couple of small requests admitted or finishing) copies
+    // their blocks with plain async copies; otherwise one scatter and one
+    // gather launch move every request's data.
+    bool direct_in = scat.size() <= kDirectCopies;
+    for (auto& sp : scat) direct_in = direct_in && sp.first->block_bytes <= kDirectBlockMax;
+    const bool direct_out = S.finishing.size() <= kDirectCopies;
     // upload layout: [queue heads | inputs | items by class | jobs | scatter | gather]
+    // (direct: the inputs are whole block images, zeroed outputs included)
     Ws u;
     u.take(256);
-    const uint64_t in_off = u.take(in_total);
+    uint64_t in_bytes_up = in_total;
+    if (direct_in) {
+        in_bytes_up = 0;
+        for (auto& sp : scat) in_bytes_up += round_up(sp.first->block_bytes, 256);
+    }
+    const uint64_t in_off = u.take(in_bytes_up);
     std::vector<BatchItem> items;
     items.reserve(nitems);
     for (int c = 0; c < kClasses; ++c) items.insert(items.end(), citems[c].begin(), citems[c].end());
     const uint64_t items_off = u.take(items.size() * sizeof(BatchItem));
     const uint64_t jobs_off = u.take(jobs.size() * sizeof(BatchJob));
     size_t nscat = 0, ngath = 0;
-    for (auto& sp : scat)
-        nscat += (sp.first->in_bytes + kCopyPiece - 1) / kCopyPiece +
-                 (sp.first->block_bytes - sp.first->small_rel + kCopyPiece - 1) / kCopyPiece;
-    for (auto& f : S.finishing) ngath += (f.first->small_bytes + kCopyPiece - 1) / kCopyPiece;
+    if (!direct_in)
+        for (auto& sp : scat)
+            nscat += (sp.first->in_bytes + kCopyPiece - 1) / kCopyPiece +
+                     (sp.first->block_bytes - sp.first->small_rel + kCopyPiece - 1) / kCopyPiece;
+    if (!direct_out)
+        for (auto& f : S.finishing) ngath += (f.first->small_bytes + kCopyPiece - 1) / kCopyPiece;
     const uint64_t scat_off = u.take(nscat * sizeof(CopyDesc));
     const uint64_t gath_off = u.take(ngath * sizeof(CopyDesc));
     if (gace_status st = alloc_step(S, u.off, rb_total)) return st;
     std::vector<CopyDesc> sdesc, gdesc;
-    for (auto& sp : scat) {
-        Live& lv = *sp.first;
-        unsigned char* blk = arena + lv.block;
-        add_copies(sdesc, blk, S.dev + in_off + sp.second, lv.in_bytes);
-        add_copies(sdesc, blk + lv.small_rel, nullptr, lv.block_bytes - lv.small_rel);
-    }
-    for (auto& f : S.finishing)
-        add_copies(gdesc, S.rb_dev + f.second, arena + f.first->block + f.first->small_rel, f.first->small_bytes);
+    if (!direct_in)
+        for (auto& sp : scat) {
+            Live& lv = *sp.first;
+            unsigned char* blk = arena + lv.block;
+            add_copies(sdesc, blk, S.dev + in_off + sp.second, lv.in_bytes);
+            add_copies(sdesc, blk + lv.small_rel, nullptr, lv.block_bytes - lv.small_rel);
+        }
+    if (!direct_out)
+        for (auto& f : S.finishing)
+            add_copies(gdesc, S.rb_dev + f.second, arena + f.first->block + f.first->small_rel, f.first->small_bytes);
     if (sdesc.size() != nscat || gdesc.size() != ngath)
         return fail(GACE_ECUDA, "serving step: %zu / %zu copy descriptors, %zu / %zu expected", sdesc.size(),
                     gdesc.size(), nscat, ngath);
     memset(S.host, 0, 256);
-    if (in_total) memcpy(S.host + in_off, inbuf.data(), in_total);
+    std::vector<std::pair<Live*, uint64_t>> images;  // direct: request, offset of its block image
+    if (direct_in) {
+        uint64_t at = in_off;
+        for (auto& sp : scat) {
+            Live& lv = *sp.first;
+            if (lv.in_bytes) memcpy(S.host + at, inbuf.data() + sp.second, lv.in_bytes);
+            memset(S.host + at + lv.in_bytes, 0, lv.block_bytes - lv.in_bytes);
+            images.emplace_back(&lv, at);
+            at += round_up(lv.block_bytes, 256);
+        }
+    } else if (in_total) {
+        memcpy(S.host + in_off, inbuf.data(), in_total);
+    }
     if (!items.empty()) memcpy(S.host + items_off, items.data(), items.size() * sizeof(BatchItem));
     if (!jobs.empty()) memcpy(S.host + jobs_off, jobs.data(), jobs.size() * sizeof(BatchJob));
     if (nscat) memcpy(S.host + scat_off, sdesc.data(), nscat * sizeof(CopyDesc));
     if (ngath) memcpy(S.host + gath_off, gdesc.data(), ngath * sizeof(CopyDesc));
     const int copy_grid = std::max(1, ctx->sms * 4);
     CK(cudaMemcpyAsync(S.dev, S.host, u.off, cudaMemcpyHostToDevice, stream));
+    for (auto& im : images)
+        CK(cudaMemcpyAsync(arena + im.first->block, S.host + im.second, im.first->block_bytes, cudaMemcpyHostToDevice,
+                           stream));
     if (nscat) {
         CK(copy_launch(reinterpret_cast<const CopyDesc*>(S.dev + scat_off), static_cast<uint32_t>(nscat),
                        std::min<int>(copy_grid, static_cast<int>(nscat)), stream));
@@ -725,8 +766,12 @@ gace_status ServeState::build_step(StepSet& S, std::vector<std::unique_ptr<Live>
         CK(copy_launch(reinterpret_cast<const CopyDesc*>(S.dev + gath_off), static_cast<uint32_t>(ngath),
                        std::min<int>(copy_grid, static_cast<int>(ngath)), stream));
         ++S.copies;
+        if (rb_total) CK(cudaMemcpyAsync(S.rb_host, S.rb_dev, rb_total, cudaMemcpyDeviceToHost, stream));
+    } else {
+        for (auto& f : S.finishing)
+            CK(cudaMemcpyAsync(S.rb_host + f.second, arena + f.first->block + f.first->small_rel,
+                               f.first->small_bytes, cudaMemcpyDeviceToHost, stream));
     }
-    if (rb_total) CK(cudaMemcpyAsync(S.rb_host, S.rb_dev, rb_total, cudaMemcpyDeviceToHost, stream));
     CK(cudaEventRecord(S.done, stream));
     S.busy = true;
     S.t_enqueued = now_ns();

@@ -52,37 +52,56 @@ __device__ __forceinline__ void smem_byte_max(uint32_t* words, uint32_t j, uint3
     }
 }
 
-// HLL over groups of four rows g = first, first + stride, ... < end: rank of
-// each value, then a max-update of its register (CTA copy in shared memory
-// when SMEM, else the global 32-bit registers).
+// HLL of one group of four rows starting at row0 (values in v): rank of each
+// value, then a max-update of its register (CTA copy in shared memory when
+// SMEM, else the global 32-bit registers).
 template <bool SMEM, int DT>
+__device__ __forceinline__ void hll_quad(const HllArgs& A, uint32_t* sregs, const Quad& v, uint64_t row0) {
+    const unsigned char* sbytes = reinterpret_cast<const unsigned char*>(sregs);
+    // ranks of the four values first (independent), then the register checks
+    uint32_t j[4], rho[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        hll_rank(canonical_key(DT, v.lo[r], v.hi[r]), A.seedhash, A.p, j[r], rho[r]);
+        if (row0 + r >= A.nrows) rho[r] = 0;  // past the end: never raises a register
+    }
+    if (SMEM) {
+        uint32_t cur[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) cur[r] = *reinterpret_cast<const volatile unsigned char*>(&sbytes[j[r]]);
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            if (rho[r] > cur[r]) smem_byte_max(sregs, j[r], rho[r], A.status);
+    } else {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            if (rho[r] > *reinterpret_cast<volatile uint32_t*>(&A.regs[j[r]])) atomicMax(&A.regs[j[r]], rho[r]);
+    }
+}
+
+// HLL over groups of four rows g = first, first + stride, ... < end; U = 2
+// takes two groups per iteration with both loads issued before either is
+// hashed (the second load may fall past `end`; it is bounded by the table and
+// ignored), for kernels with few warps per SM.
+template <bool SMEM, int DT, int U = 1>
 __device__ __forceinline__ void hll_groups(const HllArgs& A, uint32_t* sregs, uint64_t first, uint64_t end,
                                            uint64_t stride) {
-    const unsigned char* sbytes = reinterpret_cast<const unsigned char*>(sregs);
     constexpr uint32_t width = DT == 1 ? 8 : 4;
-    for (uint64_t g = first; g < end; g += stride) {
-        const uint64_t row0 = g * 4;
-        Quad v;
-        load_quad_global(A.col, width, row0, A.nrows, v);
-        // ranks of the four values first (independent), then the register checks
-        uint32_t j[4], rho[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            hll_rank(canonical_key(DT, v.lo[r], v.hi[r]), A.seedhash, A.p, j[r], rho[r]);
-            if (row0 + r >= A.nrows) rho[r] = 0;  // past the end: never raises a register
+    if (U == 1) {
+        for (uint64_t g = first; g < end; g += stride) {
+            Quad v;
+            load_quad_global(A.col, width, g * 4, A.nrows, v);
+            hll_quad<SMEM, DT>(A, sregs, v, g * 4);
         }
-        if (SMEM) {
-            uint32_t cur[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) cur[r] = *reinterpret_cast<const volatile unsigned char*>(&sbytes[j[r]]);
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-                if (rho[r] > cur[r]) smem_byte_max(sregs, j[r], rho[r], A.status);
-        } else {
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-                if (rho[r] > *reinterpret_cast<volatile uint32_t*>(&A.regs[j[r]])) atomicMax(&A.regs[j[r]], rho[r]);
-        }
+        return;
+    }
+    for (uint64_t g = first; g < end; g += 2 * stride) {
+        const uint64_t g2 = g + stride;
+        Quad v0, v1;
+        load_quad_global(A.col, width, g * 4, A.nrows, v0);
+        load_quad_global(A.col, width, g2 * 4, A.nrows, v1);
+        hll_quad<SMEM, DT>(A, sregs, v0, g * 4);
+        if (g2 < end) hll_quad<SMEM, DT>(A, sregs, v1, g2 * 4);
     }
 }
 
@@ -98,16 +117,26 @@ __device__ __forceinline__ void hll_merge(const HllArgs& A, const uint32_t* sreg
 
 // ---------------------------------------------------------------- join sides
 
-__device__ __forceinline__ void side_pass(const SideArgs& A, uint64_t row0, bool pass[4]) {
+// Filter of two groups of four rows (row0a, row0b): each term's two loads are
+// issued before either is tested.
+__device__ __forceinline__ void side_pass2(const SideArgs& A, uint64_t row0a, uint64_t row0b, bool pa[4],
+                                           bool pb[4]) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) pass[r] = row0 + r < A.nrows;
+    for (int r = 0; r < 4; ++r) {
+        pa[r] = row0a + r < A.nrows;
+        pb[r] = row0b + r < A.nrows;
+    }
     for (uint32_t t = 0; t < A.nterms; ++t) {
         const FilterTerm& ft = A.terms[t];
-        Quad v;
-        load_quad_global(A.slot_ptr[ft.slot], A.slot_dtype[ft.slot] == 1 ? 8 : 4, row0, A.nrows, v);
+        const uint32_t w = A.slot_dtype[ft.slot] == 1 ? 8 : 4;
+        Quad va, vb;
+        load_quad_global(A.slot_ptr[ft.slot], w, row0a, A.nrows, va);
+        load_quad_global(A.slot_ptr[ft.slot], w, row0b, A.nrows, vb);
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
-            pass[r] = pass[r] && term_holds(ft.kind, ft.c, v.lo[r], v.hi[r], A.pool);
+        for (int r = 0; r < 4; ++r) {
+            pa[r] = pa[r] && term_holds(ft.kind, ft.c, va.lo[r], va.hi[r], A.pool);
+            pb[r] = pb[r] && term_holds(ft.kind, ft.c, vb.lo[r], vb.hi[r], A.pool);
+        }
     }
 }
 
@@ -124,53 +153,78 @@ __device__ __forceinline__ void side_keys(const SideArgs& A, uint32_t slot, uint
 
 
 // One side of a join over warp-uniform groups of four rows: gb = first (the
-// warp's first group), first + stride, ... < end, lane l taking group gb + l.
+// warp's first group), first + stride, ... < end, lane l taking group gb + l;
+// two such sweeps per iteration, their loads issued together.
 // MODE 0: h[key] += 1 (AGG: equal keys of a warp combined with match_any);
 // 1: acc += weight32[key]; 2: acc += weight64[key]; 3: w64[key] += h2[fk2].
 // npass counts the rows that pass the filter; a passing row with a key outside
 // [0, domain) sets kStatusKeyDomain when strict.
+template <int MODE, bool AGG>
+__device__ __forceinline__ void side_rows(const SideArgs& A, uint32_t* hist, int strict, const void* weight,
+                                          uint64_t domain2, unsigned long long* w64, const int64_t key[4],
+                                          const int64_t fk2[4], const bool pass_in[4], bool mine,
+                                          unsigned long long& npass, unsigned long long& acc) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const bool pass = pass_in[r] && mine;
+        const bool in_dom = key[r] >= 0 && static_cast<uint64_t>(key[r]) < A.domain;
+        npass += pass ? 1 : 0;
+        if (pass && !in_dom && strict) atomicOr(A.status, kStatusKeyDomain);
+        const bool use = pass && in_dom;
+        if (MODE == 0) {
+            if (AGG) {
+                const unsigned long long k = use ? static_cast<unsigned long long>(key[r]) : ~0ull;
+                const unsigned grp = __match_any_sync(kFullMask, k);
+                if (use && (__ffs(grp) - 1) == lane) atomicAdd(&hist[k], __popc(grp));
+            } else if (use) {
+                atomicAdd(&hist[key[r]], 1u);
+            }
+        } else if (MODE == 1) {
+            if (use) acc += static_cast<const uint32_t*>(weight)[key[r]];
+        } else if (MODE == 2) {
+            if (use) acc += static_cast<const unsigned long long*>(weight)[key[r]];
+        } else {
+            if (use && fk2[r] >= 0 && static_cast<uint64_t>(fk2[r]) < domain2) {
+                const uint32_t h = static_cast<const uint32_t*>(weight)[fk2[r]];
+                if (h) atomicAdd(&w64[key[r]], static_cast<unsigned long long>(h));
+            }
+        }
+    }
+}
+
 template <int MODE, bool AGG>
 __device__ __forceinline__ void side_groups(const SideArgs& A, uint32_t* hist, int strict, const void* weight,
                                             uint32_t fk2_slot, uint64_t domain2, unsigned long long* w64,
                                             uint64_t first, uint64_t end, uint64_t stride,
                                             unsigned long long& npass, unsigned long long& acc) {
     const int lane = threadIdx.x & 31;
-    for (uint64_t gb = first; gb < end; gb += stride) {
-        const uint64_t g = gb + lane;
-        const uint64_t row0 = g * 4;
-        const bool mine = g < end;  // groups past the range read as rows past the table
-        int64_t key[4];
-        side_keys(A, A.key_slot, row0, key);
-        int64_t fk2[4] = {0, 0, 0, 0};
-        if (MODE == 3) side_keys(A, fk2_slot, row0, fk2);
-        bool pass[4];
-        side_pass(A, row0, pass);
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            pass[r] = pass[r] && mine;
-            const bool in_dom = key[r] >= 0 && static_cast<uint64_t>(key[r]) < A.domain;
-            npass += pass[r] ? 1 : 0;
-            if (pass[r] && !in_dom && strict) atomicOr(A.status, kStatusKeyDomain);
-            const bool use = pass[r] && in_dom;
-            if (MODE == 0) {
-                if (AGG) {
-                    const unsigned long long k = use ? static_cast<unsigned long long>(key[r]) : ~0ull;
-                    const unsigned grp = __match_any_sync(kFullMask, k);
-                    if (use && (__ffs(grp) - 1) == lane) atomicAdd(&hist[k], __popc(grp));
-                } else if (use) {
-                    atomicAdd(&hist[key[r]], 1u);
-                }
-            } else if (MODE == 1) {
-                if (use) acc += static_cast<const uint32_t*>(weight)[key[r]];
-            } else if (MODE == 2) {
-                if (use) acc += static_cast<const unsigned long long*>(weight)[key[r]];
-            } else {
-                if (use && fk2[r] >= 0 && static_cast<uint64_t>(fk2[r]) < domain2) {
-                    const uint32_t h = static_cast<const uint32_t*>(weight)[fk2[r]];
-                    if (h) atomicAdd(&w64[key[r]], static_cast<unsigned long long>(h));
-                }
-            }
+    for (uint64_t gb = first; gb < end; gb += 2 * stride) {
+        const uint64_t ga = gb + lane, gc = gb + stride + lane;
+        // groups past the range read as rows past the table (or are ignored)
+        const bool mine_a = ga < end, mine_c = gc < end;
+        int64_t ka[4], kc[4];
+        side_keys(A, A.key_slot, ga * 4, ka);
+        side_keys(A, A.key_slot, gc * 4, kc);
+        int64_t fa[4] = {0, 0, 0, 0}, fc[4] = {0, 0, 0, 0};
+        if (MODE == 3) {
+            side_keys(A, fk2_slot, ga * 4, fa);
+            side_keys(A, fk2_slot, gc * 4, fc);
         }
+        bool pa[4], pc[4];
+        side_pass2(A, ga * 4, gc * 4, pa, pc);
+        side_rows<MODE, AGG>(A, hist, strict, weight, domain2, w64, ka, fa, pa, mine_a, npass, acc);
+        if (gb + stride < end)  // warp-uniform: every lane reaches the match_any of the second sweep
+            side_rows<MODE, AGG>(A, hist, strict, weight, domain2, w64, kc, fc, pc, mine_c, npass, acc);
+    }
+}
+
+// A CTA's shared-memory histogram of K bins into the global one (nonzero bins).
+__device__ __forceinline__ void hist_merge(const uint32_t* shist, uint32_t* ghist, uint32_t K, uint32_t tid,
+                                           uint32_t nthreads) {
+    for (uint32_t i = tid; i < K; i += nthreads) {
+        const uint32_t v = shist[i];
+        if (v) atomicAdd(&ghist[i], v);
     }
 }
 

@@ -170,10 +170,20 @@ def test_fused_probes_on_one_table(g, gctx, batched):
         preds = make_predicates(t, int(rng.integers(1, 4)), 1, 3, seed=500 + i)
         smp = [pool[k] for k in rng.choice(len(pool), int(rng.integers(1, 4)), replace=False)]
         specs.append((preds, smp, bool(rng.random() < 0.5)))
+    # members that share row sets and read a subset of one member's columns: fused
+    def rng_term(c, k):
+        if t.dtypes[c] == I32:
+            return Term(c, RANGE, 10 * k, 10 * k + 50_000)
+        return Term(c, RANGE, -1.0 + 0.1 * k, 0.5 + 0.1 * k)
+    shared = [Sample(ROWS, 0.1, 7), Sample(FULL)]
+    specs.append(([[rng_term(1, 0), rng_term(2, 0), rng_term(3, 0)]], shared, True))
+    for k in range(1, 12):
+        cols = [1 + (k % 3)] if k % 2 else [1, 2 + (k % 2)]
+        specs.append(([[rng_term(c, k) for c in cols], [rng_term(cols[0], k + 1)]], shared, bool(k % 3)))
     breqs = [g.ProbeRequest(tid, p, s, t.dtypes, marginals=m) for p, s, m in specs]
     bad = g.ProbeRequest(tid, [[Term(99, RANGE, 0, 1)]], [Sample(FULL)], t.dtypes)
     st = g.gace_run_batch(gctx, breqs[:20] + [bad] + breqs[20:], raise_on_error=False)
-    assert st[20] == g.GACE_EINVAL and st[:20] + st[21:] == [0] * 40
+    assert st[20] == g.GACE_EINVAL and st[:20] + st[21:] == [0] * len(specs)
     for (preds, smp, m), q in zip(specs, breqs):
         res, marg = g.gace_probe_batch(gctx, tid, preds, smp, t.dtypes, marginals=m)
         for f in ("match", "sample_rows", "sel"):

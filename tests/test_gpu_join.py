@@ -119,3 +119,35 @@ def test_always_false_filter(g, gctx, cuda):
             assert out == {"card": 0, "fact_rows": 0, "dim_rows": 100, "dim2_rows": 0}
     finally:
         g.gace_unload(gctx, fid)
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_skewed_keys_small_domain(g, gctx, orc, cuda, method):
+    """A dimension of 4M rows whose keys are Zipf-skewed over a 4096-key
+    domain (a quarter of the rows on key 0), and a fact of 6M rows over the
+    same domain: the dimension (and, for the dot product, the fact) histogram
+    runs per CTA in shared memory; counts equal the oracle's."""
+    from workloads import I32, zipf_column, uniform_int_column
+    from workloads.gen import _gen
+
+    gen = _gen(4242, cuda)
+    K = 4096
+    dk = zipf_column(4_000_000, 1.3, K, gen, cuda)
+    d1 = uniform_int_column(4_000_000, 0, 100, gen, cuda)
+    fk = zipf_column(6_000_000, 1.1, K, gen, cuda)
+    f1 = uniform_int_column(6_000_000, 0, 100, gen, cuda)
+    assert float((dk == 0).float().mean()) > 0.2
+    d = Table("d", [dk, d1], [I32, I32])
+    f = Table("f", [fk, f1], [I32, I32])
+    did, fid = g.gace_load_columns(gctx, d.columns), g.gace_load_columns(gctx, f.columns)
+    try:
+        for wd, wf in ((100, 100), (30, 70)):
+            dt, ft = [Term(1, RANGE, 0, wd)], [Term(1, RANGE, 0, wf)]
+            out = g.gace_join_card(gctx, g.JoinSideSpec(fid, 0, ft, f.dtypes), g.JoinSideSpec(did, 0, dt, d.dtypes),
+                                   K, None, 0, 0, method)
+            rc, card, fp, dp = orc.join_card(JoinSide(_host(f), 0, ft), JoinSide(_host(d), 0, dt), K)
+            assert rc == 0
+            assert (out["card"], out["fact_rows"], out["dim_rows"]) == (card, fp, dp)
+    finally:
+        g.gace_unload(gctx, did)
+        g.gace_unload(gctx, fid)

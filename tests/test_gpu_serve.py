@@ -184,6 +184,16 @@ def test_fused_admission(g, sctx, served, cuda):
         preds = make_predicates(t, int(rng.integers(1, 4)), 1, 3, seed=900 + i)
         smp = [pool[k] for k in rng.choice(len(pool), int(rng.integers(1, 4)), replace=False)]
         specs.append((preds, smp, bool(rng.random() < 0.5)))
+    # members that share row sets and read a subset of one member's columns: fused
+    def rng_term(c, k):
+        if t.dtypes[c] == I32:
+            return Term(c, RANGE, 10 * k, 10 * k + 50_000)
+        return Term(c, RANGE, -1.0 + 0.1 * k, 0.5 + 0.1 * k)
+    shared = [Sample(ROWS, 0.1, 7), Sample(FULL)]
+    specs.append(([[rng_term(1, 0), rng_term(2, 0), rng_term(3, 0)]], shared, True))
+    for k in range(1, 12):
+        cols = [1 + (k % 3)] if k % 2 else [1, 2 + (k % 2)]
+        specs.append(([[rng_term(c, k) for c in cols], [rng_term(cols[0], k + 1)]], shared, bool(k % 3)))
     g.gace_serve_start(sctx, step_rows=4096, chunk_rows=4096)
     try:
         hold = g.ProbeRequest(slow, [[Term(0, RANGE, 0, 1000)]], [Sample(FULL)], [I32])
