@@ -143,14 +143,14 @@ cudaError_t hll_launch(const HllArgs& a, int sms, cudaStream_t s) {
 
 cudaError_t hist_launch(const SideArgs& a, uint32_t* hist, int strict, int aggregate, int sms,
                         cudaStream_t s) {
-    // small domains over enough rows (each CTA at least 16 rows per bin, so
+    // small domains over enough rows (each CTA at least 4 rows per bin, so
     // that its merge stays a small part of its work): shared-memory histograms
-    if (aggregate && a.domain <= kSmemHistMax && a.nrows >= 16 * a.domain * 8) {
+    if (aggregate && a.domain <= kSmemHistMax && a.nrows >= 4 * a.domain * 16) {
         const uint32_t smem = static_cast<uint32_t>(a.domain) * 4u;
         cudaError_t e = cudaFuncSetAttribute(k_hist_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(smem));
         if (e != cudaSuccess) return e;
-        const uint64_t want = a.nrows / (16 * a.domain);
+        const uint64_t want = a.nrows / (4 * a.domain);
         const int grid = static_cast<int>(want < static_cast<uint64_t>(sms) ? want : sms);
         k_hist_smem<<<grid, kHistThreads, smem, s>>>(a, hist, strict);
         return cudaGetLastError();

@@ -174,9 +174,14 @@ __device__ __forceinline__ void side_rows(const SideArgs& A, uint32_t* hist, int
         const bool use = pass && in_dom;
         if (MODE == 0) {
             if (AGG) {
-                const unsigned long long k = use ? static_cast<unsigned long long>(key[r]) : ~0ull;
-                const unsigned grp = __match_any_sync(kFullMask, k);
-                if (use && (__ffs(grp) - 1) == lane) atomicAdd(&hist[k], __popc(grp));
+                // a domain below 2^32 keeps every key below 0xFFFFFFFF, free to
+                // mark the lanes without a row: a 32-bit match suffices
+                unsigned grp;
+                if (A.domain <= 0xFFFFFFFFull)
+                    grp = __match_any_sync(kFullMask, use ? static_cast<uint32_t>(key[r]) : 0xFFFFFFFFu);
+                else
+                    grp = __match_any_sync(kFullMask, use ? static_cast<unsigned long long>(key[r]) : ~0ull);
+                if (use && (__ffs(grp) - 1) == lane) atomicAdd(&hist[key[r]], __popc(grp));
             } else if (use) {
                 atomicAdd(&hist[key[r]], 1u);
             }
