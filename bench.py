@@ -230,22 +230,48 @@ def run_reference(args, d: Dist):
 
 # ----------------------------------------------------------------- GACE arm
 
+def measured_traffic(fam, rows_per_launch):
+    """DRAM bytes per launch of a kernel family from its committed ncu capture
+    (profiles/roofline_traffic.json: bytes per row of one captured launch,
+    scaled by rows), or None when there is none or the kernel's sources have
+    changed since the capture."""
+    import hashlib
+
+    try:
+        with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
+            rec = json.load(f)
+        if rec.get("kernel") != fam:
+            return None
+        h = hashlib.sha256()
+        for src in rec["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+    except (OSError, ValueError, KeyError):
+        return None
+    if h.hexdigest() != rec["sources_sha256"]:
+        return None
+    return rec["bytes_per_row"] * rows_per_launch
+
+
 def roofline_of(stats, peaks, sms):
     """Roofline object of the kernel family with the most device time."""
     fam, st = max(stats.items(), key=lambda kv: kv[1]["total_ms"])
     sec = st["total_ms"] / 1000.0
+    rows_per_launch = st["rows"] / max(1, st["launches"])
+    traffic = measured_traffic(fam, rows_per_launch)
+    algo_bytes = st["bytes"] / max(1, st["launches"])
     if fam == "probe_wide":
         # compare operations against the INT32 lane peak: SMs x 128 lanes x max clock
         peak = sms * 128 * peaks["sm_max_mhz"] * 1e6 / 1e12
         achieved = st["ops"] / sec / 1e12
         return fam, {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": traffic, "algorithmic_bytes_per_launch": algo_bytes,
                      "work": "compare ops (EQ 1, RANGE 2, IN-k k per row)",
                      "peak_source": f"{sms} SMs x 128 INT32 lanes x {peaks['sm_max_mhz']:.0f} MHz",
                      "launches": st["launches"], "avg_launch_ms": st["total_ms"] / st["launches"]}
     achieved = st["bytes"] / sec / 1e9
     return fam, {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                 "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "algorithmic_bytes_per_launch": algo_bytes,
                  "launches": st["launches"], "avg_launch_ms": st["total_ms"] / st["launches"]}
 
 
