@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -184,11 +185,37 @@ uint32_t in_count(const NTerm& t) {
     return t.kind == kInI64 ? static_cast<uint32_t>(t.in.size() / 2) : static_cast<uint32_t>(t.in.size());
 }
 
-// Upper bound of the pool words a term adds to a pass: its IN values (narrow
-// passes) or its entries in a column table of up to 4x as many entries as
-// values, 2 words per 32-bit key and 4 per 64-bit key (wide passes).
-uint32_t pool_estimate(const NTerm& t) {
-    return 16u * static_cast<uint32_t>(std::max<size_t>(1, t.in.size()));
+// Pool words of one column's tables in a wide pass (an upper bound for a
+// narrow pass, whose pool holds only the IN values): one hash table per group
+// of 32 EQ/IN terms in order, all of one capacity (the next power of two >=
+// twice the largest group's entries, at least 64), one interval tree per full
+// group of 32 range terms (or last group of at least kTreeMin), and one word
+// of alignment.
+uint32_t ColPool::words() const {
+    const uint32_t trees = nr / 32 + (nr % 32 >= kTreeMin ? 1 : 0);
+    uint64_t w = 1;
+    if (!vs.empty()) {
+        uint64_t most = 0;
+        for (size_t g = 0; g < vs.size(); g += 32) {
+            uint64_t n = 0;
+            for (size_t k = g; k < std::min(vs.size(), g + 32); ++k) n += vs[k];
+            most = std::max(most, n);
+        }
+        uint32_t tlog = 6;
+        while ((1ull << tlog) < 2 * most) ++tlog;
+        w += static_cast<uint64_t>((vs.size() + 31) / 32) * (1ull << tlog) * (is64 ? 4u : 2u);
+    }
+    w += static_cast<uint64_t>(trees) * (is64 ? kTreeWords64 : kTreeWords32);
+    return w > 0xFFFFFFFFull ? 0xFFFFFFFFu : static_cast<uint32_t>(w);
+}
+
+void ColPool::add(const NTerm& t) {
+    if (is_in_kind(t.kind))
+        vs.push_back(in_count(t));
+    else if (term_cost(t) == 1)
+        vs.push_back(1);  // a single value: looked up like an EQ term
+    else
+        ++nr;
 }
 
 // Minimum compares a row needs for a term: one for a single value, two for a
@@ -263,6 +290,78 @@ gace_status read_status(gace_ctx* ctx, unsigned int st) {
                     (unsigned long long)(ctx->timeout_ns / 1000000ull));
     if (st & kStatusCasLimit) return fail(GACE_ETIMEDOUT, "a bounded device CAS loop gave up");
     return GACE_OK;
+}
+
+// Order-preserving unsigned key of a column value: the sign bit flipped for
+// integers; for float32 bits, -0 taken as +0, negatives complemented, positives
+// with the sign bit set, and NaN below every key (it is in no range).
+uint64_t value_key(uint64_t bits, uint32_t dtype) {
+    if (dtype == GACE_I32) return static_cast<uint32_t>(bits) ^ 0x80000000u;
+    if (dtype == GACE_I64) return bits ^ 0x8000000000000000ull;
+    uint32_t f = static_cast<uint32_t>(bits);
+    if ((f << 1) == 0) f = 0;
+    if ((f & 0x7FFFFFFFu) > 0x7F800000u) return 0;
+    return (f & 0x80000000u) ? ~f : (f | 0x80000000u);
+}
+
+// Inclusive key interval of a normalised range term.
+std::pair<uint64_t, uint64_t> range_keys(const NTerm& t, uint32_t dtype) {
+    if (dtype == GACE_I32) {
+        const uint32_t lo = static_cast<uint32_t>(t.a), hi = lo + static_cast<uint32_t>(t.b);
+        return {value_key(lo, dtype), value_key(hi, dtype)};
+    }
+    if (dtype == GACE_I64) return {value_key(t.a, dtype), value_key(t.a + t.b, dtype)};
+    return {value_key(t.a, dtype), value_key(t.b, dtype)};
+}
+
+// One group's interval tree (layout in gace_internal.h): endpoints are the
+// intervals' starts and the keys just past their ends; the mask of rank r (r
+// endpoints <= the key) holds the terms whose interval contains endpoint r-1.
+void build_range_tree(const std::vector<std::pair<uint64_t, uint64_t>>& iv, bool is64, uint32_t* out) {
+    const uint64_t kmax = is64 ? ~0ull : 0xFFFFFFFFull;
+    std::vector<uint64_t> e;
+    for (const auto& x : iv) {
+        e.push_back(x.first);
+        if (x.second < kmax) e.push_back(x.second + 1);
+    }
+    std::sort(e.begin(), e.end());
+    e.erase(std::unique(e.begin(), e.end()), e.end());
+    const size_t m = e.size();  // <= 64 for 32 intervals
+    std::vector<uint64_t> sorted(e);
+    sorted.resize(kTreeNodes, kmax);
+    // level-order (1-based) layout of the complete tree whose in-order is `sorted`
+    std::vector<uint64_t> node(kTreeNodes + 1);
+    size_t next = 0;
+    std::function<void(size_t)> fill = [&](size_t i) {
+        if (i > kTreeNodes) return;
+        fill(2 * i);
+        node[i] = sorted[next++];
+        fill(2 * i + 1);
+    };
+    fill(1);
+    uint32_t* masks = out + (is64 ? 2 * kTreeNodes + 2 : kTreeNodes + 1);
+    for (size_t i = 1; i <= kTreeNodes; ++i) {
+        if (is64) {
+            out[2 * (i - 1)] = static_cast<uint32_t>(node[i]);
+            out[2 * (i - 1) + 1] = static_cast<uint32_t>(node[i] >> 32);
+        } else {
+            out[i - 1] = static_cast<uint32_t>(node[i]);
+        }
+    }
+    uint32_t last = 0;
+    for (size_t r = 0; r <= kTreeNodes; ++r) {
+        uint32_t mask = 0;
+        if (r == 0) {
+            mask = 0;
+        } else if (r <= m) {
+            for (size_t k = 0; k < iv.size(); ++k)
+                if (iv[k].first <= e[r - 1] && e[r - 1] <= iv[k].second) mask |= 1u << k;
+            last = mask;
+        } else {
+            mask = last;  // only the largest key reaches past the real endpoints
+        }
+        masks[r] = mask;
+    }
 }
 
 // Builds the device form of a pass and the probe arguments (without pointers).
@@ -380,6 +479,29 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
                         }
                     }
                 }
+            }
+        }
+    }
+    if (!narrow) {
+        // one interval tree per full group of 32 range terms of a column (and
+        // per last group of at least kTreeMin); fewer terms are cheaper by compare
+        for (uint32_t s = 0; s < nslots; ++s) {
+            SlotDesc& sd = A.slots[s];
+            const uint32_t all = sd.rend - sd.rbeg, rem = all % 32;
+            const uint32_t nr = all - (rem >= kTreeMin ? 0 : rem);
+            sd.rtree = nr;
+            if (nr == 0) continue;
+            const bool is64 = sd.dtype == GACE_I64;
+            const uint32_t gw = is64 ? kTreeWords64 : kTreeWords32;
+            if (ps.pool.size() & 1) ps.pool.push_back(0);  // 8-byte aligned key pairs
+            sd.rgroups = (nr + 31) / 32;
+            sd.roff = static_cast<uint32_t>(ps.pool.size());
+            ps.pool.resize(ps.pool.size() + static_cast<size_t>(sd.rgroups) * gw, 0u);
+            for (uint32_t g = 0; g < sd.rgroups; ++g) {
+                std::vector<std::pair<uint64_t, uint64_t>> iv;  // inclusive key intervals
+                for (uint32_t k = 32 * g; k < std::min(nr, 32 * g + 32); ++k)
+                    iv.push_back(range_keys(uterms[order[sd.rbeg + k]], sd.dtype));
+                build_range_tree(iv, is64, ps.pool.data() + sd.roff + static_cast<size_t>(g) * gw);
             }
         }
     }
@@ -659,7 +781,7 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
         Pass cur;
         std::map<uint32_t, bool> in_cur;
         uint32_t pool_words = 0;
-        std::map<uint32_t, bool> cols_cur;
+        std::map<uint32_t, ColPool> cols_cur;  // the pass's columns and their tables
         auto flush = [&]() {
             if (!cur.preds.empty() || !cur.uterms.empty()) passes.push_back(cur);
             cur = Pass();
@@ -667,51 +789,80 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
             cols_cur.clear();
             pool_words = 0;
         };
+        // the pass's columns and pool words with the terms `add` added
+        auto with_terms = [&](const std::vector<uint32_t>& add, std::map<uint32_t, ColPool>& touched) {
+            uint64_t total = pool_words;
+            for (uint32_t u : add) {
+                const uint32_t col = uterms[u].col;
+                auto it = touched.find(col);
+                if (it == touched.end()) {
+                    auto base = cols_cur.find(col);
+                    ColPool c;
+                    if (base != cols_cur.end()) {
+                        c = base->second;
+                    } else {
+                        c.is64 = tab.cols[col].dtype == GACE_I64;
+                    }
+                    it = touched.emplace(col, std::move(c)).first;
+                }
+                it->second.add(uterms[u]);
+            }
+            for (const auto& kv : touched) {
+                auto base = cols_cur.find(kv.first);
+                total += kv.second.words() - (base != cols_cur.end() ? base->second.words() : 0u);
+            }
+            return total;
+        };
+        auto commit = [&](const std::vector<uint32_t>& add, std::map<uint32_t, ColPool>& touched, uint64_t total) {
+            for (uint32_t u : add) {
+                in_cur[u] = true;
+                cur.uterms.push_back(u);
+                u_pass[u] = static_cast<int32_t>(passes.size());
+            }
+            for (auto& kv : touched) cols_cur[kv.first] = std::move(kv.second);
+            pool_words = static_cast<uint32_t>(total);
+        };
         for (uint32_t p = 0; p < npreds; ++p) {
             if (plan.pstate[p] != 0) continue;
             const std::vector<uint32_t>& pu = plan.pred_u[p];
-            uint32_t add_t = 0, add_pool = 0, add_c = 0;
-            for (uint32_t u : pu)
-                if (!in_cur.count(u)) {
-                    ++add_t;
-                    add_pool += pool_estimate(uterms[u]);
-                    if (!cols_cur.count(uterms[u].col)) {
-                        ++add_c;
-                        add_pool += 256;  // smallest table of a new column
-                    }
-                }
             if (pu.size() > kPassTerms) return fail(GACE_EINVAL, "predicate %u has too many terms", p);
+            std::vector<uint32_t> add;
+            for (uint32_t u : pu)
+                if (!in_cur.count(u)) add.push_back(u);
+            std::map<uint32_t, ColPool> touched;
+            uint64_t total = with_terms(add, touched);
             // a predicate too large for a shared pass gets one of its own (a
             // single predicate evaluates IN lists by compare, with no tables)
+            const size_t ncols = cols_cur.size() + std::count_if(touched.begin(), touched.end(), [&](const auto& kv) {
+                                     return !cols_cur.count(kv.first);
+                                 });
             if (!cur.preds.empty() &&
-                (cur.uterms.size() + add_t > kPassTerms || cur.preds.size() + 1 > kPassPreds ||
-                 pool_words + add_pool > kPassPool || cols_cur.size() + add_c > static_cast<size_t>(kMaxSlots)))
+                (cur.uterms.size() + add.size() > kPassTerms || cur.preds.size() + 1 > kPassPreds ||
+                 total > kPassPool || ncols > static_cast<size_t>(kMaxSlots))) {
                 flush();
-            for (uint32_t u : pu)
-                if (!in_cur.count(u)) {
-                    in_cur[u] = true;
-                    cols_cur[uterms[u].col] = true;
-                    cur.uterms.push_back(u);
-                    u_pass[u] = static_cast<int32_t>(passes.size());
-                }
-            pool_words += add_pool;
+                add.assign(pu.begin(), pu.end());
+                touched.clear();
+                total = with_terms(add, touched);
+            }
+            commit(add, touched, total);
             cur.preds.push_back(p);
         }
         // terms whose marginals are wanted but that no device predicate placed
         if (plan.want_marg) {
             for (uint32_t u = 0; u < uterms.size(); ++u) {
                 if (u_pass[u] >= 0) continue;
-                const uint32_t add_c = cols_cur.count(uterms[u].col) ? 0 : 1;
-                const uint32_t add_pool = pool_estimate(uterms[u]) + 256 * add_c;
+                std::vector<uint32_t> add{u};
+                std::map<uint32_t, ColPool> touched;
+                uint64_t total = with_terms(add, touched);
+                const size_t ncols = cols_cur.size() + (cols_cur.count(uterms[u].col) ? 0 : 1);
                 if (!cur.uterms.empty() &&
-                    (cur.uterms.size() + 1 > kPassTerms || pool_words + add_pool > kPassPool ||
-                     cols_cur.size() + add_c > static_cast<size_t>(kMaxSlots)))
+                    (cur.uterms.size() + 1 > kPassTerms || total > kPassPool ||
+                     ncols > static_cast<size_t>(kMaxSlots))) {
                     flush();
-                cur.uterms.push_back(u);
-                in_cur[u] = true;
-                cols_cur[uterms[u].col] = true;
-                pool_words += add_pool;
-                u_pass[u] = static_cast<int32_t>(passes.size());
+                    touched.clear();
+                    total = with_terms(add, touched);
+                }
+                commit(add, touched, total);
             }
         }
         flush();

@@ -232,7 +232,22 @@ struct NTerm {
 gace_status normalize_term(const gace_term& t, int dtype, const gace_scalar* in_values, uint32_t nin, NTerm& out);
 bool is_in_kind(uint32_t k);
 uint32_t in_count(const NTerm& t);
-uint32_t pool_estimate(const NTerm& t);
+
+#ifndef GACE_TREE_MIN
+#define GACE_TREE_MIN 32
+#endif
+// A column's range terms beyond its full groups of 32 use an interval tree only
+// when at least this many (a tree costs about as much as this many compares).
+constexpr uint32_t kTreeMin = GACE_TREE_MIN;
+
+// The tables one column's terms need in a wide pass (pass packing).
+struct ColPool {
+    std::vector<uint32_t> vs;  // entries of each EQ / IN term, in order
+    uint32_t nr = 0;           // multi-value range terms
+    bool is64 = false;         // 64-bit keys
+    void add(const NTerm& t);
+    uint32_t words() const;
+};
 uint64_t term_cost(const NTerm& t);
 DevTerm make_devterm(const NTerm& t, uint32_t pool_off);
 
@@ -247,8 +262,14 @@ gace_status make_set(const gace_sample& s, SetDesc& d);
 
 // ---------------------------------------------------------------- probe plan
 
-constexpr uint32_t kPassTerms = 256;
-constexpr uint32_t kPassPreds = 256;
+#ifndef GACE_PASS_TERMS
+#define GACE_PASS_TERMS 256
+#endif
+#ifndef GACE_PASS_PREDS
+#define GACE_PASS_PREDS 256
+#endif
+constexpr uint32_t kPassTerms = GACE_PASS_TERMS;
+constexpr uint32_t kPassPreds = GACE_PASS_PREDS;
 constexpr uint32_t kPassPool = 16384;  // pool words: IN lists (narrow) or EQ/IN tables (wide)
 
 struct Pass {

@@ -52,7 +52,20 @@ struct SlotDesc {
     uint32_t toff;       // wide passes: pool word offset of the slot's hash tables
     uint32_t tlog;       // log2 of each table's capacity (entries)
     uint32_t ngroups;    // tables (groups of up to 32 EQ/IN terms)
+    uint32_t roff;       // wide passes: pool word offset of the slot's range trees
+    uint32_t rgroups;    // range trees (groups of up to 32 range terms)
+    uint32_t rtree;      // range terms [rbeg, rbeg + rtree) by tree, the rest by compare
 };
+
+// A wide pass's range terms of one column, 32 at a time, as an interval tree:
+// the group's distinct interval endpoints (order-preserving unsigned keys,
+// padded with the largest key to 127) in level order, then the 128 term masks
+// indexed by the number of endpoints <= a key.  A row takes 7 comparisons and
+// one mask load for the whole group.
+constexpr int kTreeLevels = 7;
+constexpr uint32_t kTreeNodes = 127;
+constexpr uint32_t kTreeWords32 = 256;  // 127 keys, 1 pad, 128 masks
+constexpr uint32_t kTreeWords64 = 384;  // 127 key pairs, 2 pad, 128 masks
 
 // Hash of a key into a wide pass's EQ/IN table of 2^tlog entries (host and
 // device build and probe the same tables).

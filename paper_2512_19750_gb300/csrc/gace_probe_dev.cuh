@@ -359,32 +359,141 @@ __device__ __forceinline__ void eval_valueset(const SlotDesc& sd, const Vals<NQ>
 }
 
 
+// Order-preserving unsigned key of one value (the host's value_key): low word
+// in lo, high word in hi (0 unless 64-bit).
+__device__ __forceinline__ void value_key(uint32_t dtype, uint32_t vlo, uint32_t vhi, uint32_t& lo,
+                                          uint32_t& hi) {
+    if (dtype == 0) {
+        lo = vlo ^ 0x80000000u;
+        hi = 0;
+    } else if (dtype == 1) {
+        lo = vlo;
+        hi = vhi ^ 0x80000000u;
+    } else {
+        uint32_t f = (vlo << 1) == 0 ? 0u : vlo;  // -0 is +0
+        if ((f & 0x7FFFFFFFu) > 0x7F800000u)
+            lo = 0;  // NaN: below every range
+        else
+            lo = (f & 0x80000000u) ? ~f : (f | 0x80000000u);
+        hi = 0;
+    }
+}
+
+// Range terms of one column slot in a wide pass: per group of 32, every row
+// descends the group's interval tree (7 levels, level-order keys in shared
+// memory, so a level's lanes read distinct banks) to the number of endpoints
+// <= its key, which indexes the 32-bit mask of the group's terms that contain
+// it; a warp transpose of each row-group's masks hands lane t the 32-row mask
+// of term t.
+template <int NQ>
+__device__ __forceinline__ void eval_range_trees(const SlotDesc& sd, const Vals<NQ>& v, const uint32_t* pool,
+                                                 uint4* tm, int lane) {
+    constexpr int R = 4 * NQ;
+    const bool is64 = sd.dtype == 1;
+    uint32_t klo[R], khi[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) value_key(sd.dtype, v.lo[i], v.hi[i], klo[i], khi[i]);
+    const uint32_t nr = sd.rtree;
+    const uint32_t gw = is64 ? kTreeWords64 : kTreeWords32;
+    for (uint32_t g = 0; g < sd.rgroups; ++g) {
+        const uint32_t* tree = pool + sd.roff + g * gw;
+        const uint32_t* masks = tree + (is64 ? 2 * kTreeNodes + 2 : kTreeNodes + 1);
+        uint32_t w[R];
+        if (is64) {
+            const uint2* node = reinterpret_cast<const uint2*>(tree);
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                uint32_t n = 1;
+#pragma unroll
+                for (int d = 0; d < kTreeLevels; ++d) {
+                    const uint2 e = node[n - 1];
+                    const bool ge = khi[i] > e.y || (khi[i] == e.y && klo[i] >= e.x);
+                    n = 2 * n + (ge ? 1u : 0u);
+                }
+                w[i] = masks[n - (1u << kTreeLevels)];
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                uint32_t n = 1;
+#pragma unroll
+                for (int d = 0; d < kTreeLevels; ++d) n = 2 * n + (klo[i] >= tree[n - 1] ? 1u : 0u);
+                w[i] = masks[n - (1u << kTreeLevels)];
+            }
+        }
+        uint4 out[NQ];
+#pragma unroll
+        for (int h = 0; h < NQ; ++h) {
+            out[h].x = transpose32(w[4 * h + 0], lane);
+            out[h].y = transpose32(w[4 * h + 1], lane);
+            out[h].z = transpose32(w[4 * h + 2], lane);
+            out[h].w = transpose32(w[4 * h + 3], lane);
+        }
+        const uint32_t k = 32u * g + lane;
+        if (k < nr) {
+#pragma unroll
+            for (int h = 0; h < NQ; ++h) tm[(sd.rbeg + k) * NQ + h] = out[h];
+        }
+    }
+}
+
 // The wide pass over warp slices sl = first, first + stride, ... < end of
-// 128 rows each: row-set masks, range terms by compare, EQ and IN terms by
-// table, then lanes take predicates (and terms, for marginals) and add
+// 128 rows each: row-set masks, range terms by interval tree, EQ and IN terms
+// by table, then lanes take predicates (and terms, for marginals) and add
 // popcounts into the CTA's 32-bit counters.  Returns the warp's count of
 // rows in each row set `lane` (lanes < nsets).
 __device__ __forceinline__ uint32_t wide_slices(const ProbeArgs& A, const Smem& S, int lane, uint64_t first,
                                                 uint64_t end, uint64_t stride) {
     uint32_t nsr = 0;
+    // Column loads run one column ahead of the evaluation (and the next
+    // slice's first column is loaded before the counting), so that a warp does
+    // not wait out the memory latency once per column.
+    Vals<1> cur;
+    bool have = false;  // cur holds the current slice's first column
     for (uint64_t sl = first; sl < end; sl += stride) {
         const uint64_t slice0 = sl * kSliceRows;
+        if (!have && A.nslots)
+            load_vals_global<1>(A.slots[0].ptr, A.slots[0].width, slice0, A.nrows, lane, cur);
+        have = false;
         set_masks<1>(A, slice0, S.keep, lane);
+        __syncwarp();
+        // the row sets with a row in this slice (warp-uniform): sparse samples
+        // are empty in most slices, and a slice in no set needs no evaluation
+        uint32_t active = 0;
+        for (uint32_t q = 0; q < A.nsets; ++q) {
+            const uint4 k = S.keep[q];
+            if (k.x | k.y | k.z | k.w) active |= 1u << q;
+        }
+        if (!active) {
+            __syncwarp();  // every lane has read S.keep before lane 0 rewrites it
+            continue;
+        }
+        const uint64_t next = sl + stride;
         for (uint32_t s = 0; s < A.nslots; ++s) {
             const SlotDesc& sd = A.slots[s];
-            Vals<1> v;
-            load_vals_global<1>(sd.ptr, sd.width, slice0, A.nrows, lane, v);
-            SlotDesc ranges = sd;  // ranges by compare; EQ and IN terms by table
-            ranges.iend = sd.rend;
-            eval_slot<1>(ranges, v, S.st, S.pool, S.tm, lane);
-            if (sd.iend > sd.rend) eval_valueset<1>(sd, v, S.pool, S.tm, lane);
+            const Vals<1> v = cur;
+            if (s + 1 < A.nslots) {
+                load_vals_global<1>(A.slots[s + 1].ptr, A.slots[s + 1].width, slice0, A.nrows, lane, cur);
+            } else if (next < end) {
+                load_vals_global<1>(A.slots[0].ptr, A.slots[0].width, next * kSliceRows, A.nrows, lane, cur);
+                have = true;
+            }
+            if (sd.rgroups) eval_range_trees<1>(sd, v, S.pool, S.tm, lane);  // ranges by tree
+            if (sd.rbeg + sd.rtree < sd.rend) {  // the remaining ranges by compare
+                SlotDesc ranges = sd;
+                ranges.rbeg = sd.rbeg + sd.rtree;
+                ranges.iend = sd.rend;
+                eval_slot<1>(ranges, v, S.st, S.pool, S.tm, lane);
+            }
+            if (sd.iend > sd.rend) eval_valueset<1>(sd, v, S.pool, S.tm, lane);  // EQ and IN by table
         }
         __syncwarp();
         for (uint32_t p = lane; p < A.npreds; p += 32) {
             const uint32_t b = S.poff[p], e = S.poff[p + 1];
             uint4 acc = S.tm[S.pterm[b]];
             for (uint32_t k = b + 1; k < e; ++k) acc = and4(acc, S.tm[S.pterm[k]]);
-            for (uint32_t q = 0; q < A.nsets; ++q) {
+            for (uint32_t a = active; a; a &= a - 1) {
+                const uint32_t q = __ffs(a) - 1;
                 const uint32_t c = popc4(acc, S.keep[q]);
                 if (c) atomicAdd(&S.cnt[q * A.npreds + p], c);
             }
@@ -392,7 +501,8 @@ __device__ __forceinline__ uint32_t wide_slices(const ProbeArgs& A, const Smem& 
         if (A.want_marg) {
             for (uint32_t t = lane; t < A.nterms; t += 32) {
                 const uint4 m = S.tm[t];
-                for (uint32_t q = 0; q < A.nsets; ++q) {
+                for (uint32_t a = active; a; a &= a - 1) {
+                    const uint32_t q = __ffs(a) - 1;
                     const uint32_t c = popc4(m, S.keep[q]);
                     if (c) atomicAdd(&S.marg[q * A.nterms + t], c);
                 }
@@ -402,7 +512,7 @@ __device__ __forceinline__ uint32_t wide_slices(const ProbeArgs& A, const Smem& 
             const uint4 k = S.keep[lane];
             nsr += __popc(k.x) + __popc(k.y) + __popc(k.z) + __popc(k.w);
         }
-        __syncwarp();
+        __syncwarp();  // S.keep and S.tm are rewritten by the next slice
     }
     return nsr;
 }

@@ -132,6 +132,19 @@ __device__ __forceinline__ bool narrow_run(const ProbeArgs& A, const Smem& S, in
         uint4 vm[NQ];
         if (HASH) {
             set_masks<NQ>(A, slice0, S.keep, lane);
+            __syncwarp();
+            // a slice with no row in any set adds nothing: skip its evaluation
+            uint32_t any = 0;
+            for (uint32_t q = 0; q < nsets; ++q)
+#pragma unroll
+                for (int h = 0; h < NQ; ++h) {
+                    const uint4 k = S.keep[q * NQ + h];
+                    any |= k.x | k.y | k.z | k.w;
+                }
+            if (!any) {
+                __syncwarp();  // every lane has read S.keep before lane 0 rewrites it
+                return;
+            }
         } else if (!tile_full) {
 #define PV(i) (slice0 + 128u * ((i) / 4) + 4u * lane + ((i) % 4) < A.nrows)
             GACE_BALLOTS(NQ, PV, vm);
@@ -322,6 +335,7 @@ __device__ __forceinline__ bool single_run(const ProbeArgs& A, const Smem& S, in
             GACE_ROWBITS(R, PV, base);
 #undef PV
         }
+        if (HASH && !__any_sync(kFullMask, base != 0u)) return;  // no row of the slice is in the set
         uint32_t ok = base;
         for (uint32_t s = 0; s < A.nslots; ++s) {
             const SlotDesc& sd = A.slots[s];

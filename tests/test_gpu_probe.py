@@ -291,3 +291,43 @@ def test_wide_pass_value_tables(g, gctx, orc, cuda):
                     [Sample(FULL), Sample(ROWS, 0.4, 5), Sample(BLOCKS, 0.5, 5, 128)])
     finally:
         g.gace_unload(gctx, tid)
+
+
+def test_wide_pass_range_trees(g, gctx, orc, cuda):
+    """Wide passes evaluate range terms by per-column interval trees of 32
+    terms: more than 32 overlapping ranges per column (several trees), nested,
+    shared and touching endpoints, unbounded ones, on int32, int64 and float32
+    columns, alone and in conjunctions."""
+    rng = np.random.default_rng(17)
+    n = 100_003
+    i32 = rng.integers(-1000, 1000, n).astype(np.int32)
+    i64 = rng.integers(-1000, 1000, n).astype(np.int64) * (2**34 + 3)
+    f32 = (rng.standard_normal(n) * 10).astype(np.float32)
+    f32[::97] = np.nan
+    f32[::101] = -0.0
+    cols = [i32, i64, f32]
+    preds = []
+    for k in range(80):
+        a, b = sorted(int(x) for x in rng.integers(-1100, 1100, 2))
+        preds.append([Term(0, RANGE, a, b + (k % 3))])
+    preds += [[Term(0, RANGE, -2**31, 0)], [Term(0, RANGE, 0, 2**31 - 1)], [Term(0, RANGE, -5, 5)],
+              [Term(0, RANGE, 5, 15)], [Term(0, RANGE, -5, 15)], [Term(0, RANGE, 10, 3)]]
+    for k in range(40):
+        a, b = sorted(int(x) for x in rng.integers(-1100, 1100, 2))
+        preds.append([Term(1, RANGE, a * (2**34 + 3), b * (2**34 + 3) + k)])
+    preds += [[Term(1, RANGE, -2**63, 0)], [Term(1, RANGE, 1, 2**63 - 1)]]
+    for k in range(40):
+        a, b = sorted(float(x) for x in rng.standard_normal(2) * 12)
+        preds.append([Term(2, RANGE, a, b)])
+    preds += [[Term(2, RANGE, float("-inf"), 0.0)], [Term(2, RANGE, -0.0, float("inf"))],
+              [Term(2, RANGE, 0.0, 1e-30)], [Term(2, RANGE, float("-inf"), float("inf"))]]
+    for k in range(30):
+        a, b = sorted(int(x) for x in rng.integers(-1000, 1000, 2))
+        c, d = sorted(float(x) for x in rng.standard_normal(2) * 10)
+        preds.append([Term(0, RANGE, a, b), Term(2, RANGE, c, d)])
+    tid = g.gace_load_columns(gctx, cols)
+    try:
+        check_probe(g, orc, gctx, tid, cols, [I32, I64, F32], preds,
+                    [Sample(FULL), Sample(ROWS, 0.3, 11), Sample(BLOCKS, 0.5, 2, 1000)])
+    finally:
+        g.gace_unload(gctx, tid)
