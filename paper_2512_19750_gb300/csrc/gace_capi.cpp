@@ -523,16 +523,21 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
     A.timeout_ns = ctx->timeout_ns;
 
     // Narrow passes (the gate's single probes) stream staged tiles of about
-    // 16 KB through a 3-deep bulk-copy pipeline so that many CTAs fit on an SM;
-    // wide passes are ALU-bound and load directly.
+    // 32 KB through a bulk-copy pipeline two or three stages deep (at most
+    // 64 KB per CTA, so that three or four CTAs fit on an SM); wide passes are
+    // ALU-bound and load directly.
     uint32_t rowbytes = 0;
     for (uint32_t s = 0; s < nslots; ++s) rowbytes += A.slots[s].width;
     ps.rowbytes = rowbytes;
     A.narrow = narrow ? 1u : 0u;
     const uint32_t sweep = (A.narrow ? 2u : 1u) * kSliceRows * kProbeWarps;  // rows of one CTA sweep
+#ifndef GACE_STAGE_TARGET_KB
+#define GACE_STAGE_TARGET_KB 32
+#endif
     uint32_t tile_rows = sweep;
     if (rowbytes > 0)
-        while (tile_rows * 2 * rowbytes <= 16384 && tile_rows < 8 * sweep) tile_rows *= 2;  // ~16 KB stages
+        while (tile_rows * 2 * rowbytes <= (GACE_STAGE_TARGET_KB << 10) && tile_rows < 8 * sweep)
+            tile_rows *= 2;  // stages of about GACE_STAGE_TARGET_KB
     else
         tile_rows = 8 * sweep;
     A.tile_rows = tile_rows;
