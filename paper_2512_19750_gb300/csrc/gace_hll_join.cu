@@ -69,8 +69,20 @@ __global__ void __launch_bounds__(kHistThreads, 1)
     if (threadIdx.x == 0 && tp) atomicAdd(A.pass_count, tp);
 }
 
+#ifndef GACE_GATHER_GROUPS
+#define GACE_GATHER_GROUPS 1
+#endif
+// Groups of four rows per thread and iteration: gathers (a weight load that
+// waits on its key) run best one group at a time with more threads resident;
+// histogram updates two at a time.
+template <int MODE>
+__host__ __device__ constexpr int side_unroll() { return (MODE == 1 || MODE == 2) ? GACE_GATHER_GROUPS : 2; }
+
+#ifndef GACE_GATHER_CTAS
+#define GACE_GATHER_CTAS 4
+#endif
 template <int MODE, bool AGG>
-__global__ void __launch_bounds__(kJoinThreads, 4)
+__global__ void __launch_bounds__(kJoinThreads, (MODE == 1 || MODE == 2) ? GACE_GATHER_CTAS : 4)
     k_side(const __grid_constant__ SideArgs A, uint32_t* hist, int strict, const void* weight,
            unsigned long long* out_sum, uint32_t fk2_slot, uint64_t domain2,
            unsigned long long* w64) {
@@ -78,7 +90,7 @@ __global__ void __launch_bounds__(kJoinThreads, 4)
     const int lane = threadIdx.x & 31;
     unsigned long long npass = 0, acc = 0;
     // warp-uniform trip count so that every lane reaches the warp collectives
-    side_groups<MODE, AGG>(A, hist, strict, weight, fk2_slot, domain2, w64,
+    side_groups<MODE, AGG, side_unroll<MODE>()>(A, hist, strict, weight, fk2_slot, domain2, w64,
                            static_cast<uint64_t>(blockIdx.x) * kJoinThreads + (threadIdx.x - lane),
                            (A.nrows + 3) / 4, static_cast<uint64_t>(gridDim.x) * kJoinThreads, npass, acc);
     const unsigned long long tp = block_sum_u64<kJoinThreads / 32>(npass, scratch);

@@ -117,26 +117,25 @@ __device__ __forceinline__ void hll_merge(const HllArgs& A, const uint32_t* sreg
 
 // ---------------------------------------------------------------- join sides
 
-// Filter of two groups of four rows (row0a, row0b): each term's two loads are
-// issued before either is tested.
-__device__ __forceinline__ void side_pass2(const SideArgs& A, uint64_t row0a, uint64_t row0b, bool pa[4],
-                                           bool pb[4]) {
+// Filter of U groups of four rows (starting rows row0[u]): each term's U
+// loads are issued before any is tested.
+template <int U>
+__device__ __forceinline__ void side_pass_u(const SideArgs& A, const uint64_t (&row0)[U], bool (&p)[U][4]) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        pa[r] = row0a + r < A.nrows;
-        pb[r] = row0b + r < A.nrows;
-    }
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) p[u][r] = row0[u] + r < A.nrows;
     for (uint32_t t = 0; t < A.nterms; ++t) {
         const FilterTerm& ft = A.terms[t];
         const uint32_t w = A.slot_dtype[ft.slot] == 1 ? 8 : 4;
-        Quad va, vb;
-        load_quad_global(A.slot_ptr[ft.slot], w, row0a, A.nrows, va);
-        load_quad_global(A.slot_ptr[ft.slot], w, row0b, A.nrows, vb);
+        Quad v[U];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            pa[r] = pa[r] && term_holds(ft.kind, ft.c, va.lo[r], va.hi[r], A.pool);
-            pb[r] = pb[r] && term_holds(ft.kind, ft.c, vb.lo[r], vb.hi[r], A.pool);
-        }
+        for (int u = 0; u < U; ++u) load_quad_global(A.slot_ptr[ft.slot], w, row0[u], A.nrows, v[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                p[u][r] = p[u][r] && term_holds(ft.kind, ft.c, v[u].lo[r], v[u].hi[r], A.pool);
     }
 }
 
@@ -154,7 +153,7 @@ __device__ __forceinline__ void side_keys(const SideArgs& A, uint32_t slot, uint
 
 // One side of a join over warp-uniform groups of four rows: gb = first (the
 // warp's first group), first + stride, ... < end, lane l taking group gb + l;
-// two such sweeps per iteration, their loads issued together.
+// U such sweeps per iteration (side_groups), their loads issued together.
 // MODE 0: h[key] += 1 (AGG: equal keys of a warp combined with match_any);
 // 1: acc += weight32[key]; 2: acc += weight64[key]; 3: w64[key] += h2[fk2].
 // npass counts the rows that pass the filter; a passing row with a key outside
@@ -198,29 +197,33 @@ __device__ __forceinline__ void side_rows(const SideArgs& A, uint32_t* hist, int
     }
 }
 
-template <int MODE, bool AGG>
+template <int MODE, bool AGG, int U = 2>
 __device__ __forceinline__ void side_groups(const SideArgs& A, uint32_t* hist, int strict, const void* weight,
                                             uint32_t fk2_slot, uint64_t domain2, unsigned long long* w64,
                                             uint64_t first, uint64_t end, uint64_t stride,
                                             unsigned long long& npass, unsigned long long& acc) {
     const int lane = threadIdx.x & 31;
-    for (uint64_t gb = first; gb < end; gb += 2 * stride) {
-        const uint64_t ga = gb + lane, gc = gb + stride + lane;
-        // groups past the range read as rows past the table (or are ignored)
-        const bool mine_a = ga < end, mine_c = gc < end;
-        int64_t ka[4], kc[4];
-        side_keys(A, A.key_slot, ga * 4, ka);
-        side_keys(A, A.key_slot, gc * 4, kc);
-        int64_t fa[4] = {0, 0, 0, 0}, fc[4] = {0, 0, 0, 0};
-        if (MODE == 3) {
-            side_keys(A, fk2_slot, ga * 4, fa);
-            side_keys(A, fk2_slot, gc * 4, fc);
+    for (uint64_t gb = first; gb < end; gb += U * stride) {
+        uint64_t row0[U];
+        bool mine[U];
+        int64_t key[U][4], fk2[U][4];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t gu = gb + u * stride + lane;
+            row0[u] = gu * 4;
+            mine[u] = gu < end;  // groups past the range read as rows past the table (or are ignored)
+            side_keys(A, A.key_slot, row0[u], key[u]);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) fk2[u][r] = 0;
+            if (MODE == 3) side_keys(A, fk2_slot, row0[u], fk2[u]);
         }
-        bool pa[4], pc[4];
-        side_pass2(A, ga * 4, gc * 4, pa, pc);
-        side_rows<MODE, AGG>(A, hist, strict, weight, domain2, w64, ka, fa, pa, mine_a, npass, acc);
-        if (gb + stride < end)  // warp-uniform: every lane reaches the match_any of the second sweep
-            side_rows<MODE, AGG>(A, hist, strict, weight, domain2, w64, kc, fc, pc, mine_c, npass, acc);
+        bool p[U][4];
+        side_pass_u<U>(A, row0, p);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (gb + u * stride < end)  // warp-uniform: every lane reaches the match_any of each sweep
+                side_rows<MODE, AGG>(A, hist, strict, weight, domain2, w64, key[u], fk2[u], p[u], mine[u], npass,
+                                     acc);
     }
 }
 
