@@ -335,6 +335,7 @@ void emit_jobs(ReqPlan& rp, unsigned char* dws, unsigned int* batch_status, std:
         jr.job.hll.status = batch_status;
         jr.units = rp.hll.nrows;
         jr.smem = rp.hll.p <= 16 ? (1u << rp.hll.p) : 0u;
+        jr.cost = 4;  // two 64-bit multiplies and a register update per row
         jr.family = "batch_hll";
         jr.rows = jr.units;
         jr.bytes = jr.units * dtype_width(static_cast<int>(rp.hll.dtype));
@@ -361,6 +362,7 @@ void emit_jobs(ReqPlan& rp, unsigned char* dws, unsigned int* batch_status, std:
     uint32_t* hf = reinterpret_cast<uint32_t*>(dws + rp.hf_off);
     auto side_job = [&](uint32_t kind, int i, uint32_t phase, uint32_t strict) {
         JobRec jr;
+        jr.cost = 2;  // latency-bound: a key's filter, then its weight or histogram update
         jr.job.kind = kind;
         jr.job.side = side_dev(i);
         jr.job.strict = strict;
@@ -388,7 +390,7 @@ void emit_jobs(ReqPlan& rp, unsigned char* dws, unsigned int* batch_status, std:
         if (domain > kSmemHistMax) return;
         jr.cls = kClassHist;
         jr.smem = static_cast<uint32_t>(domain) * 4u;
-        jr.granule = round_up(16 * domain, 128);  // at least 16 rows per bin and item
+        jr.granule = round_up(4 * domain, 128);  // at least 4 rows per bin and item
     };
     // phase 0: the dimension histogram the others read (and the fact histogram)
     JobRec h = side_job(kJobHist, two ? 2 : 1, 0, 1);
@@ -436,6 +438,31 @@ void emit_jobs(ReqPlan& rp, unsigned char* dws, unsigned int* batch_status, std:
     }
 }
 
+gace_status batch_setup(gace_ctx* ctx) {
+    if (ctx->batch_ready) return GACE_OK;
+    cudaError_t e = batch_configure(ctx->smem_optin);
+    if (e != cudaSuccess) return cuda_fail(e, "batch kernel attributes");
+    for (cudaStream_t& a : ctx->batch_aux)
+        if (!a && (e = cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e, "batch streams");
+    for (int ph = 0; ph < kPhases; ++ph) {
+        if (!ctx->batch_fork[ph] &&
+            (e = cudaEventCreateWithFlags(&ctx->batch_fork[ph], cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(e, "batch events");
+        for (cudaEvent_t& j : ctx->batch_join[ph])
+            if (!j && (e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(e, "batch events");
+    }
+    ctx->batch_ready = true;
+    return GACE_OK;
+}
+
+uint64_t item_units(const JobRec& jr, uint64_t chunk) {
+    uint64_t piece = std::max<uint64_t>(128, chunk / jr.cost);
+    if (jr.cls == kClassProbe) piece = std::max<uint64_t>(piece, 4 * jr.granule);  // bulk copies overlap
+    return round_up(piece, jr.granule);
+}
+
 // Items of `chunk` units per job, ordered by phase, then class; the range of
 // each (phase, class).
 void make_items(const std::vector<JobRec>& jobs, uint64_t chunk, std::vector<BatchItem>& items,
@@ -446,10 +473,7 @@ void make_items(const std::vector<JobRec>& jobs, uint64_t chunk, std::vector<Bat
             pbeg[ph][c] = static_cast<uint32_t>(items.size());
             for (uint32_t j = 0; j < jobs.size(); ++j) {
                 if (jobs[j].phase != static_cast<uint32_t>(ph) || jobs[j].cls != c) continue;
-                // a probe item spans a few tiles, so that its bulk copies overlap
-                const uint64_t piece = jobs[j].cls == kClassProbe ? std::max<uint64_t>(chunk, 4 * jobs[j].granule)
-                                                                  : chunk;
-                const uint64_t step = round_up(piece, jobs[j].granule);
+                const uint64_t step = item_units(jobs[j], chunk);
                 for (uint64_t b = 0; b < jobs[j].units; b += step) {
                     BatchItem it{};
                     it.job = j;
@@ -560,13 +584,24 @@ cudaError_t enqueue_batch(gace_ctx* ctx, const BatchRun& br, cudaStream_t s) {
     const BatchItem* items = reinterpret_cast<const BatchItem*>(dws + br.items_off);
     const BatchJob* jobs = reinterpret_cast<const BatchJob*>(dws + br.jobs_off);
     unsigned int* heads = reinterpret_cast<unsigned int*>(dws + br.small_base + 256);
-    for (int ph = 0; ph < kPhases; ++ph)
+    for (int ph = 0; ph < kPhases; ++ph) {
+        // a phase's classes on parallel streams (graph branches), joined before the next phase
+        if ((e = cudaEventRecord(ctx->batch_fork[ph], s)) != cudaSuccess) return e;
+        int branch = 0;
         for (int c = 0; c < kClasses; ++c) {
             if (!br.pcnt[ph][c]) continue;
+            cudaStream_t on = branch == 0 ? s : ctx->batch_aux[branch - 1];
+            if (branch > 0 && (e = cudaStreamWaitEvent(on, ctx->batch_fork[ph], 0)) != cudaSuccess) return e;
             if ((e = batch_launch(items + br.pbeg[ph][c], br.pcnt[ph][c], jobs, heads + ph * kClasses + c,
-                                  br.grid[c], br.smem[c], c, s)) != cudaSuccess)
+                                  br.grid[c], br.smem[c], c, on)) != cudaSuccess)
                 return e;
+            if (branch > 0) {
+                if ((e = cudaEventRecord(ctx->batch_join[ph][branch - 1], on)) != cudaSuccess) return e;
+                if ((e = cudaStreamWaitEvent(s, ctx->batch_join[ph][branch - 1], 0)) != cudaSuccess) return e;
+            }
+            ++branch;
         }
+    }
     return cudaMemcpyAsync(pin + br.small_base, dws + br.small_base, br.small_end - br.small_base,
                            cudaMemcpyDeviceToHost, s);
 }
@@ -796,12 +831,7 @@ namespace {
 gace_status batch_prologue(gace_ctx* ctx, const gace_request* reqs, uint32_t n) {
     if (gace_status s = check_ctx(ctx)) return s;
     if (n && !reqs) return fail(GACE_EINVAL, "reqs is NULL");
-    if (!ctx->batch_ready) {
-        cudaError_t e = batch_configure(ctx->smem_optin);
-        if (e != cudaSuccess) return cuda_fail(e, "batch kernel attributes");
-        ctx->batch_ready = true;
-    }
-    return GACE_OK;
+    return batch_setup(ctx);
 }
 
 }  // namespace

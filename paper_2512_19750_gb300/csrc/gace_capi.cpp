@@ -1055,6 +1055,13 @@ gace_status gace_destroy(gace_ctx* ctx) {
         for (cudaEvent_t e : ctx->ev_free) cudaEventDestroy(e);
         if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
         if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+        for (cudaStream_t a : ctx->batch_aux)
+            if (a) cudaStreamDestroy(a);
+        for (int ph = 0; ph < kPhases; ++ph) {
+            if (ctx->batch_fork[ph]) cudaEventDestroy(ctx->batch_fork[ph]);
+            for (cudaEvent_t j : ctx->batch_join[ph])
+                if (j) cudaEventDestroy(j);
+        }
         if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     }
     delete ctx;

@@ -159,6 +159,9 @@ struct gace_ctx {
     };
     std::map<std::pair<int, int>, TuneEntry> tune;  // (log2 jobs, log2 rows) -> best
     cudaStream_t capture_stream = nullptr;
+    cudaStream_t batch_aux[kClasses - 1] = {};  // a phase's other classes run beside the first
+    cudaEvent_t batch_fork[kPhases] = {};
+    cudaEvent_t batch_join[kPhases][kClasses - 1] = {};
     cudaGraphExec_t graph_exec = nullptr;
     std::vector<uint64_t> graph_key;
     bool batch_ready = false;
@@ -357,7 +360,6 @@ gace_status build_side(gace_ctx* ctx, const gace_join_side& js, const char* name
 // ---------------------------------------------------------------- batched and served forms
 
 constexpr uint64_t kDefaultChunk = 1ull << 20;
-constexpr int kPhases = 3;
 constexpr uint32_t kHllSmem = 1u << 16;  // one-byte registers for p <= 16
 
 struct JobRec {
@@ -367,6 +369,10 @@ struct JobRec {
     uint64_t granule = 128;  // items start on multiples of this (a narrow pass's tile)
     int cls = kClassGeneral;  // the persistent kernel that drains its items
     uint32_t smem = 0;        // dynamic shared memory its items need
+    uint32_t cost = 1;        // time per unit relative to a narrow probe row: items get chunk / cost
+                              // units, so that items of every kind take about as long
+                              // (long items of one kind leave the other CTAs idle at a
+                              // launch's end)
     const char* family = "";
     uint64_t rows = 0, bytes = 0, ops = 0;  // statistics
 };
@@ -460,6 +466,11 @@ void place_request(ReqPlan& rp, Ws& win, Ws& wsmall, Ws& wbig);
 void shift_request(ReqPlan& rp, uint64_t in_base, uint64_t small_base, uint64_t big_base);
 // Jobs of a request, with device pointers into the workspace at dws.
 void emit_jobs(ReqPlan& rp, unsigned char* dws, unsigned int* status, std::vector<JobRec>& jobs);
+// One-time setup of the batch kernels' attributes, streams and events.
+gace_status batch_setup(gace_ctx* ctx);
+// Units per item of a job for a chunk size: chunk / cost, on the job's
+// granule, probe items at least four tiles.
+uint64_t item_units(const JobRec& jr, uint64_t chunk);
 // Items of `chunk` units per job, ordered by phase, then class.
 void make_items(const std::vector<JobRec>& jobs, uint64_t chunk, std::vector<BatchItem>& items,
                 uint32_t (&pbeg)[kPhases][kClasses], uint32_t (&pcnt)[kPhases][kClasses]);

@@ -258,6 +258,7 @@ constexpr int kClassProbe = 0;
 constexpr int kClassGeneral = 1;
 constexpr int kClassHist = 2;
 constexpr int kClasses = 3;
+constexpr int kPhases = 3;  // dependency phases of a batch (a join's histogram before its readers)
 
 // Key domains up to this many entries are histogrammed per CTA in shared
 // memory (hierarchical atomics: skewed keys do not serialise on one global

@@ -61,7 +61,6 @@ constexpr uint64_t kCopyPiece = 1ull << 16;    // bytes per scatter / gather des
 constexpr size_t kMaxStepItems = 1u << 16;     // items per step
 constexpr uint64_t kCtasPerSmGuess = 3;         // resident batch CTAs per SM, for sizing light steps
 constexpr uint64_t kItemsPerCta = 2;
-constexpr uint64_t kMinTilesPerItem = 4;        // a probe item spans a few tiles, so its copies overlap
 constexpr size_t kDirectCopies = 2;             // at most this many blocks moved by plain copies per step
 constexpr uint64_t kDirectBlockMax = 256u << 10;
 constexpr uint64_t kSpinNs = 500000;            // busy-wait on a step's completion before sleeping
@@ -220,6 +219,7 @@ struct StepSet {
     unsigned char* rb_dev = nullptr;   // gathered small outputs
     uint64_t rb_cap = 0;
     cudaEvent_t done = nullptr, k0 = nullptr, k1 = nullptr;
+    cudaEvent_t fork = nullptr, join[kClasses - 1] = {};
     bool busy = false, timed = false;
     std::vector<std::pair<Live*, uint64_t>> finishing;  // request, read-back offset
     uint64_t rows = 0, bytes = 0, ops = 0;
@@ -241,6 +241,7 @@ struct ServeState {
     unsigned char* arena = nullptr;
     Arena alloc;
     cudaStream_t stream = nullptr;
+    cudaStream_t aux[kClasses - 1] = {};  // a step's other classes run beside the first
     std::thread thr;
 
     // guarded by mu
@@ -556,6 +557,7 @@ void ServeState::fail_all(gace_status st, const std::string& msg) {
         }
     }
     cudaStreamSynchronize(stream);
+    for (cudaStream_t a : aux) cudaStreamSynchronize(a);
     for (StepSet& S : sets) {
         S.busy = false;
         S.finishing.clear();
@@ -642,9 +644,7 @@ gace_status ServeState::build_step(StepSet& S, std::vector<std::unique_ptr<Live>
                 }
                 const uint32_t j = lv.pjobs[lv.jk];
                 const JobRec& jr = lv.jobs[j];
-                const uint64_t piece = jr.cls == kClassProbe ? std::max(step_chunk, kMinTilesPerItem * jr.granule)
-                                                             : step_chunk;
-                const uint64_t b = lv.unit, e = std::min(jr.units, b + round_up(piece, jr.granule));
+                const uint64_t b = lv.unit, e = std::min(jr.units, b + item_units(jr, step_chunk));
                 BatchItem it{};
                 it.job = lv.step_job_base + j;
                 it.begin = b;
@@ -746,7 +746,11 @@ gace_status ServeState::build_step(StepSet& S, std::vector<std::unique_ptr<Live>
     S.launches = 0;
     if (!items.empty()) {
         CK(cudaEventRecord(S.k0, stream));
+        // the classes' persistent kernels on parallel streams: one kernel's
+        // draining CTAs leave their slots to the next kernel's instead of idling
+        CK(cudaEventRecord(S.fork, stream));
         size_t first = 0;
+        int branch = 0;
         for (int c = 0; c < kClasses; ++c) {
             const size_t cnt = citems[c].size();
             if (!cnt) continue;
@@ -754,10 +758,17 @@ gace_status ServeState::build_step(StepSet& S, std::vector<std::unique_ptr<Live>
             if (per_sm < 1)
                 return fail(GACE_ECUDA, "batch kernel cannot be resident with %u bytes of shared memory", smem[c]);
             const int grid = static_cast<int>(std::min<size_t>(static_cast<size_t>(per_sm) * ctx->sms, cnt));
+            cudaStream_t on = branch == 0 ? stream : aux[branch - 1];
+            if (branch > 0) CK(cudaStreamWaitEvent(on, S.fork, 0));
             CK(batch_launch(reinterpret_cast<const BatchItem*>(S.dev + items_off) + first, static_cast<uint32_t>(cnt),
                             reinterpret_cast<const BatchJob*>(S.dev + jobs_off),
-                            reinterpret_cast<unsigned int*>(S.dev) + c, grid, smem[c], c, stream));
+                            reinterpret_cast<unsigned int*>(S.dev) + c, grid, smem[c], c, on));
+            if (branch > 0) {
+                CK(cudaEventRecord(S.join[branch - 1], on));
+                CK(cudaStreamWaitEvent(stream, S.join[branch - 1], 0));
+            }
             first += cnt;
+            ++branch;
             ++S.launches;
         }
         CK(cudaEventRecord(S.k1, stream));
@@ -932,7 +943,9 @@ void free_server(ServeState& s) {
         if (S.dev) cudaFree(S.dev);
         if (S.rb_host) cudaFreeHost(S.rb_host);
         if (S.rb_dev) cudaFree(S.rb_dev);
-        for (cudaEvent_t e : {S.done, S.k0, S.k1})
+        for (cudaEvent_t e : {S.done, S.k0, S.k1, S.fork})
+            if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : S.join)
             if (e) cudaEventDestroy(e);
         S = StepSet();
     }
@@ -940,6 +953,10 @@ void free_server(ServeState& s) {
     s.arena = nullptr;
     if (s.stream) cudaStreamDestroy(s.stream);
     s.stream = nullptr;
+    for (cudaStream_t& a : s.aux) {
+        if (a) cudaStreamDestroy(a);
+        a = nullptr;
+    }
 }
 
 // Starts the scheduler; the caller holds ctx->mu and ctx->serve is empty.
@@ -963,11 +980,7 @@ gace_status start_locked(gace_ctx* ctx, const gace_serve_config* cfg, std::share
         return fail(GACE_ENOMEM, "serving arena of %llu bytes exceeds the HBM budget",
                     (unsigned long long)c.arena_bytes);
     DeviceGuard g(ctx->device);
-    if (!ctx->batch_ready) {
-        cudaError_t e = batch_configure(ctx->smem_optin);
-        if (e != cudaSuccess) return cuda_fail(e, "batch kernel attributes");
-        ctx->batch_ready = true;
-    }
+    if (gace_status st = batch_setup(ctx)) return st;
     auto undo = [&](gace_status st) {
         free_server(*s);
         return st;
@@ -980,10 +993,17 @@ gace_status start_locked(gace_ctx* ctx, const gace_serve_config* cfg, std::share
     }
     if ((e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)) != cudaSuccess)
         return undo(cuda_fail(e, "serving stream"));
+    for (cudaStream_t& a : s->aux)
+        if ((e = cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking)) != cudaSuccess)
+            return undo(cuda_fail(e, "serving stream"));
     for (StepSet& S : s->sets) {
         if ((e = cudaEventCreateWithFlags(&S.done, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&S.fork, cudaEventDisableTiming)) != cudaSuccess ||
             (e = cudaEventCreate(&S.k0)) != cudaSuccess || (e = cudaEventCreate(&S.k1)) != cudaSuccess)
             return undo(cuda_fail(e, "serving events"));
+        for (cudaEvent_t& j : S.join)
+            if ((e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming)) != cudaSuccess)
+                return undo(cuda_fail(e, "serving events"));
     }
     s->alloc.reset(c.arena_bytes);
     ctx->used += c.arena_bytes;
