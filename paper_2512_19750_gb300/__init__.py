@@ -238,6 +238,8 @@ class ProbeRequest:
         self.nsamples = len(samples)
         self.results = np.zeros((len(samples), self.b.npreds), dtype=RESULT_DTYPE)
         self.marginals = np.zeros((len(samples), self.b.nterms), dtype=np.uint64) if marginals else None
+        self.req = _capi.gace_request()
+        self.fill(self.req)
 
     def fill(self, r):
         r.kind, r.table_id = _capi.GACE_REQ_PROBE, self.table_id
@@ -257,6 +259,8 @@ class NdvRequest:
         self.table_id, self.col, self.p, self.seed = table_id, col, p, int(hash_seed) & ((1 << 64) - 1)
         self.registers = np.zeros(1 << p, dtype=np.uint8)
         self._est = C.c_double()
+        self.req = _capi.gace_request()
+        self.fill(self.req)
 
     @property
     def estimate(self) -> float:
@@ -285,6 +289,8 @@ class JoinRequest:
             self.spec.hops = 1
         self.spec.method = method
         self.out = _capi.gace_join_result()
+        self.req = _capi.gace_request()
+        self.fill(self.req)
 
     @property
     def result(self) -> dict:
@@ -299,25 +305,43 @@ class JoinRequest:
 
 
 def _request_array(requests):
+    if isinstance(requests, RequestArray):
+        return requests.arr
     arr = (_capi.gace_request * max(1, len(requests)))()
     for k, q in enumerate(requests):
-        q.fill(arr[k])
+        arr[k] = q.req
     return arr
 
 
+class RequestArray:
+    """The C array of a list of request objects, marshalled once and passed
+    to gace_run_batch / gace_tune_batch any number of times (every run writes
+    the requests' outputs again)."""
+
+    def __init__(self, requests):
+        self.requests = list(requests)
+        self.arr = _request_array(self.requests)
+
+    def __len__(self):
+        return len(self.requests)
+
+
 def gace_run_batch(ctx, requests, raise_on_error: bool = True):
-    """Runs ProbeRequest / NdvRequest / JoinRequest objects as one batch;
-    returns the per-request statuses (and raises on the first failure unless
-    raise_on_error is False)."""
+    """Runs ProbeRequest / NdvRequest / JoinRequest objects (a list or a
+    RequestArray) as one batch; returns the per-request statuses (and raises
+    on the first failure unless raise_on_error is False)."""
     arr = _request_array(requests)
-    st = (C.c_int * max(1, len(requests)))()
-    rc = lib().gace_run_batch(ctx, arr, len(requests), st)
+    n = len(requests)
+    st = (C.c_int * max(1, n))()
+    rc = lib().gace_run_batch(ctx, arr, n, st)
     if raise_on_error:
         check(rc, "gace_run_batch")
-    return [int(st[i]) for i in range(len(requests))]
+    return [int(st[i]) for i in range(n)]
 
 
 def gace_tune_batch(ctx, requests) -> None:
+    """Tunes the batched form for batches shaped like `requests` (a list or a
+    RequestArray); the requests receive their outputs."""
     arr = _request_array(requests)
     check(lib().gace_tune_batch(ctx, arr, len(requests)), "gace_tune_batch")
 
@@ -354,10 +378,8 @@ def _ctx_key(ctx) -> int:
 def gace_submit(ctx, request) -> int:
     """Queues a ProbeRequest / NdvRequest / JoinRequest; returns its ticket.
     The request object receives the outputs once gace_poll reports completion."""
-    r = _capi.gace_request()
-    request.fill(r)
     t = C.c_uint64()
-    check(lib().gace_submit(ctx, C.byref(r), C.byref(t)), "gace_submit")
+    check(lib().gace_submit(ctx, C.byref(request.req), C.byref(t)), "gace_submit")
     _SUBMITTED[(_ctx_key(ctx), t.value)] = request
     return t.value
 
@@ -411,5 +433,6 @@ def gace_status_string(s: int) -> str:
 
 
 __all__ = [n for n in dir() if n.startswith(("gace_", "GACE_"))] + [
-    "GaceError", "JoinRequest", "JoinSideSpec", "NdvRequest", "ProbeRequest", "RESULT_DTYPE", "TermBatch",
+    "GaceError", "JoinRequest", "JoinSideSpec", "NdvRequest", "ProbeRequest", "RESULT_DTYPE", "RequestArray",
+    "TermBatch",
     "check", "lib"]
