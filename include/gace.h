@@ -358,7 +358,10 @@ gace_status gace_tune_load(gace_ctx* ctx, const char* path);
  * two in flight, each with one upload, one scatter of the newly admitted
  * requests' inputs, the batch launch, one gather of the finished requests'
  * counters and one read-back.  A request completes when its last chunk has
- * run; its results are identical to the synchronous call's.  Results of
+ * run; its results are identical to the synchronous call's.  A request that
+ * arrives at an idle server (nothing in flight, nothing else queued) is run
+ * at once through its synchronous call on the context's stream: with nothing
+ * to batch it with, a step would only add latency.  Results of
  * NDV requests are kept on the host as a sketch cache (LRU) that answers
  * later requests for the same table, column, p and seed at submission.
  * gace_unload forgets a table's sketches and fails with GACE_EBUSY while
@@ -371,7 +374,13 @@ typedef struct {
     uint64_t step_rows;     /* units (rows) per scheduling step; 0 = 2^29 */
     uint64_t chunk_rows;    /* rows per chunk (at most 2^30), rounded up to a multiple of 128, and
                                for a narrow probe pass to a multiple of its tile; 0 = 2^18 */
+    uint32_t flags;         /* GACE_SERVE_* */
+    uint32_t reserved;
 } gace_serve_config;
+
+/* Never run a request alone through its synchronous call: every request goes
+ * through the steps (tests of the batching machinery). */
+#define GACE_SERVE_ALWAYS_STEP 1u
 
 /* Starts the scheduler (cfg may be NULL: defaults); its arena counts against
  * the context's HBM budget.  GACE_EBUSY when it is already running: stop it
@@ -424,8 +433,10 @@ gace_status gace_serve_replay(gace_ctx* ctx, const gace_request* reqs, uint32_t 
  * requests, with launches = requests and total_ms = the summed wall time:
  * serve_req_queue (submission to admission), serve_req_run (admission to the
  * step with the request's last chunk), serve_req_gpu (that step's enqueue to
- * the scheduler seeing it complete), serve_req_finish (outputs assembled and
- * the ticket completed).
+ * the scheduler seeing it complete, or the synchronous call of a request run
+ * alone), serve_req_finish (outputs assembled and the ticket completed); and
+ * "serve_alone", whose launches count the requests an idle server ran
+ * through their synchronous call.
  */
 typedef struct {
     char name[24];      /* kernel family, NUL-terminated */

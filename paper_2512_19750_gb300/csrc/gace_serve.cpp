@@ -269,6 +269,8 @@ struct ServeState {
     Phases phases;                // published with the kernel statistics
 
     void run();
+    void run_alone(Live& lv);
+    void publish_phases();
     void take(std::vector<std::unique_ptr<Live>>& cands);
     void admit(std::vector<std::unique_ptr<Live>>& cands, std::vector<std::unique_ptr<Live>>& admitted,
                bool& blocked);
@@ -411,6 +413,21 @@ gace_status alloc_step(StepSet& S, uint64_t up, uint64_t rb) {
         S.rb_cap = cap;
     }
     return GACE_OK;
+}
+
+// One request through its synchronous call (the plain path).
+gace_status run_plain(gace_ctx* ctx, const gace_request& q) {
+    switch (q.kind) {
+        case GACE_REQ_PROBE:
+            return gace_probe_batch(ctx, q.table_id, q.samples, q.nsamples, q.terms, q.nterms, q.in_values, q.nin,
+                                    q.preds, q.npreds, q.results, q.term_marginals);
+        case GACE_REQ_NDV:
+            return gace_ndv(ctx, q.table_id, q.col, q.p, q.hash_seed, q.registers_out, q.estimate_out);
+        case GACE_REQ_JOIN:
+            return gace_join_card(ctx, q.join, q.join_out);
+        default:
+            return fail(GACE_EINVAL, "request kind %u invalid", q.kind);
+    }
 }
 
 }  // namespace
@@ -848,25 +865,63 @@ void ServeState::complete(StepSet& S) {
         if (ctx->timing) k.ms += ms;
         if (S.launches) ctx->stats["batch_kernel"].launches += S.launches;
         if (S.copies) ctx->stats["serve_copy"].launches += S.copies;
-        // request phases: launches = requests, total_ms = summed time
-        const char* names[4] = {"serve_req_queue", "serve_req_run", "serve_req_gpu", "serve_req_finish"};
-        const uint64_t vals[4] = {phases.queue, phases.run, phases.gpu, phases.finish};
-        for (int i = 0; i < 4; ++i) {
-            gace_ctx::KStat& q = ctx->stats[names[i]];
-            q.launches += phases.n;
-            q.ms += vals[i] / 1e6;
-        }
-        phases = Phases();
+        publish_phases();
     }
     live.erase(std::remove_if(live.begin(), live.end(),
                               [](const std::unique_ptr<Live>& p) { return p->finished; }),
                live.end());
 }
 
+// A request alone on an idle server runs through its synchronous call on the
+// scheduler thread: with nothing to batch it with, a step's upload, launches
+// and read-back would only add latency (a lone request fills one step anyway,
+// so requests arriving meanwhile wait no longer than they would behind it).
+void ServeState::run_alone(Live& lv) {
+    ++nlive;
+    lv.t_admit = now_ns();
+    std::vector<uint8_t> regs;
+    double est = 0.0;
+    if (lv.req.q.kind == GACE_REQ_NDV && lv.cacheable) {  // the cache keeps what the caller may not want
+        if (!lv.req.q.registers_out) {
+            regs.resize(1ull << lv.req.q.p);
+            lv.req.q.registers_out = regs.data();
+        }
+        if (!lv.req.q.estimate_out) lv.req.q.estimate_out = &est;
+    }
+    const gace_status st = run_plain(ctx, lv.req.q);
+    const std::string err = st != GACE_OK ? std::string(gace_last_error()) : std::string();
+    lv.t_last = now_ns();
+    lv.rp.kind = lv.req.q.kind;
+    if (lv.req.q.kind == GACE_REQ_NDV) lv.rp.hll.p = lv.req.q.p;
+    finish(lv, st, err);
+    const uint64_t t_done = now_ns();
+    phases.n += 1;
+    phases.queue += lv.t_admit - lv.t_submit;
+    phases.gpu += lv.t_last - lv.t_admit;
+    phases.finish += t_done - lv.t_last;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->stats["serve_alone"].launches += 1;
+    publish_phases();
+}
+
+// The request phases into the kernel statistics: launches = requests,
+// total_ms = summed time (the caller holds ctx->mu).
+void ServeState::publish_phases() {
+    const char* names[4] = {"serve_req_queue", "serve_req_run", "serve_req_gpu", "serve_req_finish"};
+    const uint64_t vals[4] = {phases.queue, phases.run, phases.gpu, phases.finish};
+    for (int i = 0; i < 4; ++i) {
+        gace_ctx::KStat& q = ctx->stats[names[i]];
+        q.launches += phases.n;
+        q.ms += vals[i] / 1e6;
+    }
+    phases = Phases();
+}
+
 void ServeState::run() {
     cudaSetDevice(ctx->device);
     for (;;) {
         std::vector<std::unique_ptr<Live>> cands, admitted;
+        std::unique_ptr<Live> fast;
         bool blocked = false, quit = false;
         auto issuable = [&]() {
             for (auto& p : live)
@@ -894,11 +949,22 @@ void ServeState::run() {
                 }
                 npending.store(0, std::memory_order_relaxed);
             } else if (!quit) {
-                take(cands);
-                if (cands.empty() && !pending.empty()) blocked = true;
+                if (!(cfg.flags & GACE_SERVE_ALWAYS_STEP) && live.empty() && !sets[0].busy && !sets[1].busy &&
+                    pending.size() == 1) {
+                    fast = std::move(pending.front());  // an idle server: nothing to batch with
+                    pending.pop_front();
+                    npending.store(0, std::memory_order_relaxed);
+                } else {
+                    take(cands);
+                    if (cands.empty() && !pending.empty()) blocked = true;
+                }
             }
         }
         if (quit) break;
+        if (fast) {
+            run_alone(*fast);
+            continue;
+        }
         if (!cands.empty()) admit(cands, admitted, blocked);
         if (!admitted.empty() || issuable()) {
             StepSet& S = sets[step & 1];
@@ -1096,20 +1162,6 @@ gace_status submit_request(gace_ctx* ctx, const gace_request& req, uint64_t* tic
     }
     srv->cv_work.notify_one();
     return GACE_OK;
-}
-
-gace_status run_plain(gace_ctx* ctx, const gace_request& q) {
-    switch (q.kind) {
-        case GACE_REQ_PROBE:
-            return gace_probe_batch(ctx, q.table_id, q.samples, q.nsamples, q.terms, q.nterms, q.in_values, q.nin,
-                                    q.preds, q.npreds, q.results, q.term_marginals);
-        case GACE_REQ_NDV:
-            return gace_ndv(ctx, q.table_id, q.col, q.p, q.hash_seed, q.registers_out, q.estimate_out);
-        case GACE_REQ_JOIN:
-            return gace_join_card(ctx, q.join, q.join_out);
-        default:
-            return fail(GACE_EINVAL, "request kind %u invalid", q.kind);
-    }
 }
 
 void wait_until(uint64_t t) {

@@ -42,7 +42,7 @@ def _submit_all(g, ctx, breqs):
 @pytest.mark.parametrize("step_rows,chunk_rows", [(0, 0), (1 << 16, 1 << 12), (300, 128)])
 def test_served_equals_synchronous_calls(g, sctx, served, step_rows, chunk_rows):
     tables, reqs, tids = served
-    g.gace_serve_start(sctx, step_rows=step_rows, chunk_rows=chunk_rows, sketch_cache=-1)
+    g.gace_serve_start(sctx, step_rows=step_rows, chunk_rows=chunk_rows, sketch_cache=-1, always_step=True)
     try:
         breqs = to_requests(g, tids, tables, reqs)
         _submit_all(g, sctx, breqs)
@@ -55,7 +55,7 @@ def test_admission_by_memory(g, sctx, served):
     """A 1 MiB arena and two slots: most requests wait for admission and all
     still come back exact."""
     tables, reqs, tids = served
-    g.gace_serve_start(sctx, arena_bytes=1 << 20, max_inflight=2, sketch_cache=-1)
+    g.gace_serve_start(sctx, arena_bytes=1 << 20, max_inflight=2, sketch_cache=-1, always_step=True)
     try:
         pick = reqs[:60]
         breqs = to_requests(g, tids, tables, pick)
@@ -74,7 +74,7 @@ def test_admission_by_memory(g, sctx, served):
 
 def test_tickets_cache_and_unload(g, sctx, served, cuda):
     tables, reqs, tids = served
-    g.gace_serve_start(sctx, step_rows=128, chunk_rows=128)
+    g.gace_serve_start(sctx, step_rows=128, chunk_rows=128, always_step=True)
     try:
         with pytest.raises(g.GaceError) as e:
             g.gace_poll(sctx, 987654321, 0)
@@ -134,7 +134,7 @@ def test_join_chain_served(g, sctx, orc, cuda):
     f, d, d2 = make_join(n_fact=300_001, n_dim=20_000, n_dim2=3000, seed=8, device=cuda)
     fid, did, d2id = (g.gace_load_columns(sctx, t.columns, borrow=True) for t in (f, d, d2))
     try:
-        g.gace_serve_start(sctx, step_rows=1 << 15, chunk_rows=1 << 13)
+        g.gace_serve_start(sctx, step_rows=1 << 15, chunk_rows=1 << 13, always_step=True)
         F = g.JoinSideSpec(fid, 0, [Term(1, RANGE, 0, 300)], f.dtypes)
         D = g.JoinSideSpec(did, 0, [Term(2, RANGE, 100, 900)], d.dtypes)
         D2 = g.JoinSideSpec(d2id, 0, [Term(1, RANGE, 0, 500)], d2.dtypes)
@@ -194,7 +194,7 @@ def test_fused_admission(g, sctx, served, cuda):
     for k in range(1, 12):
         cols = [1 + (k % 3)] if k % 2 else [1, 2 + (k % 2)]
         specs.append(([[rng_term(c, k) for c in cols], [rng_term(cols[0], k + 1)]], shared, bool(k % 3)))
-    g.gace_serve_start(sctx, step_rows=4096, chunk_rows=4096)
+    g.gace_serve_start(sctx, step_rows=4096, chunk_rows=4096, always_step=True)
     try:
         hold = g.ProbeRequest(slow, [[Term(0, RANGE, 0, 1000)]], [Sample(FULL)], [I32])
         th = g.gace_submit(sctx, hold)
@@ -214,3 +214,21 @@ def test_fused_admission(g, sctx, served, cuda):
     finally:
         g.gace_serve_stop(sctx)
         g.gace_unload(sctx, slow)
+
+
+def test_request_alone_on_idle_server(g, sctx, served):
+    """An idle server runs a lone request through its synchronous call; the
+    results are the same, and requests that overlap still take the steps."""
+    tables, reqs, tids = served
+    g.gace_serve_start(sctx, sketch_cache=-1)
+    try:
+        g.gace_stats_reset(sctx)
+        pick = reqs[:12]
+        breqs = to_requests(g, tids, tables, pick)
+        for q in breqs:  # one at a time: each finds the server idle
+            assert g.gace_poll(sctx, g.gace_submit(sctx, q), POLL_US)
+        st = g.gace_stats_read(sctx)
+        assert st["serve_alone"]["launches"] == len(pick)
+        check_against_sync(g, sctx, tids, tables, pick, breqs)
+    finally:
+        g.gace_serve_stop(sctx)
