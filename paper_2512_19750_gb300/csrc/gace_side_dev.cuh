@@ -30,8 +30,9 @@ __device__ __forceinline__ void hll_rank(uint64_t key, uint64_t seedhash, uint32
                                          uint32_t& j, uint32_t& rho) {
     const uint64_t h = splitmix64(key ^ seedhash);
     j = static_cast<uint32_t>(h >> (64 - p));
-    const uint64_t w = h << p;
-    rho = w ? static_cast<uint32_t>(__clzll(static_cast<long long>(w))) + 1u : 65u - p;
+    // rho = leading zeros of the 64 - p bits after the index, + 1; a sentinel
+    // one at bit p - 1 (below them) makes an all-zero remainder give 65 - p
+    rho = static_cast<uint32_t>(__clzll(static_cast<long long>((h << p) | (1ull << (p - 1))))) + 1u;
 }
 
 // byte-wise max in shared memory via CAS on the containing word (bounded)
@@ -61,9 +62,11 @@ __device__ __forceinline__ void hll_quad(const HllArgs& A, uint32_t* sregs, cons
     // ranks of the four values first (independent), then the register checks
     uint32_t j[4], rho[4];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        hll_rank(canonical_key(DT, v.lo[r], v.hi[r]), A.seedhash, A.p, j[r], rho[r]);
-        if (row0 + r >= A.nrows) rho[r] = 0;  // past the end: never raises a register
+    for (int r = 0; r < 4; ++r) hll_rank(canonical_key(DT, v.lo[r], v.hi[r]), A.seedhash, A.p, j[r], rho[r]);
+    if (row0 + 3 >= A.nrows) {  // only the table's last quad runs past its end
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            if (row0 + r >= A.nrows) rho[r] = 0;  // never raises a register
     }
     if (SMEM) {
         uint32_t cur[4];
