@@ -598,6 +598,43 @@ double hll_estimate_host(const uint8_t* regs, uint32_t p) {
     return e;
 }
 
+// Staged side scans (k_side_staged) stream tiles of about 32 KB per stage
+// through two or three stages (at most 64 KB per CTA, three CTAs per SM), like
+// the narrow probes; columns that are not 16-byte aligned, or rows too wide
+// for two stages, keep the direct-load kernel (stage_bytes = 0).
+#ifndef GACE_SIDE_STAGED
+#define GACE_SIDE_STAGED 1
+#endif
+void plan_side_stages(SideArgs& a) {
+    constexpr uint32_t kTarget = 32u << 10, kBudget = 64u << 10;
+    const uint32_t sweep = kSideSlice * kSideWarps;
+    uint32_t rowbytes = 0;
+    bool aligned = true;
+    for (uint32_t s = 0; s < a.nslots; ++s) {
+        rowbytes += a.slot_width[s];
+        aligned = aligned && a.slot_aligned[s];
+    }
+    a.stage_bytes = 0;
+    a.nstages = 1;
+    a.tile_rows = sweep;
+    uint32_t tile = sweep;
+    while (tile * 2 * rowbytes <= kTarget && tile < 8 * sweep) tile *= 2;
+    uint32_t nst = 3;
+    while (nst > 2 && nst * tile * rowbytes > kBudget) --nst;
+    if (!GACE_SIDE_STAGED || !aligned || rowbytes == 0 || nst * tile * rowbytes > kBudget) return;
+    a.tile_rows = tile;
+    a.nstages = nst;
+    a.stage_bytes = tile * rowbytes;
+    uint32_t off = 0;
+    for (uint32_t s = 0; s < a.nslots; ++s) {
+        a.slot_soff[s] = off;
+        off += tile * a.slot_width[s];
+    }
+    a.smem_bytes = kSideStageOff + nst * a.stage_bytes;
+    a.ntiles = (a.nrows + tile - 1) / tile;
+    a.nstaged = a.nrows / tile;
+}
+
 gace_status build_side(gace_ctx* ctx, const gace_join_side& js, const char* name, int extra_col,
                               SideArgs& a, std::vector<uint32_t>& pool, TableRec** tab_out, uint32_t* extra_slot,
                               SideWork& work) {
@@ -661,7 +698,10 @@ gace_status build_side(gace_ctx* ctx, const gace_join_side& js, const char* name
         a.slot_ptr[s] = tab->cols[slot_col[s]].dptr;
         a.slot_dtype[s] = static_cast<uint32_t>(tab->cols[slot_col[s]].dtype);
         a.slot_aligned[s] = (reinterpret_cast<uintptr_t>(a.slot_ptr[s]) & 15u) == 0;
+        a.slot_width[s] = dtype_width(tab->cols[slot_col[s]].dtype);
     }
+    a.timeout_ns = ctx->timeout_ns;
+    plan_side_stages(a);
     *tab_out = tab;
     return GACE_OK;
 }

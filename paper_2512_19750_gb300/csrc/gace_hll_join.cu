@@ -101,6 +101,29 @@ __global__ void __launch_bounds__(kJoinThreads, (MODE == 1 || MODE == 2) ? GACE_
     }
 }
 
+// The side modes over tiles staged in shared memory by the bulk-copy pipeline
+// (tables whose referenced columns are 16-byte aligned and narrow enough for
+// two stages); three CTAs per SM.
+template <int MODE, bool AGG>
+__global__ void __launch_bounds__(kJoinThreads, 3)
+    k_side_staged(const __grid_constant__ SideArgs A, uint32_t* hist, int strict, const void* weight,
+                  unsigned long long* out_sum, uint32_t fk2_slot, uint64_t domain2, unsigned long long* w64) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ unsigned long long scratch[kJoinThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned long long npass = 0, acc = 0;
+    if (!side_tiles<MODE, AGG>(A, reinterpret_cast<uint64_t*>(smem), smem + kSideStageOff, tid, lane, warp,
+                               blockIdx.x, A.ntiles, gridDim.x, hist, strict, weight, fk2_slot, domain2, w64, npass,
+                               acc))
+        return;  // a pipeline wait gave up: the status says so
+    const unsigned long long tp = block_sum_u64<kJoinThreads / 32>(npass, scratch);
+    if (threadIdx.x == 0 && tp) atomicAdd(A.pass_count, tp);
+    if (MODE == 1 || MODE == 2) {
+        const unsigned long long ta = block_sum_u64<kJoinThreads / 32>(acc, scratch);
+        if (threadIdx.x == 0 && ta) atomicAdd(out_sum, ta);
+    }
+}
+
 template <bool B64>
 __global__ void __launch_bounds__(kJoinThreads)
     k_dot(const uint32_t* a, const void* b, uint64_t n, unsigned long long* sum) {
@@ -153,6 +176,25 @@ cudaError_t hll_launch(const HllArgs& a, int sms, cudaStream_t s) {
     }
 }
 
+// A staged side launch: grid = min(tiles, SMs x resident CTAs).
+template <int MODE, bool AGG>
+static cudaError_t staged_launch(const SideArgs& a, int sms, cudaStream_t s, uint32_t* hist, int strict,
+                                 const void* weight, unsigned long long* out_sum, uint32_t fk2_slot, uint64_t domain2,
+                                 unsigned long long* w64) {
+    cudaError_t e = cudaFuncSetAttribute(k_side_staged<MODE, AGG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(a.smem_bytes));
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_side_staged<MODE, AGG>, kJoinThreads, a.smem_bytes);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    const uint64_t cap = static_cast<uint64_t>(sms) * occ;
+    const int grid = static_cast<int>(a.ntiles < cap ? (a.ntiles ? a.ntiles : 1) : cap);
+    k_side_staged<MODE, AGG><<<grid, kJoinThreads, a.smem_bytes, s>>>(a, hist, strict, weight, out_sum, fk2_slot,
+                                                                       domain2, w64);
+    return cudaGetLastError();
+}
+
 cudaError_t hist_launch(const SideArgs& a, uint32_t* hist, int strict, int aggregate, int sms,
                         cudaStream_t s) {
     // small domains over enough rows (each CTA at least 4 rows per bin, so
@@ -167,6 +209,9 @@ cudaError_t hist_launch(const SideArgs& a, uint32_t* hist, int strict, int aggre
         k_hist_smem<<<grid, kHistThreads, smem, s>>>(a, hist, strict);
         return cudaGetLastError();
     }
+    if (a.stage_bytes)
+        return aggregate ? staged_launch<0, true>(a, sms, s, hist, strict, nullptr, nullptr, 0, 0, nullptr)
+                         : staged_launch<0, false>(a, sms, s, hist, strict, nullptr, nullptr, 0, 0, nullptr);
     const int grid = grid_for((a.nrows + 3) / 4, kJoinThreads, sms, 8);
     if (aggregate)
         k_side<0, true><<<grid, kJoinThreads, 0, s>>>(a, hist, strict, nullptr, nullptr, 0, 0, nullptr);
@@ -178,6 +223,7 @@ cudaError_t hist_launch(const SideArgs& a, uint32_t* hist, int strict, int aggre
 cudaError_t chain_weight_launch(const SideArgs& a, uint32_t fk2_slot, uint64_t domain2,
                                 const uint32_t* h2, unsigned long long* w, int sms,
                                 cudaStream_t s) {
+    if (a.stage_bytes) return staged_launch<3, false>(a, sms, s, nullptr, 1, h2, nullptr, fk2_slot, domain2, w);
     const int grid = grid_for((a.nrows + 3) / 4, kJoinThreads, sms, 8);
     k_side<3, false><<<grid, kJoinThreads, 0, s>>>(a, nullptr, 1, h2, nullptr, fk2_slot, domain2, w);
     return cudaGetLastError();
@@ -185,6 +231,9 @@ cudaError_t chain_weight_launch(const SideArgs& a, uint32_t fk2_slot, uint64_t d
 
 cudaError_t gather_launch(const SideArgs& a, const void* weight, int weight64,
                           unsigned long long* sum, int sms, cudaStream_t s) {
+    if (a.stage_bytes)
+        return weight64 ? staged_launch<2, false>(a, sms, s, nullptr, 0, weight, sum, 0, 0, nullptr)
+                        : staged_launch<1, false>(a, sms, s, nullptr, 0, weight, sum, 0, 0, nullptr);
     const int grid = grid_for((a.nrows + 3) / 4, kJoinThreads, sms, 8);
     if (weight64)
         k_side<2, false><<<grid, kJoinThreads, 0, s>>>(a, nullptr, 0, weight, sum, 0, 0, nullptr);

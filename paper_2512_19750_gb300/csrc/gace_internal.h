@@ -182,7 +182,24 @@ struct SideArgs {
     uint64_t domain;         // keys must lie in [0, domain)
     unsigned long long* pass_count;
     unsigned int* status;
+    // Staged scans (stage_bytes > 0): tiles of tile_rows rows of every slot
+    // pass through shared memory, slot s at byte slot_soff[s] of a stage
+    // buffer; tiles below nstaged are bulk-copied, the rest read directly.
+    uint64_t ntiles;
+    uint64_t nstaged;
+    uint32_t tile_rows;
+    uint32_t stage_bytes;
+    uint32_t nstages;
+    uint32_t smem_bytes;     // dynamic shared memory of a staged launch
+    uint32_t slot_width[kMaxFilterSlots];
+    uint32_t slot_soff[kMaxFilterSlots];
+    uint64_t timeout_ns;
 };
+
+// Rows of one warp step of a staged side scan (8 per lane) and its CTA shape.
+constexpr uint32_t kSideSlice = 256;
+constexpr int kSideWarps = 8;
+constexpr uint32_t kSideStageOff = 128;  // stage buffers follow the mbarriers
 
 // h[key] += 1 for filtered rows; strict: out-of-domain key sets kStatusKeyDomain
 cudaError_t hist_launch(const SideArgs& a, uint32_t* hist, int strict, int aggregate,

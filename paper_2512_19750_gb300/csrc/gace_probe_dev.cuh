@@ -8,6 +8,7 @@
 
 #include "gace_device.cuh"
 #include "gace_internal.h"
+#include "gace_stage.cuh"
 
 namespace gace {
 namespace probe_dev {
@@ -73,43 +74,6 @@ __device__ __forceinline__ void flush(const ProbeArgs& A, const Smem& s, int tid
     }
     for (uint32_t i = tid; i < A.nsets; i += kThreads)
         if (s.ns[i]) atomicAdd(&A.nsamp[i], static_cast<unsigned long long>(s.ns[i]));
-}
-
-// Values of NQ quads per lane: quad h covers rows slice0 + 128 h + 4 lane + r.
-template <int NQ>
-struct Vals {
-    uint32_t lo[4 * NQ];
-    uint32_t hi[4 * NQ];
-};
-
-template <int NQ>
-__device__ __forceinline__ void load_vals_smem(const unsigned char* slot_tile, uint32_t slice_local,
-                                               uint32_t width, int lane, Vals<NQ>& v) {
-#pragma unroll
-    for (int h = 0; h < NQ; ++h) {
-        Quad q;
-        load_quad_smem(slot_tile + (slice_local + 128u * h + 4u * lane) * width, width, q);
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            v.lo[4 * h + r] = q.lo[r];
-            v.hi[4 * h + r] = q.hi[r];
-        }
-    }
-}
-
-template <int NQ>
-__device__ __forceinline__ void load_vals_global(const void* ptr, uint32_t width, uint64_t slice0,
-                                                 uint64_t nrows, int lane, Vals<NQ>& v) {
-#pragma unroll
-    for (int h = 0; h < NQ; ++h) {
-        Quad q;
-        load_quad_global(ptr, width, slice0 + 128u * h + 4u * lane, nrows, q);
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            v.lo[4 * h + r] = q.lo[r];
-            v.hi[4 * h + r] = q.hi[r];
-        }
-    }
 }
 
 // Ballots of a per-row predicate over the lane's 4 NQ rows: NQ masks of 4 x 32 rows.

@@ -18,6 +18,7 @@
 #include "gace_device.cuh"
 #include "gace_internal.h"
 #include "gace_probe_dev.cuh"
+#include "gace_stage.cuh"
 
 namespace gace {
 namespace probe_dev {
@@ -34,74 +35,15 @@ __device__ __forceinline__ void issue_tile(const ProbeArgs& A, unsigned char* st
     }
 }
 
-// The staged tile pipeline of the narrow evaluations: one thread keeps up to
-// `nstages` bulk copies of the referenced columns in flight; each warp runs
-// `body(staged, sbuf, j, slice0, tile_full)` on its slices of every tile.  The
-// CTA takes tiles first, first + stride, ... below end (a whole grid striding
-// over the table, or one CTA over the tiles of a work item).  Tiles from
-// A.nstaged on (the partial last tile, and every tile when a column is not
-// 16-byte aligned) are read with plain loads by the body.  Returns true with
-// the stage barriers invalidated (their shared memory free for reuse), or
-// false when a wait gave up: the status bit is set and the CTA's copies in
-// flight have been waited for (with the same limit).
+// The staged tile pipeline of the narrow evaluations over the pass's column
+// slots: each warp runs `body(staged, sbuf, j, slice0, tile_full)` on its
+// slices of every tile (tile_pipeline gives the contract).
 template <uint32_t kSlice, class Body>
 __device__ __forceinline__ bool run_tiles(const ProbeArgs& A, const Smem& S, int tid, int warp, uint64_t first,
                                           uint64_t end, uint64_t stride, Body&& body) {
-    const uint64_t staged_end = end < A.nstaged ? end : A.nstaged;
-    if (tid == 0) {
-        for (uint32_t s = 0; s < A.nstages; ++s) mbar_init(smem_u32(&S.bars[s]), 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    if (tid == 0) {
-        for (uint32_t s = 0; s < A.nstages; ++s) {
-            const uint64_t tile = first + s * stride;
-            if (tile < staged_end) issue_tile(A, S.stages + s * A.stage_bytes, &S.bars[s], tile);
-        }
-    }
-    const uint32_t nslices = A.tile_rows / kSlice;
-    uint64_t it = 0;
-    for (;; ++it) {
-        const uint64_t tile = first + it * stride;
-        if (tile >= end) {
-            if (tid == 0)
-                for (uint32_t s = 0; s < A.nstages; ++s) mbar_inval(smem_u32(&S.bars[s]));
-            return true;
-        }
-        const bool staged = tile < A.nstaged;
-        const uint32_t stage = static_cast<uint32_t>(it % A.nstages);
-        bool fail = false;
-        if (staged)
-            fail = !mbar_wait_bounded(smem_u32(&S.bars[stage]),
-                                      static_cast<uint32_t>((it / A.nstages) & 1), A.timeout_ns);
-        if (!fail) {
-            const unsigned char* sbuf = S.stages + stage * A.stage_bytes;
-            const uint64_t tile_row0 = tile * A.tile_rows;
-            const bool tile_full = tile_row0 + A.tile_rows <= A.nrows;
-            for (uint32_t j = warp; j < nslices; j += kProbeWarps) {
-                const uint64_t slice0 = tile_row0 + static_cast<uint64_t>(j) * kSlice;
-                if (slice0 >= A.nrows) break;
-                body(staged, sbuf, j, slice0, tile_full);
-            }
-        }
-        if (__syncthreads_or(fail)) break;
-        if (tid == 0) {
-            const uint64_t next = tile + A.nstages * stride;
-            if (next < staged_end) issue_tile(A, S.stages + stage * A.stage_bytes, &S.bars[stage], next);
-        }
-    }
-    if (tid == 0) {
-        atomicOr(A.status, kStatusTimeout);
-        // let this CTA's copies in flight land before its shared memory is left
-        for (uint32_t k = 0; k < A.nstages; ++k) {
-            const uint64_t it2 = it + k;
-            const uint64_t tile2 = first + it2 * stride;
-            if (tile2 < staged_end)
-                mbar_wait_bounded(smem_u32(&S.bars[it2 % A.nstages]),
-                                  static_cast<uint32_t>((it2 / A.nstages) & 1), A.timeout_ns);
-        }
-    }
-    return false;
+    return tile_pipeline<kSlice, kProbeWarps>(
+        A, S.bars, S.stages, tid, warp, first, end, stride,
+        [&](unsigned char* stage, uint64_t* bar, uint64_t tile) { issue_tile(A, stage, bar, tile); }, body);
 }
 
 // HASH: some row set is a hashed sample (else the only device set is "all rows",
@@ -220,14 +162,6 @@ __device__ __forceinline__ bool narrow_run(const ProbeArgs& A, const Smem& S, in
     if (HASH && lane < static_cast<int>(nsets) && nsr) atomicAdd(&S.ns[lane], nsr);
     return true;
 }
-
-// Bit i of the result: per-row predicate `pred_expr(i)` for the lane's 4 NQ rows.
-#define GACE_ROWBITS(R_, pred_expr, out)               \
-    do {                                               \
-        out = 0u;                                      \
-        _Pragma("unroll") for (int i_ = 0; i_ < R_; ++i_) \
-            if (pred_expr(i_)) out |= 1u << i_;        \
-    } while (0)
 
 // Single-predicate evaluation of one column slot: for every term of the slot,
 // the lane's row results as a bit mask; ok &= mask; with marginals, the warp

@@ -8,6 +8,7 @@
 
 #include "gace_device.cuh"
 #include "gace_internal.h"
+#include "gace_stage.cuh"
 
 namespace gace {
 namespace side_dev {
@@ -228,6 +229,162 @@ __device__ __forceinline__ void side_groups(const SideArgs& A, uint32_t* hist, i
                 side_rows<MODE, AGG>(A, hist, strict, weight, domain2, w64, key[u], fk2[u], p[u], mine[u], npass,
                                      acc);
     }
+}
+
+// ------------------------------------------------------- staged side scans
+//
+// The same side modes over tiles that a bulk-copy pipeline stages in shared
+// memory (tile_pipeline): no warp waits on a column load, so a gather's only
+// latency is its weight load from L2.  A lane takes eight rows of each 256-row
+// slice (quad h = rows slice0 + 128 h + 4 lane + r, bit 4 h + r of its masks).
+
+template <int NQ>
+__device__ __forceinline__ void side_vals(const SideArgs& A, uint32_t slot, bool staged, const unsigned char* sbuf,
+                                          uint32_t j, uint64_t slice0, int lane, Vals<NQ>& v) {
+    if (staged)
+        load_vals_smem<NQ>(sbuf + A.slot_soff[slot], j * kSideSlice, A.slot_width[slot], lane, v);
+    else
+        load_vals_global<NQ>(A.slot_ptr[slot], A.slot_width[slot], slice0, A.nrows, lane, v);
+}
+
+// Rows (bits) of the lane's values on which one filter term holds; the kind
+// is tested once for all rows.
+template <int NQ>
+__device__ __forceinline__ uint32_t filter_bits(const FilterTerm& ft, const Vals<NQ>& v, const uint32_t* pool) {
+    constexpr int R = 4 * NQ;
+    const DevTerm& c = ft.c;
+    uint32_t b = 0u;
+    switch (ft.kind) {
+        case kRangeI32: {
+#define PR(i) ((v.lo[i] - c.a_lo) <= c.b_lo)
+            GACE_ROWBITS(R, PR, b);
+#undef PR
+            break;
+        }
+        case kRangeI64: {
+            const uint64_t lo = join64(c.a_lo, c.a_hi), span = join64(c.b_lo, c.b_hi);
+#define PR(i) ((join64(v.lo[i], v.hi[i]) - lo) <= span)
+            GACE_ROWBITS(R, PR, b);
+#undef PR
+            break;
+        }
+        case kRangeF32: {
+            const float lo = __uint_as_float(c.a_lo), hi = __uint_as_float(c.b_lo);
+#define PR(i) (__uint_as_float(v.lo[i]) >= lo && __uint_as_float(v.lo[i]) <= hi)
+            GACE_ROWBITS(R, PR, b);
+#undef PR
+            break;
+        }
+        default: {  // IN lists
+#define PT(i) term_holds(ft.kind, c, v.lo[i], v.hi[i], pool)
+            GACE_ROWBITS(R, PT, b);
+#undef PT
+            break;
+        }
+    }
+    return b;
+}
+
+__device__ __forceinline__ int64_t key_of(uint32_t dtype, uint32_t lo, uint32_t hi) {
+    return dtype == 1 ? static_cast<int64_t>(join64(lo, hi)) : static_cast<int64_t>(static_cast<int32_t>(lo));
+}
+
+// One side mode over tiles [first, end) of the staged scan (stride: the grid's
+// CTAs); npass and acc are per thread.  MODE as in side_rows.  False when a
+// pipeline wait gave up (kStatusTimeout set).
+template <int MODE, bool AGG>
+__device__ __forceinline__ bool side_tiles(const SideArgs& A, uint64_t* bars, unsigned char* stages, int tid,
+                                           int lane, int warp, uint64_t first, uint64_t end, uint64_t stride,
+                                           uint32_t* hist, int strict, const void* weight, uint32_t fk2_slot,
+                                           uint64_t domain2, unsigned long long* w64, unsigned long long& npass,
+                                           unsigned long long& acc) {
+    constexpr int NQ = 2, R = 4 * NQ;
+    constexpr uint32_t kAll = (1u << R) - 1u;
+    bool bad_key = false;
+    const uint32_t key_dt = A.slot_dtype[A.key_slot];
+    const uint32_t fk2_dt = MODE == 3 ? A.slot_dtype[fk2_slot] : 0u;
+    const bool ok = tile_pipeline<kSideSlice, kSideWarps>(
+        A, bars, stages, tid, warp, first, end, stride,
+        [&](unsigned char* stage, uint64_t* bar, uint64_t tile) {
+            const uint32_t b = smem_u32(bar);
+            mbar_arrive_expect_tx(b, A.stage_bytes);
+            const uint64_t row0 = tile * A.tile_rows;
+            for (uint32_t s = 0; s < A.nslots; ++s) {
+                const unsigned char* src = static_cast<const unsigned char*>(A.slot_ptr[s]) + row0 * A.slot_width[s];
+                bulk_g2s(smem_u32(stage + A.slot_soff[s]), src, A.tile_rows * A.slot_width[s], b);
+            }
+        },
+        [&](bool staged, const unsigned char* sbuf, uint32_t j, uint64_t slice0, bool tile_full) {
+            uint32_t pass = kAll;
+            if (!tile_full) {
+#define PV(i) (slice0 + 128u * ((i) / 4) + 4u * lane + ((i) % 4) < A.nrows)
+                GACE_ROWBITS(R, PV, pass);
+#undef PV
+            }
+            for (uint32_t t = 0; t < A.nterms; ++t) {
+                const FilterTerm& ft = A.terms[t];
+                Vals<NQ> v;
+                side_vals<NQ>(A, ft.slot, staged, sbuf, j, slice0, lane, v);
+                pass &= filter_bits<NQ>(ft, v, A.pool);
+            }
+            npass += __popc(pass);
+            if (!__any_sync(kFullMask, pass != 0u)) return;  // warp-uniform
+            Vals<NQ> kv, fv;
+            side_vals<NQ>(A, A.key_slot, staged, sbuf, j, slice0, lane, kv);
+            if (MODE == 3) side_vals<NQ>(A, fk2_slot, staged, sbuf, j, slice0, lane, fv);
+            uint32_t use = 0u;
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                const int64_t k = key_of(key_dt, kv.lo[i], kv.hi[i]);
+                const bool in_dom = k >= 0 && static_cast<uint64_t>(k) < A.domain;
+                if ((pass >> i) & 1u) {
+                    if (in_dom) use |= 1u << i;
+                    else bad_key = true;
+                }
+            }
+            if (MODE == 1 || MODE == 2) {
+                // every weight load of the lane issued before any is added
+                unsigned long long w[R];
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    const uint64_t k = static_cast<uint64_t>(key_of(key_dt, kv.lo[i], kv.hi[i]));
+                    w[i] = 0;
+                    if ((use >> i) & 1u)
+                        w[i] = MODE == 2 ? __ldg(static_cast<const unsigned long long*>(weight) + k)
+                                         : __ldg(static_cast<const uint32_t*>(weight) + k);
+                }
+#pragma unroll
+                for (int i = 0; i < R; ++i) acc += w[i];
+            } else if (MODE == 0) {
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    const bool u = (use >> i) & 1u;
+                    const uint64_t k = static_cast<uint64_t>(key_of(key_dt, kv.lo[i], kv.hi[i]));
+                    if (AGG) {
+                        unsigned grp;
+                        if (A.domain <= 0xFFFFFFFFull)
+                            grp = __match_any_sync(kFullMask, u ? static_cast<uint32_t>(k) : 0xFFFFFFFFu);
+                        else
+                            grp = __match_any_sync(kFullMask, u ? static_cast<unsigned long long>(k) : ~0ull);
+                        if (u && (__ffs(grp) - 1) == lane) atomicAdd(&hist[k], __popc(grp));
+                    } else if (u) {
+                        atomicAdd(&hist[k], 1u);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    const int64_t f2 = key_of(fk2_dt, fv.lo[i], fv.hi[i]);
+                    if (((use >> i) & 1u) && f2 >= 0 && static_cast<uint64_t>(f2) < domain2) {
+                        const uint32_t h = static_cast<const uint32_t*>(weight)[f2];
+                        if (h)
+                            atomicAdd(&w64[key_of(key_dt, kv.lo[i], kv.hi[i])], static_cast<unsigned long long>(h));
+                    }
+                }
+            }
+        });
+    if (bad_key && strict) atomicOr(A.status, kStatusKeyDomain);
+    return ok;
 }
 
 // A CTA's shared-memory histogram of K bins into the global one (nonzero bins).

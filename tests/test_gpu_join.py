@@ -151,3 +151,43 @@ def test_skewed_keys_small_domain(g, gctx, orc, cuda, method):
     finally:
         g.gace_unload(gctx, did)
         g.gace_unload(gctx, fid)
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_staged_and_direct_sides(g, gctx, orc, cuda, method):
+    """The same join over 16-byte aligned columns (staged scans) and over
+    columns borrowed one element off alignment (direct loads), with int64
+    keys and float32, int64 and IN filters on several columns: both equal the
+    oracle, row counts included, over ragged tile tails."""
+    from workloads import F32
+
+    gen = torch.Generator(device=cuda).manual_seed(31)
+    nf, nd, K = 1_000_003, 50_001, 50_000
+    fk = torch.randint(-3, K + 3, (nf + 1,), generator=gen, device=cuda, dtype=torch.int64)
+    f1 = torch.rand(nf + 1, generator=gen, device=cuda, dtype=torch.float32)
+    f2 = torch.randint(0, 1000, (nf + 1,), generator=gen, device=cuda, dtype=torch.int64)
+    dk = torch.randint(0, K, (nd + 1,), generator=gen, device=cuda, dtype=torch.int64)
+    d1 = torch.randint(0, 100, (nd + 1,), generator=gen, device=cuda, dtype=torch.int32)
+    fdt, ddt = [I64, F32, I64], [I64, I32]
+    ft = [Term(1, RANGE, 0.25, 0.75), Term(2, RANGE, 100, 899), Term(2, IN, values=tuple(range(0, 1000, 2)))]
+    dt = [Term(1, RANGE, 10, 60)]
+    results = []
+    for aligned in (True, False):  # the same values: copies, then views one element in
+        fcols = [fk[1:], f1[1:], f2[1:]]
+        dcols = [dk[1:], d1[1:]]
+        if aligned:
+            fcols, dcols = [c.clone() for c in fcols], [c.clone() for c in dcols]
+        fid, did = g.gace_load_columns(gctx, fcols, borrow=True), g.gace_load_columns(gctx, dcols, borrow=True)
+        try:
+            out = g.gace_join_card(gctx, g.JoinSideSpec(fid, 0, ft, fdt), g.JoinSideSpec(did, 0, dt, ddt), K,
+                                   None, 0, 0, method)
+            F = Table("f", [c.cpu() for c in fcols], fdt)
+            D = Table("d", [c.cpu() for c in dcols], ddt)
+            rc, card, fp, dp = orc.join_card(JoinSide(F, 0, ft), JoinSide(D, 0, dt), K)
+            assert rc == 0
+            assert (out["card"], out["fact_rows"], out["dim_rows"]) == (card, fp, dp), aligned
+            results.append(out)
+        finally:
+            g.gace_unload(gctx, fid)
+            g.gace_unload(gctx, did)
+    assert results[0] == results[1]
