@@ -605,8 +605,18 @@ double hll_estimate_host(const uint8_t* regs, uint32_t p) {
 #ifndef GACE_SIDE_STAGED
 #define GACE_SIDE_STAGED 1
 #endif
+#ifndef GACE_SIDE_TARGET_KB
+#define GACE_SIDE_TARGET_KB 32
+#endif
+#ifndef GACE_SIDE_BUDGET_KB
+#define GACE_SIDE_BUDGET_KB 64
+#endif
+#ifndef GACE_SIDE_STAGES
+#define GACE_SIDE_STAGES 3
+#endif
 void plan_side_stages(SideArgs& a) {
-    constexpr uint32_t kTarget = 32u << 10, kBudget = 64u << 10;
+    constexpr uint32_t kTarget = GACE_SIDE_TARGET_KB << 10, kBudget = GACE_SIDE_BUDGET_KB << 10;
+    static_assert(GACE_SIDE_STAGES >= 2 && GACE_SIDE_STAGES <= kMaxStages, "stage count");
     const uint32_t sweep = kSideSlice * kSideWarps;
     uint32_t rowbytes = 0;
     bool aligned = true;
@@ -619,7 +629,7 @@ void plan_side_stages(SideArgs& a) {
     a.tile_rows = sweep;
     uint32_t tile = sweep;
     while (tile * 2 * rowbytes <= kTarget && tile < 8 * sweep) tile *= 2;
-    uint32_t nst = 3;
+    uint32_t nst = GACE_SIDE_STAGES;
     while (nst > 2 && nst * tile * rowbytes > kBudget) --nst;
     if (!GACE_SIDE_STAGED || !aligned || rowbytes == 0 || nst * tile * rowbytes > kBudget) return;
     a.tile_rows = tile;

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "gace_device.cuh"
 #include "gace_internal.h"
 #include "gace_stage.cuh"
@@ -242,7 +244,7 @@ template <int NQ>
 __device__ __forceinline__ void side_vals(const SideArgs& A, uint32_t slot, bool staged, const unsigned char* sbuf,
                                           uint32_t j, uint64_t slice0, int lane, Vals<NQ>& v) {
     if (staged)
-        load_vals_smem<NQ>(sbuf + A.slot_soff[slot], j * kSideSlice, A.slot_width[slot], lane, v);
+        load_vals_smem<NQ>(sbuf + A.slot_soff[slot], j * 128u * NQ, A.slot_width[slot], lane, v);
     else
         load_vals_global<NQ>(A.slot_ptr[slot], A.slot_width[slot], slice0, A.nrows, lane, v);
 }
@@ -289,21 +291,49 @@ __device__ __forceinline__ int64_t key_of(uint32_t dtype, uint32_t lo, uint32_t 
     return dtype == 1 ? static_cast<int64_t>(join64(lo, hi)) : static_cast<int64_t>(static_cast<int32_t>(lo));
 }
 
+// Key of row i of the lane's values as an index, and whether it lies in
+// [0, domain).  An int32 key is in the domain iff its bits, read unsigned, are
+// below min(domain, 2^31) (negative keys read as 2^31 or more).
+template <bool KEY64, int NQ>
+__device__ __forceinline__ uint64_t key_index(const Vals<NQ>& v, int i, uint64_t domain, uint32_t dom32,
+                                              bool& in_dom) {
+    if (KEY64) {
+        const uint64_t k = join64(v.lo[i], v.hi[i]);
+        in_dom = k < domain;  // a negative key reads as 2^63 or more
+        return k;
+    }
+    in_dom = v.lo[i] < dom32;
+    return v.lo[i];
+}
+
+// Rows of one staged side scan step per lane: gathers take 16 (sixteen
+// weight loads in flight before any is added), the atomic modes 8.
+template <int MODE>
+__host__ __device__ constexpr int side_nq() { return (MODE == 1 || MODE == 2) ? 4 : 2; }
+
 // One side mode over tiles [first, end) of the staged scan (stride: the grid's
-// CTAs); npass and acc are per thread.  MODE as in side_rows.  False when a
-// pipeline wait gave up (kStatusTimeout set).
-template <int MODE, bool AGG>
+// CTAs); npass and acc are per thread.  MODE as in side_rows; KEY64: the key
+// column is int64 (else int32).  False when a pipeline wait gave up
+// (kStatusTimeout set).
+template <int MODE, bool AGG, bool KEY64>
 __device__ __forceinline__ bool side_tiles(const SideArgs& A, uint64_t* bars, unsigned char* stages, int tid,
                                            int lane, int warp, uint64_t first, uint64_t end, uint64_t stride,
                                            uint32_t* hist, int strict, const void* weight, uint32_t fk2_slot,
                                            uint64_t domain2, unsigned long long* w64, unsigned long long& npass,
                                            unsigned long long& acc) {
-    constexpr int NQ = 2, R = 4 * NQ;
-    constexpr uint32_t kAll = (1u << R) - 1u;
+    constexpr int NQ = side_nq<MODE>(), R = 4 * NQ;
+    constexpr uint32_t kSlice = 128u * NQ;
+    constexpr uint32_t kAll = R == 32 ? 0xFFFFFFFFu : (1u << R) - 1u;
     bool bad_key = false;
-    const uint32_t key_dt = A.slot_dtype[A.key_slot];
+    const uint32_t dom32 = A.domain < 0x80000000ull ? static_cast<uint32_t>(A.domain) : 0x80000000u;
+    // 32-bit gathers: the weights loaded in one step are added in the lane's
+    // next step, so that their latency overlaps the next tile's wait and filter
+    using W = typename std::conditional<MODE == 2, unsigned long long, uint32_t>::type;
+    W wp[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) wp[i] = 0;
     const uint32_t fk2_dt = MODE == 3 ? A.slot_dtype[fk2_slot] : 0u;
-    const bool ok = tile_pipeline<kSideSlice, kSideWarps>(
+    const bool ok = tile_pipeline<kSlice, kSideWarps>(
         A, bars, stages, tid, warp, first, end, stride,
         [&](unsigned char* stage, uint64_t* bar, uint64_t tile) {
             const uint32_t b = smem_u32(bar);
@@ -328,41 +358,47 @@ __device__ __forceinline__ bool side_tiles(const SideArgs& A, uint64_t* bars, un
                 pass &= filter_bits<NQ>(ft, v, A.pool);
             }
             npass += __popc(pass);
+            if (MODE == 1) {
+#pragma unroll
+                for (int i = 0; i < R; ++i) acc += wp[i];
+#pragma unroll
+                for (int i = 0; i < R; ++i) wp[i] = 0;
+            }
             if (!__any_sync(kFullMask, pass != 0u)) return;  // warp-uniform
-            Vals<NQ> kv, fv;
+            Vals<NQ> kv;
             side_vals<NQ>(A, A.key_slot, staged, sbuf, j, slice0, lane, kv);
-            if (MODE == 3) side_vals<NQ>(A, fk2_slot, staged, sbuf, j, slice0, lane, fv);
             uint32_t use = 0u;
 #pragma unroll
             for (int i = 0; i < R; ++i) {
-                const int64_t k = key_of(key_dt, kv.lo[i], kv.hi[i]);
-                const bool in_dom = k >= 0 && static_cast<uint64_t>(k) < A.domain;
-                if ((pass >> i) & 1u) {
-                    if (in_dom) use |= 1u << i;
-                    else bad_key = true;
-                }
+                bool in_dom;
+                key_index<KEY64>(kv, i, A.domain, dom32, in_dom);
+                if (in_dom) use |= 1u << i;
             }
+            bad_key |= (pass & ~use) != 0u;
+            use &= pass;
             if (MODE == 1 || MODE == 2) {
-                // every weight load of the lane issued before any is added
-                unsigned long long w[R];
+                // every weight load of the step issued at once; added next step
 #pragma unroll
                 for (int i = 0; i < R; ++i) {
-                    const uint64_t k = static_cast<uint64_t>(key_of(key_dt, kv.lo[i], kv.hi[i]));
-                    w[i] = 0;
-                    if ((use >> i) & 1u)
-                        w[i] = MODE == 2 ? __ldg(static_cast<const unsigned long long*>(weight) + k)
-                                         : __ldg(static_cast<const uint32_t*>(weight) + k);
+                    bool d;
+                    const uint64_t k = key_index<KEY64>(kv, i, A.domain, dom32, d);
+                    if ((use >> i) & 1u) wp[i] = __ldg(static_cast<const W*>(weight) + k);
                 }
+                if (MODE == 2) {  // 64-bit weights: no registers to carry them over, added at once
 #pragma unroll
-                for (int i = 0; i < R; ++i) acc += w[i];
+                    for (int i = 0; i < R; ++i) acc += wp[i];
+#pragma unroll
+                    for (int i = 0; i < R; ++i) wp[i] = 0;
+                }
             } else if (MODE == 0) {
 #pragma unroll
                 for (int i = 0; i < R; ++i) {
                     const bool u = (use >> i) & 1u;
-                    const uint64_t k = static_cast<uint64_t>(key_of(key_dt, kv.lo[i], kv.hi[i]));
+                    bool d;
+                    const uint64_t k = key_index<KEY64>(kv, i, A.domain, dom32, d);
                     if (AGG) {
                         unsigned grp;
-                        if (A.domain <= 0xFFFFFFFFull)
+                        if (!KEY64 || A.domain <= 0xFFFFFFFFull)  // keys below 0xFFFFFFFF: a 32-bit match
                             grp = __match_any_sync(kFullMask, u ? static_cast<uint32_t>(k) : 0xFFFFFFFFu);
                         else
                             grp = __match_any_sync(kFullMask, u ? static_cast<unsigned long long>(k) : ~0ull);
@@ -372,17 +408,24 @@ __device__ __forceinline__ bool side_tiles(const SideArgs& A, uint64_t* bars, un
                     }
                 }
             } else {
+                Vals<NQ> fv;
+                side_vals<NQ>(A, fk2_slot, staged, sbuf, j, slice0, lane, fv);
 #pragma unroll
                 for (int i = 0; i < R; ++i) {
                     const int64_t f2 = key_of(fk2_dt, fv.lo[i], fv.hi[i]);
                     if (((use >> i) & 1u) && f2 >= 0 && static_cast<uint64_t>(f2) < domain2) {
                         const uint32_t h = static_cast<const uint32_t*>(weight)[f2];
+                        bool d;
                         if (h)
-                            atomicAdd(&w64[key_of(key_dt, kv.lo[i], kv.hi[i])], static_cast<unsigned long long>(h));
+                            atomicAdd(&w64[key_index<KEY64>(kv, i, A.domain, dom32, d)],
+                                      static_cast<unsigned long long>(h));
                     }
                 }
             }
         });
+    if (MODE == 1)
+#pragma unroll
+        for (int i = 0; i < R; ++i) acc += wp[i];
     if (bad_key && strict) atomicOr(A.status, kStatusKeyDomain);
     return ok;
 }
