@@ -180,6 +180,66 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch_probe(const BatchItem* __
     }
 }
 
+// Join sides of tables staged through shared memory (gathers, chain weights,
+// histograms over large key domains): per item, the staged tile pipeline over
+// the item's tiles.  The side arguments are copied into shared memory once per
+// item.
+template <int MODE, bool AGG>
+__device__ __forceinline__ bool side_item_staged(const SideArgs& A, const BatchJob& J, const BatchItem& it,
+                                                 unsigned char* smem, int tid, int lane, int warp,
+                                                 unsigned long long& npass, unsigned long long& acc) {
+    const uint64_t first = it.begin / A.tile_rows;
+    uint64_t end = (it.end + A.tile_rows - 1) / A.tile_rows;
+    if (end > A.ntiles) end = A.ntiles;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+    unsigned char* stages = smem + kSideStageOff;
+    if (A.slot_dtype[A.key_slot] == 1)
+        return side_tiles<MODE, AGG, true>(A, bars, stages, tid, lane, warp, first, end, 1, J.hist, J.strict,
+                                           J.weight, J.fk2_slot, J.domain2, J.w64, npass, acc);
+    return side_tiles<MODE, AGG, false>(A, bars, stages, tid, lane, warp, first, end, 1, J.hist, J.strict, J.weight,
+                                        J.fk2_slot, J.domain2, J.w64, npass, acc);
+}
+
+__global__ void __launch_bounds__(kThreads, 3) k_batch_side(const BatchItem* __restrict__ items, uint32_t nitems,
+                                                            const BatchJob* __restrict__ jobs, unsigned int* head) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint32_t s_item;
+    __shared__ __align__(16) SideArgs sA;
+    __shared__ unsigned long long scratch[kProbeWarps];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(head, 1u);
+        __syncthreads();
+        const uint32_t k = s_item;
+        if (k >= nitems) return;
+        const BatchItem it = items[k];
+        const BatchJob& J = jobs[it.job];
+        {
+            const uint4* src = reinterpret_cast<const uint4*>(J.side);
+            uint4* dst = reinterpret_cast<uint4*>(&sA);
+            for (uint32_t i = tid; i < sizeof(SideArgs) / 16; i += kThreads) dst[i] = src[i];
+        }
+        __syncthreads();  // sA and s_item are read below; both are rewritten only after the next barrier
+        unsigned long long npass = 0, acc = 0;
+        bool ok;
+        switch (J.kind) {
+            case kJobHist:
+            case kJobHistAgg: ok = side_item_staged<0, true>(sA, J, it, smem, tid, lane, warp, npass, acc); break;
+            case kJobGather32: ok = side_item_staged<1, false>(sA, J, it, smem, tid, lane, warp, npass, acc); break;
+            case kJobGather64: ok = side_item_staged<2, false>(sA, J, it, smem, tid, lane, warp, npass, acc); break;
+            default: ok = side_item_staged<3, false>(sA, J, it, smem, tid, lane, warp, npass, acc); break;
+        }
+        if (!ok) return;  // uniform over the CTA; the status word says why
+        const unsigned long long tp = block_sum_u64<kProbeWarps>(npass, scratch);
+        if (tid == 0 && tp) atomicAdd(sA.pass_count, tp);
+        if (J.kind == kJobGather32 || J.kind == kJobGather64) {
+            const unsigned long long ta = block_sum_u64<kProbeWarps>(acc, scratch);
+            if (tid == 0 && ta) atomicAdd(J.out, ta);
+        }
+        __syncthreads();  // shared memory is reused by the next item
+    }
+}
+
 // Join histograms over small key domains: per item, a shared-memory
 // histogram of the item's rows (equal keys of a warp combined first), then
 // its nonzero bins into the job's global histogram.
@@ -247,6 +307,7 @@ cudaError_t batch_configure(int smem_optin) {
     cudaError_t e = configure_one(k_batch, smem_optin);
     if (e == cudaSuccess) e = configure_one(k_batch_probe, smem_optin);
     if (e == cudaSuccess) e = configure_one(k_batch_hist, smem_optin);
+    if (e == cudaSuccess) e = configure_one(k_batch_side, smem_optin);
     return e;
 }
 
@@ -257,6 +318,8 @@ int batch_occupancy(uint32_t smem_bytes, int cls) {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_probe, kThreads, smem_bytes);
     else if (cls == kClassHist)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_hist, kHistThreads, smem_bytes);
+    else if (cls == kClassSide)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_side, kThreads, smem_bytes);
     else
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch, kThreads, smem_bytes);
     return e == cudaSuccess ? n : 0;
@@ -268,6 +331,8 @@ cudaError_t batch_launch(const BatchItem* items, uint32_t nitems, const BatchJob
         k_batch_probe<<<grid, kThreads, smem_bytes, s>>>(items, nitems, jobs, head);
     else if (cls == kClassHist)
         k_batch_hist<<<grid, kHistThreads, smem_bytes, s>>>(items, nitems, jobs, head);
+    else if (cls == kClassSide)
+        k_batch_side<<<grid, kThreads, smem_bytes, s>>>(items, nitems, jobs, head);
     else
         k_batch<<<grid, kThreads, smem_bytes, s>>>(items, nitems, jobs, head);
     return cudaGetLastError();

@@ -363,6 +363,11 @@ void emit_jobs(ReqPlan& rp, unsigned char* dws, unsigned int* batch_status, std:
     auto side_job = [&](uint32_t kind, int i, uint32_t phase, uint32_t strict) {
         JobRec jr;
         jr.cost = 2;  // latency-bound: a key's filter, then its weight or histogram update
+        if (rp.side[i].stage_bytes) {  // aligned, narrow rows: the staged side kernel, by whole tiles
+            jr.cls = kClassSide;
+            jr.smem = rp.side[i].smem_bytes;
+            jr.granule = rp.side[i].tile_rows;
+        }
         jr.job.kind = kind;
         jr.job.side = side_dev(i);
         jr.job.strict = strict;
@@ -459,7 +464,8 @@ gace_status batch_setup(gace_ctx* ctx) {
 
 uint64_t item_units(const JobRec& jr, uint64_t chunk) {
     uint64_t piece = std::max<uint64_t>(128, chunk / jr.cost);
-    if (jr.cls == kClassProbe) piece = std::max<uint64_t>(piece, 4 * jr.granule);  // bulk copies overlap
+    if (jr.cls == kClassProbe || jr.cls == kClassSide)
+        piece = std::max<uint64_t>(piece, 4 * jr.granule);  // bulk copies overlap
     return round_up(piece, jr.granule);
 }
 
@@ -495,8 +501,8 @@ struct BatchRun {
     std::vector<BatchItem> items;
     uint32_t pbeg[kPhases][kClasses] = {}, pcnt[kPhases][kClasses] = {};
     uint64_t jobs_off = 0, items_off = 0, in_end = 0, small_base = 0, small_end = 0, end = 0;
-    uint32_t smem[kClasses] = {0, 0, 0};
-    int grid[kClasses] = {1, 1, 1};
+    uint32_t smem[kClasses] = {};
+    int grid[kClasses] = {1, 1, 1, 1};
     uint64_t rows = 0, bytes = 0, ops = 0;
     int launches = 0;
 };

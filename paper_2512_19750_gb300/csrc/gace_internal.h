@@ -168,7 +168,7 @@ struct FilterTerm {
     DevTerm c;
 };
 
-struct SideArgs {
+struct alignas(16) SideArgs {
     uint64_t nrows;
     uint32_t nslots;
     uint32_t nterms;
@@ -195,6 +195,8 @@ struct SideArgs {
     uint32_t slot_soff[kMaxFilterSlots];
     uint64_t timeout_ns;
 };
+
+static_assert(sizeof(SideArgs) % 16 == 0, "SideArgs is copied in 16-byte words");
 
 // Rows of one warp step of a staged side scan (8 per lane) and its CTA shape.
 constexpr uint32_t kSideSlice = 256;
@@ -269,12 +271,14 @@ struct CopyDesc {
 
 // Item classes, each drained by its own persistent kernel: narrow and
 // single-predicate probe items (k_batch_probe), join histograms over small
-// key domains counted in shared memory (k_batch_hist), everything else
-// (k_batch).
+// key domains counted in shared memory (k_batch_hist), join sides whose
+// columns stream through the staged tile pipeline (k_batch_side), everything
+// else (k_batch).
 constexpr int kClassProbe = 0;
 constexpr int kClassGeneral = 1;
 constexpr int kClassHist = 2;
-constexpr int kClasses = 3;
+constexpr int kClassSide = 3;
+constexpr int kClasses = 4;
 constexpr int kPhases = 3;  // dependency phases of a batch (a join's histogram before its readers)
 
 // Key domains up to this many entries are histogrammed per CTA in shared

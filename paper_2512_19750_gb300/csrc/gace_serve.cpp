@@ -628,7 +628,7 @@ gace_status ServeState::build_step(StepSet& S, std::vector<std::unique_ptr<Live>
     }
     std::vector<BatchItem> citems[kClasses];
     std::vector<BatchJob> jobs;
-    uint32_t smem[kClasses] = {0, 0, 0};
+    uint32_t smem[kClasses] = {};
     size_t nitems = 0;
     if (!ring.empty()) {
         const size_t n = ring.size();
