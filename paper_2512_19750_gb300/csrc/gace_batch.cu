@@ -200,7 +200,10 @@ __device__ __forceinline__ bool side_item_staged(const SideArgs& A, const BatchJ
                                         J.fk2_slot, J.domain2, J.w64, npass, acc);
 }
 
-__global__ void __launch_bounds__(kThreads, 3) k_batch_side(const BatchItem* __restrict__ items, uint32_t nitems,
+#ifndef GACE_BATCH_SIDE_CTAS
+#define GACE_BATCH_SIDE_CTAS 2
+#endif
+__global__ void __launch_bounds__(kThreads, GACE_BATCH_SIDE_CTAS) k_batch_side(const BatchItem* __restrict__ items, uint32_t nitems,
                                                             const BatchJob* __restrict__ jobs, unsigned int* head) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint32_t s_item;

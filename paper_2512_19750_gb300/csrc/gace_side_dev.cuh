@@ -93,21 +93,21 @@ template <bool SMEM, int DT, int U = 1>
 __device__ __forceinline__ void hll_groups(const HllArgs& A, uint32_t* sregs, uint64_t first, uint64_t end,
                                            uint64_t stride) {
     constexpr uint32_t width = DT == 1 ? 8 : 4;
-    if (U == 1) {
+    if constexpr (U == 1) {
         for (uint64_t g = first; g < end; g += stride) {
             Quad v;
             load_quad_global(A.col, width, g * 4, A.nrows, v);
             hll_quad<SMEM, DT>(A, sregs, v, g * 4);
         }
-        return;
-    }
-    for (uint64_t g = first; g < end; g += 2 * stride) {
-        const uint64_t g2 = g + stride;
-        Quad v0, v1;
-        load_quad_global(A.col, width, g * 4, A.nrows, v0);
-        load_quad_global(A.col, width, g2 * 4, A.nrows, v1);
-        hll_quad<SMEM, DT>(A, sregs, v0, g * 4);
-        if (g2 < end) hll_quad<SMEM, DT>(A, sregs, v1, g2 * 4);
+    } else {
+        for (uint64_t g = first; g < end; g += 2 * stride) {
+            const uint64_t g2 = g + stride;
+            Quad v0, v1;
+            load_quad_global(A.col, width, g * 4, A.nrows, v0);
+            load_quad_global(A.col, width, g2 * 4, A.nrows, v1);
+            hll_quad<SMEM, DT>(A, sregs, v0, g * 4);
+            if (g2 < end) hll_quad<SMEM, DT>(A, sregs, v1, g2 * 4);
+        }
     }
 }
 
