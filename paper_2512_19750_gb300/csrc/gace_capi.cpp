@@ -577,6 +577,15 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
     }
     A.ntiles = (tab.nrows + A.tile_rows - 1) / A.tile_rows;
     A.nstaged = staged ? tab.nrows / A.tile_rows : 0;
+    // A narrow pass whose row sets are all block samples reads only the tiles
+    // that hold a sampled block (the point of sampling whole blocks), when a
+    // tile spans few enough blocks to test them all.
+    bool blocks_only = A.narrow && A.nsets > 0;
+    for (uint32_t q = 0; q < A.nsets; ++q) {
+        const SetDesc& d = A.sets[q];
+        blocks_only = blocks_only && d.kind == 2 && d.mode == 2 && d.block_rows * kSkipBlocksPerTile >= A.tile_rows;
+    }
+    A.skip_tiles = blocks_only ? 1u : 0u;
     return GACE_OK;
 }
 

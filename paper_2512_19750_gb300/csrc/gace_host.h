@@ -353,6 +353,8 @@ double hll_estimate_host(const uint8_t* regs, uint32_t p);
 struct SideWork {
     uint64_t rows = 0, rowbytes = 0, ops_per_row = 1;
 };
+// A pass skips tiles only when each spans at most this many sample blocks.
+constexpr uint64_t kSkipBlocksPerTile = 8;
 void plan_side_stages(SideArgs& a);
 gace_status build_side(gace_ctx* ctx, const gace_join_side& js, const char* name, int extra_col, SideArgs& a,
                        std::vector<uint32_t>& pool, TableRec** tab_out, uint32_t* extra_slot, SideWork& work);

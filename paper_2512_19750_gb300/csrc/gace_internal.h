@@ -97,6 +97,7 @@ struct alignas(16) ProbeArgs {
     uint32_t nslots, nsets, nterms, npreds, npool, npredterms;
     uint32_t want_marg;
     uint32_t narrow;        // 1: lane-owned counters, staged tiles; 0: wide batch kernel
+    uint32_t skip_tiles;    // 1: every row set is a block sample; tiles with no sampled block are skipped
     uint32_t smem_bytes;
     // smem byte offsets
     uint32_t off_stage, off_terms, off_pool, off_poff, off_pterm, off_tm, off_keep,

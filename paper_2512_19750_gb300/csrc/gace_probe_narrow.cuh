@@ -35,15 +35,35 @@ __device__ __forceinline__ void issue_tile(const ProbeArgs& A, unsigned char* st
     }
 }
 
+// Whether any row of a tile lies in a sampled block of some row set (every
+// set of a pass that skips tiles is a block sample): the tile's blocks are
+// hashed as the per-row membership test hashes them.
+__device__ __forceinline__ bool probe_tile_live(const ProbeArgs& A, uint64_t tile) {
+    const uint64_t r0 = tile * A.tile_rows;
+    const uint64_t r1 = (r0 + A.tile_rows < A.nrows ? r0 + A.tile_rows : A.nrows) - 1;
+    for (uint32_t q = 0; q < A.nsets; ++q) {
+        const SetDesc& sd = A.sets[q];
+        if (sd.kind != 2 || sd.mode != 2) return true;
+        const uint64_t b0 = sd.block_shift >= 0 ? r0 >> sd.block_shift : r0 / sd.block_rows;
+        const uint64_t b1 = sd.block_shift >= 0 ? r1 >> sd.block_shift : r1 / sd.block_rows;
+        for (uint64_t b = b0; b <= b1; ++b)
+            if (splitmix64(b ^ sd.seedhash) < sd.thresh) return true;
+    }
+    return false;
+}
+
 // The staged tile pipeline of the narrow evaluations over the pass's column
 // slots: each warp runs `body(staged, sbuf, j, slice0, tile_full)` on its
-// slices of every tile (tile_pipeline gives the contract).
-template <uint32_t kSlice, class Body>
+// slices of every tile that can hold a counted row (tile_pipeline gives the
+// contract).
+// HASH: the pass has hashed row sets, so it may skip tiles.
+template <uint32_t kSlice, bool HASH, class Body>
 __device__ __forceinline__ bool run_tiles(const ProbeArgs& A, const Smem& S, int tid, int warp, uint64_t first,
                                           uint64_t end, uint64_t stride, Body&& body) {
     return tile_pipeline<kSlice, kProbeWarps>(
         A, S.bars, S.stages, tid, warp, first, end, stride,
-        [&](unsigned char* stage, uint64_t* bar, uint64_t tile) { issue_tile(A, stage, bar, tile); }, body);
+        [&](unsigned char* stage, uint64_t* bar, uint64_t tile) { issue_tile(A, stage, bar, tile); }, body,
+        HASH && A.skip_tiles != 0, [&](uint64_t tile) { return probe_tile_live(A, tile); });
 }
 
 // HASH: some row set is a hashed sample (else the only device set is "all rows",
@@ -68,7 +88,7 @@ __device__ __forceinline__ bool narrow_run(const ProbeArgs& A, const Smem& S, in
     const uint32_t pb = has_pred ? S.poff[lane] : 0, pe = has_pred ? S.poff[lane + 1] : 0;
     const uint32_t nsets = HASH ? A.nsets : 1;
 
-    const bool ok = run_tiles<kSlice>(A, S, tid, warp, first, end, stride,
+    const bool ok = run_tiles<kSlice, HASH>(A, S, tid, warp, first, end, stride,
                                       [&](bool staged, const unsigned char* sbuf, uint32_t j, uint64_t slice0,
                                           bool tile_full) {
         uint4 vm[NQ];
@@ -249,7 +269,7 @@ __device__ __forceinline__ bool single_run(const ProbeArgs& A, const Smem& S, in
     uint32_t cnt = 0, nsr = 0, tc = 0;
     const bool marg = A.want_marg != 0;
 
-    const bool ok_run = run_tiles<kSlice>(A, S, tid, warp, first, end, stride,
+    const bool ok_run = run_tiles<kSlice, HASH>(A, S, tid, warp, first, end, stride,
                                           [&](bool staged, const unsigned char* sbuf, uint32_t j, uint64_t slice0,
                                               bool tile_full) {
         // bit i: row slice0 + 128 (i / 4) + 4 lane + i % 4 is in the row set

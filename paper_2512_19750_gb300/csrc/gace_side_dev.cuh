@@ -422,7 +422,8 @@ __device__ __forceinline__ bool side_tiles(const SideArgs& A, uint64_t* bars, un
                     }
                 }
             }
-        });
+        },
+        false, AllTiles());
     if (MODE == 1)
 #pragma unroll
         for (int i = 0; i < R; ++i) acc += wp[i];

@@ -66,35 +66,54 @@ __device__ __forceinline__ void load_vals_global(const void* ptr, uint32_t width
 // nstaged, tile_rows, stage_bytes, nstages, timeout_ns, status); `bars` holds
 // nstages mbarriers and `stages` nstages buffers of stage_bytes.  The CTA takes
 // tiles first, first + stride, ... below end (a whole grid striding over the
-// table, or one CTA over the tiles of a work item); thread 0 issues a tile's
-// copies with issue(stage buffer, mbarrier, tile), and each of the kWarps
-// warps runs body(staged, stage buffer, j, slice0, tile_full) on slices j =
-// warp, warp + kWarps, ... of kSlice rows.  Tiles from nstaged on (the partial
-// last tile, and every tile of a scan that is not staged) are not copied: the
-// body reads them with plain loads.  Returns true with the mbarriers
-// invalidated (their shared memory free for reuse), or false when a wait gave
-// up: the status bit is set and the CTA's copies in flight have been waited for
-// (with the same limit).
-template <uint32_t kSlice, int kWarps, class Args, class Issue, class Body>
+// table, or one CTA over the tiles of a work item); when `skip` is set, only
+// the tiles for which live(tile) holds (a tile that is not live has no row the
+// scan counts: it is neither copied nor evaluated).  Warp 0 finds the tiles
+// to copy and its lane 0 issues them with issue(stage buffer, mbarrier, tile);
+// each of the kWarps warps runs body(staged, stage buffer, j, slice0,
+// tile_full) on slices j = warp, warp + kWarps, ... of kSlice rows.  Tiles
+// from nstaged on (the partial last tile, and every tile of a scan that is not
+// staged) are not copied: the body reads them with plain loads.  Returns true
+// with the mbarriers invalidated (their shared memory free for reuse), or false
+// when a wait gave up: the status bit is set and the CTA's copies in flight
+// have been waited for (with the same limit).
+template <uint32_t kSlice, int kWarps, class Args, class Issue, class Body, class Live>
 __device__ __forceinline__ bool tile_pipeline(const Args& A, uint64_t* bars, unsigned char* stages, int tid,
                                               int warp, uint64_t first, uint64_t end, uint64_t stride,
-                                              Issue&& issue, Body&& body) {
+                                              Issue&& issue, Body&& body, bool skip, Live&& live) {
+    const int lane = tid & 31;
     const uint64_t staged_end = end < A.nstaged ? end : A.nstaged;
+    // The first tile at or after t on the CTA's progression that is live (end
+    // if none); with `skip`, a warp-collective search 32 candidates at a time.
+    auto next = [&](uint64_t t) -> uint64_t {
+        if (!skip) return t;
+        for (; t < end; t += 32 * stride) {
+            const uint64_t c = t + static_cast<uint64_t>(lane) * stride;
+            const unsigned m = __ballot_sync(kFullMask, c < end && live(c));
+            if (m) return t + static_cast<uint64_t>(__ffs(m) - 1) * stride;
+        }
+        return end;
+    };
     if (tid == 0) {
         for (uint32_t s = 0; s < A.nstages; ++s) mbar_init(smem_u32(&bars[s]), 1);
         fence_mbar_init();
     }
     __syncthreads();
-    if (tid == 0) {
+    // warp 0 copies the tile nstages tiles ahead of the one evaluated: without
+    // skipping, tile + nstages * stride; with it, the cursor ptile
+    uint64_t ptile = end;
+    if (warp == 0) {
+        ptile = next(first);
         for (uint32_t s = 0; s < A.nstages; ++s) {
-            const uint64_t tile = first + s * stride;
-            if (tile < staged_end) issue(stages + s * A.stage_bytes, &bars[s], tile);
+            const uint64_t pt = skip ? ptile : first + s * stride;
+            if (pt < staged_end && lane == 0) issue(stages + s * A.stage_bytes, &bars[s], pt);
+            if (skip && ptile < end) ptile = next(ptile + stride);
         }
     }
     const uint32_t nslices = A.tile_rows / kSlice;
+    uint64_t tile = next(first);
     uint64_t it = 0;
     for (;; ++it) {
-        const uint64_t tile = first + it * stride;
         if (tile >= end) {
             if (tid == 0)
                 for (uint32_t s = 0; s < A.nstages; ++s) mbar_inval(smem_u32(&bars[s]));
@@ -117,24 +136,33 @@ __device__ __forceinline__ bool tile_pipeline(const Args& A, uint64_t* bars, uns
             }
         }
         if (__syncthreads_or(fail)) break;
-        if (tid == 0) {
-            const uint64_t next = tile + A.nstages * stride;
-            if (next < staged_end) issue(stages + stage * A.stage_bytes, &bars[stage], next);
+        if (warp == 0) {
+            const uint64_t pt = skip ? ptile : tile + A.nstages * stride;
+            if (pt < staged_end && lane == 0) issue(stages + stage * A.stage_bytes, &bars[stage], pt);
+            if (skip && ptile < end) ptile = next(ptile + stride);
         }
+        tile = next(tile + stride);
     }
-    if (tid == 0) {
-        atomicOr(A.status, kStatusTimeout);
-        // let this CTA's copies in flight land before its shared memory is left
+    if (warp == 0) {
+        if (lane == 0) atomicOr(A.status, kStatusTimeout);
+        // let this CTA's copies in flight (the tiles from the failed one on)
+        // land before its shared memory is left
+        uint64_t t2 = tile;
         for (uint32_t k = 0; k < A.nstages; ++k) {
             const uint64_t it2 = it + k;
-            const uint64_t tile2 = first + it2 * stride;
-            if (tile2 < staged_end)
+            if (t2 < staged_end && lane == 0)
                 mbar_wait_bounded(smem_u32(&bars[it2 % A.nstages]), static_cast<uint32_t>((it2 / A.nstages) & 1),
                                   A.timeout_ns);
+            if (t2 < end) t2 = next(t2 + stride);
         }
     }
     return false;
 }
+
+// Every tile live: the pipeline without tile skipping.
+struct AllTiles {
+    __device__ __forceinline__ bool operator()(uint64_t) const { return true; }
+};
 
 }  // namespace dev
 }  // namespace gace

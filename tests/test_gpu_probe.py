@@ -331,3 +331,29 @@ def test_wide_pass_range_trees(g, gctx, orc, cuda):
                     [Sample(FULL), Sample(ROWS, 0.3, 11), Sample(BLOCKS, 0.5, 2, 1000)])
     finally:
         g.gace_unload(gctx, tid)
+
+
+@pytest.mark.parametrize("samples", [
+    [Sample(BLOCKS, 0.01, 42, 4096)],
+    [Sample(BLOCKS, 0.05, 7, 3000)],
+    [Sample(BLOCKS, 0.02, 1, 65536), Sample(BLOCKS, 0.3, 9, 8192)],
+    [Sample(BLOCKS, 0.01, 5, 1000)],
+    [Sample(BLOCKS, 0.001, 3, 2048), Sample(BLOCKS, 0.0, 3, 2048)],
+])
+@pytest.mark.parametrize("npreds", [1, 3])
+def test_block_samples_skip_tiles(g, gctx, orc, cuda, samples, npreds):
+    """Probes whose row sets are all block samples read only the tiles that
+    hold a sampled block: counts, sample sizes and marginals still equal the
+    oracle's over int32 and int64 columns, several thousand tiles and a ragged
+    tail (block sizes that are and are not powers of two, several sets, a
+    block size too small for skipping, an empty sample)."""
+    t = make_skew_corr(n=3_000_777, seed=77, device=cuda)
+    for cols in ([0, 2], [4, 5]):
+        sub = Table(t.name, [t.columns[c] for c in cols], [t.dtypes[c] for c in cols], [t.domains[c] for c in cols])
+        preds = make_predicates(sub, npreds, 1, 2, seed=npreds)
+        preds = [[Term(cols[x.col], x.op, x.a, x.b, x.values) for x in p] for p in preds]
+        tid = g.gace_load_columns(gctx, t.columns, borrow=True)
+        try:
+            check_probe(g, orc, gctx, tid, host_columns(t), t.dtypes, preds, samples)
+        finally:
+            g.gace_unload(gctx, tid)
