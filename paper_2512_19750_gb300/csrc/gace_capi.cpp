@@ -845,6 +845,7 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
         Pass cur;
         std::map<uint32_t, bool> in_cur;
         uint32_t pool_words = 0;
+        uint64_t pred_terms = 0;               // predicate-term entries of the pass
         std::map<uint32_t, ColPool> cols_cur;  // the pass's columns and their tables
         auto flush = [&]() {
             if (!cur.preds.empty() || !cur.uterms.empty()) passes.push_back(cur);
@@ -852,6 +853,21 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
             in_cur.clear();
             cols_cur.clear();
             pool_words = 0;
+            pred_terms = 0;
+        };
+        // shared memory of a wide pass of nt terms, np predicates, npt
+        // predicate-term entries and `pool` pool words (the layout of
+        // probe_layout), against what keeps kWideCtas CTAs per SM (1 KB of
+        // each CTA's share is reserved by the hardware)
+        const uint64_t nsets_dev = sets.size();
+        const uint64_t smem_budget = static_cast<uint64_t>(ctx->smem_per_sm) / kWideCtas - 1024;
+        auto wide_smem = [&](uint64_t nt, uint64_t np, uint64_t npt, uint64_t pool) {
+            uint64_t off = 128 + nt * 16;
+            off = round_up(off + pool * 4, 16) + (np + 1) * 4;
+            off = round_up(off + npt * 4, 16);
+            off += static_cast<uint64_t>(kProbeWarps) * (nt + nsets_dev) * 16 + nsets_dev * np * 4;
+            off += plan.want_marg ? nsets_dev * nt * 4 : 0;
+            return round_up(off + nsets_dev * 4, 16);
         };
         // the pass's columns and pool words with the terms `add` added
         auto with_terms = [&](const std::vector<uint32_t>& add, std::map<uint32_t, ColPool>& touched) {
@@ -902,7 +918,9 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
                                  });
             if (!cur.preds.empty() &&
                 (cur.uterms.size() + add.size() > kPassTerms || cur.preds.size() + 1 > kPassPreds ||
-                 total > kPassPool || ncols > static_cast<size_t>(kMaxSlots))) {
+                 total > kPassPool || ncols > static_cast<size_t>(kMaxSlots) ||
+                 wide_smem(cur.uterms.size() + add.size(), cur.preds.size() + 1, pred_terms + pu.size(), total) >
+                     smem_budget)) {
                 flush();
                 add.assign(pu.begin(), pu.end());
                 touched.clear();
@@ -910,6 +928,7 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
             }
             commit(add, touched, total);
             cur.preds.push_back(p);
+            pred_terms += pu.size();
         }
         // terms whose marginals are wanted but that no device predicate placed
         if (plan.want_marg) {
@@ -921,7 +940,8 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
                 const size_t ncols = cols_cur.size() + (cols_cur.count(uterms[u].col) ? 0 : 1);
                 if (!cur.uterms.empty() &&
                     (cur.uterms.size() + 1 > kPassTerms || total > kPassPool ||
-                     ncols > static_cast<size_t>(kMaxSlots))) {
+                     ncols > static_cast<size_t>(kMaxSlots) ||
+                     wide_smem(cur.uterms.size() + 1, cur.preds.size(), pred_terms, total) > smem_budget)) {
                     flush();
                     touched.clear();
                     total = with_terms(add, touched);
@@ -1085,6 +1105,9 @@ gace_status gace_create(gace_ctx** out, const gace_config* cfg) {
     if ((e = cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c.device)) !=
         cudaSuccess)
         return bail(cuda_fail(e, "cudaDeviceGetAttribute(smem opt-in)"));
+    if ((e = cudaDeviceGetAttribute(&ctx->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c.device)) !=
+        cudaSuccess)
+        return bail(cuda_fail(e, "cudaDeviceGetAttribute(smem per SM)"));
     if (c.stream) {
         ctx->stream = static_cast<cudaStream_t>(c.stream);
     } else {

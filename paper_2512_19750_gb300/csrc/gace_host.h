@@ -85,6 +85,7 @@ struct gace_ctx {
     bool own_stream = false;
     int sms = 0;
     int smem_optin = 0;
+    int smem_per_sm = 0;     // shared memory of one SM (bytes)
     uint64_t budget = 0;       // 0 = unlimited
     uint64_t used = 0;         // owned tables + workspace + pinned
     uint64_t timeout_ns = 2000ull * 1000000ull;
@@ -237,7 +238,7 @@ bool is_in_kind(uint32_t k);
 uint32_t in_count(const NTerm& t);
 
 #ifndef GACE_TREE_MIN
-#define GACE_TREE_MIN 32
+#define GACE_TREE_MIN 24
 #endif
 // A column's range terms beyond its full groups of 32 use an interval tree only
 // when at least this many (a tree costs about as much as this many compares).
@@ -265,14 +266,22 @@ gace_status make_set(const gace_sample& s, SetDesc& d);
 
 // ---------------------------------------------------------------- probe plan
 
+// A pass holds at most kPassTerms terms and kPassPreds predicates, and no
+// more than keeps kWideCtas CTAs of the wide kernel resident per SM (its
+// register budget allows three): the larger the pass, the fewer full scans of
+// the referenced columns, until the pass's shared memory costs a CTA.
 #ifndef GACE_PASS_TERMS
-#define GACE_PASS_TERMS 256
+#define GACE_PASS_TERMS 512
 #endif
 #ifndef GACE_PASS_PREDS
-#define GACE_PASS_PREDS 256
+#define GACE_PASS_PREDS 512
+#endif
+#ifndef GACE_WIDE_CTAS
+#define GACE_WIDE_CTAS 3
 #endif
 constexpr uint32_t kPassTerms = GACE_PASS_TERMS;
 constexpr uint32_t kPassPreds = GACE_PASS_PREDS;
+constexpr int kWideCtas = GACE_WIDE_CTAS;
 constexpr uint32_t kPassPool = 16384;  // pool words: IN lists (narrow) or EQ/IN tables (wide)
 
 struct Pass {
