@@ -193,11 +193,20 @@ __device__ __forceinline__ bool side_item_staged(const SideArgs& A, const BatchJ
     if (end > A.ntiles) end = A.ntiles;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
     unsigned char* stages = smem + kSideStageOff;
+    // gathers take 16 rows per lane when a tile holds such a step for every warp
+    constexpr int NQ = side_nq<MODE>();
+    if (NQ > 2 && A.tile_rows % (128u * NQ * kSideWarps) != 0) {
+        if (A.slot_dtype[A.key_slot] == 1)
+            return side_tiles<MODE, AGG, true, 2>(A, bars, stages, tid, lane, warp, first, end, 1, J.hist, J.strict,
+                                                  J.weight, J.fk2_slot, J.domain2, J.w64, npass, acc);
+        return side_tiles<MODE, AGG, false, 2>(A, bars, stages, tid, lane, warp, first, end, 1, J.hist, J.strict,
+                                               J.weight, J.fk2_slot, J.domain2, J.w64, npass, acc);
+    }
     if (A.slot_dtype[A.key_slot] == 1)
-        return side_tiles<MODE, AGG, true>(A, bars, stages, tid, lane, warp, first, end, 1, J.hist, J.strict,
-                                           J.weight, J.fk2_slot, J.domain2, J.w64, npass, acc);
-    return side_tiles<MODE, AGG, false>(A, bars, stages, tid, lane, warp, first, end, 1, J.hist, J.strict, J.weight,
-                                        J.fk2_slot, J.domain2, J.w64, npass, acc);
+        return side_tiles<MODE, AGG, true, NQ>(A, bars, stages, tid, lane, warp, first, end, 1, J.hist, J.strict,
+                                               J.weight, J.fk2_slot, J.domain2, J.w64, npass, acc);
+    return side_tiles<MODE, AGG, false, NQ>(A, bars, stages, tid, lane, warp, first, end, 1, J.hist, J.strict,
+                                            J.weight, J.fk2_slot, J.domain2, J.w64, npass, acc);
 }
 
 #ifndef GACE_BATCH_SIDE_CTAS

@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kJoinThreads, (MODE == 1 || MODE == 2) ? GACE_
 // The side modes over tiles staged in shared memory by the bulk-copy pipeline
 // (tables whose referenced columns are 16-byte aligned and narrow enough for
 // two stages); three CTAs per SM.
-template <int MODE, bool AGG, bool KEY64>
+template <int MODE, bool AGG, bool KEY64, int NQ>
 __global__ void __launch_bounds__(kJoinThreads, 3)
     k_side_staged(const __grid_constant__ SideArgs A, uint32_t* hist, int strict, const void* weight,
                   unsigned long long* out_sum, uint32_t fk2_slot, uint64_t domain2, unsigned long long* w64) {
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kJoinThreads, 3)
     __shared__ unsigned long long scratch[kJoinThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     unsigned long long npass = 0, acc = 0;
-    if (!side_tiles<MODE, AGG, KEY64>(A, reinterpret_cast<uint64_t*>(smem), smem + kSideStageOff, tid, lane, warp,
+    if (!side_tiles<MODE, AGG, KEY64, NQ>(A, reinterpret_cast<uint64_t*>(smem), smem + kSideStageOff, tid, lane, warp,
                                blockIdx.x, A.ntiles, gridDim.x, hist, strict, weight, fk2_slot, domain2, w64, npass,
                                acc))
         return;  // a pipeline wait gave up: the status says so
@@ -177,20 +177,20 @@ cudaError_t hll_launch(const HllArgs& a, int sms, cudaStream_t s) {
 }
 
 // A staged side launch: grid = min(tiles, SMs x resident CTAs).
-template <int MODE, bool AGG, bool KEY64>
+template <int MODE, bool AGG, bool KEY64, int NQ>
 static cudaError_t staged_launch_t(const SideArgs& a, int sms, cudaStream_t s, uint32_t* hist, int strict,
                                  const void* weight, unsigned long long* out_sum, uint32_t fk2_slot, uint64_t domain2,
                                  unsigned long long* w64) {
-    cudaError_t e = cudaFuncSetAttribute(k_side_staged<MODE, AGG, KEY64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_side_staged<MODE, AGG, KEY64, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(a.smem_bytes));
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_side_staged<MODE, AGG, KEY64>, kJoinThreads, a.smem_bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_side_staged<MODE, AGG, KEY64, NQ>, kJoinThreads, a.smem_bytes);
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
     const uint64_t cap = static_cast<uint64_t>(sms) * occ;
     const int grid = static_cast<int>(a.ntiles < cap ? (a.ntiles ? a.ntiles : 1) : cap);
-    k_side_staged<MODE, AGG, KEY64><<<grid, kJoinThreads, a.smem_bytes, s>>>(a, hist, strict, weight, out_sum, fk2_slot,
+    k_side_staged<MODE, AGG, KEY64, NQ><<<grid, kJoinThreads, a.smem_bytes, s>>>(a, hist, strict, weight, out_sum, fk2_slot,
                                                                        domain2, w64);
     return cudaGetLastError();
 }
@@ -199,9 +199,16 @@ template <int MODE, bool AGG>
 static cudaError_t staged_launch(const SideArgs& a, int sms, cudaStream_t s, uint32_t* hist, int strict,
                                  const void* weight, unsigned long long* out_sum, uint32_t fk2_slot, uint64_t domain2,
                                  unsigned long long* w64) {
+    // gathers take 16 rows per lane when a tile holds such a step for every warp
+    constexpr int NQ = side_nq<MODE>();
+    if (NQ > 2 && a.tile_rows % (128u * NQ * kSideWarps) != 0) {
+        if (a.slot_dtype[a.key_slot] == 1)
+            return staged_launch_t<MODE, AGG, true, 2>(a, sms, s, hist, strict, weight, out_sum, fk2_slot, domain2, w64);
+        return staged_launch_t<MODE, AGG, false, 2>(a, sms, s, hist, strict, weight, out_sum, fk2_slot, domain2, w64);
+    }
     if (a.slot_dtype[a.key_slot] == 1)
-        return staged_launch_t<MODE, AGG, true>(a, sms, s, hist, strict, weight, out_sum, fk2_slot, domain2, w64);
-    return staged_launch_t<MODE, AGG, false>(a, sms, s, hist, strict, weight, out_sum, fk2_slot, domain2, w64);
+        return staged_launch_t<MODE, AGG, true, NQ>(a, sms, s, hist, strict, weight, out_sum, fk2_slot, domain2, w64);
+    return staged_launch_t<MODE, AGG, false, NQ>(a, sms, s, hist, strict, weight, out_sum, fk2_slot, domain2, w64);
 }
 
 cudaError_t hist_launch(const SideArgs& a, uint32_t* hist, int strict, int aggregate, int sms,

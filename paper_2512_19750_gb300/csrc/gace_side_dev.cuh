@@ -313,15 +313,16 @@ __host__ __device__ constexpr int side_nq() { return (MODE == 1 || MODE == 2) ? 
 
 // One side mode over tiles [first, end) of the staged scan (stride: the grid's
 // CTAs); npass and acc are per thread.  MODE as in side_rows; KEY64: the key
-// column is int64 (else int32).  False when a pipeline wait gave up
-// (kStatusTimeout set).
-template <int MODE, bool AGG, bool KEY64>
+// column is int64 (else int32); NQ quads of rows per lane and step, WARPS warps
+// per CTA (a tile holds a multiple of 128 NQ WARPS rows).  False when a
+// pipeline wait gave up (kStatusTimeout set).
+template <int MODE, bool AGG, bool KEY64, int NQ = side_nq<MODE>(), int WARPS = kSideWarps>
 __device__ __forceinline__ bool side_tiles(const SideArgs& A, uint64_t* bars, unsigned char* stages, int tid,
                                            int lane, int warp, uint64_t first, uint64_t end, uint64_t stride,
                                            uint32_t* hist, int strict, const void* weight, uint32_t fk2_slot,
                                            uint64_t domain2, unsigned long long* w64, unsigned long long& npass,
                                            unsigned long long& acc) {
-    constexpr int NQ = side_nq<MODE>(), R = 4 * NQ;
+    constexpr int R = 4 * NQ;
     constexpr uint32_t kSlice = 128u * NQ;
     constexpr uint32_t kAll = R == 32 ? 0xFFFFFFFFu : (1u << R) - 1u;
     bool bad_key = false;
@@ -333,7 +334,7 @@ __device__ __forceinline__ bool side_tiles(const SideArgs& A, uint64_t* bars, un
 #pragma unroll
     for (int i = 0; i < R; ++i) wp[i] = 0;
     const uint32_t fk2_dt = MODE == 3 ? A.slot_dtype[fk2_slot] : 0u;
-    const bool ok = tile_pipeline<kSlice, kSideWarps>(
+    const bool ok = tile_pipeline<kSlice, WARPS>(
         A, bars, stages, tid, warp, first, end, stride,
         [&](unsigned char* stage, uint64_t* bar, uint64_t tile) {
             const uint32_t b = smem_u32(bar);

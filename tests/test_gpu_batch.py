@@ -86,11 +86,16 @@ def test_graph_replay_with_new_contents(g, gctx, batched):
         _check_against_sync(g, gctx, tids, tables, batch, breqs)
 
 
-def test_joins_every_method_and_chain(g, gctx, orc, cuda):
+@pytest.mark.parametrize("fact_filters", [1, 2])
+def test_joins_every_method_and_chain(g, gctx, orc, cuda, fact_filters):
+    """Every join method and the chain in one batch, equal to the synchronous
+    calls and the oracle; with two fact filters the fact side reads three
+    columns (12-byte rows: half-size tiles in the staged side kernel)."""
     f, d, d2 = make_join(n_fact=700_001, n_dim=50_000, n_dim2=5000, seed=5, device=cuda)
     fid, did, d2id = (g.gace_load_columns(gctx, t.columns) for t in (f, d, d2))
     try:
-        ft, dt, d2t = [Term(1, RANGE, 0, 300)], [Term(2, RANGE, 100, 900)], [Term(1, RANGE, 0, 500)]
+        ft = [Term(1, RANGE, 0, 300)] + ([Term(2, RANGE, 50, 950)] if fact_filters == 2 else [])
+        dt, d2t = [Term(2, RANGE, 100, 900)], [Term(1, RANGE, 0, 500)]
         F = g.JoinSideSpec(fid, 0, ft, f.dtypes)
         D = g.JoinSideSpec(did, 0, dt, d.dtypes)
         D2 = g.JoinSideSpec(d2id, 0, d2t, d2.dtypes)
