@@ -188,7 +188,7 @@ uint32_t in_count(const NTerm& t) {
 // Pool words of one column's tables in a wide pass (an upper bound for a
 // narrow pass, whose pool holds only the IN values): one hash table per group
 // of 32 EQ/IN terms in order, all of one capacity (the next power of two >=
-// twice the largest group's entries, at least 64), one interval tree per full
+// kVsSlotsPerEntry times the largest group's entries, at least 64), one interval tree per full
 // group of 32 range terms (or last group of at least kTreeMin), and one word
 // of alignment.
 uint32_t ColPool::words() const {
@@ -202,7 +202,7 @@ uint32_t ColPool::words() const {
             most = std::max(most, n);
         }
         uint32_t tlog = 6;
-        while ((1ull << tlog) < 2 * most) ++tlog;
+        while ((1ull << tlog) < kVsSlotsPerEntry * most) ++tlog;
         w += static_cast<uint64_t>((vs.size() + 31) / 32) * (1ull << tlog) * (is64 ? 4u : 2u);
     }
     w += static_cast<uint64_t>(trees) * (is64 ? kTreeWords64 : kTreeWords32);
@@ -452,7 +452,7 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
                 most = std::max(most, n);
             }
             uint32_t tlog = 6;
-            while ((1ull << tlog) < 2 * most) ++tlog;
+            while ((1ull << tlog) < kVsSlotsPerEntry * most) ++tlog;
             sd.tlog = tlog;
             const uint32_t cap = 1u << tlog;
             sd.toff = static_cast<uint32_t>(ps.pool.size());

@@ -237,6 +237,13 @@ gace_status normalize_term(const gace_term& t, int dtype, const gace_scalar* in_
 bool is_in_kind(uint32_t k);
 uint32_t in_count(const NTerm& t);
 
+// Slots per entry of a wide pass's EQ/IN hash tables (the inverse of their
+// load factor): linear probing, so a miss walks to the next empty slot.
+#ifndef GACE_VS_SLOTS
+#define GACE_VS_SLOTS 2
+#endif
+constexpr uint64_t kVsSlotsPerEntry = GACE_VS_SLOTS;
+
 #ifndef GACE_TREE_MIN
 #define GACE_TREE_MIN 24
 #endif
