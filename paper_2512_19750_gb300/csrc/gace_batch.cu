@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(kHistThreads, 1) k_batch_hist(const BatchItem*
         for (uint32_t i = tid; i < K; i += kHistThreads) shist[i] = 0;
         __syncthreads();  // also: every thread has read s_item
         unsigned long long npass = 0, acc = 0;
-        side_groups<0, true>(SA, shist, J.strict, nullptr, 0, 0, nullptr, it.begin / 4 + (tid - lane),
+        side_groups<0, kSmemHistAgg>(SA, shist, J.strict, nullptr, 0, 0, nullptr, it.begin / 4 + (tid - lane),
                              (it.end + 3) / 4, kHistThreads, npass, acc);
         __syncthreads();
         hist_merge(shist, J.hist, K, tid, kHistThreads);

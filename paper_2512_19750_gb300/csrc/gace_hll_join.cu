@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kHistThreads, 1)
     for (uint32_t i = threadIdx.x; i < K; i += kHistThreads) shist[i] = 0;
     __syncthreads();
     unsigned long long npass = 0, acc = 0;
-    side_groups<0, true>(A, shist, strict, nullptr, 0, 0, nullptr,
+    side_groups<0, kSmemHistAgg>(A, shist, strict, nullptr, 0, 0, nullptr,
                          static_cast<uint64_t>(blockIdx.x) * kHistThreads + (threadIdx.x - lane), (A.nrows + 3) / 4,
                          static_cast<uint64_t>(gridDim.x) * kHistThreads, npass, acc);
     __syncthreads();

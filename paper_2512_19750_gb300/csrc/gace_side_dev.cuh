@@ -29,13 +29,17 @@ __device__ __forceinline__ uint64_t canonical_key(uint32_t dtype, uint32_t lo, u
     return lo;
 }
 
+// Register index j = the top p bits of the hash (p <= 18: within its high
+// word) and rho = the leading zeros of the remaining 64 - p bits, + 1.  With
+// r = those bits, 2 r + 1 has 63 - (64 - p) + (leading zeros of r) + 1
+// leading zeros, and 1 (63) when r = 0, which gives rho = 65 - p there: no
+// variable-width 64-bit shift per row (the mask is loop-invariant).
 __device__ __forceinline__ void hll_rank(uint64_t key, uint64_t seedhash, uint32_t p,
                                          uint32_t& j, uint32_t& rho) {
     const uint64_t h = splitmix64(key ^ seedhash);
-    j = static_cast<uint32_t>(h >> (64 - p));
-    // rho = leading zeros of the 64 - p bits after the index, + 1; a sentinel
-    // one at bit p - 1 (below them) makes an all-zero remainder give 65 - p
-    rho = static_cast<uint32_t>(__clzll(static_cast<long long>((h << p) | (1ull << (p - 1))))) + 1u;
+    j = static_cast<uint32_t>(h >> 32) >> (32 - p);
+    const uint64_t r = h & ((1ull << (64 - p)) - 1);
+    rho = static_cast<uint32_t>(__clzll(static_cast<long long>(2 * r + 1))) + 2u - p;
 }
 
 // byte-wise max in shared memory via CAS on the containing word (bounded)
@@ -431,6 +435,15 @@ __device__ __forceinline__ bool side_tiles(const SideArgs& A, uint64_t* bars, un
     if (bad_key && strict) atomicOr(A.status, kStatusKeyDomain);
     return ok;
 }
+
+// Shared-memory histograms add each row with its own atomic: combining a
+// warp's equal keys first (__match_any_sync, which global histograms need)
+// costs more there than the same-address conflicts it saves, even on
+// Zipf-hot keys.
+#ifndef GACE_SMEM_HIST_AGG
+#define GACE_SMEM_HIST_AGG 0
+#endif
+constexpr bool kSmemHistAgg = GACE_SMEM_HIST_AGG != 0;
 
 // A CTA's shared-memory histogram of K bins into the global one (nonzero bins).
 __device__ __forceinline__ void hist_merge(const uint32_t* shist, uint32_t* ghist, uint32_t K, uint32_t tid,
