@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define GACE_ABI_VERSION 1
+#define GACE_ABI_VERSION 2
 
 typedef enum {
     GACE_OK = 0,
@@ -418,6 +418,106 @@ gace_status gace_poll(gace_ctx* ctx, uint64_t ticket, uint64_t timeout_us);
  */
 gace_status gace_serve_replay(gace_ctx* ctx, const gace_request* reqs, uint32_t n, const uint64_t* arrival_ns,
                               uint32_t mode, uint64_t* done_ns, gace_status* statuses);
+
+/* ------------------------------------------------------------ Risky Gate */
+/*
+ * The trust metrics that decide whether a query goes to the GPU path
+ * (Section III-A, III-C), evaluated on host doubles; no GPU is used.
+ *
+ *   drift D = |NDV_hist - NDV_est| / NDV_hist                 (Eq. 1), flagged
+ *             when D >= drift_min (0.25 in the paper);
+ *   selectivity error |S_est - S_probe|                       (Eq. 2), flagged
+ *             when > sel_err_max (0.01);
+ *   PCS = P(A,B) / (P(A) P(B))                                (Eq. 3), flagged
+ *             when > pcs_high (1.6) or < pcs_low (0.7).
+ *
+ * A zero field of the config takes the paper's value; a NULL config takes all
+ * four.  An input that is NaN leaves its signal out (its flag clear, its
+ * output NaN); so does ndv_hist <= 0 or infinite (D is undefined), and a NaN
+ * PCS (a zero marginal, gace_pred_result.pcs).  Errors: GACE_EINVAL for NULL
+ * in/out with n > 0, or a threshold that is negative, NaN or infinite, or
+ * pcs_low > pcs_high; outputs are then untouched.
+ */
+typedef struct {
+    double drift_min;    /* 0 -> 0.25 */
+    double sel_err_max;  /* 0 -> 0.01 */
+    double pcs_high;     /* 0 -> 1.6 */
+    double pcs_low;      /* 0 -> 0.7 */
+} gace_gate_config;
+
+typedef struct {
+    double ndv_hist;   /* the optimizer's histogram NDV (NaN: no drift signal) */
+    double ndv_est;    /* the measured NDV, e.g. gace_ndv's estimate */
+    double sel_est;    /* the optimizer's selectivity (NaN: no selectivity signal) */
+    double sel_probe;  /* the measured selectivity, gace_pred_result.sel */
+    double pcs;        /* gace_pred_result.pcs of a 2-term predicate (NaN: none) */
+} gace_gate_input;
+
+#define GACE_RISK_DRIFT 1u
+#define GACE_RISK_SELECTIVITY 2u
+#define GACE_RISK_CORRELATION 4u
+
+typedef struct {
+    uint32_t flags;    /* OR of GACE_RISK_* */
+    uint32_t reserved;
+    double drift;      /* D, NaN when the signal is left out */
+    double sel_err;    /* |S_est - S_probe|, NaN when left out */
+} gace_gate_result;
+
+gace_status gace_gate_eval(const gace_gate_config* cfg, const gace_gate_input* in, uint32_t n,
+                           gace_gate_result* out);
+
+/*
+ * Break-even logic (Section V, item 2; Eq. 4 models the measurement cost as
+ * the kernel time): predicted cost of one synchronous probe of npreds
+ * predicates (K) on nsets row sets (M) over nrows rows (N), and whether it
+ * beats the caller's alternative (alt_ms, e.g. the CPU's dynamic sampling).
+ *
+ *   batches of at most 32 predicates and 32 terms (narrow):
+ *     kernel_ms = N * row_bytes / hbm_rate + N * hashed_sets * hash_ns
+ *   larger batches (wide passes, ALU-bound):
+ *     kernel_ms = N * ops_per_row / ops_rate
+ *   transfer_ms = resident ? 0 : N * row_bytes / h2d_rate   (key-only copy)
+ *   total_ms = call_ms + kernel_ms + transfer_ms;  offload = total_ms < alt_ms
+ *
+ * ops_per_row is the batch's compare operations per row (1 per equality, 2
+ * per range, k per IN list of k values); 0 takes 2 per term.  The rates are
+ * the context's own measurements: every probe launch timed while
+ * gace_stats_reset(ctx, 1) is in effect adds to a cost table that
+ * gace_stats_reset does not clear (narrow launches give hbm_rate, wide ones
+ * ops_rate); a rate without measurements takes its GB300 default (hbm 5e12 B/s,
+ * ops 1.3e13 /s, h2d 8e10 B/s, hash 1.5e-3 ns per row and set, call 0.03 ms).
+ * The answer reports the rates it used.  Errors: GACE_EINVAL for NULL
+ * arguments, nsets = 0, hashed_sets > nsets, or a NaN / negative alt_ms.
+ */
+typedef struct {
+    uint64_t nrows;        /* N */
+    uint32_t npreds;       /* K */
+    uint32_t nsets;        /* M: row sets (full scan and samples) */
+    uint32_t hashed_sets;  /* of which row or block samples (hashed per row) */
+    uint32_t nterms;       /* distinct terms of the batch */
+    uint32_t row_bytes;    /* bytes per row of the referenced columns */
+    uint32_t resident;     /* 1: columns in HBM; 0: copied from host per probe */
+    double ops_per_row;    /* 0: 2 * nterms */
+    double alt_ms;         /* the alternative's cost */
+} gace_cost_query;
+
+typedef struct {
+    double total_ms;
+    double kernel_ms;
+    double transfer_ms;
+    double call_ms;
+    double hbm_rate;       /* bytes/s */
+    double ops_rate;       /* compare ops/s */
+    double h2d_rate;       /* bytes/s */
+    double hash_ns;        /* per row and hashed set */
+    uint32_t narrow;       /* 1: the narrow kernels' model was used */
+    uint32_t offload;      /* 1: total_ms < alt_ms */
+    uint32_t measured;     /* bit 0: hbm_rate measured, bit 1: ops_rate measured */
+    uint32_t reserved;
+} gace_cost_answer;
+
+gace_status gace_break_even(gace_ctx* ctx, const gace_cost_query* q, gace_cost_answer* out);
 
 /*
  * Kernel statistics of a context (tracing; the paper decomposes probe time

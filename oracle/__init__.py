@@ -8,6 +8,7 @@ module compiles it with gcc and marshals workload descriptions into it.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 
@@ -273,3 +274,50 @@ def chain_card(fact, dim1, dim1_fk2_col: int, dim2, key_domain1: int, key_domain
                               int(key_domain1), int(key_domain2), C.byref(card), C.byref(fp),
                               C.byref(p1), C.byref(p2))
     return rc, int(card.value), int(fp.value), int(p1.value), int(p2.value)
+
+
+# ---------------------------------------------------------------- Risky Gate
+# Section III-C: the three trust metrics and the paper's thresholds.
+GATE_DRIFT_MIN = 0.25   # Eq. 1: D >= 0.25 triggers
+GATE_SEL_ERR_MAX = 0.01  # Eq. 2: |S_est - S_probe| > 0.01 triggers
+GATE_PCS_HIGH = 1.6     # Eq. 3: PCS > 1.6 (underestimation risk)
+GATE_PCS_LOW = 0.7      # Eq. 3: PCS < 0.7 (overestimation risk)
+RISK_DRIFT, RISK_SELECTIVITY, RISK_CORRELATION = 1, 2, 4
+
+
+def gate(ndv_hist=math.nan, ndv_est=math.nan, sel_est=math.nan, sel_probe=math.nan, pcs=math.nan,
+         drift_min=GATE_DRIFT_MIN, sel_err_max=GATE_SEL_ERR_MAX, pcs_high=GATE_PCS_HIGH, pcs_low=GATE_PCS_LOW):
+    """(flags, D, |S_est - S_probe|) of one query's signals.  A NaN input
+    leaves its signal out; D is defined only for a positive, finite NDV_hist."""
+    flags, drift, sel_err = 0, math.nan, math.nan
+    # Eq. 1
+    if math.isfinite(ndv_hist) and ndv_hist > 0 and not math.isnan(ndv_est):
+        drift = abs(ndv_hist - ndv_est) / ndv_hist
+        if drift >= drift_min:
+            flags |= RISK_DRIFT
+    # Eq. 2
+    if not math.isnan(sel_est) and not math.isnan(sel_probe):
+        sel_err = abs(sel_est - sel_probe)
+        if sel_err > sel_err_max:
+            flags |= RISK_SELECTIVITY
+    # Eq. 3
+    if not math.isnan(pcs) and (pcs > pcs_high or pcs < pcs_low):
+        flags |= RISK_CORRELATION
+    return flags, drift, sel_err
+
+
+def probe_cost(nrows, npreds, nterms, row_bytes, hashed_sets, resident, ops_per_row, alt_ms, rates):
+    """Break-even model of Section V (item 2) with the measurement cost of
+    Eq. 4 as kernel time: rates = dict(hbm_rate, ops_rate, h2d_rate, hash_ns,
+    call_ms).  Batches of at most 32 predicates and 32 terms stream the
+    referenced columns (plus one hash per row and hashed set); larger ones
+    cost their compare operations.  Returns (total_ms, narrow, offload)."""
+    narrow = npreds <= 32 and nterms <= 32
+    if narrow:
+        kernel = nrows * row_bytes / rates["hbm_rate"] * 1e3 + nrows * hashed_sets * rates["hash_ns"] * 1e-6
+    else:
+        ops = ops_per_row if ops_per_row > 0 else 2.0 * nterms
+        kernel = nrows * ops / rates["ops_rate"] * 1e3
+    transfer = 0.0 if resident else nrows * row_bytes / rates["h2d_rate"] * 1e3
+    total = rates["call_ms"] + kernel + transfer
+    return total, narrow, total < alt_ms

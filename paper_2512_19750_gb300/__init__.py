@@ -17,7 +17,7 @@ from ._capi import (GACE_BLOCKS, GACE_BORROW, GACE_COPY, GACE_EBUSY, GACE_ECUDA,
                     GACE_F32, GACE_FULL, GACE_I32,
                     GACE_I64, GACE_IN, GACE_JOIN_AUTO, GACE_JOIN_GATHER, GACE_JOIN_HIST_DOT,
                     GACE_OK, GACE_RANGE, GACE_REQ_JOIN, GACE_REQ_NDV, GACE_REQ_PROBE, GACE_ROWS,
-                    GaceError, check, lib)
+                    GACE_RISK_CORRELATION, GACE_RISK_DRIFT, GACE_RISK_SELECTIVITY, GaceError, check, lib)
 
 RESULT_DTYPE = np.dtype([("match", "<u8"), ("sample_rows", "<u8"), ("sel", "<f8"), ("pcs", "<f8")])
 _NP_OF = {GACE_I32: np.int32, GACE_I64: np.int64, GACE_F32: np.float32}
@@ -408,6 +408,43 @@ def gace_serve_replay(ctx, requests, arrival_ns, mode: int = 0):
     lib().gace_serve_replay(ctx, arr, n, arrival.ctypes.data_as(C.POINTER(C.c_uint64)), mode,
                             done.ctypes.data_as(C.POINTER(C.c_uint64)), st.ctypes.data_as(C.POINTER(C.c_int)))
     return done[:n], st[:n]
+
+
+def gace_gate_eval(inputs, config=None):
+    """Risky Gate trust metrics (Eq. 1-3) of each input, a dict with keys
+    ndv_hist, ndv_est, sel_est, sel_probe, pcs (missing keys are NaN: that
+    signal is left out).  config: dict of drift_min, sel_err_max, pcs_high,
+    pcs_low (missing or 0 = the paper's thresholds).  Returns (flags, drift,
+    sel_err) numpy arrays."""
+    n = len(inputs)
+    arr = (_capi.gace_gate_input * max(1, n))()
+    nan = float("nan")
+    for i, x in enumerate(inputs):
+        arr[i] = _capi.gace_gate_input(*(float(x.get(k, nan)) for k in
+                                         ("ndv_hist", "ndv_est", "sel_est", "sel_probe", "pcs")))
+    out = (_capi.gace_gate_result * max(1, n))()
+    cfg = None
+    if config is not None:
+        cfg = C.byref(_capi.gace_gate_config(*(float(config.get(k, 0.0)) for k in
+                                               ("drift_min", "sel_err_max", "pcs_high", "pcs_low"))))
+    check(lib().gace_gate_eval(cfg, arr, n, out), "gace_gate_eval")
+    flags = np.array([out[i].flags for i in range(n)], dtype=np.uint32)
+    drift = np.array([out[i].drift for i in range(n)], dtype=np.float64)
+    sel_err = np.array([out[i].sel_err for i in range(n)], dtype=np.float64)
+    return flags, drift, sel_err
+
+
+def gace_break_even(ctx, nrows: int, npreds: int, nsets: int = 1, hashed_sets: int = 0, nterms: int | None = None,
+                    row_bytes: int = 4, resident: bool = True, ops_per_row: float = 0.0,
+                    alt_ms: float = 0.0) -> dict:
+    """Predicted cost of one probe and whether it beats alt_ms (the
+    break-even logic of Section V); see gace_break_even in gace.h."""
+    q = _capi.gace_cost_query(int(nrows), int(npreds), int(nsets), int(hashed_sets),
+                              int(npreds if nterms is None else nterms), int(row_bytes), 1 if resident else 0,
+                              float(ops_per_row), float(alt_ms))
+    a = _capi.gace_cost_answer()
+    check(lib().gace_break_even(ctx, C.byref(q), C.byref(a)), "gace_break_even")
+    return {k: getattr(a, k) for k, _ in _capi.gace_cost_answer._fields_ if k != "reserved"}
 
 
 def gace_stats_reset(ctx, time_kernels: bool = False) -> None:

@@ -97,6 +97,35 @@ class gace_kernel_stat(C.Structure):
                 ("bytes", C.c_uint64), ("ops", C.c_uint64), ("total_ms", C.c_double)]
 
 
+class gace_gate_config(C.Structure):
+    _fields_ = [("drift_min", C.c_double), ("sel_err_max", C.c_double), ("pcs_high", C.c_double),
+                ("pcs_low", C.c_double)]
+
+
+class gace_gate_input(C.Structure):
+    _fields_ = [("ndv_hist", C.c_double), ("ndv_est", C.c_double), ("sel_est", C.c_double),
+                ("sel_probe", C.c_double), ("pcs", C.c_double)]
+
+
+class gace_gate_result(C.Structure):
+    _fields_ = [("flags", C.c_uint32), ("reserved", C.c_uint32), ("drift", C.c_double), ("sel_err", C.c_double)]
+
+
+class gace_cost_query(C.Structure):
+    _fields_ = [("nrows", C.c_uint64), ("npreds", C.c_uint32), ("nsets", C.c_uint32), ("hashed_sets", C.c_uint32),
+                ("nterms", C.c_uint32), ("row_bytes", C.c_uint32), ("resident", C.c_uint32),
+                ("ops_per_row", C.c_double), ("alt_ms", C.c_double)]
+
+
+class gace_cost_answer(C.Structure):
+    _fields_ = [("total_ms", C.c_double), ("kernel_ms", C.c_double), ("transfer_ms", C.c_double),
+                ("call_ms", C.c_double), ("hbm_rate", C.c_double), ("ops_rate", C.c_double),
+                ("h2d_rate", C.c_double), ("hash_ns", C.c_double), ("narrow", C.c_uint32),
+                ("offload", C.c_uint32), ("measured", C.c_uint32), ("reserved", C.c_uint32)]
+
+
+GACE_RISK_DRIFT, GACE_RISK_SELECTIVITY, GACE_RISK_CORRELATION = 1, 2, 4
+
 ctx_p = C.c_void_p
 
 # name -> (restype, argtypes); every function declared in include/gace.h
@@ -125,6 +154,9 @@ PROTOTYPES = {
     "gace_poll": (C.c_int, [ctx_p, C.c_uint64, C.c_uint64]),
     "gace_serve_replay": (C.c_int, [ctx_p, C.POINTER(gace_request), C.c_uint32, C.POINTER(C.c_uint64),
                                     C.c_uint32, C.POINTER(C.c_uint64), C.POINTER(C.c_int)]),
+    "gace_gate_eval": (C.c_int, [C.POINTER(gace_gate_config), C.POINTER(gace_gate_input), C.c_uint32,
+                                 C.POINTER(gace_gate_result)]),
+    "gace_break_even": (C.c_int, [ctx_p, C.POINTER(gace_cost_query), C.POINTER(gace_cost_answer)]),
     "gace_stats_reset": (C.c_int, [ctx_p, C.c_uint32]),
     "gace_stats_read": (C.c_int, [ctx_p, C.POINTER(gace_kernel_stat), C.c_uint32,
                                   C.POINTER(C.c_uint32)]),

@@ -15,7 +15,7 @@ OBJDIR = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_SOURCES = ["gace_probe.cu", "gace_hll_join.cu", "gace_noalloc.cu", "gace_batch.cu"]
-HOST_SOURCES = ["gace_capi.cpp", "gace_batch_host.cpp", "gace_serve.cpp"]
+HOST_SOURCES = ["gace_capi.cpp", "gace_batch_host.cpp", "gace_serve.cpp", "gace_gate.cpp"]
 
 
 def cuda_home() -> str:

@@ -106,8 +106,16 @@ struct gace_ctx {
     struct Timed {
         std::string name;
         cudaEvent_t a, b;
+        uint64_t bytes, ops;
     };
     std::map<std::string, KStat> stats;
+    // measured probe costs for the break-even model (kept across stats resets):
+    // the timed narrow and wide probe launches' work and device time
+    struct CostRec {
+        uint64_t launches = 0;
+        double bytes = 0.0, ops = 0.0, ms = 0.0;
+    };
+    CostRec cost_narrow, cost_wide;
     bool timing = false;
     std::vector<cudaEvent_t> ev_free;
     std::vector<Timed> pending;
@@ -137,7 +145,7 @@ struct gace_ctx {
         if (a) cudaEventRecord(a, stream);
         cudaError_t e = launch();
         if (b) cudaEventRecord(b, stream);
-        if (a && b) pending.push_back({name, a, b});
+        if (a && b) pending.push_back({name, a, b, bytes, ops});
         return e;
     }
 
@@ -145,7 +153,16 @@ struct gace_ctx {
     void collect() {
         for (auto& t : pending) {
             float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) stats[t.name].ms += ms;
+            if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+                stats[t.name].ms += ms;
+                CostRec* c = t.name == "probe_narrow" ? &cost_narrow : t.name == "probe_wide" ? &cost_wide : nullptr;
+                if (c) {
+                    c->launches++;
+                    c->bytes += static_cast<double>(t.bytes);
+                    c->ops += static_cast<double>(t.ops);
+                    c->ms += ms;
+                }
+            }
             ev_free.push_back(t.a);
             ev_free.push_back(t.b);
         }

@@ -438,3 +438,58 @@ def test_chain_reduces_to_two_table_join(orc):
     rc, card3, *_ = orc.chain_card(F, D1, 1, D2, K1, K2)
     rc2, card2, *_ = orc.join_card(F, D1, K1)
     assert rc == rc2 == 0 and card3 == card2
+
+
+# ----------------------------------------------------------------- Risky Gate
+
+def test_gate_hand_worked_cases(orc):
+    """Section III-C, Eq. 1-3 with the paper's thresholds: the cases of
+    tests/golden/gate_cases.json, worked by hand."""
+    import json
+    import os
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", "gate_cases.json")) as f:
+        cases = json.load(f)["cases"]
+    for c in cases:
+        args = {k: float(c[k]) for k in ("ndv_hist", "ndv_est", "sel_est", "sel_probe", "pcs") if k in c}
+        flags, drift, sel_err = orc.gate(**args)
+        assert flags == c["flags"], c["note"]
+        if "drift" in c:
+            assert (math.isnan(drift) if c["drift"] is None else math.isclose(drift, c["drift"], rel_tol=1e-12)), c
+        if "sel_err" in c:
+            assert math.isclose(sel_err, c["sel_err"], rel_tol=1e-12), c
+
+
+def test_gate_thresholds_are_the_papers(orc):
+    assert (orc.GATE_DRIFT_MIN, orc.GATE_SEL_ERR_MAX, orc.GATE_PCS_HIGH, orc.GATE_PCS_LOW) == (0.25, 0.01, 1.6, 0.7)
+    # each flag is monotone in its signal's distance from the trusted value
+    prev = 0
+    for est in (1000, 900, 800, 760, 750, 700, 0):
+        f = orc.gate(ndv_hist=1000.0, ndv_est=float(est))[0]
+        assert f >= prev
+        prev = f
+    assert [orc.gate(pcs=x)[0] for x in (0.5, 0.69, 0.7, 1.0, 1.6, 1.61, 3.0)] == [4, 4, 0, 0, 0, 4, 4]
+    # a missing signal never flags
+    assert orc.gate() == (0, orc.gate()[1], orc.gate()[2]) and orc.gate()[0] == 0
+
+
+def test_probe_cost_closed_forms(orc):
+    """The break-even model (Section V, item 2): call cost alone at N = 0;
+    linear in N; a narrow batch costs its bytes, a wide one its compare
+    operations; the break-even N solves total = alt."""
+    r = dict(hbm_rate=4e12, ops_rate=1e13, h2d_rate=5e10, hash_ns=2e-3, call_ms=0.05)
+    assert orc.probe_cost(0, 1, 1, 4, 0, True, 0.0, 1.0, r) == (0.05, True, True)
+    t1 = orc.probe_cost(10**8, 1, 1, 4, 0, True, 0.0, 0.0, r)[0] - 0.05
+    t2 = orc.probe_cost(2 * 10**8, 1, 1, 4, 0, True, 0.0, 0.0, r)[0] - 0.05
+    assert math.isclose(t1, 0.1, rel_tol=1e-12) and math.isclose(t2, 2 * t1, rel_tol=1e-12)  # 400 MB at 4 TB/s
+    # one hashed set adds N x 2 ps: 0.2 ms for 1e8 rows
+    assert math.isclose(orc.probe_cost(10**8, 1, 2, 4, 1, True, 0.0, 0.0, r)[0] - 0.05, 0.3, rel_tol=1e-12)
+    # 33 predicates take the wide model: 1e8 rows x 100 ops at 1e13/s = 1 ms
+    total, narrow, _ = orc.probe_cost(10**8, 33, 33, 4, 0, True, 100.0, 0.0, r)
+    assert not narrow and math.isclose(total - 0.05, 1.0, rel_tol=1e-12)
+    # non-resident columns add their copy: 400 MB at 50 GB/s = 8 ms
+    assert math.isclose(orc.probe_cost(10**8, 1, 1, 4, 0, False, 0.0, 0.0, r)[0] - 0.05, 8.1, rel_tol=1e-12)
+    # break-even: offload exactly when total < alt
+    n_star = (1.0 - 0.05) / (4 / 4e12 * 1e3)
+    assert orc.probe_cost(int(n_star) - 1, 1, 1, 4, 0, True, 0.0, 1.0, r)[2]
+    assert not orc.probe_cost(int(n_star) + 1, 1, 1, 4, 0, True, 0.0, 1.0, r)[2]
