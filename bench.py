@@ -31,6 +31,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -339,6 +341,7 @@ def run_gace(args, d: Dist):
     extras = {}
     if not args.no_extras:
         extras["single_probe"] = single_probes(g, ctx, tid, table, peaks, stream)
+        extras["stability"] = stability_leg(g, ctx, tid, table)
         extras["e2e"] = e2e_leg(g, ctx, table, preds, samples, batch, args, stream)
     g.gace_unload(ctx, tid)
     if not args.no_extras:
@@ -369,6 +372,7 @@ def run_gace(args, d: Dist):
             "clocks": clocks,
             "single_probe": extras.get("single_probe"),
             "join": extras.get("join"),
+            "stability": extras.get("stability"),
             "batched": extras.get("batched"),
             "served": extras.get("served"),
         }
@@ -381,6 +385,49 @@ def _timed_calls(g, ctx, fn, reps):
     for _ in range(reps):
         fn()
     return g.gace_stats_read(ctx)
+
+
+def sampled_estimates(g, ctx, tid, dtypes, preds, rate, seeds, block_rows=0):
+    """sel of every predicate and PCS of every 2-term predicate for each seed
+    of a row (or block) sample at one rate: arrays [seeds][preds].  Eight
+    samples per call (the probe's row sets)."""
+    from workloads import BLOCKS, ROWS, Sample
+
+    sel, pcs = [], []
+    for b in range(0, len(seeds), 8):
+        smp = [Sample(BLOCKS, rate, s, block_rows) if block_rows else Sample(ROWS, rate, s) for s in seeds[b:b + 8]]
+        res, _ = g.gace_probe_batch(ctx, tid, preds, smp, dtypes)
+        sel.extend(res["sel"][:len(smp)].tolist())
+        pcs.extend(res["pcs"][:len(smp)].tolist())
+    return np.array(sel), np.array(pcs)
+
+
+def cv(x):
+    """Coefficient of variation across seeds (axis 0), NaN where the mean is 0."""
+    m = x.mean(axis=0)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return np.where(m != 0, x.std(axis=0) / m, np.nan)
+
+
+def stability_leg(g, ctx, tid, table):
+    """Estimation stability vs budget (the paper's Experiment B): the
+    coefficient of variation over 100 seeds of sel(A and B) and of PCS for
+    two-column conjunctions (a correlated pair, c0/c1, and an independent
+    one, c2/c6), per row-sample rate and for 4096-row block samples."""
+    from workloads import RANGE, Term
+
+    preds = [[Term(0, RANGE, 0, 40), Term(1, RANGE, 0, 40)], [Term(2, RANGE, 0, 40), Term(6, RANGE, -0.5, 0.5)]]
+    seeds = list(range(1, 101))
+    out = {}
+    for label, rate, block in (("rows 0.1%", 0.001, 0), ("rows 1%", 0.01, 0), ("rows 10%", 0.1, 0),
+                               ("blocks 1%", 0.01, 4096), ("blocks 10%", 0.1, 4096)):
+        t0 = time.perf_counter()
+        sel, pcs = sampled_estimates(g, ctx, tid, table.dtypes, preds, rate, seeds, block)
+        out[label] = {"cv_sel": [round(float(x), 5) for x in cv(sel)], "cv_pcs": [round(float(x), 5) for x in cv(pcs)],
+                      "mean_pcs": [round(float(x), 4) for x in np.nanmean(pcs, axis=0)],
+                      "wall_ms_100_seeds": round(1000 * (time.perf_counter() - t0), 2)}
+    out["predicates"] = "A and B: c0 in [0,40) and c1 in [0,40) (copula rho 0.9); c2 in [0,40) and c6 in [-0.5,0.5)"
+    return out
 
 
 def single_probes(g, ctx, tid, table, peaks, stream):
