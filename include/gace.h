@@ -364,8 +364,14 @@ gace_status gace_tune_load(gace_ctx* ctx, const char* path);
  * to batch it with, a step would only add latency.  Results of
  * NDV requests are kept on the host as a sketch cache (LRU) that answers
  * later requests for the same table, column, p and seed at submission.
- * gace_unload forgets a table's sketches and fails with GACE_EBUSY while
- * requests on that table are queued or in flight.
+ * Probe results are cached the same way by bind value (Section V, item 3):
+ * the count of every predicate, term and sample size a finished probe
+ * returned is kept under (table, row set, the predicate's normalised terms in
+ * canonical order), so a later probe whose every count is known (the same
+ * predicates in another batch, order or spelling) is answered at submission
+ * with the synchronous call's results.  gace_unload forgets a table's
+ * sketches and counts and fails with GACE_EBUSY while requests on that table
+ * are queued or in flight.
  */
 typedef struct {
     uint64_t arena_bytes;   /* device bytes for the state of requests in flight; 0 = 1 GiB */
@@ -375,7 +381,7 @@ typedef struct {
     uint64_t chunk_rows;    /* rows per chunk (at most 2^30), rounded up to a multiple of 128, and
                                for a narrow probe pass to a multiple of its tile; 0 = 2^18 */
     uint32_t flags;         /* GACE_SERVE_* */
-    uint32_t reserved;
+    int32_t probe_cache;    /* probe counts kept for reuse (entries); 0 = 65536, < 0 = no cache */
 } gace_serve_config;
 
 /* Never run a request alone through its synchronous call: every request goes

@@ -89,7 +89,7 @@ GACE_SERVE_ALWAYS_STEP = 1
 class gace_serve_config(C.Structure):
     _fields_ = [("arena_bytes", C.c_uint64), ("max_inflight", C.c_uint32), ("sketch_cache", C.c_int32),
                 ("step_rows", C.c_uint64), ("chunk_rows", C.c_uint64), ("flags", C.c_uint32),
-                ("reserved", C.c_uint32)]
+                ("probe_cache", C.c_int32)]
 
 
 class gace_kernel_stat(C.Structure):

@@ -1030,30 +1030,13 @@ void assemble_probe(const ProbePlan& plan, const ProbeRequest& r,
     for (uint32_t k = 0; k < passes.size(); ++k)
         for (uint32_t i = 0; i < passes[k].preds.size(); ++i)
             ploc[passes[k].preds[i]] = {static_cast<int32_t>(k), i};
-    for (uint32_t s = 0; s < nsamples; ++s) {
-        for (uint32_t p = 0; p < npreds; ++p) {
-            uint64_t m = 0;
-            if (plan.pstate[p] == 2) {
-                m = ns[s];
-            } else if (plan.pstate[p] == 0 && plan.set_dev[s] >= 0) {
-                const Pass& ps = passes[ploc[p].first];
-                m = pass_out[ploc[p].first][static_cast<uint64_t>(plan.set_dev[s]) * ps.args.npreds + ploc[p].second];
-            }
-            gace_pred_result& res = r.results[static_cast<uint64_t>(s) * npreds + p];
-            res.match = m;
-            res.sample_rows = ns[s];
-            res.sel = ns[s] ? static_cast<double>(m) / static_cast<double>(ns[s]) : 0.0;
-            res.pcs = std::numeric_limits<double>::quiet_NaN();
-            if (r.preds[p].term_cnt == 2) {
-                const uint64_t ca = marg_of(r.preds[p].term_off, s), cb = marg_of(r.preds[p].term_off + 1, s);
-                if (ca != 0 && cb != 0)
-                    res.pcs = (static_cast<double>(m) * static_cast<double>(ns[s])) /
-                              (static_cast<double>(ca) * static_cast<double>(cb));
-            }
-        }
-        if (r.term_marginals)
-            for (uint32_t t = 0; t < nterms; ++t) r.term_marginals[static_cast<uint64_t>(s) * nterms + t] = marg_of(t, s);
-    }
+    assemble_probe_counts(
+        plan, r, [&](uint32_t s) { return ns[s]; },
+        [&](uint32_t p, uint32_t s) -> uint64_t {
+            const Pass& ps = passes[ploc[p].first];
+            return pass_out[ploc[p].first][static_cast<uint64_t>(plan.set_dev[s]) * ps.args.npreds + ploc[p].second];
+        },
+        marg_of);
 }
 
 }  // namespace host

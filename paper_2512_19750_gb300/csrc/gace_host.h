@@ -7,6 +7,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <limits>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -378,6 +379,41 @@ void stage_pass(Pass& ps, unsigned char* pin, unsigned char* dws, unsigned int* 
 // Results from the passes' counters (host copies, one pointer per pass).
 void assemble_probe(const ProbePlan& plan, const ProbeRequest& r,
                     const std::vector<const unsigned long long*>& pass_out);
+
+// The request's outputs from its counts: ns_of(s) = rows of sample s (0 for
+// an empty sample), match_of(p, s) = count of device predicate p on the
+// sample, marg_of(t, s) = marginal of input term t (0 when never true or the
+// sample is empty).  The one place where selectivities and PCS are computed,
+// so that counts from passes and counts from the served form's result cache
+// give the same doubles.
+template <class NsOf, class MatchOf, class MargOf>
+void assemble_probe_counts(const ProbePlan& plan, const ProbeRequest& r, NsOf&& ns_of, MatchOf&& match_of,
+                           MargOf&& marg_of) {
+    const uint32_t nsamples = r.nsamples, nterms = r.nterms, npreds = r.npreds;
+    for (uint32_t s = 0; s < nsamples; ++s) {
+        const uint64_t ns = ns_of(s);
+        for (uint32_t p = 0; p < npreds; ++p) {
+            uint64_t m = 0;
+            if (plan.pstate[p] == 2)
+                m = ns;
+            else if (plan.pstate[p] == 0 && plan.set_dev[s] >= 0)
+                m = match_of(p, s);
+            gace_pred_result& res = r.results[static_cast<uint64_t>(s) * npreds + p];
+            res.match = m;
+            res.sample_rows = ns;
+            res.sel = ns ? static_cast<double>(m) / static_cast<double>(ns) : 0.0;
+            res.pcs = std::numeric_limits<double>::quiet_NaN();
+            if (r.preds[p].term_cnt == 2) {
+                const uint64_t ca = marg_of(r.preds[p].term_off, s), cb = marg_of(r.preds[p].term_off + 1, s);
+                if (ca != 0 && cb != 0)
+                    res.pcs = (static_cast<double>(m) * static_cast<double>(ns)) /
+                              (static_cast<double>(ca) * static_cast<double>(cb));
+            }
+        }
+        if (r.term_marginals)
+            for (uint32_t t = 0; t < nterms; ++t) r.term_marginals[static_cast<uint64_t>(s) * nterms + t] = marg_of(t, s);
+    }
+}
 
 // ---------------------------------------------------------------- HLL, joins
 

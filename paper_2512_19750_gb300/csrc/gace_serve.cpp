@@ -55,6 +55,7 @@ namespace {
 constexpr uint64_t kDefaultArena = 1ull << 30;
 constexpr uint32_t kDefaultInflight = 4096;
 constexpr int32_t kDefaultSketches = 1024;
+constexpr int32_t kDefaultProbeCounts = 1 << 16;
 constexpr uint64_t kDefaultStepRows = 1ull << 29;
 constexpr uint64_t kDefaultServeChunk = 1ull << 18;
 constexpr uint64_t kCopyPiece = 1ull << 16;    // bytes per scatter / gather descriptor
@@ -122,6 +123,15 @@ struct SketchKey {
     bool operator<(const SketchKey& o) const {
         return std::tie(table, col, p, seed) < std::tie(o.table, o.col, o.p, o.seed);
     }
+};
+
+// A count a finished probe returned (a predicate's match, a term's marginal,
+// a sample's size), kept for reuse (Section V, item 3: probe results cached
+// by bind value); keyed by count_key.
+struct CountEntry {
+    uint64_t value;
+    uint32_t table;
+    std::list<std::string>::iterator lru;
 };
 
 struct Sketch {
@@ -256,6 +266,8 @@ struct ServeState {
     uint64_t next_ticket = 1;
     std::map<SketchKey, Sketch> cache;
     std::list<SketchKey> lru;
+    std::unordered_map<std::string, CountEntry> counts;
+    std::list<std::string> counts_lru;
     gace_status sticky = GACE_OK;  // a CUDA failure of the scheduler
     std::string sticky_msg;
 
@@ -388,6 +400,117 @@ void cache_put(ServeState& srv, const SketchKey& key, std::vector<uint8_t>&& reg
 }
 
 SketchKey sketch_key(const gace_request& q) { return SketchKey{q.table_id, q.col, q.p, q.hash_seed}; }
+
+// Key of a count: the table, the row set (kind, keep rule, threshold, seed
+// hash, block size) and the conjunction's normalised terms in canonical
+// order (none: the set's sample size).  Equal keys are equal counts, whatever
+// the request that measured them.
+std::string count_key(uint32_t table, const SetDesc& d, std::vector<const NTerm*> terms) {
+    std::sort(terms.begin(), terms.end(), [](const NTerm* a, const NTerm* b) { return *a < *b; });
+    std::string k;
+    auto put = [&](const void* p, size_t n) { k.append(static_cast<const char*>(p), n); };
+    put(&table, 4);
+    put(&d.kind, 4);
+    put(&d.mode, 4);
+    put(&d.thresh, 8);
+    put(&d.seedhash, 8);
+    put(&d.block_rows, 8);
+    for (const NTerm* t : terms) {
+        const uint32_t nin = static_cast<uint32_t>(t->in.size());
+        put(&t->col, 4);
+        put(&t->kind, 4);
+        put(&t->a, 8);
+        put(&t->b, 8);
+        put(&nin, 4);
+        if (nin) put(t->in.data(), 4ull * nin);
+    }
+    return k;
+}
+
+std::vector<const NTerm*> pred_terms(const ProbePlan& plan, uint32_t p) {
+    std::vector<const NTerm*> v;
+    for (uint32_t u : plan.pred_u[p]) v.push_back(&plan.uterms[u]);
+    return v;
+}
+
+// Keeps the counts of a finished probe (caller holds srv.mu).
+void counts_put(ServeState& srv, uint32_t table, const ReqPlan& rp) {
+    const size_t cap = static_cast<size_t>(srv.cfg.probe_cache);
+    if (!cap) return;
+    const ProbePlan& plan = rp.plan;
+    const ProbeRequest& r = rp.pr;
+    auto put = [&](std::string&& key, uint64_t v) {
+        auto it = srv.counts.find(key);
+        if (it != srv.counts.end()) {
+            srv.counts_lru.splice(srv.counts_lru.begin(), srv.counts_lru, it->second.lru);
+            return;
+        }
+        srv.counts_lru.push_front(key);
+        srv.counts.emplace(std::move(key), CountEntry{v, table, srv.counts_lru.begin()});
+        while (srv.counts.size() > cap) {
+            srv.counts.erase(srv.counts_lru.back());
+            srv.counts_lru.pop_back();
+        }
+    };
+    for (uint32_t s = 0; s < r.nsamples; ++s) {
+        if (plan.set_dev[s] < 0) continue;
+        const SetDesc& d = plan.sets[plan.set_dev[s]].d;
+        if (r.npreds) put(count_key(table, d, {}), r.results[static_cast<uint64_t>(s) * r.npreds].sample_rows);
+        for (uint32_t p = 0; p < r.npreds; ++p)
+            if (plan.pstate[p] == 0)
+                put(count_key(table, d, pred_terms(plan, p)), r.results[static_cast<uint64_t>(s) * r.npreds + p].match);
+        if (r.term_marginals)
+            for (uint32_t t = 0; t < r.nterms; ++t)
+                if (plan.t2u[t] != UINT32_MAX)
+                    put(count_key(table, d, {&plan.uterms[plan.t2u[t]]}),
+                        r.term_marginals[static_cast<uint64_t>(s) * r.nterms + t]);
+    }
+}
+
+// Answers a compiled probe from kept counts when every count it needs is
+// known (caller holds srv.mu): the outputs are assembled exactly as the
+// synchronous call assembles them.
+bool counts_answer(ServeState& srv, uint32_t table, const ReqPlan& rp) {
+    if (!srv.cfg.probe_cache) return false;
+    const ProbePlan& plan = rp.plan;
+    const ProbeRequest& r = rp.pr;
+    const uint32_t ns = r.nsamples, np = r.npreds, nt = r.nterms;
+    bool want_marg = r.term_marginals != nullptr;
+    for (uint32_t p = 0; p < np; ++p) want_marg = want_marg || r.preds[p].term_cnt == 2;
+    std::vector<uint64_t> nsv(ns, 0), match(static_cast<size_t>(ns) * np, 0), marg;
+    if (want_marg) marg.assign(static_cast<size_t>(ns) * nt, 0);
+    std::vector<std::list<std::string>::iterator> touched;
+    auto get = [&](const std::string& key, uint64_t& v) {
+        auto it = srv.counts.find(key);
+        if (it == srv.counts.end()) return false;
+        v = it->second.value;
+        touched.push_back(it->second.lru);
+        return true;
+    };
+    for (uint32_t s = 0; s < ns; ++s) {
+        if (plan.set_dev[s] < 0) continue;
+        const SetDesc& d = plan.sets[plan.set_dev[s]].d;
+        if (d.mode == 1) {
+            nsv[s] = plan.tab->nrows;
+        } else if (!get(count_key(table, d, {}), nsv[s])) {
+            return false;
+        }
+        for (uint32_t p = 0; p < np; ++p)
+            if (plan.pstate[p] == 0 && !get(count_key(table, d, pred_terms(plan, p)), match[static_cast<size_t>(s) * np + p]))
+                return false;
+        if (want_marg)
+            for (uint32_t t = 0; t < nt; ++t)
+                if (plan.t2u[t] != UINT32_MAX &&
+                    !get(count_key(table, d, {&plan.uterms[plan.t2u[t]]}), marg[static_cast<size_t>(s) * nt + t]))
+                    return false;
+    }
+    for (auto& it : touched) srv.counts_lru.splice(srv.counts_lru.begin(), srv.counts_lru, it);
+    assemble_probe_counts(
+        plan, r, [&](uint32_t s) { return nsv[s]; },
+        [&](uint32_t p, uint32_t s) { return match[static_cast<size_t>(s) * np + p]; },
+        [&](uint32_t t, uint32_t s) -> uint64_t { return want_marg ? marg[static_cast<size_t>(s) * nt + t] : 0; });
+    return true;
+}
 
 gace_status alloc_step(StepSet& S, uint64_t up, uint64_t rb) {
     if (up > S.cap) {
@@ -561,6 +684,7 @@ void ServeState::finish(Live& lv, gace_status st, const std::string& err) {
         std::vector<uint8_t> regs(lv.req.q.registers_out, lv.req.q.registers_out + (1ull << lv.rp.hll.p));
         cache_put(*this, sketch_key(lv.req.q), std::move(regs), *lv.req.q.estimate_out);
     }
+    if (st == GACE_OK && lv.req.q.kind == GACE_REQ_PROBE && lv.rp.plan.tab) counts_put(*this, lv.req.q.table_id, lv.rp);
     deliver(*this, lv.ticket, lv.sink, lv.sink_index, st, err);
     lv.finished = true;
 }
@@ -1035,6 +1159,8 @@ gace_status start_locked(gace_ctx* ctx, const gace_serve_config* cfg, std::share
     if (!c.max_inflight) c.max_inflight = kDefaultInflight;
     if (!c.sketch_cache) c.sketch_cache = kDefaultSketches;
     if (c.sketch_cache < 0) c.sketch_cache = 0;
+    if (!c.probe_cache) c.probe_cache = kDefaultProbeCounts;
+    if (c.probe_cache < 0) c.probe_cache = 0;
     if (!c.step_rows) c.step_rows = kDefaultStepRows;
     if (!c.chunk_rows) c.chunk_rows = kDefaultServeChunk;
     // the kernels count an item's rows in 32-bit shared counters
@@ -1144,6 +1270,17 @@ gace_status submit_request(gace_ctx* ctx, const gace_request& req, uint64_t* tic
         lv->cacheable = true;
     }
     if (gace_status s = compile_request(ctx, q, lv->rp)) return s;
+    if (q.kind == GACE_REQ_PROBE && srv->cfg.probe_cache > 0) {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        if (counts_answer(*srv, q.table_id, lv->rp)) {
+            const uint64_t t = srv->next_ticket++;
+            if (ticket_out) *ticket_out = t;
+            if (!sink) srv->open[t] = true;
+            deliver(*srv, t, sink, idx, GACE_OK, std::string());
+            ctx->stats["serve_probe_cache"].launches += 1;
+            return GACE_OK;
+        }
+    }
     layout_request(*lv);
     lv->fusable = fusable_probe(q) && lv->rp.plan.passes.size() <= 1;
     if (lv->block_bytes > srv->cfg.arena_bytes)
@@ -1190,6 +1327,14 @@ gace_status serve_forget_table(gace_ctx* ctx, uint32_t table_id) {
         if (it->first.table == table_id) {
             s->lru.erase(it->second.lru);
             it = s->cache.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    for (auto it = s->counts.begin(); it != s->counts.end();) {
+        if (it->second.table == table_id) {
+            s->counts_lru.erase(it->second.lru);
+            it = s->counts.erase(it);
         } else {
             ++it;
         }

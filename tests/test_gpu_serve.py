@@ -42,7 +42,8 @@ def _submit_all(g, ctx, breqs):
 @pytest.mark.parametrize("step_rows,chunk_rows", [(0, 0), (1 << 16, 1 << 12), (300, 128)])
 def test_served_equals_synchronous_calls(g, sctx, served, step_rows, chunk_rows):
     tables, reqs, tids = served
-    g.gace_serve_start(sctx, step_rows=step_rows, chunk_rows=chunk_rows, sketch_cache=-1, always_step=True)
+    g.gace_serve_start(sctx, step_rows=step_rows, chunk_rows=chunk_rows, sketch_cache=-1, always_step=True,
+                        probe_cache=-1)
     try:
         breqs = to_requests(g, tids, tables, reqs)
         _submit_all(g, sctx, breqs)
@@ -55,7 +56,7 @@ def test_admission_by_memory(g, sctx, served):
     """A 1 MiB arena and two slots: most requests wait for admission and all
     still come back exact."""
     tables, reqs, tids = served
-    g.gace_serve_start(sctx, arena_bytes=1 << 20, max_inflight=2, sketch_cache=-1, always_step=True)
+    g.gace_serve_start(sctx, arena_bytes=1 << 20, max_inflight=2, sketch_cache=-1, always_step=True, probe_cache=-1)
     try:
         pick = reqs[:60]
         breqs = to_requests(g, tids, tables, pick)
@@ -194,7 +195,7 @@ def test_fused_admission(g, sctx, served, cuda):
     for k in range(1, 12):
         cols = [1 + (k % 3)] if k % 2 else [1, 2 + (k % 2)]
         specs.append(([[rng_term(c, k) for c in cols], [rng_term(cols[0], k + 1)]], shared, bool(k % 3)))
-    g.gace_serve_start(sctx, step_rows=4096, chunk_rows=4096, always_step=True)
+    g.gace_serve_start(sctx, step_rows=4096, chunk_rows=4096, always_step=True, probe_cache=-1)
     try:
         hold = g.ProbeRequest(slow, [[Term(0, RANGE, 0, 1000)]], [Sample(FULL)], [I32])
         th = g.gace_submit(sctx, hold)
@@ -220,7 +221,7 @@ def test_request_alone_on_idle_server(g, sctx, served):
     """An idle server runs a lone request through its synchronous call; the
     results are the same, and requests that overlap still take the steps."""
     tables, reqs, tids = served
-    g.gace_serve_start(sctx, sketch_cache=-1)
+    g.gace_serve_start(sctx, sketch_cache=-1, probe_cache=-1)
     try:
         g.gace_stats_reset(sctx)
         pick = reqs[:12]
@@ -232,3 +233,52 @@ def test_request_alone_on_idle_server(g, sctx, served):
         check_against_sync(g, sctx, tids, tables, pick, breqs)
     finally:
         g.gace_serve_stop(sctx)
+
+
+def test_probe_result_cache(g, sctx, cuda):
+    """A probe whose every count an earlier probe returned (the same
+    predicates in another order, spelling and batch) is answered at
+    submission with the synchronous call's results; unloading the table
+    forgets its counts."""
+    import torch
+
+    from workloads import EQ, IN, ROWS
+
+    gen = torch.Generator(device=cuda).manual_seed(5)
+    cols = [torch.randint(0, 1000, (2_000_003,), generator=gen, device=cuda, dtype=torch.int32) for _ in range(3)]
+    tid = g.gace_load_columns(sctx, cols, borrow=True)
+    dt = [I32] * 3
+    smp = [Sample(FULL), Sample(ROWS, 0.1, 3)]
+    a, b, c, d = (Term(0, RANGE, 10, 400), Term(1, EQ, 7), Term(2, IN, values=(1, 5, 9, 5)),
+                  Term(1, RANGE, 0, 500))
+    first = [[a, b], [c], [a, d, c]]
+    again = [[b, a], [Term(2, IN, values=(9, 1, 5))], [c, d, a], [a, a, b]]  # same conjunctions, other spellings
+    g.gace_serve_start(sctx)
+    try:
+        g.gace_stats_reset(sctx)
+        q1 = g.ProbeRequest(tid, first, smp, dt, marginals=True)
+        assert g.gace_poll(sctx, g.gace_submit(sctx, q1), POLL_US)
+        q2 = g.ProbeRequest(tid, again, smp, dt, marginals=True)
+        assert g.gace_poll(sctx, g.gace_submit(sctx, q2), 0)  # complete at submission
+        assert g.gace_stats_read(sctx)["serve_probe_cache"]["launches"] == 1
+        res, marg = g.gace_probe_batch(sctx, tid, again, smp, dt, marginals=True)
+        for f in ("match", "sample_rows", "sel"):
+            assert np.array_equal(q2.results[f], res[f])
+        assert np.array_equal(q2.results["pcs"], res["pcs"], equal_nan=True)
+        assert np.array_equal(q2.marginals, marg)
+        # a predicate never measured is not answered from the cache
+        q3 = g.ProbeRequest(tid, [[a, c]], smp, dt)
+        t3 = g.gace_submit(sctx, q3)
+        assert g.gace_poll(sctx, t3, POLL_US)
+        assert g.gace_stats_read(sctx)["serve_probe_cache"]["launches"] == 1
+        # unloading forgets the table's counts: other data under the same probe
+        g.gace_unload(sctx, tid)
+        cols2 = [torch.randint(0, 1000, (2_000_003,), generator=gen, device=cuda, dtype=torch.int32) for _ in range(3)]
+        tid = g.gace_load_columns(sctx, cols2, borrow=True)
+        q4 = g.ProbeRequest(tid, again, smp, dt, marginals=True)
+        assert g.gace_poll(sctx, g.gace_submit(sctx, q4), POLL_US)
+        res, marg = g.gace_probe_batch(sctx, tid, again, smp, dt, marginals=True)
+        assert np.array_equal(q4.results["match"], res["match"]) and np.array_equal(q4.marginals, marg)
+    finally:
+        g.gace_serve_stop(sctx)
+        g.gace_unload(sctx, tid)
