@@ -342,7 +342,7 @@ def run_gace(args, d: Dist):
     if not args.no_extras:
         extras["single_probe"] = single_probes(g, ctx, tid, table, peaks, stream)
         extras["stability"] = stability_leg(g, ctx, tid, table)
-        extras["e2e"] = e2e_leg(g, ctx, table, preds, samples, batch, args, stream)
+        extras["e2e"], extras["overhead"] = e2e_leg(g, ctx, table, preds, samples, batch, args, stream)
     g.gace_unload(ctx, tid)
     if not args.no_extras:
         del table
@@ -373,6 +373,7 @@ def run_gace(args, d: Dist):
             "single_probe": extras.get("single_probe"),
             "join": extras.get("join"),
             "stability": extras.get("stability"),
+            "overhead": extras.get("overhead"),
             "batched": extras.get("batched"),
             "served": extras.get("served"),
         }
@@ -477,8 +478,44 @@ def e2e_leg(g, ctx, table, preds, samples, batch, args, stream):
         once()
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / reps
-    return {"value": table.nrows / dt, "unit": "rows/s", "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1000.0, "steps": reps}
+    out = {"value": table.nrows / dt, "unit": "rows/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1000.0, "steps": reps}
+    overhead = overhead_leg(g, ctx, host, table.dtypes)
+    del host
+    return out, overhead
+
+
+def overhead_leg(g, ctx, host, dtypes):
+    """Probe overhead decomposition (the paper's Experiment A) for tables that
+    are not resident: H2D of the columns from pinned host memory (key-only:
+    the two referenced columns; full-row: all eight), the kernel, and the
+    read-back with the host's reduction into results, for N = 1e4 .. 1e8 rows
+    of one two-term probe (median of 3)."""
+    from workloads import FULL, RANGE, Sample, Term
+
+    preds = [[Term(0, RANGE, 0, 40), Term(1, RANGE, 0, 40)]]
+    out = {}
+    for mode, cols in (("key-only", [0, 1]), ("full-row", list(range(len(host))))):
+        out[mode] = {}
+        for n in (10**4, 10**5, 10**6, 10**7, 10**8):
+            if n > host[0].numel():
+                continue
+            ph = []
+            for _ in range(3):
+                t0 = time.perf_counter()
+                tid = g.gace_load_columns(ctx, [host[c][:n] for c in cols])
+                t1 = time.perf_counter()
+                g.gace_stats_reset(ctx, time_kernels=True)
+                g.gace_probe_batch(ctx, tid, preds, [Sample(FULL)], [dtypes[c] for c in cols])
+                t2 = time.perf_counter()
+                kern = sum(v["total_ms"] for v in g.gace_stats_read(ctx).values())
+                g.gace_unload(ctx, tid)
+                ph.append(((t1 - t0) * 1e3, kern, (t2 - t1) * 1e3 - kern))
+            h2d, kern, rest = (statistics.median(x[i] for x in ph) for i in range(3))
+            out[mode][f"{n:.0e}"] = {"h2d_ms": round(h2d, 4), "kernel_ms": round(kern, 4),
+                                     "d2h_and_reduction_ms": round(rest, 4), "total_ms": round(h2d + kern + rest, 4),
+                                     "transfer_share": round(h2d / (h2d + kern + rest), 3)}
+    return out
 
 
 def join_leg(g, ctx, dev, peaks, stream):
@@ -587,7 +624,8 @@ def batched_leg(g, ctx, dev, args):
     zero = np.zeros(n, dtype=np.uint64)
     plain_done, plain_st = g.gace_serve_replay(ctx, to_gace_requests(g, tids, tables, reqs), zero, mode=1)
     plain_wall = float(plain_done.max()) / 1e9
-    g.gace_serve_start(ctx, sketch_cache=-1)
+    # no result caches: the warm-up run would answer the timed run's requests
+    g.gace_serve_start(ctx, sketch_cache=-1, probe_cache=-1)
     g.gace_serve_replay(ctx, to_gace_requests(g, tids, tables, reqs), zero, mode=0)  # warm-up
     served_done, served_st = g.gace_serve_replay(ctx, to_gace_requests(g, tids, tables, reqs), zero, mode=0)
     g.gace_serve_stop(ctx)
