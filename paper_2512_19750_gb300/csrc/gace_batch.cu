@@ -253,15 +253,17 @@ __global__ void __launch_bounds__(kThreads, GACE_BATCH_SIDE_CTAS) k_batch_side(c
 }
 
 // Join histograms over small key domains: per item, a shared-memory
-// histogram of the item's rows (equal keys of a warp combined first), then
-// its nonzero bins into the job's global histogram.
+// histogram of the item's rows (after the staging buffers when the side's
+// columns stream through the tile pipeline), then its nonzero bins into the
+// job's global histogram.
 __global__ void __launch_bounds__(kHistThreads, 1) k_batch_hist(const BatchItem* __restrict__ items, uint32_t nitems,
                                                                 const BatchJob* __restrict__ jobs,
                                                                 unsigned int* head) {
-    extern __shared__ __align__(16) uint32_t shist[];
+    extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint32_t s_item;
+    __shared__ __align__(16) SideArgs sA;
     __shared__ unsigned long long scratch[kHistThreads / 32];
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (;;) {
         if (tid == 0) s_item = atomicAdd(head, 1u);
         __syncthreads();
@@ -269,13 +271,36 @@ __global__ void __launch_bounds__(kHistThreads, 1) k_batch_hist(const BatchItem*
         if (k >= nitems) return;
         const BatchItem it = items[k];
         const BatchJob& J = jobs[it.job];
-        const SideArgs& SA = *J.side;
+        {
+            const uint4* src = reinterpret_cast<const uint4*>(J.side);
+            uint4* dst = reinterpret_cast<uint4*>(&sA);
+            for (uint32_t i = tid; i < sizeof(SideArgs) / 16; i += kHistThreads) dst[i] = src[i];
+        }
+        __syncthreads();  // sA and s_item are read below; both are rewritten only after the next barrier
+        const SideArgs& SA = sA;
+        const bool staged = SA.stage_bytes && SA.tile_rows % (128u * (kHistThreads / 32)) == 0;
+        uint32_t* shist = reinterpret_cast<uint32_t*>(smem + (staged ? SA.smem_bytes : 0u));
         const uint32_t K = static_cast<uint32_t>(SA.domain);
         for (uint32_t i = tid; i < K; i += kHistThreads) shist[i] = 0;
-        __syncthreads();  // also: every thread has read s_item
+        __syncthreads();
         unsigned long long npass = 0, acc = 0;
-        side_groups<0, kSmemHistAgg>(SA, shist, J.strict, nullptr, 0, 0, nullptr, it.begin / 4 + (tid - lane),
-                             (it.end + 3) / 4, kHistThreads, npass, acc);
+        if (staged) {
+            const uint64_t first = it.begin / SA.tile_rows;
+            uint64_t end = (it.end + SA.tile_rows - 1) / SA.tile_rows;
+            if (end > SA.ntiles) end = SA.ntiles;
+            uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+            const bool ok = SA.slot_dtype[SA.key_slot] == 1
+                                ? side_tiles<0, kSmemHistAgg, true, 1, kHistThreads / 32>(
+                                      SA, bars, smem + kSideStageOff, tid, lane, warp, first, end, 1, shist, J.strict,
+                                      nullptr, 0, 0, nullptr, npass, acc)
+                                : side_tiles<0, kSmemHistAgg, false, 1, kHistThreads / 32>(
+                                      SA, bars, smem + kSideStageOff, tid, lane, warp, first, end, 1, shist, J.strict,
+                                      nullptr, 0, 0, nullptr, npass, acc);
+            if (!ok) return;  // uniform over the CTA; the status word says why
+        } else {
+            side_groups<0, kSmemHistAgg>(SA, shist, J.strict, nullptr, 0, 0, nullptr, it.begin / 4 + (tid - lane),
+                                         (it.end + 3) / 4, kHistThreads, npass, acc);
+        }
         __syncthreads();
         hist_merge(shist, J.hist, K, tid, kHistThreads);
         const unsigned long long tp = block_sum_u64<kHistThreads / 32>(npass, scratch);  // synchronises

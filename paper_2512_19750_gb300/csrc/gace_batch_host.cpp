@@ -390,22 +390,26 @@ void emit_jobs(ReqPlan& rp, unsigned char* dws, unsigned int* batch_status, std:
         jr.ops = n;
         return jr;
     };
-    // small key domains are histogrammed per CTA in shared memory
-    auto smem_hist = [&](JobRec& jr, uint64_t domain) {
+    // small key domains are histogrammed per CTA in shared memory (after the
+    // staging buffers when the side's columns stream through the pipeline)
+    auto smem_hist = [&](JobRec& jr, int i, uint64_t domain) {
         if (domain > kSmemHistMax) return;
+        const SideArgs& sa = rp.side[i];
+        const bool staged = sa.stage_bytes && sa.tile_rows % (128u * (kHistThreads / 32)) == 0;
         jr.cls = kClassHist;
-        jr.smem = static_cast<uint32_t>(domain) * 4u;
+        jr.smem = (staged ? sa.smem_bytes : 0u) + static_cast<uint32_t>(domain) * 4u;
         jr.granule = round_up(4 * domain, 128);  // at least 4 rows per bin and item
+        if (staged) jr.granule = round_up(jr.granule, sa.tile_rows);
     };
     // phase 0: the dimension histogram the others read (and the fact histogram)
     JobRec h = side_job(kJobHist, two ? 2 : 1, 0, 1);
     h.job.hist = hd;
-    smem_hist(h, two ? rp.K2 : rp.K);
+    smem_hist(h, two ? 2 : 1, two ? rp.K2 : rp.K);
     jobs.push_back(h);
     if (rp.hist_dot) {
         JobRec hfj = side_job(kJobHistAgg, 0, 0, 0);
         hfj.job.hist = hf;
-        smem_hist(hfj, rp.K);
+        smem_hist(hfj, 0, rp.K);
         jobs.push_back(hfj);
     }
     // its largest entry for the overflow check

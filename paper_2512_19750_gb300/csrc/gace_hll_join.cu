@@ -69,6 +69,30 @@ __global__ void __launch_bounds__(kHistThreads, 1)
     if (threadIdx.x == 0 && tp) atomicAdd(A.pass_count, tp);
 }
 
+// The same over tiles staged in shared memory: the stage buffers, then the
+// histogram; 32 warps take a tile 128 rows each.
+template <bool KEY64>
+__global__ void __launch_bounds__(kHistThreads, 1)
+    k_hist_smem_staged(const __grid_constant__ SideArgs A, uint32_t* hist, int strict) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ unsigned long long scratch[kHistThreads / 32];
+    uint32_t* shist = reinterpret_cast<uint32_t*>(smem + A.smem_bytes);
+    const uint32_t K = static_cast<uint32_t>(A.domain);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (uint32_t i = tid; i < K; i += kHistThreads) shist[i] = 0;
+    __syncthreads();
+    unsigned long long npass = 0, acc = 0;
+    if (!side_tiles<0, kSmemHistAgg, KEY64, 1, kHistThreads / 32>(A, reinterpret_cast<uint64_t*>(smem),
+                                                                  smem + kSideStageOff, tid, lane, warp, blockIdx.x,
+                                                                  A.ntiles, gridDim.x, shist, strict, nullptr, 0, 0,
+                                                                  nullptr, npass, acc))
+        return;  // a pipeline wait gave up: the status says so
+    __syncthreads();
+    hist_merge(shist, hist, K, tid, kHistThreads);
+    const unsigned long long tp = block_sum_u64<kHistThreads / 32>(npass, scratch);
+    if (tid == 0 && tp) atomicAdd(A.pass_count, tp);
+}
+
 #ifndef GACE_GATHER_GROUPS
 #define GACE_GATHER_GROUPS 1
 #endif
@@ -215,6 +239,21 @@ cudaError_t hist_launch(const SideArgs& a, uint32_t* hist, int strict, int aggre
                         cudaStream_t s) {
     // small domains over enough rows (each CTA at least 4 rows per bin, so
     // that its merge stays a small part of its work): shared-memory histograms
+#ifndef GACE_HIST_STAGED
+#define GACE_HIST_STAGED 1
+#endif
+    if (GACE_HIST_STAGED && aggregate && a.domain <= kSmemHistMax && a.nrows >= 4 * a.domain * 16 &&
+        a.stage_bytes && a.tile_rows % (128u * (kHistThreads / 32)) == 0) {
+        const uint32_t smem = a.smem_bytes + static_cast<uint32_t>(a.domain) * 4u;
+        auto kern = a.slot_dtype[a.key_slot] == 1 ? k_hist_smem_staged<true> : k_hist_smem_staged<false>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        uint64_t want = a.nrows / (4 * a.domain);
+        if (want > a.ntiles) want = a.ntiles;
+        const int grid = static_cast<int>(want < static_cast<uint64_t>(sms) ? (want ? want : 1) : sms);
+        kern<<<grid, kHistThreads, smem, s>>>(a, hist, strict);
+        return cudaGetLastError();
+    }
     if (aggregate && a.domain <= kSmemHistMax && a.nrows >= 4 * a.domain * 16) {
         const uint32_t smem = static_cast<uint32_t>(a.domain) * 4u;
         cudaError_t e = cudaFuncSetAttribute(k_hist_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
