@@ -21,6 +21,7 @@
 
 #include "gace_device.cuh"
 #include "gace_internal.h"
+
 #include "gace_probe_dev.cuh"
 #include "gace_probe_narrow.cuh"
 #include "gace_side_dev.cuh"
@@ -140,7 +141,13 @@ __global__ void __launch_bounds__(kThreads, 3) k_batch(const BatchItem* __restri
 // are HBM-bound and want the register budget and occupancy of the plain
 // narrow kernels rather than the general kernel's.  The pass arguments are
 // copied into shared memory once per item.
-__global__ void __launch_bounds__(kThreads, 4) k_batch_probe(const BatchItem* __restrict__ items, uint32_t nitems,
+// Three CTAs per SM: the class launch is sized by its largest pass's shared
+// memory (three CTAs' worth in practice), and the registers of the fourth
+// would only add spills.
+#ifndef GACE_BATCH_PROBE_CTAS
+#define GACE_BATCH_PROBE_CTAS 3
+#endif
+__global__ void __launch_bounds__(kThreads, GACE_BATCH_PROBE_CTAS) k_batch_probe(const BatchItem* __restrict__ items, uint32_t nitems,
                                                              const BatchJob* __restrict__ jobs, unsigned int* head) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint32_t s_item;
