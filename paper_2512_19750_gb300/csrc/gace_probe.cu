@@ -29,10 +29,6 @@
 
 #include "gace_device.cuh"
 #include "gace_internal.h"
-
-#ifndef GACE_PROBE_CTAS
-#define GACE_PROBE_CTAS 4
-#endif
 #include "gace_probe_dev.cuh"
 #include "gace_probe_narrow.cuh"
 
@@ -47,7 +43,7 @@ using namespace probe_dev;
 // Grid-striding kernels over the whole table (HASH: some row set is a hashed
 // sample; MAXS: row sets held in registers per lane).
 template <bool HASH, int MAXS>
-__global__ void __launch_bounds__(kThreads, GACE_PROBE_CTAS) k_probe_narrow(const __grid_constant__ ProbeArgs A) {
+__global__ void __launch_bounds__(kThreads, 4) k_probe_narrow(const __grid_constant__ ProbeArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const Smem S = carve(A, smem, warp);
@@ -59,7 +55,7 @@ __global__ void __launch_bounds__(kThreads, GACE_PROBE_CTAS) k_probe_narrow(cons
 }
 
 template <bool HASH>
-__global__ void __launch_bounds__(kThreads, GACE_PROBE_CTAS) k_probe_single(const __grid_constant__ ProbeArgs A) {
+__global__ void __launch_bounds__(kThreads, 4) k_probe_single(const __grid_constant__ ProbeArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const Smem S = carve(A, smem, warp);
