@@ -209,11 +209,24 @@ __device__ __forceinline__ bool side_item_staged(const SideArgs& A, const BatchJ
         return side_tiles<MODE, AGG, false, 2>(A, bars, stages, tid, lane, warp, first, end, 1, J.hist, J.strict,
                                                J.weight, J.fk2_slot, J.domain2, J.w64, npass, acc);
     }
-    if (A.slot_dtype[A.key_slot] == 1)
-        return side_tiles<MODE, AGG, true, NQ>(A, bars, stages, tid, lane, warp, first, end, 1, J.hist, J.strict,
-                                               J.weight, J.fk2_slot, J.domain2, J.w64, npass, acc);
-    return side_tiles<MODE, AGG, false, NQ>(A, bars, stages, tid, lane, warp, first, end, 1, J.hist, J.strict,
-                                            J.weight, J.fk2_slot, J.domain2, J.w64, npass, acc);
+    // skewed keys into a global histogram: a hot-key cache after the stages
+    uint32_t* hot = nullptr;
+    if (MODE == 0 && AGG && kHotCache && A.domain <= 0xFFFFFFFFull) {
+        hot = reinterpret_cast<uint32_t*>(smem + A.smem_bytes);
+        hot_init(hot, kHotLog, tid, kThreads);
+    }
+    const bool ok = A.slot_dtype[A.key_slot] == 1
+                        ? side_tiles<MODE, AGG, true, NQ>(A, bars, stages, tid, lane, warp, first, end, 1, J.hist,
+                                                          J.strict, J.weight, J.fk2_slot, J.domain2, J.w64, npass,
+                                                          acc, hot, kHotLog)
+                        : side_tiles<MODE, AGG, false, NQ>(A, bars, stages, tid, lane, warp, first, end, 1, J.hist,
+                                                           J.strict, J.weight, J.fk2_slot, J.domain2, J.w64, npass,
+                                                           acc, hot, kHotLog);
+    if (ok && hot) {
+        __syncthreads();
+        hot_flush(hot, kHotLog, J.hist, tid, kThreads);
+    }
+    return ok;
 }
 
 #ifndef GACE_BATCH_SIDE_CTAS

@@ -34,6 +34,7 @@
 #include <vector>
 
 #include "gace_host.h"
+#include "gace_hot.h"
 
 namespace gace {
 namespace host {
@@ -365,7 +366,10 @@ void emit_jobs(ReqPlan& rp, unsigned char* dws, unsigned int* batch_status, std:
         jr.cost = 2;  // latency-bound: a key's filter, then its weight or histogram update
         if (rp.side[i].stage_bytes) {  // aligned, narrow rows: the staged side kernel, by whole tiles
             jr.cls = kClassSide;
-            jr.smem = rp.side[i].smem_bytes;
+            // global histograms keep a hot-key cache (8 bytes per slot) after the stages
+            const bool hot =
+                kHotCache && (kind == kJobHist || kind == kJobHistAgg) && rp.side[i].domain <= 0xFFFFFFFFull;
+            jr.smem = rp.side[i].smem_bytes + (hot ? 8u << kHotLog : 0u);
             jr.granule = rp.side[i].tile_rows;
         }
         jr.job.kind = kind;

@@ -136,10 +136,20 @@ __global__ void __launch_bounds__(kJoinThreads, 3)
     __shared__ unsigned long long scratch[kJoinThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     unsigned long long npass = 0, acc = 0;
+    // skewed keys into a global histogram: a hot-key cache after the stages
+    uint32_t* hot = nullptr;
+    if (MODE == 0 && AGG && kHotCache && A.domain <= 0xFFFFFFFFull) {
+        hot = reinterpret_cast<uint32_t*>(smem + A.smem_bytes);
+        hot_init(hot, kHotLog, tid, kJoinThreads);
+    }
     if (!side_tiles<MODE, AGG, KEY64, NQ>(A, reinterpret_cast<uint64_t*>(smem), smem + kSideStageOff, tid, lane, warp,
                                blockIdx.x, A.ntiles, gridDim.x, hist, strict, weight, fk2_slot, domain2, w64, npass,
-                               acc))
+                               acc, hot, kHotLog))
         return;  // a pipeline wait gave up: the status says so
+    if (hot) {
+        __syncthreads();
+        hot_flush(hot, kHotLog, hist, tid, kJoinThreads);
+    }
     const unsigned long long tp = block_sum_u64<kJoinThreads / 32>(npass, scratch);
     if (threadIdx.x == 0 && tp) atomicAdd(A.pass_count, tp);
     if (MODE == 1 || MODE == 2) {
@@ -205,16 +215,17 @@ template <int MODE, bool AGG, bool KEY64, int NQ>
 static cudaError_t staged_launch_t(const SideArgs& a, int sms, cudaStream_t s, uint32_t* hist, int strict,
                                  const void* weight, unsigned long long* out_sum, uint32_t fk2_slot, uint64_t domain2,
                                  unsigned long long* w64) {
+    const uint32_t smem = a.smem_bytes + (MODE == 0 && AGG && kHotCache ? 8u << kHotLog : 0u);
     cudaError_t e = cudaFuncSetAttribute(k_side_staged<MODE, AGG, KEY64, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(a.smem_bytes));
+                                         static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_side_staged<MODE, AGG, KEY64, NQ>, kJoinThreads, a.smem_bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_side_staged<MODE, AGG, KEY64, NQ>, kJoinThreads, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
     const uint64_t cap = static_cast<uint64_t>(sms) * occ;
     const int grid = static_cast<int>(a.ntiles < cap ? (a.ntiles ? a.ntiles : 1) : cap);
-    k_side_staged<MODE, AGG, KEY64, NQ><<<grid, kJoinThreads, a.smem_bytes, s>>>(a, hist, strict, weight, out_sum, fk2_slot,
+    k_side_staged<MODE, AGG, KEY64, NQ><<<grid, kJoinThreads, smem, s>>>(a, hist, strict, weight, out_sum, fk2_slot,
                                                                        domain2, w64);
     return cudaGetLastError();
 }

@@ -9,6 +9,7 @@
 #include <type_traits>
 
 #include "gace_device.cuh"
+#include "gace_hot.h"
 #include "gace_internal.h"
 #include "gace_stage.cuh"
 
@@ -315,6 +316,43 @@ __device__ __forceinline__ uint64_t key_index(const Vals<NQ>& v, int i, uint64_t
 template <int MODE>
 __host__ __device__ constexpr int side_nq() { return (MODE == 1 || MODE == 2) ? 4 : 2; }
 
+// A CTA's cache of hot histogram keys in shared memory (global histograms
+// of skewed keys: every CTA adding to a Zipf-hot key's one L2 address
+// serialises): 2^hot_log slots of (key, count), keys first.  A key takes the
+// slot its hash selects if the slot is free; a key that finds its slot taken
+// by another goes to the global histogram.  Every count lands in exactly one
+// place; hot_flush adds the slots into the global histogram.  Keys are below
+// 0xFFFFFFFF (the empty mark), so the domain must be below 2^32.
+constexpr uint32_t kHotEmpty = 0xFFFFFFFFu;
+
+__device__ __forceinline__ void hot_init(uint32_t* hot, uint32_t hot_log, int tid, int nthreads) {
+    for (uint32_t i = tid; i < (1u << hot_log); i += nthreads) {
+        hot[i] = kHotEmpty;
+        hot[(1u << hot_log) + i] = 0;
+    }
+}
+
+__device__ __forceinline__ void hot_add(uint32_t* hot, uint32_t hot_log, uint32_t* hist, uint32_t k, uint32_t c) {
+    const uint32_t slot = (k * 0x9E3779B1u) >> (32 - hot_log);
+    uint32_t cur = hot[slot];
+    if (cur == kHotEmpty) {
+        cur = atomicCAS(&hot[slot], kHotEmpty, k);
+        if (cur == kHotEmpty) cur = k;  // claimed
+    }
+    if (cur == k)
+        atomicAdd(&hot[(1u << hot_log) + slot], c);
+    else
+        atomicAdd(&hist[k], c);
+}
+
+__device__ __forceinline__ void hot_flush(const uint32_t* hot, uint32_t hot_log, uint32_t* hist, int tid,
+                                          int nthreads) {
+    for (uint32_t i = tid; i < (1u << hot_log); i += nthreads) {
+        const uint32_t k = hot[i], c = hot[(1u << hot_log) + i];
+        if (k != kHotEmpty && c) atomicAdd(&hist[k], c);
+    }
+}
+
 // One side mode over tiles [first, end) of the staged scan (stride: the grid's
 // CTAs); npass and acc are per thread.  MODE as in side_rows; KEY64: the key
 // column is int64 (else int32); NQ quads of rows per lane and step, WARPS warps
@@ -325,7 +363,7 @@ __device__ __forceinline__ bool side_tiles(const SideArgs& A, uint64_t* bars, un
                                            int lane, int warp, uint64_t first, uint64_t end, uint64_t stride,
                                            uint32_t* hist, int strict, const void* weight, uint32_t fk2_slot,
                                            uint64_t domain2, unsigned long long* w64, unsigned long long& npass,
-                                           unsigned long long& acc) {
+                                           unsigned long long& acc, uint32_t* hot = nullptr, uint32_t hot_log = 0) {
     constexpr int R = 4 * NQ;
     constexpr uint32_t kSlice = 128u * NQ;
     constexpr uint32_t kAll = R == 32 ? 0xFFFFFFFFu : (1u << R) - 1u;
@@ -407,7 +445,12 @@ __device__ __forceinline__ bool side_tiles(const SideArgs& A, uint64_t* bars, un
                             grp = __match_any_sync(kFullMask, u ? static_cast<uint32_t>(k) : 0xFFFFFFFFu);
                         else
                             grp = __match_any_sync(kFullMask, u ? static_cast<unsigned long long>(k) : ~0ull);
-                        if (u && (__ffs(grp) - 1) == lane) atomicAdd(&hist[k], __popc(grp));
+                        if (u && (__ffs(grp) - 1) == lane) {
+                            if (hot)
+                                hot_add(hot, hot_log, hist, static_cast<uint32_t>(k), __popc(grp));
+                            else
+                                atomicAdd(&hist[k], __popc(grp));
+                        }
                     } else if (u) {
                         atomicAdd(&hist[k], 1u);
                     }

@@ -191,3 +191,33 @@ def test_staged_and_direct_sides(g, gctx, orc, cuda, method):
             g.gace_unload(gctx, fid)
             g.gace_unload(gctx, did)
     assert results[0] == results[1]
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_skewed_keys_large_domain(g, gctx, orc, cuda, method):
+    """Zipf(1.3) keys over a 200 000-key domain (above the shared-memory
+    histogram's): the global histograms keep their hot keys in each CTA's
+    shared-memory cache; counts equal the oracle's, plain and batched."""
+    from workloads import I32, uniform_int_column, zipf_column
+    from workloads.gen import _gen
+
+    gen = _gen(5151, cuda)
+    K = 200_000
+    d = Table("d", [zipf_column(3_000_000, 1.3, K, gen, cuda), uniform_int_column(3_000_000, 0, 100, gen, cuda)],
+              [I32, I32])
+    f = Table("f", [zipf_column(5_000_000, 1.1, K, gen, cuda), uniform_int_column(5_000_000, 0, 100, gen, cuda)],
+              [I32, I32])
+    did, fid = g.gace_load_columns(gctx, d.columns), g.gace_load_columns(gctx, f.columns)
+    try:
+        dt, ft = [Term(1, RANGE, 0, 70)], [Term(1, RANGE, 10, 90)]
+        F, D = g.JoinSideSpec(fid, 0, ft, f.dtypes), g.JoinSideSpec(did, 0, dt, d.dtypes)
+        out = g.gace_join_card(gctx, F, D, K, None, 0, 0, method)
+        rc, card, fp, dp = orc.join_card(JoinSide(_host(f), 0, ft), JoinSide(_host(d), 0, dt), K)
+        assert rc == 0
+        assert (out["card"], out["fact_rows"], out["dim_rows"]) == (card, fp, dp)
+        q = g.JoinRequest(F, D, K, method=method)
+        assert g.gace_run_batch(gctx, [q]) == [0]
+        assert q.result == out
+    finally:
+        g.gace_unload(gctx, did)
+        g.gace_unload(gctx, fid)
