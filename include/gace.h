@@ -165,8 +165,11 @@ gace_status gace_unload(gace_ctx* ctx, uint32_t table_id);
 
 /*
  * Measurement Engine probe (Section III-B; Key-Only + Bitmask evaluation,
- * Section IV-H): one fused pass over the referenced columns evaluates every
- * predicate on every requested row set.
+ * Section IV-H): fused passes over the referenced columns evaluate every
+ * predicate on every requested row set (one pass unless the batch outgrows a
+ * pass's shared-memory tables; each pass reads only its own columns).  When
+ * every row set is a block sample, only the tiles that hold a sampled block
+ * are read.
  *   samples[nsamples]   1..8 row sets
  *   terms[nterms]       the terms the predicates index; identical terms are
  *                       evaluated once
