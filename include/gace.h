@@ -372,7 +372,8 @@ gace_status gace_tune_load(gace_ctx* ctx, const char* path);
  * returned is kept under (table, row set, the predicate's normalised terms in
  * canonical order), so a later probe whose every count is known (the same
  * predicates in another batch, order or spelling) is answered at submission
- * with the synchronous call's results.  gace_unload forgets a table's
+ * with the synchronous call's results.  Only small probes take part: at most
+ * 256 (predicates + terms) x samples counts.  gace_unload forgets a table's
  * sketches and counts and fails with GACE_EBUSY while requests on that table
  * are queued or in flight.
  */

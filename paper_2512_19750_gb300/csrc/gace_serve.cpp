@@ -56,6 +56,10 @@ constexpr uint64_t kDefaultArena = 1ull << 30;
 constexpr uint32_t kDefaultInflight = 4096;
 constexpr int32_t kDefaultSketches = 1024;
 constexpr int32_t kDefaultProbeCounts = 1 << 16;
+// Only probes of at most this many (predicate, sample) counts go through the
+// count cache (the gate's small probes): keying a large batch's every count
+// would cost the scheduler more than the cache saves.
+constexpr uint64_t kCachedProbeMaxCounts = 256;
 constexpr uint64_t kDefaultStepRows = 1ull << 29;
 constexpr uint64_t kDefaultServeChunk = 1ull << 18;
 constexpr uint64_t kCopyPiece = 1ull << 16;    // bytes per scatter / gather descriptor
@@ -439,6 +443,7 @@ void counts_put(ServeState& srv, uint32_t table, const ReqPlan& rp) {
     if (!cap) return;
     const ProbePlan& plan = rp.plan;
     const ProbeRequest& r = rp.pr;
+    if (static_cast<uint64_t>(r.npreds + r.nterms) * r.nsamples > kCachedProbeMaxCounts) return;
     auto put = [&](std::string&& key, uint64_t v) {
         auto it = srv.counts.find(key);
         if (it != srv.counts.end()) {
@@ -474,6 +479,7 @@ bool counts_answer(ServeState& srv, uint32_t table, const ReqPlan& rp) {
     if (!srv.cfg.probe_cache) return false;
     const ProbePlan& plan = rp.plan;
     const ProbeRequest& r = rp.pr;
+    if (static_cast<uint64_t>(r.npreds + r.nterms) * r.nsamples > kCachedProbeMaxCounts) return false;
     const uint32_t ns = r.nsamples, np = r.npreds, nt = r.nterms;
     bool want_marg = r.term_marginals != nullptr;
     for (uint32_t p = 0; p < np; ++p) want_marg = want_marg || r.preds[p].term_cnt == 2;
