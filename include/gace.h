@@ -496,7 +496,7 @@ gace_status gace_gate_eval(const gace_gate_config* cfg, const gace_gate_input* i
  * gace_stats_reset(ctx, 1) is in effect adds to a cost table that
  * gace_stats_reset does not clear (narrow launches give hbm_rate, wide ones
  * ops_rate); a rate without measurements takes its GB300 default (hbm 5e12 B/s,
- * ops 1.3e13 /s, h2d 8e10 B/s, hash 1.5e-3 ns per row and set, call 0.03 ms).
+ * ops 1.3e13 /s, h2d 2e11 B/s, hash 1.5e-3 ns per row and set, call 0.03 ms).
  * The answer reports the rates it used.  Errors: GACE_EINVAL for NULL
  * arguments, nsets = 0, hashed_sets > nsets, or a NaN / negative alt_ms.
  */
@@ -528,6 +528,17 @@ typedef struct {
 } gace_cost_answer;
 
 gace_status gace_break_even(gace_ctx* ctx, const gace_cost_query* q, gace_cost_answer* out);
+
+/*
+ * Failure detection without a fault: launches one kernel whose single
+ * device-side wait (an mbarrier phase that nothing completes) uses the same
+ * bounded wait as every pipeline, with a limit of timeout_us (1..10^7) instead
+ * of the context's.  Returns GACE_ETIMEDOUT when the wait gave up, set its
+ * status and returned, as it must; the context stays usable afterwards.
+ * GACE_EINVAL for a timeout outside its range; GACE_ECUDA if the wait did not
+ * give up.
+ */
+gace_status gace_check_wait_limit(gace_ctx* ctx, uint32_t timeout_us);
 
 /*
  * Kernel statistics of a context (tracing; the paper decomposes probe time

@@ -448,6 +448,12 @@ def gace_break_even(ctx, nrows: int, npreds: int, nsets: int = 1, hashed_sets: i
     return {k: getattr(a, k) for k, _ in _capi.gace_cost_answer._fields_ if k != "reserved"}
 
 
+def gace_check_wait_limit(ctx, timeout_us: int) -> int:
+    """Runs the bounded-wait check kernel; returns its status code
+    (GACE_ETIMEDOUT when the wait gave up as it must)."""
+    return int(lib().gace_check_wait_limit(ctx, int(timeout_us)))
+
+
 def gace_stats_reset(ctx, time_kernels: bool = False) -> None:
     check(lib().gace_stats_reset(ctx, 1 if time_kernels else 0), "gace_stats_reset")
 

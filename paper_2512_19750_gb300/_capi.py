@@ -157,6 +157,7 @@ PROTOTYPES = {
     "gace_gate_eval": (C.c_int, [C.POINTER(gace_gate_config), C.POINTER(gace_gate_input), C.c_uint32,
                                  C.POINTER(gace_gate_result)]),
     "gace_break_even": (C.c_int, [ctx_p, C.POINTER(gace_cost_query), C.POINTER(gace_cost_answer)]),
+    "gace_check_wait_limit": (C.c_int, [ctx_p, C.c_uint32]),
     "gace_stats_reset": (C.c_int, [ctx_p, C.c_uint32]),
     "gace_stats_read": (C.c_int, [ctx_p, C.POINTER(gace_kernel_stat), C.c_uint32,
                                   C.POINTER(C.c_uint32)]),

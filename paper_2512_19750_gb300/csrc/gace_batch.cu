@@ -345,10 +345,29 @@ __global__ void __launch_bounds__(256) k_copy(const CopyDesc* __restrict__ d, ui
 
 }  // namespace
 
+// One thread waits, with the context's limit, on an mbarrier phase that
+// nothing completes: the bounded wait every pipeline uses gives up, sets the
+// timeout status and returns (the failure path, exercised without a fault).
+__global__ void __launch_bounds__(32) k_wait_check(unsigned int* status, uint64_t timeout_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    const uint32_t b = smem_u32(&bar);
+    mbar_init(b, 1);
+    fence_mbar_init();
+    if (!mbar_wait_bounded(b, 0, timeout_ns)) atomicOr(status, kStatusTimeout);
+}
+
 cudaError_t copy_launch(const CopyDesc* descs, uint32_t n, int grid, cudaStream_t s) {
     k_copy<<<grid, 256, 0, s>>>(descs, n);
     return cudaGetLastError();
 }
+
+namespace host {
+cudaError_t wait_check_launch(unsigned int* status, uint64_t timeout_ns, cudaStream_t s) {
+    k_wait_check<<<1, 32, 0, s>>>(status, timeout_ns);
+    return cudaGetLastError();
+}
+}  // namespace host
 
 template <typename K>
 static cudaError_t configure_one(K kernel, int smem_optin) {

@@ -13,11 +13,12 @@ namespace {
 // Default rates, measured on GB300 with this library's kernels: a narrow
 // probe streams about 5 TB/s of referenced columns, the wide passes evaluate
 // about 1.3e13 compare operations per second, a pinned host-to-device copy
-// runs near 80 GB/s, hashing a row for a sample costs about 1.5 ps per row
+// (allocation included) runs near 200 GB/s, hashing a row for a sample costs
+// about 1.5 ps per row
 // and set, and a synchronous call's fixed cost is about 30 us.
 constexpr double kDefaultHbmRate = 5e12;
 constexpr double kDefaultOpsRate = 1.3e13;
-constexpr double kDefaultH2dRate = 8e10;
+constexpr double kDefaultH2dRate = 2e11;
 constexpr double kDefaultHashNs = 1.5e-3;
 constexpr double kDefaultCallMs = 0.03;
 
@@ -111,6 +112,24 @@ gace_status gace_break_even(gace_ctx* ctx, const gace_cost_query* q, gace_cost_a
     a.offload = a.total_ms < q->alt_ms ? 1u : 0u;
     *out = a;
     return GACE_OK;
+}
+
+gace_status gace_check_wait_limit(gace_ctx* ctx, uint32_t timeout_us) {
+    if (gace_status s = check_ctx(ctx)) return s;
+    if (timeout_us == 0 || timeout_us > 10000000u) return fail(GACE_EINVAL, "timeout_us %u outside 1..10^7", timeout_us);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    if (gace_status s = ctx->ensure_ws(256)) return s;
+    if (gace_status s = ctx->ensure_pin(256)) return s;
+    unsigned int* status = reinterpret_cast<unsigned int*>(ctx->ws);
+    cudaError_t e = cudaMemsetAsync(status, 0, 4, ctx->stream);
+    if (e == cudaSuccess) e = wait_check_launch(status, static_cast<uint64_t>(timeout_us) * 1000ull, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->pin, status, 4, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "wait check");
+    const unsigned int st = *reinterpret_cast<const unsigned int*>(ctx->pin);
+    if (st & kStatusTimeout) return fail(GACE_ETIMEDOUT, "the check's device wait gave up after %u us", timeout_us);
+    return fail(GACE_ECUDA, "the check's device wait ended without giving up");
 }
 
 }  // extern "C"

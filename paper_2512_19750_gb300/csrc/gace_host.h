@@ -424,6 +424,9 @@ struct SideWork {
 };
 // A pass skips tiles only when each spans at most this many sample blocks.
 constexpr uint64_t kSkipBlocksPerTile = 8;
+// A kernel whose one wait (on an mbarrier phase nothing completes) gives up
+// after timeout_ns and sets kStatusTimeout in *status.
+cudaError_t wait_check_launch(unsigned int* status, uint64_t timeout_ns, cudaStream_t s);
 void plan_side_stages(SideArgs& a);
 gace_status build_side(gace_ctx* ctx, const gace_join_side& js, const char* name, int extra_col, SideArgs& a,
                        std::vector<uint32_t>& pool, TableRec** tab_out, uint32_t* extra_slot, SideWork& work);
