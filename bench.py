@@ -283,9 +283,9 @@ def run_gace(args, d: Dist):
 
     import paper_2512_19750_gb300 as g
 
-    d.init("nccl")
     dev = torch.device("cuda", d.local)
-    torch.cuda.set_device(dev)
+    torch.cuda.set_device(dev)  # before the process group, so that NCCL binds this rank's GPU
+    d.init("nccl")
     peaks = load_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count or SM_COUNT_FALLBACK
     stream = torch.cuda.current_stream(dev)
