@@ -255,21 +255,37 @@ def measured_traffic(fam, rows_per_launch):
     return rec["bytes_per_row"] * rows_per_launch
 
 
-def roofline_of(stats, peaks, sms):
-    """Roofline object of the kernel family with the most device time."""
+def term_evals_per_row(preds):
+    """Term evaluations one row of the batch costs, as the measurement plan
+    counts them: 1 per EQ or RANGE term, k per IN list of k values."""
+    from workloads import IN
+
+    return sum(len(t.values) if t.op == IN else 1 for p in preds for t in p)
+
+
+def roofline_of(stats, peaks, sms, alu=None):
+    """Roofline object of the kernel family with the most device time.  For
+    the wide probe pass (integer-bound): achieved term evaluations per second
+    (alu["evals"] of them per step) against the integer lane-op rate that
+    gace_calibrate_int measured on this GPU."""
     fam, st = max(stats.items(), key=lambda kv: kv[1]["total_ms"])
     sec = st["total_ms"] / 1000.0
     rows_per_launch = st["rows"] / max(1, st["launches"])
     traffic = measured_traffic(fam, rows_per_launch)
     algo_bytes = st["bytes"] / max(1, st["launches"])
-    if fam == "probe_wide":
-        # compare operations against the INT32 lane peak: SMs x 128 lanes x max clock
-        peak = sms * 128 * peaks["sm_max_mhz"] * 1e6 / 1e12
-        achieved = st["ops"] / sec / 1e12
+    if fam == "probe_wide" and alu is not None:
+        achieved = alu["evals"] / sec / 1e12
+        peak = alu["lane_ops_per_s"] / 1e12
+        nominal = sms * 128 * peaks["sm_max_mhz"] * 1e6 / 1e12
         return fam, {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                      "frac": achieved / peak, "traffic": traffic, "algorithmic_bytes_per_launch": algo_bytes,
-                     "work": "compare ops (EQ 1, RANGE 2, IN-k k per row)",
-                     "peak_source": f"{sms} SMs x 128 INT32 lanes x {peaks['sm_max_mhz']:.0f} MHz",
+                     "work": "term evaluations (EQ 1, RANGE 1, IN-k k per row)",
+                     "peak_source": "measured: gace_calibrate_int kind 0 (32-bit xor/add lane ops) on this GPU",
+                     "lane_ops_per_sm_clk": alu["lane_ops_per_s"] / (sms * peaks["sm_max_mhz"] * 1e6),
+                     "range_tests_per_s_measured": alu["range_tests_per_s"],
+                     "frac_of_range_test_rate": alu["evals"] / sec / alu["range_tests_per_s"],
+                     "frac_of_nominal_128_lanes": achieved / nominal,
+                     "compare_ops_per_s_range_as_2": st["ops"] / sec,
                      "launches": st["launches"], "avg_launch_ms": st["total_ms"] / st["launches"]}
     achieved = st["bytes"] / sec / 1e9
     return fam, {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -323,7 +339,10 @@ def run_gace(args, d: Dist):
     ms_per_step = ms_total / args.steps
     value = d.world * n * args.steps / (ms_total / 1000.0)
     gpu_launches = sum(s["launches"] for s in stats.values())
-    fam, roof = roofline_of(stats, peaks, sms)
+    alu = {"evals": float(n) * term_evals_per_row(preds) * args.steps,
+           "lane_ops_per_s": g.gace_calibrate_int(ctx, 0, 50),
+           "range_tests_per_s": g.gace_calibrate_int(ctx, 1, 50)}
+    fam, roof = roofline_of(stats, peaks, sms, alu)
     roof["kernel"] = fam
     roof["peak_source"] = roof.get("peak_source", f"MEASURED_PEAKS.json hbm_gbs ({peaks['source']})")
     kernels = {k: {"launches": v["launches"], "total_ms": round(v["total_ms"], 3),
@@ -341,6 +360,7 @@ def run_gace(args, d: Dist):
     extras = {}
     if not args.no_extras:
         extras["single_probe"] = single_probes(g, ctx, tid, table, peaks, stream)
+        extras["plain_small"] = plain_small_leg(g, ctx, dev, peaks, stream)
         extras["stability"] = stability_leg(g, ctx, tid, table)
         extras["e2e"], extras["overhead"] = e2e_leg(g, ctx, table, preds, samples, batch, args, stream)
     g.gace_unload(ctx, tid)
@@ -371,6 +391,7 @@ def run_gace(args, d: Dist):
             "gpu_launches": gpu_launches,
             "clocks": clocks,
             "single_probe": extras.get("single_probe"),
+            "plain_small": extras.get("plain_small"),
             "join": extras.get("join"),
             "stability": extras.get("stability"),
             "overhead": extras.get("overhead"),
@@ -451,6 +472,77 @@ def single_probes(g, ctx, tid, table, peaks, stream):
         gbs = k["bytes"] / k["launches"] / (ms / 1000.0) / 1e9
         out[name] = {"kernel_ms": round(ms, 4), "rows_per_s": n / (ms / 1000.0), "gbs": gbs,
                      "frac_of_measured_hbm": gbs / peaks["hbm_gbs"]}
+    return out
+
+
+def plain_small_leg(g, ctx, dev, peaks, stream):
+    """The plain small probe: 1M rows x 4 int32 (16 MB), 64 predicates of 1-3
+    terms on the full table and a 1 % row sample (seed 42) with marginals and
+    PCS, plus HyperLogLog (p = 12) of the four columns.  The table fits in the
+    129 MB L2, so a step is latency-bound: microseconds per step (median of
+    50 after 5 warm-up, CUDA events on the library's stream around the
+    synchronous calls), and the same with a 256 MB write before each step
+    (outside the timed interval) that evicts the table from L2, for HBM bytes
+    per second."""
+    import torch
+
+    from workloads import FULL, ROWS, Sample, make_plain_small, make_predicates
+
+    t = make_plain_small(seed=1001, device=dev)
+    preds = make_predicates(t, 64, 1, 3, seed=2001)
+    samples = [Sample(FULL), Sample(ROWS, 0.01, 42)]
+    tid = g.gace_load_columns(ctx, t.columns, borrow=True)
+    batch = g.TermBatch(preds, t.dtypes)
+
+    def step():
+        g.gace_probe_batch(ctx, tid, preds, samples, t.dtypes, marginals=True, batch=batch)
+        for c in range(4):
+            g.gace_ndv(ctx, tid, c, 12, 42)
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    algo_bytes = 2 * t.nrows * 4 * 4  # the probe reads 4 columns, the 4 sketches read them again
+    out = {"workload": "1M rows x 4 int32 (c0 U[0,1e6), c1 Zipf(1.1,1e4), c2 = 7 c1 + U[0,50), c3 U[0,100)); "
+                       "64 preds of 1-3 terms x {full, rows 1 % seed 42} with marginals + PCS; HLL p=12 x 4"}
+    for mode in ("l2_resident", "l2_flushed"):
+        times = []
+        g.gace_stats_reset(ctx, time_kernels=True)
+        for i in range(55):
+            if mode == "l2_flushed":
+                flush.fill_(i & 0xFF)
+            if i == 5:
+                g.gace_stats_reset(ctx, time_kernels=True)
+            torch.cuda.synchronize(dev)
+            a.record(stream)
+            step()
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            if i >= 5:
+                times.append(a.elapsed_time(b))
+        st = g.gace_stats_read(ctx)
+        kern_us = 1000.0 * sum(v["total_ms"] for v in st.values()) / 50
+        us = 1000.0 * statistics.median(times)
+        entry = {"us_per_step": us, "us_per_probe_call": None, "kernel_us_per_step": kern_us,
+                 "kernels": {k: round(1000.0 * v["total_ms"] / 50, 2) for k, v in st.items()}}
+        if mode == "l2_flushed":
+            entry["kernel_gbs"] = algo_bytes / (kern_us * 1e-6) / 1e9
+            entry["kernel_frac_of_measured_hbm"] = entry["kernel_gbs"] / peaks["hbm_gbs"]
+        out[mode] = entry
+    # one synchronous probe call alone (no sketches), L2-resident
+    times = []
+    for i in range(55):
+        torch.cuda.synchronize(dev)
+        a.record(stream)
+        g.gace_probe_batch(ctx, tid, preds, samples, t.dtypes, marginals=True, batch=batch)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        if i >= 5:
+            times.append(a.elapsed_time(b))
+    out["l2_resident"]["us_per_probe_call"] = 1000.0 * statistics.median(times)
+    g.gace_unload(ctx, tid)
+    del flush, t
+    torch.cuda.empty_cache()
     return out
 
 
@@ -593,6 +685,22 @@ def request_bytes(tables, reqs):
     return out
 
 
+def shared_scan_bytes(tables, reqs):
+    """Algorithmic bytes of the batch when every table is scanned once for all
+    the requests on it: per table, its rows times the widths of the union of
+    the columns its requests reference."""
+    cols = {}
+    for r in reqs:
+        if r["kind"] == "probe":
+            cols.setdefault(r["table"], set()).update(term.col for p in r["preds"] for term in p)
+        elif r["kind"] == "ndv":
+            cols.setdefault(r["table"], set()).add(r["col"])
+        else:
+            for side, terms in ((r["fact"], r["fact_terms"]), (r["dim"], r["dim_terms"])):
+                cols.setdefault(side, set()).update({0} | {term.col for term in terms})
+    return sum(tables[t].nrows * sum(tables[t].columns[c].element_size() for c in cs) for t, cs in cols.items())
+
+
 def batched_leg(g, ctx, dev, args):
     """4096 mixed requests over 256 tables: one batch (persistent kernel,
     graph, autotuned chunk and grid) against one synchronous call per request
@@ -606,6 +714,7 @@ def batched_leg(g, ctx, dev, args):
                                 device=dev)
     tids = [g.gace_load_columns(ctx, t.columns, borrow=True) for t in tables]
     nbytes = sum(request_bytes(tables, reqs))
+    shared = shared_scan_bytes(tables, reqs)
     n = len(reqs)
     g.gace_tune_batch(ctx, to_gace_requests(g, tids, tables, reqs))
     breqs = g.RequestArray(to_gace_requests(g, tids, tables, reqs))  # marshalled once, run five times
@@ -624,6 +733,13 @@ def batched_leg(g, ctx, dev, args):
     zero = np.zeros(n, dtype=np.uint64)
     plain_done, plain_st = g.gace_serve_replay(ctx, to_gace_requests(g, tids, tables, reqs), zero, mode=1)
     plain_wall = float(plain_done.max()) / 1e9
+    # the plain path's device time alone: one launch sequence per request with
+    # the host's waits between requests removed (what an asynchronous plain
+    # path could reach at best)
+    g.gace_stats_reset(ctx, time_kernels=True)
+    g.gace_serve_replay(ctx, to_gace_requests(g, tids, tables, reqs), zero, mode=1)
+    plain_dev_s = sum(v["total_ms"] for v in g.gace_stats_read(ctx).values()) / 1000.0
+    g.gace_stats_reset(ctx)
     # no result caches: the warm-up run would answer the timed run's requests
     g.gace_serve_start(ctx, sketch_cache=-1, probe_cache=-1)
     g.gace_serve_replay(ctx, to_gace_requests(g, tids, tables, reqs), zero, mode=0)  # warm-up
@@ -641,9 +757,12 @@ def batched_leg(g, ctx, dev, args):
         "requests": n, "table_rows": rows, "request_bytes": nbytes,
         "batched_probes_per_s": n / wall, "batched_ms": wall * 1000.0, "batch_graph_ms": batch_ms,
         "plain_probes_per_s": n / plain_wall, "plain_ms": plain_wall * 1000.0,
+        "plain_device_only_probes_per_s": n / plain_dev_s, "plain_device_only_ms": plain_dev_s * 1000.0,
         "served_at_once_probes_per_s": n / served_wall, "served_at_once_ms": served_wall * 1000.0,
         "batched_vs_plain": plain_wall / wall,
         "batched_gbs": nbytes / wall / 1e9,
+        "shared_scan_bytes": shared,
+        "batched_gbs_shared_scan": shared / wall / 1e9,
         "all_ok": bool((plain_st == 0).all() and (served_st == 0).all()),
         "plain": "one synchronous call per request (probe / ndv / join_card) from a native loop",
     }
@@ -653,11 +772,20 @@ def served_leg(g, ctx, dev, args):
     """Open-loop Poisson arrivals of the config-4 mix over 64 tables of 1M to
     200M rows, served (continuous batching) and plain (one synchronous call
     per request in arrival order) at each rate: p50 / p99 latency and
-    throughput."""
+    throughput, in three configurations:
+      no_caches       neither side keeps anything between requests (the served
+                      form's sketch and count caches off, no resident store):
+                      continuous batching alone;
+      resident_120gb  both sides with the context's resident store (120 GB):
+                      1 % and 10 % row samples and 1 % block samples of every
+                      table materialised before the run, sketches kept as they
+                      are computed (the served form's host caches off);
+      resident_1gb    a 1 GB store, served at one rate, samples admitted on
+                      first use: admission and eviction under pressure."""
     import numpy as np
     import torch
 
-    from workloads import make_batched
+    from workloads import BLOCKS, ROWS, Sample, make_batched
 
     rates = [int(r) for r in args.serve_rates.split(",") if r]
     nmax = int(max(rates) * args.serve_window)
@@ -665,10 +793,9 @@ def served_leg(g, ctx, dev, args):
                                 nprobes=min(nmax, args.serve_cap), seed=1005, device=dev)
     tids = [g.gace_load_columns(ctx, t.columns, borrow=True) for t in tables]
     rb = np.array(request_bytes(tables, reqs), dtype=np.float64)
-    rng = np.random.default_rng(7)
     out = {"workload": "64 tables, rows log-uniform [1e6, 2e8], the config-4 request mix",
            "table_rows": sum(t.nrows for t in tables), "mean_request_bytes": float(rb.mean()),
-           "window_s": args.serve_window, "cap_requests": args.serve_cap, "rates": {}}
+           "window_s": args.serve_window, "cap_requests": args.serve_cap}
 
     def stats(arrival, done, st):
         lat = (done.astype(np.float64) - arrival.astype(np.float64)) / 1e6
@@ -679,22 +806,45 @@ def served_leg(g, ctx, dev, args):
         return {"p50_ms": p50, "p99_ms": p99, "throughput_per_s": k / (float(done.max()) / 1e9),
                 "ok": bool((st == 0).all())}
 
+    def sweep(rate_list, with_plain, label):
+        res = {}
+        rng = np.random.default_rng(7)
+        for rate in rate_list:
+            n = min(int(rate * args.serve_window), args.serve_cap, len(reqs))
+            gaps = rng.exponential(1e9 / rate, n)
+            arrival = np.cumsum(gaps).astype(np.uint64)
+            sub = reqs[:n]
+            entry = {"requests": n}
+            g.gace_serve_start(ctx, sketch_cache=-1, probe_cache=-1)
+            done, st = g.gace_serve_replay(ctx, to_gace_requests(g, tids, tables, sub), arrival, mode=0)
+            g.gace_serve_stop(ctx)
+            entry["served"] = stats(arrival, done, st)
+            if with_plain:
+                done, st = g.gace_serve_replay(ctx, to_gace_requests(g, tids, tables, sub), arrival, mode=1)
+                entry["plain"] = stats(arrival, done, st)
+            res[str(rate)] = entry
+        return res
+
     # warm-up of both paths
     warm = to_gace_requests(g, tids, tables, reqs[:64])
     g.gace_serve_replay(ctx, warm, np.zeros(len(warm), dtype=np.uint64), mode=1)
-    for rate in rates:
-        n = min(int(rate * args.serve_window), args.serve_cap, len(reqs))
-        gaps = rng.exponential(1e9 / rate, n)
-        arrival = np.cumsum(gaps).astype(np.uint64)
-        sub = reqs[:n]
-        entry = {"requests": n}
-        g.gace_serve_start(ctx)
-        done, st = g.gace_serve_replay(ctx, to_gace_requests(g, tids, tables, sub), arrival, mode=0)
-        g.gace_serve_stop(ctx)
-        entry["served"] = stats(arrival, done, st)
-        done, st = g.gace_serve_replay(ctx, to_gace_requests(g, tids, tables, sub), arrival, mode=1)
-        entry["plain"] = stats(arrival, done, st)
-        out["rates"][str(rate)] = entry
+    out["no_caches"] = sweep(rates, True, "no_caches")
+
+    g.gace_resident_configure(ctx, 120 << 30)
+    t0 = time.perf_counter()
+    for tid in tids:
+        for smp in (Sample(ROWS, 0.01, 42), Sample(ROWS, 0.1, 42), Sample(BLOCKS, 0.01, 42, 4096)):
+            g.gace_resident_prefetch(ctx, tid, smp)
+    prefetch_s = time.perf_counter() - t0
+    g.gace_serve_replay(ctx, to_gace_requests(g, tids, tables, reqs), np.zeros(len(reqs), dtype=np.uint64),
+                        mode=1)  # computes (and keeps) the sketches the mix asks for
+    out["resident_120gb"] = sweep(rates, True, "resident_120gb")
+    out["resident_120gb"]["store"] = dict(g.gace_resident_stats_read(ctx), prefetch_s=round(prefetch_s, 3))
+
+    g.gace_resident_configure(ctx, 1 << 30)
+    out["resident_1gb"] = sweep([rates[min(1, len(rates) - 1)]], False, "resident_1gb")
+    out["resident_1gb"]["store"] = g.gace_resident_stats_read(ctx)
+    g.gace_resident_configure(ctx, 0)
     for t in tids:
         g.gace_unload(ctx, t)
     del tables

@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define GACE_ABI_VERSION 2
+#define GACE_ABI_VERSION 3
 
 typedef enum {
     GACE_OK = 0,
@@ -70,6 +70,12 @@ typedef struct {
                                   workspaces); 0 = no limit */
     void* stream;              /* cudaStream_t for all work; NULL = a private
                                   non-blocking stream */
+    uint32_t max_ctas;         /* most CTAs one gace_probe_batch launch uses, to
+                                  leave SMs to other work on the GPU (0 = as
+                                  many as are resident at once); raised where a
+                                  CTA would otherwise count 2^31 rows or more
+                                  in its 32-bit counters */
+    uint32_t reserved;         /* 0 */
 } gace_config;
 
 /* One column of a table: nrows elements of dtype, densely packed. */
@@ -268,10 +274,15 @@ gace_status gace_join_card(gace_ctx* ctx, const gace_join* spec, gace_join_resul
  * word); every GPU that loads the library holds it until the process exits.
  * Every call uses all of it and clears what must start at zero, so calls that
  * overlap on the GPU (other streams or host threads) race and must be
- * serialised by the caller.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress, on the current device); make that first
- * call before any stream capture.  No cudaMalloc, cudaFree or allocating
- * library routine is called.
+ * serialised by the caller.  Each call looks up the array's device address on
+ * the current device (cudaGetSymbolAddress, which allocates nothing once the
+ * library's module is loaded there).  With CUDA's default lazy module loading,
+ * the FIRST call on each device loads the module, which may allocate and
+ * synchronise: warm the entry point up once per device before the code that
+ * must not allocate, or run with CUDA_MODULE_LOADING=EAGER.  Every call waits
+ * for its stream and copies its results to host memory, so it must never be
+ * called while a stream is being captured into a CUDA graph.  No cudaMalloc,
+ * cudaFree or allocating library routine is called.
  *   column         device pointer to nrows elements of dtype (the current device)
  *   p              4..GACE_NOALLOC_MAX_P; larger p is rejected with GACE_EINVAL
  *   stream         cudaStream_t to run on (NULL: the default stream); the call
@@ -284,6 +295,71 @@ gace_status gace_join_card(gace_ctx* ctx, const gace_join* spec, gace_join_resul
 gace_status gace_ndv_noalloc(const void* column, int32_t dtype, uint64_t nrows, uint32_t p,
                              uint64_t hash_seed, void* stream, uint8_t* registers_out,
                              double* estimate_out);
+
+/* ------------------------------------------------- resident samples and sketches */
+
+/*
+ * Materialised sample (the Measurement Engine's sampling, Section III-B, kept
+ * for the gate's repeated invocations while queries are planned, Section
+ * III-A): the rows of `sample` of table_id (GACE_ROWS or GACE_BLOCKS with
+ * 0 < rate < 1), every column, in row order, copied into a new table that the
+ * context owns (counted against the HBM budget).  A GACE_FULL probe of the new
+ * table returns exactly the counts, sample_rows, selectivities, PCS and
+ * marginals that the same probe of table_id with `sample` returns, and its
+ * row count (rows_out, may be NULL) is that sample_rows.  Two passes decide
+ * membership as the probe does (one hash per row or block); the second loads
+ * only the kept rows.  gace_unload frees the new table; unloading table_id
+ * does not.  GACE_EINVAL for another sample kind or rate, GACE_ENOMEM beyond
+ * the budget.
+ */
+gace_status gace_sample_materialize(gace_ctx* ctx, uint32_t table_id, const gace_sample* sample,
+                                    uint32_t* sample_table_out, uint64_t* rows_out);
+
+/*
+ * The resident store: samples and HyperLogLog sketches kept in device memory
+ * under a byte budget and used by every form of the calls (gace_probe_batch,
+ * gace_ndv, batched and served requests) without a change to the requests:
+ *  - a row set that is a row or block sample (0 < rate < 1) held by the store
+ *    is counted by a full scan of the resident sample (the same integers as a
+ *    scan of the base table that hashes every row).  A sample not held is
+ *    admitted (materialised) once it has been asked for admit_after times
+ *    (0 or 1: at its first use) if it fits the budget after the least recently
+ *    used entries that no request in flight is using are evicted; otherwise
+ *    (refused) the probe scans the base table;
+ *  - an NDV request whose (table, column, p, seed) sketch is held is answered
+ *    from the resident registers (2^p bytes read back); a sketch a call
+ *    computes is kept, admitted and evicted the same way.
+ * The served form rewrites a probe at submission only when all its row sets
+ * are one sample; the synchronous call splits any mix of row sets.
+ * budget_bytes = 0 turns the store off (the default) and frees its entries;
+ * so does a changed configuration.  Unloading a table drops what the store
+ * drew from it.
+ */
+#define GACE_RESIDENT_SAMPLES 1u
+#define GACE_RESIDENT_SKETCHES 2u
+typedef struct {
+    uint64_t budget_bytes;  /* device bytes for resident samples and sketches; 0 = off */
+    uint32_t admit_after;   /* uses of a sample before it is materialised (0 or 1: the first) */
+    uint32_t flags;         /* GACE_RESIDENT_SAMPLES | GACE_RESIDENT_SKETCHES; 0 = both */
+} gace_resident_config;
+
+typedef struct {
+    uint64_t budget_bytes, used_bytes;
+    uint64_t samples, sketches;          /* entries held */
+    uint64_t sample_hits, sample_misses; /* row sets counted on / not on a resident sample */
+    uint64_t admitted, refused, evicted; /* samples materialised into the store, refused, evicted */
+    uint64_t sketch_hits, sketch_misses, sketch_evicted;
+} gace_resident_stats;
+
+gace_status gace_resident_configure(gace_ctx* ctx, const gace_resident_config* cfg);
+
+/* Materialises a sample into the store now (admission and eviction as above);
+ * GACE_ENOMEM when it cannot fit, GACE_EINVAL when the store is off or the
+ * sample is not a row or block sample with 0 < rate < 1.  A sample already
+ * held is only refreshed. */
+gace_status gace_resident_prefetch(gace_ctx* ctx, uint32_t table_id, const gace_sample* sample);
+
+gace_status gace_resident_stats_read(gace_ctx* ctx, gace_resident_stats* out);
 
 /* ------------------------------------------------------------ batched form */
 
@@ -539,6 +615,23 @@ gace_status gace_break_even(gace_ctx* ctx, const gace_cost_query* q, gace_cost_a
  * give up.
  */
 gace_status gace_check_wait_limit(gace_ctx* ctx, uint32_t timeout_us);
+
+/*
+ * Roofline calibration (a measurement of the GPU; the paper has no counterpart):
+ * the rate at which this GPU retires simple 32-bit integer operations, the
+ * denominator of the integer-bound probe kernels' roofline.
+ *   kind 0  independent chains of alternating 32-bit xor and add (two
+ *           operations per step that no single instruction fuses): integer
+ *           lane operations per second;
+ *   kind 1  32-bit range tests (x - lo) <= span whose outcomes are added to
+ *           counts, one operation per test: the best rate of the simplest
+ *           term evaluation.
+ * Every SM runs as many 256-thread CTAs as fit; the launch is grown until it
+ * lasts about ms milliseconds (1..1000), then timed three times with CUDA
+ * events on the context stream; *ops_per_s receives the best.  GACE_EINVAL for
+ * another kind, ms outside its range or a NULL output.
+ */
+gace_status gace_calibrate_int(gace_ctx* ctx, uint32_t kind, uint32_t ms, double* ops_per_s);
 
 /*
  * Kernel statistics of a context (tracing; the paper decomposes probe time

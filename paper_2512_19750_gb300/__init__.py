@@ -95,8 +95,8 @@ def gace_abi_version() -> int:
 
 
 def gace_create(device: int = 0, stream=None, hbm_budget_bytes: int = 0,
-                wait_timeout_ms: int = 0) -> int:
-    cfg = _capi.gace_config(device, wait_timeout_ms, hbm_budget_bytes, _stream_handle(stream))
+                wait_timeout_ms: int = 0, max_ctas: int = 0) -> int:
+    cfg = _capi.gace_config(device, wait_timeout_ms, hbm_budget_bytes, _stream_handle(stream), max_ctas, 0)
     out = C.c_void_p()
     check(lib().gace_create(C.byref(out), C.byref(cfg)), "gace_create")
     return out.value
@@ -222,6 +222,40 @@ def gace_join_card(ctx, fact: JoinSideSpec, dim: JoinSideSpec, key_domain: int,
     check(lib().gace_join_card(ctx, C.byref(spec), C.byref(out)), "gace_join_card")
     return {"card": int(out.card), "fact_rows": int(out.fact_rows), "dim_rows": int(out.dim_rows),
             "dim2_rows": int(out.dim2_rows)}
+
+
+# ----------------------------------------------------------------- resident samples and sketches
+
+def gace_sample_materialize(ctx, table_id: int, sample):
+    """(sample table id, its rows): the rows of a row or block sample of a
+    table, every column, in row order, as a new table of the context."""
+    out = C.c_uint32()
+    rows = C.c_uint64()
+    smp = _samples([sample])
+    check(lib().gace_sample_materialize(ctx, table_id, smp, C.byref(out), C.byref(rows)), "gace_sample_materialize")
+    return int(out.value), int(rows.value)
+
+
+def gace_resident_configure(ctx, budget_bytes: int, admit_after: int = 0, samples: bool = True,
+                            sketches: bool = True) -> None:
+    """Turns the resident store of samples and sketches on (budget_bytes > 0)
+    or off (0)."""
+    flags = (_capi.GACE_RESIDENT_SAMPLES if samples else 0) | (_capi.GACE_RESIDENT_SKETCHES if sketches else 0)
+    if budget_bytes and not flags:
+        raise ValueError("a resident store keeps samples, sketches or both")
+    cfg = _capi.gace_resident_config(int(budget_bytes), int(admit_after), flags)
+    check(lib().gace_resident_configure(ctx, C.byref(cfg)), "gace_resident_configure")
+
+
+def gace_resident_prefetch(ctx, table_id: int, sample) -> None:
+    """Materialises a sample into the resident store now."""
+    check(lib().gace_resident_prefetch(ctx, table_id, _samples([sample])), "gace_resident_prefetch")
+
+
+def gace_resident_stats_read(ctx) -> dict:
+    st = _capi.gace_resident_stats()
+    check(lib().gace_resident_stats_read(ctx, C.byref(st)), "gace_resident_stats_read")
+    return {k: int(getattr(st, k)) for k, _ in _capi.gace_resident_stats._fields_}
 
 
 # ----------------------------------------------------------------- batched form
@@ -452,6 +486,14 @@ def gace_check_wait_limit(ctx, timeout_us: int) -> int:
     """Runs the bounded-wait check kernel; returns its status code
     (GACE_ETIMEDOUT when the wait gave up as it must)."""
     return int(lib().gace_check_wait_limit(ctx, int(timeout_us)))
+
+
+def gace_calibrate_int(ctx, kind: int = 0, ms: int = 50) -> float:
+    """Integer operations per second this GPU retires (kind 0: xor/add lane
+    operations; kind 1: 32-bit range tests), timed on the context stream."""
+    out = C.c_double()
+    check(lib().gace_calibrate_int(ctx, kind, ms, C.byref(out)), "gace_calibrate_int")
+    return float(out.value)
 
 
 def gace_stats_reset(ctx, time_kernels: bool = False) -> None:

@@ -27,7 +27,8 @@ class gace_scalar(C.Union):
 
 class gace_config(C.Structure):
     _fields_ = [("device", C.c_int32), ("wait_timeout_ms", C.c_uint32),
-                ("hbm_budget_bytes", C.c_uint64), ("stream", C.c_void_p)]
+                ("hbm_budget_bytes", C.c_uint64), ("stream", C.c_void_p), ("max_ctas", C.c_uint32),
+                ("reserved", C.c_uint32)]
 
 
 class gace_column(C.Structure):
@@ -125,6 +126,17 @@ class gace_cost_answer(C.Structure):
 
 
 GACE_RISK_DRIFT, GACE_RISK_SELECTIVITY, GACE_RISK_CORRELATION = 1, 2, 4
+GACE_RESIDENT_SAMPLES, GACE_RESIDENT_SKETCHES = 1, 2
+
+
+class gace_resident_config(C.Structure):
+    _fields_ = [("budget_bytes", C.c_uint64), ("admit_after", C.c_uint32), ("flags", C.c_uint32)]
+
+
+class gace_resident_stats(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in (
+        "budget_bytes", "used_bytes", "samples", "sketches", "sample_hits", "sample_misses", "admitted",
+        "refused", "evicted", "sketch_hits", "sketch_misses", "sketch_evicted")]
 
 ctx_p = C.c_void_p
 
@@ -144,6 +156,11 @@ PROTOTYPES = {
     "gace_join_card": (C.c_int, [ctx_p, C.POINTER(gace_join), C.POINTER(gace_join_result)]),
     "gace_ndv_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_uint64, C.c_uint32, C.c_uint64,
                                    C.c_void_p, C.POINTER(C.c_uint8), C.POINTER(C.c_double)]),
+    "gace_sample_materialize": (C.c_int, [ctx_p, C.c_uint32, C.POINTER(gace_sample), C.POINTER(C.c_uint32),
+                                          C.POINTER(C.c_uint64)]),
+    "gace_resident_configure": (C.c_int, [ctx_p, C.POINTER(gace_resident_config)]),
+    "gace_resident_prefetch": (C.c_int, [ctx_p, C.c_uint32, C.POINTER(gace_sample)]),
+    "gace_resident_stats_read": (C.c_int, [ctx_p, C.POINTER(gace_resident_stats)]),
     "gace_run_batch": (C.c_int, [ctx_p, C.POINTER(gace_request), C.c_uint32, C.POINTER(C.c_int)]),
     "gace_tune_batch": (C.c_int, [ctx_p, C.POINTER(gace_request), C.c_uint32]),
     "gace_tune_save": (C.c_int, [ctx_p, C.c_char_p]),
@@ -158,6 +175,7 @@ PROTOTYPES = {
                                  C.POINTER(gace_gate_result)]),
     "gace_break_even": (C.c_int, [ctx_p, C.POINTER(gace_cost_query), C.POINTER(gace_cost_answer)]),
     "gace_check_wait_limit": (C.c_int, [ctx_p, C.c_uint32]),
+    "gace_calibrate_int": (C.c_int, [ctx_p, C.c_uint32, C.c_uint32, C.POINTER(C.c_double)]),
     "gace_stats_reset": (C.c_int, [ctx_p, C.c_uint32]),
     "gace_stats_read": (C.c_int, [ctx_p, C.POINTER(gace_kernel_stat), C.c_uint32,
                                   C.POINTER(C.c_uint32)]),

@@ -14,8 +14,8 @@ LIB = os.path.join(HERE, "libgace.so")
 OBJDIR = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["gace_probe.cu", "gace_hll_join.cu", "gace_noalloc.cu", "gace_batch.cu"]
-HOST_SOURCES = ["gace_capi.cpp", "gace_batch_host.cpp", "gace_serve.cpp", "gace_gate.cpp"]
+CUDA_SOURCES = ["gace_probe.cu", "gace_hll_join.cu", "gace_noalloc.cu", "gace_batch.cu", "gace_sample.cu"]
+HOST_SOURCES = ["gace_capi.cpp", "gace_batch_host.cpp", "gace_serve.cpp", "gace_gate.cpp", "gace_resident.cpp"]
 
 
 def cuda_home() -> str:

@@ -357,6 +357,72 @@ __global__ void __launch_bounds__(32) k_wait_check(unsigned int* status, uint64_
     if (!mbar_wait_bounded(b, 0, timeout_ns)) atomicOr(status, kStatusTimeout);
 }
 
+// Roofline calibration of the integer pipes.  kind 0: eight independent chains
+// per thread of alternating 32-bit xor and add with run-time constants (no
+// single instruction does both, and neither folds across the other), two
+// operations per step; kind 1: 32-bit range tests (x - lo) <= span, 16
+// constants against eight values, each test's outcome added to a per-value
+// count (one operation per test: the unit in which a range evaluated by
+// compare is counted), the values perturbed once per iteration so that no
+// test is loop-invariant.  The results feed one conditional store so that
+// nothing is dead.
+template <int KIND>
+__global__ void __launch_bounds__(256, 8) k_int_peak(uint32_t iters, uint32_t k1, uint32_t k2, uint32_t* sink) {
+    uint32_t x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = threadIdx.x * (2u * i + 1u) + blockIdx.x * 7919u + i;
+    if (KIND == 0) {
+        for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    x[i] ^= k1;
+                    x[i] += k2;
+                }
+            }
+        }
+    } else {
+        uint32_t c[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) c[i] = 0;
+        for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const uint32_t lo = k1 + static_cast<uint32_t>(u) * k2;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) c[i] += (x[i] - lo) <= k2 ? 1u : 0u;
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) x[i] ^= c[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] += c[i];
+    }
+    uint32_t r = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) r ^= x[i];
+    if (r == 0x9E3779B9u) sink[0] = r;
+}
+
+cudaError_t int_peak_launch(int kind, uint32_t iters, int grid, uint32_t* sink, cudaStream_t s) {
+    if (kind == 0)
+        k_int_peak<0><<<grid, 256, 0, s>>>(iters, 0x5bd1e995u, 0x68e31da4u, sink);
+    else
+        k_int_peak<1><<<grid, 256, 0, s>>>(iters, 0x1000u, 0x40000u, sink);
+    return cudaGetLastError();
+}
+
+// Operations one thread of k_int_peak performs per iteration.
+uint64_t int_peak_ops_per_iter(int kind) { return kind == 0 ? 16u * 8u * 2u : 16u * 8u; }
+
+int int_peak_occupancy(int kind) {
+    int n = 0;
+    cudaError_t e = kind == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_int_peak<0>, 256, 0)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_int_peak<1>, 256, 0);
+    return e == cudaSuccess ? n : 0;
+}
+
 cudaError_t copy_launch(const CopyDesc* descs, uint32_t n, int grid, cudaStream_t s) {
     k_copy<<<grid, 256, 0, s>>>(descs, n);
     return cudaGetLastError();

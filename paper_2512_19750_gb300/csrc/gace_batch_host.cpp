@@ -820,14 +820,24 @@ std::pair<int, int> shape_key(const std::vector<ReqPlan>& rps) {
     return {log2_bucket(njobs), log2_bucket(units)};
 }
 
-gace_status report(const std::vector<ReqPlan>& rps, uint32_t n, gace_status* statuses) {
+
+// Statuses of the caller's requests (answered ones succeeded), the sketches
+// the batch computed kept; the first failure's status and message.
+gace_status report_resident(gace_ctx* ctx, const ResidentBatch& rb, const std::vector<ReqPlan>& rps, uint32_t n_in,
+                            gace_status* statuses) {
+    const uint32_t n = static_cast<uint32_t>(rb.reqs.size());
+    std::vector<gace_status> st(n);
+    for (uint32_t k = 0; k < n; ++k) st[k] = rps[k].status;
+    rb.keep_sketches(ctx, st);
+    if (statuses)
+        for (uint32_t i = 0; i < n_in; ++i) statuses[i] = GACE_OK;
     gace_status first = GACE_OK;
     std::string msg;
-    for (size_t i = 0; i < n; ++i) {
-        if (statuses) statuses[i] = rps[i].status;
-        if (first == GACE_OK && rps[i].status != GACE_OK) {
-            first = rps[i].status;
-            msg = "request " + std::to_string(i) + ": " + rps[i].error;
+    for (uint32_t k = 0; k < n; ++k) {
+        if (statuses) statuses[rb.index[k]] = st[k];
+        if (first == GACE_OK && st[k] != GACE_OK) {
+            first = st[k];
+            msg = "request " + std::to_string(rb.index[k]) + ": " + rps[k].error;
         }
     }
     if (first != GACE_OK) set_last_error_message(msg.c_str());
@@ -852,11 +862,15 @@ gace_status batch_prologue(gace_ctx* ctx, const gace_request* reqs, uint32_t n) 
 
 extern "C" {
 
-gace_status gace_run_batch(gace_ctx* ctx, const gace_request* reqs, uint32_t n, gace_status* statuses) {
+gace_status gace_run_batch(gace_ctx* ctx, const gace_request* in, uint32_t n_in, gace_status* statuses) {
     if (!ctx) return fail(GACE_EINVAL, "context is NULL");
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
-    if (gace_status s = batch_prologue(ctx, reqs, n)) return s;
+    if (gace_status s = batch_prologue(ctx, in, n_in)) return s;
+    ResidentBatch rb;
+    rb.build(ctx, in, n_in);
+    const gace_request* reqs = rb.reqs.data();
+    const uint32_t n = static_cast<uint32_t>(rb.reqs.size());
     std::vector<ReqPlan> rps;
     std::vector<std::unique_ptr<FusedProbe>> fused;
     compile_all(ctx, reqs, n, rps, fused);
@@ -872,14 +886,18 @@ gace_status gace_run_batch(gace_ctx* ctx, const gace_request* reqs, uint32_t n, 
     if (gace_status st = exec_batch(ctx, br, true)) return st;
     finish_batch(ctx, rps, br);
     finish_fused(rps, fused, n);
-    return report(rps, n, statuses);
+    return report_resident(ctx, rb, rps, n_in, statuses);
 }
 
-gace_status gace_tune_batch(gace_ctx* ctx, const gace_request* reqs, uint32_t n) {
+gace_status gace_tune_batch(gace_ctx* ctx, const gace_request* in, uint32_t n_in) {
     if (!ctx) return fail(GACE_EINVAL, "context is NULL");
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
-    if (gace_status s = batch_prologue(ctx, reqs, n)) return s;
+    if (gace_status s = batch_prologue(ctx, in, n_in)) return s;
+    ResidentBatch rb;
+    rb.build(ctx, in, n_in);
+    const gace_request* reqs = rb.reqs.data();
+    const uint32_t n = static_cast<uint32_t>(rb.reqs.size());
     std::vector<ReqPlan> rps;
     std::vector<std::unique_ptr<FusedProbe>> fused;
     compile_all(ctx, reqs, n, rps, fused);
@@ -922,7 +940,7 @@ gace_status gace_tune_batch(gace_ctx* ctx, const gace_request* reqs, uint32_t n)
     if (gace_status st = exec_batch(ctx, br, false)) return st;
     finish_batch(ctx, rps, br);
     finish_fused(rps, fused, n);
-    return report(rps, n, nullptr);
+    return report_resident(ctx, rb, rps, n_in, nullptr);
 }
 
 gace_status gace_tune_save(gace_ctx* ctx, const char* path) {

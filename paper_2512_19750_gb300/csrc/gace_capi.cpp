@@ -594,18 +594,26 @@ double hll_estimate_host(const uint8_t* regs, uint32_t p) {
     const uint64_t m = 1ull << p;
     uint64_t hist[66] = {0};
     for (uint64_t j = 0; j < m; ++j) hist[regs[j] < 65 ? regs[j] : 65]++;
-    const double dm = static_cast<double>(m);
+    return hll_estimate_from_hist(hist, p);
+}
+
+}  // namespace host
+
+double hll_estimate_from_hist(const uint64_t (&c)[66], uint32_t p) {
+    const double dm = static_cast<double>(1ull << p);
     double alpha;
-    if (m == 16) alpha = 0.673;
-    else if (m == 32) alpha = 0.697;
-    else if (m == 64) alpha = 0.709;
+    if (p == 4) alpha = 0.673;
+    else if (p == 5) alpha = 0.697;
+    else if (p == 6) alpha = 0.709;
     else alpha = 0.7213 / (1.0 + 1.079 / dm);
     double z = 0.0;
-    for (int k = 0; k <= 65; ++k) z += static_cast<double>(hist[k]) * std::ldexp(1.0, -k);
+    for (int k = 0; k <= 65; ++k) z += static_cast<double>(c[k]) * std::ldexp(1.0, -k);
     double e = alpha * dm * dm / z;
-    if (e <= 2.5 * dm && hist[0] > 0) e = dm * std::log(dm / static_cast<double>(hist[0]));
+    if (e <= 2.5 * dm && c[0] > 0) e = dm * std::log(dm / static_cast<double>(c[0]));
     return e;
 }
+
+namespace host {
 
 // Staged side scans (k_side_staged) stream tiles of about 32 KB per stage
 // through two or three stages (at most 64 KB per CTA, three CTAs per SM), like
@@ -1039,6 +1047,69 @@ void assemble_probe(const ProbePlan& plan, const ProbeRequest& r,
         marg_of);
 }
 
+gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts) {
+    // workspace: status | per pass of every part: inputs, outputs
+    Ws ws;
+    const uint64_t status_off = ws.take(256);
+    bool any_pass = false;
+    for (auto& pp : parts)
+        for (auto& ps : pp.plan.passes) {
+            ps.in_off = ws.take(ps.in_bytes);
+            ps.out_off = ws.take(ps.out_bytes);
+            any_pass = true;
+        }
+    if (gace_status st = ctx->ensure_ws(ws.off)) return st;
+    if (gace_status st = ctx->ensure_pin(ws.off + 256)) return st;
+
+    // stage inputs into pinned memory, one H2D copy, zero outputs
+    unsigned char* pin = ctx->pin;
+    unsigned char* dws = ctx->ws;
+    unsigned int* dstatus = reinterpret_cast<unsigned int*>(dws + status_off);
+    for (auto& pp : parts)
+        for (auto& ps : pp.plan.passes) stage_pass(ps, pin, dws, dstatus);
+    if (any_pass) {
+        const uint64_t first_in = status_off + 256;
+        CK(cudaMemcpyAsync(dws + first_in, pin + first_in, ws.off - first_in, cudaMemcpyHostToDevice, ctx->stream));
+        for (auto& pp : parts)
+            for (auto& ps : pp.plan.passes) CK(cudaMemsetAsync(dws + ps.out_off, 0, ps.out_bytes, ctx->stream));
+    }
+    CK(cudaMemsetAsync(dws + status_off, 0, 256, ctx->stream));
+    for (auto& pp : parts) {
+        const TableRec* tab = pp.tab;
+        for (auto& ps : pp.plan.passes) {
+            const int occ = probe_occupancy(ps.args);
+            if (occ < 1)
+                return fail(GACE_ECUDA, "probe kernel cannot be resident with %u bytes of shared memory",
+                            ps.args.smem_bytes);
+            // work units: tiles (narrow) or 8-slice warp sweeps (wide)
+            const uint64_t unit_rows =
+                ps.args.narrow ? ps.args.tile_rows : static_cast<uint64_t>(kSliceRows) * kProbeWarps;
+            const uint64_t units = (tab->nrows + unit_rows - 1) / unit_rows;
+            uint64_t grid = static_cast<uint64_t>(ctx->sms) * occ;
+            if (ctx->max_ctas && grid > ctx->max_ctas) grid = ctx->max_ctas;
+            if (grid > units) grid = units;
+            if (grid < 1) grid = 1;
+            // each CTA keeps 32-bit row counters
+            while ((units + grid - 1) / grid * unit_rows >= (1ull << 31)) grid *= 2;
+            if (grid > 0x7FFFFFFFull) return fail(GACE_EINVAL, "table too large for one probe grid");
+            const uint64_t n = tab->nrows;
+            CK(ctx->traced(ps.args.narrow ? "probe_narrow" : "probe_wide", n, n * ps.rowbytes, n * ps.ops_per_row,
+                           [&] { return probe_launch(ps.args, static_cast<int>(grid), ctx->stream); }));
+        }
+    }
+    const uint64_t rb_hi = any_pass ? ws.off : status_off + 256;
+    CK(cudaMemcpyAsync(pin + status_off, dws + status_off, rb_hi - status_off, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->collect();
+    if (gace_status st = read_status(ctx, *reinterpret_cast<unsigned int*>(pin + status_off))) return st;
+    for (auto& pp : parts) {
+        std::vector<const unsigned long long*> outs;
+        for (auto& ps : pp.plan.passes) outs.push_back(reinterpret_cast<const unsigned long long*>(pin + ps.out_off));
+        assemble_probe(pp.plan, pp.r, outs);
+    }
+    return GACE_OK;
+}
+
 }  // namespace host
 }  // namespace gace
 
@@ -1078,6 +1149,7 @@ gace_status gace_create(gace_ctx** out, const gace_config* cfg) {
     gace_ctx* ctx = new gace_ctx();
     ctx->device = c.device;
     ctx->budget = c.hbm_budget_bytes;
+    ctx->max_ctas = c.max_ctas;
     if (c.wait_timeout_ms) ctx->timeout_ns = static_cast<uint64_t>(c.wait_timeout_ms) * 1000000ull;
     auto bail = [&](gace_status s) {
         gace_destroy(ctx);
@@ -1109,10 +1181,11 @@ gace_status gace_destroy(gace_ctx* ctx) {
     serve_shutdown(ctx);
     {
         DeviceGuard g(ctx->device);
-        if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-        for (auto& kv : ctx->tables)
-            for (auto& c : kv.second.cols)
-                if (c.owned && c.dptr) cudaFree(c.dptr);
+        if (ctx->stream) {
+            resident_clear(ctx);
+            for (auto& kv : ctx->tables) free_table_columns(ctx, kv.second);
+            cudaStreamSynchronize(ctx->stream);
+        }
         if (ctx->ws) cudaFree(ctx->ws);
         if (ctx->pin) cudaFreeHost(ctx->pin);
         if (ctx->d_status) cudaFree(ctx->d_status);
@@ -1167,10 +1240,11 @@ gace_status gace_load_columns(gace_ctx* ctx, uint64_t nrows, uint32_t ncols, con
             r.dptr = const_cast<void*>(cols[c].data);
         } else {
             const uint64_t alloc = round_up(bytes + 16, 256);
-            cudaError_t e = cudaMalloc(&r.dptr, alloc);
+            // stream-ordered: no device-wide synchronisation
+            cudaError_t e = cudaMallocAsync(&r.dptr, alloc, ctx->stream);
             if (e != cudaSuccess) {
-                for (auto& x : tab.cols) cudaFree(x.dptr);
-                return fail(GACE_ENOMEM, "cudaMalloc(%llu) for column %u: %s", (unsigned long long)alloc, c,
+                for (auto& x : tab.cols) cudaFreeAsync(x.dptr, ctx->stream);
+                return fail(GACE_ENOMEM, "cudaMallocAsync(%llu) for column %u: %s", (unsigned long long)alloc, c,
                             cudaGetErrorString(e));
             }
             r.owned = true;
@@ -1180,8 +1254,8 @@ gace_status gace_load_columns(gace_ctx* ctx, uint64_t nrows, uint32_t ncols, con
                                     cols[c].on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                     ctx->stream);
                 if (e != cudaSuccess) {
-                    cudaFree(r.dptr);
-                    for (auto& x : tab.cols) cudaFree(x.dptr);
+                    cudaFreeAsync(r.dptr, ctx->stream);
+                    for (auto& x : tab.cols) cudaFreeAsync(x.dptr, ctx->stream);
                     return cuda_fail(e, "cudaMemcpyAsync(column)");
                 }
             }
@@ -1191,7 +1265,7 @@ gace_status gace_load_columns(gace_ctx* ctx, uint64_t nrows, uint32_t ncols, con
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
         for (auto& x : tab.cols)
-            if (x.owned) cudaFree(x.dptr);
+            if (x.owned) cudaFreeAsync(x.dptr, ctx->stream);
         return cuda_fail(e, "cudaStreamSynchronize(load)");
     }
     ctx->used += tab.owned_bytes;
@@ -1208,10 +1282,21 @@ gace_status gace_unload(gace_ctx* ctx, uint32_t table_id) {
     auto it = ctx->tables.find(table_id);
     if (it == ctx->tables.end()) return fail(GACE_ENOTFOUND, "table %u is not loaded", table_id);
     if (gace_status s = serve_forget_table(ctx, table_id)) return s;
-    cudaStreamSynchronize(ctx->stream);
-    for (auto& c : it->second.cols)
-        if (c.owned && c.dptr) cudaFree(c.dptr);
-    ctx->used -= it->second.owned_bytes;
+    if (resident_samples_busy(ctx, table_id))
+        return fail(GACE_EBUSY, "served requests read a resident sample of table %u", table_id);
+    if (it->second.in_store) {  // a resident sample unloaded by hand leaves the store
+        ResidentStore& R = ctx->resident;
+        for (auto e = R.samples.begin(); e != R.samples.end(); ++e)
+            if (e->second.sample_table == table_id) {
+                R.used -= e->second.bytes;
+                R.samples.erase(e);
+                break;
+            }
+    }
+    resident_forget_table(ctx, table_id);
+    // stream-ordered frees: after the work already queued on the context stream
+    it = ctx->tables.find(table_id);
+    free_table_columns(ctx, it->second);
     ctx->tables.erase(it);
     return GACE_OK;
 }
@@ -1237,57 +1322,80 @@ gace_status gace_probe_batch(gace_ctx* ctx, uint32_t table_id, const gace_sample
     TableRec* tab = find_table(ctx, table_id);
     if (!tab) return fail(GACE_ENOTFOUND, "table %u is not loaded", table_id);
     DeviceGuard g(ctx->device);
-    ProbePlan plan;
-    if (gace_status st = plan_probe(ctx, *tab, r, false, plan)) return st;
-    std::vector<Pass>& passes = plan.passes;
-
-    // workspace: status | per pass: inputs, outputs
-    Ws ws;
-    const uint64_t status_off = ws.take(256);
-    for (auto& ps : passes) {
-        ps.in_off = ws.take(ps.in_bytes);
-        ps.out_off = ws.take(ps.out_bytes);
+    for (uint32_t s = 0; s < nsamples; ++s) {
+        SetDesc d;
+        if (gace_status st = make_set(samples[s], d)) return st;
     }
-    if (gace_status st = ctx->ensure_ws(ws.off)) return st;
-    if (gace_status st = ctx->ensure_pin(ws.off + 256)) return st;
-
-    // stage inputs into pinned memory, one H2D copy, zero outputs
-    unsigned char* pin = ctx->pin;
-    unsigned char* dws = ctx->ws;
-    unsigned int* dstatus = reinterpret_cast<unsigned int*>(dws + status_off);
-    for (auto& ps : passes) stage_pass(ps, pin, dws, dstatus);
-    if (!passes.empty()) {
-        const uint64_t first_in = passes.front().in_off;
-        CK(cudaMemcpyAsync(dws + first_in, pin + first_in, ws.off - first_in, cudaMemcpyHostToDevice,
-                           ctx->stream));
-        for (auto& ps : passes) CK(cudaMemsetAsync(dws + ps.out_off, 0, ps.out_bytes, ctx->stream));
+    // Row sets held by the resident store are counted by full scans of their
+    // resident samples; the others on the base table.
+    std::vector<uint32_t> where(nsamples, 0), pinned;
+    bool any = false;
+    if (ctx->resident.samples_on()) {
+        for (uint32_t s = 0; s < nsamples; ++s) {
+            SetDesc d;
+            make_set(samples[s], d);
+            where[s] = resident_sample(ctx, table_id, d, true, pinned);
+            any = any || where[s] != 0;
+        }
     }
-    CK(cudaMemsetAsync(dws + status_off, 0, 256, ctx->stream));
-    for (auto& ps : passes) {
-        const int occ = probe_occupancy(ps.args);
-        if (occ < 1) return fail(GACE_ECUDA, "probe kernel cannot be resident with %u bytes of shared memory",
-                                 ps.args.smem_bytes);
-        // work units: tiles (narrow) or 8-slice warp sweeps (wide)
-        const uint64_t unit_rows = ps.args.narrow ? ps.args.tile_rows : static_cast<uint64_t>(kSliceRows) * kProbeWarps;
-        const uint64_t units = (tab->nrows + unit_rows - 1) / unit_rows;
-        uint64_t grid = static_cast<uint64_t>(ctx->sms) * occ;
-        if (grid > units) grid = units;
-        if (grid < 1) grid = 1;
-        // each CTA keeps 32-bit row counters
-        while ((units + grid - 1) / grid * unit_rows >= (1ull << 31)) grid *= 2;
-        if (grid > 0x7FFFFFFFull) return fail(GACE_EINVAL, "table too large for one probe grid");
-        const uint64_t n = tab->nrows;
-        CK(ctx->traced(ps.args.narrow ? "probe_narrow" : "probe_wide", n, n * ps.rowbytes, n * ps.ops_per_row,
-                       [&] { return probe_launch(ps.args, static_cast<int>(grid), ctx->stream); }));
+    std::vector<PlannedProbe> parts;
+    if (!any) {
+        parts.emplace_back();
+        parts.back().tab = tab;
+        parts.back().r = r;
+        if (gace_status st = plan_probe(ctx, *tab, r, false, parts.back().plan)) return st;
+        return run_planned(ctx, parts);
     }
-    const uint64_t rb_hi = passes.empty() ? status_off + 256 : ws.off;
-    CK(cudaMemcpyAsync(pin + status_off, dws + status_off, rb_hi - status_off, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    ctx->collect();
-    if (gace_status st = read_status(ctx, *reinterpret_cast<unsigned int*>(pin + status_off))) return st;
-    std::vector<const unsigned long long*> outs;
-    for (auto& ps : passes) outs.push_back(reinterpret_cast<const unsigned long long*>(pin + ps.out_off));
-    assemble_probe(plan, r, outs);
+    // one part per table: the base table with the samples that are not
+    // resident, and each resident sample table with one full scan; each part
+    // writes its own results, scattered to the caller's rows afterwards
+    static const gace_sample kFull{GACE_FULL, 0, 1.0, 0};
+    std::vector<uint32_t> order;  // the tables of the parts, base first
+    std::vector<std::vector<uint32_t>> members;
+    auto part_of = [&](uint32_t t) {
+        for (size_t i = 0; i < order.size(); ++i)
+            if (order[i] == t) return i;
+        order.push_back(t);
+        members.emplace_back();
+        return order.size() - 1;
+    };
+    for (uint32_t s = 0; s < nsamples; ++s) members[part_of(where[s] ? where[s] : table_id)].push_back(s);
+    parts.resize(order.size());
+    std::vector<std::vector<gace_sample>> psamples(order.size());
+    std::vector<std::vector<gace_pred_result>> pres(order.size());
+    std::vector<std::vector<uint64_t>> pmarg(order.size());
+    for (size_t i = 0; i < order.size(); ++i) {
+        PlannedProbe& pp = parts[i];
+        const bool resident = order[i] != table_id;
+        pp.tab = find_table(ctx, order[i]);
+        if (resident)
+            psamples[i].push_back(kFull);  // identical samples of one part share its counts
+        else
+            for (uint32_t s : members[i]) psamples[i].push_back(samples[s]);
+        const uint32_t ns = static_cast<uint32_t>(psamples[i].size());
+        pres[i].resize(static_cast<size_t>(ns) * npreds);
+        if (term_marginals) pmarg[i].resize(static_cast<size_t>(ns) * nterms);
+        pp.r = r;
+        pp.r.samples = psamples[i].data();
+        pp.r.nsamples = ns;
+        pp.r.results = npreds ? pres[i].data() : nullptr;
+        pp.r.term_marginals = term_marginals ? pmarg[i].data() : nullptr;
+        if (gace_status st = plan_probe(ctx, *pp.tab, pp.r, false, pp.plan)) return st;
+    }
+    if (gace_status st = run_planned(ctx, parts)) return st;
+    for (size_t i = 0; i < order.size(); ++i) {
+        const bool resident = order[i] != table_id;
+        for (size_t k = 0; k < members[i].size(); ++k) {
+            const uint32_t s = members[i][k];
+            const size_t from = resident ? 0 : k;
+            if (npreds)
+                memcpy(results + static_cast<size_t>(s) * npreds, pres[i].data() + from * npreds,
+                       npreds * sizeof(gace_pred_result));
+            if (term_marginals && nterms)
+                memcpy(term_marginals + static_cast<size_t>(s) * nterms, pmarg[i].data() + from * nterms,
+                       nterms * sizeof(uint64_t));
+        }
+    }
     return GACE_OK;
 }
 
@@ -1304,6 +1412,14 @@ gace_status gace_ndv(gace_ctx* ctx, uint32_t table_id, uint32_t col, uint32_t p,
     if (col >= tab->cols.size()) return fail(GACE_EINVAL, "column %u of a %zu-column table", col, tab->cols.size());
     DeviceGuard g(ctx->device);
     const uint64_t m = 1ull << p;
+    {  // a resident sketch of this column, p and seed answers without a scan
+        std::vector<uint8_t> regs(m);
+        if (resident_sketch_get(ctx, table_id, col, p, hash_seed, regs.data())) {
+            if (registers_out) memcpy(registers_out, regs.data(), m);
+            if (estimate_out) *estimate_out = hll_estimate_host(regs.data(), p);
+            return GACE_OK;
+        }
+    }
     Ws ws;
     const uint64_t status_off = ws.take(256);
     const uint64_t regs_off = ws.take(m * 4);
@@ -1333,6 +1449,7 @@ gace_status gace_ndv(gace_ctx* ctx, uint32_t table_id, uint32_t col, uint32_t p,
     for (uint64_t j = 0; j < m; ++j) regs[j] = static_cast<uint8_t>(r32[j]);
     if (registers_out) memcpy(registers_out, regs.data(), m);
     if (estimate_out) *estimate_out = hll_estimate_host(regs.data(), p);
+    resident_sketch_put(ctx, table_id, col, p, hash_seed, regs.data());
     return GACE_OK;
 }
 

@@ -1,5 +1,6 @@
 // gace_gate.cpp -- the Risky Gate's trust metrics (Section III-C, Eq. 1-3)
 // and the break-even cost model (Section V, item 2; Eq. 4), on the host.
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 
@@ -130,6 +131,51 @@ gace_status gace_check_wait_limit(gace_ctx* ctx, uint32_t timeout_us) {
     const unsigned int st = *reinterpret_cast<const unsigned int*>(ctx->pin);
     if (st & kStatusTimeout) return fail(GACE_ETIMEDOUT, "the check's device wait gave up after %u us", timeout_us);
     return fail(GACE_ECUDA, "the check's device wait ended without giving up");
+}
+
+gace_status gace_calibrate_int(gace_ctx* ctx, uint32_t kind, uint32_t ms, double* ops_per_s) {
+    if (gace_status s = check_ctx(ctx)) return s;
+    if (kind > 1) return fail(GACE_EINVAL, "calibration kind %u (0 or 1)", kind);
+    if (ms == 0 || ms > 1000) return fail(GACE_EINVAL, "ms %u outside 1..1000", ms);
+    if (!ops_per_s) return fail(GACE_EINVAL, "ops_per_s is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    if (gace_status s = ctx->ensure_ws(256)) return s;
+    const int occ = int_peak_occupancy(static_cast<int>(kind));
+    if (occ < 1) return fail(GACE_ECUDA, "calibration kernel cannot be resident");
+    const int grid = ctx->sms * occ;
+    uint32_t* sink = reinterpret_cast<uint32_t*>(ctx->ws);
+    cudaEvent_t a = ctx->take_event(), b = ctx->take_event();
+    if (!a || !b) return fail(GACE_ECUDA, "cudaEventCreate");
+    auto timed = [&](uint32_t iters, float* out_ms) -> cudaError_t {
+        cudaError_t e = cudaEventRecord(a, ctx->stream);
+        if (e == cudaSuccess) e = int_peak_launch(static_cast<int>(kind), iters, grid, sink, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(b, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(out_ms, a, b);
+        return e;
+    };
+    float t = 0.f;
+    uint32_t iters = 64;
+    cudaError_t e = timed(iters, &t);  // warm-up and first estimate
+    // grow the launch until it lasts about `ms` (at most 2^24 iterations)
+    while (e == cudaSuccess && t < 0.25f * ms && iters < (1u << 24)) {
+        iters *= 4;
+        e = timed(iters, &t);
+    }
+    double best = 0.0;
+    for (int rep = 0; e == cudaSuccess && rep < 3; ++rep) {
+        e = timed(iters, &t);
+        if (e == cudaSuccess && t > 0.f) {
+            const double ops = static_cast<double>(grid) * 256.0 * iters * int_peak_ops_per_iter(static_cast<int>(kind));
+            best = std::max(best, ops / (t * 1e-3));
+        }
+    }
+    ctx->ev_free.push_back(a);
+    ctx->ev_free.push_back(b);
+    if (e != cudaSuccess) return cuda_fail(e, "calibration kernel");
+    *ops_per_s = best;
+    return GACE_OK;
 }
 
 }  // extern "C"

@@ -7,6 +7,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <functional>
 #include <limits>
 #include <map>
 #include <memory>
@@ -64,7 +65,7 @@ struct DeviceGuard {
 struct ColumnRec {
     int dtype = 0;
     void* dptr = nullptr;
-    bool owned = false;
+    bool owned = false;  // allocated by the context (stream-ordered, freed with cudaFreeAsync)
     uint64_t bytes = 0;
 };
 
@@ -72,6 +73,49 @@ struct TableRec {
     uint64_t nrows = 0;
     std::vector<ColumnRec> cols;
     uint64_t owned_bytes = 0;
+    uint32_t sample_of = 0;  // a materialised sample: the table it was drawn from (0: none)
+    bool in_store = false;   // owned by the resident store (evictable)
+};
+
+// ---------------------------------------------------------------- resident store
+// Samples and HyperLogLog sketches kept in device memory under a byte budget
+// (gace_resident_configure); the caller of every function below holds ctx->mu.
+struct ResidentKey {
+    uint32_t table = 0, kind = 0;
+    uint64_t thresh = 0, seedhash = 0, block_rows = 0;
+    bool operator<(const ResidentKey& o) const {
+        return std::tie(table, kind, thresh, seedhash, block_rows) <
+               std::tie(o.table, o.kind, o.thresh, o.seedhash, o.block_rows);
+    }
+};
+struct ResidentSample {
+    uint32_t sample_table = 0;
+    uint64_t bytes = 0;
+    uint64_t last_use = 0;
+};
+struct ResidentSketchKey {
+    uint32_t table = 0, col = 0, p = 0;
+    uint64_t seed = 0;
+    bool operator<(const ResidentSketchKey& o) const {
+        return std::tie(table, col, p, seed) < std::tie(o.table, o.col, o.p, o.seed);
+    }
+};
+struct ResidentSketch {
+    unsigned char* dregs = nullptr;  // 2^p one-byte registers (device)
+    uint64_t bytes = 0;
+    uint64_t last_use = 0;
+};
+struct ResidentStore {
+    uint64_t budget = 0;      // 0: the store is off
+    uint32_t admit_after = 1;
+    uint32_t flags = 0;
+    uint64_t used = 0, tick = 0;
+    std::map<ResidentKey, ResidentSample> samples;
+    std::map<ResidentKey, uint32_t> seen;  // uses of samples that are not resident
+    std::map<ResidentSketchKey, ResidentSketch> sketches;
+    gace_resident_stats st{};
+    bool samples_on() const { return budget && (flags & GACE_RESIDENT_SAMPLES); }
+    bool sketches_on() const { return budget && (flags & GACE_RESIDENT_SKETCHES); }
 };
 
 }  // namespace host
@@ -90,6 +134,7 @@ struct gace_ctx {
     uint64_t budget = 0;       // 0 = unlimited
     uint64_t used = 0;         // owned tables + workspace + pinned
     uint64_t timeout_ns = 2000ull * 1000000ull;
+    uint32_t max_ctas = 0;     // cap on the CTAs of a probe launch (0 = none)
     std::mutex mu;
     std::unordered_map<uint32_t, TableRec> tables;
     uint32_t next_id = 1;
@@ -188,6 +233,9 @@ struct gace_ctx {
     // served form: the scheduler, when running
     std::mutex serve_mu;
     std::shared_ptr<ServeState> serve;
+
+    // resident samples and sketches
+    ResidentStore resident;
 
     bool fits(uint64_t extra) const { return budget == 0 || used + extra <= budget; }
 
@@ -376,6 +424,15 @@ void pass_sizes(Pass& ps);
 // Copies a pass's inputs into pinned staging at ps.in_off and points its
 // arguments at their device copies (workspace base dws) and at its outputs.
 void stage_pass(Pass& ps, unsigned char* pin, unsigned char* dws, unsigned int* status);
+// A probe (or one part of a probe whose row sets span several tables) with its plan.
+struct PlannedProbe {
+    const TableRec* tab = nullptr;
+    ProbeRequest r;
+    ProbePlan plan;
+};
+// Runs planned probes with one upload, their passes' launches, one read-back
+// and a wait on the context stream, then assembles each part's results.
+gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts);
 // Results from the passes' counters (host copies, one pointer per pass).
 void assemble_probe(const ProbePlan& plan, const ProbeRequest& r,
                     const std::vector<const unsigned long long*>& pass_out);
@@ -552,11 +609,62 @@ void make_items(const std::vector<JobRec>& jobs, uint64_t chunk, std::vector<Bat
 // A request's outputs from what its small-output region held.
 void finish_request(gace_ctx* ctx, ReqPlan& rp, const unsigned char* host_base, unsigned int status);
 
+// ---------------------------------------------------------------- resident store
+
+// The materialised sample of table `tab` under set d (kind 1 or 2, mode 2): a
+// new table with every column, the kept rows in row order.  room(bytes) is
+// asked, once the sample's size is known, whether that many bytes may be
+// allocated (it may evict); false refuses with GACE_ENOMEM.
+gace_status materialize_sample(gace_ctx* ctx, const TableRec& tab, const SetDesc& d,
+                               const std::function<bool(uint64_t)>& room, TableRec& out);
+// The resident sample table for (table_id, d), or 0: a hit refreshes its
+// recency; a miss counts the use and, when `admit` is set and the sample has
+// been asked for admit_after times, materialises it into the store (evicting
+// least recently used entries outside `pinned`).  Sample tables in `pinned`
+// are not evicted; the returned one is added to it.
+uint32_t resident_sample(gace_ctx* ctx, uint32_t table_id, const SetDesc& d, bool admit,
+                         std::vector<uint32_t>& pinned);
+// The resident sketch's registers into regs (host, 2^p bytes): true on a hit.
+bool resident_sketch_get(gace_ctx* ctx, uint32_t table, uint32_t col, uint32_t p, uint64_t seed, uint8_t* regs);
+// Keeps a computed sketch (when sketches are on and it fits after eviction).
+void resident_sketch_put(gace_ctx* ctx, uint32_t table, uint32_t col, uint32_t p, uint64_t seed,
+                         const uint8_t* regs);
+// Drops every resident entry drawn from table_id (its unload).
+void resident_forget_table(gace_ctx* ctx, uint32_t table_id);
+// Whether served requests read a resident sample drawn from table_id (any, for 0).
+bool resident_samples_busy(gace_ctx* ctx, uint32_t table_id);
+// Drops every entry (the store turned off, or the context destroyed).
+void resident_clear(gace_ctx* ctx);
+// Frees a table's owned columns on the context stream and its bytes from the
+// context's accounting (the caller erases it from ctx->tables).
+void free_table_columns(gace_ctx* ctx, TableRec& t);
+// A probe request whose row sets are all one sample (0 < rate < 1) that the
+// store holds (or admits) becomes a full scan of the sample table: q's
+// table_id and samples are replaced (full points at a GACE_FULL sample).
+bool resident_rewrite(gace_ctx* ctx, gace_request& q, const gace_sample* full, std::vector<uint32_t>& pinned,
+                      bool admit);
+
+// A batch's requests as the resident store sees them: probes whose one row
+// set is a resident sample rewritten to full scans of it, NDV requests
+// answered from resident sketches taken out; what runs is reqs, whose entry k
+// is the caller's request index[k].
+struct ResidentBatch {
+    std::vector<gace_request> reqs;
+    std::vector<uint32_t> index;
+    std::vector<std::vector<uint8_t>> regs;  // registers of NDV requests that did not ask for them
+    std::vector<uint32_t> pinned;
+    void build(gace_ctx* ctx, const gace_request* in, uint32_t n);
+    // After the run: keeps the sketches the batch computed.
+    void keep_sketches(gace_ctx* ctx, const std::vector<gace_status>& st) const;
+};
+
 // Served form: stops the scheduler of a context (after its requests have
 // finished); forgets a table's cached sketches, GACE_EBUSY while requests on
 // the table are in flight.  The caller holds ctx->mu for serve_forget_table.
 void serve_shutdown(gace_ctx* ctx);
 gace_status serve_forget_table(gace_ctx* ctx, uint32_t table_id);
+// Whether served requests on the table are queued or in flight.
+bool serve_table_busy(gace_ctx* ctx, uint32_t table_id);
 
 }  // namespace host
 }  // namespace gace

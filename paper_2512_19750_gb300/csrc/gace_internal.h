@@ -143,6 +143,28 @@ cudaError_t probe_configure();  // one-time kernel attributes
 cudaError_t probe_launch(const ProbeArgs& a, int grid, cudaStream_t s);
 int probe_occupancy(const ProbeArgs& a);  // CTAs per SM for this kernel and smem size
 
+// ---------------------------------------------------------------- materialised samples
+// A row or block sample compacted into its own columns (k_sample_count, then
+// k_sample_scatter), in tiles of kSampleTileRows rows.
+constexpr uint32_t kSampleTileRows = 4096;
+constexpr int kMaxSampleCols = 64;
+
+struct alignas(16) SampleArgs {
+    uint64_t nrows;
+    uint64_t ntiles;              // ceil(nrows / kSampleTileRows)
+    SetDesc set;                  // kind 1 (rows) or 2 (blocks), mode 2 (threshold)
+    uint32_t ncols;
+    uint32_t pad;
+    const void* src[kMaxSampleCols];
+    void* dst[kMaxSampleCols];    // scatter only
+    uint32_t width[kMaxSampleCols];
+    uint32_t* tile_count;         // [ntiles], written by the count pass
+    const uint64_t* tile_off;     // [ntiles], exclusive prefix sums (scatter)
+};
+
+cudaError_t sample_count_launch(const SampleArgs& a, int grid, cudaStream_t s);
+cudaError_t sample_scatter_launch(const SampleArgs& a, int grid, cudaStream_t s);
+
 // ---------------------------------------------------------------- HyperLogLog
 struct HllArgs {
     const void* col;
@@ -155,6 +177,17 @@ struct HllArgs {
     unsigned int* status;
 };
 cudaError_t hll_launch(const HllArgs& a, int sms, cudaStream_t s);
+
+// Raw HyperLogLog estimate (Flajolet, Fusy, Gandouet & Meunier, AofA 2007)
+// from the histogram of register values: c[k] registers hold k, for
+// k = 0..65 (64 - p + 1 <= 61 is the largest a register can hold).  The sum
+// runs in ascending k, so the estimate depends only on the histogram, not on
+// the order of the registers.  alpha_m = 0.673, 0.697, 0.709 for m = 16, 32,
+// 64, else 0.7213 / (1 + 1.079 / m); the linear-counting estimate m ln(m / V)
+// replaces E when E <= 2.5 m and V = c[0] > 0.  Every entry point that
+// returns an estimate calls this one function, so their doubles agree bit for
+// bit.
+double hll_estimate_from_hist(const uint64_t (&c)[66], uint32_t p);
 
 // Sets the thread-local message returned by gace_last_error().
 void set_last_error_message(const char* msg);
@@ -293,5 +326,10 @@ int batch_occupancy(uint32_t smem_bytes, int cls);
 cudaError_t batch_launch(const BatchItem* items, uint32_t nitems, const BatchJob* jobs, unsigned int* head,
                          int grid, uint32_t smem_bytes, int cls, cudaStream_t s);
 cudaError_t copy_launch(const CopyDesc* descs, uint32_t n, int grid, cudaStream_t s);
+
+// Roofline calibration kernel of the integer pipes (gace_calibrate_int).
+cudaError_t int_peak_launch(int kind, uint32_t iters, int grid, uint32_t* sink, cudaStream_t s);
+uint64_t int_peak_ops_per_iter(int kind);
+int int_peak_occupancy(int kind);
 
 }  // namespace gace

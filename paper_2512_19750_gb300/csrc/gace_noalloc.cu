@@ -14,15 +14,21 @@
 // Every call uses the whole of it, so calls that overlap on the GPU (other
 // streams, other host threads) race: callers serialise them.  Each call clears
 // what must start at zero.  Host code never hands the array's name to a kernel
-// (in host code it is only a stand-in): the first call on each device looks up
-// its device address with cudaGetSymbolAddress, with that device current, and
-// caches it; that first call should therefore come before any stream capture.
+// (in host code it is only a stand-in): every call looks up its device address
+// with cudaGetSymbolAddress on the current device, which allocates nothing once
+// the library's module is loaded on that device, and is never stale (a device
+// reset or a new primary context gives a new address, and the next call sees
+// it).  With lazy module loading (CUDA's default) the first call on a device
+// loads the module, and that load may allocate and synchronise: callers warm
+// the entry point up once per device before the code that must not allocate,
+// or set CUDA_MODULE_LOADING=EAGER.  Every call waits for its stream and reads
+// its results back into host memory, so no call may be made while a stream is
+// being captured into a CUDA graph.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <cmath>
 #include <cstdio>
-#include <mutex>
 
 #include "../../include/gace.h"
 #include "gace_internal.h"
@@ -39,7 +45,6 @@ constexpr size_t kPackedOff = (size_t(1) << kMaxP) * 4;       // uint8[2^kMaxP]
 constexpr size_t kHistOff = kPackedOff + (size_t(1) << kMaxP);  // uint32[66], padded
 constexpr size_t kStatusOff = kHistOff + 512;                 // uint32
 constexpr size_t kScratchBytes = kStatusOff + 256;
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -59,9 +64,6 @@ __global__ void __launch_bounds__(256) k_pack_hist(const uint32_t* regs, uint32_
         if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
-std::mutex g_mu;
-unsigned char* g_addr[kMaxDevices] = {nullptr};
-
 gace_status fail_msg(gace_status s, const char* msg) {
     gace::set_last_error_message(msg);
     return s;
@@ -73,16 +75,13 @@ gace_status cuda_fail(cudaError_t e, const char* what) {
     return fail_msg(GACE_ECUDA, buf);
 }
 
-// Device address of the scratch array on the current device (looked up once).
-gace_status scratch_address(int dev, unsigned char** out) {
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
-        g_addr[dev] = static_cast<unsigned char*>(p);
-    }
-    *out = g_addr[dev];
+// Device address of the scratch array on the current device, looked up on
+// every call (a cached address would outlive a device reset).
+gace_status scratch_address(unsigned char** out) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
+    *out = static_cast<unsigned char*>(p);
     return GACE_OK;
 }
 
@@ -91,21 +90,6 @@ uint64_t splitmix64_seed(uint64_t x) {
     x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
     x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
     return x ^ (x >> 31);
-}
-
-// Raw HyperLogLog estimate from the register-value histogram c[0..65].
-double estimate_from_counts(const uint32_t* c, uint32_t p) {
-    const double m = static_cast<double>(1ull << p);
-    double alpha;
-    if (p == 4) alpha = 0.673;
-    else if (p == 5) alpha = 0.697;
-    else if (p == 6) alpha = 0.709;
-    else alpha = 0.7213 / (1.0 + 1.079 / m);
-    double z = 0.0;
-    for (int k = 0; k <= 65; ++k) z += static_cast<double>(c[k]) * std::ldexp(1.0, -k);
-    double e = alpha * m * m / z;
-    if (e <= 2.5 * m && c[0] > 0) e = m * std::log(m / static_cast<double>(c[0]));
-    return e;
 }
 
 }  // namespace
@@ -123,9 +107,8 @@ extern "C" gace_status gace_ndv_noalloc(const void* column, int32_t dtype, uint6
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices) return fail_msg(GACE_EINVAL, "device ordinal above 63");
     unsigned char* base = nullptr;
-    if (gace_status st = scratch_address(dev, &base)) return st;
+    if (gace_status st = scratch_address(&base)) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const uint32_t m = 1u << p;
     uint32_t* regs = reinterpret_cast<uint32_t*>(base + kRegsOff);
@@ -162,6 +145,10 @@ extern "C" gace_status gace_ndv_noalloc(const void* column, int32_t dtype, uint6
         return cuda_fail(e, "copy status");
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     if (st) return fail_msg(GACE_ETIMEDOUT, "a bounded device CAS loop gave up");
-    if (estimate_out) *estimate_out = estimate_from_counts(counts, p);
+    if (estimate_out) {
+        uint64_t c[66];
+        for (int k = 0; k < 66; ++k) c[k] = counts[k];
+        *estimate_out = gace::hll_estimate_from_hist(c, p);
+    }
     return GACE_OK;
 }

@@ -173,6 +173,7 @@ struct Live {
     ReplaySink* sink = nullptr;
     uint32_t sink_index = 0;
     bool cacheable = false;
+    bool keep_resident = false;  // an NDV request whose sketch the resident store keeps
     bool finished = false;
     bool fusable = false;  // a probe that may share its table's scan with others
     // a fused group: the members' predicates run as one request (fp); the
@@ -962,14 +963,20 @@ void ServeState::complete(StepSet& S) {
             reinterpret_cast<const unsigned char*>(reinterpret_cast<uintptr_t>(rb) - lv.small_rel);
         lv.rp.status = GACE_OK;
         std::vector<uint8_t> regs;
-        if (lv.rp.kind == GACE_REQ_NDV && lv.cacheable && !lv.req.q.registers_out) {
-            // the cache keeps the registers even when the caller does not want them
+        const bool keeps = lv.rp.kind == GACE_REQ_NDV && (lv.cacheable || lv.keep_resident);
+        if (keeps && !lv.req.q.registers_out) {
+            // the caches keep the registers even when the caller does not want them
             regs.resize(1ull << lv.rp.hll.p);
             lv.req.q.registers_out = regs.data();
         }
         double est = 0.0;
-        if (lv.rp.kind == GACE_REQ_NDV && lv.cacheable && !lv.req.q.estimate_out) lv.req.q.estimate_out = &est;
+        if (keeps && !lv.req.q.estimate_out) lv.req.q.estimate_out = &est;
         finish_request(ctx, lv.rp, host_base, status);
+        if (lv.keep_resident && lv.rp.status == GACE_OK) {
+            const gace_request& q = lv.req.q;
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            resident_sketch_put(ctx, q.table_id, q.col, q.p, q.hash_seed, q.registers_out);
+        }
         finish(lv, lv.rp.status, lv.rp.error);
         const uint64_t t_done = now_ns();
         auto account = [&](const Live& r) {
@@ -1275,6 +1282,28 @@ gace_status submit_request(gace_ctx* ctx, const gace_request& req, uint64_t* tic
         }
         lv->cacheable = true;
     }
+    if (q.kind == GACE_REQ_NDV && ctx->resident.sketches_on() && q.p >= 4 && q.p <= 18) {
+        const TableRec* tab = find_table(ctx, q.table_id);
+        if (tab && q.col < tab->cols.size()) {
+            std::vector<uint8_t> r(1ull << q.p);
+            if (resident_sketch_get(ctx, q.table_id, q.col, q.p, q.hash_seed, r.data())) {
+                if (q.registers_out) memcpy(q.registers_out, r.data(), r.size());
+                if (q.estimate_out) *q.estimate_out = hll_estimate_host(r.data(), q.p);
+                std::lock_guard<std::mutex> lk(srv->mu);
+                const uint64_t t = srv->next_ticket++;
+                if (ticket_out) *ticket_out = t;
+                if (!sink) srv->open[t] = true;
+                deliver(*srv, t, sink, idx, GACE_OK, std::string());
+                return GACE_OK;
+            }
+            lv->keep_resident = true;
+        }
+    }
+    if (q.kind == GACE_REQ_PROBE) {  // one resident sample: a full scan of it
+        static const gace_sample kFull{GACE_FULL, 0, 1.0, 0};
+        std::vector<uint32_t> pinned;
+        resident_rewrite(ctx, lv->req.q, &kFull, pinned, true);
+    }
     if (gace_status s = compile_request(ctx, q, lv->rp)) return s;
     if (q.kind == GACE_REQ_PROBE && srv->cfg.probe_cache > 0) {
         std::lock_guard<std::mutex> lk(srv->mu);
@@ -1322,6 +1351,13 @@ void wait_until(uint64_t t) {
 }  // namespace
 
 void serve_shutdown(gace_ctx* ctx) { stop_server(ctx); }
+
+bool serve_table_busy(gace_ctx* ctx, uint32_t table_id) {
+    std::shared_ptr<ServeState> s = get_server(ctx);
+    if (!s) return false;
+    std::lock_guard<std::mutex> lk(s->mu);
+    return s->table_refs.count(table_id) != 0;
+}
 
 gace_status serve_forget_table(gace_ctx* ctx, uint32_t table_id) {
     std::shared_ptr<ServeState> s = get_server(ctx);
