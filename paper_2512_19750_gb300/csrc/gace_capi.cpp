@@ -364,6 +364,63 @@ void build_range_tree(const std::vector<std::pair<uint64_t, uint64_t>>& iv, bool
     }
 }
 
+// Two-choice (cuckoo) hash tables of a column's EQ/IN groups (layout in
+// gace_internal.h): every group's keys are placed at one of their two slots,
+// vs_slot(key, m1) or vs_slot(key, m2), moving a resident key to its other
+// slot when both are taken (at most kCuckooKicks moves per insertion).  When
+// a group cannot be placed, new multipliers are drawn (a fixed seeded
+// sequence, so a batch always gets the same tables) and, every eighth try, the
+// tables double.  All groups of a column share one capacity and the
+// multipliers.
+constexpr int kCuckooKicks = 96;
+
+bool build_cuckoo(const std::vector<std::vector<VsEntry>>& keys, bool is64, uint32_t slot, uint32_t& tlog,
+                  uint32_t& m1, uint32_t& m2, std::vector<uint32_t>& tabs) {
+    const uint32_t ew = is64 ? 4u : 2u;
+    for (uint32_t attempt = 0; attempt < 64; ++attempt) {
+        if (attempt > 0 && attempt % 8 == 0) ++tlog;
+        if (tlog > 20) return false;
+        m1 = static_cast<uint32_t>(splitmix64_host(0xC0C0ull * (slot + 1) + 2 * attempt)) | 1u;
+        m2 = static_cast<uint32_t>(splitmix64_host(0xC0C0ull * (slot + 1) + 2 * attempt + 1)) | 1u;
+        if (m1 == m2) continue;
+        const uint32_t cap = 1u << tlog;
+        tabs.assign(static_cast<size_t>(keys.size()) * cap * ew, 0u);
+        bool ok = true;
+        for (size_t g = 0; g < keys.size() && ok; ++g) {
+            uint32_t* tab = tabs.data() + g * cap * ew;
+            for (const VsEntry& e0 : keys[g]) {
+                VsEntry cur = e0;
+                uint32_t at = vs_slot(cur.lo, cur.hi, m1, tlog);
+                bool placed = false;
+                for (int kick = 0; kick <= kCuckooKicks; ++kick) {
+                    uint32_t* x = tab + static_cast<size_t>(at) * ew;
+                    uint32_t& mask = is64 ? x[2] : x[1];
+                    if (mask == 0) {
+                        x[0] = cur.lo;
+                        if (is64) x[1] = cur.hi;
+                        mask = cur.mask;
+                        placed = true;
+                        break;
+                    }
+                    const VsEntry out{x[0], is64 ? x[1] : 0u, mask};  // evicted: goes to its other slot
+                    x[0] = cur.lo;
+                    if (is64) x[1] = cur.hi;
+                    mask = cur.mask;
+                    cur = out;
+                    const uint32_t a1 = vs_slot(cur.lo, cur.hi, m1, tlog);
+                    at = a1 == at ? vs_slot(cur.lo, cur.hi, m2, tlog) : a1;
+                }
+                if (!placed) {
+                    ok = false;
+                    break;
+                }
+            }
+        }
+        if (ok) return true;
+    }
+    return false;
+}
+
 // Builds the device form of a pass and the probe arguments (without pointers).
 gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::vector<NTerm>& uterms,
                        const std::vector<std::vector<uint32_t>>& pred_u,
@@ -422,14 +479,13 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
         }
     }
     if (!narrow) {
-        // one open-addressing table per group of 32 EQ/IN terms of a column:
+        // one two-choice hash table per group of 32 EQ/IN terms of a column:
         // key -> mask of the group's terms that contain it
         for (uint32_t s = 0; s < nslots; ++s) {
             SlotDesc& sd = A.slots[s];
             const uint32_t nvs = sd.iend - sd.rend;
             if (nvs == 0) continue;
             const bool is64 = sd.dtype == GACE_I64;
-            const uint32_t ew = is64 ? 4u : 2u;
             sd.ngroups = (nvs + 31) / 32;
             // values of each term as (lo, hi) keys, floats with -0 -> +0
             std::vector<std::vector<std::pair<uint32_t, uint32_t>>> vals(nvs);
@@ -446,40 +502,26 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
                     for (auto& kv : vals[k])
                         if ((kv.first << 1) == 0) kv.first = 0;
             }
+            // distinct keys of each group with the mask of the group's terms that hold them
+            std::vector<std::vector<VsEntry>> keys(sd.ngroups);
             for (uint32_t g = 0; g < sd.ngroups; ++g) {
-                size_t n = 0;
-                for (uint32_t k = 32 * g; k < std::min(nvs, 32 * g + 32); ++k) n += vals[k].size();
-                most = std::max(most, n);
+                std::map<std::pair<uint32_t, uint32_t>, uint32_t> merged;
+                for (uint32_t k = 32 * g; k < std::min(nvs, 32 * g + 32); ++k)
+                    for (const auto& kv : vals[k]) merged[kv] |= 1u << (k - 32 * g);
+                for (const auto& e : merged) keys[g].push_back({e.first.first, e.first.second, e.second});
+                most = std::max(most, keys[g].size());
             }
             uint32_t tlog = 6;
             while ((1ull << tlog) < kVsSlotsPerEntry * most) ++tlog;
+            std::vector<uint32_t> tabs;
+            uint32_t m1 = 0, m2 = 0;
+            if (!build_cuckoo(keys, is64, s, tlog, m1, m2, tabs))
+                return fail(GACE_EINVAL, "no two-choice table holds the EQ/IN values of a column");
             sd.tlog = tlog;
-            const uint32_t cap = 1u << tlog;
+            sd.vm1 = m1;
+            sd.vm2 = m2;
             sd.toff = static_cast<uint32_t>(ps.pool.size());
-            ps.pool.resize(ps.pool.size() + static_cast<size_t>(sd.ngroups) * cap * ew, 0u);
-            for (uint32_t g = 0; g < sd.ngroups; ++g) {
-                uint32_t* tab = ps.pool.data() + sd.toff + static_cast<size_t>(g) * cap * ew;
-                for (uint32_t k = 32 * g; k < std::min(nvs, 32 * g + 32); ++k) {
-                    const uint32_t bit = 1u << (k - 32 * g);
-                    for (const auto& kv : vals[k]) {
-                        uint32_t at = vs_hash(kv.first, kv.second, is64, tlog);
-                        for (;; at = (at + 1) & (cap - 1)) {
-                            uint32_t* e = tab + static_cast<size_t>(at) * ew;
-                            uint32_t& mask = is64 ? e[2] : e[1];
-                            if (mask == 0) {
-                                e[0] = kv.first;
-                                if (is64) e[1] = kv.second;
-                                mask = bit;
-                                break;
-                            }
-                            if (e[0] == kv.first && (!is64 || e[1] == kv.second)) {
-                                mask |= bit;
-                                break;
-                            }
-                        }
-                    }
-                }
-            }
+            ps.pool.insert(ps.pool.end(), tabs.begin(), tabs.end());
         }
     }
     if (!narrow) {
@@ -1006,7 +1048,7 @@ void stage_pass(Pass& ps, unsigned char* pin, unsigned char* dws, unsigned int* 
 
 void assemble_probe(const ProbePlan& plan, const ProbeRequest& r,
                     const std::vector<const unsigned long long*>& pass_out) {
-    const uint32_t nsamples = r.nsamples, nterms = r.nterms, npreds = r.npreds;
+    const uint32_t nsamples = r.nsamples, npreds = r.npreds;
     const std::vector<Pass>& passes = plan.passes;
     std::vector<uint64_t> ns(nsamples, 0);
     for (uint32_t s = 0; s < nsamples; ++s) {
@@ -1171,6 +1213,20 @@ gace_status gace_create(gace_ctx** out, const gace_config* cfg) {
         ctx->own_stream = true;
     }
     if ((e = probe_configure()) != cudaSuccess) return bail(cuda_fail(e, "probe kernel attributes"));
+    {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = c.device;
+        if ((e = cudaMemPoolCreate(&ctx->pool, &props)) != cudaSuccess) {
+            ctx->pool = nullptr;
+            return bail(cuda_fail(e, "cudaMemPoolCreate"));
+        }
+        // freed blocks stay in the pool up to the HBM budget (all of them without one)
+        uint64_t keep = ctx->budget ? ctx->budget : ~0ull;
+        if ((e = cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess)
+            return bail(cuda_fail(e, "cudaMemPoolSetAttribute"));
+    }
     if ((e = cudaMalloc(&ctx->d_status, 256)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(status)"));
     *out = ctx;
     return GACE_OK;
@@ -1201,6 +1257,7 @@ gace_status gace_destroy(gace_ctx* ctx) {
                 if (j) cudaEventDestroy(j);
         }
         if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+        if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     }
     delete ctx;
     return GACE_OK;
@@ -1241,7 +1298,7 @@ gace_status gace_load_columns(gace_ctx* ctx, uint64_t nrows, uint32_t ncols, con
         } else {
             const uint64_t alloc = round_up(bytes + 16, 256);
             // stream-ordered: no device-wide synchronisation
-            cudaError_t e = cudaMallocAsync(&r.dptr, alloc, ctx->stream);
+            cudaError_t e = ctx->alloc_async(&r.dptr, alloc);
             if (e != cudaSuccess) {
                 for (auto& x : tab.cols) cudaFreeAsync(x.dptr, ctx->stream);
                 return fail(GACE_ENOMEM, "cudaMallocAsync(%llu) for column %u: %s", (unsigned long long)alloc, c,

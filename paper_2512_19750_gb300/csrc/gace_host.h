@@ -143,6 +143,15 @@ struct gace_ctx {
     unsigned char* pin = nullptr;  // pinned host staging
     uint64_t pin_cap = 0;
     unsigned int* d_status = nullptr;
+    // Stream-ordered allocations of the columns, samples and sketches the
+    // context owns come from its own pool, which keeps freed memory for reuse
+    // (a table loaded and unloaded step after step does not map its pages
+    // again each time) and returns it to the device when the context ends.
+    cudaMemPool_t pool = nullptr;
+
+    cudaError_t alloc_async(void** p, uint64_t bytes) {
+        return pool ? cudaMallocFromPoolAsync(p, bytes, pool, stream) : cudaMallocAsync(p, bytes, stream);
+    }
 
     // kernel statistics (tracing)
     struct KStat {
@@ -304,7 +313,7 @@ bool is_in_kind(uint32_t k);
 uint32_t in_count(const NTerm& t);
 
 // Slots per entry of a wide pass's EQ/IN hash tables (the inverse of their
-// load factor): linear probing, so a miss walks to the next empty slot.
+// load factor): a two-choice table fills reliably below half its slots.
 #ifndef GACE_VS_SLOTS
 #define GACE_VS_SLOTS 2
 #endif
@@ -326,6 +335,10 @@ struct ColPool {
     uint32_t words() const;
 };
 uint64_t term_cost(const NTerm& t);
+// One distinct value of a wide pass's EQ/IN group and the group's terms that hold it.
+struct VsEntry {
+    uint32_t lo, hi, mask;
+};
 DevTerm make_devterm(const NTerm& t, uint32_t pool_off);
 
 // ---------------------------------------------------------------- sets

@@ -55,6 +55,7 @@ struct SlotDesc {
     uint32_t roff;       // wide passes: pool word offset of the slot's range trees
     uint32_t rgroups;    // range trees (groups of up to 32 range terms)
     uint32_t rtree;      // range terms [rbeg, rbeg + rtree) by tree, the rest by compare
+    uint32_t vm1, vm2;   // wide passes: the multipliers of the hash tables' two slot functions
 };
 
 // A wide pass's range terms of one column, 32 at a time, as an interval tree:
@@ -67,14 +68,22 @@ constexpr uint32_t kTreeNodes = 127;
 constexpr uint32_t kTreeWords32 = 256;  // 127 keys, 1 pad, 128 masks
 constexpr uint32_t kTreeWords64 = 384;  // 127 key pairs, 2 pad, 128 masks
 
-// Hash of a key into a wide pass's EQ/IN table of 2^tlog entries (host and
-// device build and probe the same tables).
+// A wide pass's EQ and IN terms of one column, 32 at a time, as two-choice
+// (cuckoo) hash tables of 2^tlog entries: every distinct value of the group's
+// terms is stored once, with the mask of the group's terms that contain it,
+// at one of its two candidate slots vs_slot(key, vm1) and vs_slot(key, vm2);
+// an empty slot has mask 0.  A lookup reads both slots and ORs the masks of
+// those whose key matches: two independent loads, whatever the occupancy.
+// A 64-bit key folds to 32 bits as lo ^ rotl16(hi * m): the rotation keeps
+// keys such as 2^31 and -2^63, whose words are 2^31 and 0 swapped, apart for
+// every odd m (without it both would fold to 2^31 and share every slot).
+// Host and device compute the slots with this one function.
 #if defined(__CUDACC__)
 __host__ __device__
 #endif
-inline uint32_t vs_hash(uint32_t lo, uint32_t hi, bool is64, uint32_t tlog) {
-    const uint32_t x = is64 ? (lo ^ (hi * 0x85EBCA6Bu)) : lo;
-    return (x * 0x9E3779B1u) >> (32 - tlog);
+inline uint32_t vs_slot(uint32_t lo, uint32_t hi, uint32_t m, uint32_t tlog) {
+    const uint32_t h = hi * m;
+    return ((lo ^ ((h << 16) | (h >> 16))) * m) >> (32 - tlog);
 }
 
 struct SetDesc {

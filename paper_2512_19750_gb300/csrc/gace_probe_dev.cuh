@@ -263,23 +263,18 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
     return x;
 }
 
-// Mask of the group's EQ/IN terms that hold for key (lo, hi): open addressing,
-// linear probing; an entry with an empty mask ends the search.
-__device__ __forceinline__ uint32_t vs_lookup(const uint32_t* tab, uint32_t cap, bool is64, uint32_t h,
-                                              uint32_t lo, uint32_t hi) {
-    for (uint32_t p = 0; p < cap; ++p) {
-        const uint32_t at = (h + p) & (cap - 1);
-        if (is64) {
-            const uint4 e = reinterpret_cast<const uint4*>(tab)[at];
-            if (e.z == 0) return 0;
-            if (e.x == lo && e.y == hi) return e.z;
-        } else {
-            const uint2 e = reinterpret_cast<const uint2*>(tab)[at];
-            if (e.y == 0) return 0;
-            if (e.x == lo) return e.y;
-        }
+// Mask of the group's EQ/IN terms that hold for key (lo, hi): the masks of
+// its two candidate slots whose key matches (an empty slot's mask is 0).
+__device__ __forceinline__ uint32_t vs_lookup(const uint32_t* tab, bool is64, uint32_t s1, uint32_t s2, uint32_t lo,
+                                              uint32_t hi) {
+    if (is64) {
+        const uint4 a = reinterpret_cast<const uint4*>(tab)[s1];
+        const uint4 b = reinterpret_cast<const uint4*>(tab)[s2];
+        return ((a.x == lo && a.y == hi) ? a.z : 0u) | ((b.x == lo && b.y == hi) ? b.z : 0u);
     }
-    return 0;
+    const uint2 a = reinterpret_cast<const uint2*>(tab)[s1];
+    const uint2 b = reinterpret_cast<const uint2*>(tab)[s2];
+    return (a.x == lo ? a.y : 0u) | (b.x == lo ? b.y : 0u);
 }
 
 // EQ and IN terms of one column slot in a wide pass: one table lookup per row
@@ -292,20 +287,21 @@ __device__ __forceinline__ void eval_valueset(const SlotDesc& sd, const Vals<NQ>
     const bool is64 = sd.dtype == 1;
     const uint32_t cap = 1u << sd.tlog;
     const uint32_t ew = is64 ? 4u : 2u;
-    uint32_t klo[R], khi[R], hb[R];
+    uint32_t klo[R], khi[R], s1[R], s2[R];
 #pragma unroll
     for (int i = 0; i < R; ++i) {
         klo[i] = v.lo[i];
         khi[i] = is64 ? v.hi[i] : 0u;
         if (sd.dtype == 2 && (klo[i] << 1) == 0) klo[i] = 0;  // -0 equals +0
-        hb[i] = vs_hash(klo[i], khi[i], is64, sd.tlog);
+        s1[i] = vs_slot(klo[i], khi[i], sd.vm1, sd.tlog);
+        s2[i] = vs_slot(klo[i], khi[i], sd.vm2, sd.tlog);
     }
     const uint32_t nvs = sd.iend - sd.rend;
     for (uint32_t g = 0; g < sd.ngroups; ++g) {
         const uint32_t* tab = pool + sd.toff + g * cap * ew;
         uint32_t w[R];
 #pragma unroll
-        for (int i = 0; i < R; ++i) w[i] = vs_lookup(tab, cap, is64, hb[i], klo[i], khi[i]);
+        for (int i = 0; i < R; ++i) w[i] = vs_lookup(tab, is64, s1[i], s2[i], klo[i], khi[i]);
         uint4 out[NQ];
 #pragma unroll
         for (int h = 0; h < NQ; ++h) {

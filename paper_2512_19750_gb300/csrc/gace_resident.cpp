@@ -186,7 +186,7 @@ gace_status materialize_sample(gace_ctx* ctx, const TableRec& tab, const SetDesc
         r.dtype = tab.cols[c].dtype;
         r.bytes = total * a.width[c];
         const uint64_t alloc = round_up(r.bytes + 16, 256);
-        cudaError_t e = cudaMallocAsync(&r.dptr, alloc, ctx->stream);
+        cudaError_t e = ctx->alloc_async(&r.dptr, alloc);
         if (e != cudaSuccess) {
             for (auto& x : out.cols) cudaFreeAsync(x.dptr, ctx->stream);
             out.cols.clear();
@@ -275,7 +275,7 @@ void resident_sketch_put(gace_ctx* ctx, uint32_t table, uint32_t col, uint32_t p
     if (!make_room(ctx, bytes, none)) return;
     if (ctx->ensure_pin(m) != GACE_OK) return;
     ResidentSketch sk;
-    if (cudaMallocAsync(reinterpret_cast<void**>(&sk.dregs), bytes, ctx->stream) != cudaSuccess) return;
+    if (ctx->alloc_async(reinterpret_cast<void**>(&sk.dregs), bytes) != cudaSuccess) return;
     memcpy(ctx->pin, regs, m);
     if (cudaMemcpyAsync(sk.dregs, ctx->pin, m, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
         cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
