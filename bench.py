@@ -570,8 +570,26 @@ def e2e_leg(g, ctx, table, preds, samples, batch, args, stream):
         once()
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / reps
+    # where one more step's time goes (outside the timed steps)
+    ph = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        ta = time.perf_counter()
+        t = g.gace_load_columns(ctx, host)
+        tb = time.perf_counter()
+        g.gace_probe_batch(ctx, t, preds, samples, table.dtypes, marginals=True, batch=batch)
+        tc = time.perf_counter()
+        for c in range(len(table.columns)):
+            g.gace_ndv(ctx, t, c, 14, 42)
+        td = time.perf_counter()
+        g.gace_unload(ctx, t)
+        torch.cuda.synchronize()
+        te = time.perf_counter()
+        ph.append({"load_h2d": 1e3 * (tb - ta), "probe": 1e3 * (tc - tb), "sketches": 1e3 * (td - tc),
+                   "unload": 1e3 * (te - td)})
     out = {"value": table.nrows / dt, "unit": "rows/s", "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1000.0, "steps": reps}
+           "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1000.0, "steps": reps,
+           "phases_ms": {k: round(min(p[k] for p in ph), 3) for k in ph[0]}}
     overhead = overhead_leg(g, ctx, host, table.dtypes)
     del host
     return out, overhead
@@ -746,6 +764,28 @@ def batched_leg(g, ctx, dev, args):
     served_done, served_st = g.gace_serve_replay(ctx, to_gace_requests(g, tids, tables, reqs), zero, mode=0)
     g.gace_serve_stop(ctx)
     served_wall = float(served_done.max()) / 1e9
+    # the same batch with the context's resident store (120 GB): 1 % row and
+    # 1 % block samples of every table materialised first, sketches kept by a
+    # first run; the plain path reads the same store
+    from workloads import BLOCKS, ROWS, Sample
+    g.gace_resident_configure(ctx, 120 << 30)
+    for tid in tids:
+        for smp in (Sample(ROWS, 0.01, 42), Sample(BLOCKS, 0.01, 42, 4096)):
+            g.gace_resident_prefetch(ctx, tid, smp)
+    rreqs = g.RequestArray(to_gace_requests(g, tids, tables, reqs))
+    for _ in range(2):
+        g.gace_run_batch(ctx, rreqs)
+    rwalls = []
+    for _ in range(5):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        g.gace_run_batch(ctx, rreqs)
+        rwalls.append(time.perf_counter() - t0)
+    rwall = float(np.median(rwalls))
+    rplain_done, rplain_st = g.gace_serve_replay(ctx, to_gace_requests(g, tids, tables, reqs), zero, mode=1)
+    rplain_wall = float(rplain_done.max()) / 1e9
+    rstore = g.gace_resident_stats_read(ctx)
+    g.gace_resident_configure(ctx, 0)
     for t in tids:
         g.gace_unload(ctx, t)
     rows = sum(t.nrows for t in tables)
@@ -763,6 +803,10 @@ def batched_leg(g, ctx, dev, args):
         "batched_gbs": nbytes / wall / 1e9,
         "shared_scan_bytes": shared,
         "batched_gbs_shared_scan": shared / wall / 1e9,
+        "resident_store": {"batched_probes_per_s": n / rwall, "batched_ms": rwall * 1000.0,
+                           "plain_probes_per_s": n / rplain_wall, "plain_ms": rplain_wall * 1000.0,
+                           "batched_vs_plain": rplain_wall / rwall, "store": rstore,
+                           "ok": bool((rplain_st == 0).all())},
         "all_ok": bool((plain_st == 0).all() and (served_st == 0).all()),
         "plain": "one synchronous call per request (probe / ndv / join_card) from a native loop",
     }
@@ -780,8 +824,9 @@ def served_leg(g, ctx, dev, args):
                       1 % and 10 % row samples and 1 % block samples of every
                       table materialised before the run, sketches kept as they
                       are computed (the served form's host caches off);
-      resident_1gb    a 1 GB store, served at one rate, samples admitted on
-                      first use: admission and eviction under pressure."""
+      resident_256mb  a 256 MB store (a third of the 1 % samples the mix reads),
+                      served at one rate, samples admitted on first use:
+                      admission and eviction under pressure."""
     import numpy as np
     import torch
 
@@ -841,9 +886,9 @@ def served_leg(g, ctx, dev, args):
     out["resident_120gb"] = sweep(rates, True, "resident_120gb")
     out["resident_120gb"]["store"] = dict(g.gace_resident_stats_read(ctx), prefetch_s=round(prefetch_s, 3))
 
-    g.gace_resident_configure(ctx, 1 << 30)
-    out["resident_1gb"] = sweep([rates[min(1, len(rates) - 1)]], False, "resident_1gb")
-    out["resident_1gb"]["store"] = g.gace_resident_stats_read(ctx)
+    g.gace_resident_configure(ctx, 256 << 20)
+    out["resident_256mb"] = sweep([rates[min(1, len(rates) - 1)]], False, "resident_256mb")
+    out["resident_256mb"]["store"] = g.gace_resident_stats_read(ctx)
     g.gace_resident_configure(ctx, 0)
     for t in tids:
         g.gace_unload(ctx, t)

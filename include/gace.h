@@ -159,6 +159,10 @@ gace_status gace_destroy(gace_ctx* ctx);
  *   into device memory it owns, 256-byte aligned; counted against the budget.
  * flags == GACE_BORROW: the context keeps the device pointers; the caller keeps
  *   them alive and unchanged until gace_unload.  Every column must be on_device.
+ * Device columns are read on the context's stream: work on other streams that
+ * writes them must be complete (or ordered before that stream) when they are
+ * read.  A GACE_COPY load from device memory waits for the whole device first;
+ * a borrowed column is read by every later call on the table.
  * The probe reads each column with 16-byte bulk copies when its base address is
  * 16-byte aligned, and with plain loads otherwise (same results, slower).
  */
@@ -332,8 +336,8 @@ gace_status gace_sample_materialize(gace_ctx* ctx, uint32_t table_id, const gace
  * The served form rewrites a probe at submission only when all its row sets
  * are one sample; the synchronous call splits any mix of row sets.
  * budget_bytes = 0 turns the store off (the default) and frees its entries;
- * so does a changed configuration.  Unloading a table drops what the store
- * drew from it.
+ * a changed configuration frees them and restarts the statistics.  Unloading
+ * a table drops what the store drew from it.
  */
 #define GACE_RESIDENT_SAMPLES 1u
 #define GACE_RESIDENT_SKETCHES 2u

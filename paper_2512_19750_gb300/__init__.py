@@ -135,6 +135,12 @@ def gace_load_columns(ctx, columns, borrow: bool = False) -> int:
             nrows = rows
         elif rows != nrows:
             raise ValueError("columns differ in length")
+    if any(getattr(c, "is_cuda", False) for c in columns):
+        import torch
+
+        # the library reads the columns on its own stream: what torch queued to
+        # produce them must have finished
+        torch.cuda.synchronize()
     tid = C.c_uint32()
     check(lib().gace_load_columns(ctx, nrows or 0, n, arr, GACE_BORROW if borrow else GACE_COPY,
                                   C.byref(tid)), "gace_load_columns")

@@ -206,7 +206,7 @@ gace_status compile_probe(gace_ctx* ctx, const TableRec* tab, const gace_request
     if (gace_status s = check_probe_request(r)) return s;
     if (!tab) tab = find_table(ctx, q.table_id);
     if (!tab) return fail(GACE_ENOTFOUND, "table %u is not loaded", q.table_id);
-    return plan_probe(ctx, *tab, r, false, rp.plan);
+    return plan_probe(ctx, *tab, r, false, rp.plan, kProbeWarps);
 }
 
 // Compiles one request (argument checks, plans, join sides).

@@ -194,28 +194,29 @@ uint32_t in_count(const NTerm& t) {
 uint32_t ColPool::words() const {
     const uint32_t trees = nr / 32 + (nr % 32 >= kTreeMin ? 1 : 0);
     uint64_t w = 1;
-    if (!vs.empty()) {
-        uint64_t most = 0;
-        for (size_t g = 0; g < vs.size(); g += 32) {
-            uint64_t n = 0;
-            for (size_t k = g; k < std::min(vs.size(), g + 32); ++k) n += vs[k];
-            most = std::max(most, n);
-        }
+    if (nvs) {
         uint32_t tlog = 6;
         while ((1ull << tlog) < kVsSlotsPerEntry * most) ++tlog;
-        w += static_cast<uint64_t>((vs.size() + 31) / 32) * (1ull << tlog) * (is64 ? 4u : 2u);
+        w += static_cast<uint64_t>((nvs + 31) / 32) * (1ull << tlog) * (is64 ? 4u : 2u);
     }
     w += static_cast<uint64_t>(trees) * (is64 ? kTreeWords64 : kTreeWords32);
     return w > 0xFFFFFFFFull ? 0xFFFFFFFFu : static_cast<uint32_t>(w);
 }
 
 void ColPool::add(const NTerm& t) {
+    uint64_t entries = 0;
     if (is_in_kind(t.kind))
-        vs.push_back(in_count(t));
+        entries = in_count(t);
     else if (term_cost(t) == 1)
-        vs.push_back(1);  // a single value: looked up like an EQ term
-    else
+        entries = 1;  // a single value: looked up like an EQ term
+    if (!entries) {
         ++nr;
+        return;
+    }
+    if (nvs % 32 == 0) last = 0;  // a new group
+    last += entries;
+    most = std::max(most, last);
+    ++nvs;
 }
 
 // Minimum compares a row needs for a term: one for a single value, two for a
@@ -329,16 +330,13 @@ void build_range_tree(const std::vector<std::pair<uint64_t, uint64_t>>& iv, bool
     const size_t m = e.size();  // <= 64 for 32 intervals
     std::vector<uint64_t> sorted(e);
     sorted.resize(kTreeNodes, kmax);
-    // level-order (1-based) layout of the complete tree whose in-order is `sorted`
+    // level-order (1-based) layout of the perfect tree whose in-order is
+    // `sorted`: node i on level L (2^L <= i < 2^(L+1)) is in-order element
+    // ((2 (i - 2^L) + 1) << (levels - 1 - L)) - 1
     std::vector<uint64_t> node(kTreeNodes + 1);
-    size_t next = 0;
-    std::function<void(size_t)> fill = [&](size_t i) {
-        if (i > kTreeNodes) return;
-        fill(2 * i);
-        node[i] = sorted[next++];
-        fill(2 * i + 1);
-    };
-    fill(1);
+    for (uint32_t L = 0; L < static_cast<uint32_t>(kTreeLevels); ++L)
+        for (uint32_t i = 1u << L; i < (2u << L); ++i)
+            node[i] = sorted[((2 * (i - (1u << L)) + 1) << (kTreeLevels - 1 - L)) - 1];
     uint32_t* masks = out + (is64 ? 2 * kTreeNodes + 2 : kTreeNodes + 1);
     for (size_t i = 1; i <= kTreeNodes; ++i) {
         if (is64) {
@@ -424,7 +422,7 @@ bool build_cuckoo(const std::vector<std::vector<VsEntry>>& keys, bool is64, uint
 // Builds the device form of a pass and the probe arguments (without pointers).
 gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::vector<NTerm>& uterms,
                        const std::vector<std::vector<uint32_t>>& pred_u,
-                       const std::vector<SetPlan>& sets, bool want_marg, bool force_wide) {
+                       const std::vector<SetPlan>& sets, bool want_marg, bool force_wide, uint32_t wide_warps) {
     // Narrow passes (at most 32 predicates and terms) evaluate IN lists by
     // compare; wide passes look up every EQ and IN term of a column in that
     // column's hash tables.  Order: by column, ranges (or, wide, multi-value
@@ -440,7 +438,7 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
         const int ia = valueset(a), ib = valueset(b);
         return std::tie(a.col, ia) < std::tie(b.col, ib);
     });
-    std::map<uint32_t, uint32_t> local;
+    std::vector<uint32_t> local(uterms.size(), 0);  // unique term -> index in the pass
     ps.uterms = order;
     ps.slots.clear();
     ps.dterms.clear();
@@ -505,11 +503,21 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
             // distinct keys of each group with the mask of the group's terms that hold them
             std::vector<std::vector<VsEntry>> keys(sd.ngroups);
             for (uint32_t g = 0; g < sd.ngroups; ++g) {
-                std::map<std::pair<uint32_t, uint32_t>, uint32_t> merged;
+                std::vector<VsEntry>& out = keys[g];
                 for (uint32_t k = 32 * g; k < std::min(nvs, 32 * g + 32); ++k)
-                    for (const auto& kv : vals[k]) merged[kv] |= 1u << (k - 32 * g);
-                for (const auto& e : merged) keys[g].push_back({e.first.first, e.first.second, e.second});
-                most = std::max(most, keys[g].size());
+                    for (const auto& kv : vals[k]) out.push_back({kv.first, kv.second, 1u << (k - 32 * g)});
+                std::sort(out.begin(), out.end(), [](const VsEntry& x, const VsEntry& y) {
+                    return x.hi != y.hi ? x.hi < y.hi : x.lo < y.lo;
+                });
+                size_t n = 0;  // equal keys merged: one entry with the OR of their terms
+                for (size_t i = 0; i < out.size(); ++i) {
+                    if (n && out[n - 1].lo == out[i].lo && out[n - 1].hi == out[i].hi)
+                        out[n - 1].mask |= out[i].mask;
+                    else
+                        out[n++] = out[i];
+                }
+                out.resize(n);
+                most = std::max(most, out.size());
             }
             uint32_t tlog = 6;
             while ((1ull << tlog) < kVsSlotsPerEntry * most) ++tlog;
@@ -563,6 +571,7 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
     A.npredterms = static_cast<uint32_t>(ps.pterm.size());
     A.want_marg = want_marg ? 1u : 0u;
     A.timeout_ns = ctx->timeout_ns;
+    A.nwarps = narrow ? static_cast<uint32_t>(kProbeWarps) : wide_warps;
 
     // Narrow passes (the gate's single probes) stream staged tiles of about
     // 32 KB through a bulk-copy pipeline two or three stages deep (at most
@@ -787,7 +796,7 @@ gace_status check_probe_request(const ProbeRequest& r) {
 }
 
 gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r, bool force_wide,
-                       ProbePlan& plan) {
+                       ProbePlan& plan, uint32_t wide_warps) {
     plan = ProbePlan();
     plan.tab = &tab;
     const uint32_t nsamples = r.nsamples, nterms = r.nterms, npreds = r.npreds;
@@ -893,15 +902,20 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
     std::vector<int32_t> u_pass(uterms.size(), -1);
     {
         Pass cur;
-        std::map<uint32_t, bool> in_cur;
+        std::vector<uint8_t> in_cur(uterms.size(), 0);  // unique terms placed in the current pass
         uint32_t pool_words = 0;
-        uint64_t pred_terms = 0;               // predicate-term entries of the pass
-        std::map<uint32_t, ColPool> cols_cur;  // the pass's columns and their tables
+        uint64_t pred_terms = 0;  // predicate-term entries of the pass
+        // the pass's columns and their tables (a table has at most 64 columns)
+        std::vector<ColPool> cols_cur(tab.cols.size());
+        std::vector<uint8_t> has_col(tab.cols.size(), 0);
+        size_t ncols_cur = 0;
+        using Touched = std::vector<std::pair<uint32_t, ColPool>>;
         auto flush = [&]() {
             if (!cur.preds.empty() || !cur.uterms.empty()) passes.push_back(cur);
+            for (uint32_t u : cur.uterms) in_cur[u] = 0;
             cur = Pass();
-            in_cur.clear();
-            cols_cur.clear();
+            std::fill(has_col.begin(), has_col.end(), 0);
+            ncols_cur = 0;
             pool_words = 0;
             pred_terms = 0;
         };
@@ -910,62 +924,71 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
         // probe_layout), against what keeps kWideCtas CTAs per SM (1 KB of
         // each CTA's share is reserved by the hardware)
         const uint64_t nsets_dev = sets.size();
-        const uint64_t smem_budget = static_cast<uint64_t>(ctx->smem_per_sm) / kWideCtas - 1024;
+        const int ctas = wide_warps >= 16 ? 2 : kWideCtas;
+        const uint64_t smem_budget = static_cast<uint64_t>(ctx->smem_per_sm) / ctas - 1024;
         auto wide_smem = [&](uint64_t nt, uint64_t np, uint64_t npt, uint64_t pool) {
             uint64_t off = 128 + nt * 16;
             off = round_up(off + pool * 4, 16) + (np + 1) * 4;
             off = round_up(off + npt * 4, 16);
-            off += static_cast<uint64_t>(kProbeWarps) * (nt + nsets_dev) * 16 + nsets_dev * np * 4;
+            off += static_cast<uint64_t>(wide_warps) * (nt + nsets_dev) * 16 + nsets_dev * np * 4;
             off += plan.want_marg ? nsets_dev * nt * 4 : 0;
             return round_up(off + nsets_dev * 4, 16);
         };
         // the pass's columns and pool words with the terms `add` added
-        auto with_terms = [&](const std::vector<uint32_t>& add, std::map<uint32_t, ColPool>& touched) {
+        auto with_terms = [&](const std::vector<uint32_t>& add, Touched& touched) {
             uint64_t total = pool_words;
             for (uint32_t u : add) {
                 const uint32_t col = uterms[u].col;
-                auto it = touched.find(col);
-                if (it == touched.end()) {
-                    auto base = cols_cur.find(col);
+                size_t k = 0;
+                while (k < touched.size() && touched[k].first != col) ++k;
+                if (k == touched.size()) {
                     ColPool c;
-                    if (base != cols_cur.end()) {
-                        c = base->second;
-                    } else {
+                    if (has_col[col])
+                        c = cols_cur[col];
+                    else
                         c.is64 = tab.cols[col].dtype == GACE_I64;
-                    }
-                    it = touched.emplace(col, std::move(c)).first;
+                    touched.emplace_back(col, c);
                 }
-                it->second.add(uterms[u]);
+                touched[k].second.add(uterms[u]);
             }
-            for (const auto& kv : touched) {
-                auto base = cols_cur.find(kv.first);
-                total += kv.second.words() - (base != cols_cur.end() ? base->second.words() : 0u);
-            }
+            for (const auto& kv : touched)
+                total += kv.second.words() - (has_col[kv.first] ? cols_cur[kv.first].words() : 0u);
             return total;
         };
-        auto commit = [&](const std::vector<uint32_t>& add, std::map<uint32_t, ColPool>& touched, uint64_t total) {
+        auto new_cols = [&](const Touched& touched) {
+            size_t n = 0;
+            for (const auto& kv : touched) n += has_col[kv.first] ? 0 : 1;
+            return n;
+        };
+        auto commit = [&](const std::vector<uint32_t>& add, const Touched& touched, uint64_t total) {
             for (uint32_t u : add) {
-                in_cur[u] = true;
+                in_cur[u] = 1;
                 cur.uterms.push_back(u);
                 u_pass[u] = static_cast<int32_t>(passes.size());
             }
-            for (auto& kv : touched) cols_cur[kv.first] = std::move(kv.second);
+            for (const auto& kv : touched) {
+                if (!has_col[kv.first]) {
+                    has_col[kv.first] = 1;
+                    ++ncols_cur;
+                }
+                cols_cur[kv.first] = kv.second;
+            }
             pool_words = static_cast<uint32_t>(total);
         };
+        std::vector<uint32_t> add;
+        Touched touched;
         for (uint32_t p = 0; p < npreds; ++p) {
             if (plan.pstate[p] != 0) continue;
             const std::vector<uint32_t>& pu = plan.pred_u[p];
             if (pu.size() > kPassTerms) return fail(GACE_EINVAL, "predicate %u has too many terms", p);
-            std::vector<uint32_t> add;
+            add.clear();
             for (uint32_t u : pu)
-                if (!in_cur.count(u)) add.push_back(u);
-            std::map<uint32_t, ColPool> touched;
+                if (!in_cur[u]) add.push_back(u);
+            touched.clear();
             uint64_t total = with_terms(add, touched);
             // a predicate too large for a shared pass gets one of its own (a
             // single predicate evaluates IN lists by compare, with no tables)
-            const size_t ncols = cols_cur.size() + std::count_if(touched.begin(), touched.end(), [&](const auto& kv) {
-                                     return !cols_cur.count(kv.first);
-                                 });
+            const size_t ncols = ncols_cur + new_cols(touched);
             if (!cur.preds.empty() &&
                 (cur.uterms.size() + add.size() > kPassTerms || cur.preds.size() + 1 > kPassPreds ||
                  total > kPassPool || ncols > static_cast<size_t>(kMaxSlots) ||
@@ -984,10 +1007,10 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
         if (plan.want_marg) {
             for (uint32_t u = 0; u < uterms.size(); ++u) {
                 if (u_pass[u] >= 0) continue;
-                std::vector<uint32_t> add{u};
-                std::map<uint32_t, ColPool> touched;
+                add.assign(1, u);
+                touched.clear();
                 uint64_t total = with_terms(add, touched);
-                const size_t ncols = cols_cur.size() + (cols_cur.count(uterms[u].col) ? 0 : 1);
+                const size_t ncols = ncols_cur + (has_col[uterms[u].col] ? 0 : 1);
                 if (!cur.uterms.empty() &&
                     (cur.uterms.size() + 1 > kPassTerms || total > kPassPool ||
                      ncols > static_cast<size_t>(kMaxSlots) ||
@@ -1007,7 +1030,8 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
     if (sets.empty()) passes.clear();  // every sample is empty: nothing to count
     if (passes.empty() && need_ns) passes.push_back(Pass());  // counts sample rows only
     for (auto& ps : passes) {
-        if (gace_status st = build_pass(ctx, tab, ps, uterms, plan.pred_u, sets, plan.want_marg, force_wide))
+        if (gace_status st = build_pass(ctx, tab, ps, uterms, plan.pred_u, sets, plan.want_marg, force_wide,
+                                        wide_warps))
             return st;
         pass_sizes(ps);
     }
@@ -1125,7 +1149,7 @@ gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts) {
                             ps.args.smem_bytes);
             // work units: tiles (narrow) or 8-slice warp sweeps (wide)
             const uint64_t unit_rows =
-                ps.args.narrow ? ps.args.tile_rows : static_cast<uint64_t>(kSliceRows) * kProbeWarps;
+                ps.args.narrow ? ps.args.tile_rows : static_cast<uint64_t>(kSliceRows) * ps.args.nwarps;
             const uint64_t units = (tab->nrows + unit_rows - 1) / unit_rows;
             uint64_t grid = static_cast<uint64_t>(ctx->sms) * occ;
             if (ctx->max_ctas && grid > ctx->max_ctas) grid = ctx->max_ctas;
@@ -1279,6 +1303,13 @@ gace_status gace_load_columns(gace_ctx* ctx, uint64_t nrows, uint32_t ncols, con
     }
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
+    if (flags == GACE_COPY && nrows > 0) {
+        // device sources are read on the context stream: whatever produced
+        // them on other streams must have finished first
+        bool from_device = false;
+        for (uint32_t c = 0; c < ncols; ++c) from_device = from_device || cols[c].on_device;
+        if (from_device) CK(cudaDeviceSynchronize());
+    }
     TableRec tab;
     tab.nrows = nrows;
     uint64_t need = 0;
@@ -1400,7 +1431,7 @@ gace_status gace_probe_batch(gace_ctx* ctx, uint32_t table_id, const gace_sample
         parts.emplace_back();
         parts.back().tab = tab;
         parts.back().r = r;
-        if (gace_status st = plan_probe(ctx, *tab, r, false, parts.back().plan)) return st;
+        if (gace_status st = plan_probe(ctx, *tab, r, false, parts.back().plan, kWideWarps)) return st;
         return run_planned(ctx, parts);
     }
     // one part per table: the base table with the samples that are not
@@ -1437,7 +1468,7 @@ gace_status gace_probe_batch(gace_ctx* ctx, uint32_t table_id, const gace_sample
         pp.r.nsamples = ns;
         pp.r.results = npreds ? pres[i].data() : nullptr;
         pp.r.term_marginals = term_marginals ? pmarg[i].data() : nullptr;
-        if (gace_status st = plan_probe(ctx, *pp.tab, pp.r, false, pp.plan)) return st;
+        if (gace_status st = plan_probe(ctx, *pp.tab, pp.r, false, pp.plan, kWideWarps)) return st;
     }
     if (gace_status st = run_planned(ctx, parts)) return st;
     for (size_t i = 0; i < order.size(); ++i) {

@@ -327,10 +327,14 @@ constexpr uint64_t kVsSlotsPerEntry = GACE_VS_SLOTS;
 constexpr uint32_t kTreeMin = GACE_TREE_MIN;
 
 // The tables one column's terms need in a wide pass (pass packing).
+// Terms fill groups of 32 in order, so the open group is always the last one:
+// a few counters give the tables' size in constant time per term.
 struct ColPool {
-    std::vector<uint32_t> vs;  // entries of each EQ / IN term, in order
-    uint32_t nr = 0;           // multi-value range terms
-    bool is64 = false;         // 64-bit keys
+    uint32_t nvs = 0;    // EQ / IN terms (groups of 32, in order)
+    uint64_t last = 0;   // entries of the last group
+    uint64_t most = 0;   // entries of the fullest group
+    uint32_t nr = 0;     // multi-value range terms
+    bool is64 = false;   // 64-bit keys
     void add(const NTerm& t);
     uint32_t words() const;
 };
@@ -430,8 +434,10 @@ struct ProbePlan {
 // Argument checks that need no table.
 gace_status check_probe_request(const ProbeRequest& r);
 // Compiles a probe; force_wide builds every pass in the wide-kernel layout.
+// wide_warps: warps of the CTA that runs the plan's wide passes (kWideWarps
+// for the synchronous kernel, kProbeWarps for the batched form's).
 gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r, bool force_wide,
-                       ProbePlan& plan);
+                       ProbePlan& plan, uint32_t wide_warps);
 // Bytes of a pass's inputs (terms, pool, predicate CSR) and outputs (counters).
 void pass_sizes(Pass& ps);
 // Copies a pass's inputs into pinned staging at ps.in_off and points its

@@ -15,6 +15,19 @@ constexpr int kMaxSlots = 32;                   // distinct columns in one pass
 constexpr int kMaxSets = 8;                     // row sets in one probe
 constexpr int kMaxStages = 4;                   // bulk-copy pipeline depth
 constexpr int kNarrowMax = 32;                  // narrow kernel: predicates and terms per pass
+// Warps of the synchronous wide-pass CTA and its CTAs per SM (the shared-memory
+// tables of a pass are read by every warp of its CTA; each warp keeps its own
+// term masks).
+#ifndef GACE_WIDE_WARPS
+#define GACE_WIDE_WARPS 8
+#endif
+constexpr int kWideWarps = GACE_WIDE_WARPS;
+// CTAs per SM the compiler must fit the wide kernel's registers to (0: no
+// bound; at 8 warps its registers allow three CTAs unbounded, and a bound made
+// it spill).
+#ifndef GACE_WIDE_MINCTAS
+#define GACE_WIDE_MINCTAS (GACE_WIDE_WARPS >= 16 ? 2 : 0)
+#endif
 
 // device status word bits (first error wins for the code, bits accumulate)
 constexpr unsigned kStatusTimeout = 1u;         // an mbarrier wait gave up
@@ -108,6 +121,8 @@ struct alignas(16) ProbeArgs {
     uint32_t narrow;        // 1: lane-owned counters, staged tiles; 0: wide batch kernel
     uint32_t skip_tiles;    // 1: every row set is a block sample; tiles with no sampled block are skipped
     uint32_t smem_bytes;
+    uint32_t nwarps;        // warps of the CTA that runs the pass (per-warp mask buffers)
+    uint32_t pad_[3];
     // smem byte offsets
     uint32_t off_stage, off_terms, off_pool, off_poff, off_pterm, off_tm, off_keep,
         off_cnt, off_marg, off_ns;

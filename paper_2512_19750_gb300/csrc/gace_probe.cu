@@ -66,18 +66,26 @@ __global__ void __launch_bounds__(kThreads, 4) k_probe_single(const __grid_const
     flush(A, S, tid);
 }
 
-__global__ void __launch_bounds__(kThreads) k_probe_wide(const __grid_constant__ ProbeArgs A) {
+constexpr int kWideThreads = kWideWarps * 32;
+
+#if GACE_WIDE_MINCTAS > 0
+#define GACE_WIDE_BOUNDS __launch_bounds__(kWideThreads, GACE_WIDE_MINCTAS)
+#else
+#define GACE_WIDE_BOUNDS __launch_bounds__(kWideThreads)
+#endif
+
+__global__ void GACE_WIDE_BOUNDS k_probe_wide(const __grid_constant__ ProbeArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const Smem S = carve(A, smem, warp);
-    load_tables(A, S, tid);
+    load_tables(A, S, tid, kWideThreads);
     __syncthreads();
     const uint64_t nslices = (A.nrows + kSliceRows - 1) / kSliceRows;
-    const uint32_t nsr = wide_slices(A, S, lane, static_cast<uint64_t>(blockIdx.x) * kProbeWarps + warp, nslices,
-                                     static_cast<uint64_t>(gridDim.x) * kProbeWarps);
+    const uint32_t nsr = wide_slices(A, S, lane, static_cast<uint64_t>(blockIdx.x) * kWideWarps + warp, nslices,
+                                     static_cast<uint64_t>(gridDim.x) * kWideWarps);
     if (lane < static_cast<int>(A.nsets) && nsr) atomicAdd(&S.ns[lane], nsr);
     __syncthreads();
-    flush(A, S, tid);
+    flush(A, S, tid, kWideThreads);
 }
 
 uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
@@ -98,10 +106,11 @@ uint32_t probe_layout(ProbeArgs& a) {
     a.off_pterm = off;
     off = align_up(off + a.npredterms * 4, 16);
     const uint32_t nq = a.narrow ? 2 : 1;  // quads per lane
+    const uint32_t warps = a.nwarps ? a.nwarps : kProbeWarps;
     a.off_tm = off;
-    off += kProbeWarps * a.nterms * 16 * nq;
+    off += warps * a.nterms * 16 * nq;
     a.off_keep = off;
-    off += kProbeWarps * a.nsets * 16 * nq;
+    off += warps * a.nsets * 16 * nq;
     a.off_cnt = off;
     off += a.nsets * a.npreds * 4;
     a.off_marg = off;
@@ -137,7 +146,7 @@ int probe_occupancy(const ProbeArgs& a) {
     int n = 0;
     cudaError_t e = cudaSuccess;
     switch (variant(a)) {
-        case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_wide, kThreads, a.smem_bytes); break;
+        case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_wide, kWideThreads, a.smem_bytes); break;
         case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_narrow<false, 1>, kThreads, a.smem_bytes); break;
         case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_narrow<true, 1>, kThreads, a.smem_bytes); break;
         case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_narrow<true, kMaxSets>, kThreads, a.smem_bytes); break;
@@ -149,7 +158,7 @@ int probe_occupancy(const ProbeArgs& a) {
 
 cudaError_t probe_launch(const ProbeArgs& a, int grid, cudaStream_t s) {
     switch (variant(a)) {
-        case 0: k_probe_wide<<<grid, kThreads, a.smem_bytes, s>>>(a); break;
+        case 0: k_probe_wide<<<grid, kWideThreads, a.smem_bytes, s>>>(a); break;
         case 1: k_probe_narrow<false, 1><<<grid, kThreads, a.smem_bytes, s>>>(a); break;
         case 2: k_probe_narrow<true, 1><<<grid, kThreads, a.smem_bytes, s>>>(a); break;
         case 3: k_probe_narrow<true, kMaxSets><<<grid, kThreads, a.smem_bytes, s>>>(a); break;

@@ -48,31 +48,32 @@ __device__ __forceinline__ Smem carve(const ProbeArgs& A, unsigned char* smem, i
     return s;
 }
 
-// Copies the pass tables into shared memory and zeroes the CTA counters.
-__device__ __forceinline__ void load_tables(const ProbeArgs& A, const Smem& s, int tid) {
-    for (uint32_t i = tid; i < A.nterms; i += kThreads) s.st[i] = A.terms[i];
-    for (uint32_t i = tid; i < A.npool; i += kThreads) s.pool[i] = A.pool[i];
-    for (uint32_t i = tid; i <= A.npreds; i += kThreads) s.poff[i] = A.pred_off[i];
-    for (uint32_t i = tid; i < A.npredterms; i += kThreads) s.pterm[i] = A.pred_terms[i];
-    for (uint32_t i = tid; i < A.nsets * A.npreds; i += kThreads) s.cnt[i] = 0;
+// Copies the pass tables into shared memory and zeroes the CTA counters
+// (nthreads: the CTA's threads).
+__device__ __forceinline__ void load_tables(const ProbeArgs& A, const Smem& s, int tid, int nthreads = kThreads) {
+    for (uint32_t i = tid; i < A.nterms; i += nthreads) s.st[i] = A.terms[i];
+    for (uint32_t i = tid; i < A.npool; i += nthreads) s.pool[i] = A.pool[i];
+    for (uint32_t i = tid; i <= A.npreds; i += nthreads) s.poff[i] = A.pred_off[i];
+    for (uint32_t i = tid; i < A.npredterms; i += nthreads) s.pterm[i] = A.pred_terms[i];
+    for (uint32_t i = tid; i < A.nsets * A.npreds; i += nthreads) s.cnt[i] = 0;
     if (A.want_marg)
-        for (uint32_t i = tid; i < A.nsets * A.nterms; i += kThreads) s.marg[i] = 0;
-    for (uint32_t i = tid; i < A.nsets; i += kThreads) s.ns[i] = 0;
+        for (uint32_t i = tid; i < A.nsets * A.nterms; i += nthreads) s.marg[i] = 0;
+    for (uint32_t i = tid; i < A.nsets; i += nthreads) s.ns[i] = 0;
 }
 
 // CTA counters -> global 64-bit totals (zeros skipped).
-__device__ __forceinline__ void flush(const ProbeArgs& A, const Smem& s, int tid) {
-    for (uint32_t i = tid; i < A.nsets * A.npreds; i += kThreads) {
+__device__ __forceinline__ void flush(const ProbeArgs& A, const Smem& s, int tid, int nthreads = kThreads) {
+    for (uint32_t i = tid; i < A.nsets * A.npreds; i += nthreads) {
         const uint32_t v = s.cnt[i];
         if (v) atomicAdd(&A.counts[i], static_cast<unsigned long long>(v));
     }
     if (A.want_marg) {
-        for (uint32_t i = tid; i < A.nsets * A.nterms; i += kThreads) {
+        for (uint32_t i = tid; i < A.nsets * A.nterms; i += nthreads) {
             const uint32_t v = s.marg[i];
             if (v) atomicAdd(&A.marg[i], static_cast<unsigned long long>(v));
         }
     }
-    for (uint32_t i = tid; i < A.nsets; i += kThreads)
+    for (uint32_t i = tid; i < A.nsets; i += nthreads)
         if (s.ns[i]) atomicAdd(&A.nsamp[i], static_cast<unsigned long long>(s.ns[i]));
 }
 
@@ -248,7 +249,11 @@ __device__ __forceinline__ void eval_slot(const SlotDesc& sd, const Vals<NQ>& v,
 
 // 32 x 32 bit transpose across a warp: lane i holds row i (bit j = M[i][j]);
 // afterwards lane j holds column j (bit i = M[i][j]).  Five butterfly stages
-// swap the off-diagonal blocks of halving size.
+// swap the off-diagonal blocks of halving size s: a lane keeps the bits of its
+// own half (mask M) and takes the partner's other half, rotated into place by
+// s (lower lanes) or 32 - s (upper lanes); the bits a rotation wraps around
+// land where M keeps the lane's own bits, so one funnel shift and one
+// three-input logic operation do the stage.
 __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
 #pragma unroll
     for (int s = 16; s >= 1; s >>= 1) {
@@ -257,8 +262,11 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
                          : s == 4  ? 0x0F0F0F0Fu
                          : s == 2  ? 0x33333333u
                                    : 0x55555555u;
+        const bool up = (lane & s) != 0;
         const uint32_t y = __shfl_xor_sync(kFullMask, x, s);
-        x = (lane & s) ? ((x & ~m) | ((y & ~m) >> s)) : ((x & m) | ((y & m) << s));
+        const uint32_t t = __funnelshift_l(y, y, up ? 32 - s : s);
+        const uint32_t keep = up ? ~m : m;
+        x = (x & keep) | (t & ~keep);
     }
     return x;
 }
@@ -419,10 +427,11 @@ __device__ __forceinline__ uint32_t wide_slices(const ProbeArgs& A, const Smem& 
         __syncwarp();
         // the row sets with a row in this slice (warp-uniform): sparse samples
         // are empty in most slices, and a slice in no set needs no evaluation
-        uint32_t active = 0;
+        uint32_t active = 0, whole = 0;  // sets with a row / with every row of the slice
         for (uint32_t q = 0; q < A.nsets; ++q) {
             const uint4 k = S.keep[q];
             if (k.x | k.y | k.z | k.w) active |= 1u << q;
+            if ((k.x & k.y & k.z & k.w) == kFullMask) whole |= 1u << q;
         }
         if (!active) {
             __syncwarp();  // every lane has read S.keep before lane 0 rewrites it
@@ -448,22 +457,27 @@ __device__ __forceinline__ uint32_t wide_slices(const ProbeArgs& A, const Smem& 
             if (sd.iend > sd.rend) eval_valueset<1>(sd, v, S.pool, S.tm, lane);  // EQ and IN by table
         }
         __syncwarp();
+        // a set holding every row of the slice counts the mask's bits alone
         for (uint32_t p = lane; p < A.npreds; p += 32) {
             const uint32_t b = S.poff[p], e = S.poff[p + 1];
             uint4 acc = S.tm[S.pterm[b]];
             for (uint32_t k = b + 1; k < e; ++k) acc = and4(acc, S.tm[S.pterm[k]]);
+            const uint32_t all = __popc(acc.x) + __popc(acc.y) + __popc(acc.z) + __popc(acc.w);
+            if (!all) continue;
             for (uint32_t a = active; a; a &= a - 1) {
                 const uint32_t q = __ffs(a) - 1;
-                const uint32_t c = popc4(acc, S.keep[q]);
+                const uint32_t c = (whole >> q) & 1u ? all : popc4(acc, S.keep[q]);
                 if (c) atomicAdd(&S.cnt[q * A.npreds + p], c);
             }
         }
         if (A.want_marg) {
             for (uint32_t t = lane; t < A.nterms; t += 32) {
                 const uint4 m = S.tm[t];
+                const uint32_t all = __popc(m.x) + __popc(m.y) + __popc(m.z) + __popc(m.w);
+                if (!all) continue;
                 for (uint32_t a = active; a; a &= a - 1) {
                     const uint32_t q = __ffs(a) - 1;
-                    const uint32_t c = popc4(m, S.keep[q]);
+                    const uint32_t c = (whole >> q) & 1u ? all : popc4(m, S.keep[q]);
                     if (c) atomicAdd(&S.marg[q * A.nterms + t], c);
                 }
             }

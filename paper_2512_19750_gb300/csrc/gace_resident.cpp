@@ -400,7 +400,10 @@ gace_status gace_resident_configure(gace_ctx* ctx, const gace_resident_config* c
         return fail(GACE_EINVAL, "resident flags 0x%x invalid", c.flags);
     if (!c.flags) c.flags = GACE_RESIDENT_SAMPLES | GACE_RESIDENT_SKETCHES;
     if (resident_samples_busy(ctx, 0)) return fail(GACE_EBUSY, "served requests read resident samples");
-    if (c.budget_bytes != R.budget || c.flags != R.flags || c.admit_after != R.admit_after) resident_clear(ctx);
+    if (c.budget_bytes != R.budget || c.flags != R.flags || c.admit_after != R.admit_after) {
+        resident_clear(ctx);
+        R.st = gace_resident_stats{};  // a new configuration counts afresh
+    }
     R.budget = c.budget_bytes;
     R.flags = c.flags;
     R.admit_after = c.admit_after;

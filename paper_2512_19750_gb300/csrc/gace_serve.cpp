@@ -69,6 +69,7 @@ constexpr uint64_t kItemsPerCta = 2;
 constexpr size_t kDirectCopies = 2;             // at most this many blocks moved by plain copies per step
 constexpr uint64_t kDirectBlockMax = 256u << 10;
 constexpr uint64_t kSpinNs = 500000;            // busy-wait on a step's completion before sleeping
+constexpr uint64_t kIdleSpinNs = 2000000;       // an idle scheduler watches the queue this long before sleeping
 
 uint64_t now_ns() {
     return static_cast<uint64_t>(std::chrono::duration_cast<std::chrono::nanoseconds>(
@@ -1073,6 +1074,15 @@ void ServeState::run() {
                     quit = true;
                     break;
                 }
+                // Idle: watch the queue for a while before sleeping, so that a
+                // request arriving soon does not wait out a thread wake-up
+                // (tens of microseconds, most of a small probe's latency).
+                lk.unlock();
+                const uint64_t t0 = now_ns();
+                while (npending.load(std::memory_order_relaxed) == 0 && now_ns() - t0 < kIdleSpinNs)
+                    std::this_thread::yield();
+                lk.lock();
+                if (!pending.empty() || stop) continue;
                 cv_work.wait(lk);
             }
             if (!quit && sticky != GACE_OK) {
