@@ -1124,6 +1124,20 @@ gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts) {
             ps.out_off = ws.take(ps.out_bytes);
             any_pass = true;
         }
+    // A part with several wide passes over hashed row sets computes every
+    // slice's row-set masks once, for all its passes to load.
+    std::vector<uint64_t> mask_off(parts.size(), 0);
+    for (size_t i = 0; i < parts.size(); ++i) {
+        const ProbePlan& pl = parts[i].plan;
+        uint32_t wide = 0;
+        for (const auto& ps : pl.passes) wide += ps.args.narrow ? 0u : 1u;
+        bool hashed = false;
+        for (const auto& sp : pl.sets) hashed = hashed || sp.d.mode == 2;
+        if (wide >= 2 && hashed) {
+            const uint64_t nslices = (parts[i].tab->nrows + kSliceRows - 1) / kSliceRows;
+            mask_off[i] = ws.take(nslices * pl.sets.size() * 16);
+        }
+    }
     if (gace_status st = ctx->ensure_ws(ws.off)) return st;
     if (gace_status st = ctx->ensure_pin(ws.off + 256)) return st;
 
@@ -1140,8 +1154,17 @@ gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts) {
             for (auto& ps : pp.plan.passes) CK(cudaMemsetAsync(dws + ps.out_off, 0, ps.out_bytes, ctx->stream));
     }
     CK(cudaMemsetAsync(dws + status_off, 0, 256, ctx->stream));
-    for (auto& pp : parts) {
+    for (size_t i = 0; i < parts.size(); ++i) {
+        auto& pp = parts[i];
         const TableRec* tab = pp.tab;
+        if (mask_off[i]) {
+            uint4* masks = reinterpret_cast<uint4*>(dws + mask_off[i]);
+            const ProbeArgs& a0 = pp.plan.passes.front().args;
+            const uint64_t n = tab->nrows;
+            CK(ctx->traced("probe_setmask", n, 0, n, [&] { return setmask_launch(a0, masks, ctx->sms, ctx->stream); }));
+            for (auto& ps : pp.plan.passes)
+                if (!ps.args.narrow) ps.args.setmask = masks;
+        }
         for (auto& ps : pp.plan.passes) {
             const int occ = probe_occupancy(ps.args);
             if (occ < 1)

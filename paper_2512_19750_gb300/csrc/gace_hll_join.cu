@@ -33,6 +33,11 @@ using namespace side_dev;
 constexpr int kHllThreads = 1024;
 constexpr int kJoinThreads = 256;
 
+// Groups of four rows a thread takes per iteration (their loads issued together).
+#ifndef GACE_HLL_UNROLL
+#define GACE_HLL_UNROLL 1
+#endif
+
 template <bool SMEM, int DT>
 __global__ void __launch_bounds__(kHllThreads, 2) k_hll(const __grid_constant__ HllArgs A) {
     extern __shared__ uint32_t sregs[];
@@ -41,8 +46,8 @@ __global__ void __launch_bounds__(kHllThreads, 2) k_hll(const __grid_constant__ 
         for (uint32_t i = threadIdx.x; i < m / 4; i += kHllThreads) sregs[i] = 0;
         __syncthreads();
     }
-    hll_groups<SMEM, DT>(A, sregs, static_cast<uint64_t>(blockIdx.x) * kHllThreads + threadIdx.x,
-                         (A.nrows + 3) / 4, static_cast<uint64_t>(gridDim.x) * kHllThreads);
+    hll_groups<SMEM, DT, GACE_HLL_UNROLL>(A, sregs, static_cast<uint64_t>(blockIdx.x) * kHllThreads + threadIdx.x,
+                                          (A.nrows + 3) / 4, static_cast<uint64_t>(gridDim.x) * kHllThreads);
     if (SMEM) {
         __syncthreads();
         hll_merge(A, sregs, m, threadIdx.x, kHllThreads);

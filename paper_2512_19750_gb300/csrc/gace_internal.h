@@ -133,6 +133,8 @@ struct alignas(16) ProbeArgs {
     const uint32_t* pool;
     const uint32_t* pred_off;    // npreds + 1
     const uint32_t* pred_terms;
+    const uint4* setmask;        // wide passes: row-set masks of every 128-row slice, [slice][nsets],
+                                 // computed once for all passes of a call (nullptr: hashed per pass)
     unsigned long long* counts;  // [nsets][npreds]
     unsigned long long* marg;    // [nsets][nterms]
     unsigned long long* nsamp;   // [nsets]
@@ -165,6 +167,9 @@ static_assert(sizeof(ProbeArgs) % 16 == 0, "ProbeArgs is copied in 16-byte words
 uint32_t probe_layout(ProbeArgs& a);
 cudaError_t probe_configure();  // one-time kernel attributes
 cudaError_t probe_launch(const ProbeArgs& a, int grid, cudaStream_t s);
+// The row-set masks of every 128-row slice of a pass's table into a.setmask
+// (writable), for the wide passes that follow to load instead of hashing.
+cudaError_t setmask_launch(const ProbeArgs& a, uint4* out, int sms, cudaStream_t s);
 int probe_occupancy(const ProbeArgs& a);  // CTAs per SM for this kernel and smem size
 
 // ---------------------------------------------------------------- materialised samples

@@ -25,6 +25,7 @@
 // Counters reach the global 64-bit totals once per CTA.  No wait spins without
 // a limit: every mbarrier wait gives up after the context's timeout.
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <stdint.h>
 
 #include "gace_device.cuh"
@@ -86,6 +87,17 @@ __global__ void GACE_WIDE_BOUNDS k_probe_wide(const __grid_constant__ ProbeArgs 
     if (lane < static_cast<int>(A.nsets) && nsr) atomicAdd(&S.ns[lane], nsr);
     __syncthreads();
     flush(A, S, tid, kWideThreads);
+}
+
+// Row-set masks of 128-row slices (one warp per slice, grid-striding), the
+// same masks the wide pass would compute, into out[slice * nsets + set].
+__global__ void __launch_bounds__(256) k_probe_setmask(const __grid_constant__ ProbeArgs A, uint4* out) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t nslices = (A.nrows + kSliceRows - 1) / kSliceRows;
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * (blockDim.x / 32);
+    for (uint64_t sl = static_cast<uint64_t>(blockIdx.x) * (blockDim.x / 32) + (threadIdx.x >> 5); sl < nslices;
+         sl += stride)
+        set_masks<1>(A, sl * kSliceRows, out + sl * A.nsets, lane);
 }
 
 uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
@@ -154,6 +166,14 @@ int probe_occupancy(const ProbeArgs& a) {
         default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_single<true>, kThreads, a.smem_bytes); break;
     }
     return e == cudaSuccess ? n : 0;
+}
+
+cudaError_t setmask_launch(const ProbeArgs& a, uint4* out, int sms, cudaStream_t s) {
+    const uint64_t nslices = (a.nrows + kSliceRows - 1) / kSliceRows;
+    const uint64_t warps = static_cast<uint64_t>(sms) * 64;  // a full SM of warps each
+    const uint64_t grid = (std::min<uint64_t>(nslices, warps) + 7) / 8;
+    k_probe_setmask<<<static_cast<int>(grid ? grid : 1), 256, 0, s>>>(a, out);
+    return cudaGetLastError();
 }
 
 cudaError_t probe_launch(const ProbeArgs& a, int grid, cudaStream_t s) {

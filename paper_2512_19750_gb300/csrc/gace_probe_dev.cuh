@@ -301,8 +301,13 @@ __device__ __forceinline__ void eval_valueset(const SlotDesc& sd, const Vals<NQ>
         klo[i] = v.lo[i];
         khi[i] = is64 ? v.hi[i] : 0u;
         if (sd.dtype == 2 && (klo[i] << 1) == 0) klo[i] = 0;  // -0 equals +0
-        s1[i] = vs_slot(klo[i], khi[i], sd.vm1, sd.tlog);
-        s2[i] = vs_slot(klo[i], khi[i], sd.vm2, sd.tlog);
+        if (is64) {
+            s1[i] = vs_slot(klo[i], khi[i], sd.vm1, sd.tlog);
+            s2[i] = vs_slot(klo[i], khi[i], sd.vm2, sd.tlog);
+        } else {  // vs_slot with a zero high word
+            s1[i] = (klo[i] * sd.vm1) >> (32 - sd.tlog);
+            s2[i] = (klo[i] * sd.vm2) >> (32 - sd.tlog);
+        }
     }
     const uint32_t nvs = sd.iend - sd.rend;
     for (uint32_t g = 0; g < sd.ngroups; ++g) {
@@ -418,12 +423,21 @@ __device__ __forceinline__ uint32_t wide_slices(const ProbeArgs& A, const Smem& 
     // not wait out the memory latency once per column.
     Vals<1> cur;
     bool have = false;  // cur holds the current slice's first column
+    uint4 km = make_uint4(0u, 0u, 0u, 0u);  // this lane's row-set mask of the current slice (lanes < nsets)
+    if (A.setmask && lane < static_cast<int>(A.nsets) && first < end) km = A.setmask[first * A.nsets + lane];
     for (uint64_t sl = first; sl < end; sl += stride) {
         const uint64_t slice0 = sl * kSliceRows;
         if (!have && A.nslots)
             load_vals_global<1>(A.slots[0].ptr, A.slots[0].width, slice0, A.nrows, lane, cur);
         have = false;
-        set_masks<1>(A, slice0, S.keep, lane);
+        if (A.setmask) {  // computed once for every pass of the call; the next slice's loaded a slice ahead
+            if (lane < static_cast<int>(A.nsets)) {
+                S.keep[lane] = km;
+                if (sl + stride < end) km = A.setmask[(sl + stride) * A.nsets + lane];
+            }
+        } else {
+            set_masks<1>(A, slice0, S.keep, lane);
+        }
         __syncwarp();
         // the row sets with a row in this slice (warp-uniform): sparse samples
         // are empty in most slices, and a slice in no set needs no evaluation
