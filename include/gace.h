@@ -53,7 +53,7 @@ typedef enum {
 typedef enum { GACE_I32 = 0, GACE_I64 = 1, GACE_F32 = 2 } gace_dtype;
 typedef enum { GACE_EQ = 0, GACE_RANGE = 1, GACE_IN = 2 } gace_op;
 typedef enum { GACE_FULL = 0, GACE_ROWS = 1, GACE_BLOCKS = 2 } gace_sample_kind;
-typedef enum { GACE_COPY = 0, GACE_BORROW = 1 } gace_load_flags;
+typedef enum { GACE_COPY = 0, GACE_BORROW = 1, GACE_COPY_ON_FIRST_PROBE = 2 } gace_load_flags;
 
 typedef struct gace_ctx gace_ctx;
 
@@ -159,6 +159,15 @@ gace_status gace_destroy(gace_ctx* ctx);
  *   into device memory it owns, 256-byte aligned; counted against the budget.
  * flags == GACE_BORROW: the context keeps the device pointers; the caller keeps
  *   them alive and unchanged until gace_unload.  Every column must be on_device.
+ * flags == GACE_COPY_ON_FIRST_PROBE: host columns the context copies, like
+ *   GACE_COPY, but not before the first call that reads the table; when that
+ *   call is gace_probe_batch, the copy streams in row chunks on a second
+ *   stream while the probe's passes run on the chunks already copied (a probe
+ *   of columns that were not resident costs about the larger of the copy and
+ *   the kernels, not their sum; the paper's prototype copies key columns per
+ *   probe, Section IV-B).  The host columns must stay valid and unchanged
+ *   until that call returns (or the table is unloaded); pinned memory lets the
+ *   copy run at full speed.  Any other call completes the copy first.
  * Device columns are read on the context's stream: work on other streams that
  * writes them must be complete (or ordered before that stream) when they are
  * read.  A GACE_COPY load from device memory waits for the whole device first;

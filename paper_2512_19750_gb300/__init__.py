@@ -107,11 +107,16 @@ def gace_destroy(ctx) -> None:
     check(lib().gace_destroy(ctx), "gace_destroy")
     for key in [k for k in _SUBMITTED if k[0] == _ctx_key(ctx)]:
         del _SUBMITTED[key]
+    for key in [k for k in _LAZY_KEEP if k[0] == _ctx_key(ctx)]:
+        del _LAZY_KEEP[key]
 
 
-def gace_load_columns(ctx, columns, borrow: bool = False) -> int:
+def gace_load_columns(ctx, columns, borrow: bool = False, copy_on_first_probe: bool = False) -> int:
     """Registers a table; columns are torch tensors (CUDA or CPU) or numpy
-    arrays, all of one length.  borrow=True keeps the device pointers."""
+    arrays, all of one length.  borrow=True keeps the device pointers;
+    copy_on_first_probe=True (host columns) defers the copy to the first call
+    that reads the table, which a probe overlaps with its passes (the columns
+    must stay alive and unchanged until then)."""
     n = len(columns)
     arr = (_capi.gace_column * n)()
     keep = []
@@ -142,13 +147,20 @@ def gace_load_columns(ctx, columns, borrow: bool = False) -> int:
         # produce them must have finished
         torch.cuda.synchronize()
     tid = C.c_uint32()
-    check(lib().gace_load_columns(ctx, nrows or 0, n, arr, GACE_BORROW if borrow else GACE_COPY,
+    flags = GACE_BORROW if borrow else (_capi.GACE_COPY_ON_FIRST_PROBE if copy_on_first_probe else GACE_COPY)
+    check(lib().gace_load_columns(ctx, nrows or 0, n, arr, flags,
                                   C.byref(tid)), "gace_load_columns")
+    if copy_on_first_probe:  # the library copies them later: keep them alive until the unload
+        _LAZY_KEEP[(_ctx_key(ctx), int(tid.value))] = (keep, list(columns))
     return int(tid.value)
+
+
+_LAZY_KEEP: dict = {}  # (context, table) -> host columns a deferred copy still reads
 
 
 def gace_unload(ctx, table_id: int) -> None:
     check(lib().gace_unload(ctx, table_id), "gace_unload")
+    _LAZY_KEEP.pop((_ctx_key(ctx), int(table_id)), None)
 
 
 def gace_probe_batch(ctx, table_id: int, preds, samples, dtypes, marginals: bool = False,

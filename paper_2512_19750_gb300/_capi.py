@@ -16,7 +16,7 @@ GACE_ETIMEDOUT, GACE_ENOTFOUND, GACE_EOVERFLOW, GACE_ECUDA = 5, 6, 7, 8
 GACE_I32, GACE_I64, GACE_F32 = 0, 1, 2
 GACE_EQ, GACE_RANGE, GACE_IN = 0, 1, 2
 GACE_FULL, GACE_ROWS, GACE_BLOCKS = 0, 1, 2
-GACE_COPY, GACE_BORROW = 0, 1
+GACE_COPY, GACE_BORROW, GACE_COPY_ON_FIRST_PROBE = 0, 1, 2
 GACE_JOIN_AUTO, GACE_JOIN_HIST_DOT, GACE_JOIN_GATHER = 0, 1, 2
 GACE_REQ_PROBE, GACE_REQ_NDV, GACE_REQ_JOIN = 0, 1, 2
 

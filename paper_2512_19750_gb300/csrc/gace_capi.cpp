@@ -280,9 +280,26 @@ gace_status check_ctx(gace_ctx* ctx) {
     return GACE_OK;
 }
 
-TableRec* find_table(gace_ctx* ctx, uint32_t id) {
+TableRec* find_table_raw(gace_ctx* ctx, uint32_t id) {
     auto it = ctx->tables.find(id);
     return it == ctx->tables.end() ? nullptr : &it->second;
+}
+
+gace_status complete_load(gace_ctx* ctx, TableRec& t) {
+    if (t.pending.empty()) return GACE_OK;
+    for (size_t c = 0; c < t.cols.size(); ++c)
+        if (t.cols[c].bytes)
+            CK(cudaMemcpyAsync(t.cols[c].dptr, t.pending[c], t.cols[c].bytes, cudaMemcpyHostToDevice, ctx->stream));
+    // the served form's stream reads tables too: the copy is complete on return
+    CK(cudaStreamSynchronize(ctx->stream));
+    t.pending.clear();
+    return GACE_OK;
+}
+
+TableRec* find_table(gace_ctx* ctx, uint32_t id) {
+    TableRec* t = find_table_raw(ctx, id);
+    if (t && !t->pending.empty() && complete_load(ctx, *t) != GACE_OK) return nullptr;
+    return t;
 }
 
 gace_status read_status(gace_ctx* ctx, unsigned int st) {
@@ -1113,7 +1130,46 @@ void assemble_probe(const ProbePlan& plan, const ProbeRequest& r,
         marg_of);
 }
 
-gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts) {
+namespace {
+
+// The launch of one pass over rows [row0, row0 + rows) of its table (all of
+// it when rows == 0): the pass's arguments narrowed to those rows (row ids
+// stay table-global for the samples' hashes), the grid sized for them.
+gace_status launch_pass(gace_ctx* ctx, const Pass& ps, uint64_t nrows_all, uint64_t row0, uint64_t rows,
+                        const uint4* setmask) {
+    ProbeArgs a = ps.args;
+    if (rows) {
+        a.nrows = rows;
+        a.row0 = row0;
+        for (uint32_t s = 0; s < a.nslots; ++s)
+            a.slots[s].ptr = static_cast<const unsigned char*>(a.slots[s].ptr) + row0 * a.slots[s].width;
+        a.ntiles = (rows + a.tile_rows - 1) / a.tile_rows;
+        a.nstaged = a.stage_bytes ? rows / a.tile_rows : 0;
+    }
+    if (!a.narrow && setmask) a.setmask = setmask;
+    const int occ = probe_occupancy(a);
+    if (occ < 1)
+        return fail(GACE_ECUDA, "probe kernel cannot be resident with %u bytes of shared memory", a.smem_bytes);
+    // work units: tiles (narrow) or warp sweeps of 128-row slices (wide)
+    const uint64_t n = a.nrows;
+    const uint64_t unit_rows = a.narrow ? a.tile_rows : static_cast<uint64_t>(kSliceRows) * a.nwarps;
+    const uint64_t units = (n + unit_rows - 1) / unit_rows;
+    uint64_t grid = static_cast<uint64_t>(ctx->sms) * occ;
+    if (ctx->max_ctas && grid > ctx->max_ctas) grid = ctx->max_ctas;
+    if (grid > units) grid = units;
+    if (grid < 1) grid = 1;
+    // each CTA keeps 32-bit row counters
+    while ((units + grid - 1) / grid * unit_rows >= (1ull << 31)) grid *= 2;
+    if (grid > 0x7FFFFFFFull) return fail(GACE_EINVAL, "table too large for one probe grid");
+    (void)nrows_all;
+    CK(ctx->traced(a.narrow ? "probe_narrow" : "probe_wide", n, n * ps.rowbytes, n * ps.ops_per_row,
+                   [&] { return probe_launch(a, static_cast<int>(grid), ctx->stream); }));
+    return GACE_OK;
+}
+
+}  // namespace
+
+gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts, TableRec* lazy) {
     // workspace: status | per pass of every part: inputs, outputs
     Ws ws;
     const uint64_t status_off = ws.take(256);
@@ -1124,8 +1180,12 @@ gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts) {
             ps.out_off = ws.take(ps.out_bytes);
             any_pass = true;
         }
+    // A table whose copy is pending (one part) streams in chunks of rows, a
+    // multiple of every pass's tile; each chunk runs every pass.
+    const uint64_t chunk_rows =
+        lazy ? round_up(std::max<uint64_t>(lazy->nrows / kLoadChunks, 1ull << 20), 1ull << 16) : 0;
     // A part with several wide passes over hashed row sets computes every
-    // slice's row-set masks once, for all its passes to load.
+    // slice's row-set masks once (per chunk), for all its passes to load.
     std::vector<uint64_t> mask_off(parts.size(), 0);
     for (size_t i = 0; i < parts.size(); ++i) {
         const ProbePlan& pl = parts[i].plan;
@@ -1134,7 +1194,8 @@ gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts) {
         bool hashed = false;
         for (const auto& sp : pl.sets) hashed = hashed || sp.d.mode == 2;
         if (wide >= 2 && hashed) {
-            const uint64_t nslices = (parts[i].tab->nrows + kSliceRows - 1) / kSliceRows;
+            const uint64_t rows = lazy ? std::min<uint64_t>(chunk_rows, parts[i].tab->nrows) : parts[i].tab->nrows;
+            const uint64_t nslices = (rows + kSliceRows - 1) / kSliceRows;
             mask_off[i] = ws.take(nslices * pl.sets.size() * 16);
         }
     }
@@ -1154,42 +1215,68 @@ gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts) {
             for (auto& ps : pp.plan.passes) CK(cudaMemsetAsync(dws + ps.out_off, 0, ps.out_bytes, ctx->stream));
     }
     CK(cudaMemsetAsync(dws + status_off, 0, 256, ctx->stream));
-    for (size_t i = 0; i < parts.size(); ++i) {
-        auto& pp = parts[i];
-        const TableRec* tab = pp.tab;
-        if (mask_off[i]) {
-            uint4* masks = reinterpret_cast<uint4*>(dws + mask_off[i]);
-            const ProbeArgs& a0 = pp.plan.passes.front().args;
-            const uint64_t n = tab->nrows;
-            CK(ctx->traced("probe_setmask", n, 0, n, [&] { return setmask_launch(a0, masks, ctx->sms, ctx->stream); }));
-            for (auto& ps : pp.plan.passes)
-                if (!ps.args.narrow) ps.args.setmask = masks;
+    if (lazy) {
+        // every chunk's copy on the copy stream, all at once (they run back to
+        // back); the context stream waits for each before that chunk's passes
+        if (!ctx->copy_stream) CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+        const uint64_t n = lazy->nrows;
+        const uint64_t nchunks = (n + chunk_rows - 1) / chunk_rows;
+        while (ctx->chunk_events.size() < nchunks) {
+            cudaEvent_t ev = nullptr;
+            CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            ctx->chunk_events.push_back(ev);
         }
-        for (auto& ps : pp.plan.passes) {
-            const int occ = probe_occupancy(ps.args);
-            if (occ < 1)
-                return fail(GACE_ECUDA, "probe kernel cannot be resident with %u bytes of shared memory",
-                            ps.args.smem_bytes);
-            // work units: tiles (narrow) or 8-slice warp sweeps (wide)
-            const uint64_t unit_rows =
-                ps.args.narrow ? ps.args.tile_rows : static_cast<uint64_t>(kSliceRows) * ps.args.nwarps;
-            const uint64_t units = (tab->nrows + unit_rows - 1) / unit_rows;
-            uint64_t grid = static_cast<uint64_t>(ctx->sms) * occ;
-            if (ctx->max_ctas && grid > ctx->max_ctas) grid = ctx->max_ctas;
-            if (grid > units) grid = units;
-            if (grid < 1) grid = 1;
-            // each CTA keeps 32-bit row counters
-            while ((units + grid - 1) / grid * unit_rows >= (1ull << 31)) grid *= 2;
-            if (grid > 0x7FFFFFFFull) return fail(GACE_EINVAL, "table too large for one probe grid");
-            const uint64_t n = tab->nrows;
-            CK(ctx->traced(ps.args.narrow ? "probe_narrow" : "probe_wide", n, n * ps.rowbytes, n * ps.ops_per_row,
-                           [&] { return probe_launch(ps.args, static_cast<int>(grid), ctx->stream); }));
+        // the copy stream starts after what the context stream has queued (the
+        // columns' stream-ordered allocations)
+        CK(cudaEventRecord(ctx->chunk_events[0], ctx->stream));
+        CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->chunk_events[0], 0));
+        for (uint64_t k = 0; k < nchunks; ++k) {
+            const uint64_t r0 = k * chunk_rows, rows = std::min(chunk_rows, n - r0);
+            for (size_t c = 0; c < lazy->cols.size(); ++c) {
+                const uint64_t w = dtype_width(lazy->cols[c].dtype);
+                CK(cudaMemcpyAsync(static_cast<unsigned char*>(lazy->cols[c].dptr) + r0 * w,
+                                   static_cast<const unsigned char*>(lazy->pending[c]) + r0 * w, rows * w,
+                                   cudaMemcpyHostToDevice, ctx->copy_stream));
+            }
+            CK(cudaEventRecord(ctx->chunk_events[k], ctx->copy_stream));
+        }
+        auto& pp = parts.front();
+        for (uint64_t k = 0; k < nchunks; ++k) {
+            const uint64_t r0 = k * chunk_rows, rows = std::min(chunk_rows, n - r0);
+            CK(cudaStreamWaitEvent(ctx->stream, ctx->chunk_events[k], 0));
+            uint4* masks = nullptr;
+            if (mask_off[0]) {
+                masks = reinterpret_cast<uint4*>(dws + mask_off[0]);
+                ProbeArgs a0 = pp.plan.passes.front().args;
+                a0.nrows = rows;
+                a0.row0 = r0;
+                CK(ctx->traced("probe_setmask", rows, 0, rows,
+                               [&] { return setmask_launch(a0, masks, ctx->sms, ctx->stream); }));
+            }
+            for (auto& ps : pp.plan.passes)
+                if (gace_status st = launch_pass(ctx, ps, n, r0, rows, masks)) return st;
+        }
+    } else {
+        for (size_t i = 0; i < parts.size(); ++i) {
+            auto& pp = parts[i];
+            const TableRec* tab = pp.tab;
+            uint4* masks = nullptr;
+            if (mask_off[i]) {
+                masks = reinterpret_cast<uint4*>(dws + mask_off[i]);
+                const ProbeArgs& a0 = pp.plan.passes.front().args;
+                const uint64_t n = tab->nrows;
+                CK(ctx->traced("probe_setmask", n, 0, n,
+                               [&] { return setmask_launch(a0, masks, ctx->sms, ctx->stream); }));
+            }
+            for (auto& ps : pp.plan.passes)
+                if (gace_status st = launch_pass(ctx, ps, tab->nrows, 0, 0, masks)) return st;
         }
     }
     const uint64_t rb_hi = any_pass ? ws.off : status_off + 256;
     CK(cudaMemcpyAsync(pin + status_off, dws + status_off, rb_hi - status_off, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->collect();
+    if (lazy) lazy->pending.clear();  // the stream waited for every chunk's copy
     if (gace_status st = read_status(ctx, *reinterpret_cast<unsigned int*>(pin + status_off))) return st;
     for (auto& pp : parts) {
         std::vector<const unsigned long long*> outs;
@@ -1304,6 +1391,8 @@ gace_status gace_destroy(gace_ctx* ctx) {
                 if (j) cudaEventDestroy(j);
         }
         if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+        if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+        for (cudaEvent_t e : ctx->chunk_events) cudaEventDestroy(e);
         if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     }
     delete ctx;
@@ -1315,7 +1404,7 @@ gace_status gace_load_columns(gace_ctx* ctx, uint64_t nrows, uint32_t ncols, con
     if (gace_status s = check_ctx(ctx)) return s;
     if (!cols || !table_id_out) return fail(GACE_EINVAL, "cols or table_id_out is NULL");
     if (ncols == 0 || ncols > 64) return fail(GACE_EINVAL, "ncols %u outside 1..64", ncols);
-    if (flags > GACE_BORROW) return fail(GACE_EINVAL, "flags %u is neither COPY nor BORROW", flags);
+    if (flags > GACE_COPY_ON_FIRST_PROBE) return fail(GACE_EINVAL, "flags %u is not a gace_load_flags value", flags);
     if (nrows > (1ull << 40)) return fail(GACE_EINVAL, "nrows %llu above 2^40", (unsigned long long)nrows);
     for (uint32_t c = 0; c < ncols; ++c) {
         if (cols[c].dtype < GACE_I32 || cols[c].dtype > GACE_F32)
@@ -1323,7 +1412,10 @@ gace_status gace_load_columns(gace_ctx* ctx, uint64_t nrows, uint32_t ncols, con
         if (nrows > 0 && !cols[c].data) return fail(GACE_EINVAL, "column %u data is NULL", c);
         if (flags == GACE_BORROW && !cols[c].on_device)
             return fail(GACE_EINVAL, "GACE_BORROW needs device columns (column %u is on the host)", c);
+        if (flags == GACE_COPY_ON_FIRST_PROBE && cols[c].on_device)
+            return fail(GACE_EINVAL, "GACE_COPY_ON_FIRST_PROBE needs host columns (column %u is on the device)", c);
     }
+    const bool lazy = flags == GACE_COPY_ON_FIRST_PROBE;
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
     if (flags == GACE_COPY && nrows > 0) {
@@ -1336,7 +1428,7 @@ gace_status gace_load_columns(gace_ctx* ctx, uint64_t nrows, uint32_t ncols, con
     TableRec tab;
     tab.nrows = nrows;
     uint64_t need = 0;
-    if (flags == GACE_COPY)
+    if (flags != GACE_BORROW)
         for (uint32_t c = 0; c < ncols; ++c) need += round_up(nrows * dtype_width(cols[c].dtype) + 16, 256);
     if (!ctx->fits(need))
         return fail(GACE_ENOMEM, "table of %llu bytes exceeds the HBM budget (%llu of %llu used)",
@@ -1360,7 +1452,9 @@ gace_status gace_load_columns(gace_ctx* ctx, uint64_t nrows, uint32_t ncols, con
             }
             r.owned = true;
             tab.owned_bytes += alloc;
-            if (bytes) {
+            if (lazy) {
+                tab.pending.push_back(cols[c].data);  // copied by the first call that reads the table
+            } else if (bytes) {
                 e = cudaMemcpyAsync(r.dptr, cols[c].data, bytes,
                                     cols[c].on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                     ctx->stream);
@@ -1430,7 +1524,7 @@ gace_status gace_probe_batch(gace_ctx* ctx, uint32_t table_id, const gace_sample
     r.term_marginals = term_marginals;
     if (gace_status s = check_probe_request(r)) return s;
     std::lock_guard<std::mutex> lk(ctx->mu);
-    TableRec* tab = find_table(ctx, table_id);
+    TableRec* tab = find_table_raw(ctx, table_id);  // a pending copy may overlap the probe
     if (!tab) return fail(GACE_ENOTFOUND, "table %u is not loaded", table_id);
     DeviceGuard g(ctx->device);
     for (uint32_t s = 0; s < nsamples; ++s) {
@@ -1455,8 +1549,9 @@ gace_status gace_probe_batch(gace_ctx* ctx, uint32_t table_id, const gace_sample
         parts.back().tab = tab;
         parts.back().r = r;
         if (gace_status st = plan_probe(ctx, *tab, r, false, parts.back().plan, kWideWarps)) return st;
-        return run_planned(ctx, parts);
+        return run_planned(ctx, parts, tab->pending.empty() ? nullptr : tab);
     }
+    if (gace_status st = complete_load(ctx, *tab)) return st;
     // one part per table: the base table with the samples that are not
     // resident, and each resident sample table with one full scan; each part
     // writes its own results, scattered to the caller's rows afterwards

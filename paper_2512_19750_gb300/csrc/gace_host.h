@@ -74,6 +74,7 @@ struct TableRec {
     std::vector<ColumnRec> cols;
     uint64_t owned_bytes = 0;
     uint32_t sample_of = 0;  // a materialised sample: the table it was drawn from (0: none)
+    std::vector<const void*> pending;  // GACE_COPY_ON_FIRST_PROBE: host sources not yet copied
     bool in_store = false;   // owned by the resident store (evictable)
 };
 
@@ -148,6 +149,10 @@ struct gace_ctx {
     // (a table loaded and unloaded step after step does not map its pages
     // again each time) and returns it to the device when the context ends.
     cudaMemPool_t pool = nullptr;
+    // copies of tables loaded with GACE_COPY_ON_FIRST_PROBE, in chunks, and
+    // the events the probe's passes wait for
+    cudaStream_t copy_stream = nullptr;
+    std::vector<cudaEvent_t> chunk_events;
 
     cudaError_t alloc_async(void** p, uint64_t bytes) {
         return pool ? cudaMallocFromPoolAsync(p, bytes, pool, stream) : cudaMallocAsync(p, bytes, stream);
@@ -400,7 +405,12 @@ struct Ws {
 };
 
 gace_status check_ctx(gace_ctx* ctx);
+// A loaded table (its pending copy completed first), or nullptr.
 TableRec* find_table(gace_ctx* ctx, uint32_t id);
+// The same without completing a pending copy.
+TableRec* find_table_raw(gace_ctx* ctx, uint32_t id);
+// Copies a table's pending host sources (GACE_COPY_ON_FIRST_PROBE) and waits.
+gace_status complete_load(gace_ctx* ctx, TableRec& t);
 gace_status read_status(gace_ctx* ctx, unsigned int st);
 
 // The arguments of one probe (gace_probe_batch, or a probe request of a batch).
@@ -451,7 +461,10 @@ struct PlannedProbe {
 };
 // Runs planned probes with one upload, their passes' launches, one read-back
 // and a wait on the context stream, then assembles each part's results.
-gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts);
+// lazy: the one part's table, whose pending copy (GACE_COPY_ON_FIRST_PROBE)
+// then streams in kLoadChunks row chunks overlapped with the passes.
+gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts, TableRec* lazy = nullptr);
+constexpr uint64_t kLoadChunks = 12;
 // Results from the passes' counters (host copies, one pointer per pass).
 void assemble_probe(const ProbePlan& plan, const ProbeRequest& r,
                     const std::vector<const unsigned long long*>& pass_out);

@@ -111,6 +111,7 @@ struct SetDesc {
 
 struct alignas(16) ProbeArgs {
     uint64_t nrows;
+    uint64_t row0;          // table-global id of the first row scanned (rows are hashed by global id)
     uint64_t ntiles;        // ceil(nrows / tile_rows)
     uint64_t nstaged;       // tiles loaded by bulk copy (full tiles when staged)
     uint32_t tile_rows;     // multiple of kSliceRows * kProbeWarps (narrow kernel)

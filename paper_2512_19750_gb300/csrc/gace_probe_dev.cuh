@@ -112,21 +112,24 @@ __device__ __forceinline__ void set_masks(const ProbeArgs& A, uint64_t slice0, u
             for (int i = 0; i < R; ++i) k[i] = false;
         } else {
             if (!sd.share_prev) {
+                // membership hashes the table-global row (or block) id
                 if (sd.kind == 1) {
 #pragma unroll
-                    for (int i = 0; i < R; ++i) hsh[i] = splitmix64(row[i] ^ sd.seedhash);
+                    for (int i = 0; i < R; ++i) hsh[i] = splitmix64((A.row0 + row[i]) ^ sd.seedhash);
                 } else if (sd.block_shift >= 2) {
-                    // the four rows of a quad (a multiple of 4 apart from 0) share one block
+                    // the four rows of a quad (a multiple of 4 apart from 0, and row0 a
+                    // multiple of 4) share one block
 #pragma unroll
                     for (int h = 0; h < NQ; ++h) {
-                        const uint64_t hb = splitmix64((row[4 * h] >> sd.block_shift) ^ sd.seedhash);
+                        const uint64_t hb = splitmix64(((A.row0 + row[4 * h]) >> sd.block_shift) ^ sd.seedhash);
 #pragma unroll
                         for (int r = 0; r < 4; ++r) hsh[4 * h + r] = hb;
                     }
                 } else {
 #pragma unroll
                     for (int i = 0; i < R; ++i) {
-                        const uint64_t b = sd.block_shift >= 0 ? (row[i] >> sd.block_shift) : (row[i] / sd.block_rows);
+                        const uint64_t g = A.row0 + row[i];
+                        const uint64_t b = sd.block_shift >= 0 ? (g >> sd.block_shift) : (g / sd.block_rows);
                         hsh[i] = splitmix64(b ^ sd.seedhash);
                     }
                 }

@@ -39,8 +39,9 @@ __device__ __forceinline__ void issue_tile(const ProbeArgs& A, unsigned char* st
 // set of a pass that skips tiles is a block sample): the tile's blocks are
 // hashed as the per-row membership test hashes them.
 __device__ __forceinline__ bool probe_tile_live(const ProbeArgs& A, uint64_t tile) {
-    const uint64_t r0 = tile * A.tile_rows;
-    const uint64_t r1 = (r0 + A.tile_rows < A.nrows ? r0 + A.tile_rows : A.nrows) - 1;
+    const uint64_t l0 = tile * A.tile_rows;
+    const uint64_t r0 = A.row0 + l0;  // table-global ids of the tile's first and last rows
+    const uint64_t r1 = A.row0 + (l0 + A.tile_rows < A.nrows ? l0 + A.tile_rows : A.nrows) - 1;
     for (uint32_t q = 0; q < A.nsets; ++q) {
         const SetDesc& sd = A.sets[q];
         if (sd.kind != 2 || sd.mode != 2) return true;
@@ -280,8 +281,8 @@ __device__ __forceinline__ bool single_run(const ProbeArgs& A, const Smem& S, in
 #pragma unroll
             for (int i = 0; i < R; ++i) {
                 const uint64_t row = slice0 + 128u * (i / 4) + 4u * lane + (i % 4);
-                uint64_t x = row;
-                if (sd.kind == 2) x = sd.block_shift >= 0 ? (row >> sd.block_shift) : (row / sd.block_rows);
+                uint64_t x = A.row0 + row;  // hashed by table-global id
+                if (sd.kind == 2) x = sd.block_shift >= 0 ? (x >> sd.block_shift) : (x / sd.block_rows);
                 if (row < A.nrows && splitmix64(x ^ sd.seedhash) < sd.thresh) base |= 1u << i;
             }
         } else if (!tile_full) {
