@@ -61,7 +61,7 @@ def parse_args():
     ap.add_argument("--serve-cap", type=int, default=20000, help="requests per rate at most")
     ap.add_argument("--case", default=None,
                     choices=["narrow_i32", "narrow_4xi32", "narrow_rows1pct", "wide_batch", "hll_i32",
-                             "join_gather", "batch_mix", "batch_probes", "join_skew"],
+                             "join_gather", "batch_mix", "batch_probes", "join_skew", "materialize"],
                     help="profiling driver: run one kernel family three times on a small (--rows) case")
     return ap.parse_args()
 
@@ -984,6 +984,11 @@ def run_case(args):
     elif args.case == "hll_i32":
         for _ in range(3):
             g.gace_ndv(ctx, tid, 0, 14, 42)
+    elif args.case == "materialize":
+        from workloads import BLOCKS
+        for smp in (Sample(ROWS, 0.01, 42), Sample(BLOCKS, 0.01, 42, 4096), Sample(ROWS, 0.1, 42)):
+            sid, _ = g.gace_sample_materialize(ctx, tid, smp)
+            g.gace_unload(ctx, sid)
     print(json.dumps({"case": args.case, "rows": args.rows}))
     g.gace_destroy(ctx)
 
