@@ -199,7 +199,13 @@ uint32_t ColPool::words() const {
         while ((1ull << tlog) < kVsSlotsPerEntry * most) ++tlog;
         w += static_cast<uint64_t>((nvs + 31) / 32) * (1ull << tlog) * (is64 ? 4u : 2u);
     }
-    w += static_cast<uint64_t>(trees) * (is64 ? kTreeWords64 : kTreeWords32);
+    if (rstride) {  // rank-coded: the smaller of the column-rank tables and a byte map + local tables
+        const uint64_t g = (nr + 31) / 32, ml = std::min<uint64_t>(2ull * nr, rstride - 1);
+        const uint64_t direct = g * rstride, mapped = (rstride + 3) / 4 + g * (ml + 1);
+        w += ml <= 255 ? std::min(direct, mapped) : direct;
+    } else {
+        w += static_cast<uint64_t>(trees) * (is64 ? kTreeWords64 : kTreeWords32);
+    }
     return w > 0xFFFFFFFFull ? 0xFFFFFFFFu : static_cast<uint32_t>(w);
 }
 
@@ -439,7 +445,8 @@ bool build_cuckoo(const std::vector<std::vector<VsEntry>>& keys, bool is64, uint
 // Builds the device form of a pass and the probe arguments (without pointers).
 gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::vector<NTerm>& uterms,
                        const std::vector<std::vector<uint32_t>>& pred_u,
-                       const std::vector<SetPlan>& sets, bool want_marg, bool force_wide, uint32_t wide_warps) {
+                       const std::vector<SetPlan>& sets, bool want_marg, bool force_wide, uint32_t wide_warps,
+                       std::vector<RankCode>& codes, const std::vector<int32_t>& code_of_col) {
     // Narrow passes (at most 32 predicates and terms) evaluate IN lists by
     // compare; wide passes look up every EQ and IN term of a column in that
     // column's hash tables.  Order: by column, ranges (or, wide, multi-value
@@ -473,7 +480,13 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
         }
         ps.dterms.push_back(make_devterm(t, poff));
         ps.ops_per_row += term_cost(t);
-        if (nslots == 0 || ps.slots.back().first != t.col) {
+        // a rank-coded column's EQ/IN terms take a slot of their own in a wide
+        // pass (its ranges' slot reads ranks, not values)
+        const bool coded = !narrow && !code_of_col.empty() && code_of_col[t.col] >= 0;
+        const bool split = coded && nslots > 0 && ps.slots.back().first == t.col && valueset(t) &&
+                           A.slots[nslots - 1].iend == A.slots[nslots - 1].rend &&
+                           A.slots[nslots - 1].rend > A.slots[nslots - 1].rbeg;
+        if (nslots == 0 || ps.slots.back().first != t.col || split) {
             if (nslots == kMaxSlots) return fail(GACE_EINVAL, "a pass references more than %d columns", kMaxSlots);
             ps.slots.push_back({t.col, i});
             SlotDesc& sd = A.slots[nslots++];
@@ -550,10 +563,74 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
         }
     }
     if (!narrow) {
+        // rank-coded columns: per group of 32 range terms, the mask of the
+        // group's terms that hold each rank's keys (rank r: the keys from
+        // endpoint r-1 up to endpoint r; rank 0 lies below every interval)
+        for (uint32_t s = 0; s < nslots; ++s) {
+            SlotDesc& sd = A.slots[s];
+            const uint32_t nr = sd.rend - sd.rbeg;
+            const uint32_t col = ps.slots[s].first;
+            if (nr == 0 || code_of_col.empty() || code_of_col[col] < 0) continue;
+            if (sd.iend != sd.rend) return fail(GACE_EINVAL, "rank-coded slot of column %u holds EQ/IN terms", col);
+            RankCode& rc = codes[code_of_col[col]];
+            rc.used = true;
+            const uint32_t m = static_cast<uint32_t>(rc.keys.size());
+            // each term's endpoints inside its interval, as column endpoint
+            // indices [r0, r1), and the slot's own endpoints (local), by index
+            std::vector<std::pair<uint32_t, uint32_t>> span(nr);
+            std::vector<uint32_t> local;
+            for (uint32_t k = 0; k < nr; ++k) {
+                const auto iv = range_keys(uterms[order[sd.rbeg + k]], sd.dtype);
+                const uint32_t r0 = static_cast<uint32_t>(
+                    std::lower_bound(rc.keys.begin(), rc.keys.end(), iv.first) - rc.keys.begin());
+                const uint32_t r1 = static_cast<uint32_t>(
+                    std::upper_bound(rc.keys.begin(), rc.keys.end(), iv.second) - rc.keys.begin());
+                span[k] = {r0, r1};
+                local.push_back(r0);
+                if (r1 < m) local.push_back(r1);
+            }
+            std::sort(local.begin(), local.end());
+            local.erase(std::unique(local.begin(), local.end()), local.end());
+            const uint32_t ml = static_cast<uint32_t>(local.size());
+            sd.rtree = nr;
+            sd.rgroups = (nr + 31) / 32;
+            // a byte map from column rank to local rank when it takes less room
+            const uint64_t direct = static_cast<uint64_t>(sd.rgroups) * (m + 1);
+            const uint64_t mapped = (m + 1 + 3) / 4 + static_cast<uint64_t>(sd.rgroups) * (ml + 1);
+            const bool use_map = ml <= 255 && mapped < direct;
+            if (use_map) {
+                sd.rmap = static_cast<uint32_t>(ps.pool.size()) + 1;
+                ps.pool.resize(ps.pool.size() + (m + 1 + 3) / 4, 0u);
+                unsigned char* map = reinterpret_cast<unsigned char*>(ps.pool.data() + sd.rmap - 1);
+                // column rank r (endpoints 0 .. r-1 <= key): the local endpoints among them
+                uint32_t j = 0;
+                for (uint32_t r = 0; r <= m; ++r) {
+                    while (j < ml && local[j] < r) ++j;
+                    map[r] = static_cast<unsigned char>(j);
+                }
+            }
+            sd.rstride = use_map ? ml + 1 : m + 1;
+            sd.roff = static_cast<uint32_t>(ps.pool.size());
+            ps.pool.resize(ps.pool.size() + static_cast<size_t>(sd.rgroups) * sd.rstride, 0u);
+            // mask of rank r: the terms holding the (r-1)-th endpoint (local or column)
+            for (uint32_t k = 0; k < nr; ++k) {
+                uint32_t a = span[k].first, b = span[k].second;
+                if (use_map) {
+                    a = static_cast<uint32_t>(std::lower_bound(local.begin(), local.end(), a) - local.begin());
+                    b = static_cast<uint32_t>(std::lower_bound(local.begin(), local.end(), b) - local.begin());
+                }
+                uint32_t* masks = ps.pool.data() + sd.roff + static_cast<size_t>(k / 32) * sd.rstride;
+                for (uint32_t r = a; r < b; ++r) masks[r + 1] |= 1u << (k % 32);
+            }
+        }
+        A.ranks_only = 1;
+        for (uint32_t s = 0; s < nslots; ++s)
+            if (A.slots[s].rend > A.slots[s].rbeg && !A.slots[s].rstride) A.ranks_only = 0;
         // one interval tree per full group of 32 range terms of a column (and
         // per last group of at least kTreeMin); fewer terms are cheaper by compare
         for (uint32_t s = 0; s < nslots; ++s) {
             SlotDesc& sd = A.slots[s];
+            if (sd.rstride) continue;
             const uint32_t all = sd.rend - sd.rbeg, rem = all % 32;
             const uint32_t nr = all - (rem >= kTreeMin ? 0 : rem);
             sd.rtree = nr;
@@ -812,8 +889,35 @@ gace_status check_probe_request(const ProbeRequest& r) {
     return GACE_OK;
 }
 
+// The search tree of a rank-coded column's endpoints (RankArgs): the
+// perfect tree whose in-order is the sorted keys padded with the largest key,
+// in level order (node i of level L, 2^L <= i < 2^(L+1), is in-order element
+// ((2 (i - 2^L) + 1) << (levels - 1 - L)) - 1).
+void build_rank_tree(RankCode& rc) {
+    const bool is64 = rc.dtype == GACE_I64;
+    const uint64_t kmax = is64 ? ~0ull : 0xFFFFFFFFull;
+    const uint32_t m = static_cast<uint32_t>(rc.keys.size());
+    uint32_t levels = 1;
+    while ((1u << levels) - 1 < m) ++levels;
+    rc.levels = levels;
+    const uint32_t nkeys = (1u << levels) - 1;
+    std::vector<uint64_t> sorted(rc.keys);
+    sorted.resize(nkeys, kmax);
+    rc.tree.assign(is64 ? 2 * nkeys : nkeys, 0u);
+    for (uint32_t L = 0; L < levels; ++L)
+        for (uint32_t i = 1u << L; i < (2u << L); ++i) {
+            const uint64_t key = sorted[((2 * (i - (1u << L)) + 1) << (levels - 1 - L)) - 1];
+            if (is64) {
+                rc.tree[2 * (i - 1)] = static_cast<uint32_t>(key);
+                rc.tree[2 * (i - 1) + 1] = static_cast<uint32_t>(key >> 32);
+            } else {
+                rc.tree[i - 1] = static_cast<uint32_t>(key);
+            }
+        }
+}
+
 gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r, bool force_wide,
-                       ProbePlan& plan, uint32_t wide_warps) {
+                       ProbePlan& plan, uint32_t wide_warps, bool rank_code) {
     plan = ProbePlan();
     plan.tab = &tab;
     const uint32_t nsamples = r.nsamples, nterms = r.nterms, npreds = r.npreds;
@@ -914,6 +1018,34 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
     }
     plan.want_marg = r.term_marginals != nullptr || any_pair;
 
+    // rank coding: every column's distinct range endpoints over the whole plan
+    plan.code_of_col.assign(tab.cols.size(), -1);
+    if (rank_code) {
+        std::vector<std::vector<uint64_t>> ends(tab.cols.size());
+        for (const NTerm& t : uterms) {
+            if (is_in_kind(t.kind) || term_cost(t) != 2) continue;  // ranges of several values only
+            const uint32_t dt = static_cast<uint32_t>(tab.cols[t.col].dtype);
+            const uint64_t kmax = dt == GACE_I64 ? ~0ull : 0xFFFFFFFFull;
+            const auto iv = range_keys(t, dt);
+            ends[t.col].push_back(iv.first);
+            if (iv.second < kmax) ends[t.col].push_back(iv.second + 1);
+        }
+        for (uint32_t c = 0; c < ends.size(); ++c) {
+            std::vector<uint64_t>& e = ends[c];
+            if (e.empty()) continue;
+            std::sort(e.begin(), e.end());
+            e.erase(std::unique(e.begin(), e.end()), e.end());
+            if (e.size() > kRankPlanMax) continue;
+            RankCode rc;
+            rc.col = c;
+            rc.dtype = static_cast<uint32_t>(tab.cols[c].dtype);
+            rc.keys = std::move(e);
+            build_rank_tree(rc);
+            plan.code_of_col[c] = static_cast<int32_t>(plan.codes.size());
+            plan.codes.push_back(std::move(rc));
+        }
+    }
+
     // pack predicates into passes that fit the kernel's shared-memory tables
     std::vector<Pass>& passes = plan.passes;
     std::vector<int32_t> u_pass(uterms.size(), -1);
@@ -960,10 +1092,13 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
                 while (k < touched.size() && touched[k].first != col) ++k;
                 if (k == touched.size()) {
                     ColPool c;
-                    if (has_col[col])
+                    if (has_col[col]) {
                         c = cols_cur[col];
-                    else
+                    } else {
                         c.is64 = tab.cols[col].dtype == GACE_I64;
+                        const int32_t code = plan.code_of_col[col];
+                        c.rstride = code < 0 ? 0u : static_cast<uint32_t>(plan.codes[code].keys.size()) + 1;
+                    }
                     touched.emplace_back(col, c);
                 }
                 touched[k].second.add(uterms[u]);
@@ -972,9 +1107,11 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
                 total += kv.second.words() - (has_col[kv.first] ? cols_cur[kv.first].words() : 0u);
             return total;
         };
+        // slots of a wide pass: a rank-coded column may take two (ranges, EQ/IN)
+        auto col_slots = [&](uint32_t col) -> size_t { return plan.code_of_col[col] >= 0 ? 2 : 1; };
         auto new_cols = [&](const Touched& touched) {
             size_t n = 0;
-            for (const auto& kv : touched) n += has_col[kv.first] ? 0 : 1;
+            for (const auto& kv : touched) n += has_col[kv.first] ? 0 : col_slots(kv.first);
             return n;
         };
         auto commit = [&](const std::vector<uint32_t>& add, const Touched& touched, uint64_t total) {
@@ -986,7 +1123,7 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
             for (const auto& kv : touched) {
                 if (!has_col[kv.first]) {
                     has_col[kv.first] = 1;
-                    ++ncols_cur;
+                    ncols_cur += col_slots(kv.first);
                 }
                 cols_cur[kv.first] = kv.second;
             }
@@ -1027,7 +1164,7 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
                 add.assign(1, u);
                 touched.clear();
                 uint64_t total = with_terms(add, touched);
-                const size_t ncols = ncols_cur + (has_col[uterms[u].col] ? 0 : 1);
+                const size_t ncols = ncols_cur + (has_col[uterms[u].col] ? 0 : col_slots(uterms[u].col));
                 if (!cur.uterms.empty() &&
                     (cur.uterms.size() + 1 > kPassTerms || total > kPassPool ||
                      ncols > static_cast<size_t>(kMaxSlots) ||
@@ -1046,9 +1183,12 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
         if (s.d.mode == 2) need_ns = true;
     if (sets.empty()) passes.clear();  // every sample is empty: nothing to count
     if (passes.empty() && need_ns) passes.push_back(Pass());  // counts sample rows only
+    // the passes of a split batch are all wide: a small last pass in the
+    // narrow layout would evaluate its IN lists by compare
+    const bool all_wide = force_wide || passes.size() > 1;
     for (auto& ps : passes) {
-        if (gace_status st = build_pass(ctx, tab, ps, uterms, plan.pred_u, sets, plan.want_marg, force_wide,
-                                        wide_warps))
+        if (gace_status st = build_pass(ctx, tab, ps, uterms, plan.pred_u, sets, plan.want_marg, all_wide,
+                                        wide_warps, plan.codes, plan.code_of_col))
             return st;
         pass_sizes(ps);
     }
@@ -1135,8 +1275,9 @@ namespace {
 // The launch of one pass over rows [row0, row0 + rows) of its table (all of
 // it when rows == 0): the pass's arguments narrowed to those rows (row ids
 // stay table-global for the samples' hashes), the grid sized for them.
-gace_status launch_pass(gace_ctx* ctx, const Pass& ps, uint64_t nrows_all, uint64_t row0, uint64_t rows,
-                        const uint4* setmask) {
+// ranks: per column, the ranks of the rows launched (rank-coded slots).
+gace_status launch_pass(gace_ctx* ctx, const Pass& ps, uint64_t row0, uint64_t rows, const uint4* setmask,
+                        const std::vector<const uint16_t*>& ranks) {
     ProbeArgs a = ps.args;
     if (rows) {
         a.nrows = rows;
@@ -1147,6 +1288,12 @@ gace_status launch_pass(gace_ctx* ctx, const Pass& ps, uint64_t nrows_all, uint6
         a.nstaged = a.stage_bytes ? rows / a.tile_rows : 0;
     }
     if (!a.narrow && setmask) a.setmask = setmask;
+    for (uint32_t s = 0; s < a.nslots; ++s) {
+        if (!a.slots[s].rstride) continue;
+        const uint32_t col = ps.slots[s].first;
+        if (col >= ranks.size() || !ranks[col]) return fail(GACE_EINVAL, "rank-coded column %u has no ranks", col);
+        a.slots[s].rank = ranks[col];
+    }
     const int occ = probe_occupancy(a);
     if (occ < 1)
         return fail(GACE_ECUDA, "probe kernel cannot be resident with %u bytes of shared memory", a.smem_bytes);
@@ -1161,7 +1308,6 @@ gace_status launch_pass(gace_ctx* ctx, const Pass& ps, uint64_t nrows_all, uint6
     // each CTA keeps 32-bit row counters
     while ((units + grid - 1) / grid * unit_rows >= (1ull << 31)) grid *= 2;
     if (grid > 0x7FFFFFFFull) return fail(GACE_EINVAL, "table too large for one probe grid");
-    (void)nrows_all;
     CK(ctx->traced(a.narrow ? "probe_narrow" : "probe_wide", n, n * ps.rowbytes, n * ps.ops_per_row,
                    [&] { return probe_launch(a, static_cast<int>(grid), ctx->stream); }));
     return GACE_OK;
@@ -1170,7 +1316,9 @@ gace_status launch_pass(gace_ctx* ctx, const Pass& ps, uint64_t nrows_all, uint6
 }  // namespace
 
 gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts, TableRec* lazy) {
-    // workspace: status | per pass of every part: inputs, outputs
+    // workspace: status | inputs and outputs of every part's passes, the
+    // rank-coded columns' search trees (copied in, read back) | device-only
+    // scratch: row-set masks and ranks of one chunk of rows per part
     Ws ws;
     const uint64_t status_off = ws.take(256);
     bool any_pass = false;
@@ -1180,27 +1328,39 @@ gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts, TableRe
             ps.out_off = ws.take(ps.out_bytes);
             any_pass = true;
         }
-    // A table whose copy is pending (one part) streams in chunks of rows, a
-    // multiple of every pass's tile; each chunk runs every pass.
-    const uint64_t chunk_rows =
-        lazy ? round_up(std::max<uint64_t>(lazy->nrows / kLoadChunks, 1ull << 20), 1ull << 16) : 0;
-    // A part with several wide passes over hashed row sets computes every
-    // slice's row-set masks once (per chunk), for all its passes to load.
-    std::vector<uint64_t> mask_off(parts.size(), 0);
+    std::vector<std::vector<uint64_t>> tree_off(parts.size());
+    for (size_t i = 0; i < parts.size(); ++i)
+        for (const RankCode& rc : parts[i].plan.codes)
+            tree_off[i].push_back(rc.used ? ws.take(rc.tree.size() * 4ull) : 0);
+    const uint64_t io_end = ws.off;
+    // Rows per chunk: a table whose copy is pending (one part) streams in
+    // chunks of rows, a multiple of every pass's tile, each chunk running
+    // every pass; so does a table whose ranks would not fit kRankScratch.
+    std::vector<uint64_t> chunk(parts.size(), 0), mask_off(parts.size(), 0);
+    std::vector<std::vector<uint64_t>> rank_off(parts.size());
     for (size_t i = 0; i < parts.size(); ++i) {
         const ProbePlan& pl = parts[i].plan;
+        const uint64_t n = parts[i].tab->nrows;
+        uint64_t coded = 0;
+        for (const RankCode& rc : pl.codes) coded += rc.used ? 1 : 0;
+        uint64_t rows = n;
+        if (lazy)
+            rows = round_up(std::max<uint64_t>(n / kLoadChunks, 1ull << 20), 1ull << 16);
+        else if (coded && coded * round_up(n, kSliceRows) * 2 > kRankScratch)
+            rows = std::max<uint64_t>(kRankScratch / (coded * 2) / (1ull << 16) * (1ull << 16), 1ull << 16);
+        chunk[i] = std::min(rows, n);
+        const uint64_t crows = round_up(chunk[i], kSliceRows);
+        // A part with several wide passes over hashed row sets computes every
+        // slice's row-set masks once (per chunk), for all its passes to load.
         uint32_t wide = 0;
         for (const auto& ps : pl.passes) wide += ps.args.narrow ? 0u : 1u;
         bool hashed = false;
         for (const auto& sp : pl.sets) hashed = hashed || sp.d.mode == 2;
-        if (wide >= 2 && hashed) {
-            const uint64_t rows = lazy ? std::min<uint64_t>(chunk_rows, parts[i].tab->nrows) : parts[i].tab->nrows;
-            const uint64_t nslices = (rows + kSliceRows - 1) / kSliceRows;
-            mask_off[i] = ws.take(nslices * pl.sets.size() * 16);
-        }
+        if (wide >= 2 && hashed) mask_off[i] = ws.take((crows / kSliceRows) * pl.sets.size() * 16);
+        for (const RankCode& rc : pl.codes) rank_off[i].push_back(rc.used ? ws.take(crows * 2) : 0);
     }
     if (gace_status st = ctx->ensure_ws(ws.off)) return st;
-    if (gace_status st = ctx->ensure_pin(ws.off + 256)) return st;
+    if (gace_status st = ctx->ensure_pin(io_end + 256)) return st;
 
     // stage inputs into pinned memory, one H2D copy, zero outputs
     unsigned char* pin = ctx->pin;
@@ -1208,20 +1368,26 @@ gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts, TableRe
     unsigned int* dstatus = reinterpret_cast<unsigned int*>(dws + status_off);
     for (auto& pp : parts)
         for (auto& ps : pp.plan.passes) stage_pass(ps, pin, dws, dstatus);
-    if (any_pass) {
-        const uint64_t first_in = status_off + 256;
-        CK(cudaMemcpyAsync(dws + first_in, pin + first_in, ws.off - first_in, cudaMemcpyHostToDevice, ctx->stream));
+    for (size_t i = 0; i < parts.size(); ++i)
+        for (size_t c = 0; c < parts[i].plan.codes.size(); ++c) {
+            const RankCode& rc = parts[i].plan.codes[c];
+            if (rc.used) memcpy(pin + tree_off[i][c], rc.tree.data(), rc.tree.size() * 4ull);
+        }
+    const uint64_t first_in = status_off + 256;
+    if (io_end > first_in) {
+        CK(cudaMemcpyAsync(dws + first_in, pin + first_in, io_end - first_in, cudaMemcpyHostToDevice, ctx->stream));
         for (auto& pp : parts)
             for (auto& ps : pp.plan.passes) CK(cudaMemsetAsync(dws + ps.out_off, 0, ps.out_bytes, ctx->stream));
     }
     CK(cudaMemsetAsync(dws + status_off, 0, 256, ctx->stream));
+    uint64_t nload = 0;  // chunks of the pending copy
     if (lazy) {
         // every chunk's copy on the copy stream, all at once (they run back to
         // back); the context stream waits for each before that chunk's passes
         if (!ctx->copy_stream) CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
-        const uint64_t n = lazy->nrows;
-        const uint64_t nchunks = (n + chunk_rows - 1) / chunk_rows;
-        while (ctx->chunk_events.size() < nchunks) {
+        const uint64_t n = lazy->nrows, step = chunk[0];
+        nload = step ? (n + step - 1) / step : 0;
+        while (ctx->chunk_events.size() < std::max<uint64_t>(nload, 1)) {
             cudaEvent_t ev = nullptr;
             CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
             ctx->chunk_events.push_back(ev);
@@ -1230,8 +1396,8 @@ gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts, TableRe
         // columns' stream-ordered allocations)
         CK(cudaEventRecord(ctx->chunk_events[0], ctx->stream));
         CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->chunk_events[0], 0));
-        for (uint64_t k = 0; k < nchunks; ++k) {
-            const uint64_t r0 = k * chunk_rows, rows = std::min(chunk_rows, n - r0);
+        for (uint64_t k = 0; k < nload; ++k) {
+            const uint64_t r0 = k * step, rows = std::min(step, n - r0);
             for (size_t c = 0; c < lazy->cols.size(); ++c) {
                 const uint64_t w = dtype_width(lazy->cols[c].dtype);
                 CK(cudaMemcpyAsync(static_cast<unsigned char*>(lazy->cols[c].dptr) + r0 * w,
@@ -1240,39 +1406,48 @@ gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts, TableRe
             }
             CK(cudaEventRecord(ctx->chunk_events[k], ctx->copy_stream));
         }
-        auto& pp = parts.front();
+    }
+    for (size_t i = 0; i < parts.size(); ++i) {
+        auto& pp = parts[i];
+        const TableRec* tab = pp.tab;
+        const uint64_t n = tab->nrows, step = chunk[i];
+        const bool whole = step >= n;  // one chunk: the passes' own row counts
+        const uint64_t nchunks = whole ? 1 : (n + step - 1) / step;
+        std::vector<const uint16_t*> ranks(tab->cols.size(), nullptr);
         for (uint64_t k = 0; k < nchunks; ++k) {
-            const uint64_t r0 = k * chunk_rows, rows = std::min(chunk_rows, n - r0);
-            CK(cudaStreamWaitEvent(ctx->stream, ctx->chunk_events[k], 0));
+            const uint64_t r0 = whole ? 0 : k * step, rows = whole ? n : std::min(step, n - r0);
+            if (lazy && k < nload) CK(cudaStreamWaitEvent(ctx->stream, ctx->chunk_events[k], 0));
             uint4* masks = nullptr;
-            if (mask_off[0]) {
-                masks = reinterpret_cast<uint4*>(dws + mask_off[0]);
+            if (mask_off[i]) {
+                masks = reinterpret_cast<uint4*>(dws + mask_off[i]);
                 ProbeArgs a0 = pp.plan.passes.front().args;
                 a0.nrows = rows;
                 a0.row0 = r0;
                 CK(ctx->traced("probe_setmask", rows, 0, rows,
                                [&] { return setmask_launch(a0, masks, ctx->sms, ctx->stream); }));
             }
-            for (auto& ps : pp.plan.passes)
-                if (gace_status st = launch_pass(ctx, ps, n, r0, rows, masks)) return st;
-        }
-    } else {
-        for (size_t i = 0; i < parts.size(); ++i) {
-            auto& pp = parts[i];
-            const TableRec* tab = pp.tab;
-            uint4* masks = nullptr;
-            if (mask_off[i]) {
-                masks = reinterpret_cast<uint4*>(dws + mask_off[i]);
-                const ProbeArgs& a0 = pp.plan.passes.front().args;
-                const uint64_t n = tab->nrows;
-                CK(ctx->traced("probe_setmask", n, 0, n,
-                               [&] { return setmask_launch(a0, masks, ctx->sms, ctx->stream); }));
+            for (size_t c = 0; c < pp.plan.codes.size(); ++c) {
+                const RankCode& rc = pp.plan.codes[c];
+                if (!rc.used) continue;
+                RankArgs ra{};
+                const uint32_t w = dtype_width(static_cast<int>(rc.dtype));
+                ra.col = static_cast<const unsigned char*>(tab->cols[rc.col].dptr) + r0 * w;
+                ra.nrows = rows;
+                ra.nout = round_up(rows, kSliceRows);
+                ra.tree = reinterpret_cast<const uint32_t*>(dws + tree_off[i][c]);
+                ra.out = reinterpret_cast<uint16_t*>(dws + rank_off[i][c]);
+                ra.dtype = rc.dtype;
+                ra.levels = rc.levels;
+                ra.m = static_cast<uint32_t>(rc.keys.size());
+                ranks[rc.col] = ra.out;
+                CK(ctx->traced("probe_rank", rows, rows * (w + 2), rows,
+                               [&] { return rank_launch(ra, ctx->sms, ctx->stream); }));
             }
             for (auto& ps : pp.plan.passes)
-                if (gace_status st = launch_pass(ctx, ps, tab->nrows, 0, 0, masks)) return st;
+                if (gace_status st = launch_pass(ctx, ps, r0, whole ? 0 : rows, masks, ranks)) return st;
         }
     }
-    const uint64_t rb_hi = any_pass ? ws.off : status_off + 256;
+    const uint64_t rb_hi = any_pass ? io_end : status_off + 256;
     CK(cudaMemcpyAsync(pin + status_off, dws + status_off, rb_hi - status_off, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->collect();
@@ -1548,7 +1723,7 @@ gace_status gace_probe_batch(gace_ctx* ctx, uint32_t table_id, const gace_sample
         parts.emplace_back();
         parts.back().tab = tab;
         parts.back().r = r;
-        if (gace_status st = plan_probe(ctx, *tab, r, false, parts.back().plan, kWideWarps)) return st;
+        if (gace_status st = plan_probe(ctx, *tab, r, false, parts.back().plan, kWideWarps, true)) return st;
         return run_planned(ctx, parts, tab->pending.empty() ? nullptr : tab);
     }
     if (gace_status st = complete_load(ctx, *tab)) return st;
@@ -1586,7 +1761,7 @@ gace_status gace_probe_batch(gace_ctx* ctx, uint32_t table_id, const gace_sample
         pp.r.nsamples = ns;
         pp.r.results = npreds ? pres[i].data() : nullptr;
         pp.r.term_marginals = term_marginals ? pmarg[i].data() : nullptr;
-        if (gace_status st = plan_probe(ctx, *pp.tab, pp.r, false, pp.plan, kWideWarps)) return st;
+        if (gace_status st = plan_probe(ctx, *pp.tab, pp.r, false, pp.plan, kWideWarps, true)) return st;
     }
     if (gace_status st = run_planned(ctx, parts)) return st;
     for (size_t i = 0; i < order.size(); ++i) {

@@ -339,6 +339,7 @@ struct ColPool {
     uint64_t last = 0;   // entries of the last group
     uint64_t most = 0;   // entries of the fullest group
     uint32_t nr = 0;     // multi-value range terms
+    uint32_t rstride = 0;  // rank-coded column: mask words per group of 32 ranges (0: trees)
     bool is64 = false;   // 64-bit keys
     void add(const NTerm& t);
     uint32_t words() const;
@@ -429,6 +430,25 @@ struct ProbeRequest {
 
 // A probe compiled into device passes: row sets, deduplicated terms, the
 // predicates' states and the passes that evaluate them.
+// A column whose range terms the wide passes of a synchronous probe read by
+// rank: the sorted distinct endpoints of all the plan's range terms on it (each
+// interval's start and the key just past its end) and their search tree for
+// k_probe_rank (level order, padded with the largest key).
+struct RankCode {
+    uint32_t col = 0;
+    uint32_t dtype = 0;
+    std::vector<uint64_t> keys;
+    std::vector<uint32_t> tree;  // words: keys, or (lo, hi) pairs for int64
+    uint32_t levels = 0;
+    bool used = false;           // some wide pass of the plan reads the column's ranks
+};
+// Most endpoints a column may have to be rank-coded: each group of 32 of its
+// range terms then holds endpoints + 1 mask words of the pass's shared pool.
+#ifndef GACE_RANK_PLAN_MAX
+#define GACE_RANK_PLAN_MAX 2047
+#endif
+constexpr uint32_t kRankPlanMax = GACE_RANK_PLAN_MAX;
+
 struct ProbePlan {
     const TableRec* tab = nullptr;
     std::vector<SetPlan> sets;     // device row sets
@@ -439,6 +459,8 @@ struct ProbePlan {
     std::vector<std::vector<uint32_t>> pred_u;
     bool want_marg = false;
     std::vector<Pass> passes;
+    std::vector<RankCode> codes;       // rank-coded columns
+    std::vector<int32_t> code_of_col;  // column -> codes index, -1 if not coded
 };
 
 // Argument checks that need no table.
@@ -446,8 +468,10 @@ gace_status check_probe_request(const ProbeRequest& r);
 // Compiles a probe; force_wide builds every pass in the wide-kernel layout.
 // wide_warps: warps of the CTA that runs the plan's wide passes (kWideWarps
 // for the synchronous kernel, kProbeWarps for the batched form's).
+// rank_code: the wide passes read the range terms of columns with at most
+// kRankPlanMax endpoints by the rows' ranks (run_planned computes them).
 gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r, bool force_wide,
-                       ProbePlan& plan, uint32_t wide_warps);
+                       ProbePlan& plan, uint32_t wide_warps, bool rank_code = false);
 // Bytes of a pass's inputs (terms, pool, predicate CSR) and outputs (counters).
 void pass_sizes(Pass& ps);
 // Copies a pass's inputs into pinned staging at ps.in_off and points its
@@ -463,8 +487,14 @@ struct PlannedProbe {
 // and a wait on the context stream, then assembles each part's results.
 // lazy: the one part's table, whose pending copy (GACE_COPY_ON_FIRST_PROBE)
 // then streams in kLoadChunks row chunks overlapped with the passes.
+// A table whose rank-coded columns' ranks would take more than kRankScratch
+// bytes runs its passes in row chunks, the ranks of one chunk at a time.
 gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts, TableRec* lazy = nullptr);
 constexpr uint64_t kLoadChunks = 12;
+#ifndef GACE_RANK_SCRATCH_MB
+#define GACE_RANK_SCRATCH_MB 2048
+#endif
+constexpr uint64_t kRankScratch = static_cast<uint64_t>(GACE_RANK_SCRATCH_MB) << 20;
 // Results from the passes' counters (host copies, one pointer per pass).
 void assemble_probe(const ProbePlan& plan, const ProbeRequest& r,
                     const std::vector<const unsigned long long*>& pass_out);

@@ -69,6 +69,18 @@ struct SlotDesc {
     uint32_t rgroups;    // range trees (groups of up to 32 range terms)
     uint32_t rtree;      // range terms [rbeg, rbeg + rtree) by tree, the rest by compare
     uint32_t vm1, vm2;   // wide passes: the multipliers of the hash tables' two slot functions
+    // Rank-coded ranges (wide passes of a synchronous call): every row's rank
+    // among the column's range endpoints, written by k_probe_rank; the slot's
+    // range terms [rbeg, rend) are then read as rgroups groups of 32, group g's
+    // mask of local rank r at pool[roff + g * rstride + r], where a row's local
+    // rank (among the endpoints of this slot's terms) is its rank among the
+    // column's endpoints, mapped by the byte table at pool word rmap - 1 (rmap
+    // 0: no map, the two ranks are the same).  Such a slot holds no EQ/IN terms
+    // (they take a second slot of the column) and reads no values.  nullptr:
+    // not coded.
+    const uint16_t* rank;
+    uint32_t rstride;    // words per group (the local endpoints + 1)
+    uint32_t rmap;
 };
 
 // A wide pass's range terms of one column, 32 at a time, as an interval tree:
@@ -123,7 +135,8 @@ struct alignas(16) ProbeArgs {
     uint32_t skip_tiles;    // 1: every row set is a block sample; tiles with no sampled block are skipped
     uint32_t smem_bytes;
     uint32_t nwarps;        // warps of the CTA that runs the pass (per-warp mask buffers)
-    uint32_t pad_[3];
+    uint32_t ranks_only;    // wide passes: every slot with range terms is rank-coded
+    uint32_t pad_[2];
     // smem byte offsets
     uint32_t off_stage, off_terms, off_pool, off_poff, off_pterm, off_tm, off_keep,
         off_cnt, off_marg, off_ns;
@@ -168,6 +181,25 @@ static_assert(sizeof(ProbeArgs) % 16 == 0, "ProbeArgs is copied in 16-byte words
 uint32_t probe_layout(ProbeArgs& a);
 cudaError_t probe_configure();  // one-time kernel attributes
 cudaError_t probe_launch(const ProbeArgs& a, int grid, cudaStream_t s);
+// Rank coding of one column for the wide passes of a call: out[r] = the number
+// of the column's range endpoints <= the order-preserving key of row r (at most
+// m), for rows [0, nout) (rows >= nrows get 0), from the endpoints' search tree
+// (level order, 2^levels - 1 keys padded with the largest key; 32-bit keys, or
+// (lo, hi) word pairs for 64-bit columns).
+struct RankArgs {
+    const void* col;        // the column's first row of the range scanned
+    uint64_t nrows;
+    uint64_t nout;          // nrows rounded up to a multiple of 128
+    const uint32_t* tree;
+    uint16_t* out;
+    uint32_t dtype;
+    uint32_t levels;        // 1..13
+    uint32_t m;             // endpoints (<= 8191)
+    uint32_t pad;
+};
+constexpr uint32_t kRankMaxEndpoints = 8191;
+cudaError_t rank_launch(const RankArgs& a, int sms, cudaStream_t s);
+
 // The row-set masks of every 128-row slice of a pass's table into a.setmask
 // (writable), for the wide passes that follow to load instead of hashing.
 cudaError_t setmask_launch(const ProbeArgs& a, uint4* out, int sms, cudaStream_t s);

@@ -75,6 +75,7 @@ constexpr int kWideThreads = kWideWarps * 32;
 #define GACE_WIDE_BOUNDS __launch_bounds__(kWideThreads)
 #endif
 
+template <bool RANKS_ONLY>
 __global__ void GACE_WIDE_BOUNDS k_probe_wide(const __grid_constant__ ProbeArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -82,8 +83,8 @@ __global__ void GACE_WIDE_BOUNDS k_probe_wide(const __grid_constant__ ProbeArgs 
     load_tables(A, S, tid, kWideThreads);
     __syncthreads();
     const uint64_t nslices = (A.nrows + kSliceRows - 1) / kSliceRows;
-    const uint32_t nsr = wide_slices(A, S, lane, static_cast<uint64_t>(blockIdx.x) * kWideWarps + warp, nslices,
-                                     static_cast<uint64_t>(gridDim.x) * kWideWarps);
+    const uint32_t nsr = wide_slices<RANKS_ONLY>(A, S, lane, static_cast<uint64_t>(blockIdx.x) * kWideWarps + warp,
+                                                 nslices, static_cast<uint64_t>(gridDim.x) * kWideWarps);
     if (lane < static_cast<int>(A.nsets) && nsr) atomicAdd(&S.ns[lane], nsr);
     __syncthreads();
     flush(A, S, tid, kWideThreads);
@@ -98,6 +99,52 @@ __global__ void __launch_bounds__(256) k_probe_setmask(const __grid_constant__ P
     for (uint64_t sl = static_cast<uint64_t>(blockIdx.x) * (blockDim.x / 32) + (threadIdx.x >> 5); sl < nslices;
          sl += stride)
         set_masks<1>(A, sl * kSliceRows, out + sl * A.nsets, lane);
+}
+
+// Rank coding of one column (RankArgs): the endpoints' search tree staged in
+// shared memory, then four rows per thread per step, their descents interleaved
+// level by level (one compare each), to the number of endpoints <= each key.
+__global__ void __launch_bounds__(256) k_probe_rank(const __grid_constant__ RankArgs A) {
+    extern __shared__ uint32_t tree[];
+    const bool is64 = A.dtype == 1;
+    const uint32_t nkeys = (1u << A.levels) - 1u;
+    const uint32_t words = is64 ? 2u * nkeys : nkeys;
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) tree[i] = A.tree[i];
+    __syncthreads();
+    const uint32_t width = is64 ? 8u : 4u;
+    const uint64_t step = static_cast<uint64_t>(gridDim.x) * blockDim.x * 4u;
+    for (uint64_t r0 = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) * 4u; r0 < A.nout; r0 += step) {
+        Quad q;
+        load_quad_global(A.col, width, r0, A.nrows, q);
+        uint32_t klo[4], khi[4], n[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            value_key(A.dtype, q.lo[i], q.hi[i], klo[i], khi[i]);
+            n[i] = 1;
+        }
+        if (is64) {
+            const uint2* node = reinterpret_cast<const uint2*>(tree);
+            for (uint32_t d = 0; d < A.levels; ++d) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const uint2 e = node[n[i] - 1];
+                    n[i] = 2 * n[i] + ((khi[i] > e.y || (khi[i] == e.y && klo[i] >= e.x)) ? 1u : 0u);
+                }
+            }
+        } else {
+            for (uint32_t d = 0; d < A.levels; ++d) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) n[i] = 2 * n[i] + (klo[i] >= tree[n[i] - 1] ? 1u : 0u);
+            }
+        }
+        uint32_t rk[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t r = n[i] - (1u << A.levels);
+            rk[i] = r0 + i < A.nrows ? (r < A.m ? r : A.m) : 0u;
+        }
+        *reinterpret_cast<uint2*>(A.out + r0) = make_uint2(rk[0] | (rk[1] << 16), rk[2] | (rk[3] << 16));
+    }
 }
 
 uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
@@ -138,7 +185,11 @@ static cudaError_t set_smem(K kernel, int optin) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
 }
 
-static int variant(const ProbeArgs& a) { return probe_variant(a); }
+// probe_variant's cases, and 6: a wide pass whose range terms are all rank-coded
+static int variant(const ProbeArgs& a) {
+    const int v = probe_variant(a);
+    return v == 0 && a.ranks_only ? 6 : v;
+}
 
 cudaError_t probe_configure() {
     int dev = 0, optin = 0;
@@ -151,14 +202,16 @@ cudaError_t probe_configure() {
     if ((e = set_smem(k_probe_narrow<true, kMaxSets>, optin))) return e;
     if ((e = set_smem(k_probe_single<false>, optin))) return e;
     if ((e = set_smem(k_probe_single<true>, optin))) return e;
-    return set_smem(k_probe_wide, optin);
+    if ((e = set_smem(k_probe_wide<true>, optin))) return e;
+    return set_smem(k_probe_wide<false>, optin);
 }
 
 int probe_occupancy(const ProbeArgs& a) {
     int n = 0;
     cudaError_t e = cudaSuccess;
     switch (variant(a)) {
-        case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_wide, kWideThreads, a.smem_bytes); break;
+        case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_wide<false>, kWideThreads, a.smem_bytes); break;
+        case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_wide<true>, kWideThreads, a.smem_bytes); break;
         case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_narrow<false, 1>, kThreads, a.smem_bytes); break;
         case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_narrow<true, 1>, kThreads, a.smem_bytes); break;
         case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_narrow<true, kMaxSets>, kThreads, a.smem_bytes); break;
@@ -166,6 +219,20 @@ int probe_occupancy(const ProbeArgs& a) {
         default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_single<true>, kThreads, a.smem_bytes); break;
     }
     return e == cudaSuccess ? n : 0;
+}
+
+cudaError_t rank_launch(const RankArgs& a, int sms, cudaStream_t s) {
+    const uint32_t nkeys = (1u << a.levels) - 1u;
+    const uint32_t smem = nkeys * (a.dtype == 1 ? 8u : 4u);
+    cudaError_t e = cudaFuncSetAttribute(k_probe_rank, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    const uint64_t quads = a.nout / 4;
+    const uint64_t cap = static_cast<uint64_t>(sms) * 8 * 256;  // eight 256-thread CTAs per SM
+    const uint64_t threads = quads < cap ? quads : cap;
+    const int grid = static_cast<int>(threads ? (threads + 255) / 256 : 1);
+    k_probe_rank<<<grid, 256, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t setmask_launch(const ProbeArgs& a, uint4* out, int sms, cudaStream_t s) {
@@ -178,7 +245,8 @@ cudaError_t setmask_launch(const ProbeArgs& a, uint4* out, int sms, cudaStream_t
 
 cudaError_t probe_launch(const ProbeArgs& a, int grid, cudaStream_t s) {
     switch (variant(a)) {
-        case 0: k_probe_wide<<<grid, kWideThreads, a.smem_bytes, s>>>(a); break;
+        case 0: k_probe_wide<false><<<grid, kWideThreads, a.smem_bytes, s>>>(a); break;
+        case 6: k_probe_wide<true><<<grid, kWideThreads, a.smem_bytes, s>>>(a); break;
         case 1: k_probe_narrow<false, 1><<<grid, kThreads, a.smem_bytes, s>>>(a); break;
         case 2: k_probe_narrow<true, 1><<<grid, kThreads, a.smem_bytes, s>>>(a); break;
         case 3: k_probe_narrow<true, kMaxSets><<<grid, kThreads, a.smem_bytes, s>>>(a); break;

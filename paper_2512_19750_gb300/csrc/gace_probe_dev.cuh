@@ -413,25 +413,81 @@ __device__ __forceinline__ void eval_range_trees(const SlotDesc& sd, const Vals<
     }
 }
 
+// Range terms of a rank-coded column slot in a wide pass: each row's rank
+// among the column's endpoints (rk, computed once per call) indexes the 32-bit
+// mask of each group's terms that contain the row's value; a warp transpose of
+// each row-group's masks hands lane t the 32-row mask of term t.
+template <int NQ>
+__device__ __forceinline__ void eval_rank_groups(const SlotDesc& sd, const uint32_t (&rk)[4 * NQ],
+                                                 const uint32_t* pool, uint4* tm, int lane) {
+    constexpr int R = 4 * NQ;
+    const uint32_t nr = sd.rend - sd.rbeg;
+    uint32_t lr[R];  // local ranks
+    if (sd.rmap) {
+        const unsigned char* map = reinterpret_cast<const unsigned char*>(pool + sd.rmap - 1);
+#pragma unroll
+        for (int i = 0; i < R; ++i) lr[i] = map[rk[i]];
+    } else {
+#pragma unroll
+        for (int i = 0; i < R; ++i) lr[i] = rk[i];
+    }
+    for (uint32_t g = 0; g < sd.rgroups; ++g) {
+        const uint32_t* tab = pool + sd.roff + g * sd.rstride;
+        uint32_t w[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) w[i] = tab[lr[i]];
+        uint4 out[NQ];
+#pragma unroll
+        for (int h = 0; h < NQ; ++h) {
+            out[h].x = transpose32(w[4 * h + 0], lane);
+            out[h].y = transpose32(w[4 * h + 1], lane);
+            out[h].z = transpose32(w[4 * h + 2], lane);
+            out[h].w = transpose32(w[4 * h + 3], lane);
+        }
+        const uint32_t k = 32u * g + lane;
+        if (k < nr) {
+#pragma unroll
+            for (int h = 0; h < NQ; ++h) tm[(sd.rbeg + k) * NQ + h] = out[h];
+        }
+    }
+}
+
+// The four ranks of the lane's rows of a slice, packed in v.lo[0] and v.lo[1]
+// (rank arrays are padded to whole slices, so the load never passes their end).
+__device__ __forceinline__ void load_ranks(const uint16_t* rank, uint64_t slice0, int lane, Vals<1>& v) {
+    const uint2 r = __ldg(reinterpret_cast<const uint2*>(rank + slice0 + 4u * lane));
+    v.lo[0] = r.x;
+    v.lo[1] = r.y;
+}
+
+// One slot's values of the lane's rows of a slice, or their ranks.
+__device__ __forceinline__ void load_slot(const SlotDesc& d, uint64_t slice0, uint64_t nrows, int lane, Vals<1>& v) {
+    if (d.rank)
+        load_ranks(d.rank, slice0, lane, v);
+    else
+        load_vals_global<1>(d.ptr, d.width, slice0, nrows, lane, v);
+}
+
 // The wide pass over warp slices sl = first, first + stride, ... < end of
 // 128 rows each: row-set masks, range terms by interval tree, EQ and IN terms
 // by table, then lanes take predicates (and terms, for marginals) and add
 // popcounts into the CTA's 32-bit counters.  Returns the warp's count of
 // rows in each row set `lane` (lanes < nsets).
+// RANKS_ONLY: every slot's range terms are rank-coded (no trees, no compares).
+template <bool RANKS_ONLY = false>
 __device__ __forceinline__ uint32_t wide_slices(const ProbeArgs& A, const Smem& S, int lane, uint64_t first,
                                                 uint64_t end, uint64_t stride) {
     uint32_t nsr = 0;
     // Column loads run one column ahead of the evaluation (and the next
     // slice's first column is loaded before the counting), so that a warp does
     // not wait out the memory latency once per column.
-    Vals<1> cur;
-    bool have = false;  // cur holds the current slice's first column
+    Vals<1> cur;        // the current slot's values, or its rows' ranks (rank-coded slots)
+    bool have = false;  // cur holds the current slice's first slot
     uint4 km = make_uint4(0u, 0u, 0u, 0u);  // this lane's row-set mask of the current slice (lanes < nsets)
     if (A.setmask && lane < static_cast<int>(A.nsets) && first < end) km = A.setmask[first * A.nsets + lane];
     for (uint64_t sl = first; sl < end; sl += stride) {
         const uint64_t slice0 = sl * kSliceRows;
-        if (!have && A.nslots)
-            load_vals_global<1>(A.slots[0].ptr, A.slots[0].width, slice0, A.nrows, lane, cur);
+        if (!have && A.nslots) load_slot(A.slots[0], slice0, A.nrows, lane, cur);
         have = false;
         if (A.setmask) {  // computed once for every pass of the call; the next slice's loaded a slice ahead
             if (lane < static_cast<int>(A.nsets)) {
@@ -459,17 +515,24 @@ __device__ __forceinline__ uint32_t wide_slices(const ProbeArgs& A, const Smem& 
             const SlotDesc& sd = A.slots[s];
             const Vals<1> v = cur;
             if (s + 1 < A.nslots) {
-                load_vals_global<1>(A.slots[s + 1].ptr, A.slots[s + 1].width, slice0, A.nrows, lane, cur);
+                load_slot(A.slots[s + 1], slice0, A.nrows, lane, cur);
             } else if (next < end) {
-                load_vals_global<1>(A.slots[0].ptr, A.slots[0].width, next * kSliceRows, A.nrows, lane, cur);
+                load_slot(A.slots[0], next * kSliceRows, A.nrows, lane, cur);
                 have = true;
             }
-            if (sd.rgroups) eval_range_trees<1>(sd, v, S.pool, S.tm, lane);  // ranges by tree
-            if (sd.rbeg + sd.rtree < sd.rend) {  // the remaining ranges by compare
-                SlotDesc ranges = sd;
-                ranges.rbeg = sd.rbeg + sd.rtree;
-                ranges.iend = sd.rend;
-                eval_slot<1>(ranges, v, S.st, S.pool, S.tm, lane);
+            if (sd.rank) {  // ranges by the rows' ranks (the slot has no EQ/IN terms)
+                const uint32_t rk[4] = {v.lo[0] & 0xFFFFu, v.lo[0] >> 16, v.lo[1] & 0xFFFFu, v.lo[1] >> 16};
+                eval_rank_groups<1>(sd, rk, S.pool, S.tm, lane);
+                continue;
+            }
+            if (!RANKS_ONLY) {
+                if (sd.rgroups) eval_range_trees<1>(sd, v, S.pool, S.tm, lane);  // ranges by tree
+                if (sd.rbeg + sd.rtree < sd.rend) {  // the remaining ranges by compare
+                    SlotDesc ranges = sd;
+                    ranges.rbeg = sd.rbeg + sd.rtree;
+                    ranges.iend = sd.rend;
+                    eval_slot<1>(ranges, v, S.st, S.pool, S.tm, lane);
+                }
             }
             if (sd.iend > sd.rend) eval_valueset<1>(sd, v, S.pool, S.tm, lane);  // EQ and IN by table
         }
