@@ -199,10 +199,11 @@ uint32_t ColPool::words() const {
         while ((1ull << tlog) < kVsSlotsPerEntry * most) ++tlog;
         w += static_cast<uint64_t>((nvs + 31) / 32) * (1ull << tlog) * (is64 ? 4u : 2u);
     }
-    if (rstride) {  // rank-coded: the smaller of the column-rank tables and a byte map + local tables
-        const uint64_t g = (nr + 31) / 32, ml = std::min<uint64_t>(2ull * nr, rstride - 1);
-        const uint64_t direct = g * rstride, mapped = (rstride + 3) / 4 + g * (ml + 1);
-        w += ml <= 255 ? std::min(direct, mapped) : direct;
+    if (rstride) {  // rank-coded: the smaller of the column-rank tables and a rank map + local tables
+        const uint64_t g = (nr + 31) / 32, ml = std::min<uint64_t>(2ull * (rank_all ? niv : nr), rstride - 1);
+        const uint64_t direct = g * rstride;
+        const uint64_t mapped = (rstride * (ml <= 255 ? 1 : 2) + 3) / 4 + g * (ml + 1);
+        w += std::min(direct, mapped);
     } else {
         w += static_cast<uint64_t>(trees) * (is64 ? kTreeWords64 : kTreeWords32);
     }
@@ -210,6 +211,11 @@ uint32_t ColPool::words() const {
 }
 
 void ColPool::add(const NTerm& t) {
+    if (rank_all) {
+        ++nr;
+        niv += is_in_kind(t.kind) ? in_count(t) : 1;
+        return;
+    }
     uint64_t entries = 0;
     if (is_in_kind(t.kind))
         entries = in_count(t);
@@ -217,6 +223,7 @@ void ColPool::add(const NTerm& t) {
         entries = 1;  // a single value: looked up like an EQ term
     if (!entries) {
         ++nr;
+        ++niv;
         return;
     }
     if (nvs % 32 == 0) last = 0;  // a new group
@@ -338,6 +345,22 @@ std::pair<uint64_t, uint64_t> range_keys(const NTerm& t, uint32_t dtype) {
     return {value_key(t.a, dtype), value_key(t.b, dtype)};
 }
 
+// Inclusive key intervals of a normalised term: its range, or one one-key
+// interval per IN value (NaN values were dropped, -0 keys as +0).
+void term_intervals(const NTerm& t, uint32_t dtype, std::vector<std::pair<uint64_t, uint64_t>>& out) {
+    out.clear();
+    if (!is_in_kind(t.kind)) {
+        out.push_back(range_keys(t, dtype));
+        return;
+    }
+    const bool is64 = dtype == GACE_I64;
+    for (size_t w = 0; w < t.in.size(); w += is64 ? 2 : 1) {
+        const uint64_t bits = is64 ? (t.in[w] | (static_cast<uint64_t>(t.in[w + 1]) << 32)) : t.in[w];
+        const uint64_t k = value_key(bits, dtype);
+        out.push_back({k, k});
+    }
+}
+
 // One group's interval tree (layout in gace_internal.h): endpoints are the
 // intervals' starts and the keys just past their ends; the mask of rank r (r
 // endpoints <= the key) holds the terms whose interval contains endpoint r-1.
@@ -453,8 +476,12 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
     // ranges) first, then IN lists (or, wide, single values and IN lists).
     const bool narrow = !force_wide && ps.preds.size() <= static_cast<size_t>(kNarrowMax) &&
                         ps.uterms.size() <= static_cast<size_t>(kNarrowMax);
+    // a wide pass reads every term of a column coded with all its terms by rank
+    auto rank_all = [&](uint32_t col) {
+        return !narrow && !code_of_col.empty() && code_of_col[col] >= 0 && codes[code_of_col[col]].all_terms;
+    };
     auto valueset = [&](const NTerm& t) {
-        return is_in_kind(t.kind) || (!narrow && term_cost(t) == 1);
+        return !rank_all(t.col) && (is_in_kind(t.kind) || (!narrow && term_cost(t) == 1));
     };
     std::vector<uint32_t> order = ps.uterms;
     std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
@@ -575,38 +602,50 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
             RankCode& rc = codes[code_of_col[col]];
             rc.used = true;
             const uint32_t m = static_cast<uint32_t>(rc.keys.size());
-            // each term's endpoints inside its interval, as column endpoint
-            // indices [r0, r1), and the slot's own endpoints (local), by index
-            std::vector<std::pair<uint32_t, uint32_t>> span(nr);
-            std::vector<uint32_t> local;
+            // each key interval's endpoints as column endpoint indices [r0, r1)
+            // (term k's intervals: span[soff[k] .. soff[k+1])), and the slot's
+            // own endpoints (local), by index
+            std::vector<std::pair<uint32_t, uint32_t>> span;
+            std::vector<uint32_t> soff(1, 0), local;
+            std::vector<std::pair<uint64_t, uint64_t>> ivs;
             for (uint32_t k = 0; k < nr; ++k) {
-                const auto iv = range_keys(uterms[order[sd.rbeg + k]], sd.dtype);
-                const uint32_t r0 = static_cast<uint32_t>(
-                    std::lower_bound(rc.keys.begin(), rc.keys.end(), iv.first) - rc.keys.begin());
-                const uint32_t r1 = static_cast<uint32_t>(
-                    std::upper_bound(rc.keys.begin(), rc.keys.end(), iv.second) - rc.keys.begin());
-                span[k] = {r0, r1};
-                local.push_back(r0);
-                if (r1 < m) local.push_back(r1);
+                term_intervals(uterms[order[sd.rbeg + k]], sd.dtype, ivs);
+                for (const auto& iv : ivs) {
+                    const uint32_t r0 = static_cast<uint32_t>(
+                        std::lower_bound(rc.keys.begin(), rc.keys.end(), iv.first) - rc.keys.begin());
+                    const uint32_t r1 = static_cast<uint32_t>(
+                        std::upper_bound(rc.keys.begin(), rc.keys.end(), iv.second) - rc.keys.begin());
+                    span.push_back({r0, r1});
+                    local.push_back(r0);
+                    if (r1 < m) local.push_back(r1);
+                }
+                soff.push_back(static_cast<uint32_t>(span.size()));
             }
             std::sort(local.begin(), local.end());
             local.erase(std::unique(local.begin(), local.end()), local.end());
             const uint32_t ml = static_cast<uint32_t>(local.size());
             sd.rtree = nr;
             sd.rgroups = (nr + 31) / 32;
-            // a byte map from column rank to local rank when it takes less room
+            // a map from column rank to local rank (bytes, or 16-bit entries
+            // past 255 local endpoints) when it takes less room
+            const uint32_t mapw = ml <= 255 ? 1 : 2;
             const uint64_t direct = static_cast<uint64_t>(sd.rgroups) * (m + 1);
-            const uint64_t mapped = (m + 1 + 3) / 4 + static_cast<uint64_t>(sd.rgroups) * (ml + 1);
-            const bool use_map = ml <= 255 && mapped < direct;
+            const uint64_t mapped = ((m + 1) * mapw + 3) / 4 + static_cast<uint64_t>(sd.rgroups) * (ml + 1);
+            const bool use_map = mapped < direct;
             if (use_map) {
-                sd.rmap = static_cast<uint32_t>(ps.pool.size()) + 1;
-                ps.pool.resize(ps.pool.size() + (m + 1 + 3) / 4, 0u);
-                unsigned char* map = reinterpret_cast<unsigned char*>(ps.pool.data() + sd.rmap - 1);
+                const uint32_t off = static_cast<uint32_t>(ps.pool.size());
+                sd.rmap = (off + 1) | (mapw == 2 ? kRankMap16 : 0u);
+                ps.pool.resize(ps.pool.size() + ((m + 1) * mapw + 3) / 4, 0u);
+                unsigned char* map8 = reinterpret_cast<unsigned char*>(ps.pool.data() + off);
+                uint16_t* map16 = reinterpret_cast<uint16_t*>(ps.pool.data() + off);
                 // column rank r (endpoints 0 .. r-1 <= key): the local endpoints among them
                 uint32_t j = 0;
                 for (uint32_t r = 0; r <= m; ++r) {
                     while (j < ml && local[j] < r) ++j;
-                    map[r] = static_cast<unsigned char>(j);
+                    if (mapw == 1)
+                        map8[r] = static_cast<unsigned char>(j);
+                    else
+                        map16[r] = static_cast<uint16_t>(j);
                 }
             }
             sd.rstride = use_map ? ml + 1 : m + 1;
@@ -614,13 +653,15 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
             ps.pool.resize(ps.pool.size() + static_cast<size_t>(sd.rgroups) * sd.rstride, 0u);
             // mask of rank r: the terms holding the (r-1)-th endpoint (local or column)
             for (uint32_t k = 0; k < nr; ++k) {
-                uint32_t a = span[k].first, b = span[k].second;
-                if (use_map) {
-                    a = static_cast<uint32_t>(std::lower_bound(local.begin(), local.end(), a) - local.begin());
-                    b = static_cast<uint32_t>(std::lower_bound(local.begin(), local.end(), b) - local.begin());
-                }
                 uint32_t* masks = ps.pool.data() + sd.roff + static_cast<size_t>(k / 32) * sd.rstride;
-                for (uint32_t r = a; r < b; ++r) masks[r + 1] |= 1u << (k % 32);
+                for (uint32_t i = soff[k]; i < soff[k + 1]; ++i) {
+                    uint32_t a = span[i].first, b = span[i].second;
+                    if (use_map) {
+                        a = static_cast<uint32_t>(std::lower_bound(local.begin(), local.end(), a) - local.begin());
+                        b = static_cast<uint32_t>(std::lower_bound(local.begin(), local.end(), b) - local.begin());
+                    }
+                    for (uint32_t r = a; r < b; ++r) masks[r + 1] |= 1u << (k % 32);
+                }
             }
         }
         A.ranks_only = 1;
@@ -1021,25 +1062,41 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
     // rank coding: every column's distinct range endpoints over the whole plan
     plan.code_of_col.assign(tab.cols.size(), -1);
     if (rank_code) {
-        std::vector<std::vector<uint64_t>> ends(tab.cols.size());
+        // per column, the endpoints of its multi-value ranges and of all its
+        // terms: all terms are coded when their endpoints fit, else the ranges
+        std::vector<std::vector<uint64_t>> rng(tab.cols.size()), all(tab.cols.size());
+        std::vector<std::pair<uint64_t, uint64_t>> ivs;
         for (const NTerm& t : uterms) {
-            if (is_in_kind(t.kind) || term_cost(t) != 2) continue;  // ranges of several values only
             const uint32_t dt = static_cast<uint32_t>(tab.cols[t.col].dtype);
             const uint64_t kmax = dt == GACE_I64 ? ~0ull : 0xFFFFFFFFull;
-            const auto iv = range_keys(t, dt);
-            ends[t.col].push_back(iv.first);
-            if (iv.second < kmax) ends[t.col].push_back(iv.second + 1);
+            const bool range = !is_in_kind(t.kind) && term_cost(t) == 2;
+            term_intervals(t, dt, ivs);
+            for (const auto& iv : ivs) {
+                all[t.col].push_back(iv.first);
+                if (iv.second < kmax) all[t.col].push_back(iv.second + 1);
+                if (range) {
+                    rng[t.col].push_back(iv.first);
+                    if (iv.second < kmax) rng[t.col].push_back(iv.second + 1);
+                }
+            }
         }
-        for (uint32_t c = 0; c < ends.size(); ++c) {
-            std::vector<uint64_t>& e = ends[c];
-            if (e.empty()) continue;
+        auto distinct = [](std::vector<uint64_t>& e) {
             std::sort(e.begin(), e.end());
             e.erase(std::unique(e.begin(), e.end()), e.end());
-            if (e.size() > kRankPlanMax) continue;
+        };
+        for (uint32_t c = 0; c < tab.cols.size(); ++c) {
+            distinct(all[c]);
             RankCode rc;
+            if (!all[c].empty() && all[c].size() <= kRankPlanMax) {
+                rc.keys = std::move(all[c]);
+                rc.all_terms = true;
+            } else {
+                distinct(rng[c]);
+                if (rng[c].empty() || rng[c].size() > kRankPlanMax) continue;
+                rc.keys = std::move(rng[c]);
+            }
             rc.col = c;
             rc.dtype = static_cast<uint32_t>(tab.cols[c].dtype);
-            rc.keys = std::move(e);
             build_rank_tree(rc);
             plan.code_of_col[c] = static_cast<int32_t>(plan.codes.size());
             plan.codes.push_back(std::move(rc));
@@ -1098,6 +1155,7 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
                         c.is64 = tab.cols[col].dtype == GACE_I64;
                         const int32_t code = plan.code_of_col[col];
                         c.rstride = code < 0 ? 0u : static_cast<uint32_t>(plan.codes[code].keys.size()) + 1;
+                        c.rank_all = code >= 0 && plan.codes[code].all_terms;
                     }
                     touched.emplace_back(col, c);
                 }
@@ -1107,8 +1165,11 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
                 total += kv.second.words() - (has_col[kv.first] ? cols_cur[kv.first].words() : 0u);
             return total;
         };
-        // slots of a wide pass: a rank-coded column may take two (ranges, EQ/IN)
-        auto col_slots = [&](uint32_t col) -> size_t { return plan.code_of_col[col] >= 0 ? 2 : 1; };
+        // slots of a wide pass: a column with only its ranges rank-coded may take two (ranges, EQ/IN)
+        auto col_slots = [&](uint32_t col) -> size_t {
+            const int32_t code = plan.code_of_col[col];
+            return code >= 0 && !plan.codes[code].all_terms ? 2 : 1;
+        };
         auto new_cols = [&](const Touched& touched) {
             size_t n = 0;
             for (const auto& kv : touched) n += has_col[kv.first] ? 0 : col_slots(kv.first);

@@ -338,8 +338,10 @@ struct ColPool {
     uint32_t nvs = 0;    // EQ / IN terms (groups of 32, in order)
     uint64_t last = 0;   // entries of the last group
     uint64_t most = 0;   // entries of the fullest group
-    uint32_t nr = 0;     // multi-value range terms
-    uint32_t rstride = 0;  // rank-coded column: mask words per group of 32 ranges (0: trees)
+    uint32_t nr = 0;     // multi-value range terms (a column coded with all its terms: every term)
+    uint64_t niv = 0;    // key intervals of the rank-coded terms (one per IN value)
+    uint32_t rstride = 0;  // rank-coded column: its endpoints + 1 (0: trees)
+    bool rank_all = false;  // rank-coded with all its terms (no hash tables)
     bool is64 = false;   // 64-bit keys
     void add(const NTerm& t);
     uint32_t words() const;
@@ -430,16 +432,18 @@ struct ProbeRequest {
 
 // A probe compiled into device passes: row sets, deduplicated terms, the
 // predicates' states and the passes that evaluate them.
-// A column whose range terms the wide passes of a synchronous probe read by
-// rank: the sorted distinct endpoints of all the plan's range terms on it (each
-// interval's start and the key just past its end) and their search tree for
-// k_probe_rank (level order, padded with the largest key).
+// A column whose range terms (or all terms) the wide passes of a synchronous
+// probe read by rank: the sorted distinct endpoints of the key intervals of
+// those terms over the whole plan (each interval's start and the key just past
+// its end) and their search tree for k_probe_rank (level order, padded with the
+// largest key).
 struct RankCode {
     uint32_t col = 0;
     uint32_t dtype = 0;
     std::vector<uint64_t> keys;
     std::vector<uint32_t> tree;  // words: keys, or (lo, hi) pairs for int64
     uint32_t levels = 0;
+    bool all_terms = false;      // EQ and IN terms too (each value a one-key interval)
     bool used = false;           // some wide pass of the plan reads the column's ranks
 };
 // Most endpoints a column may have to be rank-coded: each group of 32 of its

@@ -74,10 +74,12 @@ struct SlotDesc {
     // range terms [rbeg, rend) are then read as rgroups groups of 32, group g's
     // mask of local rank r at pool[roff + g * rstride + r], where a row's local
     // rank (among the endpoints of this slot's terms) is its rank among the
-    // column's endpoints, mapped by the byte table at pool word rmap - 1 (rmap
-    // 0: no map, the two ranks are the same).  Such a slot holds no EQ/IN terms
-    // (they take a second slot of the column) and reads no values.  nullptr:
-    // not coded.
+    // column's endpoints, mapped by the table at pool word (rmap & ~kRankMap16)
+    // - 1, of bytes, or of 16-bit entries when rmap has kRankMap16 (rmap 0: no
+    // map, the two ranks are the same).  Such a slot holds no EQ/IN terms of
+    // its own: they take a second slot of the column, or the column is coded
+    // with all its terms, each an interval list in [rbeg, rend).  It reads no
+    // values.  nullptr: not coded.
     const uint16_t* rank;
     uint32_t rstride;    // words per group (the local endpoints + 1)
     uint32_t rmap;
@@ -198,6 +200,7 @@ struct RankArgs {
     uint32_t pad;
 };
 constexpr uint32_t kRankMaxEndpoints = 8191;
+constexpr uint32_t kRankMap16 = 0x80000000u;  // SlotDesc::rmap: the map has 16-bit entries
 cudaError_t rank_launch(const RankArgs& a, int sms, cudaStream_t s);
 
 // The row-set masks of every 128-row slice of a pass's table into a.setmask

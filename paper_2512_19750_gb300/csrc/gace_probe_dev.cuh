@@ -423,7 +423,11 @@ __device__ __forceinline__ void eval_rank_groups(const SlotDesc& sd, const uint3
     constexpr int R = 4 * NQ;
     const uint32_t nr = sd.rend - sd.rbeg;
     uint32_t lr[R];  // local ranks
-    if (sd.rmap) {
+    if (sd.rmap & kRankMap16) {
+        const uint16_t* map = reinterpret_cast<const uint16_t*>(pool + (sd.rmap & ~kRankMap16) - 1);
+#pragma unroll
+        for (int i = 0; i < R; ++i) lr[i] = map[rk[i]];
+    } else if (sd.rmap) {
         const unsigned char* map = reinterpret_cast<const unsigned char*>(pool + sd.rmap - 1);
 #pragma unroll
         for (int i = 0; i < R; ++i) lr[i] = map[rk[i]];
