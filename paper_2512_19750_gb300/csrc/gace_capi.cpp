@@ -469,7 +469,9 @@ bool build_cuckoo(const std::vector<std::vector<VsEntry>>& keys, bool is64, uint
 gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::vector<NTerm>& uterms,
                        const std::vector<std::vector<uint32_t>>& pred_u,
                        const std::vector<SetPlan>& sets, bool want_marg, bool force_wide, uint32_t wide_warps,
-                       std::vector<RankCode>& codes, const std::vector<int32_t>& code_of_col) {
+                       ProbePlan& plan) {
+    std::vector<RankCode>& codes = plan.codes;
+    const std::vector<int32_t>& code_of_col = plan.code_of_col;
     // Narrow passes (at most 32 predicates and terms) evaluate IN lists by
     // compare; wide passes look up every EQ and IN term of a column in that
     // column's hash tables.  Order: by column, ranges (or, wide, multi-value
@@ -602,28 +604,23 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
             RankCode& rc = codes[code_of_col[col]];
             rc.used = true;
             const uint32_t m = static_cast<uint32_t>(rc.keys.size());
-            // each key interval's endpoints as column endpoint indices [r0, r1)
-            // (term k's intervals: span[soff[k] .. soff[k+1])), and the slot's
-            // own endpoints (local), by index
-            std::vector<std::pair<uint32_t, uint32_t>> span;
-            std::vector<uint32_t> soff(1, 0), local;
-            std::vector<std::pair<uint64_t, uint64_t>> ivs;
+            // the slot's own endpoints (local) marked among the column's, and
+            // pre[r] = the local endpoints below column endpoint r: a row of
+            // column rank r has local rank pre[r]
+            std::vector<uint32_t> pre(m + 1, 0u);
             for (uint32_t k = 0; k < nr; ++k) {
-                term_intervals(uterms[order[sd.rbeg + k]], sd.dtype, ivs);
-                for (const auto& iv : ivs) {
-                    const uint32_t r0 = static_cast<uint32_t>(
-                        std::lower_bound(rc.keys.begin(), rc.keys.end(), iv.first) - rc.keys.begin());
-                    const uint32_t r1 = static_cast<uint32_t>(
-                        std::upper_bound(rc.keys.begin(), rc.keys.end(), iv.second) - rc.keys.begin());
-                    span.push_back({r0, r1});
-                    local.push_back(r0);
-                    if (r1 < m) local.push_back(r1);
+                const uint32_t u = order[sd.rbeg + k];
+                for (uint32_t i = plan.span_off[u]; i < plan.span_off[u + 1]; ++i) {
+                    pre[plan.span[i].first] = 1;
+                    if (plan.span[i].second < m) pre[plan.span[i].second] = 1;
                 }
-                soff.push_back(static_cast<uint32_t>(span.size()));
             }
-            std::sort(local.begin(), local.end());
-            local.erase(std::unique(local.begin(), local.end()), local.end());
-            const uint32_t ml = static_cast<uint32_t>(local.size());
+            uint32_t ml = 0;
+            for (uint32_t r = 0; r <= m; ++r) {
+                const uint32_t mark = pre[r];
+                pre[r] = ml;
+                ml += r < m ? mark : 0u;
+            }
             sd.rtree = nr;
             sd.rgroups = (nr + 31) / 32;
             // a map from column rank to local rank (bytes, or 16-bit entries
@@ -638,29 +635,36 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
                 ps.pool.resize(ps.pool.size() + ((m + 1) * mapw + 3) / 4, 0u);
                 unsigned char* map8 = reinterpret_cast<unsigned char*>(ps.pool.data() + off);
                 uint16_t* map16 = reinterpret_cast<uint16_t*>(ps.pool.data() + off);
-                // column rank r (endpoints 0 .. r-1 <= key): the local endpoints among them
-                uint32_t j = 0;
                 for (uint32_t r = 0; r <= m; ++r) {
-                    while (j < ml && local[j] < r) ++j;
                     if (mapw == 1)
-                        map8[r] = static_cast<unsigned char>(j);
+                        map8[r] = static_cast<unsigned char>(pre[r]);
                     else
-                        map16[r] = static_cast<uint16_t>(j);
+                        map16[r] = static_cast<uint16_t>(pre[r]);
                 }
             }
             sd.rstride = use_map ? ml + 1 : m + 1;
             sd.roff = static_cast<uint32_t>(ps.pool.size());
             ps.pool.resize(ps.pool.size() + static_cast<size_t>(sd.rgroups) * sd.rstride, 0u);
-            // mask of rank r: the terms holding the (r-1)-th endpoint (local or column)
-            for (uint32_t k = 0; k < nr; ++k) {
-                uint32_t* masks = ps.pool.data() + sd.roff + static_cast<size_t>(k / 32) * sd.rstride;
-                for (uint32_t i = soff[k]; i < soff[k + 1]; ++i) {
-                    uint32_t a = span[i].first, b = span[i].second;
-                    if (use_map) {
-                        a = static_cast<uint32_t>(std::lower_bound(local.begin(), local.end(), a) - local.begin());
-                        b = static_cast<uint32_t>(std::lower_bound(local.begin(), local.end(), b) - local.begin());
+            // mask of rank s >= 1: the terms holding the (s-1)-th endpoint
+            // (local or column); a term's intervals do not overlap, so each
+            // toggles its bit on at its first endpoint and off past its last
+            std::vector<uint32_t> flip(sd.rstride + 1);
+            for (uint32_t g = 0; g < sd.rgroups; ++g) {
+                std::fill(flip.begin(), flip.end(), 0u);
+                for (uint32_t k = 32 * g; k < std::min(nr, 32 * g + 32); ++k) {
+                    const uint32_t u = order[sd.rbeg + k], bit = 1u << (k % 32);
+                    for (uint32_t i = plan.span_off[u]; i < plan.span_off[u + 1]; ++i) {
+                        const uint32_t a = use_map ? pre[plan.span[i].first] : plan.span[i].first;
+                        const uint32_t b = use_map ? pre[plan.span[i].second] : plan.span[i].second;
+                        flip[a] ^= bit;
+                        flip[b] ^= bit;
                     }
-                    for (uint32_t r = a; r < b; ++r) masks[r + 1] |= 1u << (k % 32);
+                }
+                uint32_t* masks = ps.pool.data() + sd.roff + static_cast<size_t>(g) * sd.rstride;
+                uint32_t run = 0;
+                for (uint32_t r = 0; r + 1 < sd.rstride; ++r) {
+                    run ^= flip[r];
+                    masks[r + 1] = run;
                 }
             }
         }
@@ -1010,7 +1014,8 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
 
     // normalise and deduplicate terms
     std::vector<NTerm>& uterms = plan.uterms;
-    std::map<NTerm, uint32_t> dedup;
+    std::unordered_map<NTerm, uint32_t, NTermHash> dedup;
+    dedup.reserve(nterms);
     plan.t2u.assign(nterms, 0);
     for (uint32_t t = 0; t < nterms; ++t) {
         if (r.terms[t].col >= tab.cols.size())
@@ -1100,6 +1105,24 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
             build_rank_tree(rc);
             plan.code_of_col[c] = static_cast<int32_t>(plan.codes.size());
             plan.codes.push_back(std::move(rc));
+        }
+        // each coded term's intervals as column endpoint indices
+        plan.span_off.assign(1, 0);
+        for (const NTerm& t : uterms) {
+            const int32_t code = plan.code_of_col[t.col];
+            const bool range = !is_in_kind(t.kind) && term_cost(t) == 2;
+            if (code >= 0 && (range || plan.codes[code].all_terms)) {
+                const std::vector<uint64_t>& keys = plan.codes[code].keys;
+                term_intervals(t, static_cast<uint32_t>(tab.cols[t.col].dtype), ivs);
+                for (const auto& iv : ivs) {
+                    const uint32_t r0 =
+                        static_cast<uint32_t>(std::lower_bound(keys.begin(), keys.end(), iv.first) - keys.begin());
+                    const uint32_t r1 =
+                        static_cast<uint32_t>(std::upper_bound(keys.begin(), keys.end(), iv.second) - keys.begin());
+                    plan.span.push_back({r0, r1});
+                }
+            }
+            plan.span_off.push_back(static_cast<uint32_t>(plan.span.size()));
         }
     }
 
@@ -1249,7 +1272,7 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
     const bool all_wide = force_wide || passes.size() > 1;
     for (auto& ps : passes) {
         if (gace_status st = build_pass(ctx, tab, ps, uterms, plan.pred_u, sets, plan.want_marg, all_wide,
-                                        wide_warps, plan.codes, plan.code_of_col))
+                                        wide_warps, plan))
             return st;
         pass_sizes(ps);
     }

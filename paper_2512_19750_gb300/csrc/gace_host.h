@@ -311,6 +311,21 @@ struct NTerm {
     bool operator<(const NTerm& o) const {
         return std::tie(col, kind, a, b, in) < std::tie(o.col, o.kind, o.a, o.b, o.in);
     }
+    bool operator==(const NTerm& o) const {
+        return col == o.col && kind == o.kind && a == o.a && b == o.b && in == o.in;
+    }
+};
+// Hash of a normalised term (deduplication of a request's terms).
+struct NTermHash {
+    size_t operator()(const NTerm& t) const {
+        auto mix = [](uint64_t h, uint64_t v) {
+            h ^= v + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+            return h * 0xBF58476D1CE4E5B9ull;
+        };
+        uint64_t h = mix(mix(mix(t.col, t.kind), t.a), t.b);
+        for (uint32_t w : t.in) h = mix(h, w);
+        return static_cast<size_t>(h ^ (h >> 31));
+    }
 };
 
 gace_status normalize_term(const gace_term& t, int dtype, const gace_scalar* in_values, uint32_t nin, NTerm& out);
@@ -465,6 +480,10 @@ struct ProbePlan {
     std::vector<Pass> passes;
     std::vector<RankCode> codes;       // rank-coded columns
     std::vector<int32_t> code_of_col;  // column -> codes index, -1 if not coded
+    // per unique term read by rank, its key intervals as column endpoint
+    // indices [r0, r1): span[span_off[u] .. span_off[u + 1])
+    std::vector<uint32_t> span_off;
+    std::vector<std::pair<uint32_t, uint32_t>> span;
 };
 
 // Argument checks that need no table.
