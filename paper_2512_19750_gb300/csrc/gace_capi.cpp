@@ -669,8 +669,14 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
             }
         }
         A.ranks_only = 1;
-        for (uint32_t s = 0; s < nslots; ++s)
+        bool all_ranked = nslots > 0;  // every term of the pass read by rank
+        for (uint32_t s = 0; s < nslots; ++s) {
             if (A.slots[s].rend > A.slots[s].rbeg && !A.slots[s].rstride) A.ranks_only = 0;
+            if (!A.slots[s].rstride || A.slots[s].iend != A.slots[s].rend) all_ranked = false;
+        }
+        for (uint32_t s = 0; s < nslots && all_ranked; ++s)
+            all_ranked = codes[code_of_col[ps.slots[s].first]].hist;
+        ps.hist_marg = want_marg && all_ranked;
         // one interval tree per full group of 32 range terms of a column (and
         // per last group of at least kTreeMin); fewer terms are cheaper by compare
         for (uint32_t s = 0; s < nslots; ++s) {
@@ -708,7 +714,7 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
     A.npreds = static_cast<uint32_t>(ps.preds.size());
     A.npool = static_cast<uint32_t>(ps.pool.size());
     A.npredterms = static_cast<uint32_t>(ps.pterm.size());
-    A.want_marg = want_marg ? 1u : 0u;
+    A.want_marg = want_marg && !ps.hist_marg ? 1u : 0u;
     A.timeout_ns = ctx->timeout_ns;
     A.nwarps = narrow ? static_cast<uint32_t>(kProbeWarps) : wide_warps;
 
@@ -1103,6 +1109,9 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
             rc.col = c;
             rc.dtype = static_cast<uint32_t>(tab.cols[c].dtype);
             build_rank_tree(rc);
+            // marginals by rank histogram: one shared-memory counter per set and rank
+            rc.hist = plan.want_marg &&
+                      rc.tree.size() * 4 + sets.size() * (rc.keys.size() + 1) * 4 <= kRankHistSmem;
             plan.code_of_col[c] = static_cast<int32_t>(plan.codes.size());
             plan.codes.push_back(std::move(rc));
         }
@@ -1332,12 +1341,34 @@ void assemble_probe(const ProbePlan& plan, const ProbeRequest& r,
     for (uint32_t k = 0; k < passes.size(); ++k)
         for (uint32_t i = 0; i < passes[k].uterms.size(); ++i)
             uloc[passes[k].uterms[i]] = {static_cast<int32_t>(k), i};
+    // rank-histogram marginals: per coded column and set, pre[r] = the set's
+    // rows of rank < r; a row of rank r holds a term whose interval spans
+    // column endpoints [r0, r1) when r0 < r <= r1
+    std::vector<std::vector<uint64_t>> pre(plan.codes.size());
+    auto hist_marg = [&](uint32_t u, uint32_t ds) -> uint64_t {
+        const int32_t code = plan.code_of_col[plan.uterms[u].col];
+        const RankCode& rc = plan.codes[code];
+        const uint64_t bins = rc.keys.size() + 1;
+        std::vector<uint64_t>& p = pre[code];
+        if (p.empty()) {
+            p.assign(plan.sets.size() * (bins + 1), 0);
+            for (size_t q = 0; q < plan.sets.size(); ++q)
+                for (uint64_t r = 0; r < bins; ++r)
+                    p[q * (bins + 1) + r + 1] = p[q * (bins + 1) + r] + rc.hist_host[q * bins + r];
+        }
+        const uint64_t* pq = p.data() + ds * (bins + 1);
+        uint64_t n = 0;
+        for (uint32_t i = plan.span_off[u]; i < plan.span_off[u + 1]; ++i)
+            n += pq[plan.span[i].second + 1] - pq[plan.span[i].first + 1];
+        return n;
+    };
     auto marg_of = [&](uint32_t t, uint32_t s) -> uint64_t {
         const uint32_t u = plan.t2u[t];
         if (u == UINT32_MAX) return 0;
         const auto& L = uloc[u];
         if (L.first < 0 || plan.set_dev[s] < 0) return 0;
         const Pass& ps = passes[L.first];
+        if (ps.hist_marg) return hist_marg(u, static_cast<uint32_t>(plan.set_dev[s]));
         return pass_out[L.first][static_cast<uint64_t>(ps.args.nsets) * ps.args.npreds +
                                  static_cast<uint64_t>(plan.set_dev[s]) * ps.args.nterms + L.second];
     };
@@ -1412,10 +1443,14 @@ gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts, TableRe
             ps.out_off = ws.take(ps.out_bytes);
             any_pass = true;
         }
-    std::vector<std::vector<uint64_t>> tree_off(parts.size());
+    // rank histograms of the row sets (marginals), zeroed and read back
+    std::vector<std::vector<uint64_t>> tree_off(parts.size()), hist_off(parts.size());
     for (size_t i = 0; i < parts.size(); ++i)
-        for (const RankCode& rc : parts[i].plan.codes)
+        for (const RankCode& rc : parts[i].plan.codes) {
             tree_off[i].push_back(rc.used ? ws.take(rc.tree.size() * 4ull) : 0);
+            const uint64_t bins = parts[i].plan.sets.size() * (rc.keys.size() + 1);
+            hist_off[i].push_back(rc.used && rc.hist ? ws.take(bins * 8) : 0);
+        }
     const uint64_t io_end = ws.off;
     // Rows per chunk: a table whose copy is pending (one part) streams in
     // chunks of rows, a multiple of every pass's tile, each chunk running
@@ -1436,11 +1471,13 @@ gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts, TableRe
         const uint64_t crows = round_up(chunk[i], kSliceRows);
         // A part with several wide passes over hashed row sets computes every
         // slice's row-set masks once (per chunk), for all its passes to load.
+        // (and so does a rank pass that counts hashed sets)
         uint32_t wide = 0;
         for (const auto& ps : pl.passes) wide += ps.args.narrow ? 0u : 1u;
-        bool hashed = false;
+        bool hashed = false, hist = false;
         for (const auto& sp : pl.sets) hashed = hashed || sp.d.mode == 2;
-        if (wide >= 2 && hashed) mask_off[i] = ws.take((crows / kSliceRows) * pl.sets.size() * 16);
+        for (const RankCode& rc : pl.codes) hist = hist || (rc.used && rc.hist);
+        if ((wide >= 2 || hist) && hashed) mask_off[i] = ws.take((crows / kSliceRows) * pl.sets.size() * 16);
         for (const RankCode& rc : pl.codes) rank_off[i].push_back(rc.used ? ws.take(crows * 2) : 0);
     }
     if (gace_status st = ctx->ensure_ws(ws.off)) return st;
@@ -1462,6 +1499,12 @@ gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts, TableRe
         CK(cudaMemcpyAsync(dws + first_in, pin + first_in, io_end - first_in, cudaMemcpyHostToDevice, ctx->stream));
         for (auto& pp : parts)
             for (auto& ps : pp.plan.passes) CK(cudaMemsetAsync(dws + ps.out_off, 0, ps.out_bytes, ctx->stream));
+        for (size_t i = 0; i < parts.size(); ++i)
+            for (size_t c = 0; c < parts[i].plan.codes.size(); ++c)
+                if (hist_off[i][c])
+                    CK(cudaMemsetAsync(dws + hist_off[i][c], 0,
+                                       parts[i].plan.sets.size() * (parts[i].plan.codes[c].keys.size() + 1) * 8,
+                                       ctx->stream));
     }
     CK(cudaMemsetAsync(dws + status_off, 0, 256, ctx->stream));
     uint64_t nload = 0;  // chunks of the pending copy
@@ -1523,6 +1566,17 @@ gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts, TableRe
                 ra.dtype = rc.dtype;
                 ra.levels = rc.levels;
                 ra.m = static_cast<uint32_t>(rc.keys.size());
+                if (hist_off[i][c]) {
+                    ra.hist = reinterpret_cast<unsigned long long*>(dws + hist_off[i][c]);
+                    ra.setmask = masks;
+                    ra.nsets = static_cast<uint32_t>(pp.plan.sets.size());
+                    for (uint32_t q = 0; q < ra.nsets; ++q) {
+                        const SetDesc& d = pp.plan.sets[q].d;
+                        if (d.kind == 0 || d.mode == 1) ra.full_sets |= 1u << q;
+                    }
+                    if (!masks && ra.full_sets != (1u << ra.nsets) - 1u)
+                        return fail(GACE_EINVAL, "rank histograms of hashed sets without their masks");
+                }
                 ranks[rc.col] = ra.out;
                 CK(ctx->traced("probe_rank", rows, rows * (w + 2), rows,
                                [&] { return rank_launch(ra, ctx->sms, ctx->stream); }));
@@ -1537,6 +1591,10 @@ gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts, TableRe
     ctx->collect();
     if (lazy) lazy->pending.clear();  // the stream waited for every chunk's copy
     if (gace_status st = read_status(ctx, *reinterpret_cast<unsigned int*>(pin + status_off))) return st;
+    for (size_t i = 0; i < parts.size(); ++i)
+        for (size_t c = 0; c < parts[i].plan.codes.size(); ++c)
+            parts[i].plan.codes[c].hist_host =
+                hist_off[i][c] ? reinterpret_cast<const unsigned long long*>(pin + hist_off[i][c]) : nullptr;
     for (auto& pp : parts) {
         std::vector<const unsigned long long*> outs;
         for (auto& ps : pp.plan.passes) outs.push_back(reinterpret_cast<const unsigned long long*>(pin + ps.out_off));

@@ -410,6 +410,9 @@ struct Pass {
     uint64_t ops_per_row = 0;          // compares per row (statistics)
     uint32_t rowbytes = 0;             // bytes per row of the referenced columns
     uint64_t in_bytes = 0, out_bytes = 0;
+    // the marginals of every term come from the rank histograms of their
+    // columns (all terms rank-coded), not from the pass's counters
+    bool hist_marg = false;
 };
 
 struct Ws {
@@ -460,6 +463,8 @@ struct RankCode {
     uint32_t levels = 0;
     bool all_terms = false;      // EQ and IN terms too (each value a one-key interval)
     bool used = false;           // some wide pass of the plan reads the column's ranks
+    bool hist = false;           // the rank pass counts each row set's ranks (marginals)
+    const unsigned long long* hist_host = nullptr;  // after a run: [set][rank] counts
 };
 // Most endpoints a column may have to be rank-coded: each group of 32 of its
 // range terms then holds endpoints + 1 mask words of the pass's shared pool.
@@ -467,6 +472,8 @@ struct RankCode {
 #define GACE_RANK_PLAN_MAX 2047
 #endif
 constexpr uint32_t kRankPlanMax = GACE_RANK_PLAN_MAX;
+// Most shared memory of a rank pass that also counts its row sets' ranks.
+constexpr uint64_t kRankHistSmem = 96u << 10;
 
 struct ProbePlan {
     const TableRec* tab = nullptr;

@@ -187,21 +187,30 @@ cudaError_t probe_launch(const ProbeArgs& a, int grid, cudaStream_t s);
 // of the column's range endpoints <= the order-preserving key of row r (at most
 // m), for rows [0, nout) (rows >= nrows get 0), from the endpoints' search tree
 // (level order, 2^levels - 1 keys padded with the largest key; 32-bit keys, or
-// (lo, hi) word pairs for 64-bit columns).
+// (lo, hi) word pairs for 64-bit columns).  With hist, also the histogram of
+// the ranks of each row set's rows, added to hist[q * (m + 1) + rank]: set q
+// holds every row when bit q of full_sets is set, else the rows whose bit is
+// set in its mask of their 128-row slice, setmask[slice * nsets + q] (bit l of
+// word i: row 4 l + i of the slice).
 struct RankArgs {
     const void* col;        // the column's first row of the range scanned
     uint64_t nrows;
     uint64_t nout;          // nrows rounded up to a multiple of 128
     const uint32_t* tree;
     uint16_t* out;
+    unsigned long long* hist;  // nullptr: no histograms
+    const uint4* setmask;      // nullptr when every set holds every row
     uint32_t dtype;
     uint32_t levels;        // 1..13
     uint32_t m;             // endpoints (<= 8191)
+    uint32_t nsets;         // row sets of the histograms (<= kMaxSets)
+    uint32_t full_sets;
     uint32_t pad;
 };
 constexpr uint32_t kRankMaxEndpoints = 8191;
 constexpr uint32_t kRankMap16 = 0x80000000u;  // SlotDesc::rmap: the map has 16-bit entries
 cudaError_t rank_launch(const RankArgs& a, int sms, cudaStream_t s);
+uint32_t rank_smem(const RankArgs& a);  // shared memory of a rank launch (bytes)
 
 // The row-set masks of every 128-row slice of a pass's table into a.setmask
 // (writable), for the wide passes that follow to load instead of hashing.

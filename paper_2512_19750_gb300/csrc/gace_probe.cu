@@ -102,14 +102,19 @@ __global__ void __launch_bounds__(256) k_probe_setmask(const __grid_constant__ P
 }
 
 // Rank coding of one column (RankArgs): the endpoints' search tree staged in
-// shared memory, then four rows per thread per step, their descents interleaved
-// level by level (one compare each), to the number of endpoints <= each key.
+// shared memory, then four rows per thread per step, their descents
+// interleaved level by level (one compare each), to the number of endpoints
+// <= each key; with histograms, each row's rank is counted in a shared-memory
+// histogram of every set that holds it, added to the global one at the end.
 __global__ void __launch_bounds__(256) k_probe_rank(const __grid_constant__ RankArgs A) {
     extern __shared__ uint32_t tree[];
     const bool is64 = A.dtype == 1;
     const uint32_t nkeys = (1u << A.levels) - 1u;
     const uint32_t words = is64 ? 2u * nkeys : nkeys;
+    uint32_t* hist = tree + words;  // [set][rank], when A.hist
+    const uint32_t bins = A.hist ? A.nsets * (A.m + 1) : 0u;
     for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) tree[i] = A.tree[i];
+    for (uint32_t i = threadIdx.x; i < bins; i += blockDim.x) hist[i] = 0;
     __syncthreads();
     const uint32_t width = is64 ? 8u : 4u;
     const uint64_t step = static_cast<uint64_t>(gridDim.x) * blockDim.x * 4u;
@@ -144,6 +149,28 @@ __global__ void __launch_bounds__(256) k_probe_rank(const __grid_constant__ Rank
             rk[i] = r0 + i < A.nrows ? (r < A.m ? r : A.m) : 0u;
         }
         *reinterpret_cast<uint2*>(A.out + r0) = make_uint2(rk[0] | (rk[1] << 16), rk[2] | (rk[3] << 16));
+        if (A.hist) {
+            const uint32_t pos = static_cast<uint32_t>(r0 & 127u) >> 2;  // the quad's lane in its slice
+            for (uint32_t s = 0; s < A.nsets; ++s) {
+                uint32_t member = 0;  // bit i: row r0 + i is in set s
+                if ((A.full_sets >> s) & 1u) {
+                    member = 0xFu;
+                } else {
+                    const uint4 km = A.setmask[(r0 >> 7) * A.nsets + s];
+                    member = ((km.x >> pos) & 1u) | (((km.y >> pos) & 1u) << 1) | (((km.z >> pos) & 1u) << 2) |
+                             (((km.w >> pos) & 1u) << 3);
+                }
+                uint32_t* hs = hist + s * (A.m + 1);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (((member >> i) & 1u) && r0 + i < A.nrows) atomicAdd(hs + rk[i], 1u);
+            }
+        }
+    }
+    if (A.hist) {
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < bins; i += blockDim.x)
+            if (hist[i]) atomicAdd(A.hist + i, static_cast<unsigned long long>(hist[i]));
     }
 }
 
@@ -221,17 +248,29 @@ int probe_occupancy(const ProbeArgs& a) {
     return e == cudaSuccess ? n : 0;
 }
 
-cudaError_t rank_launch(const RankArgs& a, int sms, cudaStream_t s) {
+uint32_t rank_smem(const RankArgs& a) {
     const uint32_t nkeys = (1u << a.levels) - 1u;
-    const uint32_t smem = nkeys * (a.dtype == 1 ? 8u : 4u);
+    return nkeys * (a.dtype == 1 ? 8u : 4u) + (a.hist ? a.nsets * (a.m + 1) * 4u : 0u);
+}
+
+cudaError_t rank_launch(const RankArgs& a, int sms, cudaStream_t s) {
+    const uint32_t smem = rank_smem(a);
     cudaError_t e = cudaFuncSetAttribute(k_probe_rank, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_rank, 256, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    // a full wave of resident CTAs (each histogram flush costs one global add per bin)
     const uint64_t quads = a.nout / 4;
-    const uint64_t cap = static_cast<uint64_t>(sms) * 8 * 256;  // eight 256-thread CTAs per SM
-    const uint64_t threads = quads < cap ? quads : cap;
-    const int grid = static_cast<int>(threads ? (threads + 255) / 256 : 1);
-    k_probe_rank<<<grid, 256, smem, s>>>(a);
+    const uint64_t cap = static_cast<uint64_t>(sms) * static_cast<uint64_t>(per_sm) * 256;
+    uint64_t threads = quads < cap ? quads : cap;
+    uint64_t grid = threads ? (threads + 255) / 256 : 1;
+    // each CTA keeps 32-bit counts of the rows it ranks
+    while (a.hist && (quads + grid * 256 - 1) / (grid * 256) * 1024 >= (1ull << 31)) grid *= 2;
+    if (grid > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;
+    k_probe_rank<<<static_cast<int>(grid), 256, smem, s>>>(a);
     return cudaGetLastError();
 }
 
