@@ -1109,9 +1109,10 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
             rc.col = c;
             rc.dtype = static_cast<uint32_t>(tab.cols[c].dtype);
             build_rank_tree(rc);
-            // marginals by rank histogram: one shared-memory counter per set and rank
-            rc.hist = plan.want_marg &&
-                      rc.tree.size() * 4 + sets.size() * (rc.keys.size() + 1) * 4 <= kRankHistSmem;
+            // marginals (and single-term counts) by rank histogram: one
+            // shared-memory counter per set and rank
+            rc.hist_fits = rc.tree.size() * 4 + sets.size() * (rc.keys.size() + 1) * 4 <= kRankHistSmem;
+            rc.hist = plan.want_marg && rc.hist_fits;
             plan.code_of_col[c] = static_cast<int32_t>(plan.codes.size());
             plan.codes.push_back(std::move(rc));
         }
@@ -1132,6 +1133,18 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
                 }
             }
             plan.span_off.push_back(static_cast<uint32_t>(plan.span.size()));
+        }
+        // a batch's single-term predicates on such columns are counted from
+        // the rank histograms (their count is their term's marginal)
+        if (npreds > static_cast<uint32_t>(kNarrowMax)) {
+            for (uint32_t p = 0; p < npreds; ++p) {
+                if (plan.pstate[p] != 0 || plan.pred_u[p].size() != 1) continue;
+                const uint32_t u = plan.pred_u[p][0];
+                const int32_t code = plan.code_of_col[uterms[u].col];
+                if (code < 0 || !plan.codes[code].hist_fits || plan.span_off[u + 1] == plan.span_off[u]) continue;
+                plan.pstate[p] = 3;
+                plan.codes[code].hist = true;
+            }
         }
     }
 
@@ -1164,12 +1177,19 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
         const uint64_t nsets_dev = sets.size();
         const int ctas = wide_warps >= 16 ? 2 : kWideCtas;
         const uint64_t smem_budget = static_cast<uint64_t>(ctx->smem_per_sm) / ctas - 1024;
+        // (no marginal counters when the rank histograms count every term's)
+        bool marg_counters = plan.want_marg;
+        if (marg_counters) {
+            bool all_hist = true;
+            for (uint32_t u = 0; u < uterms.size() && all_hist; ++u) all_hist = plan.hist_term(u);
+            marg_counters = !all_hist;
+        }
         auto wide_smem = [&](uint64_t nt, uint64_t np, uint64_t npt, uint64_t pool) {
             uint64_t off = 128 + nt * 16;
             off = round_up(off + pool * 4, 16) + (np + 1) * 4;
             off = round_up(off + npt * 4, 16);
             off += static_cast<uint64_t>(wide_warps) * (nt + nsets_dev) * 16 + nsets_dev * np * 4;
-            off += plan.want_marg ? nsets_dev * nt * 4 : 0;
+            off += marg_counters ? nsets_dev * nt * 4 : 0;
             return round_up(off + nsets_dev * 4, 16);
         };
         // the pass's columns and pool words with the terms `add` added
@@ -1251,9 +1271,10 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
             pred_terms += pu.size();
         }
         // terms whose marginals are wanted but that no device predicate placed
+        // (and that no rank histogram counts)
         if (plan.want_marg) {
             for (uint32_t u = 0; u < uterms.size(); ++u) {
-                if (u_pass[u] >= 0) continue;
+                if (u_pass[u] >= 0 || plan.hist_term(u)) continue;
                 add.assign(1, u);
                 touched.clear();
                 uint64_t total = with_terms(add, touched);
@@ -1364,11 +1385,11 @@ void assemble_probe(const ProbePlan& plan, const ProbeRequest& r,
     };
     auto marg_of = [&](uint32_t t, uint32_t s) -> uint64_t {
         const uint32_t u = plan.t2u[t];
-        if (u == UINT32_MAX) return 0;
+        if (u == UINT32_MAX || plan.set_dev[s] < 0) return 0;
+        if (plan.hist_term(u)) return hist_marg(u, static_cast<uint32_t>(plan.set_dev[s]));
         const auto& L = uloc[u];
-        if (L.first < 0 || plan.set_dev[s] < 0) return 0;
+        if (L.first < 0) return 0;
         const Pass& ps = passes[L.first];
-        if (ps.hist_marg) return hist_marg(u, static_cast<uint32_t>(plan.set_dev[s]));
         return pass_out[L.first][static_cast<uint64_t>(ps.args.nsets) * ps.args.npreds +
                                  static_cast<uint64_t>(plan.set_dev[s]) * ps.args.nterms + L.second];
     };
@@ -1379,6 +1400,7 @@ void assemble_probe(const ProbePlan& plan, const ProbeRequest& r,
     assemble_probe_counts(
         plan, r, [&](uint32_t s) { return ns[s]; },
         [&](uint32_t p, uint32_t s) -> uint64_t {
+            if (plan.pstate[p] == 3) return hist_marg(plan.pred_u[p][0], static_cast<uint32_t>(plan.set_dev[s]));
             const Pass& ps = passes[ploc[p].first];
             return pass_out[ploc[p].first][static_cast<uint64_t>(plan.set_dev[s]) * ps.args.npreds + ploc[p].second];
         },
@@ -1447,9 +1469,9 @@ gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts, TableRe
     std::vector<std::vector<uint64_t>> tree_off(parts.size()), hist_off(parts.size());
     for (size_t i = 0; i < parts.size(); ++i)
         for (const RankCode& rc : parts[i].plan.codes) {
-            tree_off[i].push_back(rc.used ? ws.take(rc.tree.size() * 4ull) : 0);
+            tree_off[i].push_back(rc.used || rc.hist ? ws.take(rc.tree.size() * 4ull) : 0);
             const uint64_t bins = parts[i].plan.sets.size() * (rc.keys.size() + 1);
-            hist_off[i].push_back(rc.used && rc.hist ? ws.take(bins * 8) : 0);
+            hist_off[i].push_back(rc.hist ? ws.take(bins * 8) : 0);
         }
     const uint64_t io_end = ws.off;
     // Rows per chunk: a table whose copy is pending (one part) streams in
@@ -1476,7 +1498,7 @@ gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts, TableRe
         for (const auto& ps : pl.passes) wide += ps.args.narrow ? 0u : 1u;
         bool hashed = false, hist = false;
         for (const auto& sp : pl.sets) hashed = hashed || sp.d.mode == 2;
-        for (const RankCode& rc : pl.codes) hist = hist || (rc.used && rc.hist);
+        for (const RankCode& rc : pl.codes) hist = hist || rc.hist;
         if ((wide >= 2 || hist) && hashed) mask_off[i] = ws.take((crows / kSliceRows) * pl.sets.size() * 16);
         for (const RankCode& rc : pl.codes) rank_off[i].push_back(rc.used ? ws.take(crows * 2) : 0);
     }
@@ -1492,7 +1514,7 @@ gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts, TableRe
     for (size_t i = 0; i < parts.size(); ++i)
         for (size_t c = 0; c < parts[i].plan.codes.size(); ++c) {
             const RankCode& rc = parts[i].plan.codes[c];
-            if (rc.used) memcpy(pin + tree_off[i][c], rc.tree.data(), rc.tree.size() * 4ull);
+            if (rc.used || rc.hist) memcpy(pin + tree_off[i][c], rc.tree.data(), rc.tree.size() * 4ull);
         }
     const uint64_t first_in = status_off + 256;
     if (io_end > first_in) {
@@ -1555,14 +1577,14 @@ gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts, TableRe
             }
             for (size_t c = 0; c < pp.plan.codes.size(); ++c) {
                 const RankCode& rc = pp.plan.codes[c];
-                if (!rc.used) continue;
+                if (!rc.used && !rc.hist) continue;  // ranks for the passes, or histograms only
                 RankArgs ra{};
                 const uint32_t w = dtype_width(static_cast<int>(rc.dtype));
                 ra.col = static_cast<const unsigned char*>(tab->cols[rc.col].dptr) + r0 * w;
                 ra.nrows = rows;
                 ra.nout = round_up(rows, kSliceRows);
                 ra.tree = reinterpret_cast<const uint32_t*>(dws + tree_off[i][c]);
-                ra.out = reinterpret_cast<uint16_t*>(dws + rank_off[i][c]);
+                ra.out = rc.used ? reinterpret_cast<uint16_t*>(dws + rank_off[i][c]) : nullptr;
                 ra.dtype = rc.dtype;
                 ra.levels = rc.levels;
                 ra.m = static_cast<uint32_t>(rc.keys.size());
@@ -1578,7 +1600,7 @@ gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts, TableRe
                         return fail(GACE_EINVAL, "rank histograms of hashed sets without their masks");
                 }
                 ranks[rc.col] = ra.out;
-                CK(ctx->traced("probe_rank", rows, rows * (w + 2), rows,
+                CK(ctx->traced("probe_rank", rows, rows * (w + (rc.used ? 2 : 0)), rows,
                                [&] { return rank_launch(ra, ctx->sms, ctx->stream); }));
             }
             for (auto& ps : pp.plan.passes)

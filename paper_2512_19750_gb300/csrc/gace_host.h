@@ -463,6 +463,7 @@ struct RankCode {
     uint32_t levels = 0;
     bool all_terms = false;      // EQ and IN terms too (each value a one-key interval)
     bool used = false;           // some wide pass of the plan reads the column's ranks
+    bool hist_fits = false;      // its histograms fit the rank pass's shared memory
     bool hist = false;           // the rank pass counts each row set's ranks (marginals)
     const unsigned long long* hist_host = nullptr;  // after a run: [set][rank] counts
 };
@@ -481,7 +482,7 @@ struct ProbePlan {
     std::vector<int32_t> set_dev;  // sample -> device set, -1 if empty
     std::vector<NTerm> uterms;
     std::vector<uint32_t> t2u;     // input term -> unique term (UINT32_MAX: never true)
-    std::vector<uint8_t> pstate;   // 0 device, 1 never true, 2 always true
+    std::vector<uint8_t> pstate;   // 0 device, 1 never true, 2 always true, 3 from rank histograms
     std::vector<std::vector<uint32_t>> pred_u;
     bool want_marg = false;
     std::vector<Pass> passes;
@@ -491,6 +492,12 @@ struct ProbePlan {
     // indices [r0, r1): span[span_off[u] .. span_off[u + 1])
     std::vector<uint32_t> span_off;
     std::vector<std::pair<uint32_t, uint32_t>> span;
+    // unique term u's marginals (and, for a single-term predicate, its count)
+    // come from its column's rank histograms
+    bool hist_term(uint32_t u) const {
+        if (u + 1 >= span_off.size() || span_off[u + 1] == span_off[u]) return false;
+        return codes[code_of_col[uterms[u].col]].hist;
+    }
 };
 
 // Argument checks that need no table.
@@ -545,7 +552,7 @@ void assemble_probe_counts(const ProbePlan& plan, const ProbeRequest& r, NsOf&& 
             uint64_t m = 0;
             if (plan.pstate[p] == 2)
                 m = ns;
-            else if (plan.pstate[p] == 0 && plan.set_dev[s] >= 0)
+            else if ((plan.pstate[p] == 0 || plan.pstate[p] == 3) && plan.set_dev[s] >= 0)
                 m = match_of(p, s);
             gace_pred_result& res = r.results[static_cast<uint64_t>(s) * npreds + p];
             res.match = m;

@@ -197,7 +197,7 @@ struct RankArgs {
     uint64_t nrows;
     uint64_t nout;          // nrows rounded up to a multiple of 128
     const uint32_t* tree;
-    uint16_t* out;
+    uint16_t* out;             // nullptr: histograms only
     unsigned long long* hist;  // nullptr: no histograms
     const uint4* setmask;      // nullptr when every set holds every row
     uint32_t dtype;

@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(256) k_probe_rank(const __grid_constant__ Rank
             const uint32_t r = n[i] - (1u << A.levels);
             rk[i] = r0 + i < A.nrows ? (r < A.m ? r : A.m) : 0u;
         }
-        *reinterpret_cast<uint2*>(A.out + r0) = make_uint2(rk[0] | (rk[1] << 16), rk[2] | (rk[3] << 16));
+        if (A.out) *reinterpret_cast<uint2*>(A.out + r0) = make_uint2(rk[0] | (rk[1] << 16), rk[2] | (rk[3] << 16));
         if (A.hist) {
             const uint32_t pos = static_cast<uint32_t>(r0 & 127u) >> 2;  // the quad's lane in its slice
             for (uint32_t s = 0; s < A.nsets; ++s) {
