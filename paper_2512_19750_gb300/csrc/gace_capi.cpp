@@ -1477,7 +1477,7 @@ gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts, TableRe
     // Rows per chunk: a table whose copy is pending (one part) streams in
     // chunks of rows, a multiple of every pass's tile, each chunk running
     // every pass; so does a table whose ranks would not fit kRankScratch.
-    std::vector<uint64_t> chunk(parts.size(), 0), mask_off(parts.size(), 0);
+    std::vector<uint64_t> chunk(parts.size(), 0), mask_off(parts.size(), 0), qmask_off(parts.size(), 0);
     std::vector<std::vector<uint64_t>> rank_off(parts.size());
     for (size_t i = 0; i < parts.size(); ++i) {
         const ProbePlan& pl = parts[i].plan;
@@ -1500,6 +1500,7 @@ gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts, TableRe
         for (const auto& sp : pl.sets) hashed = hashed || sp.d.mode == 2;
         for (const RankCode& rc : pl.codes) hist = hist || rc.hist;
         if ((wide >= 2 || hist) && hashed) mask_off[i] = ws.take((crows / kSliceRows) * pl.sets.size() * 16);
+        if (hist && hashed) qmask_off[i] = ws.take(crows);  // one word per quad
         for (const RankCode& rc : pl.codes) rank_off[i].push_back(rc.used ? ws.take(crows * 2) : 0);
     }
     if (gace_status st = ctx->ensure_ws(ws.off)) return st;
@@ -1567,13 +1568,14 @@ gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts, TableRe
             const uint64_t r0 = whole ? 0 : k * step, rows = whole ? n : std::min(step, n - r0);
             if (lazy && k < nload) CK(cudaStreamWaitEvent(ctx->stream, ctx->chunk_events[k], 0));
             uint4* masks = nullptr;
+            uint32_t* qmask = qmask_off[i] ? reinterpret_cast<uint32_t*>(dws + qmask_off[i]) : nullptr;
             if (mask_off[i]) {
                 masks = reinterpret_cast<uint4*>(dws + mask_off[i]);
                 ProbeArgs a0 = pp.plan.passes.front().args;
                 a0.nrows = rows;
                 a0.row0 = r0;
                 CK(ctx->traced("probe_setmask", rows, 0, rows,
-                               [&] { return setmask_launch(a0, masks, ctx->sms, ctx->stream); }));
+                               [&] { return setmask_launch(a0, masks, qmask, ctx->sms, ctx->stream); }));
             }
             for (size_t c = 0; c < pp.plan.codes.size(); ++c) {
                 const RankCode& rc = pp.plan.codes[c];
@@ -1590,13 +1592,13 @@ gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts, TableRe
                 ra.m = static_cast<uint32_t>(rc.keys.size());
                 if (hist_off[i][c]) {
                     ra.hist = reinterpret_cast<unsigned long long*>(dws + hist_off[i][c]);
-                    ra.setmask = masks;
+                    ra.qmask = qmask;
                     ra.nsets = static_cast<uint32_t>(pp.plan.sets.size());
                     for (uint32_t q = 0; q < ra.nsets; ++q) {
                         const SetDesc& d = pp.plan.sets[q].d;
                         if (d.kind == 0 || d.mode == 1) ra.full_sets |= 1u << q;
                     }
-                    if (!masks && ra.full_sets != (1u << ra.nsets) - 1u)
+                    if (!qmask && ra.full_sets != (1u << ra.nsets) - 1u)
                         return fail(GACE_EINVAL, "rank histograms of hashed sets without their masks");
                 }
                 ranks[rc.col] = ra.out;

@@ -189,9 +189,8 @@ cudaError_t probe_launch(const ProbeArgs& a, int grid, cudaStream_t s);
 // (level order, 2^levels - 1 keys padded with the largest key; 32-bit keys, or
 // (lo, hi) word pairs for 64-bit columns).  With hist, also the histogram of
 // the ranks of each row set's rows, added to hist[q * (m + 1) + rank]: set q
-// holds every row when bit q of full_sets is set, else the rows whose bit is
-// set in its mask of their 128-row slice, setmask[slice * nsets + q] (bit l of
-// word i: row 4 l + i of the slice).
+// holds every row when bit q of full_sets is set, else the rows of each quad
+// (rows 4 j .. 4 j + 3) whose bit 4 q + i is set in qmask[j].
 struct RankArgs {
     const void* col;        // the column's first row of the range scanned
     uint64_t nrows;
@@ -199,7 +198,7 @@ struct RankArgs {
     const uint32_t* tree;
     uint16_t* out;             // nullptr: histograms only
     unsigned long long* hist;  // nullptr: no histograms
-    const uint4* setmask;      // nullptr when every set holds every row
+    const uint32_t* qmask;     // nullptr when every set holds every row
     uint32_t dtype;
     uint32_t levels;        // 1..13
     uint32_t m;             // endpoints (<= 8191)
@@ -212,9 +211,10 @@ constexpr uint32_t kRankMap16 = 0x80000000u;  // SlotDesc::rmap: the map has 16-
 cudaError_t rank_launch(const RankArgs& a, int sms, cudaStream_t s);
 uint32_t rank_smem(const RankArgs& a);  // shared memory of a rank launch (bytes)
 
-// The row-set masks of every 128-row slice of a pass's table into a.setmask
-// (writable), for the wide passes that follow to load instead of hashing.
-cudaError_t setmask_launch(const ProbeArgs& a, uint4* out, int sms, cudaStream_t s);
+// The row-set masks of every 128-row slice of a pass's table into out, for
+// the wide passes that follow to load instead of hashing, and (qmask not
+// nullptr) each quad's membership word for the rank histograms.
+cudaError_t setmask_launch(const ProbeArgs& a, uint4* out, uint32_t* qmask, int sms, cudaStream_t s);
 int probe_occupancy(const ProbeArgs& a);  // CTAs per SM for this kernel and smem size
 
 // ---------------------------------------------------------------- materialised samples

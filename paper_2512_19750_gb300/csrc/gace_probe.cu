@@ -91,14 +91,30 @@ __global__ void GACE_WIDE_BOUNDS k_probe_wide(const __grid_constant__ ProbeArgs 
 }
 
 // Row-set masks of 128-row slices (one warp per slice, grid-striding), the
-// same masks the wide pass would compute, into out[slice * nsets + set].
-__global__ void __launch_bounds__(256) k_probe_setmask(const __grid_constant__ ProbeArgs A, uint4* out) {
-    const int lane = threadIdx.x & 31;
+// same masks the wide pass would compute, into out[slice * nsets + set]; with
+// qmask, also each quad's membership word, qmask[slice * 32 + lane]: bit
+// 4 q + i set when row 4 lane + i of the slice is in set q.
+__global__ void __launch_bounds__(256) k_probe_setmask(const __grid_constant__ ProbeArgs A, uint4* out,
+                                                       uint32_t* qmask) {
+    __shared__ uint4 keep[8][kMaxSets];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t nslices = (A.nrows + kSliceRows - 1) / kSliceRows;
     const uint64_t stride = static_cast<uint64_t>(gridDim.x) * (blockDim.x / 32);
-    for (uint64_t sl = static_cast<uint64_t>(blockIdx.x) * (blockDim.x / 32) + (threadIdx.x >> 5); sl < nslices;
-         sl += stride)
-        set_masks<1>(A, sl * kSliceRows, out + sl * A.nsets, lane);
+    for (uint64_t sl = static_cast<uint64_t>(blockIdx.x) * (blockDim.x / 32) + warp; sl < nslices; sl += stride) {
+        set_masks<1>(A, sl * kSliceRows, keep[warp], lane);
+        __syncwarp();
+        if (lane < static_cast<int>(A.nsets)) out[sl * A.nsets + lane] = keep[warp][lane];
+        if (qmask) {
+            uint32_t w = 0;
+            for (uint32_t q = 0; q < A.nsets; ++q) {
+                const uint4 k = keep[warp][q];
+                w |= (((k.x >> lane) & 1u) | (((k.y >> lane) & 1u) << 1) | (((k.z >> lane) & 1u) << 2) |
+                      (((k.w >> lane) & 1u) << 3)) << (4 * q);
+            }
+            qmask[sl * 32 + lane] = w;
+        }
+        __syncwarp();  // keep[warp] is rewritten for the next slice
+    }
 }
 
 // Rank coding of one column (RankArgs): the endpoints' search tree staged in
@@ -150,20 +166,16 @@ __global__ void __launch_bounds__(256) k_probe_rank(const __grid_constant__ Rank
         }
         if (A.out) *reinterpret_cast<uint2*>(A.out + r0) = make_uint2(rk[0] | (rk[1] << 16), rk[2] | (rk[3] << 16));
         if (A.hist) {
-            const uint32_t pos = static_cast<uint32_t>(r0 & 127u) >> 2;  // the quad's lane in its slice
+            // bit 4 s + i: row r0 + i is in set s
+            const uint32_t valid = r0 + 4 <= A.nrows ? 0xFu : (r0 < A.nrows ? (1u << (A.nrows - r0)) - 1u : 0u);
+            uint32_t member = A.qmask ? A.qmask[r0 >> 2] : 0u;
             for (uint32_t s = 0; s < A.nsets; ++s) {
-                uint32_t member = 0;  // bit i: row r0 + i is in set s
-                if ((A.full_sets >> s) & 1u) {
-                    member = 0xFu;
-                } else {
-                    const uint4 km = A.setmask[(r0 >> 7) * A.nsets + s];
-                    member = ((km.x >> pos) & 1u) | (((km.y >> pos) & 1u) << 1) | (((km.z >> pos) & 1u) << 2) |
-                             (((km.w >> pos) & 1u) << 3);
-                }
+                const uint32_t bits = ((A.full_sets >> s) & 1u) ? valid : ((member >> (4 * s)) & valid);
+                if (!bits) continue;
                 uint32_t* hs = hist + s * (A.m + 1);
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
-                    if (((member >> i) & 1u) && r0 + i < A.nrows) atomicAdd(hs + rk[i], 1u);
+                    if ((bits >> i) & 1u) atomicAdd(hs + rk[i], 1u);
             }
         }
     }
@@ -274,11 +286,11 @@ cudaError_t rank_launch(const RankArgs& a, int sms, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t setmask_launch(const ProbeArgs& a, uint4* out, int sms, cudaStream_t s) {
+cudaError_t setmask_launch(const ProbeArgs& a, uint4* out, uint32_t* qmask, int sms, cudaStream_t s) {
     const uint64_t nslices = (a.nrows + kSliceRows - 1) / kSliceRows;
     const uint64_t warps = static_cast<uint64_t>(sms) * 64;  // a full SM of warps each
     const uint64_t grid = (std::min<uint64_t>(nslices, warps) + 7) / 8;
-    k_probe_setmask<<<static_cast<int>(grid ? grid : 1), 256, 0, s>>>(a, out);
+    k_probe_setmask<<<static_cast<int>(grid ? grid : 1), 256, 0, s>>>(a, out, qmask);
     return cudaGetLastError();
 }
 

@@ -83,10 +83,12 @@ def test_uncoded_column_trees_and_compares(g, gctx, orc):
 
 def test_wide_local_rank_maps(g, gctx, orc):
     """800 IN terms on one int32 column over 2046 consecutive values (2047
-    endpoints, the bound): more terms than one pass holds, so each pass maps
+    endpoints, the bound), each in a two-term predicate so that it is
+    evaluated in a pass: more terms than one pass holds, so each pass maps
     the column's ranks to several hundred local endpoints (16-bit entries).
     The two halves of the terms draw from disjoint value ranges, so no pass
-    holds every endpoint."""
+    holds every endpoint.  Single-term predicates on the same column are
+    counted from the rank histograms."""
     rng = np.random.default_rng(47)
     n = 80_021
     c0 = rng.integers(-20, 2070, n).astype(np.int32)
@@ -95,7 +97,7 @@ def test_wide_local_rank_maps(g, gctx, orc):
     for k in range(800):
         lo, hi = (0, 1023) if k < 400 else (1023, 2046)
         vals = tuple(int(v) for v in rng.integers(lo, hi, 1 + k % 4))
-        preds.append([Term(0, IN, values=vals)])
+        preds.append([Term(0, IN, values=vals), Term(1, RANGE, 0, 60 + k % 7)])
     preds += [[Term(0, IN, values=(0, 2045))], [Term(0, EQ, 1022)], [Term(0, EQ, 1023)]]
     for k in range(40):
         preds.append([Term(0, IN, values=(k, 2045 - k)), Term(1, RANGE, k, k + 30)])
