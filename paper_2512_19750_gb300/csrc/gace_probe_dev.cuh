@@ -274,6 +274,35 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
     return x;
 }
 
+// The 128-row masks of a group of nt <= 32 terms from each lane's four row
+// words (bit t of lane l's word i: term t holds for row 4 l + i): lane t gets
+// term t's.  A group of at most 16 (8) terms packs two (four) row words into
+// one word before the transpose, then fetches the other words of its term from
+// the lanes 16 (8, 16, 24) above.  Bits of w above the group's terms are 0.
+__device__ __forceinline__ uint4 transpose_group(const uint32_t (&w)[4], uint32_t nt, int lane) {
+    uint4 o;
+    if (nt <= 8) {
+        const uint32_t x = transpose32(w[0] | (w[1] << 8) | (w[2] << 16) | (w[3] << 24), lane);
+        o.x = x;
+        o.y = __shfl_down_sync(kFullMask, x, 8);
+        o.z = __shfl_down_sync(kFullMask, x, 16);
+        o.w = __shfl_down_sync(kFullMask, x, 24);
+    } else if (nt <= 16) {
+        const uint32_t a = transpose32(w[0] | (w[1] << 16), lane);
+        const uint32_t b = transpose32(w[2] | (w[3] << 16), lane);
+        o.x = a;
+        o.y = __shfl_down_sync(kFullMask, a, 16);
+        o.z = b;
+        o.w = __shfl_down_sync(kFullMask, b, 16);
+    } else {
+        o.x = transpose32(w[0], lane);
+        o.y = transpose32(w[1], lane);
+        o.z = transpose32(w[2], lane);
+        o.w = transpose32(w[3], lane);
+    }
+    return o;
+}
+
 // Mask of the group's EQ/IN terms that hold for key (lo, hi): the masks of
 // its two candidate slots whose key matches (an empty slot's mask is 0).
 __device__ __forceinline__ uint32_t vs_lookup(const uint32_t* tab, bool is64, uint32_t s1, uint32_t s2, uint32_t lo,
@@ -441,12 +470,16 @@ __device__ __forceinline__ void eval_rank_groups(const SlotDesc& sd, const uint3
 #pragma unroll
         for (int i = 0; i < R; ++i) w[i] = tab[lr[i]];
         uint4 out[NQ];
+        if constexpr (NQ == 1) {
+            out[0] = transpose_group(w, nr - 32u * g, lane);
+        } else {
 #pragma unroll
-        for (int h = 0; h < NQ; ++h) {
-            out[h].x = transpose32(w[4 * h + 0], lane);
-            out[h].y = transpose32(w[4 * h + 1], lane);
-            out[h].z = transpose32(w[4 * h + 2], lane);
-            out[h].w = transpose32(w[4 * h + 3], lane);
+            for (int h = 0; h < NQ; ++h) {
+                out[h].x = transpose32(w[4 * h + 0], lane);
+                out[h].y = transpose32(w[4 * h + 1], lane);
+                out[h].z = transpose32(w[4 * h + 2], lane);
+                out[h].w = transpose32(w[4 * h + 3], lane);
+            }
         }
         const uint32_t k = 32u * g + lane;
         if (k < nr) {
