@@ -234,16 +234,15 @@ def run_reference(args, d: Dist):
 
 def measured_traffic(fam, rows_per_launch):
     """DRAM bytes per launch of a kernel family from its committed ncu capture
-    (profiles/roofline_traffic.json: bytes per row of one captured launch,
-    scaled by rows), or None when there is none or the kernel's sources have
+    (profiles/roofline_traffic.json: bytes per row of the captured launches,
+    scaled by rows), or None when there is none or the kernels' sources have
     changed since the capture."""
     import hashlib
 
     try:
         with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
             rec = json.load(f)
-        if rec.get("kernel") != fam:
-            return None
+        k = rec["kernels"][fam]
         h = hashlib.sha256()
         for src in rec["sources"]:
             with open(os.path.join(ROOT, src), "rb") as f:
@@ -252,7 +251,7 @@ def measured_traffic(fam, rows_per_launch):
         return None
     if h.hexdigest() != rec["sources_sha256"]:
         return None
-    return rec["bytes_per_row"] * rows_per_launch
+    return k["bytes_per_row"] * rows_per_launch
 
 
 def term_evals_per_row(preds):
@@ -263,30 +262,46 @@ def term_evals_per_row(preds):
     return sum(len(t.values) if t.op == IN else 1 for p in preds for t in p)
 
 
-def roofline_of(stats, peaks, sms, alu=None):
-    """Roofline object of the kernel family with the most device time.  For
-    the wide probe pass (integer-bound): achieved term evaluations per second
-    (alu["evals"] of them per step) against the integer lane-op rate that
-    gace_calibrate_int measured on this GPU."""
+# The probe pipeline of one call: row-set masks, the rank pass of every
+# rank-coded column (ranks and per-set rank histograms), the wide passes.
+PROBE_PIPELINE = ("probe_setmask", "probe_rank", "probe_wide")
+
+
+def roofline_of(stats, peaks, sms, steps, alu=None):
+    """Roofline object of the step's dominant work.  When the wide probe pass
+    is the family with the most device time, the probe pipeline as a whole
+    (PROBE_PIPELINE): the batch's term evaluations (alu["evals"] per run)
+    per second of the pipeline's device time, against the integer lane-op
+    rate gace_calibrate_int measured on this GPU; traffic is the pipeline's
+    DRAM bytes per step from the committed captures.  Otherwise the family's
+    algorithmic bytes per second against the measured HBM copy rate."""
     fam, st = max(stats.items(), key=lambda kv: kv[1]["total_ms"])
+    if fam == "probe_wide" and alu is not None:
+        fams = [k for k in PROBE_PIPELINE if k in stats]
+        sec = sum(stats[k]["total_ms"] for k in fams) / 1000.0
+        traffic = 0.0
+        for k in fams:
+            t = measured_traffic(k, stats[k]["rows"] / max(1, stats[k]["launches"]))
+            traffic = None if t is None or traffic is None else traffic + t * stats[k]["launches"] / steps
+        achieved = alu["evals"] / sec / 1e12
+        peak = alu["lane_ops_per_s"] / 1e12
+        nominal = sms * 128 * peaks["sm_max_mhz"] * 1e6 / 1e12
+        return "probe", {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                         "frac": achieved / peak, "traffic": traffic, "traffic_per": "step",
+                         "algorithmic_bytes_per_step": sum(stats[k]["bytes"] for k in fams) / steps,
+                         "work": "term evaluations (EQ 1, RANGE 1, IN-k k per row) of the whole batch",
+                         "kernels": fams,
+                         "device_ms_per_step": {k: stats[k]["total_ms"] / steps for k in fams},
+                         "launches_per_step": {k: stats[k]["launches"] / steps for k in fams},
+                         "peak_source": "measured: gace_calibrate_int kind 0 (32-bit xor/add lane ops) on this GPU",
+                         "lane_ops_per_sm_clk": alu["lane_ops_per_s"] / (sms * peaks["sm_max_mhz"] * 1e6),
+                         "range_tests_per_s_measured": alu["range_tests_per_s"],
+                         "frac_of_range_test_rate": alu["evals"] / sec / alu["range_tests_per_s"],
+                         "frac_of_nominal_128_lanes": achieved / nominal}
     sec = st["total_ms"] / 1000.0
     rows_per_launch = st["rows"] / max(1, st["launches"])
     traffic = measured_traffic(fam, rows_per_launch)
     algo_bytes = st["bytes"] / max(1, st["launches"])
-    if fam == "probe_wide" and alu is not None:
-        achieved = alu["evals"] / sec / 1e12
-        peak = alu["lane_ops_per_s"] / 1e12
-        nominal = sms * 128 * peaks["sm_max_mhz"] * 1e6 / 1e12
-        return fam, {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                     "frac": achieved / peak, "traffic": traffic, "algorithmic_bytes_per_launch": algo_bytes,
-                     "work": "term evaluations (EQ 1, RANGE 1, IN-k k per row)",
-                     "peak_source": "measured: gace_calibrate_int kind 0 (32-bit xor/add lane ops) on this GPU",
-                     "lane_ops_per_sm_clk": alu["lane_ops_per_s"] / (sms * peaks["sm_max_mhz"] * 1e6),
-                     "range_tests_per_s_measured": alu["range_tests_per_s"],
-                     "frac_of_range_test_rate": alu["evals"] / sec / alu["range_tests_per_s"],
-                     "frac_of_nominal_128_lanes": achieved / nominal,
-                     "compare_ops_per_s_range_as_2": st["ops"] / sec,
-                     "launches": st["launches"], "avg_launch_ms": st["total_ms"] / st["launches"]}
     achieved = st["bytes"] / sec / 1e9
     return fam, {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                  "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "algorithmic_bytes_per_launch": algo_bytes,
@@ -342,7 +357,7 @@ def run_gace(args, d: Dist):
     alu = {"evals": float(n) * term_evals_per_row(preds) * args.steps,
            "lane_ops_per_s": g.gace_calibrate_int(ctx, 0, 50),
            "range_tests_per_s": g.gace_calibrate_int(ctx, 1, 50)}
-    fam, roof = roofline_of(stats, peaks, sms, alu)
+    fam, roof = roofline_of(stats, peaks, sms, args.steps, alu)
     roof["kernel"] = fam
     roof["peak_source"] = roof.get("peak_source", f"MEASURED_PEAKS.json hbm_gbs ({peaks['source']})")
     kernels = {k: {"launches": v["launches"], "total_ms": round(v["total_ms"], 3),

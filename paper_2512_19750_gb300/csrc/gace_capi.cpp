@@ -940,6 +940,39 @@ gace_status check_probe_request(const ProbeRequest& r) {
     return GACE_OK;
 }
 
+// Distinct 64-bit keys in insertion order with an open-addressing index
+// (linear probing on a splitmix64 hash) from each key to a value.
+struct KeyIndex {
+    std::vector<uint64_t> key;
+    std::vector<uint32_t> val;
+    std::vector<uint8_t> used;
+    std::vector<uint64_t> distinct;
+    uint64_t mask = 0;
+    void init(uint64_t n) {
+        uint64_t cap = 16;
+        while (cap < 2 * n) cap <<= 1;
+        key.assign(cap, 0);
+        val.assign(cap, 0);
+        used.assign(cap, 0);
+        distinct.clear();
+        mask = cap - 1;
+    }
+    uint64_t slot_of(uint64_t k) const {
+        uint64_t i = splitmix64_host(k) & mask;
+        while (used[i] && key[i] != k) i = (i + 1) & mask;
+        return i;
+    }
+    void insert(uint64_t k) {
+        const uint64_t i = slot_of(k);
+        if (used[i]) return;
+        used[i] = 1;
+        key[i] = k;
+        distinct.push_back(k);
+    }
+    void set(uint64_t k, uint32_t v) { val[slot_of(k)] = v; }
+    uint32_t find(uint64_t k) const { return val[slot_of(k)]; }  // k was inserted
+};
+
 // The search tree of a rank-coded column's endpoints (RankArgs): the
 // perfect tree whose in-order is the sorted keys padded with the largest key,
 // in level order (node i of level L, 2^L <= i < 2^(L+1), is in-order element
@@ -1073,39 +1106,52 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
     // rank coding: every column's distinct range endpoints over the whole plan
     plan.code_of_col.assign(tab.cols.size(), -1);
     if (rank_code) {
-        // per column, the endpoints of its multi-value ranges and of all its
-        // terms: all terms are coded when their endpoints fit, else the ranges
-        std::vector<std::vector<uint64_t>> rng(tab.cols.size()), all(tab.cols.size());
-        std::vector<std::pair<uint64_t, uint64_t>> ivs;
-        for (const NTerm& t : uterms) {
-            const uint32_t dt = static_cast<uint32_t>(tab.cols[t.col].dtype);
-            const uint64_t kmax = dt == GACE_I64 ? ~0ull : 0xFFFFFFFFull;
+        // per column, the distinct endpoints of all its terms' key intervals
+        // (all terms are coded when they fit), else of its multi-value ranges
+        const size_t ncols = tab.cols.size();
+        std::vector<uint32_t> ivo(uterms.size() + 1, 0);  // term u's intervals: iv[ivo[u] .. ivo[u + 1])
+        std::vector<std::pair<uint64_t, uint64_t>> iv, ivs;
+        std::vector<uint64_t> nends(ncols, 0);
+        for (uint32_t u = 0; u < uterms.size(); ++u) {
+            const NTerm& t = uterms[u];
+            term_intervals(t, static_cast<uint32_t>(tab.cols[t.col].dtype), ivs);
+            iv.insert(iv.end(), ivs.begin(), ivs.end());
+            ivo[u + 1] = static_cast<uint32_t>(iv.size());
+            nends[t.col] += 2 * ivs.size();
+        }
+        std::vector<KeyIndex> all(ncols);
+        for (uint32_t c = 0; c < ncols; ++c)
+            if (nends[c]) all[c].init(nends[c]);
+        std::vector<std::vector<uint64_t>> rng(ncols);
+        for (uint32_t u = 0; u < uterms.size(); ++u) {
+            const NTerm& t = uterms[u];
+            const uint64_t kmax = tab.cols[t.col].dtype == GACE_I64 ? ~0ull : 0xFFFFFFFFull;
             const bool range = !is_in_kind(t.kind) && term_cost(t) == 2;
-            term_intervals(t, dt, ivs);
-            for (const auto& iv : ivs) {
-                all[t.col].push_back(iv.first);
-                if (iv.second < kmax) all[t.col].push_back(iv.second + 1);
+            for (uint32_t i = ivo[u]; i < ivo[u + 1]; ++i) {
+                all[t.col].insert(iv[i].first);
+                if (iv[i].second < kmax) all[t.col].insert(iv[i].second + 1);
                 if (range) {
-                    rng[t.col].push_back(iv.first);
-                    if (iv.second < kmax) rng[t.col].push_back(iv.second + 1);
+                    rng[t.col].push_back(iv[i].first);
+                    if (iv[i].second < kmax) rng[t.col].push_back(iv[i].second + 1);
                 }
             }
         }
-        auto distinct = [](std::vector<uint64_t>& e) {
-            std::sort(e.begin(), e.end());
-            e.erase(std::unique(e.begin(), e.end()), e.end());
-        };
-        for (uint32_t c = 0; c < tab.cols.size(); ++c) {
-            distinct(all[c]);
+        for (uint32_t c = 0; c < ncols; ++c) {
             RankCode rc;
-            if (!all[c].empty() && all[c].size() <= kRankPlanMax) {
-                rc.keys = std::move(all[c]);
+            if (!all[c].distinct.empty() && all[c].distinct.size() <= kRankPlanMax) {
+                rc.keys = all[c].distinct;
                 rc.all_terms = true;
             } else {
-                distinct(rng[c]);
-                if (rng[c].empty() || rng[c].size() > kRankPlanMax) continue;
-                rc.keys = std::move(rng[c]);
+                std::vector<uint64_t>& e = rng[c];
+                std::sort(e.begin(), e.end());
+                e.erase(std::unique(e.begin(), e.end()), e.end());
+                if (e.empty() || e.size() > kRankPlanMax) continue;
+                rc.keys = std::move(e);
+                all[c].init(rc.keys.size());
+                for (uint64_t k : rc.keys) all[c].insert(k);
             }
+            std::sort(rc.keys.begin(), rc.keys.end());
+            for (uint32_t i = 0; i < rc.keys.size(); ++i) all[c].set(rc.keys[i], i);
             rc.col = c;
             rc.dtype = static_cast<uint32_t>(tab.cols[c].dtype);
             build_rank_tree(rc);
@@ -1116,21 +1162,20 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
             plan.code_of_col[c] = static_cast<int32_t>(plan.codes.size());
             plan.codes.push_back(std::move(rc));
         }
-        // each coded term's intervals as column endpoint indices
+        // each coded term's intervals as column endpoint indices: an
+        // interval [lo, hi] holds the endpoints from lo's index up to that of
+        // hi + 1 (or to the last, when hi is the largest key)
         plan.span_off.assign(1, 0);
-        for (const NTerm& t : uterms) {
+        for (uint32_t u = 0; u < uterms.size(); ++u) {
+            const NTerm& t = uterms[u];
             const int32_t code = plan.code_of_col[t.col];
             const bool range = !is_in_kind(t.kind) && term_cost(t) == 2;
             if (code >= 0 && (range || plan.codes[code].all_terms)) {
-                const std::vector<uint64_t>& keys = plan.codes[code].keys;
-                term_intervals(t, static_cast<uint32_t>(tab.cols[t.col].dtype), ivs);
-                for (const auto& iv : ivs) {
-                    const uint32_t r0 =
-                        static_cast<uint32_t>(std::lower_bound(keys.begin(), keys.end(), iv.first) - keys.begin());
-                    const uint32_t r1 =
-                        static_cast<uint32_t>(std::upper_bound(keys.begin(), keys.end(), iv.second) - keys.begin());
-                    plan.span.push_back({r0, r1});
-                }
+                const uint64_t kmax = tab.cols[t.col].dtype == GACE_I64 ? ~0ull : 0xFFFFFFFFull;
+                const uint32_t m = static_cast<uint32_t>(plan.codes[code].keys.size());
+                const KeyIndex& ki = all[t.col];
+                for (uint32_t i = ivo[u]; i < ivo[u + 1]; ++i)
+                    plan.span.push_back({ki.find(iv[i].first), iv[i].second < kmax ? ki.find(iv[i].second + 1) : m});
             }
             plan.span_off.push_back(static_cast<uint32_t>(plan.span.size()));
         }
