@@ -75,7 +75,12 @@ typedef struct {
                                   many as are resident at once); raised where a
                                   CTA would otherwise count 2^31 rows or more
                                   in its 32-bit counters */
-    uint32_t reserved;         /* 0 */
+    uint32_t rank_min_rows;    /* a gace_probe_batch call over a table of fewer
+                                  rows does not rank-code its columns
+                                  (0 selects 1048576; the call must also have
+                                  more than 32 predicates and at least 384
+                                  distinct terms).  Rank coding changes no
+                                  result, only the kernels that compute it */
 } gace_config;
 
 /* One column of a table: nrows elements of dtype, densely packed. */

@@ -95,8 +95,9 @@ def gace_abi_version() -> int:
 
 
 def gace_create(device: int = 0, stream=None, hbm_budget_bytes: int = 0,
-                wait_timeout_ms: int = 0, max_ctas: int = 0) -> int:
-    cfg = _capi.gace_config(device, wait_timeout_ms, hbm_budget_bytes, _stream_handle(stream), max_ctas, 0)
+                wait_timeout_ms: int = 0, max_ctas: int = 0, rank_min_rows: int = 0) -> int:
+    cfg = _capi.gace_config(device, wait_timeout_ms, hbm_budget_bytes, _stream_handle(stream), max_ctas,
+                            rank_min_rows)
     out = C.c_void_p()
     check(lib().gace_create(C.byref(out), C.byref(cfg)), "gace_create")
     return out.value

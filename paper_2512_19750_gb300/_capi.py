@@ -28,7 +28,7 @@ class gace_scalar(C.Union):
 class gace_config(C.Structure):
     _fields_ = [("device", C.c_int32), ("wait_timeout_ms", C.c_uint32),
                 ("hbm_budget_bytes", C.c_uint64), ("stream", C.c_void_p), ("max_ctas", C.c_uint32),
-                ("reserved", C.c_uint32)]
+                ("rank_min_rows", C.c_uint32)]
 
 
 class gace_column(C.Structure):

@@ -722,8 +722,8 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
     // 32 KB through a bulk-copy pipeline two or three stages deep (at most
     // 64 KB per CTA, so that three or four CTAs fit on an SM); wide passes are
     // ALU-bound and load directly.
-    uint32_t rowbytes = 0;
-    for (uint32_t s = 0; s < nslots; ++s) rowbytes += A.slots[s].width;
+    uint32_t rowbytes = 0;  // a rank-coded slot reads the rows' 16-bit ranks
+    for (uint32_t s = 0; s < nslots; ++s) rowbytes += A.slots[s].rstride ? 2u : A.slots[s].width;
     ps.rowbytes = rowbytes;
     A.narrow = narrow ? 1u : 0u;
     const uint32_t sweep = (A.narrow ? 2u : 1u) * kSliceRows * kProbeWarps;  // rows of one CTA sweep
@@ -1105,6 +1105,11 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
 
     // rank coding: every column's distinct range endpoints over the whole plan
     plan.code_of_col.assign(tab.cols.size(), -1);
+    // ranks pay for their pre-pass when several wide passes read them: a
+    // batch of more predicates than a narrow pass holds, with more terms than
+    // one wide pass holds, over a table of at least kRankMinRows rows
+    rank_code = rank_code && npreds > static_cast<uint32_t>(kNarrowMax) && uterms.size() >= kRankMinTerms &&
+                tab.nrows >= (ctx->rank_min_rows ? ctx->rank_min_rows : kRankMinRows);
     if (rank_code) {
         // per column, the distinct endpoints of all its terms' key intervals
         // (all terms are coded when they fit), else of its multi-value ranges
@@ -1181,7 +1186,7 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
         }
         // a batch's single-term predicates on such columns are counted from
         // the rank histograms (their count is their term's marginal)
-        if (npreds > static_cast<uint32_t>(kNarrowMax)) {
+        {
             for (uint32_t p = 0; p < npreds; ++p) {
                 if (plan.pstate[p] != 0 || plan.pred_u[p].size() != 1) continue;
                 const uint32_t u = plan.pred_u[p][0];
@@ -1712,6 +1717,7 @@ gace_status gace_create(gace_ctx** out, const gace_config* cfg) {
     ctx->device = c.device;
     ctx->budget = c.hbm_budget_bytes;
     ctx->max_ctas = c.max_ctas;
+    ctx->rank_min_rows = c.rank_min_rows;
     if (c.wait_timeout_ms) ctx->timeout_ns = static_cast<uint64_t>(c.wait_timeout_ms) * 1000000ull;
     auto bail = [&](gace_status s) {
         gace_destroy(ctx);

@@ -136,6 +136,7 @@ struct gace_ctx {
     uint64_t used = 0;         // owned tables + workspace + pinned
     uint64_t timeout_ns = 2000ull * 1000000ull;
     uint32_t max_ctas = 0;     // cap on the CTAs of a probe launch (0 = none)
+    uint64_t rank_min_rows = 0;  // smallest table a batch probe rank-codes (0: kRankMinRows)
     std::mutex mu;
     std::unordered_map<uint32_t, TableRec> tables;
     uint32_t next_id = 1;
@@ -473,6 +474,15 @@ struct RankCode {
 #define GACE_RANK_PLAN_MAX 2047
 #endif
 constexpr uint32_t kRankPlanMax = GACE_RANK_PLAN_MAX;
+// A synchronous probe rank-codes its columns when it has more than
+// kNarrowMax predicates, at least kRankMinTerms distinct terms (more than one
+// wide pass holds) and at least kRankMinRows rows (the context's
+// rank_min_rows when set).
+#ifndef GACE_RANK_MIN_TERMS
+#define GACE_RANK_MIN_TERMS 384
+#endif
+constexpr size_t kRankMinTerms = GACE_RANK_MIN_TERMS;
+constexpr uint64_t kRankMinRows = 1ull << 20;
 // Most shared memory of a rank pass that also counts its row sets' ranks.
 constexpr uint64_t kRankHistSmem = 96u << 10;
 

@@ -21,15 +21,24 @@ pytestmark = pytest.mark.gpu
 SAMPLES = [Sample(FULL), Sample(ROWS, 0.2, 13), Sample(BLOCKS, 0.3, 4, 256)]
 
 
-def _run(g, gctx, orc, cols, dtypes, preds, samples=SAMPLES):
-    tid = g.gace_load_columns(gctx, cols)
+@pytest.fixture(scope="module")
+def rctx(g):
+    """A context that rank-codes batches over tables of any size (the
+    default threshold, 2^20 rows, would leave these small tables uncoded)."""
+    ctx = g.gace_create(0, rank_min_rows=1)
+    yield ctx
+    g.gace_destroy(ctx)
+
+
+def _run(g, ctx, orc, cols, dtypes, preds, samples=SAMPLES):
+    tid = g.gace_load_columns(ctx, cols)
     try:
-        check_probe(g, orc, gctx, tid, cols, dtypes, preds, samples)
+        check_probe(g, orc, ctx, tid, cols, dtypes, preds, samples)
     finally:
-        g.gace_unload(gctx, tid)
+        g.gace_unload(ctx, tid)
 
 
-def test_ranges_coded_values_hashed(g, gctx, orc):
+def test_ranges_coded_values_hashed(g, rctx, orc):
     """Column 0 has 1100 distinct EQ values (2200 endpoints, past the bound)
     and 60 ranges: its ranges are rank-coded, its EQ and IN terms hashed in a
     second slot; column 1 (int64) is coded with all its terms."""
@@ -51,10 +60,10 @@ def test_ranges_coded_values_hashed(g, gctx, orc):
         preds.append([Term(0, RANGE, a, b + 1), Term(0, EQ, int(rng.integers(0, 4400)) // 4 * 4),
                       Term(1, EQ, int(rng.integers(-300, 300)) * (2**35 + 7))])
     preds.append([Term(0, IN, values=(0, 4, 8, 5001, -3))])
-    _run(g, gctx, orc, [c0, c1], [I32, I64], preds)
+    _run(g, rctx, orc, [c0, c1], [I32, I64], preds)
 
 
-def test_uncoded_column_trees_and_compares(g, gctx, orc):
+def test_uncoded_column_trees_and_compares(g, rctx, orc):
     """Column 0 (float32) has 1100 ranges with distinct endpoints (2200, past
     the bound) and some EQ terms: it keeps interval trees, compares and hash
     tables, so its passes take the general wide kernel; column 1 is coded."""
@@ -78,10 +87,10 @@ def test_uncoded_column_trees_and_compares(g, gctx, orc):
     for k in range(20):
         a, b = sorted(float(x) for x in rng.standard_normal(2) * 40)
         preds.append([Term(0, RANGE, a, b), Term(1, RANGE, -500 + k, 800)])
-    _run(g, gctx, orc, [c0, c1], [F32, I32], preds)
+    _run(g, rctx, orc, [c0, c1], [F32, I32], preds)
 
 
-def test_wide_local_rank_maps(g, gctx, orc):
+def test_wide_local_rank_maps(g, rctx, orc):
     """800 IN terms on one int32 column over 2046 consecutive values (2047
     endpoints, the bound), each in a two-term predicate so that it is
     evaluated in a pass: more terms than one pass holds, so each pass maps
@@ -101,10 +110,10 @@ def test_wide_local_rank_maps(g, gctx, orc):
     preds += [[Term(0, IN, values=(0, 2045))], [Term(0, EQ, 1022)], [Term(0, EQ, 1023)]]
     for k in range(40):
         preds.append([Term(0, IN, values=(k, 2045 - k)), Term(1, RANGE, k, k + 30)])
-    _run(g, gctx, orc, [c0, c1], [I32, I32], preds, [Sample(FULL), Sample(ROWS, 0.25, 3)])
+    _run(g, rctx, orc, [c0, c1], [I32, I32], preds, [Sample(FULL), Sample(ROWS, 0.25, 3)])
 
 
-def test_all_terms_coded_every_dtype(g, gctx, orc):
+def test_all_terms_coded_every_dtype(g, rctx, orc):
     """Columns of each type coded with all their terms: ranges that touch and
     nest, EQ at both ends of the domain, IN lists sharing values with ranges
     and with each other, float -0/+0 and NaN rows, conjunctions across
@@ -134,4 +143,21 @@ def test_all_terms_coded_every_dtype(g, gctx, orc):
     for k in range(40):
         preds.append([Term(0, RANGE, -k, k + 1), Term(1, IN, values=(k * (2**40 + 1), 0)),
                       Term(2, IN, values=(0.5, -1.5))])
-    _run(g, gctx, orc, [i32, i64, f32], [I32, I64, F32], preds)
+    _run(g, rctx, orc, [i32, i64, f32], [I32, I64, F32], preds)
+
+
+def test_ranks_per_chunk_of_a_streamed_table(g, rctx, orc):
+    """A host table registered with its copy deferred to its first probe
+    streams in chunks of 2^20 rows (the last ragged): each chunk gets its own
+    row-set masks, ranks and histogram counts before its passes."""
+    from parity import host_columns
+    from workloads import make_predicates, make_skew_corr
+
+    t = make_skew_corr(n=1_200_007, seed=91, device="cpu", domain=50_000)
+    host = host_columns(t)
+    preds = make_predicates(t, 400, 1, 3, seed=92, in_len=4)
+    tid = g.gace_load_columns(rctx, [c.numpy() for c in t.columns], copy_on_first_probe=True)
+    try:
+        check_probe(g, orc, rctx, tid, host, t.dtypes, preds, [Sample(FULL), Sample(ROWS, 0.05, 8)])
+    finally:
+        g.gace_unload(rctx, tid)
