@@ -55,14 +55,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_probe_narrow(const __grid_const
     flush(A, S, tid);
 }
 
-template <bool HASH>
+template <bool HASH, int NQ = 2>
 __global__ void __launch_bounds__(kThreads, 4) k_probe_single(const __grid_constant__ ProbeArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const Smem S = carve(A, smem, warp);
     load_tables(A, S, tid);
     __syncthreads();
-    if (!single_run<HASH>(A, S, tid, lane, warp, blockIdx.x, A.ntiles, gridDim.x)) return;
+    if (!single_run<HASH, NQ>(A, S, tid, lane, warp, blockIdx.x, A.ntiles, gridDim.x)) return;
     __syncthreads();
     flush(A, S, tid);
 }
@@ -224,10 +224,18 @@ static cudaError_t set_smem(K kernel, int optin) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
 }
 
-// probe_variant's cases, and 6: a wide pass whose range terms are all rank-coded
+// probe_variant's cases; 6: a wide pass whose range terms are all
+// rank-coded; 7: one predicate on all rows of columns of at most 8 bytes per
+// row, 16 rows per lane
 static int variant(const ProbeArgs& a) {
     const int v = probe_variant(a);
-    return v == 0 && a.ranks_only ? 6 : v;
+    if (v == 0 && a.ranks_only) return 6;
+    if (v == 4) {
+        uint32_t rowbytes = 0;
+        for (uint32_t s = 0; s < a.nslots; ++s) rowbytes += a.slots[s].width;
+        if (rowbytes <= 8) return 7;
+    }
+    return v;
 }
 
 cudaError_t probe_configure() {
@@ -240,6 +248,7 @@ cudaError_t probe_configure() {
     if ((e = set_smem(k_probe_narrow<true, 1>, optin))) return e;
     if ((e = set_smem(k_probe_narrow<true, kMaxSets>, optin))) return e;
     if ((e = set_smem(k_probe_single<false>, optin))) return e;
+    if ((e = set_smem(k_probe_single<false, 4>, optin))) return e;
     if ((e = set_smem(k_probe_single<true>, optin))) return e;
     if ((e = set_smem(k_probe_wide<true>, optin))) return e;
     return set_smem(k_probe_wide<false>, optin);
@@ -255,6 +264,7 @@ int probe_occupancy(const ProbeArgs& a) {
         case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_narrow<true, 1>, kThreads, a.smem_bytes); break;
         case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_narrow<true, kMaxSets>, kThreads, a.smem_bytes); break;
         case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_single<false>, kThreads, a.smem_bytes); break;
+        case 7: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_single<false, 4>, kThreads, a.smem_bytes); break;
         default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_single<true>, kThreads, a.smem_bytes); break;
     }
     return e == cudaSuccess ? n : 0;
@@ -302,6 +312,7 @@ cudaError_t probe_launch(const ProbeArgs& a, int grid, cudaStream_t s) {
         case 2: k_probe_narrow<true, 1><<<grid, kThreads, a.smem_bytes, s>>>(a); break;
         case 3: k_probe_narrow<true, kMaxSets><<<grid, kThreads, a.smem_bytes, s>>>(a); break;
         case 4: k_probe_single<false><<<grid, kThreads, a.smem_bytes, s>>>(a); break;
+        case 7: k_probe_single<false, 4><<<grid, kThreads, a.smem_bytes, s>>>(a); break;
         default: k_probe_single<true><<<grid, kThreads, a.smem_bytes, s>>>(a); break;
     }
     return cudaGetLastError();

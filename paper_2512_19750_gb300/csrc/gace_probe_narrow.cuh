@@ -259,12 +259,15 @@ __device__ __forceinline__ void single_slot(const SlotDesc& sd, const Vals<NQ>& 
 }
 
 // One predicate on one row set (the gate's single probe): every lane ANDs the
-// terms of its eight rows in predicate registers and counts the rows that pass;
-// no per-term masks go through shared memory.  HASH: the set is a hashed sample.
-template <bool HASH>
+// terms of its 4 NQ rows in predicate registers and counts the rows that
+// pass; no per-term masks go through shared memory.  HASH: the set is a hashed
+// sample.  NQ: 2, or 4 for passes of narrow rows (half the per-slice work per
+// row; the hashed form keeps 2 to stay within the registers of four CTAs per
+// SM).
+template <bool HASH, int NQ = 2>
 __device__ __forceinline__ bool single_run(const ProbeArgs& A, const Smem& S, int tid, int lane, int warp,
                                            uint64_t first, uint64_t end, uint64_t stride) {
-    constexpr int NQ = 2, R = 4 * NQ;
+    constexpr int R = 4 * NQ;
     constexpr uint32_t kSlice = 128 * NQ;
     constexpr uint32_t kAll = (1u << R) - 1u;
     uint32_t cnt = 0, nsr = 0, tc = 0;

@@ -35,12 +35,45 @@ __device__ __forceinline__ uint64_t canonical_key(uint32_t dtype, uint32_t lo, u
 // r = those bits, 2 r + 1 has 63 - (64 - p) + (leading zeros of r) + 1
 // leading zeros, and 1 (63) when r = 0, which gives rho = 65 - p there: no
 // variable-width 64-bit shift per row (the mask is loop-invariant).
+#ifndef GACE_HLL_HASH32
+#define GACE_HLL_HASH32 0
+#endif
+#if GACE_HLL_HASH32
+// x ^= x >> s (0 < s < 32) and x *= c on a 64-bit value held as two words.
+__device__ __forceinline__ void xs_words(uint32_t& lo, uint32_t& hi, int s) {
+    lo ^= __funnelshift_r(lo, hi, s);
+    hi ^= hi >> s;
+}
+__device__ __forceinline__ void mul_words(uint32_t& lo, uint32_t& hi, uint64_t c) {
+    const uint32_t cl = static_cast<uint32_t>(c), ch = static_cast<uint32_t>(c >> 32);
+    const uint32_t nh = __umulhi(lo, cl) + lo * ch + hi * cl;
+    lo *= cl;
+    hi = nh;
+}
+#endif
+
 __device__ __forceinline__ void hll_rank(uint64_t key, uint64_t seedhash, uint32_t p,
                                          uint32_t& j, uint32_t& rho) {
+#if GACE_HLL_HASH32
+    // splitmix64 of key ^ seedhash, word by word
+    uint64_t x = (key ^ seedhash) + 0x9E3779B97F4A7C15ull;
+    uint32_t lo = static_cast<uint32_t>(x), hi = static_cast<uint32_t>(x >> 32);
+    xs_words(lo, hi, 30);
+    mul_words(lo, hi, 0xBF58476D1CE4E5B9ull);
+    xs_words(lo, hi, 27);
+    mul_words(lo, hi, 0x94D049BB133111EBull);
+    xs_words(lo, hi, 31);
+    j = hi >> (32 - p);
+    // 2 r + 1 with r the low 64 - p bits: its leading zeros over both words
+    const uint32_t rh = ((hi & ((1u << (32 - p)) - 1u)) << 1) | (lo >> 31);
+    const uint32_t rl = (lo << 1) | 1u;
+    rho = (rh ? static_cast<uint32_t>(__clz(rh)) : 32u + static_cast<uint32_t>(__clz(rl))) + 2u - p;
+#else
     const uint64_t h = splitmix64(key ^ seedhash);
     j = static_cast<uint32_t>(h >> 32) >> (32 - p);
     const uint64_t r = h & ((1ull << (64 - p)) - 1);
     rho = static_cast<uint32_t>(__clzll(static_cast<long long>(2 * r + 1))) + 2u - p;
+#endif
 }
 
 // byte-wise max in shared memory via CAS on the containing word (bounded)
