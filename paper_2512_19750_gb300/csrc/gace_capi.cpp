@@ -700,6 +700,11 @@ gace_status build_pass(gace_ctx* ctx, const TableRec& tab, Pass& ps, const std::
             }
         }
     }
+    // a wide pass's lanes take every 32nd predicate: ordered by term count,
+    // the lanes of one step AND as many masks each
+    if (!narrow)
+        std::stable_sort(ps.preds.begin(), ps.preds.end(),
+                         [&](uint32_t x, uint32_t y) { return pred_u[x].size() > pred_u[y].size(); });
     ps.poff.assign(1, 0);
     ps.pterm.clear();
     for (uint32_t p : ps.preds) {
