@@ -755,7 +755,10 @@ def batched_leg(g, ctx, dev, args):
     nbytes = sum(request_bytes(tables, reqs))
     shared = shared_scan_bytes(tables, reqs)
     n = len(reqs)
+    g.gace_stats_reset(ctx)
     g.gace_tune_batch(ctx, to_gace_requests(g, tids, tables, reqs))
+    tuned = g.gace_stats_read(ctx)
+    fuse_ms = {k: round(v["total_ms"], 3) for k, v in tuned.items() if k.startswith("tune_batch_fuse")}
     breqs = g.RequestArray(to_gace_requests(g, tids, tables, reqs))  # marshalled once, run five times
     for _ in range(2):
         g.gace_run_batch(ctx, breqs)
@@ -768,6 +771,8 @@ def batched_leg(g, ctx, dev, args):
         walls.append(time.perf_counter() - t0)
     st = g.gace_stats_read(ctx)
     batch_ms = st["batch"]["total_ms"] / max(1, st["batch"]["launches"])
+    host_ms = {k[len("host_batch_"):]: round(v["total_ms"] / max(1, v["launches"]), 3)
+               for k, v in st.items() if k.startswith("host_batch_")}
     wall = float(np.median(walls))
     zero = np.zeros(n, dtype=np.uint64)
     plain_done, plain_st = g.gace_serve_replay(ctx, to_gace_requests(g, tids, tables, reqs), zero, mode=1)
@@ -817,6 +822,8 @@ def batched_leg(g, ctx, dev, args):
                     "10% joins)",
         "requests": n, "table_rows": rows, "request_bytes": nbytes,
         "batched_probes_per_s": n / wall, "batched_ms": wall * 1000.0, "batch_graph_ms": batch_ms,
+        "batch_host_phases_ms": host_ms,
+        "tuned_graph_ms_by_fusion_rule": fuse_ms,
         "plain_probes_per_s": n / plain_wall, "plain_ms": plain_wall * 1000.0,
         "plain_device_only_probes_per_s": n / plain_dev_s, "plain_device_only_ms": plain_dev_s * 1000.0,
         "served_at_once_probes_per_s": n / served_wall, "served_at_once_ms": served_wall * 1000.0,

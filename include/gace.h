@@ -419,7 +419,12 @@ typedef struct {
  * work queue.  The upload of the compiled batch, the clearing of its
  * counters, the phase launches and the read-back form one CUDA graph that is
  * replayed while batches keep the same shape.  Chunk size and grid come from
- * the context's tuning table (gace_tune_batch), else defaults.  Results are
+ * the context's tuning table (gace_tune_batch), else defaults, and so does the
+ * rule by which probes on one table are fused.  A batch of 64 or more
+ * requests is planned, and its results assembled, on a few host threads of
+ * the context.  With kernel timing on (gace_stats_reset), the host phases
+ * (host_batch_resident, _compile, _build, _run, _finish) are added to the
+ * statistics, launches = calls and total_ms = wall time.  Results are
  * identical to the synchronous calls'.  statuses (out, n entries, may be NULL)
  * receives each request's status; the return value is GACE_OK when every
  * request succeeded, else the first failing request's status.
@@ -427,10 +432,17 @@ typedef struct {
 gace_status gace_run_batch(gace_ctx* ctx, const gace_request* reqs, uint32_t n, gace_status* statuses);
 
 /*
- * Autotuner: runs the batch with each candidate chunk size (128K..8M rows)
- * and grid (1, 2 or the maximum of CTAs per SM), times every candidate with
- * CUDA events, and records the fastest for batches of this shape (jobs and
- * rows, each bucketed by powers of two) in the context's tuning table.
+ * Autotuner: runs the batch under each of three fusion rules (probes on one
+ * table fused only when they share their row sets and columns and are not
+ * single predicates on one row set; single predicates fused too; groups that
+ * take the union of their members' row sets and columns), each with every
+ * candidate chunk size (128K..8M rows) and grid (1, 2 or the maximum of CTAs
+ * per SM), times every candidate with CUDA events, and records the fastest:
+ * the fusion rule for batches of this request shape (requests and the rows of
+ * the tables they read, each bucketed by powers of two), chunk and grid for
+ * batches of the compiled shape (jobs and rows).  Results are the same
+ * integers under every rule.  Each rule's best device time is added to the
+ * kernel statistics as tune_batch_fuse0..2.
  */
 gace_status gace_tune_batch(gace_ctx* ctx, const gace_request* reqs, uint32_t n);
 

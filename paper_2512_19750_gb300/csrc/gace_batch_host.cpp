@@ -38,6 +38,62 @@
 
 namespace gace {
 namespace host {
+
+HostPool::~HostPool() {
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        stop_ = true;
+    }
+    wake_.notify_all();
+    for (std::thread& t : threads_) t.join();
+}
+
+void HostPool::work() {
+    uint64_t seen = 0;
+    for (;;) {
+        const std::function<void(uint32_t)>* fn;
+        uint32_t n;
+        {
+            std::unique_lock<std::mutex> lk(mu_);
+            wake_.wait(lk, [&] { return stop_ || gen_ != seen; });
+            if (stop_) return;
+            seen = gen_;
+            fn = fn_;
+            n = n_;
+        }
+        for (uint32_t i = next_.fetch_add(1); i < n; i = next_.fetch_add(1)) (*fn)(i);
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            if (--busy_ == 0) done_.notify_all();
+        }
+    }
+}
+
+void HostPool::run(uint32_t n, const std::function<void(uint32_t)>& fn) {
+    if (threads_.empty()) {
+        const unsigned hw = std::thread::hardware_concurrency();
+        const unsigned nt = hw > 1 ? std::min(hw - 1, 7u) : 0u;
+        for (unsigned t = 0; t < nt; ++t) threads_.emplace_back([this] { work(); });
+    }
+    if (threads_.empty() || n < 2) {
+        for (uint32_t i = 0; i < n; ++i) fn(i);
+        return;
+    }
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        fn_ = &fn;
+        n_ = n;
+        next_.store(0);
+        busy_ = static_cast<uint32_t>(threads_.size());
+        ++gen_;
+    }
+    wake_.notify_all();
+    for (uint32_t i = next_.fetch_add(1); i < n; i = next_.fetch_add(1)) fn(i);
+    std::unique_lock<std::mutex> lk(mu_);
+    done_.wait(lk, [&] { return busy_ == 0; });
+    fn_ = nullptr;
+}
+
 namespace {
 
 
@@ -54,12 +110,13 @@ int log2_bucket(uint64_t x) {
 
 }  // namespace
 
-bool fusable_probe(const gace_request& r) {
+bool fusable_probe(const gace_request& r, int mode) {
     if (r.kind != GACE_REQ_PROBE || !r.samples || r.nsamples == 0 || r.nsamples > kMaxSets) return false;
     // one predicate on one row set runs the register-only single-predicate
     // evaluation, cheaper per row than the narrow evaluation a fused group
-    // needs: fusing it would trade its bytes for more instructions per row
-    if (r.npreds <= 1 && r.nsamples <= 1) return false;
+    // needs: fusing it trades its bytes for more instructions per row, which
+    // pays only where many such requests read one table (modes 1 and 2)
+    if (mode == 0 && r.npreds <= 1 && r.nsamples <= 1) return false;
     if (r.npreds > static_cast<uint32_t>(kNarrowMax) || r.nterms > static_cast<uint32_t>(kNarrowMax)) return false;
     if (r.nin > FusedProbe::kMaxIn) return false;
     if (r.npreds && (!r.preds || !r.results)) return false;
@@ -107,7 +164,7 @@ bool FusedProbe::fits(const gace_request& r, const TableRec& t) const {
     if (!GACE_FUSE) return false;
     const uint64_t m = probe_colmask(r);
     if (m == ~0ull || mask_rowbytes(colmask | m, t) > kMaxRowBytes) return false;
-    if (!members.empty()) {
+    if (!members.empty() && mode < 2) {
         if ((m | colmask) != colmask) return false;  // a new column: no saving on it
         if (r.nsamples != members[0].q->nsamples) return false;
         for (uint32_t k = 0; k < r.nsamples; ++k)
@@ -726,7 +783,11 @@ namespace {
 // Outputs of every request from the read-back counters.
 void finish_batch(gace_ctx* ctx, std::vector<ReqPlan>& rps, const BatchRun& br) {
     const unsigned int bst = *reinterpret_cast<const unsigned int*>(ctx->pin + br.small_base);
-    for (ReqPlan& rp : rps) finish_request(ctx, rp, ctx->pin, bst);
+    const uint32_t n = static_cast<uint32_t>(rps.size());
+    if (n >= kParallelRequests)  // each request's outputs are its own
+        ctx->workers.run(n, [&](uint32_t i) { finish_request(ctx, rps[i], ctx->pin, bst); });
+    else
+        for (ReqPlan& rp : rps) finish_request(ctx, rp, ctx->pin, bst);
 }
 
 // Plans of a batch: probes on one table are fused greedily in request order
@@ -734,14 +795,14 @@ void finish_batch(gace_ctx* ctx, std::vector<ReqPlan>& rps, const BatchRun& br) 
 // request that does not compile is undone and its members compiled alone,
 // so each reports its own error.
 gace_status compile_all(gace_ctx* ctx, const gace_request* reqs, uint32_t n, std::vector<ReqPlan>& rps,
-                        std::vector<std::unique_ptr<FusedProbe>>& fused) {
+                        std::vector<std::unique_ptr<FusedProbe>>& fused, int mode) {
     rps.assign(n, ReqPlan());
     fused.clear();
     std::vector<bool> alone(n, true);
     // candidates by table, the requests reading the most columns first (they seed the groups)
     std::vector<std::pair<uint32_t, const TableRec*>> cand;
     for (uint32_t i = 0; i < n; ++i) {
-        if (!fusable_probe(reqs[i])) continue;
+        if (!fusable_probe(reqs[i], mode)) continue;
         const TableRec* tab = find_table(ctx, reqs[i].table_id);
         if (tab) cand.emplace_back(i, tab);  // else compiled alone, which reports it
     }
@@ -755,10 +816,14 @@ gace_status compile_all(gace_ctx* ctx, const gace_request* reqs, uint32_t n, std
         if (c > 0 && reqs[cand[c - 1].first].table_id != reqs[i].table_id) table_begin = fused.size();
         size_t gi = table_begin;
         while (gi < fused.size() && !fused[gi]->fits(reqs[i], *cand[c].second)) ++gi;
-        if (gi == fused.size()) fused.push_back(std::make_unique<FusedProbe>());
+        if (gi == fused.size()) {
+            fused.push_back(std::make_unique<FusedProbe>());
+            fused.back()->mode = mode;
+        }
         fused[gi]->add(i, reqs[i], *cand[c].second);
         alone[i] = false;
     }
+    std::vector<uint32_t> groups;  // fused groups of two or more members
     for (size_t f = 0; f < fused.size(); ++f) {
         FusedProbe& fp = *fused[f];
         if (fp.members.size() == 1) {  // nothing shared: the request runs as itself
@@ -766,10 +831,56 @@ gace_status compile_all(gace_ctx* ctx, const gace_request* reqs, uint32_t n, std
             continue;
         }
         fp.seal();
-        ReqPlan rp;
-        rp.status = compile_request(ctx, fp.q, rp);
-        if (rp.status != GACE_OK) {
-            for (const FusedProbe::Member& m : fp.members) alone[m.index] = true;
+        groups.push_back(static_cast<uint32_t>(f));
+    }
+    std::vector<uint32_t> lone;
+    for (uint32_t i = 0; i < n; ++i)
+        if (alone[i]) lone.push_back(i);
+    // plans of the groups and of the lone requests: each writes only its own
+    // ReqPlan, so a large batch plans them on the host workers
+    std::vector<ReqPlan> gplans(groups.size());
+    auto plan_one = [&](uint32_t k) {
+        if (k < groups.size()) {
+            gplans[k].status = compile_request(ctx, fused[groups[k]]->q, gplans[k]);
+            return;
+        }
+        const uint32_t i = lone[k - groups.size()];
+        rps[i].status = compile_request(ctx, reqs[i], rps[i]);
+        if (rps[i].status != GACE_OK) rps[i].error = gace_last_error();
+    };
+    const uint32_t ntasks = static_cast<uint32_t>(groups.size() + lone.size());
+    bool parallel = ntasks >= kParallelRequests;
+    if (parallel) {
+        // a table copied at its first use completes its copy here, once, on
+        // this thread; the workers then only read the table records
+        auto ready = [&](uint32_t id) {
+            const TableRec* t = find_table(ctx, id);
+            return !t || t->pending.empty();
+        };
+        for (uint32_t i = 0; i < n && parallel; ++i) {
+            const gace_request& q = reqs[i];
+            if (q.kind != GACE_REQ_JOIN) {
+                parallel = ready(q.table_id);
+            } else if (q.join) {
+                parallel = ready(q.join->fact.table_id) && ready(q.join->dim.table_id) &&
+                           (q.join->hops != 2 || ready(q.join->dim2.table_id));
+            }
+        }
+    }
+    if (parallel) {
+        const int device = ctx->device;
+        ctx->workers.run(ntasks, [&](uint32_t k) {
+            cudaSetDevice(device);
+            plan_one(k);
+        });
+    } else {
+        for (uint32_t k = 0; k < ntasks; ++k) plan_one(k);
+    }
+    std::vector<uint32_t> undone;  // members of groups that did not compile
+    for (size_t k = 0; k < groups.size(); ++k) {
+        const FusedProbe& fp = *fused[groups[k]];
+        if (gplans[k].status != GACE_OK) {
+            for (const FusedProbe::Member& m : fp.members) undone.push_back(m.index);
             continue;
         }
         for (const FusedProbe::Member& m : fp.members) {
@@ -777,10 +888,10 @@ gace_status compile_all(gace_ctx* ctx, const gace_request* reqs, uint32_t n, std
             rps[m.index].q = &reqs[m.index];
             rps[m.index].fused = static_cast<int>(rps.size());
         }
-        rps.push_back(std::move(rp));
+        rps.push_back(std::move(gplans[k]));
     }
-    for (uint32_t i = 0; i < n; ++i) {
-        if (!alone[i]) continue;
+    std::sort(undone.begin(), undone.end());
+    for (uint32_t i : undone) {
         rps[i].status = compile_request(ctx, reqs[i], rps[i]);
         if (rps[i].status != GACE_OK) rps[i].error = gace_last_error();
     }
@@ -800,6 +911,26 @@ void finish_fused(std::vector<ReqPlan>& rps, const std::vector<std::unique_ptr<F
         if (f->members.size() > 1 && rps[f->members[0].index].fused >= 0 &&
             rps[rps[f->members[0].index].fused].status == GACE_OK)
             f->scatter();
+}
+
+// Shape of a batch before it is planned: (log2 requests, log2 rows of the
+// tables its requests read), the key of its fusion rules.
+std::pair<int, int> request_key(gace_ctx* ctx, const gace_request* reqs, uint32_t n) {
+    uint64_t rows = 0;
+    auto add = [&](uint32_t id) {
+        if (const TableRec* t = find_table_raw(ctx, id)) rows += t->nrows;
+    };
+    for (uint32_t i = 0; i < n; ++i) {
+        const gace_request& q = reqs[i];
+        if (q.kind != GACE_REQ_JOIN) {
+            add(q.table_id);
+        } else if (q.join) {
+            add(q.join->fact.table_id);
+            add(q.join->dim.table_id);
+            if (q.join->hops == 2) add(q.join->dim2.table_id);
+        }
+    }
+    return {log2_bucket(n), log2_bucket(rows)};
 }
 
 std::pair<int, int> shape_key(const std::vector<ReqPlan>& rps) {
@@ -867,13 +998,27 @@ gace_status gace_run_batch(gace_ctx* ctx, const gace_request* in, uint32_t n_in,
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
     if (gace_status s = batch_prologue(ctx, in, n_in)) return s;
+    // host phases into the statistics when kernels are timed (launches =
+    // calls, total_ms = wall time of the phase)
+    auto t_prev = std::chrono::steady_clock::now();
+    auto phase = [&](const char* name) {
+        if (!ctx->timing) return;
+        const auto t = std::chrono::steady_clock::now();
+        gace_ctx::KStat& k = ctx->stats[name];
+        k.launches++;
+        k.ms += std::chrono::duration<double, std::milli>(t - t_prev).count();
+        t_prev = t;
+    };
     ResidentBatch rb;
     rb.build(ctx, in, n_in);
+    phase("host_batch_resident");
     const gace_request* reqs = rb.reqs.data();
     const uint32_t n = static_cast<uint32_t>(rb.reqs.size());
     std::vector<ReqPlan> rps;
     std::vector<std::unique_ptr<FusedProbe>> fused;
-    compile_all(ctx, reqs, n, rps, fused);
+    const auto ft = ctx->fuse_tune.find(request_key(ctx, reqs, n));
+    compile_all(ctx, reqs, n, rps, fused, ft == ctx->fuse_tune.end() ? 0 : ft->second);
+    phase("host_batch_compile");
     uint64_t chunk = kDefaultChunk;
     int per_sm = 0;
     const auto it = ctx->tune.find(shape_key(rps));
@@ -883,10 +1028,14 @@ gace_status gace_run_batch(gace_ctx* ctx, const gace_request* in, uint32_t n_in,
     }
     BatchRun br;
     if (gace_status st = build_batch(ctx, rps, chunk, per_sm, br)) return st;
+    phase("host_batch_build");
     if (gace_status st = exec_batch(ctx, br, true)) return st;
+    phase("host_batch_run");
     finish_batch(ctx, rps, br);
     finish_fused(rps, fused, n);
-    return report_resident(ctx, rb, rps, n_in, statuses);
+    const gace_status rs = report_resident(ctx, rb, rps, n_in, statuses);
+    phase("host_batch_finish");
+    return rs;
 }
 
 gace_status gace_tune_batch(gace_ctx* ctx, const gace_request* in, uint32_t n_in) {
@@ -898,43 +1047,60 @@ gace_status gace_tune_batch(gace_ctx* ctx, const gace_request* in, uint32_t n_in
     rb.build(ctx, in, n_in);
     const gace_request* reqs = rb.reqs.data();
     const uint32_t n = static_cast<uint32_t>(rb.reqs.size());
-    std::vector<ReqPlan> rps;
-    std::vector<std::unique_ptr<FusedProbe>> fused;
-    compile_all(ctx, reqs, n, rps, fused);
-    const std::pair<int, int> key = shape_key(rps);
     cudaEvent_t a = nullptr, b = nullptr;
     CK(cudaEventCreate(&a));
     CK(cudaEventCreate(&b));
+    // every fusion rule, each over the grid of chunk sizes and CTAs per SM
     gace_ctx::TuneEntry best;
     best.ms = std::numeric_limits<double>::infinity();
+    std::pair<int, int> best_key{0, 0};
+    int best_mode = 0;
     gace_status rc = GACE_OK;
-    for (uint64_t chunk = 1ull << 17; chunk <= (1ull << 23) && rc == GACE_OK; chunk <<= 2) {
-        for (int per_sm : {1, 2, 0}) {
-            BatchRun br;
-            if ((rc = build_batch(ctx, rps, chunk, per_sm, br)) != GACE_OK) break;
-            double ms = std::numeric_limits<double>::infinity();
-            for (int rep = 0; rep < 2 && rc == GACE_OK; ++rep) {
-                cudaEventRecord(a, ctx->stream);
-                cudaError_t e = enqueue_batch(ctx, br, ctx->stream);
-                cudaEventRecord(b, ctx->stream);
-                if (e == cudaSuccess) e = cudaEventSynchronize(b);
-                float t = 0.f;
-                if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
-                if (e != cudaSuccess) rc = cuda_fail(e, "tuning run");
-                ms = std::min(ms, static_cast<double>(t));
-            }
-            if (rc == GACE_OK && ms < best.ms) {
-                best.ms = ms;
-                best.chunk = chunk;
-                best.ctas_per_sm = per_sm;
+    for (int mode = 0; mode <= 2 && rc == GACE_OK; ++mode) {
+        std::vector<ReqPlan> rps;
+        std::vector<std::unique_ptr<FusedProbe>> fused;
+        compile_all(ctx, reqs, n, rps, fused, mode);
+        double mode_ms = std::numeric_limits<double>::infinity();
+        for (uint64_t chunk = 1ull << 17; chunk <= (1ull << 23) && rc == GACE_OK; chunk <<= 2) {
+            for (int per_sm : {1, 2, 0}) {
+                BatchRun br;
+                if ((rc = build_batch(ctx, rps, chunk, per_sm, br)) != GACE_OK) break;
+                double ms = std::numeric_limits<double>::infinity();
+                for (int rep = 0; rep < 2 && rc == GACE_OK; ++rep) {
+                    cudaEventRecord(a, ctx->stream);
+                    cudaError_t e = enqueue_batch(ctx, br, ctx->stream);
+                    cudaEventRecord(b, ctx->stream);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+                    float t = 0.f;
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+                    if (e != cudaSuccess) rc = cuda_fail(e, "tuning run");
+                    ms = std::min(ms, static_cast<double>(t));
+                }
+                mode_ms = std::min(mode_ms, ms);
+                if (rc == GACE_OK && ms < best.ms) {
+                    best.ms = ms;
+                    best.chunk = chunk;
+                    best.ctas_per_sm = per_sm;
+                    best_key = shape_key(rps);
+                    best_mode = mode;
+                }
             }
         }
+        // each rule's best device time, for the caller's record
+        gace_ctx::KStat& k = ctx->stats[mode == 0 ? "tune_batch_fuse0" : mode == 1 ? "tune_batch_fuse1"
+                                                                                      : "tune_batch_fuse2"];
+        k.launches++;
+        k.ms += mode_ms;
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (rc != GACE_OK) return rc;
-    ctx->tune[key] = best;
+    ctx->tune[best_key] = best;
+    ctx->fuse_tune[request_key(ctx, reqs, n)] = best_mode;
     // leave the requests' outputs from a run with the chosen configuration
+    std::vector<ReqPlan> rps;
+    std::vector<std::unique_ptr<FusedProbe>> fused;
+    compile_all(ctx, reqs, n, rps, fused, best_mode);
     BatchRun br;
     if (gace_status st = build_batch(ctx, rps, best.chunk, best.ctas_per_sm, br)) return st;
     if (gace_status st = exec_batch(ctx, br, false)) return st;
@@ -953,6 +1119,9 @@ gace_status gace_tune_save(gace_ctx* ctx, const char* path) {
         f << "{\"jobs_log2\": " << kv.first.first << ", \"units_log2\": " << kv.first.second
           << ", \"chunk\": " << kv.second.chunk << ", \"ctas_per_sm\": " << kv.second.ctas_per_sm
           << ", \"ms\": " << kv.second.ms << "}\n";
+    for (const auto& kv : ctx->fuse_tune)
+        f << "{\"requests_log2\": " << kv.first.first << ", \"rows_log2\": " << kv.first.second
+          << ", \"fuse\": " << kv.second << "}\n";
     return f ? GACE_OK : fail(GACE_EINVAL, "cannot write %s", path);
 }
 
@@ -964,9 +1133,13 @@ gace_status gace_tune_load(gace_ctx* ctx, const char* path) {
     if (!f) return fail(GACE_ENOTFOUND, "cannot read %s", path);
     std::string line;
     while (std::getline(f, line)) {
-        int jl = 0, ul = 0, per_sm = 0;
+        int jl = 0, ul = 0, per_sm = 0, mode = 0;
         unsigned long long chunk = 0;
         double ms = 0;
+        if (sscanf(line.c_str(), " {\"requests_log2\": %d, \"rows_log2\": %d, \"fuse\": %d", &jl, &ul, &mode) == 3) {
+            if (mode >= 0 && mode <= 2) ctx->fuse_tune[{jl, ul}] = mode;
+            continue;
+        }
         if (sscanf(line.c_str(), " {\"jobs_log2\": %d, \"units_log2\": %d, \"chunk\": %llu, \"ctas_per_sm\": %d, \"ms\": %lf",
                    &jl, &ul, &chunk, &per_sm, &ms) != 5)
             continue;

@@ -7,12 +7,15 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <atomic>
+#include <condition_variable>
 #include <functional>
 #include <limits>
 #include <map>
 #include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <unordered_map>
 #include <vector>
@@ -118,6 +121,34 @@ struct ResidentStore {
     bool samples_on() const { return budget && (flags & GACE_RESIDENT_SAMPLES); }
     bool sketches_on() const { return budget && (flags & GACE_RESIDENT_SKETCHES); }
 };
+
+// ---------------------------------------------------------------- host workers
+
+// A few host threads that plan a large batch's requests and assemble their
+// results in parallel (each request's plan and outputs are its own).  Started
+// at the first parallel call, joined when the context is destroyed.
+class HostPool {
+public:
+    ~HostPool();
+    // fn(i) for every i in [0, n), on the workers and the calling thread;
+    // returns when every call has returned.  Calls of run() do not overlap
+    // (the context's mutex is held).
+    void run(uint32_t n, const std::function<void(uint32_t)>& fn);
+
+private:
+    void work();
+    std::vector<std::thread> threads_;
+    std::mutex mu_;
+    std::condition_variable wake_, done_;
+    const std::function<void(uint32_t)>* fn_ = nullptr;
+    uint32_t n_ = 0;
+    std::atomic<uint32_t> next_{0};
+    uint32_t busy_ = 0;
+    uint64_t gen_ = 0;
+    bool stop_ = false;
+};
+// Requests at which a batch plans and assembles them on the workers.
+constexpr uint32_t kParallelRequests = 64;
 
 }  // namespace host
 }  // namespace gace
@@ -237,6 +268,9 @@ struct gace_ctx {
         double ms = 0.0;
     };
     std::map<std::pair<int, int>, TuneEntry> tune;  // (log2 jobs, log2 rows) -> best
+    // fusion rules (FusedProbe::mode) per request shape: (log2 requests,
+    // log2 rows of the tables they read) -> mode
+    std::map<std::pair<int, int>, int> fuse_tune;
     cudaStream_t capture_stream = nullptr;
     cudaStream_t batch_aux[kClasses - 1] = {};  // a phase's other classes run beside the first
     cudaEvent_t batch_fork[kPhases] = {};
@@ -251,6 +285,9 @@ struct gace_ctx {
 
     // resident samples and sketches
     ResidentStore resident;
+
+    // host workers of large batches
+    HostPool workers;
 
     bool fits(uint64_t extra) const { return budget == 0 || used + extra <= budget; }
 
@@ -670,6 +707,12 @@ struct FusedProbe {
     std::vector<uint64_t> marg;
     std::vector<Member> members;
     gace_request q{};
+    // Fusion rules: 0, the rules of fits() below (a one-predicate request on
+    // one row set runs alone); 1, such requests fuse too; 2, as 1, and a group
+    // takes the union of its members' row sets (at most kMaxSets) and of their
+    // columns (at most kMaxRowBytes per row).  The batch autotuner picks one
+    // per batch shape.
+    int mode = 0;
 
     static constexpr uint32_t kMaxIn = 1024;     // IN values of all members
 #ifndef GACE_FUSE
@@ -690,8 +733,9 @@ struct FusedProbe {
     void scatter() const;
 };
 
-// Whether a probe request is a candidate for fusion.
-bool fusable_probe(const gace_request& r);
+// Whether a probe request is a candidate for fusion under the rules of `mode`
+// (FusedProbe::mode).
+bool fusable_probe(const gace_request& r, int mode = 0);
 // The columns a probe's terms reference as a bit mask (~0 when one is >= 64);
 // fused groups are seeded with the requests that read the most columns.
 uint64_t probe_colmask(const gace_request& r);

@@ -196,3 +196,73 @@ def test_fused_probes_on_one_table(g, gctx, batched):
         assert np.array_equal(q.results["pcs"], res["pcs"], equal_nan=True)
         if m:
             assert np.array_equal(q.marginals, marg)
+
+
+def _set_fusion_rule(g, ctx, tables, reqs, n, mode, tmp_path):
+    """Loads a tuning line that makes batches of this request shape (n
+    requests reading these tables' rows) use fusion rule `mode`."""
+    import json
+
+    rows = 0
+    for r in reqs:
+        if r["kind"] == "join":
+            rows += tables[r["fact"]].nrows + tables[r["dim"]].nrows
+        else:
+            rows += tables[r["table"]].nrows
+    log2 = lambda x: max(0, int(x).bit_length() - 1)  # noqa: E731
+    path = tmp_path / f"fuse{mode}.jsonl"
+    path.write_text(json.dumps({"requests_log2": log2(n), "rows_log2": log2(rows), "fuse": mode}) + "\n")
+    g.gace_tune_load(ctx, str(path))
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_every_fusion_rule_gives_the_same_results(g, batched, tmp_path, mode):
+    """Under each fusion rule (one-predicate probes alone; fused too; groups
+    with the union of their members' row sets and columns) every request of
+    the mixed batch (planned on the host workers: more than 64 requests)
+    gives what its synchronous call gives."""
+    tables, reqs, _ = batched
+    ctx = g.gace_create(0)
+    try:
+        tids = [g.gace_load_columns(ctx, t.columns, borrow=True) for t in tables]
+        _set_fusion_rule(g, ctx, tables, reqs, len(reqs), mode, tmp_path)
+        breqs = _to_requests(g, tids, tables, reqs)
+        assert g.gace_run_batch(ctx, breqs) == [0] * len(reqs)
+        _check_against_sync(g, ctx, tids, tables, reqs, breqs)
+    finally:
+        g.gace_destroy(ctx)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_fusion_rules_on_one_table(g, batched, tmp_path, mode):
+    """One-predicate probes on one row set, and probes on different row sets
+    and columns, fused on one table under rules 1 and 2: each member's counts,
+    selectivities, PCS and marginals equal its synchronous call's."""
+    tables, _, _ = batched
+    t = tables[3]
+    pool = [Sample(FULL), Sample(ROWS, 0.01, 42), Sample(BLOCKS, 0.01, 42, 4096), Sample(ROWS, 0.1, 7),
+            Sample(BLOCKS, 0.05, 9, 512)]
+    rng = np.random.default_rng(23 + mode)
+    specs = []
+    for i in range(48):
+        npred = 1 if i % 3 else int(rng.integers(2, 4))
+        preds = make_predicates(t, npred, 1, 4, seed=900 + i)
+        smp = [pool[int(rng.integers(0, len(pool)))]] if i % 4 else \
+            [pool[k] for k in rng.choice(len(pool), 2, replace=False)]
+        specs.append((preds, smp, bool(i % 5 == 0)))
+    ctx = g.gace_create(0)
+    try:
+        tid = g.gace_load_columns(ctx, t.columns, borrow=True)
+        pseudo = [{"kind": "probe", "table": 0}] * len(specs)
+        _set_fusion_rule(g, ctx, [t], pseudo, len(specs), mode, tmp_path)
+        breqs = [g.ProbeRequest(tid, p, s, t.dtypes, marginals=m) for p, s, m in specs]
+        assert g.gace_run_batch(ctx, breqs) == [0] * len(specs)
+        for (preds, smp, m), q in zip(specs, breqs):
+            res, marg = g.gace_probe_batch(ctx, tid, preds, smp, t.dtypes, marginals=m)
+            for f in ("match", "sample_rows", "sel"):
+                assert np.array_equal(q.results[f], res[f])
+            assert np.array_equal(q.results["pcs"], res["pcs"], equal_nan=True)
+            if m:
+                assert np.array_equal(q.marginals, marg)
+    finally:
+        g.gace_destroy(ctx)
