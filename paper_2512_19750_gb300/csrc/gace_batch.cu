@@ -52,15 +52,23 @@ __device__ __forceinline__ void probe_item(const BatchJob& J, const BatchItem& i
 template <int DT>
 __device__ __forceinline__ void hll_item_t(const HllArgs& H, const BatchItem& it, uint32_t* sregs, int tid) {
     const uint64_t first = it.begin / 4 + tid, end = (it.end + 3) / 4;
-    if (H.p <= 16) {  // the host sizes shared memory for 2^16 one-byte registers
-        const uint32_t m = 1u << H.p;
-        for (uint32_t i = tid; i < m / 4; i += kThreads) sregs[i] = 0;
+    const uint32_t m = 1u << H.p;
+    // the host sizes shared memory for 2^p 32-bit registers up to p = 14,
+    // one-byte registers for p = 15, 16
+    if (H.p <= kHllWordsMaxP) {
+        hll_clear<kHllWords>(sregs, m, tid, kThreads);
         __syncthreads();
-        hll_groups<true, DT, 2>(H, sregs, first, end, kThreads);
+        hll_groups<kHllWords, DT, 2>(H, sregs, first, end, kThreads);
         __syncthreads();
-        hll_merge(H, sregs, m, tid, kThreads);
+        hll_merge<kHllWords>(H, sregs, m, tid, kThreads);
+    } else if (H.p <= 16) {
+        hll_clear<kHllBytes>(sregs, m, tid, kThreads);
+        __syncthreads();
+        hll_groups<kHllBytes, DT, 2>(H, sregs, first, end, kThreads);
+        __syncthreads();
+        hll_merge<kHllBytes>(H, sregs, m, tid, kThreads);
     } else {
-        hll_groups<false, DT, 2>(H, sregs, first, end, kThreads);
+        hll_groups<kHllGlobal, DT, 2>(H, sregs, first, end, kThreads);
     }
 }
 

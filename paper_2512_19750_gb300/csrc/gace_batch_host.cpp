@@ -392,7 +392,8 @@ void emit_jobs(ReqPlan& rp, unsigned char* dws, unsigned int* batch_status, std:
         jr.job.hll.regs = reinterpret_cast<uint32_t*>(dws + rp.regs_off);
         jr.job.hll.status = batch_status;
         jr.units = rp.hll.nrows;
-        jr.smem = rp.hll.p <= 16 ? (1u << rp.hll.p) : 0u;
+        // shared-memory registers: 32-bit up to p = 14, one byte for p = 15, 16
+        jr.smem = rp.hll.p <= 14 ? (4u << rp.hll.p) : rp.hll.p <= 16 ? (1u << rp.hll.p) : 0u;
         jr.cost = 4;  // two 64-bit multiplies and a register update per row
         jr.family = "batch_hll";
         jr.rows = jr.units;

@@ -4,11 +4,11 @@
 // NDV is the statistic behind the drift signal D of the paper (Section III-C,
 // Eq. 1); the sketch is HyperLogLog (Flajolet, Fusy, Gandouet & Meunier,
 // AofA 2007) with a 64-bit splitmix64-based hash.  Each CTA keeps a private
-// copy of the 2^p one-byte registers in shared memory (max-updated with a
-// compare-and-swap on the containing word, skipped whenever the register is
-// already large enough, which is the common case on skewed data), then merges
-// it into 32-bit global registers with atomicMax, again only where it would
-// raise them.
+// copy of the 2^p registers in shared memory, 32-bit up to p = 14 (raised by
+// one atomicMax) and one byte each above (raised by a compare-and-swap on the
+// containing word), updated only when a row's rank would raise its register;
+// the copy is then merged into 32-bit global registers with atomicMax, again
+// only where it would raise them.
 //
 // Join cardinality (the join-correlation failures the method targets,
 // Section IV-F) is the dot product of filtered key-frequency histograms.
@@ -38,19 +38,19 @@ constexpr int kJoinThreads = 256;
 #define GACE_HLL_UNROLL 1
 #endif
 
-template <bool SMEM, int DT>
+template <int REGS, int DT>
 __global__ void __launch_bounds__(kHllThreads, 2) k_hll(const __grid_constant__ HllArgs A) {
     extern __shared__ uint32_t sregs[];
     const uint32_t m = 1u << A.p;
-    if (SMEM) {
-        for (uint32_t i = threadIdx.x; i < m / 4; i += kHllThreads) sregs[i] = 0;
+    if (REGS != kHllGlobal) {
+        hll_clear<REGS>(sregs, m, threadIdx.x, kHllThreads);
         __syncthreads();
     }
-    hll_groups<SMEM, DT, GACE_HLL_UNROLL>(A, sregs, static_cast<uint64_t>(blockIdx.x) * kHllThreads + threadIdx.x,
+    hll_groups<REGS, DT, GACE_HLL_UNROLL>(A, sregs, static_cast<uint64_t>(blockIdx.x) * kHllThreads + threadIdx.x,
                                           (A.nrows + 3) / 4, static_cast<uint64_t>(gridDim.x) * kHllThreads);
-    if (SMEM) {
+    if (REGS != kHllGlobal) {
         __syncthreads();
-        hll_merge(A, sregs, m, threadIdx.x, kHllThreads);
+        hll_merge<REGS>(A, sregs, m, threadIdx.x, kHllThreads);
     }
 }
 
@@ -190,28 +190,35 @@ int grid_for(uint64_t units, int per_cta, int sms, int ctas_per_sm) {
 
 }  // namespace
 
-template <bool SMEM, int DT>
+template <int REGS, int DT>
 static cudaError_t hll_launch_t(const HllArgs& a, int sms, cudaStream_t s) {
     const uint64_t groups = (a.nrows + 3) / 4;
-    const uint32_t smem = SMEM ? (1u << a.p) : 0u;
-    cudaError_t e = cudaFuncSetAttribute(k_hll<SMEM, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const uint32_t smem = REGS == kHllWords ? (4u << a.p) : REGS == kHllBytes ? (1u << a.p) : 0u;
+    cudaError_t e = cudaFuncSetAttribute(k_hll<REGS, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_hll<SMEM, DT>, kHllThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_hll<REGS, DT>, kHllThreads, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
-    k_hll<SMEM, DT><<<grid_for(groups, kHllThreads, sms, occ), kHllThreads, smem, s>>>(a);
+    k_hll<REGS, DT><<<grid_for(groups, kHllThreads, sms, occ), kHllThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
+template <int DT>
+static cudaError_t hll_launch_dt(const HllArgs& a, int sms, cudaStream_t s) {
+    // 32-bit registers in shared memory up to p = 14 (64 KB: two CTAs per
+    // SM), one-byte registers up to p = 17 (128 KB), else straight to global
+    if (a.p <= kHllWordsMaxP) return hll_launch_t<kHllWords, DT>(a, sms, s);
+    if (a.p <= 17) return hll_launch_t<kHllBytes, DT>(a, sms, s);
+    return hll_launch_t<kHllGlobal, DT>(a, sms, s);
+}
+
 cudaError_t hll_launch(const HllArgs& a, int sms, cudaStream_t s) {
-    // registers in shared memory up to p = 17 (128 KB), else straight to global
-    const bool sm = a.p <= 17;
     switch (a.dtype) {
-        case 0: return sm ? hll_launch_t<true, 0>(a, sms, s) : hll_launch_t<false, 0>(a, sms, s);
-        case 1: return sm ? hll_launch_t<true, 1>(a, sms, s) : hll_launch_t<false, 1>(a, sms, s);
-        default: return sm ? hll_launch_t<true, 2>(a, sms, s) : hll_launch_t<false, 2>(a, sms, s);
+        case 0: return hll_launch_dt<0>(a, sms, s);
+        case 1: return hll_launch_dt<1>(a, sms, s);
+        default: return hll_launch_dt<2>(a, sms, s);
     }
 }
 

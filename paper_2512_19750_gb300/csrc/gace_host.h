@@ -168,6 +168,7 @@ struct gace_ctx {
     uint64_t timeout_ns = 2000ull * 1000000ull;
     uint32_t max_ctas = 0;     // cap on the CTAs of a probe launch (0 = none)
     uint64_t rank_min_rows = 0;  // smallest table a batch probe rank-codes (0: kRankMinRows)
+    uint32_t rank_search = 0;    // gace_config.rank_search
     std::mutex mu;
     std::unordered_map<uint32_t, TableRec> tables;
     uint32_t next_id = 1;
@@ -497,8 +498,10 @@ struct RankCode {
     uint32_t col = 0;
     uint32_t dtype = 0;
     std::vector<uint64_t> keys;
-    std::vector<uint32_t> tree;  // words: keys, or (lo, hi) pairs for int64
-    uint32_t levels = 0;
+    std::vector<uint32_t> tree;  // search tree words: keys, or (lo, hi) pairs for int64; or the bucket index
+    uint32_t levels = 0;         // search tree levels (0: the bucket index below)
+    uint64_t bbase = 0;          // bucket index (RankArgs): base key, buckets, shifts, halvings
+    uint32_t bnb = 0, bsmin = 0, bmbits = 0, bsteps = 0;
     bool all_terms = false;      // EQ and IN terms too (each value a one-key interval)
     bool used = false;           // some wide pass of the plan reads the column's ranks
     bool hist_fits = false;      // its histograms fit the rank pass's shared memory
@@ -638,7 +641,7 @@ gace_status build_side(gace_ctx* ctx, const gace_join_side& js, const char* name
 // ---------------------------------------------------------------- batched and served forms
 
 constexpr uint64_t kDefaultChunk = 1ull << 20;
-constexpr uint32_t kHllSmem = 1u << 16;  // one-byte registers for p <= 16
+constexpr uint32_t kHllSmem = 1u << 16;  // 32-bit registers for p <= 14, one-byte for p = 15, 16
 
 struct JobRec {
     BatchJob job{};

@@ -30,15 +30,6 @@ __device__ __forceinline__ uint64_t canonical_key(uint32_t dtype, uint32_t lo, u
     return lo;
 }
 
-// Register index j = the top p bits of the hash (p <= 18: within its high
-// word) and rho = the leading zeros of the remaining 64 - p bits, + 1.  With
-// r = those bits, 2 r + 1 has 63 - (64 - p) + (leading zeros of r) + 1
-// leading zeros, and 1 (63) when r = 0, which gives rho = 65 - p there: no
-// variable-width 64-bit shift per row (the mask is loop-invariant).
-#ifndef GACE_HLL_HASH32
-#define GACE_HLL_HASH32 0
-#endif
-#if GACE_HLL_HASH32
 // x ^= x >> s (0 < s < 32) and x *= c on a 64-bit value held as two words.
 __device__ __forceinline__ void xs_words(uint32_t& lo, uint32_t& hi, int s) {
     lo ^= __funnelshift_r(lo, hi, s);
@@ -50,13 +41,16 @@ __device__ __forceinline__ void mul_words(uint32_t& lo, uint32_t& hi, uint64_t c
     lo *= cl;
     hi = nh;
 }
-#endif
 
+// Register index j = the top p bits of the hash (p <= 18: within its high
+// word) and rho = the leading zeros of the remaining 64 - p bits, + 1 (65 - p
+// when they are all zero).  The hash, splitmix64 of key ^ seedhash, is taken
+// word by word; the remaining bits are the high word's low 32 - p bits, then
+// the low word, so rho is the leading zeros of the first, plus those of the
+// second when the first is zero (a zero word has 32), less p, plus 1.
 __device__ __forceinline__ void hll_rank(uint64_t key, uint64_t seedhash, uint32_t p,
                                          uint32_t& j, uint32_t& rho) {
-#if GACE_HLL_HASH32
-    // splitmix64 of key ^ seedhash, word by word
-    uint64_t x = (key ^ seedhash) + 0x9E3779B97F4A7C15ull;
+    const uint64_t x = (key ^ seedhash) + 0x9E3779B97F4A7C15ull;
     uint32_t lo = static_cast<uint32_t>(x), hi = static_cast<uint32_t>(x >> 32);
     xs_words(lo, hi, 30);
     mul_words(lo, hi, 0xBF58476D1CE4E5B9ull);
@@ -64,16 +58,8 @@ __device__ __forceinline__ void hll_rank(uint64_t key, uint64_t seedhash, uint32
     mul_words(lo, hi, 0x94D049BB133111EBull);
     xs_words(lo, hi, 31);
     j = hi >> (32 - p);
-    // 2 r + 1 with r the low 64 - p bits: its leading zeros over both words
-    const uint32_t rh = ((hi & ((1u << (32 - p)) - 1u)) << 1) | (lo >> 31);
-    const uint32_t rl = (lo << 1) | 1u;
-    rho = (rh ? static_cast<uint32_t>(__clz(rh)) : 32u + static_cast<uint32_t>(__clz(rl))) + 2u - p;
-#else
-    const uint64_t h = splitmix64(key ^ seedhash);
-    j = static_cast<uint32_t>(h >> 32) >> (32 - p);
-    const uint64_t r = h & ((1ull << (64 - p)) - 1);
-    rho = static_cast<uint32_t>(__clzll(static_cast<long long>(2 * r + 1))) + 2u - p;
-#endif
+    const uint32_t rh = hi & ((1u << (32 - p)) - 1u);
+    rho = static_cast<uint32_t>(__clz(rh)) + (rh ? 0u : static_cast<uint32_t>(__clz(lo))) + 1u - p;
 }
 
 // byte-wise max in shared memory via CAS on the containing word (bounded)
@@ -94,12 +80,20 @@ __device__ __forceinline__ void smem_byte_max(uint32_t* words, uint32_t j, uint3
     }
 }
 
+// Where a CTA keeps the registers it updates: the job's global 32-bit
+// registers, a shared-memory copy of one-byte registers (raised by a CAS on
+// the containing word), or a shared-memory copy of 32-bit registers (raised
+// by one atomicMax, no retry loop: a CTA's copy starts at zero and is raised
+// a few times per register as its rows arrive, which on data with many
+// distinct values makes the CAS loop the kernel's bottleneck).
+enum HllRegs : int { kHllGlobal = 0, kHllBytes = 1, kHllWords = 2 };
+// The largest p whose 32-bit registers a CTA keeps in shared memory (64 KB).
+constexpr uint32_t kHllWordsMaxP = 14;
+
 // HLL of one group of four rows starting at row0 (values in v): rank of each
-// value, then a max-update of its register (CTA copy in shared memory when
-// SMEM, else the global 32-bit registers).
-template <bool SMEM, int DT>
+// value, then a max-update of its register where the rank would raise it.
+template <int REGS, int DT>
 __device__ __forceinline__ void hll_quad(const HllArgs& A, uint32_t* sregs, const Quad& v, uint64_t row0) {
-    const unsigned char* sbytes = reinterpret_cast<const unsigned char*>(sregs);
     // ranks of the four values first (independent), then the register checks
     uint32_t j[4], rho[4];
 #pragma unroll
@@ -109,7 +103,15 @@ __device__ __forceinline__ void hll_quad(const HllArgs& A, uint32_t* sregs, cons
         for (int r = 0; r < 4; ++r)
             if (row0 + r >= A.nrows) rho[r] = 0;  // never raises a register
     }
-    if (SMEM) {
+    if (REGS == kHllWords) {
+        uint32_t cur[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) cur[r] = reinterpret_cast<const volatile uint32_t*>(sregs)[j[r]];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            if (rho[r] > cur[r]) atomicMax(&sregs[j[r]], rho[r]);
+    } else if (REGS == kHllBytes) {
+        const unsigned char* sbytes = reinterpret_cast<const unsigned char*>(sregs);
         uint32_t cur[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) cur[r] = *reinterpret_cast<const volatile unsigned char*>(&sbytes[j[r]]);
@@ -127,7 +129,7 @@ __device__ __forceinline__ void hll_quad(const HllArgs& A, uint32_t* sregs, cons
 // takes two groups per iteration with both loads issued before either is
 // hashed (the second load may fall past `end`; it is bounded by the table and
 // ignored), for kernels with few warps per SM.
-template <bool SMEM, int DT, int U = 1>
+template <int REGS, int DT, int U = 1>
 __device__ __forceinline__ void hll_groups(const HllArgs& A, uint32_t* sregs, uint64_t first, uint64_t end,
                                            uint64_t stride) {
     constexpr uint32_t width = DT == 1 ? 8 : 4;
@@ -135,7 +137,7 @@ __device__ __forceinline__ void hll_groups(const HllArgs& A, uint32_t* sregs, ui
         for (uint64_t g = first; g < end; g += stride) {
             Quad v;
             load_quad_global(A.col, width, g * 4, A.nrows, v);
-            hll_quad<SMEM, DT>(A, sregs, v, g * 4);
+            hll_quad<REGS, DT>(A, sregs, v, g * 4);
         }
     } else {
         for (uint64_t g = first; g < end; g += 2 * stride) {
@@ -143,18 +145,26 @@ __device__ __forceinline__ void hll_groups(const HllArgs& A, uint32_t* sregs, ui
             Quad v0, v1;
             load_quad_global(A.col, width, g * 4, A.nrows, v0);
             load_quad_global(A.col, width, g2 * 4, A.nrows, v1);
-            hll_quad<SMEM, DT>(A, sregs, v0, g * 4);
-            if (g2 < end) hll_quad<SMEM, DT>(A, sregs, v1, g2 * 4);
+            hll_quad<REGS, DT>(A, sregs, v0, g * 4);
+            if (g2 < end) hll_quad<REGS, DT>(A, sregs, v1, g2 * 4);
         }
     }
 }
 
+// Clears a CTA's shared-memory registers (m of them, REGS kHllBytes or kHllWords).
+template <int REGS>
+__device__ __forceinline__ void hll_clear(uint32_t* sregs, uint32_t m, uint32_t tid, uint32_t nthreads) {
+    const uint32_t words = REGS == kHllWords ? m : m / 4;
+    for (uint32_t i = tid; i < words; i += nthreads) sregs[i] = 0;
+}
+
 // A CTA's shared-memory registers into the global ones, only where larger.
+template <int REGS>
 __device__ __forceinline__ void hll_merge(const HllArgs& A, const uint32_t* sregs, uint32_t m, uint32_t tid,
                                           uint32_t nthreads) {
     const unsigned char* sbytes = reinterpret_cast<const unsigned char*>(sregs);
     for (uint32_t jj = tid; jj < m; jj += nthreads) {
-        const uint32_t r = sbytes[jj];
+        const uint32_t r = REGS == kHllWords ? sregs[jj] : sbytes[jj];
         if (r && r > __ldcg(&A.regs[jj])) atomicMax(&A.regs[jj], r);
     }
 }
