@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define GACE_ABI_VERSION 3
+#define GACE_ABI_VERSION 4
 
 typedef enum {
     GACE_OK = 0,
@@ -81,6 +81,14 @@ typedef struct {
                                   more than 32 predicates and at least 384
                                   distinct terms).  Rank coding changes no
                                   result, only the kernels that compute it */
+    uint32_t rank_search;      /* how the rank pass finds a value's rank among a
+                                  column's endpoints: 0 = per column, a bucket
+                                  index (the value's bucket gives the first
+                                  candidate endpoint, a few halvings the rank)
+                                  where it takes at least two fewer dependent
+                                  lookups than the search tree, else the tree;
+                                  1 = the search tree; 2 = the bucket index.
+                                  Changes no result; other values: GACE_EINVAL */
 } gace_config;
 
 /* One column of a table: nrows elements of dtype, densely packed. */
@@ -492,6 +500,9 @@ typedef struct {
                                for a narrow probe pass to a multiple of its tile; 0 = 2^18 */
     uint32_t flags;         /* GACE_SERVE_* */
     int32_t probe_cache;    /* probe counts kept for reuse (entries); 0 = 65536, < 0 = no cache */
+    uint32_t idle_spin_us;  /* an idle scheduler watches its queue this long (yielding its
+                               thread) before it sleeps, so that a request arriving meanwhile
+                               does not wait out a thread wake-up; 0 = 10000 */
 } gace_serve_config;
 
 /* Never run a request alone through its synchronous call: every request goes

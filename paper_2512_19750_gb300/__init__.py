@@ -95,9 +95,10 @@ def gace_abi_version() -> int:
 
 
 def gace_create(device: int = 0, stream=None, hbm_budget_bytes: int = 0,
-                wait_timeout_ms: int = 0, max_ctas: int = 0, rank_min_rows: int = 0) -> int:
+                wait_timeout_ms: int = 0, max_ctas: int = 0, rank_min_rows: int = 0,
+                rank_search: int = 0) -> int:
     cfg = _capi.gace_config(device, wait_timeout_ms, hbm_budget_bytes, _stream_handle(stream), max_ctas,
-                            rank_min_rows)
+                            rank_min_rows, rank_search)
     out = C.c_void_p()
     check(lib().gace_create(C.byref(out), C.byref(cfg)), "gace_create")
     return out.value
@@ -414,9 +415,10 @@ _SUBMITTED: dict = {}  # (context, ticket) -> request object whose outputs are p
 
 def gace_serve_start(ctx, arena_bytes: int = 0, max_inflight: int = 0, sketch_cache: int = 0,
                      step_rows: int = 0, chunk_rows: int = 0, always_step: bool = False,
-                     probe_cache: int = 0) -> None:
+                     probe_cache: int = 0, idle_spin_us: int = 0) -> None:
     cfg = _capi.gace_serve_config(arena_bytes, max_inflight, sketch_cache, step_rows, chunk_rows,
-                                  _capi.GACE_SERVE_ALWAYS_STEP if always_step else 0, probe_cache)
+                                  _capi.GACE_SERVE_ALWAYS_STEP if always_step else 0, probe_cache,
+                                  idle_spin_us)
     check(lib().gace_serve_start(ctx, C.byref(cfg)), "gace_serve_start")
 
 

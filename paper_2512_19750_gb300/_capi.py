@@ -28,7 +28,7 @@ class gace_scalar(C.Union):
 class gace_config(C.Structure):
     _fields_ = [("device", C.c_int32), ("wait_timeout_ms", C.c_uint32),
                 ("hbm_budget_bytes", C.c_uint64), ("stream", C.c_void_p), ("max_ctas", C.c_uint32),
-                ("rank_min_rows", C.c_uint32)]
+                ("rank_min_rows", C.c_uint32), ("rank_search", C.c_uint32)]
 
 
 class gace_column(C.Structure):
@@ -90,7 +90,7 @@ GACE_SERVE_ALWAYS_STEP = 1
 class gace_serve_config(C.Structure):
     _fields_ = [("arena_bytes", C.c_uint64), ("max_inflight", C.c_uint32), ("sketch_cache", C.c_int32),
                 ("step_rows", C.c_uint64), ("chunk_rows", C.c_uint64), ("flags", C.c_uint32),
-                ("probe_cache", C.c_int32)]
+                ("probe_cache", C.c_int32), ("idle_spin_us", C.c_uint32)]
 
 
 class gace_kernel_stat(C.Structure):

@@ -1005,6 +1005,78 @@ void build_rank_tree(RankCode& rc) {
         }
 }
 
+// Bucket of key distance d (RankArgs): linear buckets of 2^smin keys up to
+// 2^(smin + mbits + 1), then 2^mbits buckets per doubling of d.
+uint64_t rank_bucket(uint64_t d, uint32_t smin, uint32_t mbits) {
+    const int len = d ? 64 - __builtin_clzll(d) : 0;
+    const uint32_t s = std::max<int>(static_cast<int>(smin), len - static_cast<int>(mbits) - 1);
+    return (static_cast<uint64_t>(s - smin) << mbits) + (d >> s);
+}
+
+// A bucket index of a rank-coded column's endpoints instead of its search
+// tree (search: gace_config.rank_search): of linear buckets and of buckets
+// growing with the distance from the smallest endpoint (at most kRankBuckets
+// of either), the one whose fullest bucket needs the fewest halvings, taken
+// when it needs at least two fewer dependent shared-memory loads than the
+// tree (always under search 2, never under search 1).
+void build_rank_buckets(RankCode& rc, uint32_t search) {
+    constexpr uint64_t kRankBuckets = 8192;
+    const uint32_t m = static_cast<uint32_t>(rc.keys.size());
+    if (search == 1 || m == 0) return;
+    const bool is64 = rc.dtype == GACE_I64;
+    const uint32_t maxbits = is64 ? 63u : 31u;
+    const uint64_t base = rc.keys.front(), span = rc.keys.back() - base;
+    struct Cand {
+        uint32_t smin = 0, mbits = 0, steps = 99;
+        uint64_t nb = 0;
+    } best;
+    for (uint32_t mbits : {maxbits, 8u, 6u}) {
+        uint32_t smin = 0;
+        while (rank_bucket(span, smin, mbits) >= kRankBuckets) ++smin;
+        const uint64_t nb = rank_bucket(span, smin, mbits) + 1;
+        uint64_t fullest = 0, run = 0, prev = ~0ull;
+        for (uint64_t k : rc.keys) {
+            const uint64_t b = rank_bucket(k - base, smin, mbits);
+            run = b == prev ? run + 1 : 1;
+            prev = b;
+            fullest = std::max(fullest, run);
+        }
+        uint32_t steps = 0;
+        while ((1ull << steps) < fullest + 1) ++steps;
+        if (steps < best.steps || (steps == best.steps && nb < best.nb)) best = {smin, mbits, steps, nb};
+    }
+    if (search == 0 && best.steps + 1 + 2 > rc.levels) return;
+    const uint64_t kmax = is64 ? ~0ull : 0xFFFFFFFFull;
+    const uint64_t nends = m + (1ull << best.steps);
+    // the 16-bit first indices take whole 8-byte units, so that the (lo, hi)
+    // endpoint pairs of an int64 column start 8-byte aligned
+    const uint64_t start_words = rank_start_words(static_cast<uint32_t>(best.nb));
+    std::vector<uint32_t> words(start_words + nends * (is64 ? 2 : 1), 0u);
+    uint16_t* start = reinterpret_cast<uint16_t*>(words.data());
+    uint32_t i = 0;
+    for (uint64_t b = 0; b < best.nb; ++b) {  // first endpoint at or after bucket b
+        while (i < m && rank_bucket(rc.keys[i] - base, best.smin, best.mbits) < b) ++i;
+        start[b] = static_cast<uint16_t>(i);
+    }
+    uint32_t* ends = words.data() + start_words;
+    for (uint64_t e = 0; e < nends; ++e) {
+        const uint64_t key = e < m ? rc.keys[e] : kmax;
+        if (is64) {
+            ends[2 * e] = static_cast<uint32_t>(key);
+            ends[2 * e + 1] = static_cast<uint32_t>(key >> 32);
+        } else {
+            ends[e] = static_cast<uint32_t>(key);
+        }
+    }
+    rc.tree = std::move(words);
+    rc.levels = 0;
+    rc.bbase = base;
+    rc.bnb = static_cast<uint32_t>(best.nb);
+    rc.bsmin = best.smin;
+    rc.bmbits = best.mbits;
+    rc.bsteps = best.steps;
+}
+
 gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r, bool force_wide,
                        ProbePlan& plan, uint32_t wide_warps, bool rank_code) {
     plan = ProbePlan();
@@ -1165,6 +1237,7 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
             rc.col = c;
             rc.dtype = static_cast<uint32_t>(tab.cols[c].dtype);
             build_rank_tree(rc);
+            build_rank_buckets(rc, ctx->rank_search);
             // marginals (and single-term counts) by rank histogram: one
             // shared-memory counter per set and rank
             rc.hist_fits = rc.tree.size() * 4 + sets.size() * (rc.keys.size() + 1) * 4 <= kRankHistSmem;
@@ -1644,6 +1717,12 @@ gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts, TableRe
                 ra.out = rc.used ? reinterpret_cast<uint16_t*>(dws + rank_off[i][c]) : nullptr;
                 ra.dtype = rc.dtype;
                 ra.levels = rc.levels;
+                ra.words = static_cast<uint32_t>(rc.tree.size());
+                ra.base = rc.bbase;
+                ra.nb = rc.bnb;
+                ra.smin = rc.bsmin;
+                ra.mbits = rc.bmbits;
+                ra.steps = rc.bsteps;
                 ra.m = static_cast<uint32_t>(rc.keys.size());
                 if (hist_off[i][c]) {
                     ra.hist = reinterpret_cast<unsigned long long*>(dws + hist_off[i][c]);
@@ -1717,12 +1796,14 @@ gace_status gace_create(gace_ctx** out, const gace_config* cfg) {
     if (e != cudaSuccess || n == 0)
         return fail(GACE_ECUDA, "no CUDA device: %s", e != cudaSuccess ? cudaGetErrorString(e) : "count is 0");
     if (c.device < 0 || c.device >= n) return fail(GACE_EINVAL, "device %d outside 0..%d", c.device, n - 1);
+    if (c.rank_search > 2) return fail(GACE_EINVAL, "rank_search = %u (0, 1 or 2)", c.rank_search);
     DeviceGuard g(c.device);
     gace_ctx* ctx = new gace_ctx();
     ctx->device = c.device;
     ctx->budget = c.hbm_budget_bytes;
     ctx->max_ctas = c.max_ctas;
     ctx->rank_min_rows = c.rank_min_rows;
+    ctx->rank_search = c.rank_search;
     if (c.wait_timeout_ms) ctx->timeout_ns = static_cast<uint64_t>(c.wait_timeout_ms) * 1000000ull;
     auto bail = [&](gace_status s) {
         gace_destroy(ctx);

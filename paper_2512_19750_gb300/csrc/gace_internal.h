@@ -200,12 +200,25 @@ struct RankArgs {
     unsigned long long* hist;  // nullptr: no histograms
     const uint32_t* qmask;     // nullptr when every set holds every row
     uint32_t dtype;
-    uint32_t levels;        // 1..13
+    uint32_t levels;        // search tree: 1..13 levels; 0: bucket index
     uint32_t m;             // endpoints (<= 8191)
     uint32_t nsets;         // row sets of the histograms (<= kMaxSets)
     uint32_t full_sets;
-    uint32_t pad;
+    uint32_t words;         // 32-bit words at tree (staged in shared memory)
+    // Bucket index (levels == 0): a key k >= base falls in bucket
+    // ((s - smin) << mbits) + ((k - base) >> s), s = max(smin, bit length of
+    // k - base - mbits - 1), at most nb - 1 (keys below base: bucket 0);
+    // tree holds the nb 16-bit first-endpoint indices of the buckets in
+    // rank_start_words(nb) words (whole 8-byte units), then the sorted
+    // endpoints (words, or 8-byte aligned (lo, hi) pairs for int64) padded
+    // with the largest key to m + 2^steps entries; the rank is the bucket's
+    // first index plus `steps` halvings over those entries.
+    uint64_t base;
+    uint32_t nb, smin, mbits, steps;
 };
+// Words of a bucket index's first-endpoint indices: nb 16-bit entries
+// rounded up to whole 8-byte units.
+__host__ __device__ constexpr uint32_t rank_start_words(uint32_t nb) { return 2u * ((nb + 3u) / 4u); }
 constexpr uint32_t kRankMaxEndpoints = 8191;
 constexpr uint32_t kRankMap16 = 0x80000000u;  // SlotDesc::rmap: the map has 16-bit entries
 cudaError_t rank_launch(const RankArgs& a, int sms, cudaStream_t s);

@@ -117,21 +117,27 @@ __global__ void __launch_bounds__(256) k_probe_setmask(const __grid_constant__ P
     }
 }
 
-// Rank coding of one column (RankArgs): the endpoints' search tree staged in
-// shared memory, then four rows per thread per step, their descents
-// interleaved level by level (one compare each), to the number of endpoints
-// <= each key; with histograms, each row's rank is counted in a shared-memory
-// histogram of every set that holds it, added to the global one at the end.
+// Rank coding of one column (RankArgs): the endpoints' search tree (or their
+// bucket index) staged in shared memory, then four rows per thread per step:
+// with the tree, their descents interleaved level by level (one compare
+// each), to the number of endpoints <= each key; with the bucket index, each
+// key's bucket gives the index of the first endpoint at or after the bucket's
+// lower bound, and `steps` halvings over the sorted endpoints from there count
+// those <= the key (the bucket holds fewer than 2^steps, and endpoints of
+// later buckets are larger than the key).  With histograms, each row's rank
+// is counted in a shared-memory histogram of every set that holds it, added
+// to the global one at the end.
+template <bool BUCKET>
 __global__ void __launch_bounds__(256) k_probe_rank(const __grid_constant__ RankArgs A) {
-    extern __shared__ uint32_t tree[];
+    extern __shared__ __align__(16) uint32_t tree[];
     const bool is64 = A.dtype == 1;
-    const uint32_t nkeys = (1u << A.levels) - 1u;
-    const uint32_t words = is64 ? 2u * nkeys : nkeys;
-    uint32_t* hist = tree + words;  // [set][rank], when A.hist
+    uint32_t* hist = tree + A.words;  // [set][rank], when A.hist
     const uint32_t bins = A.hist ? A.nsets * (A.m + 1) : 0u;
-    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) tree[i] = A.tree[i];
+    for (uint32_t i = threadIdx.x; i < A.words; i += blockDim.x) tree[i] = A.tree[i];
     for (uint32_t i = threadIdx.x; i < bins; i += blockDim.x) hist[i] = 0;
     __syncthreads();
+    const uint16_t* start = reinterpret_cast<const uint16_t*>(tree);
+    const uint32_t* ends = tree + rank_start_words(A.nb);  // 8-byte aligned
     const uint32_t width = is64 ? 8u : 4u;
     const uint64_t step = static_cast<uint64_t>(gridDim.x) * blockDim.x * 4u;
     for (uint64_t r0 = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) * 4u; r0 < A.nout; r0 += step) {
@@ -139,30 +145,66 @@ __global__ void __launch_bounds__(256) k_probe_rank(const __grid_constant__ Rank
         load_quad_global(A.col, width, r0, A.nrows, q);
         uint32_t klo[4], khi[4], n[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            value_key(A.dtype, q.lo[i], q.hi[i], klo[i], khi[i]);
-            n[i] = 1;
-        }
-        if (is64) {
-            const uint2* node = reinterpret_cast<const uint2*>(tree);
-            for (uint32_t d = 0; d < A.levels; ++d) {
+        for (int i = 0; i < 4; ++i) value_key(A.dtype, q.lo[i], q.hi[i], klo[i], khi[i]);
+        uint32_t rk[4];
+        if (BUCKET) {
+            if (is64) {
+                const uint2* e2 = reinterpret_cast<const uint2*>(ends);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    const uint2 e = node[n[i] - 1];
-                    n[i] = 2 * n[i] + ((khi[i] > e.y || (khi[i] == e.y && klo[i] >= e.x)) ? 1u : 0u);
+                    const uint64_t k = (static_cast<uint64_t>(khi[i]) << 32) | klo[i];
+                    const uint64_t d = k >= A.base ? k - A.base : 0ull;
+                    const int s = max(static_cast<int>(A.smin), 63 - __clzll(static_cast<long long>(d)) -
+                                                                     static_cast<int>(A.mbits));
+                    const uint64_t b = (static_cast<uint64_t>(s - static_cast<int>(A.smin)) << A.mbits) + (d >> s);
+                    n[i] = start[b < A.nb ? b : A.nb - 1];
+                }
+                for (uint32_t h = (1u << A.steps) >> 1; h; h >>= 1) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const uint2 e = e2[n[i] + h - 1];
+                        n[i] += (khi[i] > e.y || (khi[i] == e.y && klo[i] >= e.x)) ? h : 0u;
+                    }
+                }
+            } else {
+                const uint32_t base = static_cast<uint32_t>(A.base);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const uint32_t d = klo[i] >= base ? klo[i] - base : 0u;
+                    const int s = max(static_cast<int>(A.smin), 31 - __clz(d) - static_cast<int>(A.mbits));
+                    const uint32_t b = (static_cast<uint32_t>(s - static_cast<int>(A.smin)) << A.mbits) + (d >> s);
+                    n[i] = start[b < A.nb ? b : A.nb - 1];
+                }
+                for (uint32_t h = (1u << A.steps) >> 1; h; h >>= 1) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) n[i] += klo[i] >= ends[n[i] + h - 1] ? h : 0u;
                 }
             }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) rk[i] = r0 + i < A.nrows ? (n[i] < A.m ? n[i] : A.m) : 0u;
         } else {
-            for (uint32_t d = 0; d < A.levels; ++d) {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) n[i] = 2 * n[i] + (klo[i] >= tree[n[i] - 1] ? 1u : 0u);
+            for (int i = 0; i < 4; ++i) n[i] = 1;
+            if (is64) {
+                const uint2* node = reinterpret_cast<const uint2*>(tree);
+                for (uint32_t d = 0; d < A.levels; ++d) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const uint2 e = node[n[i] - 1];
+                        n[i] = 2 * n[i] + ((khi[i] > e.y || (khi[i] == e.y && klo[i] >= e.x)) ? 1u : 0u);
+                    }
+                }
+            } else {
+                for (uint32_t d = 0; d < A.levels; ++d) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) n[i] = 2 * n[i] + (klo[i] >= tree[n[i] - 1] ? 1u : 0u);
+                }
             }
-        }
-        uint32_t rk[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const uint32_t r = n[i] - (1u << A.levels);
-            rk[i] = r0 + i < A.nrows ? (r < A.m ? r : A.m) : 0u;
+            for (int i = 0; i < 4; ++i) {
+                const uint32_t r = n[i] - (1u << A.levels);
+                rk[i] = r0 + i < A.nrows ? (r < A.m ? r : A.m) : 0u;
+            }
         }
         if (A.out) *reinterpret_cast<uint2*>(A.out + r0) = make_uint2(rk[0] | (rk[1] << 16), rk[2] | (rk[3] << 16));
         if (A.hist) {
@@ -271,17 +313,17 @@ int probe_occupancy(const ProbeArgs& a) {
 }
 
 uint32_t rank_smem(const RankArgs& a) {
-    const uint32_t nkeys = (1u << a.levels) - 1u;
-    return nkeys * (a.dtype == 1 ? 8u : 4u) + (a.hist ? a.nsets * (a.m + 1) * 4u : 0u);
+    return a.words * 4u + (a.hist ? a.nsets * (a.m + 1) * 4u : 0u);
 }
 
-cudaError_t rank_launch(const RankArgs& a, int sms, cudaStream_t s) {
+template <bool BUCKET>
+static cudaError_t rank_launch_t(const RankArgs& a, int sms, cudaStream_t s) {
     const uint32_t smem = rank_smem(a);
-    cudaError_t e = cudaFuncSetAttribute(k_probe_rank, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_probe_rank<BUCKET>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_rank, 256, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_rank<BUCKET>, 256, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     // a full wave of resident CTAs (each histogram flush costs one global add per bin)
@@ -292,8 +334,12 @@ cudaError_t rank_launch(const RankArgs& a, int sms, cudaStream_t s) {
     // each CTA keeps 32-bit counts of the rows it ranks
     while (a.hist && (quads + grid * 256 - 1) / (grid * 256) * 1024 >= (1ull << 31)) grid *= 2;
     if (grid > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;
-    k_probe_rank<<<static_cast<int>(grid), 256, smem, s>>>(a);
+    k_probe_rank<BUCKET><<<static_cast<int>(grid), 256, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t rank_launch(const RankArgs& a, int sms, cudaStream_t s) {
+    return a.levels ? rank_launch_t<false>(a, sms, s) : rank_launch_t<true>(a, sms, s);
 }
 
 cudaError_t setmask_launch(const ProbeArgs& a, uint4* out, uint32_t* qmask, int sms, cudaStream_t s) {

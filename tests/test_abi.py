@@ -30,7 +30,7 @@ def test_library_exports_every_declared_symbol(g):
 
 
 def test_abi_version_and_status_names(g):
-    assert g.gace_abi_version() == 3
+    assert g.gace_abi_version() == 4
     assert g.gace_status_string(0) == "GACE_OK"
     assert g.gace_status_string(7) == "GACE_EOVERFLOW"
     assert g.gace_status_string(99) == "GACE_UNKNOWN"

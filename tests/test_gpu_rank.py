@@ -2,7 +2,8 @@
 
 A column whose terms' key intervals (ranges, single values, one per IN value)
 have at most 2047 distinct endpoints over the probe is read by rank: a
-pre-pass gives every row its rank among those endpoints, and each pass maps it
+pre-pass gives every row its rank among those endpoints (by a search tree, or
+by a bucket index and a few halvings), and each pass maps it
 to the rank among its own endpoints (a byte map, or 16-bit entries past 255
 local endpoints) before one mask lookup per group of 32 terms.  Past that
 bound the column's ranges alone may be coded (EQ and IN then by hash table in
@@ -21,11 +22,13 @@ pytestmark = pytest.mark.gpu
 SAMPLES = [Sample(FULL), Sample(ROWS, 0.2, 13), Sample(BLOCKS, 0.3, 4, 256)]
 
 
-@pytest.fixture(scope="module")
-def rctx(g):
+@pytest.fixture(scope="module", params=[0, 1, 2], ids=["search_auto", "search_tree", "search_buckets"])
+def rctx(g, request):
     """A context that rank-codes batches over tables of any size (the
-    default threshold, 2^20 rows, would leave these small tables uncoded)."""
-    ctx = g.gace_create(0, rank_min_rows=1)
+    default threshold, 2^20 rows, would leave these small tables uncoded),
+    with each way of finding a value's rank: per column, by search tree
+    only, by bucket index only."""
+    ctx = g.gace_create(0, rank_min_rows=1, rank_search=request.param)
     yield ctx
     g.gace_destroy(ctx)
 
@@ -161,3 +164,32 @@ def test_ranks_per_chunk_of_a_streamed_table(g, rctx, orc):
         check_probe(g, orc, rctx, tid, host, t.dtypes, preds, [Sample(FULL), Sample(ROWS, 0.05, 8)])
     finally:
         g.gace_unload(rctx, tid)
+
+
+def test_rank_search_edge_shapes(g, rctx, orc):
+    """Columns whose endpoints stress the bucket index: one endpoint only (an
+    EQ on the largest int32), 400 ranges crowded into 64 values next to a few
+    far apart (a full bucket needs many halvings), int64 endpoints spanning
+    the whole domain, and float endpoints on both sides of zero."""
+    rng = np.random.default_rng(67)
+    n = 100_003
+    c0 = rng.integers(2**31 - 4, 2**31, n, dtype=np.int64).astype(np.int32)
+    c1 = np.concatenate([rng.integers(1000, 1064, n - 100), rng.integers(-2**31, 2**31 - 1, 100)]).astype(np.int32)
+    c2 = (rng.integers(-2**62, 2**62, n, dtype=np.int64) * 2)
+    c2[::7] = rng.integers(-50, 50, c2[::7].shape[0])
+    c3 = rng.standard_normal(n).astype(np.float32)
+    preds = [[Term(0, EQ, 2**31 - 1)] for _ in range(3)]
+    for k in range(400):
+        a = 1000 + k % 64
+        preds.append([Term(1, RANGE, a, a + 1 + (k // 64))])
+    preds += [[Term(1, RANGE, -2**31, -2**30)], [Term(1, RANGE, 2**30, 2**31 - 1)], [Term(1, EQ, -2**31)]]
+    for k in range(120):
+        a = int(rng.integers(-2**61, 2**61)) * 2
+        preds.append([Term(2, RANGE, a, a + int(rng.integers(1, 2**61)))])
+        preds.append([Term(2, EQ, int(rng.integers(-50, 50)))])
+    for k in range(120):
+        a = float(rng.standard_normal())
+        preds.append([Term(3, RANGE, a, a + float(rng.uniform(1e-4, 2.0)))])
+    for k in range(30):
+        preds.append([Term(0, EQ, 2**31 - 1), Term(1, RANGE, 1000 + k, 1010 + k), Term(3, RANGE, -0.5, 0.5)])
+    _run(g, rctx, orc, [c0, c1, c2, c3], [I32, I32, I64, F32], preds)
