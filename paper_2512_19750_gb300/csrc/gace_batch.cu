@@ -185,7 +185,15 @@ __global__ void __launch_bounds__(kThreads, GACE_BATCH_PROBE_CTAS) k_batch_probe
             case 1: ok = narrow_run<false, 1>(A, S, tid, lane, warp, first, end, 1); break;
             case 2: ok = narrow_run<true, 1>(A, S, tid, lane, warp, first, end, 1); break;
             case 3: ok = narrow_run<true, kMaxSets>(A, S, tid, lane, warp, first, end, 1); break;
-            case 4: ok = single_run<false>(A, S, tid, lane, warp, first, end, 1); break;
+            case 4: {
+                // one predicate on all rows of narrow rows (at most 8 bytes):
+                // 16 rows per lane, as the plain single-predicate kernel
+                uint32_t rowbytes = 0;
+                for (uint32_t s = 0; s < A.nslots; ++s) rowbytes += A.slots[s].width;
+                ok = rowbytes <= 8 ? single_run<false, 4>(A, S, tid, lane, warp, first, end, 1)
+                                   : single_run<false>(A, S, tid, lane, warp, first, end, 1);
+                break;
+            }
             default: ok = single_run<true>(A, S, tid, lane, warp, first, end, 1); break;
         }
         if (!ok) return;  // uniform over the CTA; the status word says why

@@ -603,15 +603,22 @@ gace_status build_batch(gace_ctx* ctx, std::vector<ReqPlan>& rps, uint64_t chunk
     unsigned char* pin = ctx->pin;
     unsigned char* dws = ctx->ws;
     unsigned int* bstatus = reinterpret_cast<unsigned int*>(dws + br.small_base);
-    // inputs: pass tables and argument copies, join sides and pools
-    for (ReqPlan& rp : rps) {
-        if (rp.status != GACE_OK || rp.fused >= 0 || rp.kind != GACE_REQ_PROBE) continue;
+    // inputs: pass tables and argument copies, join sides and pools (each
+    // request's into its own staging bytes: a large batch on the workers)
+    auto stage_one = [&](uint32_t i) {
+        ReqPlan& rp = rps[i];
+        if (rp.status != GACE_OK || rp.fused >= 0 || rp.kind != GACE_REQ_PROBE) return;
         for (size_t k = 0; k < rp.plan.passes.size(); ++k) {
             Pass& ps = rp.plan.passes[k];
             stage_pass(ps, pin, dws, bstatus);
             memcpy(pin + rp.args_off[k], &ps.args, sizeof(ProbeArgs));
         }
-    }
+    };
+    const uint32_t nrp = static_cast<uint32_t>(rps.size());
+    if (nrp >= kParallelRequests)
+        ctx->workers.run(nrp, stage_one);
+    else
+        for (uint32_t i = 0; i < nrp; ++i) stage_one(i);
     for (const JobRec& jr : br.jobs) br.smem[jr.cls] = std::max(br.smem[jr.cls], jr.smem);
     br.jobs.clear();
     for (ReqPlan& rp : rps) emit_jobs(rp, dws, bstatus, br.jobs);
