@@ -440,17 +440,22 @@ typedef struct {
 gace_status gace_run_batch(gace_ctx* ctx, const gace_request* reqs, uint32_t n, gace_status* statuses);
 
 /*
- * Autotuner: runs the batch under each of three fusion rules (probes on one
+ * Autotuner: runs the batch under each of four fusion rules (probes on one
  * table fused only when they share their row sets and columns and are not
  * single predicates on one row set; single predicates fused too; groups that
- * take the union of their members' row sets and columns), each with every
+ * take the union of their members' row sets and columns; single predicates
+ * fused only on a shared row sample, with the union of their columns), each
+ * with every
  * candidate chunk size (128K..8M rows) and grid (1, 2 or the maximum of CTAs
- * per SM), times every candidate with CUDA events, and records the fastest:
+ * per SM), times every candidate with CUDA events (and each rule's planning
+ * of the batch on the host), and records the fastest (planning plus device
+ * time):
  * the fusion rule for batches of this request shape (requests and the rows of
  * the tables they read, each bucketed by powers of two), chunk and grid for
  * batches of the compiled shape (jobs and rows).  Results are the same
  * integers under every rule.  Each rule's best device time is added to the
- * kernel statistics as tune_batch_fuse0..2.
+ * kernel statistics as tune_batch_fuse0..3, its planning time as
+ * tune_batch_plan0..3.
  */
 gace_status gace_tune_batch(gace_ctx* ctx, const gace_request* reqs, uint32_t n);
 
@@ -545,6 +550,22 @@ gace_status gace_poll(gace_ctx* ctx, uint64_t ticket, uint64_t timeout_us);
  */
 gace_status gace_serve_replay(gace_ctx* ctx, const gace_request* reqs, uint32_t n, const uint64_t* arrival_ns,
                               uint32_t mode, uint64_t* done_ns, gace_status* statuses);
+
+/*
+ * The plain path with its calls overlapped (the baseline a caller gets by
+ * issuing synchronous probes from several threads): request i runs through
+ * its synchronous call (gace_probe_batch, gace_ndv or gace_join_card) on
+ * context ctxs[i % nctx]; each context's requests run in order on a host
+ * thread of its own (the calling thread takes context 0), so calls on
+ * different contexts, each on its own stream, overlap on the GPU.  The
+ * table ids of request i must name tables registered on ctxs[i % nctx] (the
+ * same borrowed columns may be registered on every context).  statuses (out,
+ * n entries, may be NULL) receives each request's status; the return value is
+ * GACE_OK when every request succeeded, else the first failing request's
+ * status.  No context may be used by another thread during the call.
+ */
+gace_status gace_run_plain_async(gace_ctx* const* ctxs, uint32_t nctx, const gace_request* reqs, uint32_t n,
+                                 gace_status* statuses);
 
 /* ------------------------------------------------------------ Risky Gate */
 /*

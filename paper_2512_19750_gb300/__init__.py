@@ -466,6 +466,18 @@ def gace_serve_replay(ctx, requests, arrival_ns, mode: int = 0):
     return done[:n], st[:n]
 
 
+def gace_run_plain_async(ctxs, requests):
+    """Request i (a request object or RequestArray entry whose table ids are
+    those of ctxs[i % len(ctxs)]) through its synchronous call on that context,
+    one host thread per context; returns the per-request statuses."""
+    n = len(requests)
+    arr = _request_array(requests)
+    cs = (C.c_void_p * len(ctxs))(*ctxs)
+    st = np.zeros(max(1, n), dtype=np.int32)
+    lib().gace_run_plain_async(cs, len(ctxs), arr, n, st.ctypes.data_as(C.POINTER(C.c_int)))
+    return [int(x) for x in st[:n]]
+
+
 def gace_gate_eval(inputs, config=None):
     """Risky Gate trust metrics (Eq. 1-3) of each input, a dict with keys
     ndv_hist, ndv_est, sel_est, sel_probe, pcs (missing keys are NaN: that

@@ -171,6 +171,8 @@ PROTOTYPES = {
     "gace_poll": (C.c_int, [ctx_p, C.c_uint64, C.c_uint64]),
     "gace_serve_replay": (C.c_int, [ctx_p, C.POINTER(gace_request), C.c_uint32, C.POINTER(C.c_uint64),
                                     C.c_uint32, C.POINTER(C.c_uint64), C.POINTER(C.c_int)]),
+    "gace_run_plain_async": (C.c_int, [C.POINTER(ctx_p), C.c_uint32, C.POINTER(gace_request), C.c_uint32,
+                                       C.POINTER(C.c_int)]),
     "gace_gate_eval": (C.c_int, [C.POINTER(gace_gate_config), C.POINTER(gace_gate_input), C.c_uint32,
                                  C.POINTER(gace_gate_result)]),
     "gace_break_even": (C.c_int, [ctx_p, C.POINTER(gace_cost_query), C.POINTER(gace_cost_answer)]),

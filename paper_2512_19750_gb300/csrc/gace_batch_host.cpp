@@ -115,8 +115,14 @@ bool fusable_probe(const gace_request& r, int mode) {
     // one predicate on one row set runs the register-only single-predicate
     // evaluation, cheaper per row than the narrow evaluation a fused group
     // needs: fusing it trades its bytes for more instructions per row, which
-    // pays only where many such requests read one table (modes 1 and 2)
-    if (mode == 0 && r.npreds <= 1 && r.nsamples <= 1) return false;
+    // pays only where many such requests read one table (modes 1 and 2), or
+    // where each of them would hash every row for the same row sample (mode 3)
+    if (r.npreds <= 1 && r.nsamples <= 1) {
+        if (mode == 0) return false;
+        if (mode == 3 && !(r.nsamples == 1 && r.samples[0].kind == GACE_ROWS && r.samples[0].rate > 0.0 &&
+                           r.samples[0].rate < 1.0))
+            return false;
+    }
     if (r.npreds > static_cast<uint32_t>(kNarrowMax) || r.nterms > static_cast<uint32_t>(kNarrowMax)) return false;
     if (r.nin > FusedProbe::kMaxIn) return false;
     if (r.npreds && (!r.preds || !r.results)) return false;
@@ -164,11 +170,13 @@ bool FusedProbe::fits(const gace_request& r, const TableRec& t) const {
     if (!GACE_FUSE) return false;
     const uint64_t m = probe_colmask(r);
     if (m == ~0ull || mask_rowbytes(colmask | m, t) > kMaxRowBytes) return false;
-    if (!members.empty() && mode < 2) {
-        if ((m | colmask) != colmask) return false;  // a new column: no saving on it
-        if (r.nsamples != members[0].q->nsamples) return false;
-        for (uint32_t k = 0; k < r.nsamples; ++k)
-            if (!same_sample(r.samples[k], members[0].q->samples[k])) return false;
+    if (!members.empty()) {
+        if (mode < 2 && (m | colmask) != colmask) return false;  // a new column: no saving on it
+        if (mode != 2) {  // the same row sets (rule 2 takes their union)
+            if (r.nsamples != members[0].q->nsamples) return false;
+            for (uint32_t k = 0; k < r.nsamples; ++k)
+                if (!same_sample(r.samples[k], members[0].q->samples[k])) return false;
+        }
     }
     if (preds.size() + r.npreds > static_cast<size_t>(kNarrowMax)) return false;
     if (terms.size() + r.nterms > static_cast<size_t>(kNarrowMax)) return false;
@@ -804,7 +812,11 @@ void finish_batch(gace_ctx* ctx, std::vector<ReqPlan>& rps, const BatchRun& br) 
 // so each reports its own error.
 gace_status compile_all(gace_ctx* ctx, const gace_request* reqs, uint32_t n, std::vector<ReqPlan>& rps,
                         std::vector<std::unique_ptr<FusedProbe>>& fused, int mode) {
-    rps.assign(n, ReqPlan());
+    // one plan per request, then one per fused group (at most one per
+    // request): reserved at once, so that appending groups moves no plan
+    rps.clear();
+    rps.reserve(2 * static_cast<size_t>(n));
+    rps.resize(n);
     fused.clear();
     std::vector<bool> alone(n, true);
     // candidates by table, the requests reading the most columns first (they seed the groups)
@@ -1061,13 +1073,18 @@ gace_status gace_tune_batch(gace_ctx* ctx, const gace_request* in, uint32_t n_in
     // every fusion rule, each over the grid of chunk sizes and CTAs per SM
     gace_ctx::TuneEntry best;
     best.ms = std::numeric_limits<double>::infinity();
+    double best_total = std::numeric_limits<double>::infinity();
     std::pair<int, int> best_key{0, 0};
     int best_mode = 0;
     gace_status rc = GACE_OK;
-    for (int mode = 0; mode <= 2 && rc == GACE_OK; ++mode) {
+    for (int mode = 0; mode <= 3 && rc == GACE_OK; ++mode) {
         std::vector<ReqPlan> rps;
         std::vector<std::unique_ptr<FusedProbe>> fused;
+        // a rule is judged by the batch's planning time plus its device time
+        const auto t_plan = std::chrono::steady_clock::now();
         compile_all(ctx, reqs, n, rps, fused, mode);
+        const double plan_ms =
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_plan).count();
         double mode_ms = std::numeric_limits<double>::infinity();
         for (uint64_t chunk = 1ull << 17; chunk <= (1ull << 23) && rc == GACE_OK; chunk <<= 2) {
             for (int per_sm : {1, 2, 0}) {
@@ -1085,7 +1102,8 @@ gace_status gace_tune_batch(gace_ctx* ctx, const gace_request* in, uint32_t n_in
                     ms = std::min(ms, static_cast<double>(t));
                 }
                 mode_ms = std::min(mode_ms, ms);
-                if (rc == GACE_OK && ms < best.ms) {
+                if (rc == GACE_OK && plan_ms + ms < best_total) {
+                    best_total = plan_ms + ms;
                     best.ms = ms;
                     best.chunk = chunk;
                     best.ctas_per_sm = per_sm;
@@ -1094,11 +1112,17 @@ gace_status gace_tune_batch(gace_ctx* ctx, const gace_request* in, uint32_t n_in
                 }
             }
         }
-        // each rule's best device time, for the caller's record
-        gace_ctx::KStat& k = ctx->stats[mode == 0 ? "tune_batch_fuse0" : mode == 1 ? "tune_batch_fuse1"
-                                                                                      : "tune_batch_fuse2"];
+        // each rule's best device time and its planning time, for the caller's record
+        static const char* const kNames[4] = {"tune_batch_fuse0", "tune_batch_fuse1", "tune_batch_fuse2",
+                                              "tune_batch_fuse3"};
+        static const char* const kPlan[4] = {"tune_batch_plan0", "tune_batch_plan1", "tune_batch_plan2",
+                                             "tune_batch_plan3"};
+        gace_ctx::KStat& k = ctx->stats[kNames[mode]];
         k.launches++;
         k.ms += mode_ms;
+        gace_ctx::KStat& kp = ctx->stats[kPlan[mode]];
+        kp.launches++;
+        kp.ms += plan_ms;
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
@@ -1145,7 +1169,7 @@ gace_status gace_tune_load(gace_ctx* ctx, const char* path) {
         unsigned long long chunk = 0;
         double ms = 0;
         if (sscanf(line.c_str(), " {\"requests_log2\": %d, \"rows_log2\": %d, \"fuse\": %d", &jl, &ul, &mode) == 3) {
-            if (mode >= 0 && mode <= 2) ctx->fuse_tune[{jl, ul}] = mode;
+            if (mode >= 0 && mode <= 3) ctx->fuse_tune[{jl, ul}] = mode;
             continue;
         }
         if (sscanf(line.c_str(), " {\"jobs_log2\": %d, \"units_log2\": %d, \"chunk\": %llu, \"ctas_per_sm\": %d, \"ms\": %lf",

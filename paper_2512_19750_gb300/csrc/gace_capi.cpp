@@ -1007,7 +1007,7 @@ void build_rank_tree(RankCode& rc) {
 
 // Bucket of key distance d (RankArgs): linear buckets of 2^smin keys up to
 // 2^(smin + mbits + 1), then 2^mbits buckets per doubling of d.
-uint64_t rank_bucket(uint64_t d, uint32_t smin, uint32_t mbits) {
+static inline uint64_t rank_bucket(uint64_t d, uint32_t smin, uint32_t mbits) {
     const int len = d ? 64 - __builtin_clzll(d) : 0;
     const uint32_t s = std::max<int>(static_cast<int>(smin), len - static_cast<int>(mbits) - 1);
     return (static_cast<uint64_t>(s - smin) << mbits) + (d >> s);
@@ -1053,9 +1053,12 @@ void build_rank_buckets(RankCode& rc, uint32_t search) {
     const uint64_t start_words = rank_start_words(static_cast<uint32_t>(best.nb));
     std::vector<uint32_t> words(start_words + nends * (is64 ? 2 : 1), 0u);
     uint16_t* start = reinterpret_cast<uint16_t*>(words.data());
+    std::vector<uint32_t> bucket(m);  // each endpoint's bucket (non-decreasing)
+    for (uint32_t k = 0; k < m; ++k)
+        bucket[k] = static_cast<uint32_t>(rank_bucket(rc.keys[k] - base, best.smin, best.mbits));
     uint32_t i = 0;
     for (uint64_t b = 0; b < best.nb; ++b) {  // first endpoint at or after bucket b
-        while (i < m && rank_bucket(rc.keys[i] - base, best.smin, best.mbits) < b) ++i;
+        while (i < m && bucket[i] < b) ++i;
         start[b] = static_cast<uint16_t>(i);
     }
     uint32_t* ends = words.data() + start_words;
@@ -1078,7 +1081,10 @@ void build_rank_buckets(RankCode& rc, uint32_t search) {
 }
 
 gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r, bool force_wide,
-                       ProbePlan& plan, uint32_t wide_warps, bool rank_code) {
+                       ProbePlan& plan, uint32_t wide_warps, bool rank_code, bool trace) {
+    auto phase = [&](const char* name) {
+        if (trace) ctx->host_phase(name);
+    };
     plan = ProbePlan();
     plan.tab = &tab;
     const uint32_t nsamples = r.nsamples, nterms = r.nterms, npreds = r.npreds;
@@ -1128,6 +1134,7 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
         sets.push_back(c);
     }
 
+    phase("host_plan_sets");
     // normalise and deduplicate terms
     std::vector<NTerm>& uterms = plan.uterms;
     std::unordered_map<NTerm, uint32_t, NTermHash> dedup;
@@ -1180,6 +1187,7 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
     }
     plan.want_marg = r.term_marginals != nullptr || any_pair;
 
+    phase("host_plan_terms");
     // rank coding: every column's distinct range endpoints over the whole plan
     plan.code_of_col.assign(tab.cols.size(), -1);
     // ranks pay for their pre-pass when several wide passes read them: a
@@ -1276,6 +1284,7 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
         }
     }
 
+    phase("host_plan_rank");
     // pack predicates into passes that fit the kernel's shared-memory tables
     std::vector<Pass>& passes = plan.passes;
     std::vector<int32_t> u_pass(uterms.size(), -1);
@@ -1420,6 +1429,7 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
         }
         flush();
     }
+    phase("host_plan_pack");
     bool need_ns = false;
     for (auto& s : sets)
         if (s.d.mode == 2) need_ns = true;
@@ -1434,6 +1444,7 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
             return st;
         pass_sizes(ps);
     }
+    phase("host_plan_build");
     return GACE_OK;
 }
 
@@ -1658,6 +1669,7 @@ gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts, TableRe
                                        ctx->stream));
     }
     CK(cudaMemsetAsync(dws + status_off, 0, 256, ctx->stream));
+    ctx->host_phase("host_probe_stage");
     uint64_t nload = 0;  // chunks of the pending copy
     if (lazy) {
         // every chunk's copy on the copy stream, all at once (they run back to
@@ -1745,7 +1757,9 @@ gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts, TableRe
     }
     const uint64_t rb_hi = any_pass ? io_end : status_off + 256;
     CK(cudaMemcpyAsync(pin + status_off, dws + status_off, rb_hi - status_off, cudaMemcpyDeviceToHost, ctx->stream));
+    ctx->host_phase("host_probe_launch");
     CK(cudaStreamSynchronize(ctx->stream));
+    ctx->host_phase("host_probe_wait");
     ctx->collect();
     if (lazy) lazy->pending.clear();  // the stream waited for every chunk's copy
     if (gace_status st = read_status(ctx, *reinterpret_cast<unsigned int*>(pin + status_off))) return st;
@@ -1758,6 +1772,7 @@ gace_status run_planned(gace_ctx* ctx, std::vector<PlannedProbe>& parts, TableRe
         for (auto& ps : pp.plan.passes) outs.push_back(reinterpret_cast<const unsigned long long*>(pin + ps.out_off));
         assemble_probe(pp.plan, pp.r, outs);
     }
+    ctx->host_phase("host_probe_finish");
     return GACE_OK;
 }
 
@@ -2002,6 +2017,7 @@ gace_status gace_probe_batch(gace_ctx* ctx, uint32_t table_id, const gace_sample
     r.term_marginals = term_marginals;
     if (gace_status s = check_probe_request(r)) return s;
     std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->phase_t = std::chrono::steady_clock::now();
     TableRec* tab = find_table_raw(ctx, table_id);  // a pending copy may overlap the probe
     if (!tab) return fail(GACE_ENOTFOUND, "table %u is not loaded", table_id);
     DeviceGuard g(ctx->device);
@@ -2026,7 +2042,8 @@ gace_status gace_probe_batch(gace_ctx* ctx, uint32_t table_id, const gace_sample
         parts.emplace_back();
         parts.back().tab = tab;
         parts.back().r = r;
-        if (gace_status st = plan_probe(ctx, *tab, r, false, parts.back().plan, kWideWarps, true)) return st;
+        if (gace_status st = plan_probe(ctx, *tab, r, false, parts.back().plan, kWideWarps, true, true)) return st;
+        ctx->host_phase("host_probe_plan");
         return run_planned(ctx, parts, tab->pending.empty() ? nullptr : tab);
     }
     if (gace_status st = complete_load(ctx, *tab)) return st;
@@ -2064,8 +2081,9 @@ gace_status gace_probe_batch(gace_ctx* ctx, uint32_t table_id, const gace_sample
         pp.r.nsamples = ns;
         pp.r.results = npreds ? pres[i].data() : nullptr;
         pp.r.term_marginals = term_marginals ? pmarg[i].data() : nullptr;
-        if (gace_status st = plan_probe(ctx, *pp.tab, pp.r, false, pp.plan, kWideWarps, true)) return st;
+        if (gace_status st = plan_probe(ctx, *pp.tab, pp.r, false, pp.plan, kWideWarps, true, true)) return st;
     }
+    ctx->host_phase("host_probe_plan");
     if (gace_status st = run_planned(ctx, parts)) return st;
     for (size_t i = 0; i < order.size(); ++i) {
         const bool resident = order[i] != table_id;

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <chrono>
 #include <condition_variable>
 #include <functional>
 #include <limits>
@@ -240,6 +241,18 @@ struct gace_ctx {
         if (b) cudaEventRecord(b, stream);
         if (a && b) pending.push_back({name, a, b, bytes, ops});
         return e;
+    }
+
+    // Host phases of a call (when timing): the wall time since phase_t into
+    // stats[name] (launches = phases recorded), then phase_t restarts.
+    std::chrono::steady_clock::time_point phase_t;
+    void host_phase(const char* name) {
+        if (!timing) return;
+        const auto now = std::chrono::steady_clock::now();
+        KStat& k = stats[name];
+        k.launches++;
+        k.ms += std::chrono::duration<double, std::milli>(now - phase_t).count();
+        phase_t = now;
     }
 
     // After a stream synchronisation: fold event pairs into the statistics.
@@ -557,8 +570,11 @@ gace_status check_probe_request(const ProbeRequest& r);
 // for the synchronous kernel, kProbeWarps for the batched form's).
 // rank_code: the wide passes read the range terms of columns with at most
 // kRankPlanMax endpoints by the rows' ranks (run_planned computes them).
+// trace: the planner's phases go to the context's statistics when it times
+// (host_plan_sets, _terms, _rank, _pack, _build; only from a caller that
+// holds the context's mutex and plans on one thread).
 gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r, bool force_wide,
-                       ProbePlan& plan, uint32_t wide_warps, bool rank_code = false);
+                       ProbePlan& plan, uint32_t wide_warps, bool rank_code = false, bool trace = false);
 // Bytes of a pass's inputs (terms, pool, predicate CSR) and outputs (counters).
 void pass_sizes(Pass& ps);
 // Copies a pass's inputs into pinned staging at ps.in_off and points its
@@ -660,6 +676,32 @@ struct JobRec {
 
 // A compiled request: its plan and where its data sits in the arena
 // (offsets relative to the input, small-output and big-output regions).
+// The sides of a join request, allocated at their first use: a batch builds
+// one plan per request and most requests are not joins (three sides take
+// 5.5 KB, most of a plan).
+struct JoinSides {
+    std::unique_ptr<SideArgs[]> p;
+    SideArgs& operator[](int i) {
+        if (!p) p.reset(new SideArgs[3]());
+        return p[i];
+    }
+    const SideArgs& operator[](int i) const { return p[i]; }
+    JoinSides() = default;
+    JoinSides(JoinSides&&) = default;
+    JoinSides& operator=(JoinSides&&) = default;
+    JoinSides(const JoinSides& o) { *this = o; }
+    JoinSides& operator=(const JoinSides& o) {
+        if (this != &o) {
+            p.reset();
+            if (o.p) {
+                p.reset(new SideArgs[3]());
+                for (int i = 0; i < 3; ++i) p[i] = o.p[i];
+            }
+        }
+        return *this;
+    }
+};
+
 struct ReqPlan {
     gace_status status = GACE_OK;
     std::string error;
@@ -675,7 +717,7 @@ struct ReqPlan {
     TableRec* tab = nullptr;
     // join
     gace_join spec{};
-    SideArgs side[3]{};
+    JoinSides side;
     SideWork work[3]{};
     TableRec* tabs[3]{};
     uint32_t fk2_slot = 0;
@@ -713,8 +755,10 @@ struct FusedProbe {
     // Fusion rules: 0, the rules of fits() below (a one-predicate request on
     // one row set runs alone); 1, such requests fuse too; 2, as 1, and a group
     // takes the union of its members' row sets (at most kMaxSets) and of their
-    // columns (at most kMaxRowBytes per row).  The batch autotuner picks one
-    // per batch shape.
+    // columns (at most kMaxRowBytes per row); 3, only such requests on a
+    // hashed row sample fuse (then one hash per row serves the group), with
+    // the same row sets and the union of their columns.  The batch autotuner
+    // picks one per batch shape.
     int mode = 0;
 
     static constexpr uint32_t kMaxIn = 1024;     // IN values of all members

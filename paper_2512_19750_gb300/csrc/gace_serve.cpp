@@ -69,7 +69,8 @@ constexpr uint64_t kItemsPerCta = 2;
 constexpr size_t kDirectCopies = 2;             // at most this many blocks moved by plain copies per step
 constexpr uint64_t kDirectBlockMax = 256u << 10;
 constexpr uint64_t kSpinNs = 500000;            // busy-wait on a step's completion before sleeping
-constexpr uint64_t kIdleSpinNs = 2000000;       // an idle scheduler watches the queue this long before sleeping
+constexpr uint64_t kIdleSpinUs = 10000;         // an idle scheduler watches the queue this long before sleeping
+                                                // (gace_serve_config.idle_spin_us = 0)
 
 uint64_t now_ns() {
     return static_cast<uint64_t>(std::chrono::duration_cast<std::chrono::nanoseconds>(
@@ -1079,7 +1080,8 @@ void ServeState::run() {
                 // (tens of microseconds, most of a small probe's latency).
                 lk.unlock();
                 const uint64_t t0 = now_ns();
-                while (npending.load(std::memory_order_relaxed) == 0 && now_ns() - t0 < kIdleSpinNs)
+                const uint64_t spin_ns = (cfg.idle_spin_us ? cfg.idle_spin_us : kIdleSpinUs) * 1000ull;
+                while (npending.load(std::memory_order_relaxed) == 0 && now_ns() - t0 < spin_ns)
                     std::this_thread::yield();
                 lk.lock();
                 if (!pending.empty() || stop) continue;
@@ -1480,6 +1482,36 @@ gace_status gace_serve_replay(gace_ctx* ctx, const gace_request* reqs, uint32_t 
     }
     for (uint32_t i = 0; i < n; ++i)
         if (st[i] != GACE_OK) return st[i];
+    return GACE_OK;
+}
+
+gace_status gace_run_plain_async(gace_ctx* const* ctxs, uint32_t nctx, const gace_request* reqs, uint32_t n,
+                                 gace_status* statuses) {
+    if (nctx == 0 || !ctxs) return fail(GACE_EINVAL, "ctxs is NULL or nctx is 0");
+    if (n && !reqs) return fail(GACE_EINVAL, "reqs is NULL");
+    for (uint32_t k = 0; k < nctx; ++k)
+        if (gace_status s = check_ctx(ctxs[k])) return s;
+    std::vector<gace_status> local(statuses ? 0 : n);
+    gace_status* st = statuses ? statuses : local.data();
+    // context k's requests k, k + nctx, ... in order, on a thread of its own;
+    // each call waits for its own stream only, so calls on different
+    // contexts overlap on the GPU
+    std::vector<std::string> first_error(nctx);
+    auto lane = [&](uint32_t k) {
+        for (uint32_t i = k; i < n; i += nctx) {
+            st[i] = run_plain(ctxs[k], reqs[i]);
+            if (st[i] != GACE_OK && first_error[k].empty()) first_error[k] = gace_last_error();
+        }
+    };
+    std::vector<std::thread> threads;
+    for (uint32_t k = 1; k < nctx; ++k) threads.emplace_back(lane, k);
+    lane(0);
+    for (std::thread& t : threads) t.join();
+    for (uint32_t i = 0; i < n; ++i)
+        if (st[i] != GACE_OK) {
+            set_last_error_message(("request " + std::to_string(i) + ": " + first_error[i % nctx]).c_str());
+            return st[i];
+        }
     return GACE_OK;
 }
 

@@ -215,10 +215,11 @@ def _set_fusion_rule(g, ctx, tables, reqs, n, mode, tmp_path):
     g.gace_tune_load(ctx, str(path))
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_every_fusion_rule_gives_the_same_results(g, batched, tmp_path, mode):
     """Under each fusion rule (one-predicate probes alone; fused too; groups
-    with the union of their members' row sets and columns) every request of
+    with the union of their members' row sets and columns; fused only on a
+    shared row sample, with the union of their columns) every request of
     the mixed batch (planned on the host workers: more than 64 requests)
     gives what its synchronous call gives."""
     tables, reqs, _ = batched
@@ -233,10 +234,10 @@ def test_every_fusion_rule_gives_the_same_results(g, batched, tmp_path, mode):
         g.gace_destroy(ctx)
 
 
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [1, 2, 3])
 def test_fusion_rules_on_one_table(g, batched, tmp_path, mode):
     """One-predicate probes on one row set, and probes on different row sets
-    and columns, fused on one table under rules 1 and 2: each member's counts,
+    and columns, fused on one table under rules 1, 2 and 3: each member's counts,
     selectivities, PCS and marginals equal its synchronous call's."""
     tables, _, _ = batched
     t = tables[3]
@@ -266,3 +267,24 @@ def test_fusion_rules_on_one_table(g, batched, tmp_path, mode):
                 assert np.array_equal(q.marginals, marg)
     finally:
         g.gace_destroy(ctx)
+
+
+def test_plain_async_equals_synchronous_calls(g, gctx, batched):
+    """The plain path with its calls spread over three contexts (one host
+    thread and stream each, request i on context i % 3, each context holding
+    the same borrowed columns): every request gives what its synchronous call
+    gives, and a bad request fails alone."""
+    tables, reqs, tids = batched
+    ctxs = [g.gace_create(0) for _ in range(3)]
+    try:
+        ctids = [[g.gace_load_columns(c, t.columns, borrow=True) for t in tables] for c in ctxs]
+        sub = reqs[:90]
+        per = [_to_requests(g, ctids[i % 3], tables, [r])[0] for i, r in enumerate(sub)]
+        assert g.gace_run_plain_async(ctxs, per) == [0] * len(sub)
+        _check_against_sync(g, gctx, tids, tables, sub, per)
+        bad = g.NdvRequest(12345, 0, 12, 1)
+        st = g.gace_run_plain_async(ctxs, per[:4] + [bad] + per[4:8])
+        assert st[4] == g.GACE_ENOTFOUND and st[:4] + st[5:] == [0] * 8
+    finally:
+        for c in ctxs:
+            g.gace_destroy(c)

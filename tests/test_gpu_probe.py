@@ -357,3 +357,26 @@ def test_block_samples_skip_tiles(g, gctx, orc, cuda, samples, npreds):
             check_probe(g, orc, gctx, tid, host_columns(t), t.dtypes, preds, samples)
         finally:
             g.gace_unload(gctx, tid)
+
+
+@pytest.mark.parametrize("n", [1000, 65537, 1_000_003])
+def test_single_predicate_sparse_row_samples(g, gctx, orc, cuda, n):
+    """One predicate of 1-4 terms over int32, int64 and float32 columns on one
+    sparse row sample (the single-predicate evaluation with per-row hashing):
+    counts, sample sizes and marginals equal the oracle's at every rate, on
+    ragged tails."""
+    rng = np.random.default_rng(n)
+    c0 = rng.integers(-1000, 1000, n).astype(np.int32)
+    c1 = rng.integers(-2**40, 2**40, n).astype(np.int64)
+    c2 = rng.standard_normal(n).astype(np.float32)
+    c3 = rng.integers(0, 50, n).astype(np.int32)
+    cols, dtypes = [c0, c1, c2, c3], [I32, I64, F32, I32]
+    terms = [Term(0, RANGE, -300, 400), Term(1, RANGE, -2**39, 2**39), Term(2, RANGE, -1.0, 0.5),
+             Term(3, IN, values=(1, 3, 5, 7, 11, 13)), Term(0, EQ, 17)]
+    tid = g.gace_load_columns(gctx, [torch.as_tensor(c, device=cuda) for c in cols])
+    try:
+        for k, pred in enumerate([terms[:1], terms[1:2], terms[2:3], terms[:4], [terms[4]], [terms[1], terms[3]]]):
+            for rate in (0.001, 0.01, 1 / 32, 0.05):
+                check_probe(g, orc, gctx, tid, cols, dtypes, [pred], [Sample(ROWS, rate, 7 + k)])
+    finally:
+        g.gace_unload(gctx, tid)
