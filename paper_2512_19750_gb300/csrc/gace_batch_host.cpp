@@ -402,7 +402,7 @@ void emit_jobs(ReqPlan& rp, unsigned char* dws, unsigned int* batch_status, std:
         jr.units = rp.hll.nrows;
         // shared-memory registers: 32-bit up to p = 14, one byte for p = 15, 16
         jr.smem = rp.hll.p <= 14 ? (4u << rp.hll.p) : rp.hll.p <= 16 ? (1u << rp.hll.p) : 0u;
-        jr.cost = 4;  // two 64-bit multiplies and a register update per row
+        jr.cost = 2;  // a 64-bit hash and a register check per row
         jr.family = "batch_hll";
         jr.rows = jr.units;
         jr.bytes = jr.units * dtype_width(static_cast<int>(rp.hll.dtype));

@@ -1226,8 +1226,13 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
                 }
             }
         }
-        for (uint32_t c = 0; c < ncols; ++c) {
-            RankCode rc;
+        // each column's code (its endpoints sorted, their search tree or
+        // bucket index): independent per column, so on the context's host
+        // workers (the caller holds the context's mutex)
+        std::vector<RankCode> percol(ncols);
+        std::vector<uint8_t> coded(ncols, 0);
+        auto code_col = [&](uint32_t c) {
+            RankCode& rc = percol[c];
             if (!all[c].distinct.empty() && all[c].distinct.size() <= kRankPlanMax) {
                 rc.keys = all[c].distinct;
                 rc.all_terms = true;
@@ -1235,7 +1240,7 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
                 std::vector<uint64_t>& e = rng[c];
                 std::sort(e.begin(), e.end());
                 e.erase(std::unique(e.begin(), e.end()), e.end());
-                if (e.empty() || e.size() > kRankPlanMax) continue;
+                if (e.empty() || e.size() > kRankPlanMax) return;
                 rc.keys = std::move(e);
                 all[c].init(rc.keys.size());
                 for (uint64_t k : rc.keys) all[c].insert(k);
@@ -1250,8 +1255,16 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
             // shared-memory counter per set and rank
             rc.hist_fits = rc.tree.size() * 4 + sets.size() * (rc.keys.size() + 1) * 4 <= kRankHistSmem;
             rc.hist = plan.want_marg && rc.hist_fits;
+            coded[c] = 1;
+        };
+        if (ncols >= 2)
+            ctx->workers.run(static_cast<uint32_t>(ncols), code_col);
+        else
+            for (uint32_t c = 0; c < ncols; ++c) code_col(c);
+        for (uint32_t c = 0; c < ncols; ++c) {
+            if (!coded[c]) continue;
             plan.code_of_col[c] = static_cast<int32_t>(plan.codes.size());
-            plan.codes.push_back(std::move(rc));
+            plan.codes.push_back(std::move(percol[c]));
         }
         // each coded term's intervals as column endpoint indices: an
         // interval [lo, hi] holds the endpoints from lo's index up to that of

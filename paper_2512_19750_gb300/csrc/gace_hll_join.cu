@@ -22,6 +22,7 @@
 
 #include "gace_device.cuh"
 #include "gace_internal.h"
+#include "gace_launch.cuh"
 #include "gace_side_dev.cuh"
 
 namespace gace {
@@ -194,8 +195,7 @@ template <int REGS, int DT>
 static cudaError_t hll_launch_t(const HllArgs& a, int sms, cudaStream_t s) {
     const uint64_t groups = (a.nrows + 3) / 4;
     const uint32_t smem = REGS == kHllWords ? (4u << a.p) : REGS == kHllBytes ? (1u << a.p) : 0u;
-    cudaError_t e = cudaFuncSetAttribute(k_hll<REGS, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    cudaError_t e = smem_allow_max<k_hll<REGS, DT>>();
     if (e != cudaSuccess) return e;
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_hll<REGS, DT>, kHllThreads, smem);
@@ -228,8 +228,7 @@ static cudaError_t staged_launch_t(const SideArgs& a, int sms, cudaStream_t s, u
                                  const void* weight, unsigned long long* out_sum, uint32_t fk2_slot, uint64_t domain2,
                                  unsigned long long* w64) {
     const uint32_t smem = a.smem_bytes + (MODE == 0 && AGG && kHotCache ? 8u << kHotLog : 0u);
-    cudaError_t e = cudaFuncSetAttribute(k_side_staged<MODE, AGG, KEY64, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    cudaError_t e = smem_allow_max<k_side_staged<MODE, AGG, KEY64, NQ>>();
     if (e != cudaSuccess) return e;
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_side_staged<MODE, AGG, KEY64, NQ>, kJoinThreads, smem);
@@ -268,8 +267,9 @@ cudaError_t hist_launch(const SideArgs& a, uint32_t* hist, int strict, int aggre
     if (GACE_HIST_STAGED && aggregate && a.domain <= kSmemHistMax && a.nrows >= 4 * a.domain * 16 &&
         a.stage_bytes && a.tile_rows % (128u * (kHistThreads / 32)) == 0) {
         const uint32_t smem = a.smem_bytes + static_cast<uint32_t>(a.domain) * 4u;
-        auto kern = a.slot_dtype[a.key_slot] == 1 ? k_hist_smem_staged<true> : k_hist_smem_staged<false>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        const bool key64 = a.slot_dtype[a.key_slot] == 1;
+        auto kern = key64 ? k_hist_smem_staged<true> : k_hist_smem_staged<false>;
+        cudaError_t e = key64 ? smem_allow_max<k_hist_smem_staged<true>>() : smem_allow_max<k_hist_smem_staged<false>>();
         if (e != cudaSuccess) return e;
         uint64_t want = a.nrows / (4 * a.domain);
         if (want > a.ntiles) want = a.ntiles;
@@ -279,8 +279,7 @@ cudaError_t hist_launch(const SideArgs& a, uint32_t* hist, int strict, int aggre
     }
     if (aggregate && a.domain <= kSmemHistMax && a.nrows >= 4 * a.domain * 16) {
         const uint32_t smem = static_cast<uint32_t>(a.domain) * 4u;
-        cudaError_t e = cudaFuncSetAttribute(k_hist_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(smem));
+        cudaError_t e = smem_allow_max<k_hist_smem>();
         if (e != cudaSuccess) return e;
         const uint64_t want = a.nrows / (4 * a.domain);
         const int grid = static_cast<int>(want < static_cast<uint64_t>(sms) ? want : sms);

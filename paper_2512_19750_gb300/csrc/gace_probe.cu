@@ -30,6 +30,7 @@
 
 #include "gace_device.cuh"
 #include "gace_internal.h"
+#include "gace_launch.cuh"
 #include "gace_probe_dev.cuh"
 #include "gace_probe_narrow.cuh"
 
@@ -319,8 +320,7 @@ uint32_t rank_smem(const RankArgs& a) {
 template <bool BUCKET>
 static cudaError_t rank_launch_t(const RankArgs& a, int sms, cudaStream_t s) {
     const uint32_t smem = rank_smem(a);
-    cudaError_t e = cudaFuncSetAttribute(k_probe_rank<BUCKET>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    cudaError_t e = smem_allow_max<k_probe_rank<BUCKET>>();
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_rank<BUCKET>, 256, smem);

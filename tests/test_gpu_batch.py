@@ -288,3 +288,25 @@ def test_plain_async_equals_synchronous_calls(g, gctx, batched):
     finally:
         for c in ctxs:
             g.gace_destroy(c)
+
+
+def test_plain_async_concurrent_sketches_of_different_sizes(g, batched):
+    """Sketches of p = 12 and p = 14 (16 KB and 64 KB of shared registers)
+    launched at once from four contexts on four host threads: every call
+    succeeds (each kernel's shared-memory limit is set once, to the device's
+    maximum, not per launch to the launch's own size, which another thread's
+    launch could undercut) and gives its synchronous call's registers."""
+    tables, _, _ = batched
+    ctxs = [g.gace_create(0) for _ in range(4)]
+    try:
+        ctids = [[g.gace_load_columns(c, t.columns, borrow=True) for t in tables] for c in ctxs]
+        for _ in range(3):
+            reqs = [g.NdvRequest(ctids[i % 4][i % len(tables)], 0, 12 if (i // 4) % 2 else 14, 5)
+                    for i in range(160)]
+            assert g.gace_run_plain_async(ctxs, reqs) == [0] * len(reqs)
+            for i in range(0, len(reqs), 37):
+                regs, est = g.gace_ndv(ctxs[0], ctids[0][i % len(tables)], 0, 12 if (i // 4) % 2 else 14, 5)
+                assert np.array_equal(reqs[i].registers, regs) and reqs[i].estimate == est
+    finally:
+        for c in ctxs:
+            g.gace_destroy(c)
