@@ -1137,6 +1137,7 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
     phase("host_plan_sets");
     // normalise and deduplicate terms
     std::vector<NTerm>& uterms = plan.uterms;
+    uterms.reserve(nterms);
     std::unordered_map<NTerm, uint32_t, NTermHash> dedup;
     dedup.reserve(nterms);
     plan.t2u.assign(nterms, 0);
@@ -1151,12 +1152,9 @@ gace_status plan_probe(gace_ctx* ctx, const TableRec& tab, const ProbeRequest& r
             plan.t2u[t] = UINT32_MAX;
             continue;
         }
-        auto it = dedup.find(n);
-        if (it == dedup.end()) {
-            it = dedup.emplace(n, static_cast<uint32_t>(uterms.size())).first;
-            uterms.push_back(n);
-        }
-        plan.t2u[t] = it->second;
+        const auto ins = dedup.try_emplace(n, static_cast<uint32_t>(uterms.size()));
+        if (ins.second) uterms.push_back(std::move(n));
+        plan.t2u[t] = ins.first->second;
     }
     // predicates: 0 device, 1 never true, 2 always true (no terms)
     plan.pstate.assign(npreds, 0);
