@@ -513,6 +513,11 @@ typedef struct {
 /* Never run a request alone through its synchronous call: every request goes
  * through the steps (tests of the batching machinery). */
 #define GACE_SERVE_ALWAYS_STEP 1u
+/* Fuse admitted one-predicate probes on one table that share a hashed row
+ * sample (then one hash per row serves the group, with the union of their
+ * columns), as the batched form's fusion rule 3 does; without it such probes
+ * run alone.  Changes no result. */
+#define GACE_SERVE_FUSE_SAMPLES 2u
 
 /* Starts the scheduler (cfg may be NULL: defaults); its arena counts against
  * the context's HBM budget.  GACE_EBUSY when it is already running: stop it

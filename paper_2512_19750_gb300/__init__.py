@@ -415,10 +415,11 @@ _SUBMITTED: dict = {}  # (context, ticket) -> request object whose outputs are p
 
 def gace_serve_start(ctx, arena_bytes: int = 0, max_inflight: int = 0, sketch_cache: int = 0,
                      step_rows: int = 0, chunk_rows: int = 0, always_step: bool = False,
-                     probe_cache: int = 0, idle_spin_us: int = 0) -> None:
-    cfg = _capi.gace_serve_config(arena_bytes, max_inflight, sketch_cache, step_rows, chunk_rows,
-                                  _capi.GACE_SERVE_ALWAYS_STEP if always_step else 0, probe_cache,
-                                  idle_spin_us)
+                     probe_cache: int = 0, idle_spin_us: int = 0, fuse_samples: bool = False) -> None:
+    flags = (_capi.GACE_SERVE_ALWAYS_STEP if always_step else 0) | \
+        (_capi.GACE_SERVE_FUSE_SAMPLES if fuse_samples else 0)
+    cfg = _capi.gace_serve_config(arena_bytes, max_inflight, sketch_cache, step_rows, chunk_rows, flags,
+                                  probe_cache, idle_spin_us)
     check(lib().gace_serve_start(ctx, C.byref(cfg)), "gace_serve_start")
 
 

@@ -85,6 +85,7 @@ class gace_request(C.Structure):
 
 
 GACE_SERVE_ALWAYS_STEP = 1
+GACE_SERVE_FUSE_SAMPLES = 2
 
 
 class gace_serve_config(C.Structure):

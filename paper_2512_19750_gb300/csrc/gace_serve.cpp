@@ -298,6 +298,8 @@ struct ServeState {
     void finish(Live& lv, gace_status st, const std::string& err);
     void fail_all(gace_status st, const std::string& msg);
     int occupancy(uint32_t smem, int cls);  // CTAs of a batch kernel per SM
+    // the fusion rule of admitted probes (FusedProbe::mode)
+    int fuse_rule() const { return (cfg.flags & GACE_SERVE_FUSE_SAMPLES) ? 3 : 0; }
 };
 
 namespace {
@@ -615,6 +617,7 @@ void ServeState::admit(std::vector<std::unique_ptr<Live>>& cands, std::vector<st
         if (!grp) {
             auto fresh = std::make_unique<Live>();
             fresh->fp = std::make_unique<FusedProbe>();
+            fresh->fp->mode = fuse_rule();
             grp = fresh.get();
             groups.push_back(grp);
             units.push_back(std::move(fresh));
@@ -1329,7 +1332,7 @@ gace_status submit_request(gace_ctx* ctx, const gace_request& req, uint64_t* tic
         }
     }
     layout_request(*lv);
-    lv->fusable = fusable_probe(q) && lv->rp.plan.passes.size() <= 1;
+    lv->fusable = fusable_probe(q, srv->fuse_rule()) && lv->rp.plan.passes.size() <= 1;
     if (lv->block_bytes > srv->cfg.arena_bytes)
         return fail(GACE_ENOMEM, "the request needs %llu bytes of the %llu-byte serving arena",
                     (unsigned long long)lv->block_bytes, (unsigned long long)srv->cfg.arena_bytes);

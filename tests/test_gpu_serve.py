@@ -164,10 +164,12 @@ def test_destroy_drains_a_running_server(g, served, cuda):
     g.gace_destroy(ctx)  # waits for the queued requests, then frees the arena
 
 
-def test_fused_admission(g, sctx, served, cuda):
+@pytest.mark.parametrize("fuse_samples", [False, True])
+def test_fused_admission(g, sctx, served, cuda, fuse_samples):
     """Probes on one table that queue up while the GPU is busy are admitted
     together and run as fused requests (shared scans); each member's results
-    equal its own synchronous call's."""
+    equal its own synchronous call's.  With fuse_samples, one-predicate probes
+    on a shared row sample fuse too."""
     import torch
 
     from workloads import BLOCKS, ROWS, make_predicates
@@ -195,7 +197,12 @@ def test_fused_admission(g, sctx, served, cuda):
     for k in range(1, 12):
         cols = [1 + (k % 3)] if k % 2 else [1, 2 + (k % 2)]
         specs.append(([[rng_term(c, k) for c in cols], [rng_term(cols[0], k + 1)]], shared, bool(k % 3)))
-    g.gace_serve_start(sctx, step_rows=4096, chunk_rows=4096, always_step=True, probe_cache=-1)
+    # one-predicate probes on a row sample (fused under fuse_samples)
+    for k in range(12):
+        preds = make_predicates(t, 1, 1, 4, seed=700 + k)
+        specs.append((preds, [Sample(ROWS, 0.01, 42) if k % 3 else Sample(ROWS, 0.1, 7)], bool(k % 2)))
+    g.gace_serve_start(sctx, step_rows=4096, chunk_rows=4096, always_step=True, probe_cache=-1,
+                       fuse_samples=fuse_samples)
     try:
         hold = g.ProbeRequest(slow, [[Term(0, RANGE, 0, 1000)]], [Sample(FULL)], [I32])
         th = g.gace_submit(sctx, hold)
