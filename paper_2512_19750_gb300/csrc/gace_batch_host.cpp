@@ -1080,7 +1080,7 @@ gace_status gace_tune_batch(gace_ctx* ctx, const gace_request* in, uint32_t n_in
     for (int mode = 0; mode <= 3 && rc == GACE_OK; ++mode) {
         std::vector<ReqPlan> rps;
         std::vector<std::unique_ptr<FusedProbe>> fused;
-        // a rule is judged by the batch's planning time plus its device time
+        // a rule is ranked by the batch's planning time plus its device time
         const auto t_plan = std::chrono::steady_clock::now();
         compile_all(ctx, reqs, n, rps, fused, mode);
         const double plan_ms =
