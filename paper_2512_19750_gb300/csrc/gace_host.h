@@ -527,6 +527,11 @@ struct RankCode {
 #define GACE_RANK_PLAN_MAX 2047
 #endif
 constexpr uint32_t kRankPlanMax = GACE_RANK_PLAN_MAX;
+// A coded column's search structures from its sorted keys: the level-order
+// search tree (rc.tree, rc.levels), then, per rank_search (gace_config), the
+// bucket index in its place (rc.levels = 0, rc.b*; RankArgs).
+void build_rank_tree(RankCode& rc);
+void build_rank_buckets(RankCode& rc, uint32_t search);
 // A synchronous probe rank-codes its columns when it has more than
 // kNarrowMax predicates, at least kRankMinTerms distinct terms (more than one
 // wide pass holds) and at least kRankMinRows rows (the context's
