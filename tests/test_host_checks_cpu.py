@@ -1,0 +1,45 @@
+"""Host parts of the library checked on the CPU (no GPU), each by a small
+program built against the library: the rank pass's search structures, built
+by the planner and searched as the rank pass reads them (tests/rank_index_check.cu
+builds each coded column's level-order search tree and bucket index
+(build_rank_tree, build_rank_buckets under every rank_search setting) for
+random endpoint sets of 32- and 64-bit keys, emulates the kernel's searches
+and compares every rank with the number of endpoints <= the key), and the
+context's host worker pool (tests/host_pool_check.cu)."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+from conftest import ROOT
+
+
+def _run_host_check(g, tmp_path, name):
+    """Compiles tests/<name>.cu against the library's host headers, links it
+    with the built library and runs it; its output must start with "ok"."""
+    from paper_2512_19750_gb300 import build as b
+
+    nvcc = os.path.join(b.cuda_home(), "bin", "nvcc")
+    if not os.path.exists(nvcc):
+        nvcc = shutil.which("nvcc")
+    if not nvcc:
+        pytest.skip("nvcc is not installed")
+    exe = str(tmp_path / name)
+    lib_dir = os.path.dirname(g._capi.LIB_PATH)
+    cmd = [nvcc, "-O2", "-std=c++17", "-x", "cu", "-I", os.path.join(ROOT, "include"),
+           "-I", os.path.join(lib_dir, "csrc"), "-o", exe, os.path.join(ROOT, "tests", name + ".cu"),
+           "-L", lib_dir, "-lgace", "-Xlinker", "-rpath," + lib_dir]
+    subprocess.run(cmd, check=True, capture_output=True, timeout=600)
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0 and out.stdout.startswith("ok"), out.stdout + out.stderr
+
+
+def test_rank_tree_and_bucket_index_give_every_rank(g, tmp_path):
+    _run_host_check(g, tmp_path, "rank_index_check")
+
+
+def test_host_worker_pool_handles_every_index_once(g, tmp_path):
+    """The workers that plan and assemble a large batch (HostPool): every
+    index of every run handled exactly once, over 300 runs in a row."""
+    _run_host_check(g, tmp_path, "host_pool_check")
