@@ -4,8 +4,9 @@ by the planner and searched as the rank pass reads them (tests/rank_index_check.
 builds each coded column's level-order search tree and bucket index
 (build_rank_tree, build_rank_buckets under every rank_search setting) for
 random endpoint sets of 32- and 64-bit keys, emulates the kernel's searches
-and compares every rank with the number of endpoints <= the key), and the
-context's host worker pool (tests/host_pool_check.cu)."""
+and compares every rank with the number of endpoints <= the key), the
+context's host worker pool (tests/host_pool_check.cu) and the batched form's
+fusion rules (tests/fusion_rules_check.cu)."""
 import os
 import shutil
 import subprocess
@@ -43,3 +44,9 @@ def test_host_worker_pool_handles_every_index_once(g, tmp_path):
     """The workers that plan and assemble a large batch (HostPool): every
     index of every run handled exactly once, over 300 runs in a row."""
     _run_host_check(g, tmp_path, "host_pool_check")
+
+
+def test_fusion_rules_of_the_batched_form(g, tmp_path):
+    """Which probe requests may fuse, and with which group, under each of the
+    batched form's fusion rules, and the limits every rule keeps."""
+    _run_host_check(g, tmp_path, "fusion_rules_check")
